@@ -1,0 +1,207 @@
+/*
+ * ecmc.h -- C ABI of the GB300 parallel event-chain Monte Carlo library
+ * (libecmc.so) for two-dimensional hard disks.
+ *
+ * Method: Kampmann, Boltz, Kierfeld, "Parallelized event chain algorithm for
+ * dense hard sphere and polymer systems", arXiv:1409.6948.
+ *   Sec. 2 (eq. 1)   N hard disks of diameter sigma in a periodic L x L box.
+ *   Sec. 3.2         straight event chain: the active disk moves along d until
+ *                    it touches another disk, the rest of the displacement
+ *                    budget ell passes to the disk it hit.
+ *   Sec. 3.4         one sweep: cells on a randomly shifted square lattice,
+ *                    2x2 blocks coloured in four colours, the colours visited
+ *                    in a random order, n_m chain starts per cell drawn with
+ *                    replacement, chains reflected at the cell walls and at
+ *                    frozen disks (Fig. 1).
+ *   Sec. 2 (eq. pressure) and the collision form of the pressure noted at the
+ *                    end of Sec. 3.4: the pressure estimators.
+ *
+ * Conventions for every function:
+ *   - returns ECMC_OK (0) or a negative ECMC_ERR_* code; ecmc_strerror()
+ *     gives a message and ecmc_last_error_message() the detail of the most
+ *     recent failure on the calling thread;
+ *   - a handle is used by one host thread at a time;
+ *   - "host" pointers are ordinary (pageable or pinned) host memory,
+ *     "device" pointers are CUDA device memory of the handle's device; the
+ *     library never takes ownership of caller memory;
+ *   - positions are exchanged in disk-id order as interleaved pairs
+ *     xy[2*i] = x_i, xy[2*i+1] = y_i (float64), wrapped into [0, L).
+ *   - work is enqueued on the handle's stream (ecmc_set_stream; default: a
+ *     stream the library creates); functions that return data to the host
+ *     synchronise that stream.
+ */
+#ifndef ECMC_H
+#define ECMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define ECMC_OK 0
+#define ECMC_ERR_ARG -1         /* invalid argument or parameter combination     */
+#define ECMC_ERR_CUDA -2        /* a CUDA runtime call failed                    */
+#define ECMC_ERR_OOM -3         /* device or host allocation failed              */
+#define ECMC_ERR_OVERLAP -4     /* two disks closer than sigma (beyond rounding) */
+#define ECMC_ERR_TIMEOUT -5     /* a bounded device-side wait gave up            */
+#define ECMC_ERR_STATE -6       /* call not valid in the handle's current state  */
+#define ECMC_ERR_CAPACITY -7    /* a cell frame exceeded its capacity            */
+#define ECMC_ERR_UNSUPPORTED -8 /* option not available in this build            */
+#define ECMC_ERR_CHAIN_CAP -9   /* a chain hit the per-chain event cap           */
+
+/* ---- parameters (ecmc_set_param / ecmc_get_param) ---------------------- */
+/* Chains started per cell and sweep, n_m (Sec. 3.4 step 5).  Default:
+ * eq. (nm) of Sec. 4, n_m = max(1, round((N / cells) lambda0 / ell)) with
+ * lambda0 = sigma (eta_hcp - eta) / (2 eta_hcp). */
+#define ECMC_PARAM_N_CHAINS 1
+/* Direction rule: ECMC_DIR_PM_AXIS_ALT (default) = axis x on even sweeps and
+ * y on odd sweeps, sign drawn per chain; ECMC_DIR_POS_ONLY = sign always +
+ * (a variant that is not reversible, Sec. 3.2; kept for negative tests). */
+#define ECMC_PARAM_DIR_MODE 2
+/* Candidate geometry: ECMC_PREC_FP64 = every candidate tested in FP64;
+ * ECMC_PREC_FP32_GEOM (default) = candidates screened in FP32 cell-relative
+ * coordinates with rigorous error bounds, the contact decided in FP64.  Both
+ * give bit-identical trajectories. */
+#define ECMC_PARAM_PRECISION 3
+/* Replica number: second word of the Philox key (seed, replica). */
+#define ECMC_PARAM_REPLICA 4
+/* Lanes cooperating on one cell in the sweep kernel: 1, 2, 4, 8, 16, 32, or
+ * 0 = automatic (default). */
+#define ECMC_PARAM_LANES_PER_CELL 5
+/* Pair-correlation histogram: bin width (default 0.01 sigma) and upper edge
+ * (default 5 sigma); changing either clears the accumulated histogram. */
+#define ECMC_PARAM_GR_DR 6
+#define ECMC_PARAM_GR_RMAX 7
+/* 1 = record per-kernel CUDA-event times (ecmc_kernel_times), 0 = off. */
+#define ECMC_PARAM_TIMING 8
+/* Local bin side of the candidate search in units of sigma (>= 1.0625). */
+#define ECMC_PARAM_BIN_SIDE 9
+
+#define ECMC_DIR_PM_AXIS_ALT 0
+#define ECMC_DIR_POS_ONLY 1
+#define ECMC_PREC_FP64 0
+#define ECMC_PREC_FP32_GEOM 1
+
+typedef struct ecmc_ctx* ecmc_t;
+
+typedef struct {
+  int64_t sweeps;      /* sweeps since the last reset                           */
+  int64_t chains;      /* chains run (a cell without members starts none)       */
+  int64_t events;      /* contacts: lifts + reflections at frozen disks         */
+  int64_t lifts;       /* contacts with an active disk (budget passed on)       */
+  int64_t frozen_hits; /* contacts with a frozen disk (chain reflected)         */
+  int64_t wall_hits;   /* reflections at a cell wall (not counted as events)    */
+  int64_t fp64_evals;  /* candidates evaluated in FP64 (FP32_GEOM screening)    */
+  double sum_b;        /* sum over contacts of the separation along d           */
+  double sum_disp;     /* sum over chains of the displacement budget ell        */
+} ecmc_counters_t;
+
+typedef struct {
+  double bin_ms;       /* cell binning kernels (count, scan, scatter)           */
+  double phase_ms;     /* the four colour-phase sweep kernels                   */
+  double other_ms;     /* everything else enqueued by ecmc_sweep                */
+  int64_t bin_launches;
+  int64_t phase_launches;
+  int64_t other_launches;
+} ecmc_timing_t;
+
+/* Create a system of N disks of diameter sigma in the periodic L x L box,
+ * started on a k x k square lattice (k = sqrt(N); disk iy*k + ix at
+ * ((ix + 1/2) L/k, (iy + 1/2) L/k)), with cells_x x cells_y cells (both
+ * even and >= 2; w = L/cells_x and h = L/cells_y must exceed sigma), total
+ * chain displacement ell, Philox seed `seed`.  Sec. 2 and Sec. 3.4.
+ * Errors: ECMC_ERR_ARG (N not a perfect square or < 1, cells odd or < 2,
+ * w or h <= sigma, L/k <= sigma so the lattice would overlap, ell < 0),
+ * ECMC_ERR_CUDA, ECMC_ERR_OOM.  *out receives the handle (owned by the
+ * library until ecmc_destroy). */
+int ecmc_create(ecmc_t* out, int64_t N, double L, double sigma, int cells_x, int cells_y,
+                double ell, uint64_t seed);
+
+/* Release the handle and all its device memory.  NULL is accepted. */
+int ecmc_destroy(ecmc_t h);
+
+/* Set / query one ECMC_PARAM_* value.  ECMC_ERR_ARG for an unknown key or a
+ * value out of range. */
+int ecmc_set_param(ecmc_t h, int key, double value);
+int ecmc_get_param(ecmc_t h, int key, double* value);
+
+/* Use the caller's CUDA stream (a cudaStream_t passed as void*, or NULL for
+ * the library's own stream) for all later work.  The caller keeps ownership
+ * of the stream and must keep it alive while the handle uses it. */
+int ecmc_set_stream(ecmc_t h, void* stream);
+
+/* Replace the configuration by the 2N values at xy (interleaved, id order;
+ * device memory if on_device != 0, else host memory) and set the sweep
+ * counter to t0 (the Philox counter of the next sweep).  Values are wrapped
+ * into [0, L).  Errors: ECMC_ERR_ARG (NULL, t0 < 0). */
+int ecmc_set_positions(ecmc_t h, const double* xy, int on_device, int64_t t0);
+
+/* Enqueue n_sweeps sweeps (Sec. 3.4 steps 1-7) on the handle's stream.
+ * Asynchronous: errors raised on the device (ECMC_ERR_CAPACITY,
+ * ECMC_ERR_CHAIN_CAP) are reported by the next synchronising call. */
+int ecmc_sweep(ecmc_t h, int64_t n_sweeps);
+
+/* Wait for the handle's stream; report device-side errors. */
+int ecmc_synchronize(ecmc_t h);
+
+/* Copy the configuration out (2N doubles, interleaved, id order) into
+ * caller memory (device if on_device != 0). */
+int ecmc_positions(ecmc_t h, double* xy_out, int on_device);
+
+/* Current sweep counter (the Philox counter of the next sweep). */
+int ecmc_sweep_index(ecmc_t h, int64_t* t);
+
+/* Counters accumulated since creation or the last ecmc_reset_stats. */
+int ecmc_counters(ecmc_t h, ecmc_counters_t* out);
+
+/* Clear counters, pressure accumulators and the pair histogram. */
+int ecmc_reset_stats(ecmc_t h);
+
+/* Pressure from the collision sums since the last reset:
+ * beta P sigma^2 = rho sigma^2 (1 + sum_b / sum_disp) (collision form of
+ * eq. pressure).  stderr_out (may be NULL) is the standard error from batch
+ * means over the sweeps since the reset (0 if fewer than 2 sweeps).
+ * ECMC_ERR_STATE if no chain has run since the reset. */
+int ecmc_pressure(ecmc_t h, double* betaP_sigma2, double* stderr_out);
+
+/* Add the pair histogram of the current configuration to the accumulated
+ * one: ordered pairs with sigma + i dr <= d < sigma + (i+1) dr (Sec. 2). */
+int ecmc_gr_measure(ecmc_t h);
+
+/* Accumulated counts (int64[nbins]) and number of measurements.
+ * ECMC_ERR_ARG if nbins differs from the configured bin count. */
+int ecmc_gr_counts(ecmc_t h, int64_t* counts, int nbins, int64_t* n_meas);
+
+/* Normalised g(R_i) = <n(r_i)> / (N rho 2 pi R_i dr) with the area-weighted
+ * radius R_i = 2 (e1^3 - e0^3) / (3 (e1^2 - e0^2)) of each bin (Sec. 2);
+ * r_out (may be NULL) receives R_i. */
+int ecmc_gr(ecmc_t h, double* g_out, double* r_out, int nbins);
+
+/* Number of histogram bins for the current GR_DR / GR_RMAX. */
+int ecmc_gr_nbins(ecmc_t h, int* nbins);
+
+/* Smallest minimum-image pair distance of the current configuration among
+ * pairs closer than 2 sigma (2 sigma if none). */
+int ecmc_min_distance(ecmc_t h, double* dmin);
+
+/* Cell of every disk (by id) used by the most recent sweep, cy*cells_x+cx. */
+int ecmc_last_cells(ecmc_t h, int32_t* cell_of_id);
+
+/* Per-kernel times accumulated while ECMC_PARAM_TIMING is 1. */
+int ecmc_kernel_times(ecmc_t h, ecmc_timing_t* out);
+
+/* Message for an error code (static string). */
+const char* ecmc_strerror(int code);
+
+/* Detail of the most recent failure on the calling thread (static buffer). */
+const char* ecmc_last_error_message(void);
+
+/* Library version string. */
+const char* ecmc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ECMC_H */

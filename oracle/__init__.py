@@ -1,0 +1,225 @@
+"""Python access to the oracle: the plain sequential FP64 C implementation of
+the parallel event-chain sweep (Kampmann, Boltz, Kierfeld, arXiv:1409.6948).
+
+TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` use this module; the product library never does.
+Everything here is argument marshalling around ``liboracle.so``; the
+arithmetic is in ``ecmc_oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+
+from . import build as _build
+
+DIR_PM_AXIS_ALT = 0
+DIR_POS_ONLY = 1
+DIR_ISOTROPIC = 2
+LIST_WITH_REPL = 0
+LIST_WITHOUT_REPL = 1
+FLAG_NO_SHIFT = 1
+FLAG_BRUTE_FROZEN = 2
+FLAG_REVERSE_CELLS = 4
+FLAG_FIXED_COLOURS = 8
+FLAG_SPECULAR_AXIS = 16
+
+
+class Params(C.Structure):
+    _fields_ = [("N", C.c_int64), ("L", C.c_double), ("sigma", C.c_double),
+                ("cells_x", C.c_int), ("cells_y", C.c_int), ("ell", C.c_double),
+                ("n_m", C.c_int), ("seed", C.c_uint64), ("replica", C.c_uint64),
+                ("dir_mode", C.c_int), ("list_mode", C.c_int), ("flags", C.c_uint)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("sweeps", C.c_int64), ("chains", C.c_int64), ("events", C.c_int64),
+                ("lifts", C.c_int64), ("frozen_hits", C.c_int64), ("wall_hits", C.c_int64),
+                ("capped", C.c_int64), ("sum_b", C.c_double), ("sum_disp", C.c_double),
+                ("sum_b_w", C.c_double), ("sum_disp_w", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+CHAIN_REC = np.dtype([("start_id", np.int64), ("end_id", np.int64), ("events", np.int64),
+                      ("walls", np.int64)])
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        d, i64, u64 = C.POINTER(C.c_double), C.c_int64, C.c_uint64
+        L.orc_philox4x64_10.argtypes = [C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
+                                        C.POINTER(C.c_uint64)]
+        L.orc_philox4x64_10.restype = None
+        L.orc_sweep_draws.argtypes = [C.POINTER(Params), i64, d, d, C.POINTER(C.c_int)]
+        L.orc_sweep_draws.restype = None
+        L.orc_bin.argtypes = [C.POINTER(Params), i64, d, d, C.POINTER(C.c_int32)]
+        L.orc_bin.restype = C.c_int
+        L.orc_default_nm.argtypes = [i64, C.c_double, C.c_double, C.c_int, C.c_int, C.c_double]
+        L.orc_default_nm.restype = C.c_int
+        L.orc_sweeps.argtypes = [C.POINTER(Params), d, d, i64, i64, C.POINTER(Stats), C.c_void_p]
+        L.orc_sweeps.restype = C.c_int
+        L.orc_seq_sweeps.argtypes = [i64, C.c_double, C.c_double, C.c_double, i64, u64, u64,
+                                     d, d, i64, i64, C.POINTER(Stats)]
+        L.orc_seq_sweeps.restype = C.c_int
+        L.orc_gr_counts.argtypes = [i64, C.c_double, d, d, C.c_double, C.c_double, C.c_int,
+                                    i64, i64, C.POINTER(C.c_int64)]
+        L.orc_gr_counts.restype = None
+        L.orc_min_dist2.argtypes = [i64, C.c_double, d, d, C.c_double]
+        L.orc_min_dist2.restype = C.c_double
+        L.orc_run_chain_frame.argtypes = [C.c_int, C.c_int, d, d, C.POINTER(C.c_int64),
+                                          C.POINTER(C.c_int32), C.c_double, C.c_double,
+                                          C.c_double, C.c_int, C.c_double, C.c_double,
+                                          C.c_double, C.c_int, C.POINTER(Stats), C.c_void_p]
+        L.orc_run_chain_frame.restype = C.c_int
+        L.orc_sweeps_snap.argtypes = [C.POINTER(Params), d, d, i64, i64, C.POINTER(Stats), d, d]
+        L.orc_sweeps_snap.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _dptr(a):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def philox(ctr, key):
+    c = (C.c_uint64 * 4)(*[int(v) & (2**64 - 1) for v in ctr])
+    k = (C.c_uint64 * 2)(*[int(v) & (2**64 - 1) for v in key])
+    o = (C.c_uint64 * 4)()
+    lib().orc_philox4x64_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def make_params(N, L, sigma, cells_x, cells_y, ell, n_m, seed, replica=0,
+                dir_mode=DIR_PM_AXIS_ALT, list_mode=LIST_WITH_REPL, flags=0):
+    return Params(int(N), float(L), float(sigma), int(cells_x), int(cells_y), float(ell),
+                  int(n_m), int(seed), int(replica), int(dir_mode), int(list_mode), int(flags))
+
+
+def sweep_draws(p, t):
+    sx, sy = C.c_double(), C.c_double()
+    perm = (C.c_int * 4)()
+    lib().orc_sweep_draws(C.byref(p), int(t), C.byref(sx), C.byref(sy), perm)
+    return sx.value, sy.value, list(perm)
+
+
+def bin_cells(p, t, x, y):
+    cell = np.empty(p.N, np.int32)
+    lib().orc_bin(C.byref(p), int(t), _dptr(x), _dptr(y),
+                  cell.ctypes.data_as(C.POINTER(C.c_int32)))
+    return cell
+
+
+def default_nm(N, L, sigma, cells_x, cells_y, ell):
+    return lib().orc_default_nm(int(N), float(L), float(sigma), int(cells_x), int(cells_y),
+                                float(ell))
+
+
+def sweeps(p, x, y, t0, n_sweeps, stats=None, records=False):
+    """Run n_sweeps sweeps in place on x, y (float64, id order).  Returns
+    (stats, records) where records is a structured array
+    [n_sweeps, cells, n_m] of CHAIN_REC or None."""
+    st = stats if stats is not None else Stats()
+    recs = None
+    rp = None
+    if records:
+        recs = np.zeros((n_sweeps, p.cells_x * p.cells_y, p.n_m), CHAIN_REC)
+        rp = recs.ctypes.data_as(C.c_void_p)
+    rc = lib().orc_sweeps(C.byref(p), _dptr(x), _dptr(y), int(t0), int(n_sweeps), C.byref(st), rp)
+    if rc != 0:
+        raise ValueError("oracle rejected the parameters (rc=%d)" % rc)
+    return st, recs
+
+
+def sweeps_snap(p, x, y, t0, n_sweeps, stats=None):
+    """Like sweeps(); also returns the configuration after every sweep as
+    arrays [n_sweeps, N]."""
+    st = stats if stats is not None else Stats()
+    sx = np.empty((n_sweeps, p.N))
+    sy = np.empty((n_sweeps, p.N))
+    rc = lib().orc_sweeps_snap(C.byref(p), _dptr(x), _dptr(y), int(t0), int(n_sweeps),
+                               C.byref(st), _dptr(sx), _dptr(sy))
+    if rc != 0:
+        raise ValueError("oracle rejected the parameters (rc=%d)" % rc)
+    return st, sx, sy
+
+
+def seq_sweeps(N, L, sigma, ell, n_chains, seed, replica, x, y, t0, n_sweeps, stats=None):
+    st = stats if stats is not None else Stats()
+    rc = lib().orc_seq_sweeps(int(N), float(L), float(sigma), float(ell), int(n_chains),
+                              int(seed), int(replica), _dptr(x), _dptr(y), int(t0),
+                              int(n_sweeps), C.byref(st))
+    if rc != 0:
+        raise ValueError("oracle rejected the parameters (rc=%d)" % rc)
+    return st
+
+
+def gr_counts(L, x, y, sigma, dr, nbins, i_begin=0, i_end=None, counts=None):
+    N = x.shape[0]
+    if i_end is None:
+        i_end = N
+    if counts is None:
+        counts = np.zeros(nbins, np.int64)
+    lib().orc_gr_counts(int(N), float(L), _dptr(x), _dptr(y), float(sigma), float(dr),
+                        int(nbins), int(i_begin), int(i_end),
+                        counts.ctypes.data_as(C.POINTER(C.c_int64)))
+    return counts
+
+
+def min_dist2(L, x, y, rcut=2.0):
+    return lib().orc_min_dist2(int(x.shape[0]), float(L), _dptr(x), _dptr(y), float(rcut))
+
+
+def run_chain_frame(X, Y, n_mem, m, dx, dy, ell, w, h, sigma=1.0, ids=None, imgs=None,
+                    specular=False):
+    """One chain on an explicit frame; returns (X, Y, stats, record)."""
+    X = np.ascontiguousarray(X, dtype=np.float64).copy()
+    Y = np.ascontiguousarray(Y, dtype=np.float64).copy()
+    n = X.shape[0]
+    ids = np.arange(n, dtype=np.int64) if ids is None else np.asarray(ids, np.int64)
+    imgs = np.full(n, 4, np.int32) if imgs is None else np.asarray(imgs, np.int32)
+    st = Stats()
+    rec = np.zeros(1, CHAIN_REC)
+    rc = lib().orc_run_chain_frame(n, int(n_mem), _dptr(X), _dptr(Y),
+                                   ids.ctypes.data_as(C.POINTER(C.c_int64)),
+                                   imgs.ctypes.data_as(C.POINTER(C.c_int32)), float(w), float(h),
+                                   float(sigma), int(m), float(dx), float(dy), float(ell),
+                                   int(bool(specular)), C.byref(st),
+                                   rec.ctypes.data_as(C.c_void_p))
+    if rc != 0:
+        raise ValueError("bad frame")
+    return X, Y, st, rec[0]
+
+
+def gr_normalise(counts, n_meas, N, L, sigma, dr):
+    """g(R_i) = <n(r_i)> / (N rho 2 pi R_i dr) with the area-weighted radius
+    R_i of each bin (Sec. 2); bins span [sigma + i dr, sigma + (i+1) dr)."""
+    nb = counts.shape[0]
+    e0 = sigma + dr * np.arange(nb)
+    e1 = e0 + dr
+    R = 2.0 * (e1**3 - e0**3) / (3.0 * (e1**2 - e0**2))
+    rho = N / (L * L)
+    g = (counts / float(n_meas)) / (N * rho * 2.0 * math.pi * R * dr)
+    return R, g
+
+
+def pressure_from_sums(sum_b, sum_disp, N, L, sigma):
+    """beta P sigma^2 = rho sigma^2 (1 + sum_b / sum_disp): collision form of
+    eq. (pressure)."""
+    rho = N / (L * L)
+    return rho * sigma * sigma * (1.0 + sum_b / sum_disp)
+
+
+def pressure_from_gcontact(g_contact, N, L, sigma):
+    """eq. (pressure): beta P sigma^2 = sigma^2 rho (1 + pi/2 sigma^2 rho g(sigma+))."""
+    rho = N / (L * L)
+    return sigma * sigma * rho * (1.0 + 0.5 * math.pi * sigma * sigma * rho * g_contact)
