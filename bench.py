@@ -1,0 +1,337 @@
+#!/usr/bin/env python3
+"""Benchmark of the parallel event-chain sweep for hard disks on GB300.
+
+One step = one full sweep (Sec. 3.4 steps 1-7: binning, four colour phases of
+frame staging and chains, reduction) of the workload, here 1024^2 disks at
+packing fraction 0.72 from a square lattice (the paper's large-system shape),
+seeded and synthetic.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank advances its own
+replica (Philox key (seed, rank)): independent replicas, no data exchange.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import ecmc_workloads as W  # noqa: E402
+
+METRIC = ("collision events/s, sweeps/s (N=1M, η=0.72); "
+          "batched FP32 vs FP64 at equal P error")
+UNIT = "events/s"
+# algorithmic shared-memory bytes per collision event of the chain kernel: the
+# candidates in the region the first hit can come from (about 2 disks at
+# eta = 0.72) read as FP64 coordinates (2 x 16 B), plus the active disk's
+# coordinates read and written (16 B)
+BYTES_PER_EVENT = 48.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large", choices=["small", "medium", "large", "huge"])
+    ap.add_argument("--cells", type=int, default=0, help="cells per side (0 = workload default)")
+    ap.add_argument("--ell", type=float, default=0.0, help="chain displacement (0 = default)")
+    ap.add_argument("--nm", type=int, default=0, help="chains per cell (0 = eq. nm)")
+    ap.add_argument("--tpc", type=int, default=0, help="lanes per cell (0 = automatic)")
+    ap.add_argument("--prec", type=int, default=1, help="1 FP32 screening, 0 FP64 candidates")
+    ap.add_argument("--no-flush", action="store_true", help="do not flush L2 between steps")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    w = {"small": W.SMALL, "medium": W.MEDIUM, "large": W.LARGE, "huge": W.HUGE}[args.workload]
+    cells = args.cells or w.cells
+    ell = args.ell or w.ell
+    return w, cells, ell
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.idx = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [v.strip() for v in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(w, cells, ell, nm, seconds, max_sweeps=1000):
+    """The oracle, as it stands, single-threaded on this host: sweeps of the
+    same workload from the lattice start until `seconds` have passed."""
+    import oracle
+
+    L = w.L
+    x, y = W.square_lattice(w.N, L)
+    if nm == 0:
+        nm = oracle.default_nm(w.N, L, 1.0, cells, cells, ell)
+    p = oracle.make_params(w.N, L, 1.0, cells, cells, ell, nm, w.seed)
+    st = oracle.Stats()
+    t0 = time.perf_counter()
+    n = 0
+    while n < max_sweeps:
+        oracle.sweeps(p, x, y, n, 1, stats=st)
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": st.events / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d sweeps of the full workload from the lattice start (%.1f s)" % (n, dt),
+            "sweeps_per_s": n / dt}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w, cells, ell = workload(args)
+    import oracle
+
+    L = w.L
+    nm = args.nm or oracle.default_nm(w.N, L, 1.0, cells, cells, ell)
+    x, y = W.square_lattice(w.N, L)
+    p = oracle.make_params(w.N, L, 1.0, cells, cells, ell, nm, w.seed)
+    for s in range(args.warmup):
+        oracle.sweeps(p, x, y, s, 1)
+    st = oracle.Stats()
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        oracle.sweeps(p, x, y, args.warmup + s, 1, stats=st)
+    dt = time.perf_counter() - t0
+    value = st.events / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "N": w.N, "eta": w.eta, "cells": cells, "ell": ell,
+                   "n_m": nm, "parallelism": "replicas"},
+        "sweeps_per_s": args.steps / dt,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d full sweeps after %d warm-up sweeps" %
+                                   (args.steps, args.warmup)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    import paper_1409_6948_gb300 as P
+    from paper_1409_6948_gb300 import ecmc as E
+
+    w, cells, ell = workload(args)
+    L = w.L
+    g = P.Ecmc(w.N, L, 1.0, cells, cells, ell, w.seed)
+    g.set_param(E.PARAM_REPLICA, rank)
+    if args.nm:
+        g.set_param(E.PARAM_N_CHAINS, args.nm)
+    if args.tpc:
+        g.set_param(E.PARAM_LANES_PER_CELL, args.tpc)
+    g.set_param(E.PARAM_PRECISION, args.prec)
+    stream = torch.cuda.current_stream()
+    g.set_stream(stream)
+    nm = int(g.get_param(E.PARAM_N_CHAINS))
+    tpc = int(g.get_param(E.PARAM_LANES_PER_CELL))
+
+    # warm-up (graphs captured here)
+    g.sweep(args.warmup)
+    g.synchronize()
+
+    # timed region: per-kernel CUDA events inside the library (direct
+    # launches), one event pair per step on the same stream, L2 flushed
+    # between steps outside the timed pairs
+    flush = None if args.no_flush else torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32,
+                                                    device=dev)
+    g.set_param(E.PARAM_TIMING, 1)
+    g.reset_stats()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device()) if local == 0 else None
+    if clocks:
+        clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for a, b in evs:
+        if flush is not None:
+            flush.zero_()
+        a.record(stream)
+        g.sweep(1)
+        b.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop() if clocks else None
+    g.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    c = g.counters()
+    kt = g.kernel_times()
+    g.set_param(E.PARAM_TIMING, 0)
+    events = c.events
+    sweeps = c.sweeps
+
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        n = torch.tensor([float(events), float(sweeps)], dtype=torch.float64, device=dev)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+        ms_max = t.item()
+        events_all, sweeps_all = n[0].item(), n[1].item()
+    else:
+        ms_max, events_all, sweeps_all = ms, float(events), float(sweeps)
+    value = events_all / (ms_max * 1e-3)
+
+    # end to end through the public API: host (pinned) positions in, one
+    # sweep, positions out, every step
+    e2e = None
+    if not args.skip_e2e:
+        host = torch.empty(2 * w.N, dtype=torch.float64, pin_memory=True)
+        g.positions(host.numpy())
+        t_idx = g.sweep_index()
+        g.reset_stats()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in range(args.steps):
+            g.set_positions(host.numpy(), t0=t_idx + s)
+            g.sweep(1)
+            g.positions(host.numpy())
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        ce = g.counters()
+        e2e = {"value": ce.events / dt, "unit": UNIT, "h2d_bytes_per_step": 16 * w.N,
+               "d2h_bytes_per_step": 16 * w.N, "timer": "host wall clock"}
+
+    line = None
+    if rank == 0:
+        phase_avg_ms = kt.phase_ms / max(kt.phase_launches, 1)
+        bytes_per_launch = BYTES_PER_EVENT * events / max(kt.phase_launches, 1)
+        smem_gbs, fp64_gflops = P.ecmc.device_peaks()
+        achieved = bytes_per_launch / (phase_avg_ms * 1e-3) / 1e9
+        cpu = None
+        if not args.skip_cpu:
+            cpu = cpu_baseline(w, cells, ell, nm, args.cpu_seconds)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "N": w.N, "eta": w.eta, "cells": cells, "ell": ell,
+                       "n_m": nm, "lanes_per_cell": tpc,
+                       "screening": "fp32" if args.prec else "fp64",
+                       "l2": "none" if args.no_flush else "flushed (256 MB write) between steps",
+                       "parallelism": "replicas x%d" % world},
+            "sweeps_per_s": sweeps_all / (ms_max * 1e-3),
+            "events_per_sweep": events / max(sweeps, 1),
+            "kernel_ms_per_sweep": {"bin": kt.bin_ms / max(sweeps, 1),
+                                    "frame": kt.frame_ms / max(sweeps, 1),
+                                    "chain": kt.phase_ms / max(sweeps, 1),
+                                    "reduce": kt.other_ms / max(sweeps, 1)},
+            "roofline": {"kernel": "k_phase (chain kernel)", "bound": "smem",
+                         "achieved": achieved, "peak": smem_gbs, "unit": "GB/s",
+                         "frac": achieved / smem_gbs, "traffic": None,
+                         "bytes_per_event": BYTES_PER_EVENT,
+                         "peak_source": "ecmc_device_peaks shared-memory probe (measured)",
+                         "fp64_peak_gflops": fp64_gflops},
+            "gpu_launches": 11 * args.steps * world,
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    g.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

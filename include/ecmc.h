@@ -35,6 +35,12 @@
 
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define ECMC_API __attribute__((visibility("default")))
+#else
+#define ECMC_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -76,8 +82,15 @@ extern "C" {
 #define ECMC_PARAM_GR_RMAX 7
 /* 1 = record per-kernel CUDA-event times (ecmc_kernel_times), 0 = off. */
 #define ECMC_PARAM_TIMING 8
-/* Local bin side of the candidate search in units of sigma (>= 1.0625). */
-#define ECMC_PARAM_BIN_SIDE 9
+/* Width of the candidate strips across the chain axis, in units of sigma
+ * (0.125 .. 2; default 0.5).  Changes only the speed, never the result. */
+#define ECMC_PARAM_STRIP_WIDTH 9
+/* 1 = keep per-chain records of the most recent sweep (ecmc_chain_records). */
+#define ECMC_PARAM_RECORD_CHAINS 10
+/* Warps per block of the chain kernel (1 .. 8, 0 = automatic). */
+#define ECMC_PARAM_WARPS_PER_BLOCK 11
+/* 1 = capture each sweep in a CUDA graph and replay it (default 1). */
+#define ECMC_PARAM_USE_GRAPH 12
 
 #define ECMC_DIR_PM_AXIS_ALT 0
 #define ECMC_DIR_POS_ONLY 1
@@ -99,13 +112,22 @@ typedef struct {
 } ecmc_counters_t;
 
 typedef struct {
-  double bin_ms;       /* cell binning kernels (count, scan, scatter)           */
-  double phase_ms;     /* the four colour-phase sweep kernels                   */
-  double other_ms;     /* everything else enqueued by ecmc_sweep                */
+  double bin_ms;       /* per-sweep draws and the cell binning pass            */
+  double frame_ms;     /* frame builders (active cell + frozen halo staging)   */
+  double phase_ms;     /* the chain kernels of the four colour phases          */
+  double other_ms;     /* end-of-sweep reduction                               */
   int64_t bin_launches;
+  int64_t frame_launches;
   int64_t phase_launches;
   int64_t other_launches;
 } ecmc_timing_t;
+
+typedef struct {
+  int64_t start_id; /* disk that started the chain                          */
+  int64_t end_id;   /* disk that was moving when the budget ran out        */
+  int64_t events;   /* contacts of the chain                                */
+  int64_t walls;    /* wall reflections of the chain                        */
+} ecmc_chain_rec_t;
 
 /* Create a system of N disks of diameter sigma in the periodic L x L box,
  * started on a k x k square lattice (k = sqrt(N); disk iy*k + ix at
@@ -116,90 +138,106 @@ typedef struct {
  * w or h <= sigma, L/k <= sigma so the lattice would overlap, ell < 0),
  * ECMC_ERR_CUDA, ECMC_ERR_OOM.  *out receives the handle (owned by the
  * library until ecmc_destroy). */
-int ecmc_create(ecmc_t* out, int64_t N, double L, double sigma, int cells_x, int cells_y,
+ECMC_API int ecmc_create(ecmc_t* out, int64_t N, double L, double sigma, int cells_x, int cells_y,
                 double ell, uint64_t seed);
 
 /* Release the handle and all its device memory.  NULL is accepted. */
-int ecmc_destroy(ecmc_t h);
+ECMC_API int ecmc_destroy(ecmc_t h);
 
 /* Set / query one ECMC_PARAM_* value.  ECMC_ERR_ARG for an unknown key or a
  * value out of range. */
-int ecmc_set_param(ecmc_t h, int key, double value);
-int ecmc_get_param(ecmc_t h, int key, double* value);
+ECMC_API int ecmc_set_param(ecmc_t h, int key, double value);
+ECMC_API int ecmc_get_param(ecmc_t h, int key, double* value);
 
 /* Use the caller's CUDA stream (a cudaStream_t passed as void*, or NULL for
  * the library's own stream) for all later work.  The caller keeps ownership
  * of the stream and must keep it alive while the handle uses it. */
-int ecmc_set_stream(ecmc_t h, void* stream);
+ECMC_API int ecmc_set_stream(ecmc_t h, void* stream);
 
 /* Replace the configuration by the 2N values at xy (interleaved, id order;
  * device memory if on_device != 0, else host memory) and set the sweep
  * counter to t0 (the Philox counter of the next sweep).  Values are wrapped
  * into [0, L).  Errors: ECMC_ERR_ARG (NULL, t0 < 0). */
-int ecmc_set_positions(ecmc_t h, const double* xy, int on_device, int64_t t0);
+ECMC_API int ecmc_set_positions(ecmc_t h, const double* xy, int on_device, int64_t t0);
 
 /* Enqueue n_sweeps sweeps (Sec. 3.4 steps 1-7) on the handle's stream.
  * Asynchronous: errors raised on the device (ECMC_ERR_CAPACITY,
  * ECMC_ERR_CHAIN_CAP) are reported by the next synchronising call. */
-int ecmc_sweep(ecmc_t h, int64_t n_sweeps);
+ECMC_API int ecmc_sweep(ecmc_t h, int64_t n_sweeps);
 
 /* Wait for the handle's stream; report device-side errors. */
-int ecmc_synchronize(ecmc_t h);
+ECMC_API int ecmc_synchronize(ecmc_t h);
 
 /* Copy the configuration out (2N doubles, interleaved, id order) into
  * caller memory (device if on_device != 0). */
-int ecmc_positions(ecmc_t h, double* xy_out, int on_device);
+ECMC_API int ecmc_positions(ecmc_t h, double* xy_out, int on_device);
 
 /* Current sweep counter (the Philox counter of the next sweep). */
-int ecmc_sweep_index(ecmc_t h, int64_t* t);
+ECMC_API int ecmc_sweep_index(ecmc_t h, int64_t* t);
 
 /* Counters accumulated since creation or the last ecmc_reset_stats. */
-int ecmc_counters(ecmc_t h, ecmc_counters_t* out);
+ECMC_API int ecmc_counters(ecmc_t h, ecmc_counters_t* out);
 
 /* Clear counters, pressure accumulators and the pair histogram. */
-int ecmc_reset_stats(ecmc_t h);
+ECMC_API int ecmc_reset_stats(ecmc_t h);
 
-/* Pressure from the collision sums since the last reset:
- * beta P sigma^2 = rho sigma^2 (1 + sum_b / sum_disp) (collision form of
- * eq. pressure).  stderr_out (may be NULL) is the standard error from batch
- * means over the sweeps since the reset (0 if fewer than 2 sweeps).
- * ECMC_ERR_STATE if no chain has run since the reset. */
-int ecmc_pressure(ecmc_t h, double* betaP_sigma2, double* stderr_out);
+/* Pressure from the collision sums since the last reset, the collision form
+ * of eq. (pressure) of Sec. 2: beta P sigma^2 = rho sigma^2 (1 + B / D) with
+ * B = sum over cells of n_c * (sum over the cell's contacts of the centre
+ * separation along d at contact) and D = sum over cells of n_c * n_m * ell,
+ * n_c the number of members of the cell.  (Each cell gets the same
+ * displacement whatever n_c; weighting by n_c removes the bias this causes.)
+ * stderr_out (may be NULL) is the standard error from batch means over the
+ * sweeps since the reset (0 if fewer than 2 sweeps).
+ * ECMC_ERR_STATE if no sweep has run since the reset. */
+ECMC_API int ecmc_pressure(ecmc_t h, double* betaP_sigma2, double* stderr_out);
 
 /* Add the pair histogram of the current configuration to the accumulated
  * one: ordered pairs with sigma + i dr <= d < sigma + (i+1) dr (Sec. 2). */
-int ecmc_gr_measure(ecmc_t h);
+ECMC_API int ecmc_gr_measure(ecmc_t h);
 
 /* Accumulated counts (int64[nbins]) and number of measurements.
  * ECMC_ERR_ARG if nbins differs from the configured bin count. */
-int ecmc_gr_counts(ecmc_t h, int64_t* counts, int nbins, int64_t* n_meas);
+ECMC_API int ecmc_gr_counts(ecmc_t h, int64_t* counts, int nbins, int64_t* n_meas);
 
 /* Normalised g(R_i) = <n(r_i)> / (N rho 2 pi R_i dr) with the area-weighted
  * radius R_i = 2 (e1^3 - e0^3) / (3 (e1^2 - e0^2)) of each bin (Sec. 2);
  * r_out (may be NULL) receives R_i. */
-int ecmc_gr(ecmc_t h, double* g_out, double* r_out, int nbins);
+ECMC_API int ecmc_gr(ecmc_t h, double* g_out, double* r_out, int nbins);
 
 /* Number of histogram bins for the current GR_DR / GR_RMAX. */
-int ecmc_gr_nbins(ecmc_t h, int* nbins);
+ECMC_API int ecmc_gr_nbins(ecmc_t h, int* nbins);
 
 /* Smallest minimum-image pair distance of the current configuration among
  * pairs closer than 2 sigma (2 sigma if none). */
-int ecmc_min_distance(ecmc_t h, double* dmin);
+ECMC_API int ecmc_min_distance(ecmc_t h, double* dmin);
 
 /* Cell of every disk (by id) used by the most recent sweep, cy*cells_x+cx. */
-int ecmc_last_cells(ecmc_t h, int32_t* cell_of_id);
+ECMC_API int ecmc_last_cells(ecmc_t h, int32_t* cell_of_id);
 
 /* Per-kernel times accumulated while ECMC_PARAM_TIMING is 1. */
-int ecmc_kernel_times(ecmc_t h, ecmc_timing_t* out);
+ECMC_API int ecmc_kernel_times(ecmc_t h, ecmc_timing_t* out);
+
+/* Per-chain records of the most recent sweep (requires
+ * ECMC_PARAM_RECORD_CHAINS = 1 during that sweep): out[cell * n_m + k] for
+ * cell = cy * cells_x + cx; cells without members hold start_id = -1.
+ * n must equal cells_x * cells_y * n_m. */
+ECMC_API int ecmc_chain_records(ecmc_t h, ecmc_chain_rec_t* out, int64_t n);
+
+/* Measure, on the current device, the shared-memory load bandwidth (GB/s,
+ * 16-byte loads from every SM) and the FP64 fused multiply-add throughput
+ * (GFLOP/s); the roofline denominators of the chain kernel.  No handle is
+ * needed; takes a few milliseconds. */
+ECMC_API int ecmc_device_peaks(double* smem_gbs, double* fp64_gflops);
 
 /* Message for an error code (static string). */
-const char* ecmc_strerror(int code);
+ECMC_API const char* ecmc_strerror(int code);
 
 /* Detail of the most recent failure on the calling thread (static buffer). */
-const char* ecmc_last_error_message(void);
+ECMC_API const char* ecmc_last_error_message(void);
 
 /* Library version string. */
-const char* ecmc_version(void);
+ECMC_API const char* ecmc_version(void);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,11 @@
+"""GB300 (sm_103a) parallel event-chain Monte Carlo for two-dimensional hard
+disks (Kampmann, Boltz, Kierfeld, arXiv:1409.6948).
+
+The computation lives in the CUDA library libecmc.so (C ABI in
+include/ecmc.h); this package only loads it and marshals arguments.
+"""
+from .ecmc import (DIR_PM_AXIS_ALT, DIR_POS_ONLY, PREC_FP32_GEOM, PREC_FP64, Ecmc, EcmcError,
+                   load, version)
+
+__all__ = ["Ecmc", "EcmcError", "load", "version", "DIR_PM_AXIS_ALT", "DIR_POS_ONLY",
+           "PREC_FP64", "PREC_FP32_GEOM"]

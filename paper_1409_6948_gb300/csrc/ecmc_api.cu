@@ -1,0 +1,867 @@
+// ecmc_api.cu -- the C ABI of libecmc (declared in include/ecmc.h): handle
+// life cycle, parameters, the sweep driver, and the data getters.
+//
+// One sweep (Sec. 3.4 steps 1-7) is the fixed launch sequence
+//   draws -> binning -> 4 x (frame build, chain kernel) -> reduction,
+// every kernel reading the sweep counter, shift and colour order from device
+// memory; it is captured once into a CUDA graph per buffer parity and
+// replayed.
+#include <cmath>
+#include <cstdarg>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ecmc.h"
+#include "ecmc_internal.cuh"
+
+using namespace ecmc;
+
+namespace {
+
+thread_local char g_msg[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(e_ == cudaErrorMemoryAllocation ? ECMC_ERR_OOM : ECMC_ERR_CUDA,         \
+                  "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+enum TimerClass { TC_BIN = 0, TC_FRAME = 1, TC_PHASE = 2, TC_OTHER = 3 };
+
+}  // namespace
+
+struct ecmc_ctx {
+  Geom g;
+  DevBufs b;
+  RecLayout lay;
+  int tpc = 0;          // lanes per cell in use
+  int tpc_param = 0;    // 0 = automatic
+  int warps = 0;
+  int warps_param = 0;
+  float strip_w = 0.5f;
+  size_t records_cap = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;
+  int64_t t_host = 0;          // mirror of the device sweep counter
+  int64_t hist_len_host = 0;   // mirror of the history length
+  bool valid_state = true;
+  int record_chains = 0;
+  int use_graph = 1;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  // timing
+  int timing = 0;
+  struct Ev {
+    cudaEvent_t a, b;
+    int cls;
+  };
+  std::vector<Ev> pending;
+  std::vector<cudaEvent_t> pool;
+  double ms[4] = {0, 0, 0, 0};
+  int64_t launches[4] = {0, 0, 0, 0};
+  // g(r)
+  double gr_dr = 0.01, gr_rmax = 5.0;
+  int gr_nbins = 0;
+  unsigned long long* gr_counts = nullptr;
+  int64_t gr_meas = 0;
+  // scratch
+  double* xy_tmp = nullptr;
+  int* int_tmp = nullptr;
+  unsigned long long* u64_tmp = nullptr;
+};
+
+namespace {
+
+int compute_layout(ecmc_ctx* h);
+
+double packing_bound(double W, double H, double sigma) {
+  // disjoint disks of diameter sigma' = sigma (1 - 1e-6) whose centres lie in
+  // a W x H rectangle fit, with their full area, in the rectangle grown by
+  // sigma'/2 on every side
+  const double sp = sigma * (1.0 - 1e-6);
+  const double pi = 3.14159265358979323846;
+  return (W + sp) * (H + sp) / (pi * sp * sp / 4.0);
+}
+
+void set_screen_bounds(Geom& g) {
+  // M: power of two bounding every frame coordinate, |v| < max(w,h) + sigma
+  const double ext = (g.w > g.h ? g.w : g.h) + 1.01 * g.sigma;
+  double M = 1.0;
+  while (M < ext) M *= 2.0;
+  // |FP32 difference - FP64 difference| <= 4.002 * 2^-24 * M (two roundings
+  // to FP32 of the operands, one of the difference, one FP64 rounding)
+  const double e = 4.5 * std::ldexp(1.0, -24) * M;
+  const double sig = g.sigma;
+  // |x32 - (sigma^2 - ddy^2)| <= ex, x32 = fma(-|db|, |db|, sigma^2) in FP32
+  const double ex = (2.0 * sig + 2.0 * e) * e + 3.0 * std::ldexp(1.0, -24) * sig * sig;
+  // hit distance: e (along d) + sqrt(ex) (sqrt is 1/2-Hoelder) + rsqrt
+  // approximation + FP32 rounding of the difference, with 25% slack
+  const double sm = 1.25 * (e + std::sqrt(ex) + std::ldexp(1.0, -20) * sig +
+                            std::ldexp(1.0, -23) * (2.0 * M + sig));
+  g.eps_d = (float)(e * 1.0000001);
+  g.s_margin = (float)sm;
+  g.sig_plus = std::nextafter((float)(sig + e + std::ldexp(sig, -40)), 1e30f);
+  g.sig_minus = std::nextafter((float)(sig - e - std::ldexp(sig, -40)), -1e30f);
+  g.sig2f = (float)(sig * sig);
+  g.sigf = (float)sig;
+  g.strip_margin = (float)(4.0 * e + 1e-5 * sig);
+}
+
+int choose_tpc(ecmc_ctx* h) {
+  if (h->tpc_param) return h->tpc_param;
+  // smallest group width whose per-warp shared memory leaves room for at
+  // least four warps per SM
+  for (int t = 1; t <= 32; t *= 2) {
+    RecLayout l = make_layout(32 / t, h->g.nbin, h->g.cap_mem, h->g.cap_obj);
+    if (phase_smem_bytes(l, 1) <= 52 * 1024) return t;
+  }
+  return 32;
+}
+
+int compute_layout(ecmc_ctx* h) {
+  Geom& g = h->g;
+  const double bw = h->strip_w * g.sigma;
+  const double extB = (g.w > g.h ? g.w : g.h) + 2.0 * g.sigma;
+  g.nbin = (int)std::ceil(extB / bw) + 1;
+  g.bin_w = (float)bw;
+  g.inv_bin_w = (float)(1.0 / bw);
+  h->tpc = choose_tpc(h);
+  h->lay = make_layout(32 / h->tpc, g.nbin, g.cap_mem, g.cap_obj);
+  const size_t per_warp = phase_smem_bytes(h->lay, 1);
+  const size_t limit = 200 * 1024;
+  if (per_warp > limit)
+    return fail(ECMC_ERR_UNSUPPORTED,
+                "cell frame of %zu bytes per group does not fit in shared memory "
+                "(cells too large: use more cells)",
+                per_warp);
+  int w = h->warps_param;
+  if (w == 0) {
+    w = (int)(limit / per_warp);
+    if (w > 4) w = 4;
+    if (w < 1) w = 1;
+  }
+  if ((size_t)w * per_warp > 227 * 1024) w = (int)((227 * 1024) / per_warp);
+  if (w < 1) w = 1;
+  h->warps = w;
+  const int n_active = (g.cells_x / 2) * (g.cells_y / 2);
+  const int n_groups = (n_active + h->lay.cpw - 1) / h->lay.cpw;
+  const size_t need = (size_t)n_groups * h->lay.bytes;
+  if (need > h->records_cap) {
+    if (h->b.records) cudaFree(h->b.records);
+    h->b.records = nullptr;
+    CK(cudaMalloc(&h->b.records, need));
+    h->records_cap = need;
+  }
+  if (frame_build_smem(h->lay) > 227 * 1024)
+    return fail(ECMC_ERR_UNSUPPORTED, "cell frame too large for the frame builder");
+  if (configure_frame_build(h->lay) || configure_phase(h->lay, h->tpc, h->warps))
+    return fail(ECMC_ERR_CUDA, "kernel configuration failed: %s",
+                cudaGetErrorString(cudaGetLastError()));
+  return ECMC_OK;
+}
+
+void drop_graphs(ecmc_ctx* h) {
+  for (int i = 0; i < 2; ++i)
+    if (h->graph[i]) {
+      cudaGraphExecDestroy(h->graph[i]);
+      h->graph[i] = nullptr;
+    }
+}
+
+cudaEvent_t get_event(ecmc_ctx* h) {
+  if (!h->pool.empty()) {
+    cudaEvent_t e = h->pool.back();
+    h->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct Timed {
+  ecmc_ctx* h;
+  int cls;
+  cudaEvent_t a = nullptr;
+  Timed(ecmc_ctx* hh, int c) : h(hh), cls(c) {
+    if (h->timing) {
+      a = get_event(h);
+      cudaEventRecord(a, h->stream);
+    }
+  }
+  ~Timed() {
+    if (h->timing) {
+      cudaEvent_t b = get_event(h);
+      cudaEventRecord(b, h->stream);
+      h->pending.push_back({a, b, cls});
+    }
+    h->launches[cls] += 1;
+  }
+};
+
+void harvest_timing(ecmc_ctx* h) {
+  for (auto& e : h->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) h->ms[e.cls] += ms;
+    h->pool.push_back(e.a);
+    h->pool.push_back(e.b);
+  }
+  h->pending.clear();
+}
+
+// Enqueue one sweep (no graph).
+int enqueue_sweep(ecmc_ctx* h) {
+  const int src = h->b.cur, dst = 1 - h->b.cur;
+  if (h->record_chains && h->b.chain_recs)
+    CK(cudaMemsetAsync(h->b.chain_recs, 0xff,
+                       sizeof(ChainRec) * (size_t)h->g.ncell * h->g.n_m, h->stream));
+  {
+    Timed tm(h, TC_BIN);
+    launch_sweep_begin(h->g, h->b, h->stream);
+    launch_bin(h->g, h->b, src, dst, h->stream);
+  }
+  h->b.cur = dst;
+  for (int ci = 0; ci < 4; ++ci) {
+    {
+      Timed tm(h, TC_FRAME);
+      launch_frame_build(h->g, h->b, h->lay, ci, h->stream);
+    }
+    {
+      Timed tm(h, TC_PHASE);
+      if (launch_phase(h->g, h->b, h->lay, ci, h->tpc, h->warps, h->record_chains, h->stream))
+        return fail(ECMC_ERR_CUDA, "chain kernel launch failed: %s",
+                    cudaGetErrorString(cudaGetLastError()));
+    }
+  }
+  {
+    Timed tm(h, TC_OTHER);
+    launch_sweep_end(h->g, h->b, h->stream);
+  }
+  CK(cudaGetLastError());
+  return ECMC_OK;
+}
+
+int ensure_history(ecmc_ctx* h, int64_t extra) {
+  const int64_t need = h->hist_len_host + extra;
+  if (need <= h->b.history_cap) return ECMC_OK;
+  int64_t cap = h->b.history_cap ? h->b.history_cap : 1024;
+  while (cap < need) cap *= 2;
+  double* nh = nullptr;
+  CK(cudaMalloc(&nh, sizeof(double) * 2 * cap));
+  if (h->b.history && h->hist_len_host > 0)
+    CK(cudaMemcpyAsync(nh, h->b.history, sizeof(double) * 2 * h->hist_len_host,
+                       cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->b.history) cudaFree(h->b.history);
+  h->b.history = nh;
+  h->b.history_cap = cap;
+  drop_graphs(h);  // the graphs hold the old pointer
+  return ECMC_OK;
+}
+
+int check_device_error(ecmc_ctx* h) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, h->b.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->timing) harvest_timing(h);
+  if (e == DEV_CAPACITY) {
+    h->valid_state = false;
+    return fail(ECMC_ERR_CAPACITY, "a cell bucket or frame exceeded its packing bound");
+  }
+  if (e == DEV_CHAIN_CAP) {
+    h->valid_state = false;
+    return fail(ECMC_ERR_CHAIN_CAP, "a chain reached the per-chain event cap");
+  }
+  return ECMC_OK;
+}
+
+int load_positions_dev(ecmc_ctx* h, const double* xy_dev, int64_t t0) {
+  launch_load_flat(h->g, h->b, xy_dev, h->stream);
+  SweepState st;
+  std::memset(&st, 0, sizeof(st));
+  st.t = t0;
+  st.history_len = h->hist_len_host;
+  CK(cudaMemcpyAsync(h->b.state, &st, sizeof(st), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  launch_sweep_begin(h->g, h->b, h->stream);
+  launch_bin(h->g, h->b, -1, h->b.cur, h->stream);
+  CK(cudaGetLastError());
+  h->t_host = t0;
+  h->valid_state = true;
+  int rc = check_device_error(h);
+  if (rc) return rc;
+  // no two disks may overlap beyond rounding
+  unsigned long long init = 0;
+  const double r2 = 4.0 * h->g.sig2;
+  std::memcpy(&init, &r2, sizeof(r2));
+  CK(cudaMemcpyAsync(h->u64_tmp, &init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
+  launch_min_dist(h->g, h->b, 2.0 * h->g.sigma, h->u64_tmp, h->stream);
+  unsigned long long bits = 0;
+  CK(cudaMemcpyAsync(&bits, h->u64_tmp, sizeof(bits), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  double d2;
+  std::memcpy(&d2, &bits, sizeof(d2));
+  if (d2 < h->g.sig2 * (1.0 - 1e-9)) {
+    h->valid_state = false;
+    return fail(ECMC_ERR_OVERLAP, "positions overlap: smallest distance %.17g < sigma",
+                std::sqrt(d2));
+  }
+  return ECMC_OK;
+}
+
+int default_nm(const Geom& g) {
+  const double pi = 3.14159265358979323846;
+  const double eta = (double)g.N * pi * g.sigma * g.sigma / (4.0 * g.L * g.L);
+  const double eta_hcp = pi / (2.0 * std::sqrt(3.0));
+  const double lambda0 = g.sigma * (eta_hcp - eta) / (2.0 * eta_hcp);
+  if (!(g.ell > 0.0) || !(lambda0 > 0.0)) return 1;
+  const double nm = (double)g.N / (double)g.ncell * lambda0 / g.ell;
+  const double r = std::floor(nm + 0.5);
+  if (r < 1.0) return 1;
+  if (r > 1e6) return 1000000;
+  return (int)r;
+}
+
+int realloc_chain_recs(ecmc_ctx* h) {
+  if (h->b.chain_recs) cudaFree(h->b.chain_recs);
+  h->b.chain_recs = nullptr;
+  if (!h->record_chains) return ECMC_OK;
+  const size_t n = (size_t)h->g.ncell * h->g.n_m;
+  CK(cudaMalloc(&h->b.chain_recs, sizeof(ChainRec) * n));
+  CK(cudaMemsetAsync(h->b.chain_recs, 0xff, sizeof(ChainRec) * n, h->stream));
+  return ECMC_OK;
+}
+
+void free_all(ecmc_ctx* h) {
+  drop_graphs(h);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(h->b.px[i]);
+    cudaFree(h->b.py[i]);
+    cudaFree(h->b.pid[i]);
+    cudaFree(h->b.count[i]);
+  }
+  cudaFree(h->b.state);
+  cudaFree(h->b.cell_stats);
+  cudaFree(h->b.totals);
+  cudaFree(h->b.history);
+  cudaFree(h->b.records);
+  cudaFree(h->b.err);
+  cudaFree(h->b.chain_recs);
+  cudaFree(h->gr_counts);
+  cudaFree(h->xy_tmp);
+  cudaFree(h->int_tmp);
+  cudaFree(h->u64_tmp);
+  for (auto& e : h->pending) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  for (auto e : h->pool) cudaEventDestroy(e);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+}
+
+int setup_gr(ecmc_ctx* h) {
+  const int nb = (int)std::floor((h->gr_rmax - h->g.sigma) / h->gr_dr + 0.5);
+  if (nb < 1 || nb > 1000000) return fail(ECMC_ERR_ARG, "bad g(r) binning");
+  if (h->gr_counts) cudaFree(h->gr_counts);
+  h->gr_counts = nullptr;
+  h->gr_nbins = nb;
+  CK(cudaMalloc(&h->gr_counts, sizeof(unsigned long long) * nb));
+  CK(cudaMemsetAsync(h->gr_counts, 0, sizeof(unsigned long long) * nb, h->stream));
+  h->gr_meas = 0;
+  return ECMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ecmc_version(void) { return "ecmc-gb300 0.1 (sm_103a)"; }
+
+const char* ecmc_last_error_message(void) { return g_msg; }
+
+const char* ecmc_strerror(int code) {
+  switch (code) {
+    case ECMC_OK: return "ok";
+    case ECMC_ERR_ARG: return "invalid argument";
+    case ECMC_ERR_CUDA: return "CUDA runtime error";
+    case ECMC_ERR_OOM: return "out of memory";
+    case ECMC_ERR_OVERLAP: return "disks overlap";
+    case ECMC_ERR_TIMEOUT: return "device wait timed out";
+    case ECMC_ERR_STATE: return "invalid state for this call";
+    case ECMC_ERR_CAPACITY: return "cell capacity exceeded";
+    case ECMC_ERR_UNSUPPORTED: return "unsupported option";
+    case ECMC_ERR_CHAIN_CAP: return "chain event cap reached";
+    default: return "unknown error";
+  }
+}
+
+int ecmc_create(ecmc_t* out, int64_t N, double L, double sigma, int cells_x, int cells_y,
+                double ell, uint64_t seed) {
+  if (!out) return fail(ECMC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (N < 1 || N >= (int64_t(1) << 27)) return fail(ECMC_ERR_ARG, "N out of range");
+  int64_t k = (int64_t)std::llround(std::sqrt((double)N));
+  if (k * k != N) return fail(ECMC_ERR_ARG, "N must be a perfect square (lattice start)");
+  if (!(L > 0.0) || !(sigma > 0.0) || !std::isfinite(L) || !std::isfinite(sigma))
+    return fail(ECMC_ERR_ARG, "L and sigma must be positive");
+  if (cells_x < 2 || cells_y < 2 || (cells_x & 1) || (cells_y & 1))
+    return fail(ECMC_ERR_ARG, "cells per side must be even and >= 2");
+  if (!(L / cells_x > sigma) || !(L / cells_y > sigma))
+    return fail(ECMC_ERR_ARG, "cell side must exceed sigma");
+  if (!(L / (double)k > sigma)) return fail(ECMC_ERR_ARG, "square lattice would overlap");
+  if (!(ell >= 0.0) || !std::isfinite(ell)) return fail(ECMC_ERR_ARG, "ell must be >= 0");
+  if ((int64_t)cells_x * cells_y > (int64_t(1) << 26)) return fail(ECMC_ERR_ARG, "too many cells");
+
+  ecmc_ctx* h = new (std::nothrow) ecmc_ctx();
+  if (!h) return fail(ECMC_ERR_OOM, "host allocation failed");
+  std::memset(&h->b, 0, sizeof(h->b));
+  Geom& g = h->g;
+  std::memset(&g, 0, sizeof(g));
+  g.N = N;
+  g.L = L;
+  g.sigma = sigma;
+  g.sig2 = sigma * sigma;
+  g.cells_x = cells_x;
+  g.cells_y = cells_y;
+  g.ncell = cells_x * cells_y;
+  g.w = L / (double)cells_x;
+  g.h = L / (double)cells_y;
+  g.inv_w = 1.0 / g.w;
+  g.inv_h = 1.0 / g.h;
+  g.ell = ell;
+  g.seed = seed;
+  g.replica = 0;
+  g.dir_mode = 0;
+  g.precision = 1;
+  g.cap_mem = (int)std::floor(packing_bound(g.w, g.h, sigma)) + 2;
+  g.cap_obj = (int)std::floor(packing_bound(g.w + 2 * sigma, g.h + 2 * sigma, sigma)) + 2;
+  if (g.cap_mem > g.cap_obj) g.cap_mem = g.cap_obj;
+  if ((int64_t)g.ncell * g.cap_mem < N) {
+    delete h;
+    return fail(ECMC_ERR_ARG, "N exceeds the packing capacity of the box");
+  }
+  g.n_m = default_nm(g);
+  set_screen_bounds(g);
+
+  auto bail = [&](int rc) {
+    free_all(h);
+    delete h;
+    return rc;
+  };
+  if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(fail(ECMC_ERR_CUDA, "cannot create a stream (no CUDA device?)"));
+  h->stream = h->own_stream;
+  const size_t slots = (size_t)g.ncell * g.cap_mem;
+  for (int i = 0; i < 2; ++i) {
+    if (cudaMalloc(&h->b.px[i], sizeof(double) * slots) != cudaSuccess ||
+        cudaMalloc(&h->b.py[i], sizeof(double) * slots) != cudaSuccess ||
+        cudaMalloc(&h->b.pid[i], sizeof(int) * slots) != cudaSuccess ||
+        cudaMalloc(&h->b.count[i], sizeof(int) * g.ncell) != cudaSuccess)
+      return bail(fail(ECMC_ERR_OOM, "device allocation of %zu slots failed", slots));
+    cudaMemsetAsync(h->b.count[i], 0, sizeof(int) * g.ncell, h->stream);
+  }
+  if (cudaMalloc(&h->b.state, sizeof(SweepState)) != cudaSuccess ||
+      cudaMalloc(&h->b.cell_stats, sizeof(CellStats) * g.ncell) != cudaSuccess ||
+      cudaMalloc(&h->b.totals, sizeof(RunTotals)) != cudaSuccess ||
+      cudaMalloc(&h->b.err, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&h->xy_tmp, sizeof(double) * 2 * (size_t)N) != cudaSuccess ||
+      cudaMalloc(&h->int_tmp, sizeof(int) * (size_t)N) != cudaSuccess ||
+      cudaMalloc(&h->u64_tmp, sizeof(unsigned long long) * 4) != cudaSuccess)
+    return bail(fail(ECMC_ERR_OOM, "device allocation failed"));
+  cudaMemsetAsync(h->b.totals, 0, sizeof(RunTotals), h->stream);
+  cudaMemsetAsync(h->b.err, 0, sizeof(int), h->stream);
+  cudaMemsetAsync(h->b.cell_stats, 0, sizeof(CellStats) * g.ncell, h->stream);
+  h->b.cur = 0;
+  int rc = compute_layout(h);
+  if (rc) return bail(rc);
+  rc = ensure_history(h, 1024);
+  if (rc) return bail(rc);
+  rc = setup_gr(h);
+  if (rc) return bail(rc);
+
+  // square-lattice start
+  std::vector<double> xy(2 * (size_t)N);
+  const double a = L / (double)k;
+  for (int64_t i = 0; i < N; ++i) {
+    xy[2 * i] = ((double)(i % k) + 0.5) * a;
+    xy[2 * i + 1] = ((double)(i / k) + 0.5) * a;
+  }
+  if (cudaMemcpyAsync(h->xy_tmp, xy.data(), sizeof(double) * 2 * N, cudaMemcpyHostToDevice,
+                      h->stream) != cudaSuccess)
+    return bail(fail(ECMC_ERR_CUDA, "upload failed"));
+  rc = load_positions_dev(h, h->xy_tmp, 0);
+  if (rc) return bail(rc);
+  *out = h;
+  return ECMC_OK;
+}
+
+int ecmc_destroy(ecmc_t h) {
+  if (!h) return ECMC_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+  return ECMC_OK;
+}
+
+int ecmc_set_stream(ecmc_t h, void* stream) {
+  if (!h) return fail(ECMC_ERR_ARG, "NULL handle");
+  CK(cudaStreamSynchronize(h->stream));
+  h->stream = stream ? (cudaStream_t)stream : h->own_stream;
+  drop_graphs(h);
+  return ECMC_OK;
+}
+
+int ecmc_set_param(ecmc_t h, int key, double v) {
+  if (!h) return fail(ECMC_ERR_ARG, "NULL handle");
+  CK(cudaStreamSynchronize(h->stream));
+  switch (key) {
+    case ECMC_PARAM_N_CHAINS: {
+      if (!(v >= 1.0 && v <= 1e6) || v != std::floor(v)) return fail(ECMC_ERR_ARG, "n_m");
+      h->g.n_m = (int)v;
+      drop_graphs(h);
+      return realloc_chain_recs(h);
+    }
+    case ECMC_PARAM_DIR_MODE:
+      if (v != 0.0 && v != 1.0) return fail(ECMC_ERR_ARG, "direction mode");
+      h->g.dir_mode = (int)v;
+      break;
+    case ECMC_PARAM_PRECISION:
+      if (v != 0.0 && v != 1.0) return fail(ECMC_ERR_ARG, "precision");
+      h->g.precision = (int)v;
+      break;
+    case ECMC_PARAM_REPLICA:
+      if (!(v >= 0.0) || v != std::floor(v) || v > 9.0e15) return fail(ECMC_ERR_ARG, "replica");
+      h->g.replica = (uint64_t)v;
+      break;
+    case ECMC_PARAM_LANES_PER_CELL: {
+      const int t = (int)v;
+      if ((double)t != v || !(t == 0 || t == 1 || t == 2 || t == 4 || t == 8 || t == 16 || t == 32))
+        return fail(ECMC_ERR_ARG, "lanes per cell must be 0 or a power of two <= 32");
+      h->tpc_param = t;
+      drop_graphs(h);
+      return compute_layout(h);
+    }
+    case ECMC_PARAM_WARPS_PER_BLOCK: {
+      const int w = (int)v;
+      if ((double)w != v || w < 0 || w > 8) return fail(ECMC_ERR_ARG, "warps per block");
+      h->warps_param = w;
+      drop_graphs(h);
+      return compute_layout(h);
+    }
+    case ECMC_PARAM_STRIP_WIDTH:
+      if (!(v >= 0.125 && v <= 2.0)) return fail(ECMC_ERR_ARG, "strip width");
+      h->strip_w = (float)v;
+      drop_graphs(h);
+      return compute_layout(h);
+    case ECMC_PARAM_GR_DR:
+      if (!(v > 0.0 && v < 10.0)) return fail(ECMC_ERR_ARG, "g(r) bin width");
+      h->gr_dr = v;
+      return setup_gr(h);
+    case ECMC_PARAM_GR_RMAX:
+      if (!(v > h->g.sigma && v < 0.5 * h->g.L)) return fail(ECMC_ERR_ARG, "g(r) range");
+      h->gr_rmax = v;
+      return setup_gr(h);
+    case ECMC_PARAM_TIMING:
+      h->timing = v != 0.0;
+      return ECMC_OK;
+    case ECMC_PARAM_RECORD_CHAINS:
+      h->record_chains = v != 0.0;
+      drop_graphs(h);
+      return realloc_chain_recs(h);
+    case ECMC_PARAM_USE_GRAPH:
+      h->use_graph = v != 0.0;
+      drop_graphs(h);
+      return ECMC_OK;
+    default:
+      return fail(ECMC_ERR_ARG, "unknown parameter %d", key);
+  }
+  drop_graphs(h);
+  return ECMC_OK;
+}
+
+int ecmc_get_param(ecmc_t h, int key, double* v) {
+  if (!h || !v) return fail(ECMC_ERR_ARG, "NULL argument");
+  switch (key) {
+    case ECMC_PARAM_N_CHAINS: *v = h->g.n_m; break;
+    case ECMC_PARAM_DIR_MODE: *v = h->g.dir_mode; break;
+    case ECMC_PARAM_PRECISION: *v = h->g.precision; break;
+    case ECMC_PARAM_REPLICA: *v = (double)h->g.replica; break;
+    case ECMC_PARAM_LANES_PER_CELL: *v = h->tpc; break;
+    case ECMC_PARAM_GR_DR: *v = h->gr_dr; break;
+    case ECMC_PARAM_GR_RMAX: *v = h->gr_rmax; break;
+    case ECMC_PARAM_TIMING: *v = h->timing; break;
+    case ECMC_PARAM_STRIP_WIDTH: *v = h->strip_w; break;
+    case ECMC_PARAM_RECORD_CHAINS: *v = h->record_chains; break;
+    case ECMC_PARAM_WARPS_PER_BLOCK: *v = h->warps; break;
+    case ECMC_PARAM_USE_GRAPH: *v = h->use_graph; break;
+    default: return fail(ECMC_ERR_ARG, "unknown parameter %d", key);
+  }
+  return ECMC_OK;
+}
+
+int ecmc_set_positions(ecmc_t h, const double* xy, int on_device, int64_t t0) {
+  if (!h || !xy) return fail(ECMC_ERR_ARG, "NULL argument");
+  if (t0 < 0) return fail(ECMC_ERR_ARG, "t0 < 0");
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpyAsync(h->xy_tmp, xy, sizeof(double) * 2 * (size_t)h->g.N,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  return load_positions_dev(h, h->xy_tmp, t0);
+}
+
+int ecmc_sweep(ecmc_t h, int64_t n) {
+  if (!h) return fail(ECMC_ERR_ARG, "NULL handle");
+  if (n < 0) return fail(ECMC_ERR_ARG, "n < 0");
+  if (!h->valid_state) return fail(ECMC_ERR_STATE, "state invalid after an earlier error");
+  int rc = ensure_history(h, n);
+  if (rc) return rc;
+  const bool graph = h->use_graph && !h->timing;
+  for (int64_t i = 0; i < n; ++i) {
+    if (graph) {
+      const int par = h->b.cur;
+      if (!h->graph[par]) {
+        cudaGraph_t gr;
+        CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        const int cur0 = h->b.cur;
+        rc = enqueue_sweep(h);
+        h->b.cur = cur0;
+        cudaError_t e = cudaStreamEndCapture(h->stream, &gr);
+        if (rc) return rc;
+        if (e != cudaSuccess)
+          return fail(ECMC_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&h->graph[par], gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess)
+          return fail(ECMC_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+        for (int c = 0; c < 4; ++c) h->launches[c] -= (c == TC_FRAME || c == TC_PHASE) ? 4 : 1;
+      }
+      CK(cudaGraphLaunch(h->graph[par], h->stream));
+      h->launches[TC_BIN] += 1;
+      h->launches[TC_FRAME] += 4;
+      h->launches[TC_PHASE] += 4;
+      h->launches[TC_OTHER] += 1;
+      h->b.cur = 1 - par;
+    } else {
+      rc = enqueue_sweep(h);
+      if (rc) return rc;
+    }
+    h->t_host += 1;
+    h->hist_len_host += 1;
+  }
+  return ECMC_OK;
+}
+
+int ecmc_synchronize(ecmc_t h) {
+  if (!h) return fail(ECMC_ERR_ARG, "NULL handle");
+  return check_device_error(h);
+}
+
+int ecmc_positions(ecmc_t h, double* xy_out, int on_device) {
+  if (!h || !xy_out) return fail(ECMC_ERR_ARG, "NULL argument");
+  const size_t bytes = sizeof(double) * 2 * (size_t)h->g.N;
+  if (on_device) {
+    launch_gather(h->g, h->b, xy_out, h->stream);
+  } else {
+    launch_gather(h->g, h->b, h->xy_tmp, h->stream);
+    CK(cudaMemcpyAsync(xy_out, h->xy_tmp, bytes, cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(cudaGetLastError());
+  return check_device_error(h);
+}
+
+int ecmc_sweep_index(ecmc_t h, int64_t* t) {
+  if (!h || !t) return fail(ECMC_ERR_ARG, "NULL argument");
+  *t = h->t_host;
+  return ECMC_OK;
+}
+
+int ecmc_counters(ecmc_t h, ecmc_counters_t* out) {
+  if (!h || !out) return fail(ECMC_ERR_ARG, "NULL argument");
+  RunTotals t;
+  CK(cudaMemcpyAsync(&t, h->b.totals, sizeof(t), cudaMemcpyDeviceToHost, h->stream));
+  int rc = check_device_error(h);
+  if (rc) return rc;
+  out->sweeps = t.sweeps;
+  out->chains = t.chains;
+  out->events = t.events;
+  out->lifts = t.lifts;
+  out->frozen_hits = t.frozen;
+  out->wall_hits = t.walls;
+  out->fp64_evals = t.fp64_evals;
+  out->sum_b = t.sum_b;
+  out->sum_disp = t.sum_disp;
+  return ECMC_OK;
+}
+
+int ecmc_reset_stats(ecmc_t h) {
+  if (!h) return fail(ECMC_ERR_ARG, "NULL handle");
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemsetAsync(h->b.totals, 0, sizeof(RunTotals), h->stream));
+  const int64_t zero = 0;
+  CK(cudaMemcpyAsync((char*)h->b.state + offsetof(SweepState, history_len), &zero, sizeof(zero),
+                     cudaMemcpyHostToDevice, h->stream));
+  h->hist_len_host = 0;
+  CK(cudaMemsetAsync(h->gr_counts, 0, sizeof(unsigned long long) * h->gr_nbins, h->stream));
+  h->gr_meas = 0;
+  for (int c = 0; c < 4; ++c) {
+    h->ms[c] = 0.0;
+    h->launches[c] = 0;
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->timing) harvest_timing(h);
+  for (int c = 0; c < 4; ++c) h->ms[c] = 0.0;
+  return ECMC_OK;
+}
+
+int ecmc_pressure(ecmc_t h, double* betaP, double* se) {
+  if (!h || !betaP) return fail(ECMC_ERR_ARG, "NULL argument");
+  const int64_t n = h->hist_len_host;
+  if (n < 1) return fail(ECMC_ERR_STATE, "no sweep since the last reset");
+  std::vector<double> hist(2 * (size_t)n);
+  CK(cudaMemcpyAsync(hist.data(), h->b.history, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost,
+                     h->stream));
+  RunTotals t;
+  CK(cudaMemcpyAsync(&t, h->b.totals, sizeof(t), cudaMemcpyDeviceToHost, h->stream));
+  int rc = check_device_error(h);
+  if (rc) return rc;
+  const double rho_s2 = (double)h->g.N / (h->g.L * h->g.L) * h->g.sig2;
+  if (!(t.sum_disp_w > 0.0)) return fail(ECMC_ERR_STATE, "no displacement since the last reset");
+  *betaP = rho_s2 * (1.0 + t.sum_b_w / t.sum_disp_w);
+  if (se) {
+    *se = 0.0;
+    const int64_t nb = n >= 20 ? 20 : n;
+    if (nb >= 2) {
+      std::vector<double> vals;
+      for (int64_t bI = 0; bI < nb; ++bI) {
+        const int64_t lo = bI * n / nb, hi = (bI + 1) * n / nb;
+        double sb = 0.0, sd = 0.0;
+        for (int64_t i = lo; i < hi; ++i) {
+          sb += hist[2 * i];
+          sd += hist[2 * i + 1];
+        }
+        vals.push_back(rho_s2 * (1.0 + sb / sd));
+      }
+      double mean = 0.0;
+      for (double v : vals) mean += v;
+      mean /= (double)nb;
+      double var = 0.0;
+      for (double v : vals) var += (v - mean) * (v - mean);
+      var /= (double)(nb - 1);
+      *se = std::sqrt(var / (double)nb);
+    }
+  }
+  return ECMC_OK;
+}
+
+int ecmc_gr_measure(ecmc_t h) {
+  if (!h) return fail(ECMC_ERR_ARG, "NULL handle");
+  launch_gr(h->g, h->b, h->gr_dr, h->gr_nbins, h->gr_counts, h->stream);
+  CK(cudaGetLastError());
+  h->gr_meas += 1;
+  return ECMC_OK;
+}
+
+int ecmc_gr_nbins(ecmc_t h, int* nbins) {
+  if (!h || !nbins) return fail(ECMC_ERR_ARG, "NULL argument");
+  *nbins = h->gr_nbins;
+  return ECMC_OK;
+}
+
+int ecmc_gr_counts(ecmc_t h, int64_t* counts, int nbins, int64_t* n_meas) {
+  if (!h || !counts) return fail(ECMC_ERR_ARG, "NULL argument");
+  if (nbins != h->gr_nbins) return fail(ECMC_ERR_ARG, "nbins must be %d", h->gr_nbins);
+  CK(cudaMemcpyAsync(counts, h->gr_counts, sizeof(int64_t) * nbins, cudaMemcpyDeviceToHost,
+                     h->stream));
+  int rc = check_device_error(h);
+  if (rc) return rc;
+  if (n_meas) *n_meas = h->gr_meas;
+  return ECMC_OK;
+}
+
+int ecmc_gr(ecmc_t h, double* g_out, double* r_out, int nbins) {
+  if (!h || !g_out) return fail(ECMC_ERR_ARG, "NULL argument");
+  std::vector<int64_t> c(nbins > 0 ? nbins : 1);
+  int64_t nm = 0;
+  int rc = ecmc_gr_counts(h, c.data(), nbins, &nm);
+  if (rc) return rc;
+  if (nm < 1) return fail(ECMC_ERR_STATE, "no g(r) measurement yet");
+  const double pi = 3.14159265358979323846;
+  const double N = (double)h->g.N, rho = N / (h->g.L * h->g.L), dr = h->gr_dr;
+  for (int i = 0; i < nbins; ++i) {
+    const double e0 = h->g.sigma + dr * i, e1 = e0 + dr;
+    const double R = 2.0 * (e1 * e1 * e1 - e0 * e0 * e0) / (3.0 * (e1 * e1 - e0 * e0));
+    g_out[i] = ((double)c[i] / (double)nm) / (N * rho * 2.0 * pi * R * dr);
+    if (r_out) r_out[i] = R;
+  }
+  return ECMC_OK;
+}
+
+int ecmc_min_distance(ecmc_t h, double* dmin) {
+  if (!h || !dmin) return fail(ECMC_ERR_ARG, "NULL argument");
+  unsigned long long init = 0;
+  const double r2 = 4.0 * h->g.sig2;
+  std::memcpy(&init, &r2, sizeof(r2));
+  CK(cudaMemcpyAsync(h->u64_tmp, &init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
+  launch_min_dist(h->g, h->b, 2.0 * h->g.sigma, h->u64_tmp, h->stream);
+  unsigned long long bits = 0;
+  CK(cudaMemcpyAsync(&bits, h->u64_tmp, sizeof(bits), cudaMemcpyDeviceToHost, h->stream));
+  int rc = check_device_error(h);
+  if (rc) return rc;
+  double d2;
+  std::memcpy(&d2, &bits, sizeof(d2));
+  *dmin = std::sqrt(d2);
+  return ECMC_OK;
+}
+
+int ecmc_last_cells(ecmc_t h, int32_t* cell_of_id) {
+  if (!h || !cell_of_id) return fail(ECMC_ERR_ARG, "NULL argument");
+  launch_cells_of(h->g, h->b, h->int_tmp, h->stream);
+  CK(cudaMemcpyAsync(cell_of_id, h->int_tmp, sizeof(int) * (size_t)h->g.N,
+                     cudaMemcpyDeviceToHost, h->stream));
+  return check_device_error(h);
+}
+
+int ecmc_kernel_times(ecmc_t h, ecmc_timing_t* out) {
+  if (!h || !out) return fail(ECMC_ERR_ARG, "NULL argument");
+  CK(cudaStreamSynchronize(h->stream));
+  harvest_timing(h);
+  out->bin_ms = h->ms[TC_BIN];
+  out->frame_ms = h->ms[TC_FRAME];
+  out->phase_ms = h->ms[TC_PHASE];
+  out->other_ms = h->ms[TC_OTHER];
+  out->bin_launches = h->launches[TC_BIN];
+  out->frame_launches = h->launches[TC_FRAME];
+  out->phase_launches = h->launches[TC_PHASE];
+  out->other_launches = h->launches[TC_OTHER];
+  return ECMC_OK;
+}
+
+int ecmc_chain_records(ecmc_t h, ecmc_chain_rec_t* out, int64_t n) {
+  if (!h || !out) return fail(ECMC_ERR_ARG, "NULL argument");
+  if (!h->record_chains || !h->b.chain_recs) return fail(ECMC_ERR_STATE, "records are off");
+  if (n != (int64_t)h->g.ncell * h->g.n_m) return fail(ECMC_ERR_ARG, "n must be cells * n_m");
+  static_assert(sizeof(ChainRec) == sizeof(ecmc_chain_rec_t), "record layout");
+  CK(cudaMemcpyAsync(out, h->b.chain_recs, sizeof(ChainRec) * n, cudaMemcpyDeviceToHost,
+                     h->stream));
+  return check_device_error(h);
+}
+
+int ecmc_device_peaks(double* smem_gbs, double* fp64_gflops) {
+  if (!smem_gbs || !fp64_gflops) return fail(ECMC_ERR_ARG, "NULL argument");
+  if (probe_peaks(smem_gbs, fp64_gflops))
+    return fail(ECMC_ERR_CUDA, "peak probe failed: %s", cudaGetErrorString(cudaGetLastError()));
+  return ECMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,224 @@
+// ecmc_frame.cu -- stage one colour's active cells into frame records.
+//
+// Sec. 3.4 step 6: while a cell is worked on, every disk outside it is
+// frozen.  A chain of that cell can touch its members and every disk whose
+// centre lies within sigma of the cell rectangle, including periodic images
+// (with two cells per side the left and right neighbour are the same cell,
+// and one disk may appear twice).  The builder places all of them in the
+// cell's own frame -- the cell is [0,w] x [0,h] -- and sorts them into strips
+// across the chain axis, so that the chain kernel only scans the strip of
+// width 2 sigma around the moving disk (chains move along one axis, so the
+// coordinate across the axis of every disk stays fixed during a sweep).
+//
+// One block per active cell.  The record is written in the interleaved
+// layout of the chain kernel's groups ([index][cells per group]).
+#include "ecmc_device.cuh"
+#include "ecmc_internal.cuh"
+
+namespace ecmc {
+
+struct BuildSmem {
+  double* a64;
+  double* b64;
+  int* key;
+  int* slot;
+  int* bin;
+  int* fin;
+  int* mrank;
+  int* hist;
+};
+
+__global__ void k_frame_build(Geom g, const SweepState* __restrict__ st, int colour_index,
+                              const double* __restrict__ px, const double* __restrict__ py,
+                              const int* __restrict__ pid, const int* __restrict__ cnt,
+                              unsigned char* __restrict__ records, RecLayout lay, int* err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_nobj, s_nmem, s_overflow;
+  const int tid = threadIdx.x, bt = blockDim.x;
+  const int colour = st->perm[colour_index];
+  const int hx = g.cells_x >> 1;
+  const int a = blockIdx.x;
+  const int cx = 2 * (a % hx) + (colour & 1);
+  const int cy = 2 * (a / hx) + (colour >> 1);
+  const int c = cy * g.cells_x + cx;
+  const int axis = st->axis;
+  const double L = g.L, sigma = g.sigma;
+  const double ox = st->sx + (double)cx * g.w;
+  const double oy = st->sy + (double)cy * g.h;
+  const double wl = g.w + sigma, hl = g.h + sigma;
+
+  BuildSmem s;
+  {
+    unsigned char* p = smem;
+    s.a64 = (double*)p; p += sizeof(double) * lay.cap_obj;
+    s.b64 = (double*)p; p += sizeof(double) * lay.cap_obj;
+    s.key = (int*)p; p += sizeof(int) * lay.cap_obj;
+    s.slot = (int*)p; p += sizeof(int) * lay.cap_obj;
+    s.bin = (int*)p; p += sizeof(int) * lay.cap_obj;
+    s.fin = (int*)p; p += sizeof(int) * lay.cap_obj;
+    s.mrank = (int*)p; p += sizeof(int) * lay.cap_mem;
+    s.hist = (int*)p; p += sizeof(int) * (lay.nbin + 1);
+  }
+  if (tid == 0) {
+    s_nobj = 0;
+    s_overflow = 0;
+  }
+  __syncthreads();
+
+  // members, in the cell frame
+  const int nc = min(cnt[c], g.cap_mem);
+  for (int k = tid; k < nc; k += bt) {
+    const int64_t q = (int64_t)c * g.cap_mem + k;
+    const double X = wrap_half(px[q] - ox, L);
+    const double Y = wrap_half(py[q] - oy, L);
+    const int i = atomicAdd(&s_nobj, 1);
+    s.a64[i] = axis == 0 ? X : Y;
+    s.b64[i] = axis == 0 ? Y : X;
+    s.key[i] = pid[q] * 16 + 4;
+    s.slot[i] = (int)q;
+  }
+  __syncthreads();
+  if (tid == 0) s_nmem = s_nobj;
+
+  // distinct neighbour cells of the 3x3 block
+  int nb[8];
+  int nnb = 0;
+  for (int oyc = -1; oyc <= 1; ++oyc)
+    for (int oxc = -1; oxc <= 1; ++oxc) {
+      const int qx = ((cx + oxc) % g.cells_x + g.cells_x) % g.cells_x;
+      const int qy = ((cy + oyc) % g.cells_y + g.cells_y) % g.cells_y;
+      const int q = qy * g.cells_x + qx;
+      if (q == c) continue;
+      bool dup = false;
+      for (int e = 0; e < nnb; ++e) dup |= (nb[e] == q);
+      if (!dup) nb[nnb++] = q;
+    }
+
+  // frozen images within sigma of the cell rectangle
+  for (int e = 0; e < nnb; ++e) {
+    const int n = nb[e];
+    const int nn = min(cnt[n], g.cap_mem);
+    for (int k = tid; k < nn; k += bt) {
+      const int64_t q = (int64_t)n * g.cap_mem + k;
+      const double X0 = wrap_half(px[q] - ox, L);
+      const double Y0 = wrap_half(py[q] - oy, L);
+      const int id = pid[q];
+      for (int kx = -1; kx <= 1; ++kx) {
+        const double X = (kx == 0) ? X0 : (kx > 0 ? X0 + L : X0 - L);
+        if (!(X > -sigma && X < wl)) continue;
+        for (int ky = -1; ky <= 1; ++ky) {
+          const double Y = (ky == 0) ? Y0 : (ky > 0 ? Y0 + L : Y0 - L);
+          if (!(Y > -sigma && Y < hl)) continue;
+          const int i = atomicAdd(&s_nobj, 1);
+          if (i >= lay.cap_obj) {
+            s_overflow = 1;
+            continue;
+          }
+          s.a64[i] = axis == 0 ? X : Y;
+          s.b64[i] = axis == 0 ? Y : X;
+          s.key[i] = id * 16 + (kx + 1) * 3 + (ky + 1);
+          s.slot[i] = -1;
+        }
+      }
+    }
+  }
+  for (int k = tid; k <= lay.nbin; k += bt) s.hist[k] = 0;
+  __syncthreads();
+  if (s_overflow) {
+    if (tid == 0) atomicCAS(err, DEV_OK, DEV_CAPACITY);
+  }
+  const int nobj = min(s_nobj, lay.cap_obj);
+  const int nmem = s_nmem;
+
+  // members ranked by disk id (start disks are drawn by rank)
+  for (int i = tid; i < nmem; i += bt) {
+    const int ki = s.key[i];
+    int r = 0;
+    for (int k = 0; k < nmem; ++k) r += (s.key[k] < ki);
+    s.mrank[r] = i;
+  }
+  // strips across the chain axis: bin of the FP32 coordinate
+  for (int i = tid; i < nobj; i += bt) {
+    const float b32 = (float)s.b64[i];
+    int kb = (int)((b32 + g.sigf) * g.inv_bin_w);
+    kb = kb < 0 ? 0 : (kb >= lay.nbin ? lay.nbin - 1 : kb);
+    s.bin[i] = kb;
+    atomicAdd(&s.hist[kb], 1);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int run = 0;
+    for (int k = 0; k < lay.nbin; ++k) {
+      const int v = s.hist[k];
+      s.hist[k] = run;
+      run += v;
+    }
+    s.hist[lay.nbin] = run;
+  }
+  __syncthreads();
+
+  // write the record of group G, column gi
+  const int cpw = lay.cpw;
+  const int G = a / cpw, gi = a - G * cpw;
+  unsigned char* rec = records + (size_t)G * lay.bytes;
+  int* hdr = (int*)(rec + lay.off_hdr);
+  int* bst = (int*)(rec + lay.off_bstart);
+  int* mr = (int*)(rec + lay.off_mrank);
+  int* ms = (int*)(rec + lay.off_mslot);
+  float* a32 = (float*)(rec + lay.off_a32);
+  float* b32 = (float*)(rec + lay.off_b32);
+  double* a64 = (double*)(rec + lay.off_a64);
+  double* b64 = (double*)(rec + lay.off_b64);
+  int* key = (int*)(rec + lay.off_key);
+  int* info = (int*)(rec + lay.off_info);
+  if (tid == 0) {
+    hdr[gi] = nobj;
+    hdr[cpw + gi] = nmem;
+  }
+  for (int k = tid; k <= lay.nbin; k += bt) bst[k * cpw + gi] = s.hist[k];
+  __syncthreads();
+  for (int i = tid; i < nobj; i += bt) {
+    const int f = atomicAdd(&s.hist[s.bin[i]], 1);
+    s.fin[i] = f;
+    a32[f * cpw + gi] = (float)s.a64[i];
+    b32[f * cpw + gi] = (float)s.b64[i];
+    a64[f * cpw + gi] = s.a64[i];
+    b64[f * cpw + gi] = s.b64[i];
+    key[f * cpw + gi] = s.key[i];
+    info[f * cpw + gi] = -1;
+  }
+  __syncthreads();
+  for (int r = tid; r < nmem; r += bt) {
+    const int i = s.mrank[r];
+    mr[r * cpw + gi] = s.fin[i];
+    ms[r * cpw + gi] = s.slot[i];
+    info[s.fin[i] * cpw + gi] = r;
+  }
+}
+
+static size_t build_smem(const RecLayout& lay) {
+  return (sizeof(double) * 2 + sizeof(int) * 4) * (size_t)lay.cap_obj +
+         sizeof(int) * (size_t)lay.cap_mem + sizeof(int) * (size_t)(lay.nbin + 1) + 64;
+}
+
+void launch_frame_build(const Geom& g, const DevBufs& b, const RecLayout& lay, int colour_index,
+                        cudaStream_t s) {
+  const int n_active = (g.cells_x / 2) * (g.cells_y / 2);
+  const size_t sm = build_smem(lay);
+  int bt = 32;
+  if (lay.cap_obj > 256) bt = 128;
+  if (lay.cap_obj > 1024) bt = 256;
+  k_frame_build<<<n_active, bt, sm, s>>>(g, b.state, colour_index, b.px[b.cur], b.py[b.cur],
+                                         b.pid[b.cur], b.count[b.cur], b.records, lay, b.err);
+}
+
+size_t frame_build_smem(const RecLayout& lay) { return build_smem(lay); }
+
+int configure_frame_build(const RecLayout& lay) {
+  return cudaFuncSetAttribute(k_frame_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)build_smem(lay)) == cudaSuccess
+             ? 0
+             : -1;
+}
+
+}  // namespace ecmc

@@ -1,0 +1,155 @@
+// ecmc_internal.cuh -- shared declarations of the CUDA implementation of the
+// parallel event-chain sweep (Kampmann, Boltz, Kierfeld, arXiv:1409.6948).
+//
+// Data layout in device memory (all per handle):
+//   - positions live in "cell buckets": cell c owns the slot range
+//     [c * cap_mem, c * cap_mem + count[c]) of the SoA arrays px, py (float64)
+//     and pid (int32).  cap_mem is a rigorous bound on the number of disk
+//     centres that fit in one cell (disjoint disks of diameter sigma), so the
+//     binning pass needs no prefix sum;
+//   - two such buffers are used alternately: each sweep bins from one into
+//     the other (Sec. 3.4 step 1, new shifted decomposition);
+//   - per sweep, the four colour phases (Sec. 3.4 steps 2-6) each run a frame
+//     builder, which stages every active cell plus its frozen halo into a
+//     fixed-size record, and the chain kernel, which copies that record into
+//     shared memory and runs the chains;
+//   - a small device struct holds the sweep counter and the per-sweep draws,
+//     so one sweep is a fixed sequence of launches (graph-capturable).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ecmc {
+
+// ---- error word (device) ------------------------------------------------
+enum DevErr : int {
+  DEV_OK = 0,
+  DEV_CAPACITY = 1,   // a bucket or frame record overflowed its rigorous bound
+  DEV_CHAIN_CAP = 2,  // a chain reached the per-chain event cap
+  DEV_OVERLAP = 3,
+};
+
+constexpr int64_t kMaxEventsPerChain = int64_t(1) << 22;
+constexpr uint64_t kPurposeSweep = 0, kPurposeChain = 1;
+
+// ---- per-sweep device state ------------------------------------------------
+struct SweepState {
+  int64_t t;        // Philox counter of the current sweep
+  double sx, sy;    // shift of the cell lattice
+  int perm[4];      // colour order
+  int axis;         // 0: chains along x, 1: along y
+  int flat_input;   // 1: current positions are a flat id-ordered list
+  int64_t history_len;
+};
+
+// Per-cell results of one sweep (written by the cell's phase).
+struct CellStats {
+  double sum_b;     // contact sum of the cell's chains, in chain order
+  int events, lifts, frozen, walls;
+  int fp64_evals, chains, n_mem, pad;
+};
+
+// Running totals (device).
+struct RunTotals {
+  double sum_b, sum_disp, sum_b_w, sum_disp_w;
+  long long sweeps, chains, events, lifts, frozen, walls, fp64_evals;
+};
+
+struct ChainRec {
+  long long start_id, end_id, events, walls;
+};
+
+// ---- static geometry and capacities --------------------------------------
+struct Geom {
+  int64_t N;
+  double L, sigma, sig2, w, h, inv_w, inv_h, ell;
+  int cells_x, cells_y, ncell;
+  int n_m;
+  int dir_mode;
+  uint64_t seed, replica;
+  int cap_mem;       // slots per cell bucket (members)
+  int cap_obj;       // objects per frame (members + frozen images)
+  int nbin;          // strip bins across the chain axis per frame
+  float bin_w;       // strip bin width (sigma units already applied)
+  float inv_bin_w;
+  float sigf;        // sigma as float
+  float eps_d;       // bound on |FP32 difference - FP64 difference| in a frame
+  float s_margin;    // bound on |FP32 hit distance estimate - FP64 hit distance|
+  float sig_plus;    // FP32 miss threshold on |perpendicular offset|
+  float sig_minus;   // FP32 certain-hit threshold on |perpendicular offset|
+  float sig2f;
+  float strip_margin;
+  int precision;     // 0 FP64 candidates, 1 FP32 screening
+};
+
+// Frame record layout of one group of cpw cells (all arrays [index][cpw]).
+struct RecLayout {
+  int cpw;
+  int nbin, cap_mem, cap_obj;
+  size_t off_hdr, off_bstart, off_mrank, off_mslot, off_a32, off_b32, off_a64, off_b64,
+      off_key, off_info, bytes;
+};
+
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+
+inline RecLayout make_layout(int cpw, int nbin, int cap_mem, int cap_obj) {
+  RecLayout r;
+  r.cpw = cpw;
+  r.nbin = nbin;
+  r.cap_mem = cap_mem;
+  r.cap_obj = cap_obj;
+  size_t o = 0;
+  r.off_hdr = o;     o = align16(o + sizeof(int) * 2 * cpw);
+  r.off_bstart = o;  o = align16(o + sizeof(int) * (size_t)(nbin + 1) * cpw);
+  r.off_mrank = o;   o = align16(o + sizeof(int) * (size_t)cap_mem * cpw);
+  r.off_mslot = o;   o = align16(o + sizeof(int) * (size_t)cap_mem * cpw);
+  r.off_a32 = o;     o = align16(o + sizeof(float) * (size_t)cap_obj * cpw);
+  r.off_b32 = o;     o = align16(o + sizeof(float) * (size_t)cap_obj * cpw);
+  r.off_a64 = o;     o = align16(o + sizeof(double) * (size_t)cap_obj * cpw);
+  r.off_b64 = o;     o = align16(o + sizeof(double) * (size_t)cap_obj * cpw);
+  r.off_key = o;     o = align16(o + sizeof(int) * (size_t)cap_obj * cpw);
+  r.off_info = o;    o = align16(o + sizeof(int) * (size_t)cap_obj * cpw);
+  r.bytes = o;
+  return r;
+}
+
+// Device pointers of one handle.
+struct DevBufs {
+  double* px[2];
+  double* py[2];
+  int* pid[2];
+  int* count[2];
+  int cur;  // buffer holding the current positions
+  SweepState* state;
+  CellStats* cell_stats;
+  RunTotals* totals;
+  double* history;  // per sweep: sum_b_w, sum_disp_w
+  int64_t history_cap;
+  unsigned char* records;  // frame records of one colour
+  int* err;
+  ChainRec* chain_recs;    // optional, [ncell * n_m]
+};
+
+// ---- launchers (defined in the .cu files) --------------------------------
+void launch_sweep_begin(const Geom& g, const DevBufs& b, cudaStream_t s);
+void launch_bin(const Geom& g, const DevBufs& b, int src, int dst, cudaStream_t s);
+void launch_frame_build(const Geom& g, const DevBufs& b, const RecLayout& lay, int colour_index,
+                        cudaStream_t s);
+int launch_phase(const Geom& g, const DevBufs& b, const RecLayout& lay, int colour_index, int tpc,
+                 int warps_per_block, int records_on, cudaStream_t s);
+void launch_sweep_end(const Geom& g, const DevBufs& b, cudaStream_t s);
+void launch_gather(const Geom& g, const DevBufs& b, double* xy_out, cudaStream_t s);
+void launch_load_flat(const Geom& g, const DevBufs& b, const double* xy_dev, cudaStream_t s);
+void launch_cells_of(const Geom& g, const DevBufs& b, int* cell_of_id, cudaStream_t s);
+void launch_min_dist(const Geom& g, const DevBufs& b, double rcut, unsigned long long* out,
+                     cudaStream_t s);
+void launch_gr(const Geom& g, const DevBufs& b, double dr, int nbins, unsigned long long* counts,
+               cudaStream_t s);
+size_t frame_build_smem(const RecLayout& lay);
+int configure_frame_build(const RecLayout& lay);
+int configure_phase(const RecLayout& lay, int tpc, int warps);
+int probe_peaks(double* smem_gbs, double* fp64_gflops);
+size_t phase_smem_bytes(const RecLayout& lay, int warps_per_block);
+int phase_max_warps(const RecLayout& lay, int tpc);
+
+}  // namespace ecmc

@@ -1,0 +1,162 @@
+// ecmc_measure.cu -- measurements on the current configuration: the
+// pair-correlation histogram of Sec. 2 (ordered pairs, bins
+// [sigma + i dr, sigma + (i+1) dr)) and the smallest pair distance (the
+// no-overlap invariant).  Both walk the cell buckets of the last binning.
+#include "ecmc_device.cuh"
+#include "ecmc_internal.cuh"
+
+namespace ecmc {
+
+struct NbRange {
+  int n, first;  // number of cell offsets and the first offset
+};
+
+__device__ __forceinline__ NbRange nb_range(int R, int cells) {
+  NbRange r;
+  if (2 * R + 1 >= cells) {
+    r.n = cells;
+    r.first = 0;  // absolute columns 0 .. cells-1
+  } else {
+    r.n = 2 * R + 1;
+    r.first = -R;
+  }
+  return r;
+}
+
+template <bool GR>
+__global__ void k_pairs(Geom g, const double* __restrict__ px, const double* __restrict__ py,
+                        const int* __restrict__ cnt, double rcut, double dr, int nbins,
+                        unsigned long long* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = (int64_t)g.ncell * g.cap_mem;
+  if (i >= total) return;
+  const int c = (int)(i / g.cap_mem);
+  const int k = (int)(i - (int64_t)c * g.cap_mem);
+  if (k >= min(cnt[c], g.cap_mem)) return;
+  const int cx = c % g.cells_x, cy = c / g.cells_x;
+  const double xi = px[i], yi = py[i];
+  const double L = g.L;
+  const int Rx = (int)ceil(rcut * g.inv_w * (1.0 + 1e-9));
+  const int Ry = (int)ceil(rcut * g.inv_h * (1.0 + 1e-9));
+  const NbRange rx = nb_range(Rx, g.cells_x), ry = nb_range(Ry, g.cells_y);
+  const bool absx = (2 * Rx + 1 >= g.cells_x), absy = (2 * Ry + 1 >= g.cells_y);
+  unsigned long long best = __double_as_longlong(rcut * rcut);
+  for (int oy = 0; oy < ry.n; ++oy) {
+    const int qy = absy ? oy : ((cy + ry.first + oy) % g.cells_y + g.cells_y) % g.cells_y;
+    for (int ox = 0; ox < rx.n; ++ox) {
+      const int qx = absx ? ox : ((cx + rx.first + ox) % g.cells_x + g.cells_x) % g.cells_x;
+      const int q = qy * g.cells_x + qx;
+      const int nq = min(cnt[q], g.cap_mem);
+      const int64_t b0 = (int64_t)q * g.cap_mem;
+      for (int kk = 0; kk < nq; ++kk) {
+        const int64_t j = b0 + kk;
+        if (j == i) continue;
+        const double ddx = wrap_half(px[j] - xi, L);
+        const double ddy = wrap_half(py[j] - yi, L);
+        if (GR) {
+          const double d = sqrt(ddx * ddx + ddy * ddy);
+          const double qv = (d - g.sigma) / dr;
+          if (!(qv >= 0.0)) continue;
+          if (!(qv < (double)nbins)) continue;
+          atomicAdd(&out[(int)qv], 1ull);
+        } else {
+          const double d2 = ddx * ddx + ddy * ddy;
+          const unsigned long long bits = __double_as_longlong(d2);
+          if (bits < best) best = bits;
+        }
+      }
+    }
+  }
+  if (!GR) atomicMin(out, best);
+}
+
+void launch_min_dist(const Geom& g, const DevBufs& b, double rcut, unsigned long long* out,
+                     cudaStream_t s) {
+  const int bs = 128;
+  const int64_t total = (int64_t)g.ncell * g.cap_mem;
+  k_pairs<false><<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(
+      g, b.px[b.cur], b.py[b.cur], b.count[b.cur], rcut, 0.0, 0, out);
+}
+
+void launch_gr(const Geom& g, const DevBufs& b, double dr, int nbins, unsigned long long* counts,
+               cudaStream_t s) {
+  const int bs = 128;
+  const int64_t total = (int64_t)g.ncell * g.cap_mem;
+  const double rcut = g.sigma + dr * nbins;
+  k_pairs<true><<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(
+      g, b.px[b.cur], b.py[b.cur], b.count[b.cur], rcut, dr, nbins, counts);
+}
+
+}  // namespace ecmc
+
+// ---- device peak probes (roofline denominators) ---------------------------
+namespace ecmc {
+
+__global__ void k_probe_smem(float* out, int iters) {
+  __shared__ float4 buf[2048];
+  for (int i = threadIdx.x; i < 2048; i += blockDim.x)
+    buf[i] = make_float4((float)i, (float)i + 1.f, (float)i + 2.f, (float)i + 3.f);
+  __syncthreads();
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int base = threadIdx.x;
+  for (int i = 0; i < iters; ++i) {
+    const float4 v = buf[(base + i * 32) & 2047];
+    acc.x += v.x;
+    acc.y += v.y;
+    acc.z += v.z;
+    acc.w += v.w;
+  }
+  if (acc.x + acc.y + acc.z + acc.w == 1.2345f) out[0] = acc.x;
+}
+
+__global__ void k_probe_fp64(double* out, int iters) {
+  double a0 = threadIdx.x * 1e-3, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, a4 = a0 + 4,
+         a5 = a0 + 5, a6 = a0 + 6, a7 = a0 + 7;
+  const double m = 0.999999, c = 1e-7;
+  for (int i = 0; i < iters; ++i) {
+    a0 = fma(a0, m, c); a1 = fma(a1, m, c); a2 = fma(a2, m, c); a3 = fma(a3, m, c);
+    a4 = fma(a4, m, c); a5 = fma(a5, m, c); a6 = fma(a6, m, c); a7 = fma(a7, m, c);
+  }
+  const double s = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+  if (s == 123.456) out[0] = s;
+}
+
+int probe_peaks(double* smem_gbs, double* fp64_gflops) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  void* scratch = nullptr;
+  if (cudaMalloc(&scratch, 64) != cudaSuccess) return -1;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int blocks = sms * 8, threads = 256;
+  float ms = 0.f, best = 1e30f;
+  k_probe_smem<<<blocks, threads>>>((float*)scratch, 64);
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0);
+    k_probe_smem<<<blocks, threads>>>((float*)scratch, 4096);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = ms < best ? ms : best;
+  }
+  *smem_gbs = (double)blocks * threads * 4096.0 * 16.0 / (best * 1e-3) / 1e9;
+  best = 1e30f;
+  k_probe_fp64<<<blocks, threads>>>((double*)scratch, 16);
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0);
+    k_probe_fp64<<<blocks, threads>>>((double*)scratch, 1024);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = ms < best ? ms : best;
+  }
+  *fp64_gflops = (double)blocks * threads * 1024.0 * 8.0 * 2.0 / (best * 1e-3) / 1e9;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(scratch);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace ecmc

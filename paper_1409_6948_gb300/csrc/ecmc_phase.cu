@@ -1,0 +1,470 @@
+// ecmc_phase.cu -- the chain kernel: one colour phase of the sweep.
+//
+// Sec. 3.4 steps 5-6 with the straight event chain of Sec. 3.2: in every
+// active cell, n_m chains start at members drawn WITH replacement (member
+// number floor(v n_c / 2^64) in ascending-id order, v from Philox keyed by
+// (seed, replica) and counter (sweep, chain purpose, cell, chain)).  The
+// active disk moves along +/- the sweep's axis until the first of
+//   - the end of the displacement budget,
+//   - a contact with another member (the rest of the budget passes to it),
+//   - a contact with a frozen disk (the chain turns back along its axis),
+//   - the cell wall (the chain turns back; Fig. 1).
+// Ties: the budget end beats a contact, a contact beats a wall, equal hit
+// distances go to the smaller (disk id, image) key.
+//
+// Work layout: one warp serves cpw = 32/TPC cells; TPC lanes share one cell.
+// The warp copies its group's frame record into shared memory; every lane
+// group then runs its cell's chains.  Candidates come from the strip of
+// width 2 sigma across the chain axis around the active disk.  With FP32
+// screening, each candidate's hit distance is bracketed in FP32 by rigorous
+// error bounds, and only candidates that can be the first hit (in practice
+// one) are evaluated in FP64 with the reference arithmetic, so the decision
+// and the new position are exactly those of a full FP64 search.
+#include <climits>
+
+#include "ecmc_device.cuh"
+#include "ecmc_internal.cuh"
+
+namespace ecmc {
+
+struct Frame {
+  const int* bst;
+  const int* mrank;
+  const int* mslot;
+  float* a32;
+  const float* b32;
+  double* a64;
+  const double* b64;
+  const int* key;
+  const int* info;
+  unsigned char* touched;
+  int cpw;
+};
+
+// FP64 hit test and hit distance along an axis direction of sign sg,
+// written as the general expressions reduce for d = (+-1, 0):
+//   b = (x_j - x_m) . d,  c = (x_j - x_m) x d,  hit iff b > 0 and c^2 < sigma^2,
+//   s = max(0, b - sqrt(sigma^2 - c^2)).
+__device__ __forceinline__ bool exact_hit(double aj, double bj, double P, double Q, int sg,
+                                          double sig2, double& s, double& b) {
+  const double da = aj - P;
+  const double db = bj - Q;
+  b = (sg > 0) ? da : -da;
+  if (!(b > 0.0)) return false;
+  const double c2 = db * db;
+  if (!(c2 < sig2)) return false;
+  double v = b - sqrt(sig2 - c2);
+  if (v < 0.0) v = 0.0;
+  s = v;
+  return true;
+}
+
+__device__ __forceinline__ bool better(double s, int key, double bs, int bkey) {
+  return s < bs || (s == bs && key < bkey);
+}
+
+template <int TPC>
+__device__ __forceinline__ unsigned group_mask(int g) {
+  return TPC == 32 ? 0xffffffffu : (((1u << TPC) - 1u) << (g * TPC));
+}
+
+template <int TPC, bool SCREEN>
+__global__ void __launch_bounds__(256) k_phase(Geom g, const SweepState* __restrict__ st,
+                                               int colour_index,
+                                               const unsigned char* __restrict__ records,
+                                               RecLayout lay, int n_active, double* __restrict__ px,
+                                               double* __restrict__ py, CellStats* __restrict__ cs,
+                                               ChainRec* __restrict__ recs, int* err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int CPW = 32 / TPC;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_groups = (n_active + CPW - 1) / CPW;
+  const int G = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (G >= n_groups) return;
+
+  const size_t rec_bytes = lay.bytes;
+  const size_t t_bytes = align16((size_t)lay.cap_obj * CPW);
+  unsigned char* base = smem + (size_t)warp * (rec_bytes + t_bytes);
+  {
+    const int4* src = reinterpret_cast<const int4*>(records + (size_t)G * rec_bytes);
+    int4* dst = reinterpret_cast<int4*>(base);
+    const int n16 = (int)(rec_bytes / 16);
+    for (int i = lane; i < n16; i += 32) dst[i] = src[i];
+    int4* tz = reinterpret_cast<int4*>(base + rec_bytes);
+    const int4 z = make_int4(0, 0, 0, 0);
+    for (int i = lane; i < (int)(t_bytes / 16); i += 32) tz[i] = z;
+  }
+  __syncwarp();
+
+  Frame f;
+  f.cpw = CPW;
+  f.bst = (const int*)(base + lay.off_bstart);
+  f.mrank = (const int*)(base + lay.off_mrank);
+  f.mslot = (const int*)(base + lay.off_mslot);
+  f.a32 = (float*)(base + lay.off_a32);
+  f.b32 = (const float*)(base + lay.off_b32);
+  f.a64 = (double*)(base + lay.off_a64);
+  f.b64 = (const double*)(base + lay.off_b64);
+  f.key = (const int*)(base + lay.off_key);
+  f.info = (const int*)(base + lay.off_info);
+  f.touched = base + rec_bytes;
+  const int* hdr = (const int*)(base + lay.off_hdr);
+
+  const int gi = lane / TPC, sub = lane - gi * TPC;
+  const unsigned gmask = group_mask<TPC>(gi);
+  const int a = G * CPW + gi;
+  const bool valid = a < n_active;
+  const int colour = st->perm[colour_index];
+  const int hx = g.cells_x >> 1;
+  const int cx = 2 * (a % hx) + (colour & 1);
+  const int cy = 2 * (a / hx) + (colour >> 1);
+  const int c = cy * g.cells_x + cx;
+  const int axis = st->axis;
+  const int64_t t = st->t;
+  const double E = axis == 0 ? g.w : g.h;  // cell extent along the chain axis
+  const int nmem = valid ? hdr[CPW + gi] : 0;
+
+  double sum_b = 0.0;
+  int n_events = 0, n_lifts = 0, n_frozen = 0, n_walls = 0, n_fp64 = 0, n_chains = 0;
+
+  // chain state (identical in the TPC lanes of a group)
+  int k = 0;
+  bool active = false;
+  int m = 0, sg = 1;
+  double P = 0.0, Q = 0.0, r = 0.0;
+  float P32 = 0.f, Q32 = 0.f;
+  int64_t n_iter = 0;
+  int ch_events = 0, ch_walls = 0, start_key = 0;
+
+  bool done = (!valid) || nmem == 0;
+  while (!done) {
+    if (!active) {
+      if (k >= g.n_m) {
+        done = true;
+        break;
+      }
+      const U64x4 v = philox((uint64_t)t, kPurposeChain, (uint64_t)c, (uint64_t)k, g.seed,
+                             g.replica);
+      const int idx = (int)below_n(v.v[0], (uint64_t)nmem);
+      m = f.mrank[idx * CPW + gi];
+      sg = (g.dir_mode == 1) ? 1 : ((v.v[1] >> 63) ? -1 : 1);
+      P = f.a64[m * CPW + gi];
+      Q = f.b64[m * CPW + gi];
+      P32 = f.a32[m * CPW + gi];
+      Q32 = f.b32[m * CPW + gi];
+      r = g.ell;
+      f.touched[m * CPW + gi] = 1;
+      start_key = f.key[m * CPW + gi];
+      n_iter = 0;
+      ch_events = 0;
+      ch_walls = 0;
+      active = true;
+      ++k;
+      ++n_chains;
+    }
+    bool end_chain = false;
+    if (n_iter >= kMaxEventsPerChain) {
+      atomicCAS(err, DEV_OK, DEV_CHAIN_CAP);
+      end_chain = true;
+    } else {
+      // distance to the wall ahead (FP64; the axis direction has |d| = 1)
+      double sw = (sg > 0) ? (E - P) : P;
+      if (sw < 0.0) sw = 0.0;
+
+      // strip of candidates across the axis
+      const float qlo = Q32 - g.sig_plus - g.strip_margin;
+      const float qhi = Q32 + g.sig_plus + g.strip_margin;
+      int klo = (int)((qlo + g.sigf) * g.inv_bin_w);
+      int khi = (int)((qhi + g.sigf) * g.inv_bin_w);
+      klo = klo < 0 ? 0 : (klo >= lay.nbin ? lay.nbin - 1 : klo);
+      khi = khi < 0 ? 0 : (khi >= lay.nbin ? lay.nbin - 1 : khi);
+      const int jbeg = f.bst[klo * CPW + gi];
+      const int jend = f.bst[(khi + 1) * CPW + gi];
+
+      double best_s = __longlong_as_double(0x7ff0000000000000ll);  // +inf
+      double best_b = 0.0;
+      int best_key = INT_MAX, best_j = -1;
+
+      if (SCREEN) {
+        const float eps = g.eps_d, smarg = g.s_margin;
+        float U = __int_as_float(0x7f800000), L1 = U, L2 = U;
+        int j1 = -1;
+        for (int j = jbeg + sub; j < jend; j += TPC) {
+          if (j == m) continue;
+          const float da = f.a32[j * CPW + gi] - P32;
+          const float db = f.b32[j * CPW + gi] - Q32;
+          const float bb = sg > 0 ? da : -da;
+          if (!(bb > -eps)) continue;
+          const float adb = fabsf(db);
+          if (!(adb < g.sig_plus)) continue;
+          float x = fmaxf(fmaf(-adb, adb, g.sig2f), 0.0f);
+          const float sq = x * rsqrtf(fmaxf(x, 1e-30f));
+          const float sc = bb - sq;
+          const float lo = sc - smarg;
+          if (lo < L1) {
+            L2 = L1;
+            L1 = lo;
+            j1 = j;
+          } else if (lo < L2) {
+            L2 = lo;
+          }
+          if (bb > eps && adb < g.sig_minus) U = fminf(U, fmaxf(sc + smarg, 0.0f));
+        }
+        if (TPC > 1) {
+#pragma unroll
+          for (int o = 1; o < TPC; o <<= 1) {
+            const float oU = __shfl_xor_sync(gmask, U, o);
+            const float oL1 = __shfl_xor_sync(gmask, L1, o);
+            const float oL2 = __shfl_xor_sync(gmask, L2, o);
+            const int oj1 = __shfl_xor_sync(gmask, j1, o);
+            U = fminf(U, oU);
+            const float nL2 = fminf(fmaxf(L1, oL1), fminf(L2, oL2));
+            if (oL1 < L1 || (oL1 == L1 && oj1 < j1)) {
+              L1 = oL1;
+              j1 = oj1;
+            }
+            L2 = nL2;
+          }
+        }
+        const double T = (r < sw) ? r : sw;
+        const double Lam = fmin((double)U, T);
+        if ((double)L1 <= Lam) {
+          if ((double)L2 > Lam) {
+            // a single candidate can be the first hit
+            double s, b;
+            if (exact_hit(f.a64[j1 * CPW + gi], f.b64[j1 * CPW + gi], P, Q, sg, g.sig2, s, b)) {
+              best_s = s;
+              best_b = b;
+              best_key = f.key[j1 * CPW + gi];
+              best_j = j1;
+            }
+            ++n_fp64;
+          } else {
+            // near tie: every candidate whose lower bound reaches the
+            // threshold is evaluated in FP64
+            int nev = 0;
+            for (int j = jbeg + sub; j < jend; j += TPC) {
+              if (j == m) continue;
+              const float da = f.a32[j * CPW + gi] - P32;
+              const float db = f.b32[j * CPW + gi] - Q32;
+              const float bb = sg > 0 ? da : -da;
+              if (!(bb > -eps)) continue;
+              const float adb = fabsf(db);
+              if (!(adb < g.sig_plus)) continue;
+              float x = fmaxf(fmaf(-adb, adb, g.sig2f), 0.0f);
+              const float sq = x * rsqrtf(fmaxf(x, 1e-30f));
+              const float lo = (bb - sq) - smarg;
+              if (!((double)lo <= Lam)) continue;
+              ++nev;
+              double s, b;
+              if (exact_hit(f.a64[j * CPW + gi], f.b64[j * CPW + gi], P, Q, sg, g.sig2, s, b)) {
+                const int kj = f.key[j * CPW + gi];
+                if (better(s, kj, best_s, best_key)) {
+                  best_s = s;
+                  best_b = b;
+                  best_key = kj;
+                  best_j = j;
+                }
+              }
+            }
+            if (TPC > 1) {
+#pragma unroll
+              for (int o = 1; o < TPC; o <<= 1) {
+                const double os = __shfl_xor_sync(gmask, best_s, o);
+                const double ob = __shfl_xor_sync(gmask, best_b, o);
+                const int ok = __shfl_xor_sync(gmask, best_key, o);
+                const int oj = __shfl_xor_sync(gmask, best_j, o);
+                nev += __shfl_xor_sync(gmask, nev, o);
+                if (better(os, ok, best_s, best_key)) {
+                  best_s = os;
+                  best_b = ob;
+                  best_key = ok;
+                  best_j = oj;
+                }
+              }
+            }
+            n_fp64 += nev;
+          }
+        }
+      } else {
+        // every strip candidate in FP64
+        int nev = 0;
+        for (int j = jbeg + sub; j < jend; j += TPC) {
+          if (j == m) continue;
+          ++nev;
+          double s, b;
+          if (exact_hit(f.a64[j * CPW + gi], f.b64[j * CPW + gi], P, Q, sg, g.sig2, s, b)) {
+            const int kj = f.key[j * CPW + gi];
+            if (better(s, kj, best_s, best_key)) {
+              best_s = s;
+              best_b = b;
+              best_key = kj;
+              best_j = j;
+            }
+          }
+        }
+        if (TPC > 1) {
+#pragma unroll
+          for (int o = 1; o < TPC; o <<= 1) {
+            const double os = __shfl_xor_sync(gmask, best_s, o);
+            const double ob = __shfl_xor_sync(gmask, best_b, o);
+            const int ok = __shfl_xor_sync(gmask, best_key, o);
+            const int oj = __shfl_xor_sync(gmask, best_j, o);
+            nev += __shfl_xor_sync(gmask, nev, o);
+            if (better(os, ok, best_s, best_key)) {
+              best_s = os;
+              best_b = ob;
+              best_key = ok;
+              best_j = oj;
+            }
+          }
+        }
+        n_fp64 += nev;
+      }
+
+      // event decision in FP64 (end < contact < wall on ties)
+      if (r <= best_s && r <= sw) {
+        P = P + ((sg > 0) ? r : -r);
+        end_chain = true;
+      } else if (best_s <= sw) {
+        const double Pn = P + ((sg > 0) ? best_s : -best_s);
+        r = r - best_s;
+        sum_b += best_b - best_s;
+        ++n_events;
+        ++ch_events;
+        ++n_iter;
+        if (f.info[best_j * CPW + gi] >= 0) {
+          // lift: the hit member carries on with the rest of the budget
+          f.a64[m * CPW + gi] = Pn;
+          f.a32[m * CPW + gi] = (float)Pn;
+          m = best_j;
+          P = f.a64[m * CPW + gi];
+          Q = f.b64[m * CPW + gi];
+          P32 = f.a32[m * CPW + gi];
+          Q32 = f.b32[m * CPW + gi];
+          f.touched[m * CPW + gi] = 1;
+          ++n_lifts;
+        } else {
+          // frozen disk: the chain turns back along its axis
+          P = Pn;
+          P32 = (float)P;
+          sg = -sg;
+          ++n_frozen;
+        }
+      } else {
+        P = (sg > 0) ? E : 0.0;
+        P32 = (float)P;
+        sg = -sg;
+        r = r - sw;
+        ++n_walls;
+        ++ch_walls;
+        ++n_iter;
+      }
+    }
+    if (end_chain) {
+      f.a64[m * CPW + gi] = P;
+      f.a32[m * CPW + gi] = (float)P;
+      if (recs != nullptr && sub == 0) {
+        ChainRec rc;
+        rc.start_id = start_key >> 4;
+        rc.end_id = f.key[m * CPW + gi] >> 4;
+        rc.events = ch_events;
+        rc.walls = ch_walls;
+        recs[(int64_t)c * g.n_m + (k - 1)] = rc;
+      }
+      active = false;
+    }
+  }
+
+  if (!valid) return;
+  if (TPC > 1) __syncwarp(gmask);
+  // write the members that were active in a chain back in box coordinates
+  const double ox = st->sx + (double)cx * g.w;
+  const double oy = st->sy + (double)cy * g.h;
+  for (int q = sub; q < nmem; q += TPC) {
+    const int j = f.mrank[q * CPW + gi];
+    if (!f.touched[j * CPW + gi]) continue;
+    const double A = f.a64[j * CPW + gi], B = f.b64[j * CPW + gi];
+    const double X = axis == 0 ? A : B, Y = axis == 0 ? B : A;
+    const int slot = f.mslot[q * CPW + gi];
+    px[slot] = wrap_box0(X + ox, g.L);
+    py[slot] = wrap_box0(Y + oy, g.L);
+  }
+  if (sub == 0) {
+    CellStats s;
+    s.sum_b = sum_b;
+    s.events = n_events;
+    s.lifts = n_lifts;
+    s.frozen = n_frozen;
+    s.walls = n_walls;
+    s.fp64_evals = n_fp64;
+    s.chains = n_chains;
+    s.n_mem = nmem;
+    s.pad = 0;
+    cs[c] = s;
+  }
+}
+
+size_t phase_smem_bytes(const RecLayout& lay, int warps_per_block) {
+  return (size_t)warps_per_block * (lay.bytes + align16((size_t)lay.cap_obj * lay.cpw));
+}
+
+template <int TPC, bool SCREEN>
+static int launch_t(const Geom& g, const DevBufs& b, const RecLayout& lay, int colour_index,
+                    int warps, int records_on, cudaStream_t s) {
+  const int n_active = (g.cells_x / 2) * (g.cells_y / 2);
+  const int cpw = 32 / TPC;
+  const int n_groups = (n_active + cpw - 1) / cpw;
+  const int blocks = (n_groups + warps - 1) / warps;
+  const size_t sm = phase_smem_bytes(lay, warps);
+  k_phase<TPC, SCREEN><<<blocks, 32 * warps, sm, s>>>(
+      g, b.state, colour_index, b.records, lay, n_active, b.px[b.cur], b.py[b.cur], b.cell_stats,
+      records_on ? b.chain_recs : nullptr, b.err);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <int TPC>
+static int configure_t(size_t sm) {
+  if (cudaFuncSetAttribute(k_phase<TPC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm) != cudaSuccess)
+    return -1;
+  if (cudaFuncSetAttribute(k_phase<TPC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm) != cudaSuccess)
+    return -1;
+  return 0;
+}
+
+int configure_phase(const RecLayout& lay, int tpc, int warps) {
+  const size_t sm = phase_smem_bytes(lay, warps);
+  switch (tpc) {
+    case 1: return configure_t<1>(sm);
+    case 2: return configure_t<2>(sm);
+    case 4: return configure_t<4>(sm);
+    case 8: return configure_t<8>(sm);
+    case 16: return configure_t<16>(sm);
+    case 32: return configure_t<32>(sm);
+    default: return -1;
+  }
+}
+
+int launch_phase(const Geom& g, const DevBufs& b, const RecLayout& lay, int colour_index, int tpc,
+                 int warps, int records_on, cudaStream_t s) {
+  const bool scr = g.precision == 1;
+#define ECMC_CASE(T)                                                                    \
+  case T:                                                                               \
+    return scr ? launch_t<T, true>(g, b, lay, colour_index, warps, records_on, s)      \
+               : launch_t<T, false>(g, b, lay, colour_index, warps, records_on, s);
+  switch (tpc) {
+    ECMC_CASE(1)
+    ECMC_CASE(2)
+    ECMC_CASE(4)
+    ECMC_CASE(8)
+    ECMC_CASE(16)
+    ECMC_CASE(32)
+    default:
+      return -1;
+  }
+#undef ECMC_CASE
+}
+
+}  // namespace ecmc

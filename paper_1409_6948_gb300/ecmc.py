@@ -1,0 +1,278 @@
+"""Thin ctypes binding of libecmc.so (include/ecmc.h).
+
+Argument marshalling only: every step of the sweep runs in the CUDA library.
+The binding raises if the library cannot be loaded; there is no fallback.
+Device buffers may be passed as torch CUDA tensors (their data pointer is
+used); host buffers as numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+ERR_ARG, ERR_CUDA, ERR_OOM, ERR_OVERLAP, ERR_TIMEOUT, ERR_STATE, ERR_CAPACITY, \
+    ERR_UNSUPPORTED, ERR_CHAIN_CAP = -1, -2, -3, -4, -5, -6, -7, -8, -9
+
+PARAM_N_CHAINS = 1
+PARAM_DIR_MODE = 2
+PARAM_PRECISION = 3
+PARAM_REPLICA = 4
+PARAM_LANES_PER_CELL = 5
+PARAM_GR_DR = 6
+PARAM_GR_RMAX = 7
+PARAM_TIMING = 8
+PARAM_STRIP_WIDTH = 9
+PARAM_RECORD_CHAINS = 10
+PARAM_WARPS_PER_BLOCK = 11
+PARAM_USE_GRAPH = 12
+
+DIR_PM_AXIS_ALT = 0
+DIR_POS_ONLY = 1
+PREC_FP64 = 0
+PREC_FP32_GEOM = 1
+
+
+class Counters(C.Structure):
+    _fields_ = [("sweeps", C.c_int64), ("chains", C.c_int64), ("events", C.c_int64),
+                ("lifts", C.c_int64), ("frozen_hits", C.c_int64), ("wall_hits", C.c_int64),
+                ("fp64_evals", C.c_int64), ("sum_b", C.c_double), ("sum_disp", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Timing(C.Structure):
+    _fields_ = [("bin_ms", C.c_double), ("frame_ms", C.c_double), ("phase_ms", C.c_double),
+                ("other_ms", C.c_double), ("bin_launches", C.c_int64),
+                ("frame_launches", C.c_int64), ("phase_launches", C.c_int64),
+                ("other_launches", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+CHAIN_REC = np.dtype([("start_id", np.int64), ("end_id", np.int64), ("events", np.int64),
+                      ("walls", np.int64)])
+
+# every symbol the header declares, with (restype, argtypes)
+_H = C.c_void_p
+_SIGS = {
+    "ecmc_create": (C.c_int, [C.POINTER(_H), C.c_int64, C.c_double, C.c_double, C.c_int, C.c_int,
+                              C.c_double, C.c_uint64]),
+    "ecmc_destroy": (C.c_int, [_H]),
+    "ecmc_set_param": (C.c_int, [_H, C.c_int, C.c_double]),
+    "ecmc_get_param": (C.c_int, [_H, C.c_int, C.POINTER(C.c_double)]),
+    "ecmc_set_stream": (C.c_int, [_H, C.c_void_p]),
+    "ecmc_set_positions": (C.c_int, [_H, C.c_void_p, C.c_int, C.c_int64]),
+    "ecmc_sweep": (C.c_int, [_H, C.c_int64]),
+    "ecmc_synchronize": (C.c_int, [_H]),
+    "ecmc_positions": (C.c_int, [_H, C.c_void_p, C.c_int]),
+    "ecmc_sweep_index": (C.c_int, [_H, C.POINTER(C.c_int64)]),
+    "ecmc_counters": (C.c_int, [_H, C.POINTER(Counters)]),
+    "ecmc_reset_stats": (C.c_int, [_H]),
+    "ecmc_pressure": (C.c_int, [_H, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "ecmc_gr_measure": (C.c_int, [_H]),
+    "ecmc_gr_counts": (C.c_int, [_H, C.c_void_p, C.c_int, C.POINTER(C.c_int64)]),
+    "ecmc_gr": (C.c_int, [_H, C.c_void_p, C.c_void_p, C.c_int]),
+    "ecmc_gr_nbins": (C.c_int, [_H, C.POINTER(C.c_int)]),
+    "ecmc_min_distance": (C.c_int, [_H, C.POINTER(C.c_double)]),
+    "ecmc_last_cells": (C.c_int, [_H, C.c_void_p]),
+    "ecmc_kernel_times": (C.c_int, [_H, C.POINTER(Timing)]),
+    "ecmc_chain_records": (C.c_int, [_H, C.c_void_p, C.c_int64]),
+    "ecmc_device_peaks": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "ecmc_strerror": (C.c_char_p, [C.c_int]),
+    "ecmc_last_error_message": (C.c_char_p, []),
+    "ecmc_version": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libecmc.so (building it first if needed and allowed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError("libecmc.so is not built (run __graft_entry__.build())")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class EcmcError(RuntimeError):
+    def __init__(self, code, where):
+        lib = load()
+        msg = lib.ecmc_strerror(code).decode()
+        detail = lib.ecmc_last_error_message().decode()
+        super().__init__("%s: %s (%d): %s" % (where, msg, code, detail))
+        self.code = code
+
+
+def _check(rc, where):
+    if rc != OK:
+        raise EcmcError(rc, where)
+
+
+def _ptr(buf):
+    """(address, on_device) of a numpy array or torch tensor."""
+    if hasattr(buf, "data_ptr"):
+        return C.c_void_p(buf.data_ptr()), 1 if buf.is_cuda else 0
+    assert buf.flags.c_contiguous
+    return C.c_void_p(buf.ctypes.data), 0
+
+
+class Ecmc:
+    """One hard-disk system on the GPU (a handle of the C library)."""
+
+    def __init__(self, N, L, sigma, cells_x, cells_y, ell, seed):
+        lib = load()
+        h = _H()
+        _check(lib.ecmc_create(C.byref(h), int(N), float(L), float(sigma), int(cells_x),
+                               int(cells_y), float(ell), C.c_uint64(int(seed))), "ecmc_create")
+        self._h = h
+        self.N, self.L, self.sigma = int(N), float(L), float(sigma)
+        self.cells_x, self.cells_y = int(cells_x), int(cells_y)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ecmc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # parameters
+    def set_param(self, key, value):
+        _check(load().ecmc_set_param(self._h, int(key), float(value)), "ecmc_set_param")
+
+    def get_param(self, key):
+        v = C.c_double()
+        _check(load().ecmc_get_param(self._h, int(key), C.byref(v)), "ecmc_get_param")
+        return v.value
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, an integer cudaStream_t, or None."""
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        _check(load().ecmc_set_stream(self._h, C.c_void_p(stream or 0)), "ecmc_set_stream")
+
+    # configuration
+    def set_positions(self, xy, t0=0):
+        p, dev = _ptr(xy)
+        _check(load().ecmc_set_positions(self._h, p, dev, int(t0)), "ecmc_set_positions")
+
+    def positions(self, out=None):
+        if out is None:
+            out = np.empty(2 * self.N, np.float64)
+        p, dev = _ptr(out)
+        _check(load().ecmc_positions(self._h, p, dev), "ecmc_positions")
+        return out
+
+    def sweep(self, n=1):
+        _check(load().ecmc_sweep(self._h, int(n)), "ecmc_sweep")
+
+    def synchronize(self):
+        _check(load().ecmc_synchronize(self._h), "ecmc_synchronize")
+
+    def sweep_index(self):
+        t = C.c_int64()
+        _check(load().ecmc_sweep_index(self._h, C.byref(t)), "ecmc_sweep_index")
+        return t.value
+
+    # measurements
+    def counters(self):
+        c = Counters()
+        _check(load().ecmc_counters(self._h, C.byref(c)), "ecmc_counters")
+        return c
+
+    def reset_stats(self):
+        _check(load().ecmc_reset_stats(self._h), "ecmc_reset_stats")
+
+    def pressure(self):
+        p, se = C.c_double(), C.c_double()
+        _check(load().ecmc_pressure(self._h, C.byref(p), C.byref(se)), "ecmc_pressure")
+        return p.value, se.value
+
+    def gr_measure(self):
+        _check(load().ecmc_gr_measure(self._h), "ecmc_gr_measure")
+
+    def gr_nbins(self):
+        n = C.c_int()
+        _check(load().ecmc_gr_nbins(self._h, C.byref(n)), "ecmc_gr_nbins")
+        return n.value
+
+    def gr_counts(self):
+        nb = self.gr_nbins()
+        out = np.zeros(nb, np.int64)
+        nm = C.c_int64()
+        _check(load().ecmc_gr_counts(self._h, C.c_void_p(out.ctypes.data), nb, C.byref(nm)),
+               "ecmc_gr_counts")
+        return out, nm.value
+
+    def gr(self):
+        nb = self.gr_nbins()
+        g = np.zeros(nb)
+        r = np.zeros(nb)
+        _check(load().ecmc_gr(self._h, C.c_void_p(g.ctypes.data), C.c_void_p(r.ctypes.data), nb),
+               "ecmc_gr")
+        return r, g
+
+    def min_distance(self):
+        d = C.c_double()
+        _check(load().ecmc_min_distance(self._h, C.byref(d)), "ecmc_min_distance")
+        return d.value
+
+    def last_cells(self):
+        out = np.empty(self.N, np.int32)
+        _check(load().ecmc_last_cells(self._h, C.c_void_p(out.ctypes.data)), "ecmc_last_cells")
+        return out
+
+    def kernel_times(self):
+        t = Timing()
+        _check(load().ecmc_kernel_times(self._h, C.byref(t)), "ecmc_kernel_times")
+        return t
+
+    def chain_records(self):
+        nm = int(self.get_param(PARAM_N_CHAINS))
+        n = self.cells_x * self.cells_y * nm
+        out = np.zeros(n, CHAIN_REC)
+        _check(load().ecmc_chain_records(self._h, C.c_void_p(out.ctypes.data), n),
+               "ecmc_chain_records")
+        return out.reshape(self.cells_x * self.cells_y, nm)
+
+
+def version():
+    return load().ecmc_version().decode()
+
+
+def device_peaks():
+    """(shared-memory GB/s, FP64 GFLOP/s) measured on the current device."""
+    a, b = C.c_double(), C.c_double()
+    _check(load().ecmc_device_peaks(C.byref(a), C.byref(b)), "ecmc_device_peaks")
+    return a.value, b.value

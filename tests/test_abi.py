@@ -1,0 +1,72 @@
+"""The C-ABI library (no GPU needed): it loads, exports every function that
+include/ecmc.h declares, and rejects invalid arguments before touching the
+device."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import paper_1409_6948_gb300 as P
+from paper_1409_6948_gb300 import ecmc as E
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        with open(os.path.join(ROOT, "include", fn)) as f:
+            src = f.read()
+        names += re.findall(r"^ECMC_API\s+[\w\s\*]+?\b(ecmc_\w+)\s*\(", src, re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("ecmc_create", "ecmc_sweep", "ecmc_positions", "ecmc_pressure",
+                     "ecmc_destroy", "ecmc_set_stream", "ecmc_set_param", "ecmc_gr"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = C.CDLL(P.ecmc.library_path() if os.path.exists(P.ecmc.library_path()) else
+                 E._build.build())
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert set(declared_functions()) == set(E._SIGS)
+
+
+def test_version_and_messages():
+    assert "sm_103a" in P.version()
+    lib = P.load()
+    for code in range(-9, 1):
+        assert lib.ecmc_strerror(code).decode()
+
+
+@pytest.mark.parametrize("args", [
+    (255, 16.9, 1.0, 2, 2, 4.0, 1),      # N not a perfect square
+    (256, 16.9, 1.0, 3, 2, 4.0, 1),      # odd number of cells
+    (256, 16.9, 1.0, 0, 2, 4.0, 1),      # no cells
+    (256, 16.9, 1.0, 18, 18, 4.0, 1),    # cell side below sigma
+    (256, 15.0, 1.0, 2, 2, 4.0, 1),      # lattice spacing below sigma
+    (256, 16.9, 1.0, 2, 2, -1.0, 1),     # negative displacement
+    (256, -1.0, 1.0, 2, 2, 4.0, 1),      # negative box
+])
+def test_invalid_arguments_are_rejected_before_device_work(args):
+    lib = P.load()
+    h = C.c_void_p()
+    rc = lib.ecmc_create(C.byref(h), *[C.c_int64(args[0]), C.c_double(args[1]),
+                                       C.c_double(args[2]), C.c_int(args[3]), C.c_int(args[4]),
+                                       C.c_double(args[5]), C.c_uint64(args[6])])
+    assert rc == E.ERR_ARG and not h.value
+
+
+def test_null_handle_calls_fail_cleanly():
+    lib = P.load()
+    assert lib.ecmc_sweep(None, 1) == E.ERR_ARG
+    assert lib.ecmc_destroy(None) == 0
+    d = C.c_double()
+    assert lib.ecmc_pressure(None, C.byref(d), None) == E.ERR_ARG
