@@ -34,7 +34,8 @@
  *     per chain (the "+x/+y only" variant is not reversible, Sec. 3.2);
  *   - shift uniform on [0,w) x [0,h); colour order uniform over the 24
  *     orders, shared by all blocks; colour = (cx mod 2) + 2 (cy mod 2);
- *   - a disk belongs to the cell holding its centre (half-open cells);
+ *   - a disk belongs to the cell holding its centre (half-open cells),
+ *     cx = floor((x - s_x mod L) * (1/w)) clamped to the grid;
  *     start disk = member number floor(v n_c / 2^64) in ascending-id order;
  *   - geometry is done in the frame of the active cell: the cell occupies
  *     [0,w] x [0,h]; its members and every periodic image of every other
@@ -147,7 +148,8 @@ void orc_sweep_draws(const orc_params* p, int64_t t, double* shift_x, double* sh
 static int cell_index_1d(double v, double shift, double L, double w, int cells) {
   double u = v - shift;
   if (u < 0.0) u += L;
-  int c = (int)(u / w);
+  const double inv_w = 1.0 / w;
+  int c = (int)(u * inv_w);
   if (c >= cells) c = cells - 1;
   if (c < 0) c = 0;
   return c;
