@@ -207,7 +207,10 @@ def run_ours(args):
     if args.tpc:
         g.set_param(E.PARAM_LANES_PER_CELL, args.tpc)
     g.set_param(E.PARAM_PRECISION, args.prec)
-    stream = torch.cuda.current_stream()
+    # a stream of our own (torch's default stream is the legacy NULL stream,
+    # which the library reads as "use your own stream")
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     g.set_stream(stream)
     nm = int(g.get_param(E.PARAM_N_CHAINS))
     tpc = int(g.get_param(E.PARAM_LANES_PER_CELL))

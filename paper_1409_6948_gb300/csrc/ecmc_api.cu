@@ -140,7 +140,7 @@ int compute_layout(ecmc_ctx* h) {
   h->tpc = choose_tpc(h);
   h->lay = make_layout(32 / h->tpc, g.nbin, g.cap_mem, g.cap_obj);
   const size_t per_warp = phase_smem_bytes(h->lay, 1);
-  const size_t limit = 200 * 1024;
+  const size_t limit = 232448;  // opt-in shared memory per block on sm_103
   if (per_warp > limit)
     return fail(ECMC_ERR_UNSUPPORTED,
                 "cell frame of %zu bytes per group does not fit in shared memory "
@@ -152,7 +152,7 @@ int compute_layout(ecmc_ctx* h) {
     if (w > 4) w = 4;
     if (w < 1) w = 1;
   }
-  if ((size_t)w * per_warp > 227 * 1024) w = (int)((227 * 1024) / per_warp);
+  if ((size_t)w * per_warp > limit) w = (int)(limit / per_warp);
   if (w < 1) w = 1;
   h->warps = w;
   const int n_active = (g.cells_x / 2) * (g.cells_y / 2);
@@ -164,7 +164,7 @@ int compute_layout(ecmc_ctx* h) {
     CK(cudaMalloc(&h->b.records, need));
     h->records_cap = need;
   }
-  if (frame_build_smem(h->lay) > 227 * 1024)
+  if (frame_build_smem(h->lay) > limit)
     return fail(ECMC_ERR_UNSUPPORTED, "cell frame too large for the frame builder");
   if (configure_frame_build(h->lay) || configure_phase(h->lay, h->tpc, h->warps))
     return fail(ECMC_ERR_CUDA, "kernel configuration failed: %s",

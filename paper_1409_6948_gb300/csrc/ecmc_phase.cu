@@ -63,11 +63,6 @@ __device__ __forceinline__ bool better(double s, int key, double bs, int bkey) {
   return s < bs || (s == bs && key < bkey);
 }
 
-template <int TPC>
-__device__ __forceinline__ unsigned group_mask(int g) {
-  return TPC == 32 ? 0xffffffffu : (((1u << TPC) - 1u) << (g * TPC));
-}
-
 template <int TPC, bool SCREEN>
 __global__ void __launch_bounds__(256) k_phase(Geom g, const SweepState* __restrict__ st,
                                                int colour_index,
@@ -111,7 +106,6 @@ __global__ void __launch_bounds__(256) k_phase(Geom g, const SweepState* __restr
   const int* hdr = (const int*)(base + lay.off_hdr);
 
   const int gi = lane / TPC, sub = lane - gi * TPC;
-  const unsigned gmask = group_mask<TPC>(gi);
   const int a = G * CPW + gi;
   const bool valid = a < n_active;
   const int colour = st->perm[colour_index];
@@ -126,8 +120,13 @@ __global__ void __launch_bounds__(256) k_phase(Geom g, const SweepState* __restr
 
   double sum_b = 0.0;
   int n_events = 0, n_lifts = 0, n_frozen = 0, n_walls = 0, n_fp64 = 0, n_chains = 0;
+  const double INF = __longlong_as_double(0x7ff0000000000000ll);
+  const unsigned FULL = 0xffffffffu;
 
-  // chain state (identical in the TPC lanes of a group)
+  // Chain state, identical in the TPC lanes of a group.  The loop is
+  // warp-uniform: every lane runs the same instruction stream each event
+  // (lanes whose cell is finished are masked), so one FP64 instruction
+  // serves every cell of the warp.
   int k = 0;
   bool active = false;
   int m = 0, sg = 1;
@@ -135,182 +134,152 @@ __global__ void __launch_bounds__(256) k_phase(Geom g, const SweepState* __restr
   float P32 = 0.f, Q32 = 0.f;
   int64_t n_iter = 0;
   int ch_events = 0, ch_walls = 0, start_key = 0;
-
   bool done = (!valid) || nmem == 0;
-  while (!done) {
-    if (!active) {
+
+  for (;;) {
+    if (!done && !active) {
       if (k >= g.n_m) {
         done = true;
-        break;
+      } else {
+        // start disk drawn with replacement among the members, sign of d
+        const U64x4 v = philox((uint64_t)t, kPurposeChain, (uint64_t)c, (uint64_t)k, g.seed,
+                               g.replica);
+        const int idx = (int)below_n(v.v[0], (uint64_t)nmem);
+        m = f.mrank[idx * CPW + gi];
+        sg = (g.dir_mode == 1) ? 1 : ((v.v[1] >> 63) ? -1 : 1);
+        P = f.a64[m * CPW + gi];
+        Q = f.b64[m * CPW + gi];
+        P32 = f.a32[m * CPW + gi];
+        Q32 = f.b32[m * CPW + gi];
+        r = g.ell;
+        f.touched[m * CPW + gi] = 1;
+        start_key = f.key[m * CPW + gi];
+        n_iter = 0;
+        ch_events = 0;
+        ch_walls = 0;
+        active = true;
+        ++k;
+        ++n_chains;
       }
-      const U64x4 v = philox((uint64_t)t, kPurposeChain, (uint64_t)c, (uint64_t)k, g.seed,
-                             g.replica);
-      const int idx = (int)below_n(v.v[0], (uint64_t)nmem);
-      m = f.mrank[idx * CPW + gi];
-      sg = (g.dir_mode == 1) ? 1 : ((v.v[1] >> 63) ? -1 : 1);
-      P = f.a64[m * CPW + gi];
-      Q = f.b64[m * CPW + gi];
-      P32 = f.a32[m * CPW + gi];
-      Q32 = f.b32[m * CPW + gi];
-      r = g.ell;
-      f.touched[m * CPW + gi] = 1;
-      start_key = f.key[m * CPW + gi];
-      n_iter = 0;
-      ch_events = 0;
-      ch_walls = 0;
-      active = true;
-      ++k;
-      ++n_chains;
     }
-    bool end_chain = false;
-    if (n_iter >= kMaxEventsPerChain) {
-      atomicCAS(err, DEV_OK, DEV_CHAIN_CAP);
-      end_chain = true;
-    } else {
-      // distance to the wall ahead (FP64; the axis direction has |d| = 1)
-      double sw = (sg > 0) ? (E - P) : P;
-      if (sw < 0.0) sw = 0.0;
+    if (__all_sync(FULL, done)) break;
+    const bool live = !done;
+    const bool capped = live && (n_iter >= kMaxEventsPerChain);
+    if (capped) atomicCAS(err, DEV_OK, DEV_CHAIN_CAP);
+    const bool go = live && !capped;
 
-      // strip of candidates across the axis
+    // distance to the wall ahead (the axis direction has |d| = 1)
+    const double sw0 = (sg > 0) ? (E - P) : P;
+    const double sw = (sw0 < 0.0) ? 0.0 : sw0;
+
+    // candidate strip across the axis
+    int jbeg = 0, jend = 0;
+    if (go) {
       const float qlo = Q32 - g.sig_plus - g.strip_margin;
       const float qhi = Q32 + g.sig_plus + g.strip_margin;
       int klo = (int)((qlo + g.sigf) * g.inv_bin_w);
       int khi = (int)((qhi + g.sigf) * g.inv_bin_w);
       klo = klo < 0 ? 0 : (klo >= lay.nbin ? lay.nbin - 1 : klo);
       khi = khi < 0 ? 0 : (khi >= lay.nbin ? lay.nbin - 1 : khi);
-      const int jbeg = f.bst[klo * CPW + gi];
-      const int jend = f.bst[(khi + 1) * CPW + gi];
+      jbeg = f.bst[klo * CPW + gi];
+      jend = f.bst[(khi + 1) * CPW + gi];
+    }
 
-      double best_s = __longlong_as_double(0x7ff0000000000000ll);  // +inf
-      double best_b = 0.0;
-      int best_key = INT_MAX, best_j = -1;
-
-      if (SCREEN) {
-        const float eps = g.eps_d, smarg = g.s_margin;
-        float U = __int_as_float(0x7f800000), L1 = U, L2 = U;
-        int j1 = -1;
-        for (int j = jbeg + sub; j < jend; j += TPC) {
-          if (j == m) continue;
-          const float da = f.a32[j * CPW + gi] - P32;
-          const float db = f.b32[j * CPW + gi] - Q32;
-          const float bb = sg > 0 ? da : -da;
-          if (!(bb > -eps)) continue;
-          const float adb = fabsf(db);
-          if (!(adb < g.sig_plus)) continue;
-          float x = fmaxf(fmaf(-adb, adb, g.sig2f), 0.0f);
-          const float sq = x * rsqrtf(fmaxf(x, 1e-30f));
-          const float sc = bb - sq;
-          const float lo = sc - smarg;
-          if (lo < L1) {
-            L2 = L1;
-            L1 = lo;
-            j1 = j;
-          } else if (lo < L2) {
-            L2 = lo;
-          }
-          if (bb > eps && adb < g.sig_minus) U = fminf(U, fmaxf(sc + smarg, 0.0f));
+    double best_s = INF, best_b = 0.0;
+    int best_key = INT_MAX, best_j = m;
+    if (SCREEN) {
+      const float eps = g.eps_d, smarg = g.s_margin;
+      float U = __int_as_float(0x7f800000), L1 = U, L2 = U;
+      int j1 = m;
+      for (int j = jbeg + sub; j < jend; j += TPC) {
+        if (j == m) continue;
+        const float da = f.a32[j * CPW + gi] - P32;
+        const float db = f.b32[j * CPW + gi] - Q32;
+        const float bb = sg > 0 ? da : -da;
+        if (!(bb > -eps)) continue;
+        const float adb = fabsf(db);
+        if (!(adb < g.sig_plus)) continue;
+        const float x = fmaxf(fmaf(-adb, adb, g.sig2f), 0.0f);
+        const float sc = bb - x * rsqrtf(fmaxf(x, 1e-30f));
+        const float lo = sc - smarg;
+        if (lo < L1) {
+          L2 = L1;
+          L1 = lo;
+          j1 = j;
+        } else if (lo < L2) {
+          L2 = lo;
         }
-        if (TPC > 1) {
+        if (bb > eps && adb < g.sig_minus) U = fminf(U, fmaxf(sc + smarg, 0.0f));
+      }
+      if (TPC > 1) {
 #pragma unroll
-          for (int o = 1; o < TPC; o <<= 1) {
-            const float oU = __shfl_xor_sync(gmask, U, o);
-            const float oL1 = __shfl_xor_sync(gmask, L1, o);
-            const float oL2 = __shfl_xor_sync(gmask, L2, o);
-            const int oj1 = __shfl_xor_sync(gmask, j1, o);
-            U = fminf(U, oU);
-            const float nL2 = fminf(fmaxf(L1, oL1), fminf(L2, oL2));
-            if (oL1 < L1 || (oL1 == L1 && oj1 < j1)) {
-              L1 = oL1;
-              j1 = oj1;
-            }
-            L2 = nL2;
+        for (int o = 1; o < TPC; o <<= 1) {
+          const float oU = __shfl_xor_sync(FULL, U, o);
+          const float oL1 = __shfl_xor_sync(FULL, L1, o);
+          const float oL2 = __shfl_xor_sync(FULL, L2, o);
+          const int oj1 = __shfl_xor_sync(FULL, j1, o);
+          U = fminf(U, oU);
+          const float nL2 = fminf(fmaxf(L1, oL1), fminf(L2, oL2));
+          if (oL1 < L1 || (oL1 == L1 && oj1 < j1)) {
+            L1 = oL1;
+            j1 = oj1;
           }
+          L2 = nL2;
         }
-        const double T = (r < sw) ? r : sw;
-        const double Lam = fmin((double)U, T);
-        if ((double)L1 <= Lam) {
-          if ((double)L2 > Lam) {
-            // a single candidate can be the first hit
-            double s, b;
-            if (exact_hit(f.a64[j1 * CPW + gi], f.b64[j1 * CPW + gi], P, Q, sg, g.sig2, s, b)) {
-              best_s = s;
-              best_b = b;
-              best_key = f.key[j1 * CPW + gi];
-              best_j = j1;
-            }
-            ++n_fp64;
-          } else {
-            // near tie: every candidate whose lower bound reaches the
-            // threshold is evaluated in FP64
-            int nev = 0;
-            for (int j = jbeg + sub; j < jend; j += TPC) {
-              if (j == m) continue;
-              const float da = f.a32[j * CPW + gi] - P32;
-              const float db = f.b32[j * CPW + gi] - Q32;
-              const float bb = sg > 0 ? da : -da;
-              if (!(bb > -eps)) continue;
-              const float adb = fabsf(db);
-              if (!(adb < g.sig_plus)) continue;
-              float x = fmaxf(fmaf(-adb, adb, g.sig2f), 0.0f);
-              const float sq = x * rsqrtf(fmaxf(x, 1e-30f));
-              const float lo = (bb - sq) - smarg;
-              if (!((double)lo <= Lam)) continue;
-              ++nev;
-              double s, b;
-              if (exact_hit(f.a64[j * CPW + gi], f.b64[j * CPW + gi], P, Q, sg, g.sig2, s, b)) {
-                const int kj = f.key[j * CPW + gi];
-                if (better(s, kj, best_s, best_key)) {
-                  best_s = s;
-                  best_b = b;
-                  best_key = kj;
-                  best_j = j;
-                }
-              }
-            }
-            if (TPC > 1) {
-#pragma unroll
-              for (int o = 1; o < TPC; o <<= 1) {
-                const double os = __shfl_xor_sync(gmask, best_s, o);
-                const double ob = __shfl_xor_sync(gmask, best_b, o);
-                const int ok = __shfl_xor_sync(gmask, best_key, o);
-                const int oj = __shfl_xor_sync(gmask, best_j, o);
-                nev += __shfl_xor_sync(gmask, nev, o);
-                if (better(os, ok, best_s, best_key)) {
-                  best_s = os;
-                  best_b = ob;
-                  best_key = ok;
-                  best_j = oj;
-                }
-              }
-            }
-            n_fp64 += nev;
-          }
-        }
-      } else {
-        // every strip candidate in FP64
+      }
+      // exact FP64 evaluation of the candidates that can be the first hit:
+      // those whose lower bound reaches min(smallest certain upper bound,
+      // budget, wall distance)
+      const double T = (r < sw) ? r : sw;
+      const double Lam = fmin((double)U, T);
+      const bool need = go && ((double)L1 <= Lam);
+      const bool multi = need && ((double)L2 <= Lam);
+      const bool single = need && !multi;
+      const int jj = single ? j1 : m;
+      double s1, b1;
+      const bool h1 = exact_hit(f.a64[jj * CPW + gi], f.b64[jj * CPW + gi], P, Q, sg, g.sig2,
+                                s1, b1);
+      if (single && h1) {
+        best_s = s1;
+        best_b = b1;
+        best_j = jj;
+      }
+      n_fp64 += single ? 1 : 0;
+      if (__any_sync(FULL, multi)) {
         int nev = 0;
-        for (int j = jbeg + sub; j < jend; j += TPC) {
-          if (j == m) continue;
-          ++nev;
-          double s, b;
-          if (exact_hit(f.a64[j * CPW + gi], f.b64[j * CPW + gi], P, Q, sg, g.sig2, s, b)) {
-            const int kj = f.key[j * CPW + gi];
-            if (better(s, kj, best_s, best_key)) {
-              best_s = s;
-              best_b = b;
-              best_key = kj;
-              best_j = j;
+        if (multi) {
+          for (int j = jbeg + sub; j < jend; j += TPC) {
+            if (j == m) continue;
+            const float da = f.a32[j * CPW + gi] - P32;
+            const float db = f.b32[j * CPW + gi] - Q32;
+            const float bb = sg > 0 ? da : -da;
+            if (!(bb > -eps)) continue;
+            const float adb = fabsf(db);
+            if (!(adb < g.sig_plus)) continue;
+            const float x = fmaxf(fmaf(-adb, adb, g.sig2f), 0.0f);
+            const float lo = (bb - x * rsqrtf(fmaxf(x, 1e-30f))) - smarg;
+            if (!((double)lo <= Lam)) continue;
+            ++nev;
+            double s, b;
+            if (exact_hit(f.a64[j * CPW + gi], f.b64[j * CPW + gi], P, Q, sg, g.sig2, s, b)) {
+              const int kj = f.key[j * CPW + gi];
+              if (better(s, kj, best_s, best_key)) {
+                best_s = s;
+                best_b = b;
+                best_key = kj;
+                best_j = j;
+              }
             }
           }
         }
         if (TPC > 1) {
 #pragma unroll
           for (int o = 1; o < TPC; o <<= 1) {
-            const double os = __shfl_xor_sync(gmask, best_s, o);
-            const double ob = __shfl_xor_sync(gmask, best_b, o);
-            const int ok = __shfl_xor_sync(gmask, best_key, o);
-            const int oj = __shfl_xor_sync(gmask, best_j, o);
-            nev += __shfl_xor_sync(gmask, nev, o);
+            const double os = __shfl_xor_sync(FULL, best_s, o);
+            const double ob = __shfl_xor_sync(FULL, best_b, o);
+            const int ok = __shfl_xor_sync(FULL, best_key, o);
+            const int oj = __shfl_xor_sync(FULL, best_j, o);
+            nev += __shfl_xor_sync(FULL, nev, o);
             if (better(os, ok, best_s, best_key)) {
               best_s = os;
               best_b = ob;
@@ -321,49 +290,86 @@ __global__ void __launch_bounds__(256) k_phase(Geom g, const SweepState* __restr
         }
         n_fp64 += nev;
       }
-
-      // event decision in FP64 (end < contact < wall on ties)
-      if (r <= best_s && r <= sw) {
-        P = P + ((sg > 0) ? r : -r);
-        end_chain = true;
-      } else if (best_s <= sw) {
-        const double Pn = P + ((sg > 0) ? best_s : -best_s);
-        r = r - best_s;
-        sum_b += best_b - best_s;
-        ++n_events;
-        ++ch_events;
-        ++n_iter;
-        if (f.info[best_j * CPW + gi] >= 0) {
-          // lift: the hit member carries on with the rest of the budget
-          f.a64[m * CPW + gi] = Pn;
-          f.a32[m * CPW + gi] = (float)Pn;
-          m = best_j;
-          P = f.a64[m * CPW + gi];
-          Q = f.b64[m * CPW + gi];
-          P32 = f.a32[m * CPW + gi];
-          Q32 = f.b32[m * CPW + gi];
-          f.touched[m * CPW + gi] = 1;
-          ++n_lifts;
-        } else {
-          // frozen disk: the chain turns back along its axis
-          P = Pn;
-          P32 = (float)P;
-          sg = -sg;
-          ++n_frozen;
+    } else {
+      // every strip candidate in FP64
+      int nev = 0;
+      for (int j = jbeg + sub; j < jend; j += TPC) {
+        if (j == m) continue;
+        ++nev;
+        double s, b;
+        if (exact_hit(f.a64[j * CPW + gi], f.b64[j * CPW + gi], P, Q, sg, g.sig2, s, b)) {
+          const int kj = f.key[j * CPW + gi];
+          if (better(s, kj, best_s, best_key)) {
+            best_s = s;
+            best_b = b;
+            best_key = kj;
+            best_j = j;
+          }
         }
-      } else {
-        P = (sg > 0) ? E : 0.0;
-        P32 = (float)P;
-        sg = -sg;
-        r = r - sw;
-        ++n_walls;
-        ++ch_walls;
-        ++n_iter;
       }
+      if (TPC > 1) {
+#pragma unroll
+        for (int o = 1; o < TPC; o <<= 1) {
+          const double os = __shfl_xor_sync(FULL, best_s, o);
+          const double ob = __shfl_xor_sync(FULL, best_b, o);
+          const int ok = __shfl_xor_sync(FULL, best_key, o);
+          const int oj = __shfl_xor_sync(FULL, best_j, o);
+          nev += __shfl_xor_sync(FULL, nev, o);
+          if (better(os, ok, best_s, best_key)) {
+            best_s = os;
+            best_b = ob;
+            best_key = ok;
+            best_j = oj;
+          }
+        }
+      }
+      n_fp64 += nev;
+    }
+
+    // event decision in FP64 (budget end < contact < wall on ties), as
+    // selects so that all lanes share one instruction stream
+    const bool is_end = (r <= best_s) && (r <= sw);
+    const bool is_contact = !is_end && (best_s <= sw);
+    const bool is_wall = !is_end && !is_contact;
+    const double step = is_end ? r : (is_contact ? best_s : sw);
+    const double Pstep = P + ((sg > 0) ? step : -step);
+    const double Pnew = is_wall ? ((sg > 0) ? E : 0.0) : Pstep;
+    const double rnew = r - step;
+    const double addb = is_contact ? (best_b - best_s) : 0.0;
+    const float P32n = (float)Pnew;
+    bool end_chain = capped;
+    if (go) {
+      sum_b += addb;
+      r = rnew;
+      const bool is_lift = is_contact && (f.info[best_j * CPW + gi] >= 0);
+      n_events += is_contact ? 1 : 0;
+      ch_events += is_contact ? 1 : 0;
+      n_lifts += is_lift ? 1 : 0;
+      n_frozen += (is_contact && !is_lift) ? 1 : 0;
+      n_walls += is_wall ? 1 : 0;
+      ch_walls += is_wall ? 1 : 0;
+      n_iter += (is_contact || is_wall) ? 1 : 0;
+      if (is_lift) {
+        // the hit member carries on with the rest of the budget
+        f.a64[m * CPW + gi] = Pnew;
+        f.a32[m * CPW + gi] = P32n;
+        m = best_j;
+        P = f.a64[m * CPW + gi];
+        Q = f.b64[m * CPW + gi];
+        P32 = f.a32[m * CPW + gi];
+        Q32 = f.b32[m * CPW + gi];
+        f.touched[m * CPW + gi] = 1;
+      } else {
+        P = Pnew;
+        P32 = P32n;
+        // frozen disk or wall: the chain turns back along its axis
+        if (!is_end) sg = -sg;
+      }
+      end_chain = is_end;
     }
     if (end_chain) {
       f.a64[m * CPW + gi] = P;
-      f.a32[m * CPW + gi] = (float)P;
+      f.a32[m * CPW + gi] = P32;
       if (recs != nullptr && sub == 0) {
         ChainRec rc;
         rc.start_id = start_key >> 4;
@@ -376,8 +382,8 @@ __global__ void __launch_bounds__(256) k_phase(Geom g, const SweepState* __restr
     }
   }
 
+  __syncwarp();
   if (!valid) return;
-  if (TPC > 1) __syncwarp(gmask);
   // write the members that were active in a chain back in box coordinates
   const double ox = st->sx + (double)cx * g.w;
   const double oy = st->sy + (double)cy * g.h;
