@@ -100,9 +100,11 @@ void set_screen_bounds(Geom& g) {
   const double ext = (g.w > g.h ? g.w : g.h) + 1.01 * g.sigma;
   double M = 1.0;
   while (M < ext) M *= 2.0;
-  // |FP32 difference - FP64 difference| <= 4.002 * 2^-24 * M (two roundings
-  // to FP32 of the operands, one of the difference, one FP64 rounding)
-  const double e = 4.5 * std::ldexp(1.0, -24) * M;
+  // |FP32 difference - FP64 difference| <= 6 * 2^-24 * M + tiny: each FP32
+  // operand is within 2^-23 M of its FP64 value (rounded to nearest in the
+  // frame builder, truncated toward zero after a move), the FP32 difference
+  // adds 2^-23 M, the FP64 difference 2^-52 M
+  const double e = 6.5 * std::ldexp(1.0, -24) * M;
   const double sig = g.sigma;
   // |x32 - (sigma^2 - ddy^2)| <= ex, x32 = fma(-|db|, |db|, sigma^2) in FP32
   const double ex = (2.0 * sig + 2.0 * e) * e + 3.0 * std::ldexp(1.0, -24) * sig * sig;
@@ -147,11 +149,7 @@ int compute_layout(ecmc_ctx* h) {
                 "(cells too large: use more cells)",
                 per_warp);
   int w = h->warps_param;
-  if (w == 0) {
-    w = (int)(limit / per_warp);
-    if (w > 4) w = 4;
-    if (w < 1) w = 1;
-  }
+  if (w == 0) w = 1;  // one warp per block spreads the groups over every SM
   if ((size_t)w * per_warp > limit) w = (int)(limit / per_warp);
   if (w < 1) w = 1;
   h->warps = w;

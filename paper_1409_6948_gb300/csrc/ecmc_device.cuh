@@ -73,3 +73,47 @@ __device__ __forceinline__ int cell_1d(double v, double shift, double L, double 
 }
 
 }  // namespace ecmc
+
+namespace ecmc {
+
+// ---- FP64 comparisons and conversions on the integer pipes ---------------
+// For doubles that are >= +0 (or +inf), the order of the bit patterns read
+// as signed 64-bit integers is the numeric order; negative values (and -0.0)
+// read as negative integers.
+__device__ __forceinline__ long long dbits(double v) { return __double_as_longlong(v); }
+__device__ __forceinline__ bool le_nn(double a, double b) { return dbits(a) <= dbits(b); }
+__device__ __forceinline__ bool lt_nn(double a, double b) { return dbits(a) < dbits(b); }
+__device__ __forceinline__ double min_nn(double a, double b) { return lt_nn(b, a) ? b : a; }
+// max(v, +0.0), mapping -0.0 to +0.0 (no result downstream distinguishes them)
+__device__ __forceinline__ double clamp0(double v) { return dbits(v) < 0 ? 0.0 : v; }
+// v with its sign flipped when neg is set (exact)
+__device__ __forceinline__ double flip_if(double v, bool neg) {
+  return __longlong_as_double(dbits(v) ^ (neg ? (long long)0x8000000000000000ull : 0ll));
+}
+
+// Double to float rounding toward zero: |v - f| < 2^-23 |v| for
+// 2^-126 <= |v| < 2^127; smaller magnitudes give +-0.
+__device__ __forceinline__ float to_float_trunc(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+  const int e = (int)((u >> 52) & 0x7ff);
+  if (e < 1023 - 126) return __int_as_float((int)sign);
+  const unsigned fe = (unsigned)(e - 1023 + 127);
+  const unsigned fm = (unsigned)((u >> 29) & 0x7fffffu);
+  return __int_as_float((int)(sign | (fe << 23) | fm));
+}
+
+// Non-negative double (or +inf) to the smallest float >= v.
+__device__ __forceinline__ float to_float_up_nn(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  if (u >= 0x7ff0000000000000ull) return __int_as_float(0x7f800000);
+  const int e = (int)(u >> 52);
+  if (e < 1023 - 126) return u == 0 ? 0.0f : __int_as_float(0x00800000);
+  if (e > 1023 + 127) return __int_as_float(0x7f800000);
+  const unsigned fe = (unsigned)(e - 1023 + 127);
+  unsigned bits = (fe << 23) | (unsigned)((u >> 29) & 0x7fffffu);
+  if (u & 0x1fffffffull) bits += 1u;  // a carry into the exponent is still the next float up
+  return __int_as_float((int)bits);
+}
+
+}  // namespace ecmc

@@ -94,14 +94,36 @@ __global__ void k_frame_build(Geom g, const SweepState* __restrict__ st, int col
       if (!dup) nb[nnb++] = q;
     }
 
-  // frozen images within sigma of the cell rectangle
+  // frozen images within sigma of the cell rectangle.  An FP32 screen with a
+  // margin well above its rounding error (|error| < 4 * 2^-23 L) discards the
+  // disks that no image can bring near the cell; the others take the FP64
+  // test, so the frame is exactly the one the FP64 test alone would build.
+  const float Lf = (float)L, hLf = 0.5f * (float)L;
+  const float oxf = to_float_trunc(ox), oyf = to_float_trunc(oy);
+  const float mf = 8.0f * 1.1920929e-7f * Lf + 1e-6f;
+  const float xlo = -(float)sigma - mf, xhi = (float)wl + mf;
+  const float ylo = -(float)sigma - mf, yhi = (float)hl + mf;
   for (int e = 0; e < nnb; ++e) {
     const int n = nb[e];
     const int nn = min(cnt[n], g.cap_mem);
     for (int k = tid; k < nn; k += bt) {
       const int64_t q = (int64_t)n * g.cap_mem + k;
-      const double X0 = wrap_half(px[q] - ox, L);
-      const double Y0 = wrap_half(py[q] - oy, L);
+      const double xq = px[q], yq = py[q];
+      {
+        float X0f = to_float_trunc(xq) - oxf;
+        X0f = X0f >= hLf ? X0f - Lf : (X0f < -hLf ? X0f + Lf : X0f);
+        float Y0f = to_float_trunc(yq) - oyf;
+        Y0f = Y0f >= hLf ? Y0f - Lf : (Y0f < -hLf ? Y0f + Lf : Y0f);
+        bool nx = false, ny = false;
+        for (int kk = -1; kk <= 1; ++kk) {
+          const float Xf = X0f + (float)kk * Lf, Yf = Y0f + (float)kk * Lf;
+          nx |= (Xf > xlo && Xf < xhi);
+          ny |= (Yf > ylo && Yf < yhi);
+        }
+        if (!(nx && ny)) continue;
+      }
+      const double X0 = wrap_half(xq - ox, L);
+      const double Y0 = wrap_half(yq - oy, L);
       const int id = pid[q];
       for (int kx = -1; kx <= 1; ++kx) {
         const double X = (kx == 0) ? X0 : (kx > 0 ? X0 + L : X0 - L);

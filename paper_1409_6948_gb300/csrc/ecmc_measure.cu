@@ -41,6 +41,9 @@ __global__ void k_pairs(Geom g, const double* __restrict__ px, const double* __r
   const NbRange rx = nb_range(Rx, g.cells_x), ry = nb_range(Ry, g.cells_y);
   const bool absx = (2 * Rx + 1 >= g.cells_x), absy = (2 * Ry + 1 >= g.cells_y);
   unsigned long long best = __double_as_longlong(rcut * rcut);
+  const float Lf = (float)L, hLf = 0.5f * Lf;
+  const float xif = to_float_trunc(xi), yif = to_float_trunc(yi);
+  const float rcf = (float)rcut + 8.0f * 1.1920929e-7f * Lf + 1e-6f;
   for (int oy = 0; oy < ry.n; ++oy) {
     const int qy = absy ? oy : ((cy + ry.first + oy) % g.cells_y + g.cells_y) % g.cells_y;
     for (int ox = 0; ox < rx.n; ++ox) {
@@ -51,6 +54,14 @@ __global__ void k_pairs(Geom g, const double* __restrict__ px, const double* __r
       for (int kk = 0; kk < nq; ++kk) {
         const int64_t j = b0 + kk;
         if (j == i) continue;
+        if (!GR) {
+          // FP32 screen: pairs farther than rcut (plus a margin above the
+          // FP32 rounding error) cannot change the minimum
+          float fx = to_float_trunc(px[j]) - xif, fy = to_float_trunc(py[j]) - yif;
+          fx = fx >= hLf ? fx - Lf : (fx < -hLf ? fx + Lf : fx);
+          fy = fy >= hLf ? fy - Lf : (fy < -hLf ? fy + Lf : fy);
+          if (fabsf(fx) > rcf || fabsf(fy) > rcf) continue;
+        }
         const double ddx = wrap_half(px[j] - xi, L);
         const double ddy = wrap_half(py[j] - yi, L);
         if (GR) {

@@ -45,18 +45,22 @@ struct Frame {
 // written as the general expressions reduce for d = (+-1, 0):
 //   b = (x_j - x_m) . d,  c = (x_j - x_m) x d,  hit iff b > 0 and c^2 < sigma^2,
 //   s = max(0, b - sqrt(sigma^2 - c^2)).
+// The arithmetic is exactly the reference's; comparisons and sign changes run
+// on the integer pipes (see ecmc_device.cuh), and the square root is taken of
+// a positive placeholder when the candidate misses, so there is no branch.
 __device__ __forceinline__ bool exact_hit(double aj, double bj, double P, double Q, int sg,
                                           double sig2, double& s, double& b) {
   const double da = aj - P;
   const double db = bj - Q;
-  b = (sg > 0) ? da : -da;
-  if (!(b > 0.0)) return false;
+  const long long bda = dbits(da);
+  const bool ahead = (sg > 0) ? (bda > 0) : (bda < 0 && bda != (long long)0x8000000000000000ull);
+  b = flip_if(da, sg < 0);
   const double c2 = db * db;
-  if (!(c2 < sig2)) return false;
-  double v = b - sqrt(sig2 - c2);
-  if (v < 0.0) v = 0.0;
-  s = v;
-  return true;
+  const bool hit = ahead && lt_nn(c2, sig2);
+  const double x = sig2 - c2;
+  const double sq = sqrt(hit ? x : 1.0);
+  s = clamp0(b - sq);
+  return hit;
 }
 
 __device__ __forceinline__ bool better(double s, int key, double bs, int bkey) {
@@ -169,8 +173,7 @@ __global__ void __launch_bounds__(256) k_phase(Geom g, const SweepState* __restr
     const bool go = live && !capped;
 
     // distance to the wall ahead (the axis direction has |d| = 1)
-    const double sw0 = (sg > 0) ? (E - P) : P;
-    const double sw = (sw0 < 0.0) ? 0.0 : sw0;
+    const double sw = clamp0((sg > 0) ? (E - P) : P);
 
     // candidate strip across the axis
     int jbeg = 0, jend = 0;
@@ -230,10 +233,9 @@ __global__ void __launch_bounds__(256) k_phase(Geom g, const SweepState* __restr
       // exact FP64 evaluation of the candidates that can be the first hit:
       // those whose lower bound reaches min(smallest certain upper bound,
       // budget, wall distance)
-      const double T = (r < sw) ? r : sw;
-      const double Lam = fmin((double)U, T);
-      const bool need = go && ((double)L1 <= Lam);
-      const bool multi = need && ((double)L2 <= Lam);
+      const float Lam = fminf(U, to_float_up_nn(min_nn(r, sw)));
+      const bool need = go && (L1 <= Lam);
+      const bool multi = need && (L2 <= Lam);
       const bool single = need && !multi;
       const int jj = single ? j1 : m;
       double s1, b1;
@@ -258,7 +260,7 @@ __global__ void __launch_bounds__(256) k_phase(Geom g, const SweepState* __restr
             if (!(adb < g.sig_plus)) continue;
             const float x = fmaxf(fmaf(-adb, adb, g.sig2f), 0.0f);
             const float lo = (bb - x * rsqrtf(fmaxf(x, 1e-30f))) - smarg;
-            if (!((double)lo <= Lam)) continue;
+            if (!(lo <= Lam)) continue;
             ++nev;
             double s, b;
             if (exact_hit(f.a64[j * CPW + gi], f.b64[j * CPW + gi], P, Q, sg, g.sig2, s, b)) {
@@ -328,18 +330,18 @@ __global__ void __launch_bounds__(256) k_phase(Geom g, const SweepState* __restr
 
     // event decision in FP64 (budget end < contact < wall on ties), as
     // selects so that all lanes share one instruction stream
-    const bool is_end = (r <= best_s) && (r <= sw);
-    const bool is_contact = !is_end && (best_s <= sw);
+    const bool is_end = le_nn(r, best_s) && le_nn(r, sw);
+    const bool is_contact = !is_end && le_nn(best_s, sw);
     const bool is_wall = !is_end && !is_contact;
     const double step = is_end ? r : (is_contact ? best_s : sw);
-    const double Pstep = P + ((sg > 0) ? step : -step);
+    const double Pstep = P + flip_if(step, sg < 0);
     const double Pnew = is_wall ? ((sg > 0) ? E : 0.0) : Pstep;
     const double rnew = r - step;
-    const double addb = is_contact ? (best_b - best_s) : 0.0;
-    const float P32n = (float)Pnew;
+    const double addb = best_b - best_s;
+    const float P32n = to_float_trunc(Pnew);
     bool end_chain = capped;
     if (go) {
-      sum_b += addb;
+      if (is_contact) sum_b += addb;
       r = rnew;
       const bool is_lift = is_contact && (f.info[best_j * CPW + gi] >= 0);
       n_events += is_contact ? 1 : 0;
