@@ -236,9 +236,11 @@ void launch_frame_build(const Geom& g, const DevBufs& b, const RecLayout& lay, i
 
 size_t frame_build_smem(const RecLayout& lay) { return build_smem(lay); }
 
+// full opt-in amount for the same reason as configure_phase
 int configure_frame_build(const RecLayout& lay) {
+  if (build_smem(lay) > 232448) return -1;
   return cudaFuncSetAttribute(k_frame_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)build_smem(lay)) == cudaSuccess
+                              232448) == cudaSuccess
              ? 0
              : -1;
 }

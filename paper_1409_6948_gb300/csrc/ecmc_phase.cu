@@ -442,8 +442,12 @@ static int configure_t(size_t sm) {
   return 0;
 }
 
+// The attribute is a per-kernel, per-process maximum: request the full opt-in
+// amount, so that a handle with small frames never lowers the limit that a
+// handle with larger frames needs.
 int configure_phase(const RecLayout& lay, int tpc, int warps) {
-  const size_t sm = phase_smem_bytes(lay, warps);
+  if (phase_smem_bytes(lay, warps) > 232448) return -1;
+  const size_t sm = 232448;
   switch (tpc) {
     case 1: return configure_t<1>(sm);
     case 2: return configure_t<2>(sm);
