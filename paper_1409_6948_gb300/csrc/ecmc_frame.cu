@@ -236,11 +236,19 @@ void launch_frame_build(const Geom& g, const DevBufs& b, const RecLayout& lay, i
 
 size_t frame_build_smem(const RecLayout& lay) { return build_smem(lay); }
 
-// full opt-in amount for the same reason as configure_phase
+// largest amount the kernel can have, for the same reason as configure_phase
 int configure_frame_build(const RecLayout& lay) {
-  if (build_smem(lay) > 232448) return -1;
-  return cudaFuncSetAttribute(k_frame_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              232448) == cudaSuccess
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+          cudaSuccess ||
+      cudaFuncGetAttributes(&fa, k_frame_build) != cudaSuccess)
+    return -1;
+  const int mx = optin - (int)fa.sharedSizeBytes;
+  if (build_smem(lay) > (size_t)mx) return -1;
+  return cudaFuncSetAttribute(k_frame_build, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) ==
+                 cudaSuccess
              ? 0
              : -1;
 }

@@ -431,23 +431,42 @@ static int launch_t(const Geom& g, const DevBufs& b, const RecLayout& lay, int c
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-template <int TPC>
-static int configure_t(size_t sm) {
-  if (cudaFuncSetAttribute(k_phase<TPC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sm) != cudaSuccess)
+// Largest dynamic shared memory a launch of `fn` may request: the device's
+// opt-in per-block amount minus the kernel's static shared memory.
+template <typename F>
+static int max_dynamic_smem(F fn, int* out) {
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+          cudaSuccess ||
+      cudaFuncGetAttributes(&fa, fn) != cudaSuccess)
     return -1;
-  if (cudaFuncSetAttribute(k_phase<TPC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sm) != cudaSuccess)
-    return -1;
+  *out = optin - (int)fa.sharedSizeBytes;
   return 0;
 }
 
-// The attribute is a per-kernel, per-process maximum: request the full opt-in
-// amount, so that a handle with small frames never lowers the limit that a
-// handle with larger frames needs.
+template <typename F>
+static int configure_fn(F fn, size_t need) {
+  int mx = 0;
+  if (max_dynamic_smem(fn, &mx) || need > (size_t)mx) return -1;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) == cudaSuccess
+             ? 0
+             : -1;
+}
+
+template <int TPC>
+static int configure_t(size_t sm) {
+  if (configure_fn(k_phase<TPC, true>, sm)) return -1;
+  if (configure_fn(k_phase<TPC, false>, sm)) return -1;
+  return 0;
+}
+
+// The attribute is a per-kernel, per-process maximum: request the largest
+// amount the kernel can have, so that a handle with small frames never lowers
+// the limit that a handle with larger frames needs.
 int configure_phase(const RecLayout& lay, int tpc, int warps) {
-  if (phase_smem_bytes(lay, warps) > 232448) return -1;
-  const size_t sm = 232448;
+  const size_t sm = phase_smem_bytes(lay, warps);
   switch (tpc) {
     case 1: return configure_t<1>(sm);
     case 2: return configure_t<2>(sm);
