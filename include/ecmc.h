@@ -230,6 +230,35 @@ ECMC_API int ecmc_chain_records(ecmc_t h, ecmc_chain_rec_t* out, int64_t n);
  * needed; takes a few milliseconds. */
 ECMC_API int ecmc_device_peaks(double* smem_gbs, double* fp64_gflops);
 
+/* Size of the static scratch array behind ecmc_sweep_noalloc (16 MiB). */
+#define ECMC_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* ecmc_sweep_noalloc: n_sweeps sweeps of a system whose positions the caller
+ * keeps in its own device memory, with no device allocation at all.  The
+ * paper has no counterpart: this is for callers that cannot call cudaMalloc,
+ * such as an application whose device memory is owned by its own pool (every
+ * allocation outside it is forbidden) or code that must not allocate after
+ * its set-up.  The scratch (cell buckets, frame records, per-cell results)
+ * comes from one static device array of ECMC_NOALLOC_SCRATCH_BYTES compiled
+ * into the library, held by every GPU that loads the library until exit.
+ *   xy         device memory, 2N float64 interleaved in disk-id order; read,
+ *              then overwritten with the positions after the sweeps
+ *   N ... ell  as for ecmc_create; n_m chains per cell; seed, replica the
+ *              Philox key; t0 the Philox counter of the first sweep
+ *   stream     cudaStream_t (NULL = legacy default stream)
+ * The sweeps are the same as those of a handle with the same parameters
+ * (ecmc_set_positions(xy, t0), ecmc_sweep(n_sweeps)), screening in FP32.
+ * The call returns after the work on `stream` has finished.  Errors:
+ * ECMC_ERR_ARG (as ecmc_create, or n_m < 1, t0 < 0), ECMC_ERR_CAPACITY (the
+ * system needs more scratch than the array holds; roughly N <= 64k disks at
+ * eta 0.7; or the input overlaps), ECMC_ERR_CUDA.  The first call on a
+ * device looks up the array's device address; make it before any stream
+ * capture.  Every call shares the array: calls that overlap on the GPU race
+ * and must be serialised by the caller. */
+ECMC_API int ecmc_sweep_noalloc(double* xy, int64_t N, double L, double sigma, int cells_x,
+                                int cells_y, double ell, int n_m, uint64_t seed, uint64_t replica,
+                                int64_t t0, int64_t n_sweeps, void* stream);
+
 /* Message for an error code (static string). */
 ECMC_API const char* ecmc_strerror(int code);
 

@@ -85,6 +85,9 @@ _SIGS = {
     "ecmc_kernel_times": (C.c_int, [_H, C.POINTER(Timing)]),
     "ecmc_chain_records": (C.c_int, [_H, C.c_void_p, C.c_int64]),
     "ecmc_device_peaks": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "ecmc_sweep_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_double, C.c_int,
+                                     C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_uint64,
+                                     C.c_int64, C.c_int64, C.c_void_p]),
     "ecmc_strerror": (C.c_char_p, [C.c_int]),
     "ecmc_last_error_message": (C.c_char_p, []),
     "ecmc_version": (C.c_char_p, []),
@@ -269,6 +272,20 @@ class Ecmc:
 
 def version():
     return load().ecmc_version().decode()
+
+
+def sweep_noalloc(xy, N, L, sigma, cells_x, cells_y, ell, n_m, seed, replica, t0, n_sweeps,
+                  stream=None):
+    """ecmc_sweep_noalloc: sweeps of caller-held device positions `xy` (a
+    torch CUDA float64 tensor of 2N values, overwritten) using only the
+    library's static scratch array; no device allocation."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    _check(load().ecmc_sweep_noalloc(C.c_void_p(xy.data_ptr()), int(N), float(L), float(sigma),
+                                     int(cells_x), int(cells_y), float(ell), int(n_m),
+                                     C.c_uint64(int(seed)), C.c_uint64(int(replica)), int(t0),
+                                     int(n_sweeps), C.c_void_p(stream or 0)),
+           "ecmc_sweep_noalloc")
 
 
 def device_peaks():
