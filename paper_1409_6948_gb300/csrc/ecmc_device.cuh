@@ -117,3 +117,26 @@ __device__ __forceinline__ float to_float_up_nn(double v) {
 }
 
 }  // namespace ecmc
+
+namespace ecmc {
+
+// Signed comparisons of doubles on the integer pipes.  Valid for finite
+// values; -0.0 and +0.0 compare equal, as in IEEE arithmetic.
+__device__ __forceinline__ long long dkey(double v) {
+  // monotone map of the bit pattern: negative values are reflected so that
+  // the signed-integer order is the numeric order
+  const long long b = __double_as_longlong(v);
+  return b >= 0 ? b : (long long)0x8000000000000000ull - b;
+}
+__device__ __forceinline__ bool dlt(double a, double b) { return dkey(a) < dkey(b); }
+__device__ __forceinline__ bool dle(double a, double b) { return dkey(a) <= dkey(b); }
+
+// periodic wrap into [-L/2, L/2) for |v| < 3L/2 (hL = L/2), comparisons on
+// the integer pipes; the additions are the same as in wrap_half
+__device__ __forceinline__ double wrap_half_i(double v, double L, double hL) {
+  if (!dlt(v, hL)) return v - L;
+  if (dlt(v, -hL)) return v + L;
+  return v;
+}
+
+}  // namespace ecmc

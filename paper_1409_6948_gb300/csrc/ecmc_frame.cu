@@ -66,11 +66,12 @@ __global__ void k_frame_build(Geom g, const SweepState* __restrict__ st, int col
   __syncthreads();
 
   // members, in the cell frame
+  const double hL = 0.5 * L;
   const int nc = min(cnt[c], g.cap_mem);
   for (int k = tid; k < nc; k += bt) {
     const int64_t q = (int64_t)c * g.cap_mem + k;
-    const double X = wrap_half(px[q] - ox, L);
-    const double Y = wrap_half(py[q] - oy, L);
+    const double X = wrap_half_i(px[q] - ox, L, hL);
+    const double Y = wrap_half_i(py[q] - oy, L, hL);
     const int i = atomicAdd(&s_nobj, 1);
     s.a64[i] = axis == 0 ? X : Y;
     s.b64[i] = axis == 0 ? Y : X;
@@ -98,7 +99,7 @@ __global__ void k_frame_build(Geom g, const SweepState* __restrict__ st, int col
   // margin well above its rounding error (|error| < 4 * 2^-23 L) discards the
   // disks that no image can bring near the cell; the others take the FP64
   // test, so the frame is exactly the one the FP64 test alone would build.
-  const float Lf = (float)L, hLf = 0.5f * (float)L;
+  const float Lf = (float)L;
   const float oxf = to_float_trunc(ox), oyf = to_float_trunc(oy);
   const float mf = 8.0f * 1.1920929e-7f * Lf + 1e-6f;
   const float xlo = -(float)sigma - mf, xhi = (float)wl + mf;
@@ -109,28 +110,33 @@ __global__ void k_frame_build(Geom g, const SweepState* __restrict__ st, int col
     for (int k = tid; k < nn; k += bt) {
       const int64_t q = (int64_t)n * g.cap_mem + k;
       const double xq = px[q], yq = py[q];
+      // offsets j*L (j = -2..2) of the unwrapped difference that the FP32
+      // screen keeps; an FP64 image k of the wrapped difference is offset
+      // j = k - (wrap shift), so the screen is tested per actual image
+      unsigned imgx = 0, imgy = 0;
       {
-        float X0f = to_float_trunc(xq) - oxf;
-        X0f = X0f >= hLf ? X0f - Lf : (X0f < -hLf ? X0f + Lf : X0f);
-        float Y0f = to_float_trunc(yq) - oyf;
-        Y0f = Y0f >= hLf ? Y0f - Lf : (Y0f < -hLf ? Y0f + Lf : Y0f);
-        bool nx = false, ny = false;
-        for (int kk = -1; kk <= 1; ++kk) {
-          const float Xf = X0f + (float)kk * Lf, Yf = Y0f + (float)kk * Lf;
-          nx |= (Xf > xlo && Xf < xhi);
-          ny |= (Yf > ylo && Yf < yhi);
+        const float rxf = to_float_trunc(xq) - oxf, ryf = to_float_trunc(yq) - oyf;
+        for (int j = -2; j <= 2; ++j) {
+          const float Xf = rxf + (float)j * Lf, Yf = ryf + (float)j * Lf;
+          imgx |= (Xf > xlo && Xf < xhi) ? (1u << (j + 2)) : 0u;
+          imgy |= (Yf > ylo && Yf < yhi) ? (1u << (j + 2)) : 0u;
         }
-        if (!(nx && ny)) continue;
+        if (!(imgx && imgy)) continue;
       }
-      const double X0 = wrap_half(xq - ox, L);
-      const double Y0 = wrap_half(yq - oy, L);
+      const double rx = xq - ox, ry = yq - oy;
+      const int swx = !dlt(rx, hL) ? 1 : (dlt(rx, -hL) ? -1 : 0);
+      const int swy = !dlt(ry, hL) ? 1 : (dlt(ry, -hL) ? -1 : 0);
+      const double X0 = swx > 0 ? rx - L : (swx < 0 ? rx + L : rx);  // wrap_half(rx, L)
+      const double Y0 = swy > 0 ? ry - L : (swy < 0 ? ry + L : ry);
       const int id = pid[q];
       for (int kx = -1; kx <= 1; ++kx) {
+        if (!(imgx & (1u << (kx - swx + 2)))) continue;
         const double X = (kx == 0) ? X0 : (kx > 0 ? X0 + L : X0 - L);
-        if (!(X > -sigma && X < wl)) continue;
+        if (!(dlt(-sigma, X) && dlt(X, wl))) continue;
         for (int ky = -1; ky <= 1; ++ky) {
+          if (!(imgy & (1u << (ky - swy + 2)))) continue;
           const double Y = (ky == 0) ? Y0 : (ky > 0 ? Y0 + L : Y0 - L);
-          if (!(Y > -sigma && Y < hl)) continue;
+          if (!(dlt(-sigma, Y) && dlt(Y, hl))) continue;
           const int i = atomicAdd(&s_nobj, 1);
           if (i >= lay.cap_obj) {
             s_overflow = 1;
@@ -161,7 +167,7 @@ __global__ void k_frame_build(Geom g, const SweepState* __restrict__ st, int col
   }
   // strips across the chain axis: bin of the FP32 coordinate
   for (int i = tid; i < nobj; i += bt) {
-    const float b32 = (float)s.b64[i];
+    const float b32 = to_float_trunc(s.b64[i]);
     int kb = (int)((b32 + g.sigf) * g.inv_bin_w);
     kb = kb < 0 ? 0 : (kb >= lay.nbin ? lay.nbin - 1 : kb);
     s.bin[i] = kb;
@@ -202,8 +208,8 @@ __global__ void k_frame_build(Geom g, const SweepState* __restrict__ st, int col
   for (int i = tid; i < nobj; i += bt) {
     const int f = atomicAdd(&s.hist[s.bin[i]], 1);
     s.fin[i] = f;
-    a32[f * cpw + gi] = (float)s.a64[i];
-    b32[f * cpw + gi] = (float)s.b64[i];
+    a32[f * cpw + gi] = to_float_trunc(s.a64[i]);
+    b32[f * cpw + gi] = to_float_trunc(s.b64[i]);
     a64[f * cpw + gi] = s.a64[i];
     b64[f * cpw + gi] = s.b64[i];
     key[f * cpw + gi] = s.key[i];
