@@ -141,6 +141,42 @@ typedef struct {
 ECMC_API int ecmc_create(ecmc_t* out, int64_t N, double L, double sigma, int cells_x, int cells_y,
                 double ell, uint64_t seed);
 
+/* One replica of a batch: an independent system (Sec. 3.4's sweep applied to
+ * each), advanced together with the others in the same launches.  The paper
+ * runs 30 independent simulations to estimate errors (Sec. 3.4, Fig. 4);
+ * here many replicas of different N and packing fraction share the GPU. */
+typedef struct {
+  int64_t N;        /* disks (a perfect square: square-lattice start)        */
+  double L;         /* box side                                             */
+  double sigma;     /* disk diameter                                        */
+  int cells_x;      /* cells per side (even, >= 2, side > sigma)            */
+  int cells_y;
+  double ell;       /* chain displacement                                   */
+  int n_m;          /* chains per cell and sweep; 0 = eq. (nm) default      */
+  uint64_t seed;    /* Philox key word 0                                    */
+  uint64_t replica; /* Philox key word 1                                    */
+} ecmc_replica_desc_t;
+
+/* Create a handle holding R independent replicas, each started on its own
+ * square lattice.  Positions of the whole handle (ecmc_positions,
+ * ecmc_set_positions) are the replicas' id-ordered pairs concatenated in
+ * replica order.  Sweeps advance every replica by one sweep in the same
+ * launches (one graph per sweep).  Errors as ecmc_create, for any replica;
+ * ECMC_ERR_ARG if R < 1. */
+ECMC_API int ecmc_create_batch(ecmc_t* out, const ecmc_replica_desc_t* desc, int R);
+
+/* Number of replicas of the handle. */
+ECMC_API int ecmc_num_replicas(ecmc_t h, int* R);
+
+/* Parameters of replica r as used (n_m resolved). */
+ECMC_API int ecmc_replica_desc(ecmc_t h, int r, ecmc_replica_desc_t* out);
+
+/* Pressure (as ecmc_pressure) and counters (as ecmc_counters) of replica r.
+ * ecmc_pressure itself reports replica 0, ecmc_counters the sum over all
+ * replicas. */
+ECMC_API int ecmc_replica_pressure(ecmc_t h, int r, double* betaP_sigma2, double* stderr_out);
+ECMC_API int ecmc_replica_counters(ecmc_t h, int r, ecmc_counters_t* out);
+
 /* Release the handle and all its device memory.  NULL is accepted. */
 ECMC_API int ecmc_destroy(ecmc_t h);
 
@@ -192,8 +228,9 @@ ECMC_API int ecmc_reset_stats(ecmc_t h);
  * ECMC_ERR_STATE if no sweep has run since the reset. */
 ECMC_API int ecmc_pressure(ecmc_t h, double* betaP_sigma2, double* stderr_out);
 
-/* Add the pair histogram of the current configuration to the accumulated
- * one: ordered pairs with sigma + i dr <= d < sigma + (i+1) dr (Sec. 2). */
+/* Add the pair histogram of the current configuration (replica 0) to the
+ * accumulated one: ordered pairs with sigma + i dr <= d < sigma + (i+1) dr
+ * (Sec. 2). */
 ECMC_API int ecmc_gr_measure(ecmc_t h);
 
 /* Accumulated counts (int64[nbins]) and number of measurements.
@@ -209,19 +246,20 @@ ECMC_API int ecmc_gr(ecmc_t h, double* g_out, double* r_out, int nbins);
 ECMC_API int ecmc_gr_nbins(ecmc_t h, int* nbins);
 
 /* Smallest minimum-image pair distance of the current configuration among
- * pairs closer than 2 sigma (2 sigma if none). */
+ * pairs closer than 2 sigma (2 sigma if none), over all replicas. */
 ECMC_API int ecmc_min_distance(ecmc_t h, double* dmin);
 
-/* Cell of every disk (by id) used by the most recent sweep, cy*cells_x+cx. */
+/* Cell of every disk (by id, replicas concatenated) in the most recent
+ * binning, cy*cells_x+cx within its replica. */
 ECMC_API int ecmc_last_cells(ecmc_t h, int32_t* cell_of_id);
 
 /* Per-kernel times accumulated while ECMC_PARAM_TIMING is 1. */
 ECMC_API int ecmc_kernel_times(ecmc_t h, ecmc_timing_t* out);
 
 /* Per-chain records of the most recent sweep (requires
- * ECMC_PARAM_RECORD_CHAINS = 1 during that sweep): out[cell * n_m + k] for
- * cell = cy * cells_x + cx; cells without members hold start_id = -1.
- * n must equal cells_x * cells_y * n_m. */
+ * ECMC_PARAM_RECORD_CHAINS = 1 during that sweep) of replica 0:
+ * out[cell * n_m + k] for cell = cy * cells_x + cx; cells without members
+ * hold start_id = -1.  n must equal cells_x * cells_y * n_m. */
 ECMC_API int ecmc_chain_records(ecmc_t h, ecmc_chain_rec_t* out, int64_t n);
 
 /* Measure, on the current device, the shared-memory load bandwidth (GB/s,

@@ -44,9 +44,17 @@ enum TimerClass { TC_BIN = 0, TC_FRAME = 1, TC_PHASE = 2, TC_OTHER = 3 };
 }  // namespace
 
 struct ecmc_ctx {
-  Geom g;
+  std::vector<Geom> geo;        // host copy of every replica's geometry
+  std::vector<int> cell_rep;    // replica of every global cell
+  std::vector<int> act_rep;     // replica of every global active cell
+  std::vector<int64_t> n_off;   // disk offsets, R + 1 entries
+  Geom* d_geo = nullptr;
+  int* d_cell_rep = nullptr;
+  int* d_act_rep = nullptr;
+  int64_t* d_n_off = nullptr;
   DevBufs b;
   RecLayout lay;
+  int precision = 1;
   int tpc = 0;          // lanes per cell in use
   int tpc_param = 0;    // 0 = automatic
   int warps = 0;
@@ -71,7 +79,7 @@ struct ecmc_ctx {
   std::vector<cudaEvent_t> pool;
   double ms[4] = {0, 0, 0, 0};
   int64_t launches[4] = {0, 0, 0, 0};
-  // g(r)
+  // g(r) of replica 0
   double gr_dr = 0.01, gr_rmax = 5.0;
   int gr_nbins = 0;
   unsigned long long* gr_counts = nullptr;
@@ -121,26 +129,42 @@ void set_screen_bounds(Geom& g) {
   g.strip_margin = (float)(4.0 * e + 1e-5 * sig);
 }
 
+int upload_geometry(ecmc_ctx* h) {
+  CK(cudaMemcpyAsync(h->d_geo, h->geo.data(), sizeof(Geom) * h->geo.size(),
+                     cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return ECMC_OK;
+}
+
+RecLayout layout_for(ecmc_ctx* h, int tpc) {
+  int nbin = 0, cap_obj = 0;
+  for (const Geom& g : h->geo) {
+    nbin = g.nbin > nbin ? g.nbin : nbin;
+    cap_obj = g.cap_obj > cap_obj ? g.cap_obj : cap_obj;
+  }
+  return make_layout(32 / tpc, nbin, h->b.cap, cap_obj);
+}
+
 int choose_tpc(ecmc_ctx* h) {
   if (h->tpc_param) return h->tpc_param;
-  // smallest group width whose per-warp shared memory leaves room for at
-  // least four warps per SM
-  for (int t = 1; t <= 32; t *= 2) {
-    RecLayout l = make_layout(32 / t, h->g.nbin, h->g.cap_mem, h->g.cap_obj);
-    if (phase_smem_bytes(l, 1) <= 52 * 1024) return t;
-  }
+  // the widest group (most cells per warp) whose frames leave room for at
+  // least four warps per SM, but at most 8 cells per warp: measured on GB300
+  // at N = 1M, eta = 0.72, 8 cells per warp beat 4, 16 and 32
+  for (int t = 4; t <= 32; t *= 2)
+    if (phase_smem_bytes(layout_for(h, t), 1) <= 52 * 1024) return t;
   return 32;
 }
 
 int compute_layout(ecmc_ctx* h) {
-  Geom& g = h->g;
-  const double bw = h->strip_w * g.sigma;
-  const double extB = (g.w > g.h ? g.w : g.h) + 2.0 * g.sigma;
-  g.nbin = (int)std::ceil(extB / bw) + 1;
-  g.bin_w = (float)bw;
-  g.inv_bin_w = (float)(1.0 / bw);
+  for (Geom& g : h->geo) {
+    const double bw = h->strip_w * g.sigma;
+    const double extB = (g.w > g.h ? g.w : g.h) + 2.0 * g.sigma;
+    g.nbin = (int)std::ceil(extB / bw) + 1;
+    g.bin_w = (float)bw;
+    g.inv_bin_w = (float)(1.0 / bw);
+  }
   h->tpc = choose_tpc(h);
-  h->lay = make_layout(32 / h->tpc, g.nbin, g.cap_mem, g.cap_obj);
+  h->lay = layout_for(h, h->tpc);
   const size_t per_warp = phase_smem_bytes(h->lay, 1);
   const size_t limit = 232448;  // opt-in shared memory per block on sm_103
   if (per_warp > limit)
@@ -153,8 +177,7 @@ int compute_layout(ecmc_ctx* h) {
   if ((size_t)w * per_warp > limit) w = (int)(limit / per_warp);
   if (w < 1) w = 1;
   h->warps = w;
-  const int n_active = (g.cells_x / 2) * (g.cells_y / 2);
-  const int n_groups = (n_active + h->lay.cpw - 1) / h->lay.cpw;
+  const int n_groups = (h->b.A_total + h->lay.cpw - 1) / h->lay.cpw;
   const size_t need = (size_t)n_groups * h->lay.bytes;
   if (need > h->records_cap) {
     if (h->b.records) cudaFree(h->b.records);
@@ -167,7 +190,7 @@ int compute_layout(ecmc_ctx* h) {
   if (configure_frame_build(h->lay) || configure_phase(h->lay, h->tpc, h->warps))
     return fail(ECMC_ERR_CUDA, "kernel configuration failed: %s",
                 cudaGetErrorString(cudaGetLastError()));
-  return ECMC_OK;
+  return upload_geometry(h);
 }
 
 void drop_graphs(ecmc_ctx* h) {
@@ -219,33 +242,34 @@ void harvest_timing(ecmc_ctx* h) {
   h->pending.clear();
 }
 
-// Enqueue one sweep (no graph).
+// Enqueue one sweep of every replica (no graph).
 int enqueue_sweep(ecmc_ctx* h) {
   const int src = h->b.cur, dst = 1 - h->b.cur;
   if (h->record_chains && h->b.chain_recs)
     CK(cudaMemsetAsync(h->b.chain_recs, 0xff,
-                       sizeof(ChainRec) * (size_t)h->g.ncell * h->g.n_m, h->stream));
+                       sizeof(ChainRec) * (size_t)h->b.C_total * h->b.rec_stride, h->stream));
   {
     Timed tm(h, TC_BIN);
-    launch_sweep_begin(h->g, h->b, h->stream);
-    launch_bin(h->g, h->b, src, dst, h->stream);
+    launch_sweep_begin(h->b, h->stream);
+    launch_bin(h->b, src, dst, h->stream);
   }
   h->b.cur = dst;
   for (int ci = 0; ci < 4; ++ci) {
     {
       Timed tm(h, TC_FRAME);
-      launch_frame_build(h->g, h->b, h->lay, ci, h->stream);
+      launch_frame_build(h->b, h->lay, ci, h->stream);
     }
     {
       Timed tm(h, TC_PHASE);
-      if (launch_phase(h->g, h->b, h->lay, ci, h->tpc, h->warps, h->record_chains, h->stream))
+      if (launch_phase(h->b, h->lay, ci, h->tpc, h->warps, h->record_chains, h->precision,
+                       h->stream))
         return fail(ECMC_ERR_CUDA, "chain kernel launch failed: %s",
                     cudaGetErrorString(cudaGetLastError()));
     }
   }
   {
     Timed tm(h, TC_OTHER);
-    launch_sweep_end(h->g, h->b, h->stream);
+    launch_sweep_end(h->b, h->stream);
   }
   CK(cudaGetLastError());
   return ECMC_OK;
@@ -257,10 +281,13 @@ int ensure_history(ecmc_ctx* h, int64_t extra) {
   int64_t cap = h->b.history_cap ? h->b.history_cap : 1024;
   while (cap < need) cap *= 2;
   double* nh = nullptr;
-  CK(cudaMalloc(&nh, sizeof(double) * 2 * cap));
-  if (h->b.history && h->hist_len_host > 0)
-    CK(cudaMemcpyAsync(nh, h->b.history, sizeof(double) * 2 * h->hist_len_host,
-                       cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMalloc(&nh, sizeof(double) * 2 * (size_t)cap * h->b.R));
+  if (h->b.history && h->hist_len_host > 0) {
+    const int64_t len = h->hist_len_host < h->b.history_cap ? h->hist_len_host : h->b.history_cap;
+    CK(cudaMemcpy2DAsync(nh, sizeof(double) * 2 * cap, h->b.history,
+                         sizeof(double) * 2 * h->b.history_cap, sizeof(double) * 2 * len, h->b.R,
+                         cudaMemcpyDeviceToDevice, h->stream));
+  }
   CK(cudaStreamSynchronize(h->stream));
   if (h->b.history) cudaFree(h->b.history);
   h->b.history = nh;
@@ -285,33 +312,48 @@ int check_device_error(ecmc_ctx* h) {
   return ECMC_OK;
 }
 
+// smallest pair distance squared over all replicas (pairs closer than 2 sigma)
+int min_dist2(ecmc_ctx* h, double* d2) {
+  double sig_max = 0.0;
+  for (const Geom& g : h->geo) sig_max = g.sigma > sig_max ? g.sigma : sig_max;
+  unsigned long long init = 0;
+  const double r2 = 4.0 * sig_max * sig_max;
+  std::memcpy(&init, &r2, sizeof(r2));
+  CK(cudaMemcpyAsync(h->u64_tmp, &init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
+  for (const Geom& g : h->geo) launch_min_dist(g, h->b, 2.0 * g.sigma, h->u64_tmp, h->stream);
+  unsigned long long bits = 0;
+  CK(cudaMemcpyAsync(&bits, h->u64_tmp, sizeof(bits), cudaMemcpyDeviceToHost, h->stream));
+  int rc = check_device_error(h);
+  if (rc) return rc;
+  std::memcpy(d2, &bits, sizeof(*d2));
+  return ECMC_OK;
+}
+
 int load_positions_dev(ecmc_ctx* h, const double* xy_dev, int64_t t0) {
-  launch_load_flat(h->g, h->b, xy_dev, h->stream);
-  SweepState st;
-  std::memset(&st, 0, sizeof(st));
-  st.t = t0;
-  st.history_len = h->hist_len_host;
-  CK(cudaMemcpyAsync(h->b.state, &st, sizeof(st), cudaMemcpyHostToDevice, h->stream));
+  launch_load_flat(h->b, xy_dev, h->stream);
+  std::vector<SweepState> st(h->b.R);
+  for (auto& v : st) {
+    std::memset(&v, 0, sizeof(v));
+    v.t = t0;
+    v.history_len = h->hist_len_host;
+  }
+  CK(cudaMemcpyAsync(h->b.state, st.data(), sizeof(SweepState) * st.size(),
+                     cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  launch_sweep_begin(h->g, h->b, h->stream);
-  launch_bin(h->g, h->b, -1, h->b.cur, h->stream);
+  launch_sweep_begin(h->b, h->stream);
+  launch_bin(h->b, -1, h->b.cur, h->stream);
   CK(cudaGetLastError());
   h->t_host = t0;
   h->valid_state = true;
   int rc = check_device_error(h);
   if (rc) return rc;
   // no two disks may overlap beyond rounding
-  unsigned long long init = 0;
-  const double r2 = 4.0 * h->g.sig2;
-  std::memcpy(&init, &r2, sizeof(r2));
-  CK(cudaMemcpyAsync(h->u64_tmp, &init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
-  launch_min_dist(h->g, h->b, 2.0 * h->g.sigma, h->u64_tmp, h->stream);
-  unsigned long long bits = 0;
-  CK(cudaMemcpyAsync(&bits, h->u64_tmp, sizeof(bits), cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  double d2;
-  std::memcpy(&d2, &bits, sizeof(d2));
-  if (d2 < h->g.sig2 * (1.0 - 1e-9)) {
+  double d2 = 0.0;
+  rc = min_dist2(h, &d2);
+  if (rc) return rc;
+  double sig2_min = 1e300;
+  for (const Geom& g : h->geo) sig2_min = g.sig2 < sig2_min ? g.sig2 : sig2_min;
+  if (d2 < sig2_min * (1.0 - 1e-9)) {
     h->valid_state = false;
     return fail(ECMC_ERR_OVERLAP, "positions overlap: smallest distance %.17g < sigma",
                 std::sqrt(d2));
@@ -335,8 +377,11 @@ int default_nm(const Geom& g) {
 int realloc_chain_recs(ecmc_ctx* h) {
   if (h->b.chain_recs) cudaFree(h->b.chain_recs);
   h->b.chain_recs = nullptr;
+  int stride = 1;
+  for (const Geom& g : h->geo) stride = g.n_m > stride ? g.n_m : stride;
+  h->b.rec_stride = stride;
   if (!h->record_chains) return ECMC_OK;
-  const size_t n = (size_t)h->g.ncell * h->g.n_m;
+  const size_t n = (size_t)h->b.C_total * stride;
   CK(cudaMalloc(&h->b.chain_recs, sizeof(ChainRec) * n));
   CK(cudaMemsetAsync(h->b.chain_recs, 0xff, sizeof(ChainRec) * n, h->stream));
   return ECMC_OK;
@@ -357,6 +402,10 @@ void free_all(ecmc_ctx* h) {
   cudaFree(h->b.records);
   cudaFree(h->b.err);
   cudaFree(h->b.chain_recs);
+  cudaFree(h->d_geo);
+  cudaFree(h->d_cell_rep);
+  cudaFree(h->d_act_rep);
+  cudaFree(h->d_n_off);
   cudaFree(h->gr_counts);
   cudaFree(h->xy_tmp);
   cudaFree(h->int_tmp);
@@ -370,7 +419,8 @@ void free_all(ecmc_ctx* h) {
 }
 
 int setup_gr(ecmc_ctx* h) {
-  const int nb = (int)std::floor((h->gr_rmax - h->g.sigma) / h->gr_dr + 0.5);
+  const Geom& g = h->geo[0];
+  const int nb = (int)std::floor((h->gr_rmax - g.sigma) / h->gr_dr + 0.5);
   if (nb < 1 || nb > 1000000) return fail(ECMC_ERR_ARG, "bad g(r) binning");
   if (h->gr_counts) cudaFree(h->gr_counts);
   h->gr_counts = nullptr;
@@ -381,11 +431,229 @@ int setup_gr(ecmc_ctx* h) {
   return ECMC_OK;
 }
 
+// Geometry, capacities and FP32 screening bounds of one replica.
+int setup_geom(const ecmc_replica_desc_t& d, Geom& g) {
+  const int64_t N = d.N;
+  if (N < 1 || N >= (int64_t(1) << 27)) return fail(ECMC_ERR_ARG, "N out of range");
+  const int64_t k = (int64_t)std::llround(std::sqrt((double)N));
+  if (k * k != N) return fail(ECMC_ERR_ARG, "N must be a perfect square (lattice start)");
+  if (!(d.L > 0.0) || !(d.sigma > 0.0) || !std::isfinite(d.L) || !std::isfinite(d.sigma))
+    return fail(ECMC_ERR_ARG, "L and sigma must be positive");
+  if (d.cells_x < 2 || d.cells_y < 2 || (d.cells_x & 1) || (d.cells_y & 1))
+    return fail(ECMC_ERR_ARG, "cells per side must be even and >= 2");
+  if (!(d.L / d.cells_x > d.sigma) || !(d.L / d.cells_y > d.sigma))
+    return fail(ECMC_ERR_ARG, "cell side must exceed sigma");
+  if (!(d.L / (double)k > d.sigma)) return fail(ECMC_ERR_ARG, "square lattice would overlap");
+  if (!(d.ell >= 0.0) || !std::isfinite(d.ell)) return fail(ECMC_ERR_ARG, "ell must be >= 0");
+  if ((int64_t)d.cells_x * d.cells_y > (int64_t(1) << 26))
+    return fail(ECMC_ERR_ARG, "too many cells");
+  if (d.n_m < 0 || d.n_m > 1000000) return fail(ECMC_ERR_ARG, "n_m out of range");
+  std::memset(&g, 0, sizeof(g));
+  g.N = N;
+  g.L = d.L;
+  g.sigma = d.sigma;
+  g.sig2 = d.sigma * d.sigma;
+  g.cells_x = d.cells_x;
+  g.cells_y = d.cells_y;
+  g.ncell = d.cells_x * d.cells_y;
+  g.nact = (d.cells_x / 2) * (d.cells_y / 2);
+  g.w = d.L / (double)d.cells_x;
+  g.h = d.L / (double)d.cells_y;
+  g.inv_w = 1.0 / g.w;
+  g.inv_h = 1.0 / g.h;
+  g.ell = d.ell;
+  g.seed = d.seed;
+  g.replica = d.replica;
+  g.dir_mode = 0;
+  g.precision = 1;
+  g.cap_mem = (int)std::floor(packing_bound(g.w, g.h, d.sigma)) + 2;
+  g.cap_obj = (int)std::floor(packing_bound(g.w + 2 * d.sigma, g.h + 2 * d.sigma, d.sigma)) + 2;
+  if (g.cap_mem > g.cap_obj) g.cap_mem = g.cap_obj;
+  if ((int64_t)g.ncell * g.cap_mem < N)
+    return fail(ECMC_ERR_ARG, "N exceeds the packing capacity of the box");
+  g.n_m = d.n_m ? d.n_m : default_nm(g);
+  set_screen_bounds(g);
+  return ECMC_OK;
+}
+
+int create_impl(ecmc_t* out, const ecmc_replica_desc_t* desc, int R) {
+  if (!out) return fail(ECMC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!desc || R < 1) return fail(ECMC_ERR_ARG, "need at least one replica");
+  ecmc_ctx* h = new (std::nothrow) ecmc_ctx();
+  if (!h) return fail(ECMC_ERR_OOM, "host allocation failed");
+  std::memset(&h->b, 0, sizeof(h->b));
+  auto bail = [&](int rc) {
+    free_all(h);
+    delete h;
+    return rc;
+  };
+  h->geo.resize(R);
+  h->n_off.assign(R + 1, 0);
+  int64_t C_total = 0, A_total = 0;
+  int cap = 0;
+  for (int r = 0; r < R; ++r) {
+    int rc = setup_geom(desc[r], h->geo[r]);
+    if (rc) {
+      delete h;
+      return rc;
+    }
+    Geom& g = h->geo[r];
+    g.rep = r;
+    g.n_off = h->n_off[r];
+    g.cell_off = (int)C_total;
+    g.act_off = (int)A_total;
+    h->n_off[r + 1] = h->n_off[r] + g.N;
+    C_total += g.ncell;
+    A_total += g.nact;
+    cap = g.cap_mem > cap ? g.cap_mem : cap;
+    if (C_total >= (int64_t(1) << 30)) {
+      delete h;
+      return fail(ECMC_ERR_ARG, "too many cells in the batch");
+    }
+  }
+  for (int r = 0; r < R; ++r) {
+    h->cell_rep.insert(h->cell_rep.end(), h->geo[r].ncell, r);
+    h->act_rep.insert(h->act_rep.end(), h->geo[r].nact, r);
+  }
+  const int64_t N_total = h->n_off[R];
+  if (N_total >= (int64_t(1) << 31) || C_total * (int64_t)cap >= (int64_t(1) << 31)) {
+    delete h;
+    return fail(ECMC_ERR_ARG, "batch too large");
+  }
+  DevBufs& b = h->b;
+  b.R = R;
+  b.C_total = (int)C_total;
+  b.A_total = (int)A_total;
+  b.cap = cap;
+  b.N_total = N_total;
+  b.cur = 0;
+
+  if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(fail(ECMC_ERR_CUDA, "cannot create a stream (no CUDA device?)"));
+  h->stream = h->own_stream;
+  const size_t slots = (size_t)C_total * cap;
+  for (int i = 0; i < 2; ++i) {
+    if (cudaMalloc(&b.px[i], sizeof(double) * slots) != cudaSuccess ||
+        cudaMalloc(&b.py[i], sizeof(double) * slots) != cudaSuccess ||
+        cudaMalloc(&b.pid[i], sizeof(int) * slots) != cudaSuccess ||
+        cudaMalloc(&b.count[i], sizeof(int) * (size_t)C_total) != cudaSuccess)
+      return bail(fail(ECMC_ERR_OOM, "device allocation of %zu slots failed", slots));
+    cudaMemsetAsync(b.count[i], 0, sizeof(int) * (size_t)C_total, h->stream);
+  }
+  if (cudaMalloc(&b.state, sizeof(SweepState) * R) != cudaSuccess ||
+      cudaMalloc(&b.cell_stats, sizeof(CellStats) * (size_t)C_total) != cudaSuccess ||
+      cudaMalloc(&b.totals, sizeof(RunTotals) * R) != cudaSuccess ||
+      cudaMalloc(&b.err, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&h->d_geo, sizeof(Geom) * R) != cudaSuccess ||
+      cudaMalloc(&h->d_cell_rep, sizeof(int) * (size_t)C_total) != cudaSuccess ||
+      cudaMalloc(&h->d_act_rep, sizeof(int) * (size_t)A_total) != cudaSuccess ||
+      cudaMalloc(&h->d_n_off, sizeof(int64_t) * (R + 1)) != cudaSuccess ||
+      cudaMalloc(&h->xy_tmp, sizeof(double) * 2 * (size_t)N_total) != cudaSuccess ||
+      cudaMalloc(&h->int_tmp, sizeof(int) * (size_t)N_total) != cudaSuccess ||
+      cudaMalloc(&h->u64_tmp, sizeof(unsigned long long) * 4) != cudaSuccess)
+    return bail(fail(ECMC_ERR_OOM, "device allocation failed"));
+  cudaMemsetAsync(b.totals, 0, sizeof(RunTotals) * R, h->stream);
+  cudaMemsetAsync(b.err, 0, sizeof(int), h->stream);
+  cudaMemsetAsync(b.cell_stats, 0, sizeof(CellStats) * (size_t)C_total, h->stream);
+  if (cudaMemcpyAsync(h->d_cell_rep, h->cell_rep.data(), sizeof(int) * C_total,
+                      cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(h->d_act_rep, h->act_rep.data(), sizeof(int) * A_total,
+                      cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(h->d_n_off, h->n_off.data(), sizeof(int64_t) * (R + 1),
+                      cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return bail(fail(ECMC_ERR_CUDA, "upload failed"));
+  b.rg = h->d_geo;
+  b.cell_rep = h->d_cell_rep;
+  b.act_rep = h->d_act_rep;
+  b.n_off = h->d_n_off;
+  int rc = compute_layout(h);
+  if (rc) return bail(rc);
+  rc = realloc_chain_recs(h);
+  if (rc) return bail(rc);
+  rc = ensure_history(h, 1024);
+  if (rc) return bail(rc);
+  rc = setup_gr(h);
+  if (rc) return bail(rc);
+
+  // square-lattice start of every replica
+  std::vector<double> xy(2 * (size_t)N_total);
+  for (int r = 0; r < R; ++r) {
+    const Geom& g = h->geo[r];
+    const int64_t k = (int64_t)std::llround(std::sqrt((double)g.N));
+    const double a = g.L / (double)k;
+    double* p = xy.data() + 2 * g.n_off;
+    for (int64_t i = 0; i < g.N; ++i) {
+      p[2 * i] = ((double)(i % k) + 0.5) * a;
+      p[2 * i + 1] = ((double)(i / k) + 0.5) * a;
+    }
+  }
+  if (cudaMemcpyAsync(h->xy_tmp, xy.data(), sizeof(double) * xy.size(), cudaMemcpyHostToDevice,
+                      h->stream) != cudaSuccess)
+    return bail(fail(ECMC_ERR_CUDA, "upload failed"));
+  rc = load_positions_dev(h, h->xy_tmp, 0);
+  if (rc) return bail(rc);
+  *out = h;
+  return ECMC_OK;
+}
+
+int pressure_of(ecmc_ctx* h, int r, double* betaP, double* se) {
+  const int64_t n = h->hist_len_host < h->b.history_cap ? h->hist_len_host : h->b.history_cap;
+  if (n < 1) return fail(ECMC_ERR_STATE, "no sweep since the last reset");
+  const Geom& g = h->geo[r];
+  std::vector<double> hist(2 * (size_t)n);
+  CK(cudaMemcpyAsync(hist.data(), h->b.history + 2 * (size_t)r * h->b.history_cap,
+                     sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, h->stream));
+  RunTotals t;
+  CK(cudaMemcpyAsync(&t, h->b.totals + r, sizeof(t), cudaMemcpyDeviceToHost, h->stream));
+  int rc = check_device_error(h);
+  if (rc) return rc;
+  const double rho_s2 = (double)g.N / (g.L * g.L) * g.sig2;
+  if (!(t.sum_disp_w > 0.0)) return fail(ECMC_ERR_STATE, "no displacement since the last reset");
+  *betaP = rho_s2 * (1.0 + t.sum_b_w / t.sum_disp_w);
+  if (se) {
+    *se = 0.0;
+    const int64_t nb = n >= 20 ? 20 : n;
+    if (nb >= 2) {
+      std::vector<double> vals;
+      for (int64_t bI = 0; bI < nb; ++bI) {
+        const int64_t lo = bI * n / nb, hi = (bI + 1) * n / nb;
+        double sb = 0.0, sd = 0.0;
+        for (int64_t i = lo; i < hi; ++i) {
+          sb += hist[2 * i];
+          sd += hist[2 * i + 1];
+        }
+        vals.push_back(rho_s2 * (1.0 + sb / sd));
+      }
+      double mean = 0.0;
+      for (double v : vals) mean += v;
+      mean /= (double)nb;
+      double var = 0.0;
+      for (double v : vals) var += (v - mean) * (v - mean);
+      var /= (double)(nb - 1);
+      *se = std::sqrt(var / (double)nb);
+    }
+  }
+  return ECMC_OK;
+}
+
+void to_counters(const RunTotals& t, ecmc_counters_t* out) {
+  out->sweeps = t.sweeps;
+  out->chains = t.chains;
+  out->events = t.events;
+  out->lifts = t.lifts;
+  out->frozen_hits = t.frozen;
+  out->wall_hits = t.walls;
+  out->fp64_evals = t.fp64_evals;
+  out->sum_b = t.sum_b;
+  out->sum_disp = t.sum_disp;
+}
+
 }  // namespace
 
 extern "C" {
 
-const char* ecmc_version(void) { return "ecmc-gb300 0.1 (sm_103a)"; }
+const char* ecmc_version(void) { return "ecmc-gb300 0.2 (sm_103a)"; }
 
 const char* ecmc_last_error_message(void) { return g_msg; }
 
@@ -407,101 +675,42 @@ const char* ecmc_strerror(int code) {
 
 int ecmc_create(ecmc_t* out, int64_t N, double L, double sigma, int cells_x, int cells_y,
                 double ell, uint64_t seed) {
-  if (!out) return fail(ECMC_ERR_ARG, "out is NULL");
-  *out = nullptr;
-  if (N < 1 || N >= (int64_t(1) << 27)) return fail(ECMC_ERR_ARG, "N out of range");
-  int64_t k = (int64_t)std::llround(std::sqrt((double)N));
-  if (k * k != N) return fail(ECMC_ERR_ARG, "N must be a perfect square (lattice start)");
-  if (!(L > 0.0) || !(sigma > 0.0) || !std::isfinite(L) || !std::isfinite(sigma))
-    return fail(ECMC_ERR_ARG, "L and sigma must be positive");
-  if (cells_x < 2 || cells_y < 2 || (cells_x & 1) || (cells_y & 1))
-    return fail(ECMC_ERR_ARG, "cells per side must be even and >= 2");
-  if (!(L / cells_x > sigma) || !(L / cells_y > sigma))
-    return fail(ECMC_ERR_ARG, "cell side must exceed sigma");
-  if (!(L / (double)k > sigma)) return fail(ECMC_ERR_ARG, "square lattice would overlap");
-  if (!(ell >= 0.0) || !std::isfinite(ell)) return fail(ECMC_ERR_ARG, "ell must be >= 0");
-  if ((int64_t)cells_x * cells_y > (int64_t(1) << 26)) return fail(ECMC_ERR_ARG, "too many cells");
+  ecmc_replica_desc_t d;
+  d.N = N;
+  d.L = L;
+  d.sigma = sigma;
+  d.cells_x = cells_x;
+  d.cells_y = cells_y;
+  d.ell = ell;
+  d.n_m = 0;
+  d.seed = seed;
+  d.replica = 0;
+  return create_impl(out, &d, 1);
+}
 
-  ecmc_ctx* h = new (std::nothrow) ecmc_ctx();
-  if (!h) return fail(ECMC_ERR_OOM, "host allocation failed");
-  std::memset(&h->b, 0, sizeof(h->b));
-  Geom& g = h->g;
-  std::memset(&g, 0, sizeof(g));
-  g.N = N;
-  g.L = L;
-  g.sigma = sigma;
-  g.sig2 = sigma * sigma;
-  g.cells_x = cells_x;
-  g.cells_y = cells_y;
-  g.ncell = cells_x * cells_y;
-  g.w = L / (double)cells_x;
-  g.h = L / (double)cells_y;
-  g.inv_w = 1.0 / g.w;
-  g.inv_h = 1.0 / g.h;
-  g.ell = ell;
-  g.seed = seed;
-  g.replica = 0;
-  g.dir_mode = 0;
-  g.precision = 1;
-  g.cap_mem = (int)std::floor(packing_bound(g.w, g.h, sigma)) + 2;
-  g.cap_obj = (int)std::floor(packing_bound(g.w + 2 * sigma, g.h + 2 * sigma, sigma)) + 2;
-  if (g.cap_mem > g.cap_obj) g.cap_mem = g.cap_obj;
-  if ((int64_t)g.ncell * g.cap_mem < N) {
-    delete h;
-    return fail(ECMC_ERR_ARG, "N exceeds the packing capacity of the box");
-  }
-  g.n_m = default_nm(g);
-  set_screen_bounds(g);
+int ecmc_create_batch(ecmc_t* out, const ecmc_replica_desc_t* desc, int R) {
+  return create_impl(out, desc, R);
+}
 
-  auto bail = [&](int rc) {
-    free_all(h);
-    delete h;
-    return rc;
-  };
-  if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess)
-    return bail(fail(ECMC_ERR_CUDA, "cannot create a stream (no CUDA device?)"));
-  h->stream = h->own_stream;
-  const size_t slots = (size_t)g.ncell * g.cap_mem;
-  for (int i = 0; i < 2; ++i) {
-    if (cudaMalloc(&h->b.px[i], sizeof(double) * slots) != cudaSuccess ||
-        cudaMalloc(&h->b.py[i], sizeof(double) * slots) != cudaSuccess ||
-        cudaMalloc(&h->b.pid[i], sizeof(int) * slots) != cudaSuccess ||
-        cudaMalloc(&h->b.count[i], sizeof(int) * g.ncell) != cudaSuccess)
-      return bail(fail(ECMC_ERR_OOM, "device allocation of %zu slots failed", slots));
-    cudaMemsetAsync(h->b.count[i], 0, sizeof(int) * g.ncell, h->stream);
-  }
-  if (cudaMalloc(&h->b.state, sizeof(SweepState)) != cudaSuccess ||
-      cudaMalloc(&h->b.cell_stats, sizeof(CellStats) * g.ncell) != cudaSuccess ||
-      cudaMalloc(&h->b.totals, sizeof(RunTotals)) != cudaSuccess ||
-      cudaMalloc(&h->b.err, sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&h->xy_tmp, sizeof(double) * 2 * (size_t)N) != cudaSuccess ||
-      cudaMalloc(&h->int_tmp, sizeof(int) * (size_t)N) != cudaSuccess ||
-      cudaMalloc(&h->u64_tmp, sizeof(unsigned long long) * 4) != cudaSuccess)
-    return bail(fail(ECMC_ERR_OOM, "device allocation failed"));
-  cudaMemsetAsync(h->b.totals, 0, sizeof(RunTotals), h->stream);
-  cudaMemsetAsync(h->b.err, 0, sizeof(int), h->stream);
-  cudaMemsetAsync(h->b.cell_stats, 0, sizeof(CellStats) * g.ncell, h->stream);
-  h->b.cur = 0;
-  int rc = compute_layout(h);
-  if (rc) return bail(rc);
-  rc = ensure_history(h, 1024);
-  if (rc) return bail(rc);
-  rc = setup_gr(h);
-  if (rc) return bail(rc);
+int ecmc_num_replicas(ecmc_t h, int* R) {
+  if (!h || !R) return fail(ECMC_ERR_ARG, "NULL argument");
+  *R = h->b.R;
+  return ECMC_OK;
+}
 
-  // square-lattice start
-  std::vector<double> xy(2 * (size_t)N);
-  const double a = L / (double)k;
-  for (int64_t i = 0; i < N; ++i) {
-    xy[2 * i] = ((double)(i % k) + 0.5) * a;
-    xy[2 * i + 1] = ((double)(i / k) + 0.5) * a;
-  }
-  if (cudaMemcpyAsync(h->xy_tmp, xy.data(), sizeof(double) * 2 * N, cudaMemcpyHostToDevice,
-                      h->stream) != cudaSuccess)
-    return bail(fail(ECMC_ERR_CUDA, "upload failed"));
-  rc = load_positions_dev(h, h->xy_tmp, 0);
-  if (rc) return bail(rc);
-  *out = h;
+int ecmc_replica_desc(ecmc_t h, int r, ecmc_replica_desc_t* out) {
+  if (!h || !out) return fail(ECMC_ERR_ARG, "NULL argument");
+  if (r < 0 || r >= h->b.R) return fail(ECMC_ERR_ARG, "replica out of range");
+  const Geom& g = h->geo[r];
+  out->N = g.N;
+  out->L = g.L;
+  out->sigma = g.sigma;
+  out->cells_x = g.cells_x;
+  out->cells_y = g.cells_y;
+  out->ell = g.ell;
+  out->n_m = g.n_m;
+  out->seed = g.seed;
+  out->replica = g.replica;
   return ECMC_OK;
 }
 
@@ -527,22 +736,26 @@ int ecmc_set_param(ecmc_t h, int key, double v) {
   switch (key) {
     case ECMC_PARAM_N_CHAINS: {
       if (!(v >= 1.0 && v <= 1e6) || v != std::floor(v)) return fail(ECMC_ERR_ARG, "n_m");
-      h->g.n_m = (int)v;
+      for (Geom& g : h->geo) g.n_m = (int)v;
       drop_graphs(h);
+      int rc = upload_geometry(h);
+      if (rc) return rc;
       return realloc_chain_recs(h);
     }
     case ECMC_PARAM_DIR_MODE:
       if (v != 0.0 && v != 1.0) return fail(ECMC_ERR_ARG, "direction mode");
-      h->g.dir_mode = (int)v;
-      break;
+      for (Geom& g : h->geo) g.dir_mode = (int)v;
+      return upload_geometry(h);
     case ECMC_PARAM_PRECISION:
       if (v != 0.0 && v != 1.0) return fail(ECMC_ERR_ARG, "precision");
-      h->g.precision = (int)v;
-      break;
+      h->precision = (int)v;
+      for (Geom& g : h->geo) g.precision = (int)v;
+      drop_graphs(h);
+      return upload_geometry(h);
     case ECMC_PARAM_REPLICA:
       if (!(v >= 0.0) || v != std::floor(v) || v > 9.0e15) return fail(ECMC_ERR_ARG, "replica");
-      h->g.replica = (uint64_t)v;
-      break;
+      h->geo[0].replica = (uint64_t)v;
+      return upload_geometry(h);
     case ECMC_PARAM_LANES_PER_CELL: {
       const int t = (int)v;
       if ((double)t != v || !(t == 0 || t == 1 || t == 2 || t == 4 || t == 8 || t == 16 || t == 32))
@@ -568,7 +781,7 @@ int ecmc_set_param(ecmc_t h, int key, double v) {
       h->gr_dr = v;
       return setup_gr(h);
     case ECMC_PARAM_GR_RMAX:
-      if (!(v > h->g.sigma && v < 0.5 * h->g.L)) return fail(ECMC_ERR_ARG, "g(r) range");
+      if (!(v > h->geo[0].sigma && v < 0.5 * h->geo[0].L)) return fail(ECMC_ERR_ARG, "g(r) range");
       h->gr_rmax = v;
       return setup_gr(h);
     case ECMC_PARAM_TIMING:
@@ -585,17 +798,15 @@ int ecmc_set_param(ecmc_t h, int key, double v) {
     default:
       return fail(ECMC_ERR_ARG, "unknown parameter %d", key);
   }
-  drop_graphs(h);
-  return ECMC_OK;
 }
 
 int ecmc_get_param(ecmc_t h, int key, double* v) {
   if (!h || !v) return fail(ECMC_ERR_ARG, "NULL argument");
   switch (key) {
-    case ECMC_PARAM_N_CHAINS: *v = h->g.n_m; break;
-    case ECMC_PARAM_DIR_MODE: *v = h->g.dir_mode; break;
-    case ECMC_PARAM_PRECISION: *v = h->g.precision; break;
-    case ECMC_PARAM_REPLICA: *v = (double)h->g.replica; break;
+    case ECMC_PARAM_N_CHAINS: *v = h->geo[0].n_m; break;
+    case ECMC_PARAM_DIR_MODE: *v = h->geo[0].dir_mode; break;
+    case ECMC_PARAM_PRECISION: *v = h->precision; break;
+    case ECMC_PARAM_REPLICA: *v = (double)h->geo[0].replica; break;
     case ECMC_PARAM_LANES_PER_CELL: *v = h->tpc; break;
     case ECMC_PARAM_GR_DR: *v = h->gr_dr; break;
     case ECMC_PARAM_GR_RMAX: *v = h->gr_rmax; break;
@@ -613,7 +824,7 @@ int ecmc_set_positions(ecmc_t h, const double* xy, int on_device, int64_t t0) {
   if (!h || !xy) return fail(ECMC_ERR_ARG, "NULL argument");
   if (t0 < 0) return fail(ECMC_ERR_ARG, "t0 < 0");
   CK(cudaStreamSynchronize(h->stream));
-  CK(cudaMemcpyAsync(h->xy_tmp, xy, sizeof(double) * 2 * (size_t)h->g.N,
+  CK(cudaMemcpyAsync(h->xy_tmp, xy, sizeof(double) * 2 * (size_t)h->b.N_total,
                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
   return load_positions_dev(h, h->xy_tmp, t0);
 }
@@ -667,11 +878,11 @@ int ecmc_synchronize(ecmc_t h) {
 
 int ecmc_positions(ecmc_t h, double* xy_out, int on_device) {
   if (!h || !xy_out) return fail(ECMC_ERR_ARG, "NULL argument");
-  const size_t bytes = sizeof(double) * 2 * (size_t)h->g.N;
+  const size_t bytes = sizeof(double) * 2 * (size_t)h->b.N_total;
   if (on_device) {
-    launch_gather(h->g, h->b, xy_out, h->stream);
+    launch_gather(h->b, xy_out, h->stream);
   } else {
-    launch_gather(h->g, h->b, h->xy_tmp, h->stream);
+    launch_gather(h->b, h->xy_tmp, h->stream);
     CK(cudaMemcpyAsync(xy_out, h->xy_tmp, bytes, cudaMemcpyDeviceToHost, h->stream));
   }
   CK(cudaGetLastError());
@@ -686,85 +897,73 @@ int ecmc_sweep_index(ecmc_t h, int64_t* t) {
 
 int ecmc_counters(ecmc_t h, ecmc_counters_t* out) {
   if (!h || !out) return fail(ECMC_ERR_ARG, "NULL argument");
-  RunTotals t;
-  CK(cudaMemcpyAsync(&t, h->b.totals, sizeof(t), cudaMemcpyDeviceToHost, h->stream));
+  std::vector<RunTotals> t(h->b.R);
+  CK(cudaMemcpyAsync(t.data(), h->b.totals, sizeof(RunTotals) * t.size(), cudaMemcpyDeviceToHost,
+                     h->stream));
   int rc = check_device_error(h);
   if (rc) return rc;
-  out->sweeps = t.sweeps;
-  out->chains = t.chains;
-  out->events = t.events;
-  out->lifts = t.lifts;
-  out->frozen_hits = t.frozen;
-  out->wall_hits = t.walls;
-  out->fp64_evals = t.fp64_evals;
-  out->sum_b = t.sum_b;
-  out->sum_disp = t.sum_disp;
+  RunTotals s;
+  std::memset(&s, 0, sizeof(s));
+  for (const RunTotals& v : t) {
+    s.sum_b += v.sum_b;
+    s.sum_disp += v.sum_disp;
+    s.sweeps = v.sweeps;
+    s.chains += v.chains;
+    s.events += v.events;
+    s.lifts += v.lifts;
+    s.frozen += v.frozen;
+    s.walls += v.walls;
+    s.fp64_evals += v.fp64_evals;
+  }
+  to_counters(s, out);
+  return ECMC_OK;
+}
+
+int ecmc_replica_counters(ecmc_t h, int r, ecmc_counters_t* out) {
+  if (!h || !out) return fail(ECMC_ERR_ARG, "NULL argument");
+  if (r < 0 || r >= h->b.R) return fail(ECMC_ERR_ARG, "replica out of range");
+  RunTotals t;
+  CK(cudaMemcpyAsync(&t, h->b.totals + r, sizeof(t), cudaMemcpyDeviceToHost, h->stream));
+  int rc = check_device_error(h);
+  if (rc) return rc;
+  to_counters(t, out);
   return ECMC_OK;
 }
 
 int ecmc_reset_stats(ecmc_t h) {
   if (!h) return fail(ECMC_ERR_ARG, "NULL handle");
   CK(cudaStreamSynchronize(h->stream));
-  CK(cudaMemsetAsync(h->b.totals, 0, sizeof(RunTotals), h->stream));
+  CK(cudaMemsetAsync(h->b.totals, 0, sizeof(RunTotals) * h->b.R, h->stream));
   const int64_t zero = 0;
-  CK(cudaMemcpyAsync((char*)h->b.state + offsetof(SweepState, history_len), &zero, sizeof(zero),
-                     cudaMemcpyHostToDevice, h->stream));
+  for (int r = 0; r < h->b.R; ++r)
+    CK(cudaMemcpyAsync((char*)(h->b.state + r) + offsetof(SweepState, history_len), &zero,
+                       sizeof(zero), cudaMemcpyHostToDevice, h->stream));
   h->hist_len_host = 0;
   CK(cudaMemsetAsync(h->gr_counts, 0, sizeof(unsigned long long) * h->gr_nbins, h->stream));
   h->gr_meas = 0;
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->timing) harvest_timing(h);
   for (int c = 0; c < 4; ++c) {
     h->ms[c] = 0.0;
     h->launches[c] = 0;
   }
-  CK(cudaStreamSynchronize(h->stream));
-  if (h->timing) harvest_timing(h);
-  for (int c = 0; c < 4; ++c) h->ms[c] = 0.0;
   return ECMC_OK;
 }
 
 int ecmc_pressure(ecmc_t h, double* betaP, double* se) {
   if (!h || !betaP) return fail(ECMC_ERR_ARG, "NULL argument");
-  const int64_t n = h->hist_len_host;
-  if (n < 1) return fail(ECMC_ERR_STATE, "no sweep since the last reset");
-  std::vector<double> hist(2 * (size_t)n);
-  CK(cudaMemcpyAsync(hist.data(), h->b.history, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost,
-                     h->stream));
-  RunTotals t;
-  CK(cudaMemcpyAsync(&t, h->b.totals, sizeof(t), cudaMemcpyDeviceToHost, h->stream));
-  int rc = check_device_error(h);
-  if (rc) return rc;
-  const double rho_s2 = (double)h->g.N / (h->g.L * h->g.L) * h->g.sig2;
-  if (!(t.sum_disp_w > 0.0)) return fail(ECMC_ERR_STATE, "no displacement since the last reset");
-  *betaP = rho_s2 * (1.0 + t.sum_b_w / t.sum_disp_w);
-  if (se) {
-    *se = 0.0;
-    const int64_t nb = n >= 20 ? 20 : n;
-    if (nb >= 2) {
-      std::vector<double> vals;
-      for (int64_t bI = 0; bI < nb; ++bI) {
-        const int64_t lo = bI * n / nb, hi = (bI + 1) * n / nb;
-        double sb = 0.0, sd = 0.0;
-        for (int64_t i = lo; i < hi; ++i) {
-          sb += hist[2 * i];
-          sd += hist[2 * i + 1];
-        }
-        vals.push_back(rho_s2 * (1.0 + sb / sd));
-      }
-      double mean = 0.0;
-      for (double v : vals) mean += v;
-      mean /= (double)nb;
-      double var = 0.0;
-      for (double v : vals) var += (v - mean) * (v - mean);
-      var /= (double)(nb - 1);
-      *se = std::sqrt(var / (double)nb);
-    }
-  }
-  return ECMC_OK;
+  return pressure_of(h, 0, betaP, se);
+}
+
+int ecmc_replica_pressure(ecmc_t h, int r, double* betaP, double* se) {
+  if (!h || !betaP) return fail(ECMC_ERR_ARG, "NULL argument");
+  if (r < 0 || r >= h->b.R) return fail(ECMC_ERR_ARG, "replica out of range");
+  return pressure_of(h, r, betaP, se);
 }
 
 int ecmc_gr_measure(ecmc_t h) {
   if (!h) return fail(ECMC_ERR_ARG, "NULL handle");
-  launch_gr(h->g, h->b, h->gr_dr, h->gr_nbins, h->gr_counts, h->stream);
+  launch_gr(h->geo[0], h->b, h->gr_dr, h->gr_nbins, h->gr_counts, h->stream);
   CK(cudaGetLastError());
   h->gr_meas += 1;
   return ECMC_OK;
@@ -794,10 +993,11 @@ int ecmc_gr(ecmc_t h, double* g_out, double* r_out, int nbins) {
   int rc = ecmc_gr_counts(h, c.data(), nbins, &nm);
   if (rc) return rc;
   if (nm < 1) return fail(ECMC_ERR_STATE, "no g(r) measurement yet");
+  const Geom& g = h->geo[0];
   const double pi = 3.14159265358979323846;
-  const double N = (double)h->g.N, rho = N / (h->g.L * h->g.L), dr = h->gr_dr;
+  const double N = (double)g.N, rho = N / (g.L * g.L), dr = h->gr_dr;
   for (int i = 0; i < nbins; ++i) {
-    const double e0 = h->g.sigma + dr * i, e1 = e0 + dr;
+    const double e0 = g.sigma + dr * i, e1 = e0 + dr;
     const double R = 2.0 * (e1 * e1 * e1 - e0 * e0 * e0) / (3.0 * (e1 * e1 - e0 * e0));
     g_out[i] = ((double)c[i] / (double)nm) / (N * rho * 2.0 * pi * R * dr);
     if (r_out) r_out[i] = R;
@@ -807,25 +1007,17 @@ int ecmc_gr(ecmc_t h, double* g_out, double* r_out, int nbins) {
 
 int ecmc_min_distance(ecmc_t h, double* dmin) {
   if (!h || !dmin) return fail(ECMC_ERR_ARG, "NULL argument");
-  unsigned long long init = 0;
-  const double r2 = 4.0 * h->g.sig2;
-  std::memcpy(&init, &r2, sizeof(r2));
-  CK(cudaMemcpyAsync(h->u64_tmp, &init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
-  launch_min_dist(h->g, h->b, 2.0 * h->g.sigma, h->u64_tmp, h->stream);
-  unsigned long long bits = 0;
-  CK(cudaMemcpyAsync(&bits, h->u64_tmp, sizeof(bits), cudaMemcpyDeviceToHost, h->stream));
-  int rc = check_device_error(h);
+  double d2 = 0.0;
+  int rc = min_dist2(h, &d2);
   if (rc) return rc;
-  double d2;
-  std::memcpy(&d2, &bits, sizeof(d2));
   *dmin = std::sqrt(d2);
   return ECMC_OK;
 }
 
 int ecmc_last_cells(ecmc_t h, int32_t* cell_of_id) {
   if (!h || !cell_of_id) return fail(ECMC_ERR_ARG, "NULL argument");
-  launch_cells_of(h->g, h->b, h->int_tmp, h->stream);
-  CK(cudaMemcpyAsync(cell_of_id, h->int_tmp, sizeof(int) * (size_t)h->g.N,
+  for (const Geom& g : h->geo) launch_cells_of(g, h->b, h->int_tmp + g.n_off, h->stream);
+  CK(cudaMemcpyAsync(cell_of_id, h->int_tmp, sizeof(int) * (size_t)h->b.N_total,
                      cudaMemcpyDeviceToHost, h->stream));
   return check_device_error(h);
 }
@@ -848,10 +1040,12 @@ int ecmc_kernel_times(ecmc_t h, ecmc_timing_t* out) {
 int ecmc_chain_records(ecmc_t h, ecmc_chain_rec_t* out, int64_t n) {
   if (!h || !out) return fail(ECMC_ERR_ARG, "NULL argument");
   if (!h->record_chains || !h->b.chain_recs) return fail(ECMC_ERR_STATE, "records are off");
-  if (n != (int64_t)h->g.ncell * h->g.n_m) return fail(ECMC_ERR_ARG, "n must be cells * n_m");
+  const Geom& g = h->geo[0];
+  if (n != (int64_t)g.ncell * g.n_m) return fail(ECMC_ERR_ARG, "n must be cells * n_m");
   static_assert(sizeof(ChainRec) == sizeof(ecmc_chain_rec_t), "record layout");
-  CK(cudaMemcpyAsync(out, h->b.chain_recs, sizeof(ChainRec) * n, cudaMemcpyDeviceToHost,
-                     h->stream));
+  CK(cudaMemcpy2DAsync(out, sizeof(ChainRec) * g.n_m, h->b.chain_recs,
+                       sizeof(ChainRec) * h->b.rec_stride, sizeof(ChainRec) * g.n_m, g.ncell,
+                       cudaMemcpyDeviceToHost, h->stream));
   return check_device_error(h);
 }
 

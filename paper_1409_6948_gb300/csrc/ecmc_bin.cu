@@ -1,5 +1,6 @@
 // ecmc_bin.cu -- per-sweep draws, cell binning into fixed-capacity buckets,
-// the end-of-sweep reduction, and the gather back to disk-id order.
+// the end-of-sweep reduction, and the gather back to disk-id order, for all
+// replicas of a handle at once.
 //
 // Sec. 3.4 steps 1-3: every sweep decomposes the box into cells on a square
 // lattice shifted by a random vector and draws one colour order for all
@@ -9,13 +10,17 @@
 
 namespace ecmc {
 
-// One thread: shift and colour order of sweep state->t from Philox(t, 0, 0, 0).
-__global__ void k_sweep_begin(Geom g, SweepState* st) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const int64_t t = st->t;
+// One thread per replica: shift and colour order of sweep state->t from
+// Philox(t, 0, 0, 0) under the replica's key.
+__global__ void k_sweep_begin(const Geom* __restrict__ rg, SweepState* st, int R) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const Geom& g = rg[r];
+  SweepState& s = st[r];
+  const int64_t t = s.t;
   U64x4 u = philox((uint64_t)t, kPurposeSweep, 0, 0, g.seed, g.replica);
-  st->sx = unit_double(u.v[0]) * g.w;
-  st->sy = unit_double(u.v[1]) * g.h;
+  s.sx = unit_double(u.v[0]) * g.w;
+  s.sy = unit_double(u.v[1]) * g.h;
   // colour order: permutation number floor(u2 * 24 / 2^64) of (0,1,2,3) in
   // lexicographic order, decoded from its factorial-base digits 6, 2, 1
   int code = (int)below_n(u.v[2], 24);
@@ -25,150 +30,166 @@ __global__ void k_sweep_begin(Geom g, SweepState* st) {
   for (int i = 0; i < 3; ++i) {
     int d = code / radix[i];
     code -= d * radix[i];
-    st->perm[i] = pool[d];
+    s.perm[i] = pool[d];
     for (int j = d; j < left - 1; ++j) pool[j] = pool[j + 1];
     --left;
   }
-  st->perm[3] = pool[0];
-  st->axis = (int)(t & 1);
+  s.perm[3] = pool[0];
+  s.axis = (int)(t & 1);
 }
 
-void launch_sweep_begin(const Geom& g, const DevBufs& b, cudaStream_t s) {
-  k_sweep_begin<<<1, 32, 0, s>>>(g, b.state);
+void launch_sweep_begin(const DevBufs& b, cudaStream_t s) {
+  k_sweep_begin<<<(b.R + 31) / 32, 32, 0, s>>>(b.rg, b.state, b.R);
 }
 
-// Bin every disk of buffer src into the buckets of buffer dst (whose counts
-// are zero on entry).  Bucketed input: thread per slot of the padded array.
-__global__ void k_bin_bucketed(Geom g, const SweepState* __restrict__ st,
-                               const double* __restrict__ px, const double* __restrict__ py,
-                               const int* __restrict__ pid, const int* __restrict__ cnt_src,
-                               double* __restrict__ qx, double* __restrict__ qy,
-                               int* __restrict__ qid, int* __restrict__ cnt_dst, int* err) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t total = (int64_t)g.ncell * g.cap_mem;
-  if (i >= total) return;
-  const int c = (int)(i / g.cap_mem);
-  const int k = (int)(i - (int64_t)c * g.cap_mem);
-  if (k >= min(__ldg(&cnt_src[c]), g.cap_mem)) return;
-  const double x = px[i], y = py[i];
-  const int id = pid[i];
-  const double sx = st->sx, sy = st->sy;
-  const int cx = cell_1d(x, sx, g.L, g.inv_w, g.cells_x);
-  const int cy = cell_1d(y, sy, g.L, g.inv_h, g.cells_y);
-  const int cn = cy * g.cells_x + cx;
+__device__ __forceinline__ void bin_one(const Geom& g, const SweepState& st, double x, double y,
+                                        int id, double* __restrict__ qx, double* __restrict__ qy,
+                                        int* __restrict__ qid, int* __restrict__ cnt_dst, int cap,
+                                        int* err) {
+  const int cx = cell_1d(x, st.sx, g.L, g.inv_w, g.cells_x);
+  const int cy = cell_1d(y, st.sy, g.L, g.inv_h, g.cells_y);
+  const int cn = g.cell_off + cy * g.cells_x + cx;
   const int r = atomicAdd(&cnt_dst[cn], 1);
-  if (r >= g.cap_mem) {
+  if (r >= cap) {
     atomicCAS(err, DEV_OK, DEV_CAPACITY);
     return;
   }
-  const int64_t o = (int64_t)cn * g.cap_mem + r;
+  const int64_t o = (int64_t)cn * cap + r;
   qx[o] = x;
   qy[o] = y;
   qid[o] = id;
 }
 
-// Flat input (positions in id order, slots 0..N-1 of px, py).
-__global__ void k_bin_flat(Geom g, const SweepState* __restrict__ st,
+// Bin every disk of buffer src into the buckets of buffer dst (whose counts
+// are zero on entry).  Bucketed input: thread per slot of the padded array.
+__global__ void k_bin_bucketed(const Geom* __restrict__ rg, const SweepState* __restrict__ st,
+                               const int* __restrict__ cell_rep, int C_total, int cap,
+                               const double* __restrict__ px, const double* __restrict__ py,
+                               const int* __restrict__ pid, const int* __restrict__ cnt_src,
+                               double* __restrict__ qx, double* __restrict__ qy,
+                               int* __restrict__ qid, int* __restrict__ cnt_dst, int* err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)C_total * cap) return;
+  const int c = (int)(i / cap);
+  const int k = (int)(i - (int64_t)c * cap);
+  if (k >= min(__ldg(&cnt_src[c]), cap)) return;
+  const int r = cell_rep[c];
+  bin_one(rg[r], st[r], px[i], py[i], pid[i], qx, qy, qid, cnt_dst, cap, err);
+}
+
+__device__ __forceinline__ int replica_of_disk(const int64_t* __restrict__ n_off, int R,
+                                               int64_t i) {
+  int lo = 0, hi = R - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (n_off[mid] <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Flat input (positions of all replicas concatenated in id order, slots
+// 0..N_total-1 of px, py).
+__global__ void k_bin_flat(const Geom* __restrict__ rg, const SweepState* __restrict__ st,
+                           const int64_t* __restrict__ n_off, int R, int64_t N_total, int cap,
                            const double* __restrict__ px, const double* __restrict__ py,
                            double* __restrict__ qx, double* __restrict__ qy, int* __restrict__ qid,
                            int* __restrict__ cnt_dst, int* err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.N) return;
-  const double x = px[i], y = py[i];
-  const int cx = cell_1d(x, st->sx, g.L, g.inv_w, g.cells_x);
-  const int cy = cell_1d(y, st->sy, g.L, g.inv_h, g.cells_y);
-  const int cn = cy * g.cells_x + cx;
-  const int r = atomicAdd(&cnt_dst[cn], 1);
-  if (r >= g.cap_mem) {
-    atomicCAS(err, DEV_OK, DEV_CAPACITY);
-    return;
-  }
-  const int64_t o = (int64_t)cn * g.cap_mem + r;
-  qx[o] = x;
-  qy[o] = y;
-  qid[o] = (int)i;
+  if (i >= N_total) return;
+  const int r = replica_of_disk(n_off, R, i);
+  bin_one(rg[r], st[r], px[i], py[i], (int)(i - n_off[r]), qx, qy, qid, cnt_dst, cap, err);
 }
 
-void launch_bin(const Geom& g, const DevBufs& b, int src, int dst, cudaStream_t s) {
-  cudaMemsetAsync(b.count[dst], 0, sizeof(int) * (size_t)g.ncell, s);
+void launch_bin(const DevBufs& b, int src, int dst, cudaStream_t s) {
+  cudaMemsetAsync(b.count[dst], 0, sizeof(int) * (size_t)b.C_total, s);
   const int bs = 256;
   if (src < 0) {  // flat input lives in buffer 1-dst
     const int sb = 1 - dst;
-    const int64_t nb = (g.N + bs - 1) / bs;
-    k_bin_flat<<<(unsigned)nb, bs, 0, s>>>(g, b.state, b.px[sb], b.py[sb], b.px[dst], b.py[dst],
-                                          b.pid[dst], b.count[dst], b.err);
+    const int64_t nb = (b.N_total + bs - 1) / bs;
+    k_bin_flat<<<(unsigned)nb, bs, 0, s>>>(b.rg, b.state, b.n_off, b.R, b.N_total, b.cap, b.px[sb],
+                                          b.py[sb], b.px[dst], b.py[dst], b.pid[dst],
+                                          b.count[dst], b.err);
   } else {
-    const int64_t total = (int64_t)g.ncell * g.cap_mem;
+    const int64_t total = (int64_t)b.C_total * b.cap;
     const int64_t nb = (total + bs - 1) / bs;
-    k_bin_bucketed<<<(unsigned)nb, bs, 0, s>>>(g, b.state, b.px[src], b.py[src], b.pid[src],
-                                              b.count[src], b.px[dst], b.py[dst], b.pid[dst],
-                                              b.count[dst], b.err);
+    k_bin_bucketed<<<(unsigned)nb, bs, 0, s>>>(b.rg, b.state, b.cell_rep, b.C_total, b.cap,
+                                              b.px[src], b.py[src], b.pid[src], b.count[src],
+                                              b.px[dst], b.py[dst], b.pid[dst], b.count[dst],
+                                              b.err);
   }
 }
 
-// Wrap caller positions (interleaved, id order) into [0, L) as a flat list.
-__global__ void k_load_flat(Geom g, const double* __restrict__ xy, double* __restrict__ px,
-                            double* __restrict__ py) {
+// Wrap caller positions (interleaved, id order, replicas concatenated) into
+// [0, L) of their replica as a flat list.
+__global__ void k_load_flat(const Geom* __restrict__ rg, const int64_t* __restrict__ n_off, int R,
+                            int64_t N_total, const double* __restrict__ xy,
+                            double* __restrict__ px, double* __restrict__ py) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.N) return;
+  if (i >= N_total) return;
+  const double L = rg[replica_of_disk(n_off, R, i)].L;
   double x = xy[2 * i], y = xy[2 * i + 1];
-  x = x - g.L * floor(x / g.L);
-  y = y - g.L * floor(y / g.L);
-  if (x >= g.L) x -= g.L;
-  if (y >= g.L) y -= g.L;
+  x = x - L * floor(x / L);
+  y = y - L * floor(y / L);
+  if (x >= L) x -= L;
+  if (y >= L) y -= L;
   px[i] = x;
   py[i] = y;
 }
 
-void launch_load_flat(const Geom& g, const DevBufs& b, const double* xy_dev, cudaStream_t s) {
+void launch_load_flat(const DevBufs& b, const double* xy_dev, cudaStream_t s) {
   const int bs = 256;
   const int other = 1 - b.cur;
-  k_load_flat<<<(unsigned)((g.N + bs - 1) / bs), bs, 0, s>>>(g, xy_dev, b.px[other], b.py[other]);
+  k_load_flat<<<(unsigned)((b.N_total + bs - 1) / bs), bs, 0, s>>>(
+      b.rg, b.n_off, b.R, b.N_total, xy_dev, b.px[other], b.py[other]);
 }
 
-// Positions back to id order (interleaved pairs).
-__global__ void k_gather(Geom g, const double* __restrict__ px, const double* __restrict__ py,
-                         const int* __restrict__ pid, const int* __restrict__ cnt,
-                         double* __restrict__ out) {
+// Positions back to id order (interleaved pairs, replicas concatenated).
+__global__ void k_gather(const Geom* __restrict__ rg, const int* __restrict__ cell_rep,
+                         int C_total, int cap, const double* __restrict__ px,
+                         const double* __restrict__ py, const int* __restrict__ pid,
+                         const int* __restrict__ cnt, double* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t total = (int64_t)g.ncell * g.cap_mem;
-  if (i >= total) return;
-  const int c = (int)(i / g.cap_mem);
-  const int k = (int)(i - (int64_t)c * g.cap_mem);
-  if (k >= min(cnt[c], g.cap_mem)) return;
-  const int id = pid[i];
-  out[2 * (int64_t)id] = px[i];
-  out[2 * (int64_t)id + 1] = py[i];
+  if (i >= (int64_t)C_total * cap) return;
+  const int c = (int)(i / cap);
+  const int k = (int)(i - (int64_t)c * cap);
+  if (k >= min(cnt[c], cap)) return;
+  const int64_t id = rg[cell_rep[c]].n_off + pid[i];
+  out[2 * id] = px[i];
+  out[2 * id + 1] = py[i];
 }
 
-void launch_gather(const Geom& g, const DevBufs& b, double* xy_out, cudaStream_t s) {
+void launch_gather(const DevBufs& b, double* xy_out, cudaStream_t s) {
   const int bs = 256;
-  const int64_t total = (int64_t)g.ncell * g.cap_mem;
-  k_gather<<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(g, b.px[b.cur], b.py[b.cur],
-                                                           b.pid[b.cur], b.count[b.cur], xy_out);
+  const int64_t total = (int64_t)b.C_total * b.cap;
+  k_gather<<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(
+      b.rg, b.cell_rep, b.C_total, b.cap, b.px[b.cur], b.py[b.cur], b.pid[b.cur], b.count[b.cur],
+      xy_out);
 }
 
-__global__ void k_cells_of(Geom g, const int* __restrict__ pid, const int* __restrict__ cnt,
-                           int* __restrict__ out) {
+// Local cell of every disk of one replica (by id) in the last binning.
+__global__ void k_cells_of(Geom g, int cap, const int* __restrict__ pid,
+                           const int* __restrict__ cnt, int* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t total = (int64_t)g.ncell * g.cap_mem;
-  if (i >= total) return;
-  const int c = (int)(i / g.cap_mem);
-  const int k = (int)(i - (int64_t)c * g.cap_mem);
-  if (k >= min(cnt[c], g.cap_mem)) return;
-  out[pid[i]] = c;
+  if (i >= (int64_t)g.ncell * cap) return;
+  const int lc = (int)(i / cap);
+  const int k = (int)(i - (int64_t)lc * cap);
+  const int c = g.cell_off + lc;
+  if (k >= min(cnt[c], cap)) return;
+  out[pid[(int64_t)c * cap + k]] = lc;
 }
 
 void launch_cells_of(const Geom& g, const DevBufs& b, int* cell_of_id, cudaStream_t s) {
   const int bs = 256;
-  const int64_t total = (int64_t)g.ncell * g.cap_mem;
-  k_cells_of<<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(g, b.pid[b.cur], b.count[b.cur],
-                                                             cell_of_id);
+  const int64_t total = (int64_t)g.ncell * b.cap;
+  k_cells_of<<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(g, b.cap, b.pid[b.cur],
+                                                             b.count[b.cur], cell_of_id);
 }
 
-// End of sweep: reduce the per-cell results in a fixed order (deterministic),
-// add them to the running totals, append the member-weighted pressure sums of
-// this sweep to the history, advance the sweep counter.
+// End of sweep, one block per replica: reduce the replica's per-cell results
+// in a fixed order (deterministic), add them to its running totals, append
+// its member-weighted pressure sums of this sweep to its history, advance its
+// sweep counter.
 __device__ __forceinline__ double warp_sum_d(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
@@ -178,17 +199,19 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
   return v;
 }
 
-__global__ void __launch_bounds__(1024) k_sweep_end(Geom g, SweepState* st,
+__global__ void __launch_bounds__(1024) k_sweep_end(const Geom* __restrict__ rg, SweepState* st,
                                                     const CellStats* __restrict__ cs,
                                                     RunTotals* tot, double* history,
                                                     int64_t history_cap) {
   __shared__ double sd[2][32];
   __shared__ long long sl[6][32];
+  const int rep = blockIdx.x;
+  const Geom& g = rg[rep];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   double b = 0.0, bw = 0.0;
   long long v[6] = {0, 0, 0, 0, 0, 0};
   for (int c = tid; c < g.ncell; c += blockDim.x) {
-    const CellStats s = cs[c];
+    const CellStats s = cs[g.cell_off + c];
     b += s.sum_b;
     bw += (double)s.n_mem * s.sum_b;
     v[0] += s.events;
@@ -216,29 +239,33 @@ __global__ void __launch_bounds__(1024) k_sweep_end(Geom g, SweepState* st,
   bw = warp_sum_d(bw);
   for (int q = 0; q < 6; ++q) v[q] = warp_sum_ll(v[q]);
   if (lane == 0) {
+    RunTotals& T = tot[rep];
+    SweepState& S = st[rep];
     const double disp_w = (double)g.N * (double)g.n_m * g.ell;
-    tot->sum_b += b;
-    tot->sum_b_w += bw;
-    tot->sum_disp += (double)v[5] * g.ell;
-    tot->sum_disp_w += disp_w;
-    tot->events += v[0];
-    tot->lifts += v[1];
-    tot->frozen += v[2];
-    tot->walls += v[3];
-    tot->fp64_evals += v[4];
-    tot->chains += v[5];
-    tot->sweeps += 1;
-    if (st->history_len < history_cap) {
-      history[2 * st->history_len] = bw;
-      history[2 * st->history_len + 1] = disp_w;
+    T.sum_b += b;
+    T.sum_b_w += bw;
+    T.sum_disp += (double)v[5] * g.ell;
+    T.sum_disp_w += disp_w;
+    T.events += v[0];
+    T.lifts += v[1];
+    T.frozen += v[2];
+    T.walls += v[3];
+    T.fp64_evals += v[4];
+    T.chains += v[5];
+    T.sweeps += 1;
+    if (history != nullptr && S.history_len < history_cap) {
+      double* h = history + 2 * ((int64_t)rep * history_cap + S.history_len);
+      h[0] = bw;
+      h[1] = disp_w;
     }
-    st->history_len += 1;
-    st->t += 1;
+    S.history_len += 1;
+    S.t += 1;
   }
 }
 
-void launch_sweep_end(const Geom& g, const DevBufs& b, cudaStream_t s) {
-  k_sweep_end<<<1, 1024, 0, s>>>(g, b.state, b.cell_stats, b.totals, b.history, b.history_cap);
+void launch_sweep_end(const DevBufs& b, cudaStream_t s) {
+  k_sweep_end<<<b.R, 1024, 0, s>>>(b.rg, b.state, b.cell_stats, b.totals, b.history,
+                                   b.history_cap);
 }
 
 }  // namespace ecmc

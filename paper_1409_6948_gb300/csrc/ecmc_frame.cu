@@ -28,19 +28,24 @@ struct BuildSmem {
   int* hist;
 };
 
-__global__ void k_frame_build(Geom g, const SweepState* __restrict__ st, int colour_index,
+__global__ void k_frame_build(const Geom* __restrict__ rg, const SweepState* __restrict__ sts,
+                              const int* __restrict__ act_rep, int cap, int colour_index,
                               const double* __restrict__ px, const double* __restrict__ py,
                               const int* __restrict__ pid, const int* __restrict__ cnt,
                               unsigned char* __restrict__ records, RecLayout lay, int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_nobj, s_nmem, s_overflow;
   const int tid = threadIdx.x, bt = blockDim.x;
+  const int a = blockIdx.x;  // global active cell
+  const int rep = act_rep[a];
+  const Geom& g = rg[rep];
+  const SweepState* st = sts + rep;
   const int colour = st->perm[colour_index];
   const int hx = g.cells_x >> 1;
-  const int a = blockIdx.x;
-  const int cx = 2 * (a % hx) + (colour & 1);
-  const int cy = 2 * (a / hx) + (colour >> 1);
-  const int c = cy * g.cells_x + cx;
+  const int la = a - g.act_off;
+  const int cx = 2 * (la % hx) + (colour & 1);
+  const int cy = 2 * (la / hx) + (colour >> 1);
+  const int c = g.cell_off + cy * g.cells_x + cx;
   const int axis = st->axis;
   const double L = g.L, sigma = g.sigma;
   const double ox = st->sx + (double)cx * g.w;
@@ -67,9 +72,9 @@ __global__ void k_frame_build(Geom g, const SweepState* __restrict__ st, int col
 
   // members, in the cell frame
   const double hL = 0.5 * L;
-  const int nc = min(cnt[c], g.cap_mem);
+  const int nc = min(cnt[c], cap);
   for (int k = tid; k < nc; k += bt) {
-    const int64_t q = (int64_t)c * g.cap_mem + k;
+    const int64_t q = (int64_t)c * cap + k;
     const double X = wrap_half_i(px[q] - ox, L, hL);
     const double Y = wrap_half_i(py[q] - oy, L, hL);
     const int i = atomicAdd(&s_nobj, 1);
@@ -88,7 +93,7 @@ __global__ void k_frame_build(Geom g, const SweepState* __restrict__ st, int col
     for (int oxc = -1; oxc <= 1; ++oxc) {
       const int qx = ((cx + oxc) % g.cells_x + g.cells_x) % g.cells_x;
       const int qy = ((cy + oyc) % g.cells_y + g.cells_y) % g.cells_y;
-      const int q = qy * g.cells_x + qx;
+      const int q = g.cell_off + qy * g.cells_x + qx;
       if (q == c) continue;
       bool dup = false;
       for (int e = 0; e < nnb; ++e) dup |= (nb[e] == q);
@@ -106,9 +111,9 @@ __global__ void k_frame_build(Geom g, const SweepState* __restrict__ st, int col
   const float ylo = -(float)sigma - mf, yhi = (float)hl + mf;
   for (int e = 0; e < nnb; ++e) {
     const int n = nb[e];
-    const int nn = min(cnt[n], g.cap_mem);
+    const int nn = min(cnt[n], cap);
     for (int k = tid; k < nn; k += bt) {
-      const int64_t q = (int64_t)n * g.cap_mem + k;
+      const int64_t q = (int64_t)n * cap + k;
       const double xq = px[q], yq = py[q];
       // offsets j*L (j = -2..2) of the unwrapped difference that the FP32
       // screen keeps; an FP64 image k of the wrapped difference is offset
@@ -229,15 +234,15 @@ static size_t build_smem(const RecLayout& lay) {
          sizeof(int) * (size_t)lay.cap_mem + sizeof(int) * (size_t)(lay.nbin + 1) + 64;
 }
 
-void launch_frame_build(const Geom& g, const DevBufs& b, const RecLayout& lay, int colour_index,
+void launch_frame_build(const DevBufs& b, const RecLayout& lay, int colour_index,
                         cudaStream_t s) {
-  const int n_active = (g.cells_x / 2) * (g.cells_y / 2);
   const size_t sm = build_smem(lay);
   int bt = 32;
   if (lay.cap_obj > 256) bt = 128;
   if (lay.cap_obj > 1024) bt = 256;
-  k_frame_build<<<n_active, bt, sm, s>>>(g, b.state, colour_index, b.px[b.cur], b.py[b.cur],
-                                         b.pid[b.cur], b.count[b.cur], b.records, lay, b.err);
+  k_frame_build<<<b.A_total, bt, sm, s>>>(b.rg, b.state, b.act_rep, b.cap, colour_index,
+                                          b.px[b.cur], b.py[b.cur], b.pid[b.cur], b.count[b.cur],
+                                          b.records, lay, b.err);
 }
 
 size_t frame_build_smem(const RecLayout& lay) { return build_smem(lay); }

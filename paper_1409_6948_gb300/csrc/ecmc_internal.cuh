@@ -59,8 +59,17 @@ struct ChainRec {
   long long start_id, end_id, events, walls;
 };
 
-// ---- static geometry and capacities --------------------------------------
+// ---- static geometry and capacities of one replica -------------------------
+// A handle holds R independent replicas (R = 1 for ecmc_create).  Their cells
+// are numbered globally: replica r owns cells [cell_off, cell_off + ncell) and,
+// in every colour phase, active cells [act_off, act_off + nact).  All cell
+// buckets have the same capacity (the largest over the replicas).
 struct Geom {
+  int64_t n_off;     // first disk of this replica in concatenated positions
+  int cell_off;      // first global cell of this replica
+  int act_off;       // first global active cell (per colour phase)
+  int nact;          // active cells per colour phase: (cells_x/2)(cells_y/2)
+  int rep;           // replica index within the handle
   int64_t N;
   double L, sigma, sig2, w, h, inv_w, inv_h, ell;
   int cells_x, cells_y, ncell;
@@ -113,33 +122,42 @@ inline RecLayout make_layout(int cpw, int nbin, int cap_mem, int cap_obj) {
   return r;
 }
 
-// Device pointers of one handle.
+// Device pointers of one handle (and the host-side sizes launches need).
 struct DevBufs {
   double* px[2];
   double* py[2];
   int* pid[2];
   int* count[2];
   int cur;  // buffer holding the current positions
-  SweepState* state;
-  CellStats* cell_stats;
-  RunTotals* totals;
-  double* history;  // per sweep: sum_b_w, sum_disp_w
+  SweepState* state;       // [R]
+  CellStats* cell_stats;   // [C_total]
+  RunTotals* totals;       // [R]
+  double* history;         // [R][history_cap] pairs: sum_b_w, sum_disp_w
   int64_t history_cap;
   unsigned char* records;  // frame records of one colour
   int* err;
-  ChainRec* chain_recs;    // optional, [ncell * n_m]
+  ChainRec* chain_recs;    // optional, [C_total * max n_m]
+  int rec_stride;          // chain records per cell
+  const Geom* rg;          // [R] device copy of the replicas' geometry
+  const int* cell_rep;     // [C_total] replica of every global cell
+  const int* act_rep;      // [A_total] replica of every global active cell
+  const int64_t* n_off;    // [R + 1] disk offsets
+  int R, C_total, A_total, cap;
+  int64_t N_total;
 };
 
 // ---- launchers (defined in the .cu files) --------------------------------
-void launch_sweep_begin(const Geom& g, const DevBufs& b, cudaStream_t s);
-void launch_bin(const Geom& g, const DevBufs& b, int src, int dst, cudaStream_t s);
-void launch_frame_build(const Geom& g, const DevBufs& b, const RecLayout& lay, int colour_index,
+// Every launcher covers all replicas of the handle, except the measurements
+// (min_dist, gr, cells_of), which take the replica's host-side geometry.
+void launch_sweep_begin(const DevBufs& b, cudaStream_t s);
+void launch_bin(const DevBufs& b, int src, int dst, cudaStream_t s);
+void launch_frame_build(const DevBufs& b, const RecLayout& lay, int colour_index,
                         cudaStream_t s);
-int launch_phase(const Geom& g, const DevBufs& b, const RecLayout& lay, int colour_index, int tpc,
-                 int warps_per_block, int records_on, cudaStream_t s);
-void launch_sweep_end(const Geom& g, const DevBufs& b, cudaStream_t s);
-void launch_gather(const Geom& g, const DevBufs& b, double* xy_out, cudaStream_t s);
-void launch_load_flat(const Geom& g, const DevBufs& b, const double* xy_dev, cudaStream_t s);
+int launch_phase(const DevBufs& b, const RecLayout& lay, int colour_index, int tpc,
+                 int warps_per_block, int records_on, int precision, cudaStream_t s);
+void launch_sweep_end(const DevBufs& b, cudaStream_t s);
+void launch_gather(const DevBufs& b, double* xy_out, cudaStream_t s);
+void launch_load_flat(const DevBufs& b, const double* xy_dev, cudaStream_t s);
 void launch_cells_of(const Geom& g, const DevBufs& b, int* cell_of_id, cudaStream_t s);
 void launch_min_dist(const Geom& g, const DevBufs& b, double rcut, unsigned long long* out,
                      cudaStream_t s);

@@ -24,16 +24,17 @@ __device__ __forceinline__ NbRange nb_range(int R, int cells) {
 }
 
 template <bool GR>
-__global__ void k_pairs(Geom g, const double* __restrict__ px, const double* __restrict__ py,
-                        const int* __restrict__ cnt, double rcut, double dr, int nbins,
-                        unsigned long long* __restrict__ out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t total = (int64_t)g.ncell * g.cap_mem;
-  if (i >= total) return;
-  const int c = (int)(i / g.cap_mem);
-  const int k = (int)(i - (int64_t)c * g.cap_mem);
-  if (k >= min(cnt[c], g.cap_mem)) return;
-  const int cx = c % g.cells_x, cy = c / g.cells_x;
+__global__ void k_pairs(Geom g, int cap, const double* __restrict__ px,
+                        const double* __restrict__ py, const int* __restrict__ cnt, double rcut,
+                        double dr, int nbins, unsigned long long* __restrict__ out) {
+  const int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (li >= (int64_t)g.ncell * cap) return;
+  const int lcell = (int)(li / cap);
+  const int k = (int)(li - (int64_t)lcell * cap);
+  const int c = g.cell_off + lcell;
+  const int64_t i = (int64_t)c * cap + k;
+  if (k >= min(cnt[c], cap)) return;
+  const int cx = lcell % g.cells_x, cy = lcell / g.cells_x;
   const double xi = px[i], yi = py[i];
   const double L = g.L;
   const int Rx = (int)ceil(rcut * g.inv_w * (1.0 + 1e-9));
@@ -48,9 +49,9 @@ __global__ void k_pairs(Geom g, const double* __restrict__ px, const double* __r
     const int qy = absy ? oy : ((cy + ry.first + oy) % g.cells_y + g.cells_y) % g.cells_y;
     for (int ox = 0; ox < rx.n; ++ox) {
       const int qx = absx ? ox : ((cx + rx.first + ox) % g.cells_x + g.cells_x) % g.cells_x;
-      const int q = qy * g.cells_x + qx;
-      const int nq = min(cnt[q], g.cap_mem);
-      const int64_t b0 = (int64_t)q * g.cap_mem;
+      const int q = g.cell_off + qy * g.cells_x + qx;
+      const int nq = min(cnt[q], cap);
+      const int64_t b0 = (int64_t)q * cap;
       for (int kk = 0; kk < nq; ++kk) {
         const int64_t j = b0 + kk;
         if (j == i) continue;
@@ -84,18 +85,18 @@ __global__ void k_pairs(Geom g, const double* __restrict__ px, const double* __r
 void launch_min_dist(const Geom& g, const DevBufs& b, double rcut, unsigned long long* out,
                      cudaStream_t s) {
   const int bs = 128;
-  const int64_t total = (int64_t)g.ncell * g.cap_mem;
+  const int64_t total = (int64_t)g.ncell * b.cap;
   k_pairs<false><<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(
-      g, b.px[b.cur], b.py[b.cur], b.count[b.cur], rcut, 0.0, 0, out);
+      g, b.cap, b.px[b.cur], b.py[b.cur], b.count[b.cur], rcut, 0.0, 0, out);
 }
 
 void launch_gr(const Geom& g, const DevBufs& b, double dr, int nbins, unsigned long long* counts,
                cudaStream_t s) {
   const int bs = 128;
-  const int64_t total = (int64_t)g.ncell * g.cap_mem;
+  const int64_t total = (int64_t)g.ncell * b.cap;
   const double rcut = g.sigma + dr * nbins;
   k_pairs<true><<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(
-      g, b.px[b.cur], b.py[b.cur], b.count[b.cur], rcut, dr, nbins, counts);
+      g, b.cap, b.px[b.cur], b.py[b.cur], b.count[b.cur], rcut, dr, nbins, counts);
 }
 
 }  // namespace ecmc

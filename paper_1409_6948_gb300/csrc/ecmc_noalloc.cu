@@ -92,6 +92,7 @@ extern "C" int ecmc_sweep_noalloc(double* xy, int64_t N, double L, double sigma,
   g.replica = replica;
   g.dir_mode = 0;
   g.precision = 1;
+  g.nact = (cells_x / 2) * (cells_y / 2);
   g.cap_mem = (int)std::floor(packing(g.w, g.h, sigma)) + 2;
   g.cap_obj = (int)std::floor(packing(g.w + 2 * sigma, g.h + 2 * sigma, sigma)) + 2;
   if (g.cap_mem > g.cap_obj) g.cap_mem = g.cap_obj;
@@ -116,7 +117,7 @@ extern "C" int ecmc_sweep_noalloc(double* xy, int64_t N, double L, double sigma,
     g.inv_bin_w = (float)(1.0 / bw);
   }
   int tpc = 32;
-  for (int t = 1; t <= 32; t *= 2) {
+  for (int t = 4; t <= 32; t *= 2) {
     if (phase_smem_bytes(make_layout(32 / t, g.nbin, g.cap_mem, g.cap_obj), 1) <= 52 * 1024) {
       tpc = t;
       break;
@@ -143,6 +144,10 @@ extern "C" int ecmc_sweep_noalloc(double* xy, int64_t N, double L, double sigma,
   const size_t o_tot = carve(off, sizeof(RunTotals));
   const size_t o_err = carve(off, sizeof(int));
   const size_t o_rec = carve(off, (size_t)n_groups * lay.bytes);
+  const size_t o_geo = carve(off, sizeof(Geom));
+  const size_t o_crep = carve(off, sizeof(int) * (size_t)g.ncell);
+  const size_t o_arep = carve(off, sizeof(int) * (size_t)n_active);
+  const size_t o_noff = carve(off, sizeof(int64_t) * 2);
   // larger systems than the static array can serve are rejected up front
   if (off > (size_t)ECMC_NOALLOC_SCRATCH_BYTES) return ECMC_ERR_CAPACITY;
 
@@ -164,7 +169,18 @@ extern "C" int ecmc_sweep_noalloc(double* xy, int64_t N, double L, double sigma,
   b.history = nullptr;
   b.history_cap = 0;
   b.chain_recs = nullptr;
+  b.rec_stride = n_m;
   b.cur = 0;
+  b.rg = reinterpret_cast<Geom*>(base + o_geo);
+  b.cell_rep = reinterpret_cast<int*>(base + o_crep);
+  b.act_rep = reinterpret_cast<int*>(base + o_arep);
+  b.n_off = reinterpret_cast<int64_t*>(base + o_noff);
+  b.R = 1;
+  b.C_total = g.ncell;
+  b.A_total = n_active;
+  b.cap = g.cap_mem;
+  b.N_total = N;
+  const int64_t n_off_host[2] = {0, N};
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (configure_frame_build(lay) || configure_phase(lay, tpc, 1)) return ECMC_ERR_CUDA;
@@ -177,26 +193,31 @@ extern "C" int ecmc_sweep_noalloc(double* xy, int64_t N, double L, double sigma,
       cudaMemsetAsync(b.count[1], 0, sizeof(int) * (size_t)g.ncell, s) != cudaSuccess ||
       cudaMemsetAsync(b.totals, 0, sizeof(RunTotals), s) != cudaSuccess ||
       cudaMemsetAsync(b.err, 0, sizeof(int), s) != cudaSuccess ||
+      cudaMemsetAsync((void*)b.cell_rep, 0, sizeof(int) * (size_t)g.ncell, s) != cudaSuccess ||
+      cudaMemsetAsync((void*)b.act_rep, 0, sizeof(int) * (size_t)n_active, s) != cudaSuccess ||
+      cudaMemcpyAsync((void*)b.rg, &g, sizeof(g), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync((void*)b.n_off, n_off_host, sizeof(n_off_host), cudaMemcpyHostToDevice,
+                      s) != cudaSuccess ||
       cudaMemcpyAsync(b.state, &st, sizeof(st), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return ECMC_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return ECMC_ERR_CUDA;
 
   // caller positions -> buckets, n sweeps, buckets -> caller positions
-  launch_load_flat(g, b, xy, s);
-  launch_sweep_begin(g, b, s);
-  launch_bin(g, b, -1, b.cur, s);
+  launch_load_flat(b, xy, s);
+  launch_sweep_begin(b, s);
+  launch_bin(b, -1, b.cur, s);
   for (int64_t i = 0; i < n_sweeps; ++i) {
     const int src = b.cur, dst = 1 - b.cur;
-    launch_sweep_begin(g, b, s);
-    launch_bin(g, b, src, dst, s);
+    launch_sweep_begin(b, s);
+    launch_bin(b, src, dst, s);
     b.cur = dst;
     for (int ci = 0; ci < 4; ++ci) {
-      launch_frame_build(g, b, lay, ci, s);
-      if (launch_phase(g, b, lay, ci, tpc, 1, 0, s)) return ECMC_ERR_CUDA;
+      launch_frame_build(b, lay, ci, s);
+      if (launch_phase(b, lay, ci, tpc, 1, 0, 1, s)) return ECMC_ERR_CUDA;
     }
-    launch_sweep_end(g, b, s);
+    launch_sweep_end(b, s);
   }
-  launch_gather(g, b, xy, s);
+  launch_gather(b, xy, s);
   if (cudaGetLastError() != cudaSuccess) return ECMC_ERR_CUDA;
   int err = 0;
   if (cudaMemcpyAsync(&err, b.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -68,12 +68,14 @@ __device__ __forceinline__ bool better(double s, int key, double bs, int bkey) {
 }
 
 template <int TPC, bool SCREEN>
-__global__ void __launch_bounds__(256) k_phase(Geom g, const SweepState* __restrict__ st,
-                                               int colour_index,
+__global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
+                                               const SweepState* __restrict__ sts,
+                                               const int* __restrict__ act_rep, int colour_index,
                                                const unsigned char* __restrict__ records,
                                                RecLayout lay, int n_active, double* __restrict__ px,
                                                double* __restrict__ py, CellStats* __restrict__ cs,
-                                               ChainRec* __restrict__ recs, int* err) {
+                                               ChainRec* __restrict__ recs, int rec_stride,
+                                               int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int CPW = 32 / TPC;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -110,13 +112,18 @@ __global__ void __launch_bounds__(256) k_phase(Geom g, const SweepState* __restr
   const int* hdr = (const int*)(base + lay.off_hdr);
 
   const int gi = lane / TPC, sub = lane - gi * TPC;
-  const int a = G * CPW + gi;
+  const int a = G * CPW + gi;  // global active cell of this lane group
   const bool valid = a < n_active;
+  const int rep = valid ? act_rep[a] : act_rep[n_active - 1];
+  const Geom& g = rg[rep];
+  const SweepState* st = sts + rep;
   const int colour = st->perm[colour_index];
   const int hx = g.cells_x >> 1;
-  const int cx = 2 * (a % hx) + (colour & 1);
-  const int cy = 2 * (a / hx) + (colour >> 1);
-  const int c = cy * g.cells_x + cx;
+  const int la = a - g.act_off;
+  const int cx = 2 * (la % hx) + (colour & 1);
+  const int cy = 2 * (la / hx) + (colour >> 1);
+  const int lc = cy * g.cells_x + cx;  // cell within the replica (Philox counter word)
+  const int c = g.cell_off + lc;       // global cell
   const int axis = st->axis;
   const int64_t t = st->t;
   const double E = axis == 0 ? g.w : g.h;  // cell extent along the chain axis
@@ -146,7 +153,7 @@ __global__ void __launch_bounds__(256) k_phase(Geom g, const SweepState* __restr
         done = true;
       } else {
         // start disk drawn with replacement among the members, sign of d
-        const U64x4 v = philox((uint64_t)t, kPurposeChain, (uint64_t)c, (uint64_t)k, g.seed,
+        const U64x4 v = philox((uint64_t)t, kPurposeChain, (uint64_t)lc, (uint64_t)k, g.seed,
                                g.replica);
         const int idx = (int)below_n(v.v[0], (uint64_t)nmem);
         m = f.mrank[idx * CPW + gi];
@@ -378,7 +385,7 @@ __global__ void __launch_bounds__(256) k_phase(Geom g, const SweepState* __restr
         rc.end_id = f.key[m * CPW + gi] >> 4;
         rc.events = ch_events;
         rc.walls = ch_walls;
-        recs[(int64_t)c * g.n_m + (k - 1)] = rc;
+        recs[(int64_t)c * rec_stride + (k - 1)] = rc;
       }
       active = false;
     }
@@ -418,16 +425,16 @@ size_t phase_smem_bytes(const RecLayout& lay, int warps_per_block) {
 }
 
 template <int TPC, bool SCREEN>
-static int launch_t(const Geom& g, const DevBufs& b, const RecLayout& lay, int colour_index,
-                    int warps, int records_on, cudaStream_t s) {
-  const int n_active = (g.cells_x / 2) * (g.cells_y / 2);
+static int launch_t(const DevBufs& b, const RecLayout& lay, int colour_index, int warps,
+                    int records_on, cudaStream_t s) {
+  const int n_active = b.A_total;
   const int cpw = 32 / TPC;
   const int n_groups = (n_active + cpw - 1) / cpw;
   const int blocks = (n_groups + warps - 1) / warps;
   const size_t sm = phase_smem_bytes(lay, warps);
   k_phase<TPC, SCREEN><<<blocks, 32 * warps, sm, s>>>(
-      g, b.state, colour_index, b.records, lay, n_active, b.px[b.cur], b.py[b.cur], b.cell_stats,
-      records_on ? b.chain_recs : nullptr, b.err);
+      b.rg, b.state, b.act_rep, colour_index, b.records, lay, n_active, b.px[b.cur], b.py[b.cur],
+      b.cell_stats, records_on ? b.chain_recs : nullptr, b.rec_stride, b.err);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -478,13 +485,13 @@ int configure_phase(const RecLayout& lay, int tpc, int warps) {
   }
 }
 
-int launch_phase(const Geom& g, const DevBufs& b, const RecLayout& lay, int colour_index, int tpc,
-                 int warps, int records_on, cudaStream_t s) {
-  const bool scr = g.precision == 1;
-#define ECMC_CASE(T)                                                                    \
-  case T:                                                                               \
-    return scr ? launch_t<T, true>(g, b, lay, colour_index, warps, records_on, s)      \
-               : launch_t<T, false>(g, b, lay, colour_index, warps, records_on, s);
+int launch_phase(const DevBufs& b, const RecLayout& lay, int colour_index, int tpc, int warps,
+                 int records_on, int precision, cudaStream_t s) {
+  const bool scr = precision == 1;
+#define ECMC_CASE(T)                                                           \
+  case T:                                                                      \
+    return scr ? launch_t<T, true>(b, lay, colour_index, warps, records_on, s) \
+               : launch_t<T, false>(b, lay, colour_index, warps, records_on, s);
   switch (tpc) {
     ECMC_CASE(1)
     ECMC_CASE(2)

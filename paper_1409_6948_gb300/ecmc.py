@@ -56,6 +56,15 @@ class Timing(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ReplicaDesc(C.Structure):
+    _fields_ = [("N", C.c_int64), ("L", C.c_double), ("sigma", C.c_double),
+                ("cells_x", C.c_int), ("cells_y", C.c_int), ("ell", C.c_double),
+                ("n_m", C.c_int), ("seed", C.c_uint64), ("replica", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 CHAIN_REC = np.dtype([("start_id", np.int64), ("end_id", np.int64), ("events", np.int64),
                       ("walls", np.int64)])
 
@@ -64,6 +73,12 @@ _H = C.c_void_p
 _SIGS = {
     "ecmc_create": (C.c_int, [C.POINTER(_H), C.c_int64, C.c_double, C.c_double, C.c_int, C.c_int,
                               C.c_double, C.c_uint64]),
+    "ecmc_create_batch": (C.c_int, [C.POINTER(_H), C.POINTER(ReplicaDesc), C.c_int]),
+    "ecmc_num_replicas": (C.c_int, [_H, C.POINTER(C.c_int)]),
+    "ecmc_replica_desc": (C.c_int, [_H, C.c_int, C.POINTER(ReplicaDesc)]),
+    "ecmc_replica_pressure": (C.c_int, [_H, C.c_int, C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double)]),
+    "ecmc_replica_counters": (C.c_int, [_H, C.c_int, C.POINTER(Counters)]),
     "ecmc_destroy": (C.c_int, [_H]),
     "ecmc_set_param": (C.c_int, [_H, C.c_int, C.c_double]),
     "ecmc_get_param": (C.c_int, [_H, C.c_int, C.POINTER(C.c_double)]),
@@ -152,6 +167,45 @@ class Ecmc:
         self._h = h
         self.N, self.L, self.sigma = int(N), float(L), float(sigma)
         self.cells_x, self.cells_y = int(cells_x), int(cells_y)
+        self.R = 1
+
+    @classmethod
+    def batch(cls, descs):
+        """A handle with several independent replicas; descs are dicts with the
+        fields of ecmc_replica_desc_t (n_m = 0 picks eq. nm)."""
+        lib = load()
+        arr = (ReplicaDesc * len(descs))()
+        for i, d in enumerate(descs):
+            arr[i] = ReplicaDesc(int(d["N"]), float(d["L"]), float(d.get("sigma", 1.0)),
+                                 int(d["cells_x"]), int(d.get("cells_y", d["cells_x"])),
+                                 float(d["ell"]), int(d.get("n_m", 0)), int(d["seed"]),
+                                 int(d.get("replica", 0)))
+        h = _H()
+        _check(lib.ecmc_create_batch(C.byref(h), arr, len(descs)), "ecmc_create_batch")
+        self = cls.__new__(cls)
+        self._h = h
+        self.R = len(descs)
+        self.N = sum(int(d["N"]) for d in descs)
+        self.L, self.sigma = float(descs[0]["L"]), float(descs[0].get("sigma", 1.0))
+        self.cells_x = int(descs[0]["cells_x"])
+        self.cells_y = int(descs[0].get("cells_y", descs[0]["cells_x"]))
+        return self
+
+    def replica_desc(self, r):
+        d = ReplicaDesc()
+        _check(load().ecmc_replica_desc(self._h, int(r), C.byref(d)), "ecmc_replica_desc")
+        return d.as_dict()
+
+    def replica_pressure(self, r):
+        p, se = C.c_double(), C.c_double()
+        _check(load().ecmc_replica_pressure(self._h, int(r), C.byref(p), C.byref(se)),
+               "ecmc_replica_pressure")
+        return p.value, se.value
+
+    def replica_counters(self, r):
+        c = Counters()
+        _check(load().ecmc_replica_counters(self._h, int(r), C.byref(c)), "ecmc_replica_counters")
+        return c
 
     def close(self):
         if getattr(self, "_h", None):
