@@ -177,6 +177,36 @@ ECMC_API int ecmc_replica_desc(ecmc_t h, int r, ecmc_replica_desc_t* out);
 ECMC_API int ecmc_replica_pressure(ecmc_t h, int r, double* betaP_sigma2, double* stderr_out);
 ECMC_API int ecmc_replica_counters(ecmc_t h, int r, ecmc_counters_t* out);
 
+/* The paper's strategy for the degree of parallelisation (Sec. 4, final
+ * paragraph), for a system of N disks of diameter sigma in an L x L box:
+ *   1) n, the number of 2x2 blocks (4n cells), is the largest with
+ *      N / (eta n) > 100, so that the chain displacement of step 2 stays
+ *      above 10 lambda0; cells per side = 2 floor(sqrt(n)), at least 2, and
+ *      reduced until the cell side exceeds min_cell_side (>= sigma);
+ *   2) ell = lambda0 (N / (eta n))^(1/2), the second form of eq. (criterion);
+ *   3) n_m from eq. (nm),
+ * with lambda0 = sigma (eta_hcp - eta) / (2 eta_hcp) (Sec. 4).  Fills the
+ * geometry fields of *out (seed and replica are left as given).
+ * ECMC_ERR_ARG if the system is too small for 2x2 cells of side > sigma. */
+ECMC_API int ecmc_suggest_parameters(int64_t N, double L, double sigma, double min_cell_side,
+                                     ecmc_replica_desc_t* out);
+
+/* One launch shape of the chain kernel and its measured time per sweep. */
+typedef struct {
+  int lanes_per_cell;
+  int warps_per_block;
+  double ms_per_sweep;
+} ecmc_tune_result_t;
+
+/* Time trial_sweeps sweeps (after one warm-up sweep) for every launch shape
+ * that fits (lanes per cell 1..32, warps per block 1, 2, 4), keep the
+ * fastest, and put the handle back exactly where it was (positions, sweep
+ * counter, statistics): every shape gives bit-identical trajectories, so the
+ * tuning does not change the simulation.  best receives the chosen shape;
+ * all (may be NULL) up to max_all measured shapes, *n_all their number. */
+ECMC_API int ecmc_autotune(ecmc_t h, int trial_sweeps, ecmc_tune_result_t* best,
+                           ecmc_tune_result_t* all, int max_all, int* n_all);
+
 /* Release the handle and all its device memory.  NULL is accepted. */
 ECMC_API int ecmc_destroy(ecmc_t h);
 

@@ -1049,6 +1049,129 @@ int ecmc_chain_records(ecmc_t h, ecmc_chain_rec_t* out, int64_t n) {
   return check_device_error(h);
 }
 
+int ecmc_suggest_parameters(int64_t N, double L, double sigma, double min_cell_side,
+                            ecmc_replica_desc_t* out) {
+  if (!out || N < 1 || !(L > 0.0) || !(sigma > 0.0)) return fail(ECMC_ERR_ARG, "bad arguments");
+  const double pi = 3.14159265358979323846;
+  const double eta = (double)N * pi * sigma * sigma / (4.0 * L * L);  // eq. (1)
+  const double eta_hcp = pi / (2.0 * std::sqrt(3.0));
+  const double lambda0 = sigma * (eta_hcp - eta) / (2.0 * eta_hcp);   // Sec. 4
+  if (!(lambda0 > 0.0)) return fail(ECMC_ERR_ARG, "packing fraction above close packing");
+  const double side_min = min_cell_side > sigma ? min_cell_side : sigma;
+  // step 1: largest n with N / (eta n) > 100
+  double n_max = (double)N / (100.0 * eta);
+  long long half = (long long)std::floor(std::sqrt(n_max > 1.0 ? n_max : 1.0));
+  if ((double)half * (double)half * 100.0 * eta >= (double)N && half > 1) --half;
+  if (half < 1) half = 1;
+  int cells = (int)(2 * half);
+  while (cells > 2 && !(L / cells > side_min)) cells -= 2;
+  if (!(L / cells > side_min)) return fail(ECMC_ERR_ARG, "box too small for 2x2 cells");
+  const double n = (double)cells * (double)cells / 4.0;
+  // step 2: eq. (criterion), ell = lambda0 (N / (eta n))^(1/2)
+  const double ell = lambda0 * std::sqrt((double)N / (eta * n));
+  // step 3: eq. (nm)
+  const double nm = (double)N / (4.0 * n) * lambda0 / ell;
+  const double nmr = std::floor(nm + 0.5);
+  out->N = N;
+  out->L = L;
+  out->sigma = sigma;
+  out->cells_x = cells;
+  out->cells_y = cells;
+  out->ell = ell;
+  out->n_m = nmr < 1.0 ? 1 : (int)nmr;
+  return ECMC_OK;
+}
+
+int ecmc_autotune(ecmc_t h, int trial_sweeps, ecmc_tune_result_t* best, ecmc_tune_result_t* all,
+                  int max_all, int* n_all) {
+  if (!h || !best || trial_sweeps < 1) return fail(ECMC_ERR_ARG, "bad arguments");
+  if (!h->valid_state) return fail(ECMC_ERR_STATE, "state invalid after an earlier error");
+  CK(cudaStreamSynchronize(h->stream));
+  // save the state
+  const size_t pos_bytes = sizeof(double) * 2 * (size_t)h->b.N_total;
+  double* saved = nullptr;
+  RunTotals* saved_tot = nullptr;
+  CK(cudaMalloc(&saved, pos_bytes));
+  if (cudaMalloc(&saved_tot, sizeof(RunTotals) * h->b.R) != cudaSuccess) {
+    cudaFree(saved);
+    return fail(ECMC_ERR_OOM, "autotune scratch");
+  }
+  launch_gather(h->b, saved, h->stream);
+  cudaMemcpyAsync(saved_tot, h->b.totals, sizeof(RunTotals) * h->b.R, cudaMemcpyDeviceToDevice,
+                  h->stream);
+  const int64_t t_saved = h->t_host, hist_saved = h->hist_len_host;
+  const int tpc0 = h->tpc_param, warps0 = h->warps_param, timing0 = h->timing;
+  h->timing = 0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  std::vector<ecmc_tune_result_t> res;
+  int rc = ECMC_OK;
+  const int tpcs[6] = {1, 2, 4, 8, 16, 32};
+  const int wps[3] = {1, 2, 4};
+  for (int ti = 0; ti < 6 && rc == ECMC_OK; ++ti)
+    for (int wi = 0; wi < 3 && rc == ECMC_OK; ++wi) {
+      h->tpc_param = tpcs[ti];
+      h->warps_param = wps[wi];
+      drop_graphs(h);
+      if (compute_layout(h) != ECMC_OK || h->warps != wps[wi]) continue;  // does not fit
+      rc = ecmc_sweep(h, 1);
+      if (rc) break;
+      cudaEventRecord(e0, h->stream);
+      rc = ecmc_sweep(h, trial_sweeps);
+      if (rc) break;
+      cudaEventRecord(e1, h->stream);
+      rc = check_device_error(h);
+      if (rc) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ecmc_tune_result_t r;
+      r.lanes_per_cell = h->tpc;
+      r.warps_per_block = h->warps;
+      r.ms_per_sweep = ms / trial_sweeps;
+      res.push_back(r);
+      // back to the saved state before the next shape
+      h->hist_len_host = hist_saved;
+      rc = load_positions_dev(h, saved, t_saved);
+      cudaMemcpyAsync(h->b.totals, saved_tot, sizeof(RunTotals) * h->b.R,
+                      cudaMemcpyDeviceToDevice, h->stream);
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->timing = timing0;
+  int bi = -1;
+  for (size_t i = 0; i < res.size(); ++i)
+    if (bi < 0 || res[i].ms_per_sweep < res[bi].ms_per_sweep) bi = (int)i;
+  if (rc == ECMC_OK && bi < 0) rc = fail(ECMC_ERR_UNSUPPORTED, "no launch shape fits");
+  if (rc == ECMC_OK) {
+    *best = res[bi];
+    h->tpc_param = res[bi].lanes_per_cell;
+    h->warps_param = res[bi].warps_per_block;
+  } else {
+    h->tpc_param = tpc0;
+    h->warps_param = warps0;
+  }
+  drop_graphs(h);
+  int rc2 = compute_layout(h);
+  h->hist_len_host = hist_saved;
+  int rc3 = load_positions_dev(h, saved, t_saved);
+  cudaMemcpyAsync(h->b.totals, saved_tot, sizeof(RunTotals) * h->b.R, cudaMemcpyDeviceToDevice,
+                  h->stream);
+  cudaStreamSynchronize(h->stream);
+  cudaFree(saved);
+  cudaFree(saved_tot);
+  if (all && n_all) {
+    const int n = (int)res.size() < max_all ? (int)res.size() : max_all;
+    for (int i = 0; i < n; ++i) all[i] = res[i];
+    *n_all = n;
+  } else if (n_all) {
+    *n_all = (int)res.size();
+  }
+  if (rc) return rc;
+  if (rc2) return rc2;
+  return rc3;
+}
+
 int ecmc_device_peaks(double* smem_gbs, double* fp64_gflops) {
   if (!smem_gbs || !fp64_gflops) return fail(ECMC_ERR_ARG, "NULL argument");
   if (probe_peaks(smem_gbs, fp64_gflops))

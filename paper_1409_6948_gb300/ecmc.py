@@ -56,6 +56,14 @@ class Timing(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("lanes_per_cell", C.c_int), ("warps_per_block", C.c_int),
+                ("ms_per_sweep", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class ReplicaDesc(C.Structure):
     _fields_ = [("N", C.c_int64), ("L", C.c_double), ("sigma", C.c_double),
                 ("cells_x", C.c_int), ("cells_y", C.c_int), ("ell", C.c_double),
@@ -79,6 +87,10 @@ _SIGS = {
     "ecmc_replica_pressure": (C.c_int, [_H, C.c_int, C.POINTER(C.c_double),
                                         C.POINTER(C.c_double)]),
     "ecmc_replica_counters": (C.c_int, [_H, C.c_int, C.POINTER(Counters)]),
+    "ecmc_suggest_parameters": (C.c_int, [C.c_int64, C.c_double, C.c_double, C.c_double,
+                                          C.POINTER(ReplicaDesc)]),
+    "ecmc_autotune": (C.c_int, [_H, C.c_int, C.POINTER(TuneResult), C.POINTER(TuneResult),
+                                C.c_int, C.POINTER(C.c_int)]),
     "ecmc_destroy": (C.c_int, [_H]),
     "ecmc_set_param": (C.c_int, [_H, C.c_int, C.c_double]),
     "ecmc_get_param": (C.c_int, [_H, C.c_int, C.POINTER(C.c_double)]),
@@ -190,6 +202,15 @@ class Ecmc:
         self.cells_x = int(descs[0]["cells_x"])
         self.cells_y = int(descs[0].get("cells_y", descs[0]["cells_x"]))
         return self
+
+    def autotune(self, trial_sweeps=3):
+        """Measure every launch shape, keep the fastest (state unchanged)."""
+        best = TuneResult()
+        arr = (TuneResult * 32)()
+        n = C.c_int()
+        _check(load().ecmc_autotune(self._h, int(trial_sweeps), C.byref(best), arr, 32,
+                                    C.byref(n)), "ecmc_autotune")
+        return best.as_dict(), [arr[i].as_dict() for i in range(n.value)]
 
     def replica_desc(self, r):
         d = ReplicaDesc()
@@ -340,6 +361,14 @@ def sweep_noalloc(xy, N, L, sigma, cells_x, cells_y, ell, n_m, seed, replica, t0
                                      C.c_uint64(int(seed)), C.c_uint64(int(replica)), int(t0),
                                      int(n_sweeps), C.c_void_p(stream or 0)),
            "ecmc_sweep_noalloc")
+
+
+def suggest_parameters(N, L, sigma=1.0, min_cell_side=0.0):
+    """The paper's three-step choice of cells, ell and n_m (Sec. 4)."""
+    d = ReplicaDesc()
+    _check(load().ecmc_suggest_parameters(int(N), float(L), float(sigma), float(min_cell_side),
+                                          C.byref(d)), "ecmc_suggest_parameters")
+    return d.as_dict()
 
 
 def device_peaks():

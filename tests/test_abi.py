@@ -70,3 +70,23 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.ecmc_destroy(None) == 0
     d = C.c_double()
     assert lib.ecmc_pressure(None, C.byref(d), None) == E.ERR_ARG
+
+
+@pytest.mark.parametrize("N,eta", [(1048576, 0.72), (262144, 0.70), (4096, 0.60), (65536, 0.708),
+                                   (4194304, 0.716)])
+def test_suggested_parameters_follow_the_papers_strategy(N, eta):
+    # Sec. 4: N / (eta n) > 100 for the largest such n; ell from eq. criterion;
+    # n_m from eq. nm (host arithmetic only, no device needed)
+    import math
+    import ecmc_workloads as W
+    L = W.box_side(N, eta)
+    d = E.suggest_parameters(N, L)
+    n = d["cells_x"] ** 2 / 4.0
+    assert d["cells_x"] % 2 == 0 and d["cells_x"] == d["cells_y"]
+    assert N / (eta * n) > 100.0
+    n_next = (d["cells_x"] + 2) ** 2 / 4.0
+    assert N / (eta * n_next) <= 100.0
+    lam = (W.ETA_HCP - eta) / (2 * W.ETA_HCP)
+    assert d["ell"] == pytest.approx(lam * math.sqrt(N / (eta * n)), rel=1e-12)
+    assert d["ell"] > 10 * lam
+    assert d["n_m"] == max(1, int(math.floor(N / (4 * n) * lam / d["ell"] + 0.5)))

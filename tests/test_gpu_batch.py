@@ -125,3 +125,22 @@ def test_set_positions_for_the_whole_batch():
     g.sweep(2)
     assert np.array_equal(g.positions(), end)
     g.close()
+
+
+def test_autotune_keeps_the_trajectory():
+    N, eta = 4096, 0.72
+    L = W.box_side(N, eta)
+    a = P.Ecmc(N, L, 1.0, 16, 16, 2.0, 3)
+    b = P.Ecmc(N, L, 1.0, 16, 16, 2.0, 3)
+    a.sweep(2)
+    b.sweep(2)
+    best, shapes = a.autotune(trial_sweeps=2)
+    assert len(shapes) >= 3 and best["ms_per_sweep"] == min(s["ms_per_sweep"] for s in shapes)
+    assert a.get_param(E.PARAM_LANES_PER_CELL) == best["lanes_per_cell"]
+    assert a.sweep_index() == 2 and np.array_equal(a.positions(), b.positions())
+    assert a.counters().sweeps == b.counters().sweeps
+    a.sweep(3)
+    b.sweep(3)
+    assert np.array_equal(a.positions(), b.positions())
+    a.close()
+    b.close()
