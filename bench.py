@@ -43,7 +43,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["small", "medium", "large", "huge"])
+    ap.add_argument("--workload", default="large",
+                    choices=["small", "medium", "large", "huge", "batch", "eos"])
+    ap.add_argument("--grid", action="store_true",
+                    help="parallelisation grid at N = 1M (cells x ell), one JSON line")
+    ap.add_argument("--paper-params", action="store_true",
+                    help="cells, ell, n_m from the paper's strategy (Sec. 4)")
+    ap.add_argument("--autotune", action="store_true", help="tune the launch shape first")
     ap.add_argument("--cells", type=int, default=0, help="cells per side (0 = workload default)")
     ap.add_argument("--ell", type=float, default=0.0, help="chain displacement (0 = default)")
     ap.add_argument("--nm", type=int, default=0, help="chains per cell (0 = eq. nm)")
@@ -57,10 +63,25 @@ def parse():
 
 
 def workload(args):
-    w = {"small": W.SMALL, "medium": W.MEDIUM, "large": W.LARGE, "huge": W.HUGE}[args.workload]
+    w = {"small": W.SMALL, "medium": W.MEDIUM, "large": W.LARGE, "huge": W.HUGE,
+         "batch": W.LARGE, "eos": W.LARGE}[args.workload]
     cells = args.cells or w.cells
     ell = args.ell or w.ell
     return w, cells, ell
+
+
+def batch_descs(args, rank):
+    """Replica batch descriptors: the paper's strategy (Sec. 4) picks cells,
+    ell and n_m for every replica; every rank runs its own replica keys."""
+    from paper_1409_6948_gb300 import ecmc as E
+
+    reps = W.replica_batch() if args.workload == "batch" else W.eos_batch()
+    out = []
+    for d in reps:
+        s = E.suggest_parameters(d["N"], d["L"], 1.0, 2.0)
+        s.update(seed=d["seed"], replica=d["replica"] + 100000 * rank, eta=d["eta"])
+        out.append(s)
+    return out
 
 
 def dist_env():
@@ -146,10 +167,89 @@ def cpu_baseline(w, cells, ell, nm, seconds, max_sweeps=1000):
             "sweeps_per_s": n / dt}
 
 
+def cpu_baseline_batch(descs, seconds):
+    """The oracle on the batch's replicas in turn (one sweep each, cycling)
+    until `seconds` have passed, single-threaded."""
+    import oracle
+
+    states = []
+    for d in descs:
+        x, y = W.square_lattice(d["N"], d["L"])
+        p = oracle.make_params(d["N"], d["L"], 1.0, d["cells_x"], d["cells_y"], d["ell"],
+                               d["n_m"], d["seed"], d["replica"])
+        states.append([p, x, y, 0])
+    st = oracle.Stats()
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < seconds:
+        s = states[n % len(states)]
+        oracle.sweeps(s[0], s[1], s[2], s[3], 1, stats=st)
+        s[3] += 1
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": st.events / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d replica sweeps (replicas in turn, from their lattice starts, %.1f s)"
+                      % (n, dt)}
+
+
+def run_grid(args):
+    """Parallelisation grid at N = 1024^2, eta = 0.72: events/s against the
+    degree of parallelisation (cells per side) and the chain displacement,
+    with the measured mean free path and the paper's criterion (eq. criterion)
+    ell* = L lambda0 / (sqrt(n) sigma) for each grid (n = blocks = cells/4)."""
+    import torch
+
+    import paper_1409_6948_gb300 as P
+    from paper_1409_6948_gb300 import ecmc as E
+
+    torch.cuda.set_device(0)
+    w = W.LARGE
+    L = w.L
+    lam0 = (W.ETA_HCP - w.eta) / (2 * W.ETA_HCP)
+    pts = []
+    for cells in W.LARGE_CELL_GRID:
+        for ell in W.LARGE_ELL_GRID:
+            pt = {"cells": cells, "ell": ell}
+            try:
+                g = P.Ecmc(w.N, L, 1.0, cells, cells, ell, w.seed)
+            except E.EcmcError as ex:
+                pt["unsupported"] = str(ex)
+                pts.append(pt)
+                continue
+            g.sweep(args.warmup)
+            g.synchronize()
+            g.reset_stats()
+            s = torch.cuda.Stream()
+            g.set_stream(s)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            g.sweep(args.steps)
+            b.record(s)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            c = g.counters()
+            n_blocks = cells * cells / 4.0
+            pt.update({"n_m": int(g.get_param(E.PARAM_N_CHAINS)),
+                       "lanes_per_cell": int(g.get_param(E.PARAM_LANES_PER_CELL)),
+                       "events_per_s": c.events / (ms * 1e-3), "sweeps_per_s": c.sweeps / (ms * 1e-3),
+                       "events_per_sweep": c.events / c.sweeps,
+                       "wall_fraction": c.wall_hits / max(c.events + c.wall_hits, 1),
+                       "free_path": c.sum_disp / max(c.events + c.wall_hits + c.chains, 1),
+                       "criterion_ell": L * lam0 / math.sqrt(n_blocks),
+                       "N_over_eta_n": w.N / (w.eta * n_blocks)})
+            pts.append(pt)
+            g.close()
+    print(json.dumps({"mode": "grid", "workload": w.name, "steps": args.steps,
+                      "warmup": args.warmup, "lambda0_eq": lam0, "points": pts}))
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    if args.workload in ("batch", "eos"):
+        return run_reference_batch(args)
     w, cells, ell = workload(args)
     import oracle
 
@@ -200,8 +300,24 @@ def run_ours(args):
 
     w, cells, ell = workload(args)
     L = w.L
-    g = P.Ecmc(w.N, L, 1.0, cells, cells, ell, w.seed)
-    g.set_param(E.PARAM_REPLICA, rank)
+    descs = None
+    if args.workload in ("batch", "eos"):
+        descs = batch_descs(args, rank)
+        g = P.Ecmc.batch(descs)
+        n_total = sum(d["N"] for d in descs)
+        wname = ("%d replicas, N %d..%d (%d disks), eta %.3f..%.3f, paper-strategy cells/ell"
+                 % (len(descs), min(d["N"] for d in descs), max(d["N"] for d in descs), n_total,
+                    min(d["eta"] for d in descs), max(d["eta"] for d in descs)))
+    else:
+        if args.paper_params:
+            sp = E.suggest_parameters(w.N, L, 1.0, 2.0)
+            cells, ell = sp["cells_x"], sp["ell"]
+        g = P.Ecmc(w.N, L, 1.0, cells, cells, ell, w.seed)
+        g.set_param(E.PARAM_REPLICA, rank)
+        if args.paper_params and not args.nm:
+            g.set_param(E.PARAM_N_CHAINS, sp["n_m"])
+        n_total = w.N
+        wname = w.name + " cells=%dx%d ell=%g" % (cells, cells, ell)
     if args.nm:
         g.set_param(E.PARAM_N_CHAINS, args.nm)
     if args.tpc:
@@ -218,6 +334,13 @@ def run_ours(args):
     # warm-up (graphs captured here)
     g.sweep(args.warmup)
     g.synchronize()
+    tuned = None
+    if args.autotune:
+        tuned, _ = g.autotune(trial_sweeps=2)
+        tpc = int(g.get_param(E.PARAM_LANES_PER_CELL))
+        g.sweep(1)
+    saved_xy = g.positions().copy() if descs is not None else None
+    saved_t = g.sweep_index()
 
     # timed region: per-kernel CUDA events inside the library (direct
     # launches), one event pair per step on the same stream, L2 flushed
@@ -265,11 +388,41 @@ def run_ours(args):
         ms_max, events_all, sweeps_all = ms, float(events), float(sweeps)
     value = events_all / (ms_max * 1e-3)
 
+    # batches: the same sweeps again with every candidate tested in FP64,
+    # from the same state; the two forms must give the same pressures
+    precision_cmp = None
+    if descs is not None:
+        p32 = [g.replica_pressure(r)[0] for r in range(len(descs))]
+        g.set_param(E.PARAM_PRECISION, 0)
+        g.set_positions(saved_xy, t0=saved_t)
+        g.reset_stats()
+        g.set_param(E.PARAM_TIMING, 1)
+        torch.cuda.synchronize()
+        for a, b in evs:
+            if flush is not None:
+                flush.zero_()
+            a.record(stream)
+            g.sweep(1)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms64 = sum(a.elapsed_time(b) for a, b in evs)
+        c64 = g.counters()
+        p64 = [g.replica_pressure(r)[0] for r in range(len(descs))]
+        g.set_param(E.PARAM_TIMING, 0)
+        g.set_param(E.PARAM_PRECISION, args.prec)
+        rel = max(abs(a - b) / abs(b) for a, b in zip(p32, p64))
+        precision_cmp = {"fp32_screening_events_per_s": events / (ms * 1e-3),
+                         "fp64_candidates_events_per_s": c64.events / (ms64 * 1e-3),
+                         "speedup": (events / ms) / (c64.events / ms64),
+                         "max_rel_pressure_diff": rel, "same_events": c64.events == events,
+                         "per_replica_eta_pressure": [(round(d["eta"], 4), p)
+                                                      for d, p in zip(descs, p32)]}
+
     # end to end through the public API: host (pinned) positions in, one
     # sweep, positions out, every step
     e2e = None
     if not args.skip_e2e:
-        host = torch.empty(2 * w.N, dtype=torch.float64, pin_memory=True)
+        host = torch.empty(2 * n_total, dtype=torch.float64, pin_memory=True)
         g.positions(host.numpy())
         t_idx = g.sweep_index()
         g.reset_stats()
@@ -282,8 +435,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         ce = g.counters()
-        e2e = {"value": ce.events / dt, "unit": UNIT, "h2d_bytes_per_step": 16 * w.N,
-               "d2h_bytes_per_step": 16 * w.N, "timer": "host wall clock"}
+        e2e = {"value": ce.events / dt, "unit": UNIT, "h2d_bytes_per_step": 16 * n_total,
+               "d2h_bytes_per_step": 16 * n_total, "timer": "host wall clock"}
 
     line = None
     if rank == 0:
@@ -292,14 +445,19 @@ def run_ours(args):
         smem_gbs, fp64_gflops = P.ecmc.device_peaks()
         achieved = bytes_per_launch / (phase_avg_ms * 1e-3) / 1e9
         cpu = None
-        if not args.skip_cpu:
+        if not args.skip_cpu and descs is None:
             cpu = cpu_baseline(w, cells, ell, nm, args.cpu_seconds)
+        elif not args.skip_cpu:
+            cpu = cpu_baseline_batch(descs, args.cpu_seconds)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "N": w.N, "eta": w.eta, "cells": cells, "ell": ell,
-                       "n_m": nm, "lanes_per_cell": tpc,
+            "config": {"workload": wname, "N": n_total, "eta": w.eta if descs is None else None,
+                       "cells": cells if descs is None else None,
+                       "ell": ell if descs is None else None,
+                       "n_m": nm if descs is None else None, "lanes_per_cell": tpc,
+                       "autotuned": tuned,
                        "screening": "fp32" if args.prec else "fp64",
                        "l2": "none" if args.no_flush else "flushed (256 MB write) between steps",
                        "parallelism": "replicas x%d" % world},
@@ -320,6 +478,8 @@ def run_ours(args):
             "e2e": e2e,
             "cpu_baseline": cpu,
         }
+        if precision_cmp is not None:
+            line["precision_comparison"] = precision_cmp
         print(json.dumps(line))
     g.close()
     if world > 1:
@@ -329,10 +489,51 @@ def run_ours(args):
     return 0
 
 
+def run_reference_batch(args):
+    """The oracle as the reference arm on a replica batch: each step is one
+    sweep of one replica, the replicas taken in turn."""
+    import oracle
+
+    from paper_1409_6948_gb300 import ecmc as E  # parameter choice only (host arithmetic)
+
+    descs = batch_descs(args, 0)
+    states = []
+    for d in descs:
+        x, y = W.square_lattice(d["N"], d["L"])
+        p = oracle.make_params(d["N"], d["L"], 1.0, d["cells_x"], d["cells_y"], d["ell"],
+                               d["n_m"], d["seed"], d["replica"])
+        states.append([p, x, y, 0])
+    for i in range(args.warmup):
+        s = states[i % len(states)]
+        oracle.sweeps(s[0], s[1], s[2], s[3], 1)
+        s[3] += 1
+    st = oracle.Stats()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        s = states[(args.warmup + i) % len(states)]
+        oracle.sweeps(s[0], s[1], s[2], s[3], 1, stats=st)
+        s[3] += 1
+    dt = time.perf_counter() - t0
+    value = st.events / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "replicas": len(descs)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d single-replica sweeps, replicas in turn" % args.steps},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.grid:
+        return run_grid(args)
     return run_ours(args)
 
 

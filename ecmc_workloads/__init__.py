@@ -92,3 +92,30 @@ HUGE = Workload("N=4194304 eta=0.716", 4194304, 0.716, 256, 8.0, seed=5)
 # Parallelisation grid at N = 1M, eta = 0.72: cells per side x ell.
 LARGE_CELL_GRID = [8, 16, 32, 64, 128, 256, 512]
 LARGE_ELL_GRID = [2.0, 8.0, 32.0]
+
+
+def round_to_square(n: float) -> int:
+    k = max(1, int(round(math.sqrt(n))))
+    return k * k
+
+
+def replica_batch(seed: int = 4, R: int = 96):
+    """Many independent replicas of uneven size and density: N log-uniform in
+    [4096, 262144] (u from numpy's Philox with key (seed, r)), rounded to a
+    perfect square for the lattice start; eta = 0.600 + 0.005 (r mod 29).
+    Returns a list of dicts with N, eta, L, seed, replica."""
+    out = []
+    for r in range(R):
+        u = np.random.Generator(np.random.Philox(key=[seed, r])).random()
+        N = round_to_square(4096.0 * 64.0**u)
+        eta = 0.600 + 0.005 * (r % 29)
+        out.append(dict(N=N, eta=eta, L=box_side(N, eta), seed=seed, replica=r))
+    return out
+
+
+def eos_batch(seed: int = 6, R: int = 32, N: int = 262144):
+    """Equation-of-state batch: R replicas of N disks at packing fractions
+    evenly spaced from 0.69 to 0.74."""
+    etas = np.linspace(0.69, 0.74, R)
+    return [dict(N=N, eta=float(e), L=box_side(N, float(e)), seed=seed, replica=r)
+            for r, e in enumerate(etas)]
