@@ -50,6 +50,12 @@ def parse():
     ap.add_argument("--paper-params", action="store_true",
                     help="cells, ell, n_m from the paper's strategy (Sec. 4)")
     ap.add_argument("--autotune", action="store_true", help="tune the launch shape first")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--melt", type=int, default=-1,
+                    help="untimed sweeps from the lattice before warm-up (default 20; the "
+                         "oracle arms run the same sweeps and reach the same state)")
+    ap.add_argument("--fixed-params", action="store_true",
+                    help="use the workload table's cells/ell instead of the paper's strategy")
     ap.add_argument("--cells", type=int, default=0, help="cells per side (0 = workload default)")
     ap.add_argument("--ell", type=float, default=0.0, help="chain displacement (0 = default)")
     ap.add_argument("--nm", type=int, default=0, help="chains per cell (0 = eq. nm)")
@@ -60,6 +66,10 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     return ap.parse_args()
+
+
+def melt_sweeps(args):
+    return 20 if args.melt < 0 else args.melt
 
 
 def workload(args):
@@ -143,9 +153,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(w, cells, ell, nm, seconds, max_sweeps=1000):
-    """The oracle, as it stands, single-threaded on this host: sweeps of the
-    same workload from the lattice start until `seconds` have passed."""
+def cpu_baseline(w, cells, ell, nm, seconds, melt=0, max_sweeps=1000):
+    """The oracle, as it stands, single-threaded on this host: the same melt
+    sweeps (untimed), then sweeps of the same workload until `seconds` have
+    passed."""
     import oracle
 
     L = w.L
@@ -153,17 +164,19 @@ def cpu_baseline(w, cells, ell, nm, seconds, max_sweeps=1000):
     if nm == 0:
         nm = oracle.default_nm(w.N, L, 1.0, cells, cells, ell)
     p = oracle.make_params(w.N, L, 1.0, cells, cells, ell, nm, w.seed)
+    oracle.sweeps(p, x, y, 0, melt)
     st = oracle.Stats()
     t0 = time.perf_counter()
     n = 0
     while n < max_sweeps:
-        oracle.sweeps(p, x, y, n, 1, stats=st)
+        oracle.sweeps(p, x, y, melt + n, 1, stats=st)
         n += 1
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
     return {"value": st.events / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d sweeps of the full workload from the lattice start (%.1f s)" % (n, dt),
+            "sample": "%d sweeps of the full workload after %d untimed melt sweeps (%.1f s)"
+                      % (n, melt, dt),
             "sweeps_per_s": n / dt}
 
 
@@ -216,7 +229,7 @@ def run_grid(args):
                 pt["unsupported"] = str(ex)
                 pts.append(pt)
                 continue
-            g.sweep(args.warmup)
+            g.sweep(melt_sweeps(args) + args.warmup)
             g.synchronize()
             g.reset_stats()
             s = torch.cuda.Stream()
@@ -254,15 +267,25 @@ def run_reference(args):
     import oracle
 
     L = w.L
-    nm = args.nm or oracle.default_nm(w.N, L, 1.0, cells, cells, ell)
+    nm = args.nm
+    if not args.fixed_params and not args.cells and not args.ell and \
+            args.workload in ("large", "huge") or args.paper_params:
+        from paper_1409_6948_gb300 import ecmc as E  # parameter choice only (host arithmetic)
+
+        sp = E.suggest_parameters(w.N, L, 1.0, 2.0)
+        cells, ell = sp["cells_x"], sp["ell"]
+        nm = nm or sp["n_m"]
+    nm = nm or oracle.default_nm(w.N, L, 1.0, cells, cells, ell)
     x, y = W.square_lattice(w.N, L)
     p = oracle.make_params(w.N, L, 1.0, cells, cells, ell, nm, w.seed)
+    melt = melt_sweeps(args)
+    oracle.sweeps(p, x, y, 0, melt)
     for s in range(args.warmup):
-        oracle.sweeps(p, x, y, s, 1)
+        oracle.sweeps(p, x, y, melt + s, 1)
     st = oracle.Stats()
     t0 = time.perf_counter()
     for s in range(args.steps):
-        oracle.sweeps(p, x, y, args.warmup + s, 1, stats=st)
+        oracle.sweeps(p, x, y, melt + args.warmup + s, 1, stats=st)
     dt = time.perf_counter() - t0
     value = st.events / dt
     line = {
@@ -270,12 +293,15 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": w.name, "N": w.N, "eta": w.eta, "cells": cells, "ell": ell,
-                   "n_m": nm, "parallelism": "replicas"},
+        "config": {"workload": w.name + " cells=%dx%d ell=%g" % (cells, cells, ell), "N": w.N,
+                   "eta": w.eta, "cells": cells, "ell": ell, "n_m": nm,
+                   "parallelism": "replicas",
+                   "start": "square lattice, %d untimed sweeps, then %d warm-up sweeps"
+                            % (melt, args.warmup)},
         "sweeps_per_s": args.steps / dt,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "%d full sweeps after %d warm-up sweeps" %
-                                   (args.steps, args.warmup)},
+                         "sample": "%d full sweeps after %d untimed melt and %d warm-up "
+                                   "sweeps" % (args.steps, melt, args.warmup)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -309,12 +335,14 @@ def run_ours(args):
                  % (len(descs), min(d["N"] for d in descs), max(d["N"] for d in descs), n_total,
                     min(d["eta"] for d in descs), max(d["eta"] for d in descs)))
     else:
-        if args.paper_params:
+        use_paper = args.paper_params or (not args.fixed_params and not args.cells and
+                                          not args.ell and args.workload in ("large", "huge"))
+        if use_paper:
             sp = E.suggest_parameters(w.N, L, 1.0, 2.0)
             cells, ell = sp["cells_x"], sp["ell"]
         g = P.Ecmc(w.N, L, 1.0, cells, cells, ell, w.seed)
         g.set_param(E.PARAM_REPLICA, rank)
-        if args.paper_params and not args.nm:
+        if use_paper and not args.nm:
             g.set_param(E.PARAM_N_CHAINS, sp["n_m"])
         n_total = w.N
         wname = w.name + " cells=%dx%d ell=%g" % (cells, cells, ell)
@@ -331,11 +359,14 @@ def run_ours(args):
     nm = int(g.get_param(E.PARAM_N_CHAINS))
     tpc = int(g.get_param(E.PARAM_LANES_PER_CELL))
 
+    # untimed preparation of the input state: melt the lattice
+    g.sweep(melt_sweeps(args))
     # warm-up (graphs captured here)
     g.sweep(args.warmup)
     g.synchronize()
     tuned = None
-    if args.autotune:
+    if (args.autotune or args.workload in ("large", "huge", "batch", "eos")) and \
+            not args.no_autotune and not args.tpc:
         tuned, _ = g.autotune(trial_sweeps=2)
         tpc = int(g.get_param(E.PARAM_LANES_PER_CELL))
         g.sweep(1)
@@ -446,7 +477,7 @@ def run_ours(args):
         achieved = bytes_per_launch / (phase_avg_ms * 1e-3) / 1e9
         cpu = None
         if not args.skip_cpu and descs is None:
-            cpu = cpu_baseline(w, cells, ell, nm, args.cpu_seconds)
+            cpu = cpu_baseline(w, cells, ell, nm, args.cpu_seconds, melt_sweeps(args))
         elif not args.skip_cpu:
             cpu = cpu_baseline_batch(descs, args.cpu_seconds)
         line = {
@@ -460,6 +491,8 @@ def run_ours(args):
                        "autotuned": tuned,
                        "screening": "fp32" if args.prec else "fp64",
                        "l2": "none" if args.no_flush else "flushed (256 MB write) between steps",
+                       "start": "square lattice, %d untimed sweeps, then %d warm-up sweeps"
+                                % (melt_sweeps(args), args.warmup),
                        "parallelism": "replicas x%d" % world},
             "sweeps_per_s": sweeps_all / (ms_max * 1e-3),
             "events_per_sweep": events / max(sweeps, 1),
