@@ -506,7 +506,9 @@ def run_ours(args):
                          "bytes_per_event": BYTES_PER_EVENT,
                          "peak_source": "ecmc_device_peaks shared-memory probe (measured)",
                          "fp64_peak_gflops": fp64_gflops},
-            "gpu_launches": 11 * args.steps * world,
+            # per sweep: draws, binning, 4 x (frame builder, chain kernel), chunk
+            # sums, end of sweep
+            "gpu_launches": 12 * args.steps * world,
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": cpu,

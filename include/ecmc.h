@@ -91,6 +91,11 @@ extern "C" {
 #define ECMC_PARAM_WARPS_PER_BLOCK 11
 /* 1 = capture each sweep in a CUDA graph and replay it (default 1). */
 #define ECMC_PARAM_USE_GRAPH 12
+/* Where the chain kernel keeps the cell frames: 0 = shared memory, 1 = FP32
+ * screening data in shared memory and FP64 coordinates in global memory,
+ * 2 = global memory (cells too large for shared memory), -1 = automatic
+ * (default).  Changes only the speed, never the result. */
+#define ECMC_PARAM_FRAME_MODE 13
 
 #define ECMC_DIR_PM_AXIS_ALT 0
 #define ECMC_DIR_POS_ONLY 1
@@ -195,11 +200,13 @@ ECMC_API int ecmc_suggest_parameters(int64_t N, double L, double sigma, double m
 typedef struct {
   int lanes_per_cell;
   int warps_per_block;
+  int frame_mode;
   double ms_per_sweep;
 } ecmc_tune_result_t;
 
 /* Time trial_sweeps sweeps (after one warm-up sweep) for every launch shape
- * that fits (lanes per cell 1..32, warps per block 1, 2, 4), keep the
+ * that fits (lanes per cell 1..32, warps per block 1 and 2, frame modes 0
+ * and 1, or 2 when nothing else fits), keep the
  * fastest, and put the handle back exactly where it was (positions, sweep
  * counter, statistics): every shape gives bit-identical trajectories, so the
  * tuning does not change the simulation.  best receives the chosen shape;

@@ -57,6 +57,14 @@ struct ecmc_ctx {
   int precision = 1;
   int tpc = 0;          // lanes per cell in use
   int tpc_param = 0;    // 0 = automatic
+  int fmode = 0;        // frame placement in use (see phase_smem_bytes)
+  int fmode_param = -1; // -1 = automatic
+  int n_sm = 0;
+  std::vector<int2> chunks;
+  std::vector<int> chunk_off;
+  int2* d_chunks = nullptr;
+  int* d_chunk_off = nullptr;
+  ChunkSums* d_partials = nullptr;
   int warps = 0;
   int warps_param = 0;
   float strip_w = 0.5f;
@@ -145,13 +153,13 @@ RecLayout layout_for(ecmc_ctx* h, int tpc) {
   return make_layout(32 / tpc, nbin, h->b.cap, cap_obj);
 }
 
-int choose_tpc(ecmc_ctx* h) {
+int choose_tpc(ecmc_ctx* h, int fmode) {
   if (h->tpc_param) return h->tpc_param;
   // the widest group (most cells per warp) whose frames leave room for at
   // least four warps per SM, but at most 8 cells per warp: measured on GB300
   // at N = 1M, eta = 0.72, 8 cells per warp beat 4, 16 and 32
   for (int t = 4; t <= 32; t *= 2)
-    if (phase_smem_bytes(layout_for(h, t), 1) <= 52 * 1024) return t;
+    if (phase_smem_bytes(layout_for(h, t), 1, fmode) <= 52 * 1024) return t;
   return 32;
 }
 
@@ -163,18 +171,42 @@ int compute_layout(ecmc_ctx* h) {
     g.bin_w = (float)bw;
     g.inv_bin_w = (float)(1.0 / bw);
   }
-  h->tpc = choose_tpc(h);
-  h->lay = layout_for(h, h->tpc);
-  const size_t per_warp = phase_smem_bytes(h->lay, 1);
   const size_t limit = 232448;  // opt-in shared memory per block on sm_103
-  if (per_warp > limit)
-    return fail(ECMC_ERR_UNSUPPORTED,
-                "cell frame of %zu bytes per group does not fit in shared memory "
-                "(cells too large: use more cells)",
-                per_warp);
+  if (h->n_sm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (h->n_sm <= 0) h->n_sm = 1;
+  }
+  // frame placement: whole frames in shared memory when every group of the
+  // phase fits at once, else only the light part (FP64 in global memory);
+  // frames too large for shared memory are used in place in global memory
+  int fmode = h->fmode_param;
+  if (fmode < 0) {
+    const int t0 = choose_tpc(h, 0);
+    const RecLayout l0 = layout_for(h, t0);
+    const size_t groups = (size_t)(h->b.A_total + l0.cpw - 1) / l0.cpw;
+    const size_t total = groups * phase_smem_bytes(l0, 1, 0);
+    fmode = (phase_smem_bytes(l0, 1, 0) <= limit &&
+             total <= (size_t)h->n_sm * limit * 9 / 10) ? 0 : 1;
+  }
+  h->tpc = choose_tpc(h, fmode);
+  h->lay = layout_for(h, h->tpc);
+  if (fmode < 2 && phase_smem_bytes(h->lay, 1, fmode) > limit) {
+    if (h->tpc_param && h->tpc_param != 32)
+      return fail(ECMC_ERR_UNSUPPORTED, "cell frames too large for %d lanes per cell",
+                  h->tpc_param);
+    h->tpc = 32;
+    h->lay = layout_for(h, 32);
+    if (phase_smem_bytes(h->lay, 1, fmode) > limit) fmode = 1;
+    if (phase_smem_bytes(h->lay, 1, fmode) > limit) fmode = 2;
+  }
+  h->fmode = fmode;
+  h->b.fmode = fmode;
+  const size_t per_warp = phase_smem_bytes(h->lay, 1, fmode);
   int w = h->warps_param;
   if (w == 0) w = 1;  // one warp per block spreads the groups over every SM
-  if ((size_t)w * per_warp > limit) w = (int)(limit / per_warp);
+  if (per_warp > 0 && (size_t)w * per_warp > limit) w = (int)(limit / per_warp);
   if (w < 1) w = 1;
   h->warps = w;
   const int n_groups = (h->b.A_total + h->lay.cpw - 1) / h->lay.cpw;
@@ -185,9 +217,19 @@ int compute_layout(ecmc_ctx* h) {
     CK(cudaMalloc(&h->b.records, need));
     h->records_cap = need;
   }
-  if (frame_build_smem(h->lay) > limit)
-    return fail(ECMC_ERR_UNSUPPORTED, "cell frame too large for the frame builder");
-  if (configure_frame_build(h->lay) || configure_phase(h->lay, h->tpc, h->warps))
+  if (h->b.gtouch) cudaFree(h->b.gtouch);
+  h->b.gtouch = nullptr;
+  if (fmode == 2)
+    CK(cudaMalloc(&h->b.gtouch, (size_t)n_groups * align16((size_t)h->lay.cap_obj * h->lay.cpw)));
+  if (h->b.stage) cudaFree(h->b.stage);
+  h->b.stage = nullptr;
+  h->b.stage_bytes = 0;
+  if (frame_build_smem(h->lay) > limit) {
+    h->b.stage_bytes = frame_build_smem(h->lay);
+    CK(cudaMalloc(&h->b.stage, h->b.stage_bytes * (size_t)h->b.A_total));
+  }
+  if ((!h->b.stage && configure_frame_build(h->lay)) ||
+      configure_phase(h->lay, h->tpc, h->warps, fmode))
     return fail(ECMC_ERR_CUDA, "kernel configuration failed: %s",
                 cudaGetErrorString(cudaGetLastError()));
   return upload_geometry(h);
@@ -400,12 +442,17 @@ void free_all(ecmc_ctx* h) {
   cudaFree(h->b.totals);
   cudaFree(h->b.history);
   cudaFree(h->b.records);
+  cudaFree(h->b.gtouch);
+  cudaFree(h->b.stage);
   cudaFree(h->b.err);
   cudaFree(h->b.chain_recs);
   cudaFree(h->d_geo);
   cudaFree(h->d_cell_rep);
   cudaFree(h->d_act_rep);
   cudaFree(h->d_n_off);
+  cudaFree(h->d_chunks);
+  cudaFree(h->d_chunk_off);
+  cudaFree(h->d_partials);
   cudaFree(h->gr_counts);
   cudaFree(h->xy_tmp);
   cudaFree(h->int_tmp);
@@ -516,6 +563,16 @@ int create_impl(ecmc_t* out, const ecmc_replica_desc_t* desc, int R) {
     h->cell_rep.insert(h->cell_rep.end(), h->geo[r].ncell, r);
     h->act_rep.insert(h->act_rep.end(), h->geo[r].nact, r);
   }
+  // end-of-sweep reduction chunks: at most 2048 cells, never across replicas
+  h->chunk_off.assign(1, 0);
+  for (int r = 0; r < R; ++r) {
+    const Geom& g = h->geo[r];
+    for (int c0 = 0; c0 < g.ncell; c0 += 2048) {
+      const int c1 = c0 + 2048 < g.ncell ? c0 + 2048 : g.ncell;
+      h->chunks.push_back(make_int2(g.cell_off + c0, g.cell_off + c1));
+    }
+    h->chunk_off.push_back((int)h->chunks.size());
+  }
   const int64_t N_total = h->n_off[R];
   if (N_total >= (int64_t(1) << 31) || C_total * (int64_t)cap >= (int64_t(1) << 31)) {
     delete h;
@@ -549,6 +606,9 @@ int create_impl(ecmc_t* out, const ecmc_replica_desc_t* desc, int R) {
       cudaMalloc(&h->d_cell_rep, sizeof(int) * (size_t)C_total) != cudaSuccess ||
       cudaMalloc(&h->d_act_rep, sizeof(int) * (size_t)A_total) != cudaSuccess ||
       cudaMalloc(&h->d_n_off, sizeof(int64_t) * (R + 1)) != cudaSuccess ||
+      cudaMalloc(&h->d_chunks, sizeof(int2) * h->chunks.size()) != cudaSuccess ||
+      cudaMalloc(&h->d_chunk_off, sizeof(int) * h->chunk_off.size()) != cudaSuccess ||
+      cudaMalloc(&h->d_partials, sizeof(ChunkSums) * h->chunks.size()) != cudaSuccess ||
       cudaMalloc(&h->xy_tmp, sizeof(double) * 2 * (size_t)N_total) != cudaSuccess ||
       cudaMalloc(&h->int_tmp, sizeof(int) * (size_t)N_total) != cudaSuccess ||
       cudaMalloc(&h->u64_tmp, sizeof(unsigned long long) * 4) != cudaSuccess)
@@ -561,8 +621,16 @@ int create_impl(ecmc_t* out, const ecmc_replica_desc_t* desc, int R) {
       cudaMemcpyAsync(h->d_act_rep, h->act_rep.data(), sizeof(int) * A_total,
                       cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
       cudaMemcpyAsync(h->d_n_off, h->n_off.data(), sizeof(int64_t) * (R + 1),
+                      cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(h->d_chunks, h->chunks.data(), sizeof(int2) * h->chunks.size(),
+                      cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(h->d_chunk_off, h->chunk_off.data(), sizeof(int) * h->chunk_off.size(),
                       cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
     return bail(fail(ECMC_ERR_CUDA, "upload failed"));
+  b.chunks = h->d_chunks;
+  b.chunk_off = h->d_chunk_off;
+  b.partials = h->d_partials;
+  b.n_chunks = (int)h->chunks.size();
   b.rg = h->d_geo;
   b.cell_rep = h->d_cell_rep;
   b.act_rep = h->d_act_rep;
@@ -795,6 +863,13 @@ int ecmc_set_param(ecmc_t h, int key, double v) {
       h->use_graph = v != 0.0;
       drop_graphs(h);
       return ECMC_OK;
+    case ECMC_PARAM_FRAME_MODE: {
+      const int m = (int)v;
+      if ((double)m != v || m < -1 || m > 2) return fail(ECMC_ERR_ARG, "frame mode");
+      h->fmode_param = m;
+      drop_graphs(h);
+      return compute_layout(h);
+    }
     default:
       return fail(ECMC_ERR_ARG, "unknown parameter %d", key);
   }
@@ -815,6 +890,7 @@ int ecmc_get_param(ecmc_t h, int key, double* v) {
     case ECMC_PARAM_RECORD_CHAINS: *v = h->record_chains; break;
     case ECMC_PARAM_WARPS_PER_BLOCK: *v = h->warps; break;
     case ECMC_PARAM_USE_GRAPH: *v = h->use_graph; break;
+    case ECMC_PARAM_FRAME_MODE: *v = h->fmode; break;
     default: return fail(ECMC_ERR_ARG, "unknown parameter %d", key);
   }
   return ECMC_OK;
@@ -1101,6 +1177,7 @@ int ecmc_autotune(ecmc_t h, int trial_sweeps, ecmc_tune_result_t* best, ecmc_tun
                   h->stream);
   const int64_t t_saved = h->t_host, hist_saved = h->hist_len_host;
   const int tpc0 = h->tpc_param, warps0 = h->warps_param, timing0 = h->timing;
+  const int fmode0 = h->fmode_param;
   h->timing = 0;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -1108,13 +1185,16 @@ int ecmc_autotune(ecmc_t h, int trial_sweeps, ecmc_tune_result_t* best, ecmc_tun
   std::vector<ecmc_tune_result_t> res;
   int rc = ECMC_OK;
   const int tpcs[6] = {1, 2, 4, 8, 16, 32};
-  const int wps[3] = {1, 2, 4};
+  const int wps[2] = {1, 2};
+  for (int fm = 0; fm < 3 && rc == ECMC_OK; ++fm)
   for (int ti = 0; ti < 6 && rc == ECMC_OK; ++ti)
-    for (int wi = 0; wi < 3 && rc == ECMC_OK; ++wi) {
+    for (int wi = 0; wi < 2 && rc == ECMC_OK; ++wi) {
       h->tpc_param = tpcs[ti];
       h->warps_param = wps[wi];
+      h->fmode_param = fm;
       drop_graphs(h);
-      if (compute_layout(h) != ECMC_OK || h->warps != wps[wi]) continue;  // does not fit
+      if (compute_layout(h) != ECMC_OK || h->warps != wps[wi] || h->fmode != fm) continue;
+      if (fm == 2 && res.size() > 0) continue;  // global frames only when nothing else fits
       rc = ecmc_sweep(h, 1);
       if (rc) break;
       cudaEventRecord(e0, h->stream);
@@ -1128,6 +1208,7 @@ int ecmc_autotune(ecmc_t h, int trial_sweeps, ecmc_tune_result_t* best, ecmc_tun
       ecmc_tune_result_t r;
       r.lanes_per_cell = h->tpc;
       r.warps_per_block = h->warps;
+      r.frame_mode = h->fmode;
       r.ms_per_sweep = ms / trial_sweeps;
       res.push_back(r);
       // back to the saved state before the next shape
@@ -1147,9 +1228,11 @@ int ecmc_autotune(ecmc_t h, int trial_sweeps, ecmc_tune_result_t* best, ecmc_tun
     *best = res[bi];
     h->tpc_param = res[bi].lanes_per_cell;
     h->warps_param = res[bi].warps_per_block;
+    h->fmode_param = res[bi].frame_mode;
   } else {
     h->tpc_param = tpc0;
     h->warps_param = warps0;
+    h->fmode_param = fmode0;
   }
   drop_graphs(h);
   int rc2 = compute_layout(h);

@@ -199,19 +199,19 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
   return v;
 }
 
-__global__ void __launch_bounds__(1024) k_sweep_end(const Geom* __restrict__ rg, SweepState* st,
-                                                    const CellStats* __restrict__ cs,
-                                                    RunTotals* tot, double* history,
-                                                    int64_t history_cap) {
-  __shared__ double sd[2][32];
-  __shared__ long long sl[6][32];
-  const int rep = blockIdx.x;
-  const Geom& g = rg[rep];
+// Partial sums over one chunk of cells (one block per chunk), in a fixed
+// order: thread-strided sums, then warp and block trees.
+__global__ void __launch_bounds__(256) k_sweep_partials(const CellStats* __restrict__ cs,
+                                                        const int2* __restrict__ chunks,
+                                                        ChunkSums* __restrict__ out) {
+  __shared__ double sd[2][8];
+  __shared__ long long sl[6][8];
+  const int2 ch = chunks[blockIdx.x];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   double b = 0.0, bw = 0.0;
   long long v[6] = {0, 0, 0, 0, 0, 0};
-  for (int c = tid; c < g.ncell; c += blockDim.x) {
-    const CellStats s = cs[g.cell_off + c];
+  for (int c = ch.x + tid; c < ch.y; c += blockDim.x) {
+    const CellStats s = cs[c];
     b += s.sum_b;
     bw += (double)s.n_mem * s.sum_b;
     v[0] += s.events;
@@ -230,42 +230,68 @@ __global__ void __launch_bounds__(1024) k_sweep_end(const Geom* __restrict__ rg,
     for (int q = 0; q < 6; ++q) sl[q][wid] = v[q];
   }
   __syncthreads();
-  if (wid != 0) return;
-  const int nw = blockDim.x >> 5;
-  b = lane < nw ? sd[0][lane] : 0.0;
-  bw = lane < nw ? sd[1][lane] : 0.0;
-  for (int q = 0; q < 6; ++q) v[q] = lane < nw ? sl[q][lane] : 0;
-  b = warp_sum_d(b);
-  bw = warp_sum_d(bw);
-  for (int q = 0; q < 6; ++q) v[q] = warp_sum_ll(v[q]);
-  if (lane == 0) {
-    RunTotals& T = tot[rep];
-    SweepState& S = st[rep];
-    const double disp_w = (double)g.N * (double)g.n_m * g.ell;
-    T.sum_b += b;
-    T.sum_b_w += bw;
-    T.sum_disp += (double)v[5] * g.ell;
-    T.sum_disp_w += disp_w;
-    T.events += v[0];
-    T.lifts += v[1];
-    T.frozen += v[2];
-    T.walls += v[3];
-    T.fp64_evals += v[4];
-    T.chains += v[5];
-    T.sweeps += 1;
-    if (history != nullptr && S.history_len < history_cap) {
-      double* h = history + 2 * ((int64_t)rep * history_cap + S.history_len);
-      h[0] = bw;
-      h[1] = disp_w;
+  if (tid == 0) {
+    ChunkSums r;
+    r.sum_b = 0.0;
+    r.sum_b_w = 0.0;
+    for (int q = 0; q < 6; ++q) r.v[q] = 0;
+    for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) {
+      r.sum_b += sd[0][wv];
+      r.sum_b_w += sd[1][wv];
+      for (int q = 0; q < 6; ++q) r.v[q] += sl[q][wv];
     }
-    S.history_len += 1;
-    S.t += 1;
+    out[blockIdx.x] = r;
   }
 }
 
+void launch_sweep_partials(const DevBufs& b, cudaStream_t s) {
+  k_sweep_partials<<<b.n_chunks, 256, 0, s>>>(b.cell_stats, b.chunks, b.partials);
+}
+
+// End of sweep, one thread per replica: add the replica's chunk sums in
+// chunk order (deterministic) to its running totals, append its
+// member-weighted pressure sums of this sweep to its history, advance its
+// sweep counter.
+__global__ void k_sweep_end(const Geom* __restrict__ rg, SweepState* st,
+                            const ChunkSums* __restrict__ part, const int* __restrict__ chunk_off,
+                            RunTotals* tot, double* history, int64_t history_cap, int R) {
+  const int rep = blockIdx.x * blockDim.x + threadIdx.x;
+  if (rep >= R) return;
+  const Geom& g = rg[rep];
+  double b = 0.0, bw = 0.0;
+  long long v[6] = {0, 0, 0, 0, 0, 0};
+  for (int k = chunk_off[rep]; k < chunk_off[rep + 1]; ++k) {
+    b += part[k].sum_b;
+    bw += part[k].sum_b_w;
+    for (int q = 0; q < 6; ++q) v[q] += part[k].v[q];
+  }
+  RunTotals& T = tot[rep];
+  SweepState& S = st[rep];
+  const double disp_w = (double)g.N * (double)g.n_m * g.ell;
+  T.sum_b += b;
+  T.sum_b_w += bw;
+  T.sum_disp += (double)v[5] * g.ell;
+  T.sum_disp_w += disp_w;
+  T.events += v[0];
+  T.lifts += v[1];
+  T.frozen += v[2];
+  T.walls += v[3];
+  T.fp64_evals += v[4];
+  T.chains += v[5];
+  T.sweeps += 1;
+  if (history != nullptr && S.history_len < history_cap) {
+    double* h = history + 2 * ((int64_t)rep * history_cap + S.history_len);
+    h[0] = bw;
+    h[1] = disp_w;
+  }
+  S.history_len += 1;
+  S.t += 1;
+}
+
 void launch_sweep_end(const DevBufs& b, cudaStream_t s) {
-  k_sweep_end<<<b.R, 1024, 0, s>>>(b.rg, b.state, b.cell_stats, b.totals, b.history,
-                                   b.history_cap);
+  launch_sweep_partials(b, s);
+  k_sweep_end<<<(b.R + 31) / 32, 32, 0, s>>>(b.rg, b.state, b.partials, b.chunk_off, b.totals,
+                                             b.history, b.history_cap, b.R);
 }
 
 }  // namespace ecmc

@@ -32,7 +32,8 @@ __global__ void k_frame_build(const Geom* __restrict__ rg, const SweepState* __r
                               const int* __restrict__ act_rep, int cap, int colour_index,
                               const double* __restrict__ px, const double* __restrict__ py,
                               const int* __restrict__ pid, const int* __restrict__ cnt,
-                              unsigned char* __restrict__ records, RecLayout lay, int* err) {
+                              unsigned char* __restrict__ records, RecLayout lay,
+                              unsigned char* __restrict__ stage, size_t stage_bytes, int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_nobj, s_nmem, s_overflow;
   const int tid = threadIdx.x, bt = blockDim.x;
@@ -54,7 +55,9 @@ __global__ void k_frame_build(const Geom* __restrict__ rg, const SweepState* __r
 
   BuildSmem s;
   {
-    unsigned char* p = smem;
+    // staging area: shared memory, or a global region per block when the
+    // frame is too large for shared memory
+    unsigned char* p = stage ? stage + (size_t)blockIdx.x * stage_bytes : smem;
     s.a64 = (double*)p; p += sizeof(double) * lay.cap_obj;
     s.b64 = (double*)p; p += sizeof(double) * lay.cap_obj;
     s.key = (int*)p; p += sizeof(int) * lay.cap_obj;
@@ -236,16 +239,17 @@ static size_t build_smem(const RecLayout& lay) {
 
 void launch_frame_build(const DevBufs& b, const RecLayout& lay, int colour_index,
                         cudaStream_t s) {
-  const size_t sm = build_smem(lay);
+  const size_t sm = b.stage ? 0 : build_smem(lay);
   int bt = 32;
   if (lay.cap_obj > 256) bt = 128;
   if (lay.cap_obj > 1024) bt = 256;
+  if (lay.cap_obj > 4096) bt = 1024;
   k_frame_build<<<b.A_total, bt, sm, s>>>(b.rg, b.state, b.act_rep, b.cap, colour_index,
                                           b.px[b.cur], b.py[b.cur], b.pid[b.cur], b.count[b.cur],
-                                          b.records, lay, b.err);
+                                          b.records, lay, b.stage, b.stage_bytes, b.err);
 }
 
-size_t frame_build_smem(const RecLayout& lay) { return build_smem(lay); }
+size_t frame_build_smem(const RecLayout& lay) { return align16(build_smem(lay)); }
 
 // largest amount the kernel can have, for the same reason as configure_phase
 int configure_frame_build(const RecLayout& lay) {

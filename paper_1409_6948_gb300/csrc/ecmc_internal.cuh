@@ -49,6 +49,12 @@ struct CellStats {
   int fp64_evals, chains, n_mem, pad;
 };
 
+// Partial sums of one chunk of a replica's cells (end-of-sweep reduction).
+struct ChunkSums {
+  double sum_b, sum_b_w;
+  long long v[6];  // events, lifts, frozen, walls, fp64_evals, chains
+};
+
 // Running totals (device).
 struct RunTotals {
   double sum_b, sum_disp, sum_b_w, sum_disp_w;
@@ -92,11 +98,14 @@ struct Geom {
 };
 
 // Frame record layout of one group of cpw cells (all arrays [index][cpw]).
+// The first light_bytes (header, strips, members, FP32 coordinates, keys)
+// are what the chain kernel scans; the FP64 coordinates follow, so that the
+// kernel may keep only the light part in shared memory.
 struct RecLayout {
   int cpw;
   int nbin, cap_mem, cap_obj;
   size_t off_hdr, off_bstart, off_mrank, off_mslot, off_a32, off_b32, off_a64, off_b64,
-      off_key, off_info, bytes;
+      off_key, off_info, light_bytes, bytes;
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
@@ -114,10 +123,11 @@ inline RecLayout make_layout(int cpw, int nbin, int cap_mem, int cap_obj) {
   r.off_mslot = o;   o = align16(o + sizeof(int) * (size_t)cap_mem * cpw);
   r.off_a32 = o;     o = align16(o + sizeof(float) * (size_t)cap_obj * cpw);
   r.off_b32 = o;     o = align16(o + sizeof(float) * (size_t)cap_obj * cpw);
-  r.off_a64 = o;     o = align16(o + sizeof(double) * (size_t)cap_obj * cpw);
-  r.off_b64 = o;     o = align16(o + sizeof(double) * (size_t)cap_obj * cpw);
   r.off_key = o;     o = align16(o + sizeof(int) * (size_t)cap_obj * cpw);
   r.off_info = o;    o = align16(o + sizeof(int) * (size_t)cap_obj * cpw);
+  r.light_bytes = o;
+  r.off_a64 = o;     o = align16(o + sizeof(double) * (size_t)cap_obj * cpw);
+  r.off_b64 = o;     o = align16(o + sizeof(double) * (size_t)cap_obj * cpw);
   r.bytes = o;
   return r;
 }
@@ -135,6 +145,10 @@ struct DevBufs {
   double* history;         // [R][history_cap] pairs: sum_b_w, sum_disp_w
   int64_t history_cap;
   unsigned char* records;  // frame records of one colour
+  unsigned char* gtouch;   // touched flags in global memory (fmode 2)
+  int fmode;               // where the chain kernel keeps the frames (see phase_smem_bytes)
+  unsigned char* stage;    // non-null: frame builder stages objects in global memory
+  size_t stage_bytes;      // per active cell
   int* err;
   ChainRec* chain_recs;    // optional, [C_total * max n_m]
   int rec_stride;          // chain records per cell
@@ -142,6 +156,10 @@ struct DevBufs {
   const int* cell_rep;     // [C_total] replica of every global cell
   const int* act_rep;      // [A_total] replica of every global active cell
   const int64_t* n_off;    // [R + 1] disk offsets
+  const int2* chunks;      // [n_chunks] (first, last+1) global cells, replica-aligned
+  const int* chunk_off;    // [R + 1] first chunk of every replica
+  ChunkSums* partials;     // [n_chunks]
+  int n_chunks;
   int R, C_total, A_total, cap;
   int64_t N_total;
 };
@@ -155,6 +173,7 @@ void launch_frame_build(const DevBufs& b, const RecLayout& lay, int colour_index
                         cudaStream_t s);
 int launch_phase(const DevBufs& b, const RecLayout& lay, int colour_index, int tpc,
                  int warps_per_block, int records_on, int precision, cudaStream_t s);
+void launch_sweep_partials(const DevBufs& b, cudaStream_t s);
 void launch_sweep_end(const DevBufs& b, cudaStream_t s);
 void launch_gather(const DevBufs& b, double* xy_out, cudaStream_t s);
 void launch_load_flat(const DevBufs& b, const double* xy_dev, cudaStream_t s);
@@ -165,9 +184,11 @@ void launch_gr(const Geom& g, const DevBufs& b, double dr, int nbins, unsigned l
                cudaStream_t s);
 size_t frame_build_smem(const RecLayout& lay);
 int configure_frame_build(const RecLayout& lay);
-int configure_phase(const RecLayout& lay, int tpc, int warps);
+int configure_phase(const RecLayout& lay, int tpc, int warps, int fmode);
 int probe_peaks(double* smem_gbs, double* fp64_gflops);
-size_t phase_smem_bytes(const RecLayout& lay, int warps_per_block);
+// fmode: 0 = whole frame in shared memory, 1 = FP64 coordinates in global
+// memory, 2 = whole frame in global memory
+size_t phase_smem_bytes(const RecLayout& lay, int warps_per_block, int fmode = 0);
 int phase_max_warps(const RecLayout& lay, int tpc);
 
 }  // namespace ecmc

@@ -118,13 +118,13 @@ extern "C" int ecmc_sweep_noalloc(double* xy, int64_t N, double L, double sigma,
   }
   int tpc = 32;
   for (int t = 4; t <= 32; t *= 2) {
-    if (phase_smem_bytes(make_layout(32 / t, g.nbin, g.cap_mem, g.cap_obj), 1) <= 52 * 1024) {
+    if (phase_smem_bytes(make_layout(32 / t, g.nbin, g.cap_mem, g.cap_obj), 1, 0) <= 52 * 1024) {
       tpc = t;
       break;
     }
   }
   const RecLayout lay = make_layout(32 / tpc, g.nbin, g.cap_mem, g.cap_obj);
-  if (phase_smem_bytes(lay, 1) > 232448 || frame_build_smem(lay) > 232448)
+  if (phase_smem_bytes(lay, 1, 0) > 232448 || frame_build_smem(lay) > 232448)
     return ECMC_ERR_UNSUPPORTED;
 
   // carve the scratch array
@@ -148,6 +148,10 @@ extern "C" int ecmc_sweep_noalloc(double* xy, int64_t N, double L, double sigma,
   const size_t o_crep = carve(off, sizeof(int) * (size_t)g.ncell);
   const size_t o_arep = carve(off, sizeof(int) * (size_t)n_active);
   const size_t o_noff = carve(off, sizeof(int64_t) * 2);
+  const int n_chunks = (g.ncell + 2047) / 2048;
+  const size_t o_chunks = carve(off, sizeof(int2) * (size_t)n_chunks);
+  const size_t o_choff = carve(off, sizeof(int) * 2);
+  const size_t o_part = carve(off, sizeof(ChunkSums) * (size_t)n_chunks);
   // larger systems than the static array can serve are rejected up front
   if (off > (size_t)ECMC_NOALLOC_SCRATCH_BYTES) return ECMC_ERR_CAPACITY;
 
@@ -180,10 +184,16 @@ extern "C" int ecmc_sweep_noalloc(double* xy, int64_t N, double L, double sigma,
   b.A_total = n_active;
   b.cap = g.cap_mem;
   b.N_total = N;
+  b.chunks = reinterpret_cast<int2*>(base + o_chunks);
+  b.chunk_off = reinterpret_cast<int*>(base + o_choff);
+  b.partials = reinterpret_cast<ChunkSums*>(base + o_part);
+  b.n_chunks = n_chunks;
+  b.fmode = 0;
   const int64_t n_off_host[2] = {0, N};
+  const int chunk_off_host[2] = {0, n_chunks};
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (configure_frame_build(lay) || configure_phase(lay, tpc, 1)) return ECMC_ERR_CUDA;
+  if (configure_frame_build(lay) || configure_phase(lay, tpc, 1, 0)) return ECMC_ERR_CUDA;
 
   // clear what must start at zero, set the sweep counter
   SweepState st;
@@ -198,8 +208,16 @@ extern "C" int ecmc_sweep_noalloc(double* xy, int64_t N, double L, double sigma,
       cudaMemcpyAsync((void*)b.rg, &g, sizeof(g), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync((void*)b.n_off, n_off_host, sizeof(n_off_host), cudaMemcpyHostToDevice,
                       s) != cudaSuccess ||
-      cudaMemcpyAsync(b.state, &st, sizeof(st), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      cudaMemcpyAsync(b.state, &st, sizeof(st), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync((void*)b.chunk_off, chunk_off_host, sizeof(chunk_off_host),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess)
     return ECMC_ERR_CUDA;
+  for (int k = 0; k < n_chunks; ++k) {
+    const int2 ch = make_int2(k * 2048, (k + 1) * 2048 < g.ncell ? (k + 1) * 2048 : g.ncell);
+    if (cudaMemcpyAsync((void*)(b.chunks + k), &ch, sizeof(ch), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+      return ECMC_ERR_CUDA;
+  }
   if (cudaStreamSynchronize(s) != cudaSuccess) return ECMC_ERR_CUDA;
 
   // caller positions -> buckets, n sweeps, buckets -> caller positions

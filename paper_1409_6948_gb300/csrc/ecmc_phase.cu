@@ -67,12 +67,18 @@ __device__ __forceinline__ bool better(double s, int key, double bs, int bkey) {
   return s < bs || (s == bs && key < bkey);
 }
 
-template <int TPC, bool SCREEN>
+// FMODE 0: the warp copies its group's whole record into shared memory;
+// FMODE 1: only the light part (FP32 coordinates, keys, strips, members), the
+// FP64 coordinates are read and written in place in global memory (more
+// cells fit in shared memory at once); FMODE 2: the whole record is used in
+// place in global memory (cells too large for shared memory).
+template <int TPC, bool SCREEN, int FMODE>
 __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
                                                const SweepState* __restrict__ sts,
                                                const int* __restrict__ act_rep, int colour_index,
-                                               const unsigned char* __restrict__ records,
-                                               RecLayout lay, int n_active, double* __restrict__ px,
+                                               unsigned char* __restrict__ records,
+                                               unsigned char* __restrict__ gtouch, RecLayout lay,
+                                               int n_active, double* __restrict__ px,
                                                double* __restrict__ py, CellStats* __restrict__ cs,
                                                ChainRec* __restrict__ recs, int rec_stride,
                                                int* err) {
@@ -85,13 +91,23 @@ __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
 
   const size_t rec_bytes = lay.bytes;
   const size_t t_bytes = align16((size_t)lay.cap_obj * CPW);
-  unsigned char* base = smem + (size_t)warp * (rec_bytes + t_bytes);
-  {
-    const int4* src = reinterpret_cast<const int4*>(records + (size_t)G * rec_bytes);
+  unsigned char* const grec = records + (size_t)G * rec_bytes;
+  unsigned char* base;
+  unsigned char* tbase;
+  if (FMODE == 2) {
+    base = grec;
+    tbase = gtouch + (size_t)G * t_bytes;
+  } else {
+    const size_t copy = FMODE == 1 ? lay.light_bytes : rec_bytes;
+    base = smem + (size_t)warp * (copy + t_bytes);
+    tbase = base + copy;
+    const int4* src = reinterpret_cast<const int4*>(grec);
     int4* dst = reinterpret_cast<int4*>(base);
-    const int n16 = (int)(rec_bytes / 16);
+    const int n16 = (int)(copy / 16);
     for (int i = lane; i < n16; i += 32) dst[i] = src[i];
-    int4* tz = reinterpret_cast<int4*>(base + rec_bytes);
+  }
+  {
+    int4* tz = reinterpret_cast<int4*>(tbase);
     const int4 z = make_int4(0, 0, 0, 0);
     for (int i = lane; i < (int)(t_bytes / 16); i += 32) tz[i] = z;
   }
@@ -104,11 +120,11 @@ __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
   f.mslot = (const int*)(base + lay.off_mslot);
   f.a32 = (float*)(base + lay.off_a32);
   f.b32 = (const float*)(base + lay.off_b32);
-  f.a64 = (double*)(base + lay.off_a64);
-  f.b64 = (const double*)(base + lay.off_b64);
+  f.a64 = (double*)((FMODE == 1 ? grec : base) + lay.off_a64);
+  f.b64 = (const double*)((FMODE == 1 ? grec : base) + lay.off_b64);
   f.key = (const int*)(base + lay.off_key);
   f.info = (const int*)(base + lay.off_info);
-  f.touched = base + rec_bytes;
+  f.touched = tbase;
   const int* hdr = (const int*)(base + lay.off_hdr);
 
   const int gi = lane / TPC, sub = lane - gi * TPC;
@@ -420,8 +436,10 @@ __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
   }
 }
 
-size_t phase_smem_bytes(const RecLayout& lay, int warps_per_block) {
-  return (size_t)warps_per_block * (lay.bytes + align16((size_t)lay.cap_obj * lay.cpw));
+size_t phase_smem_bytes(const RecLayout& lay, int warps_per_block, int fmode) {
+  if (fmode == 2) return 0;
+  const size_t copy = fmode == 1 ? lay.light_bytes : lay.bytes;
+  return (size_t)warps_per_block * (copy + align16((size_t)lay.cap_obj * lay.cpw));
 }
 
 template <int TPC, bool SCREEN>
@@ -431,10 +449,16 @@ static int launch_t(const DevBufs& b, const RecLayout& lay, int colour_index, in
   const int cpw = 32 / TPC;
   const int n_groups = (n_active + cpw - 1) / cpw;
   const int blocks = (n_groups + warps - 1) / warps;
-  const size_t sm = phase_smem_bytes(lay, warps);
-  k_phase<TPC, SCREEN><<<blocks, 32 * warps, sm, s>>>(
-      b.rg, b.state, b.act_rep, colour_index, b.records, lay, n_active, b.px[b.cur], b.py[b.cur],
-      b.cell_stats, records_on ? b.chain_recs : nullptr, b.rec_stride, b.err);
+  const size_t sm = phase_smem_bytes(lay, warps, b.fmode);
+#define ECMC_PHASE(FM)                                                                     \
+  k_phase<TPC, SCREEN, FM><<<blocks, 32 * warps, sm, s>>>(                                 \
+      b.rg, b.state, b.act_rep, colour_index, b.records, b.gtouch, lay, n_active,          \
+      b.px[b.cur], b.py[b.cur], b.cell_stats, records_on ? b.chain_recs : nullptr,         \
+      b.rec_stride, b.err)
+  if (b.fmode == 2) ECMC_PHASE(2);
+  else if (b.fmode == 1) ECMC_PHASE(1);
+  else ECMC_PHASE(0);
+#undef ECMC_PHASE
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -462,27 +486,32 @@ static int configure_fn(F fn, size_t need) {
              : -1;
 }
 
-template <int TPC>
+template <int TPC, int FM>
 static int configure_t(size_t sm) {
-  if (configure_fn(k_phase<TPC, true>, sm)) return -1;
-  if (configure_fn(k_phase<TPC, false>, sm)) return -1;
+  if (configure_fn(k_phase<TPC, true, FM>, sm)) return -1;
+  if (configure_fn(k_phase<TPC, false, FM>, sm)) return -1;
   return 0;
 }
 
 // The attribute is a per-kernel, per-process maximum: request the largest
 // amount the kernel can have, so that a handle with small frames never lowers
 // the limit that a handle with larger frames needs.
-int configure_phase(const RecLayout& lay, int tpc, int warps) {
-  const size_t sm = phase_smem_bytes(lay, warps);
+int configure_phase(const RecLayout& lay, int tpc, int warps, int fmode) {
+  if (fmode == 2) return 0;  // frames in global memory need no shared memory
+  const size_t sm = phase_smem_bytes(lay, warps, fmode);
+#define ECMC_CFG(T)                                                          \
+  case T:                                                                    \
+    return fmode == 1 ? configure_t<T, 1>(sm) : configure_t<T, 0>(sm);
   switch (tpc) {
-    case 1: return configure_t<1>(sm);
-    case 2: return configure_t<2>(sm);
-    case 4: return configure_t<4>(sm);
-    case 8: return configure_t<8>(sm);
-    case 16: return configure_t<16>(sm);
-    case 32: return configure_t<32>(sm);
+    ECMC_CFG(1)
+    ECMC_CFG(2)
+    ECMC_CFG(4)
+    ECMC_CFG(8)
+    ECMC_CFG(16)
+    ECMC_CFG(32)
     default: return -1;
   }
+#undef ECMC_CFG
 }
 
 int launch_phase(const DevBufs& b, const RecLayout& lay, int colour_index, int tpc, int warps,

@@ -30,6 +30,7 @@ PARAM_STRIP_WIDTH = 9
 PARAM_RECORD_CHAINS = 10
 PARAM_WARPS_PER_BLOCK = 11
 PARAM_USE_GRAPH = 12
+PARAM_FRAME_MODE = 13
 
 DIR_PM_AXIS_ALT = 0
 DIR_POS_ONLY = 1
@@ -58,7 +59,7 @@ class Timing(C.Structure):
 
 class TuneResult(C.Structure):
     _fields_ = [("lanes_per_cell", C.c_int), ("warps_per_block", C.c_int),
-                ("ms_per_sweep", C.c_double)]
+                ("frame_mode", C.c_int), ("ms_per_sweep", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -206,9 +207,9 @@ class Ecmc:
     def autotune(self, trial_sweeps=3):
         """Measure every launch shape, keep the fastest (state unchanged)."""
         best = TuneResult()
-        arr = (TuneResult * 32)()
+        arr = (TuneResult * 64)()
         n = C.c_int()
-        _check(load().ecmc_autotune(self._h, int(trial_sweeps), C.byref(best), arr, 32,
+        _check(load().ecmc_autotune(self._h, int(trial_sweeps), C.byref(best), arr, 64,
                                     C.byref(n)), "ecmc_autotune")
         return best.as_dict(), [arr[i].as_dict() for i in range(n.value)]
 

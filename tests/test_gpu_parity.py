@@ -29,7 +29,7 @@ REL = 1e-12
 
 
 def make(N, eta, cells_x, cells_y, ell, nm, seed, tpc=0, prec=1, dir_mode=0, records=False,
-         replica=0):
+         replica=0, fmode=-1):
     L = W.box_side(N, eta)
     g = P.Ecmc(N, L, 1.0, cells_x, cells_y, ell, seed)
     g.set_param(E.PARAM_N_CHAINS, nm)
@@ -38,6 +38,8 @@ def make(N, eta, cells_x, cells_y, ell, nm, seed, tpc=0, prec=1, dir_mode=0, rec
     g.set_param(E.PARAM_REPLICA, replica)
     if tpc:
         g.set_param(E.PARAM_LANES_PER_CELL, tpc)
+    if fmode >= 0:
+        g.set_param(E.PARAM_FRAME_MODE, fmode)
     if records:
         g.set_param(E.PARAM_RECORD_CHAINS, 1)
     p = oracle.make_params(N, L, 1.0, cells_x, cells_y, ell, nm, seed, replica,
@@ -224,3 +226,18 @@ def test_graph_replay_equals_direct_launches():
     assert np.array_equal(a.positions(), b.positions())
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("N,eta,cells,ell,nm", [
+    (4096, 0.72, 2, 4.0, 8),      # 33-sigma cells: one cell per warp, frame in shared memory
+    (16384, 0.72, 2, 4.0, 20),    # 67-sigma cells: frame used in global memory, staged builder
+])
+def test_large_cells(N, eta, cells, ell, nm):
+    run_pair(N, eta, cells, cells, ell, nm, 5, 2)
+
+
+@pytest.mark.parametrize("fmode", [0, 1, 2])
+@pytest.mark.parametrize("tpc", [1, 4, 32])
+def test_frame_placements(fmode, tpc):
+    # frames in shared memory, FP64 part in global memory, all in global memory
+    run_pair(4096, 0.72, 16, 16, 3.0, 2, 17, 3, tpc=tpc, fmode=fmode)
