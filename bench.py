@@ -51,6 +51,7 @@ def parse():
                     help="cells, ell, n_m from the paper's strategy (Sec. 4)")
     ap.add_argument("--autotune", action="store_true", help="tune the launch shape first")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--fmode", type=int, default=-1, help="frame placement 0/1/2 (-1 automatic)")
     ap.add_argument("--melt", type=int, default=-1,
                     help="untimed sweeps from the lattice before warm-up (default 20; the "
                          "oracle arms run the same sweeps and reach the same state)")
@@ -66,6 +67,24 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     return ap.parse_args()
+
+
+def combine_over_ranks(ms, events, sweeps, device=None):
+    """Whole-job figures of independent replicas on several ranks: the
+    slowest rank's timed milliseconds, and the events and sweeps of all."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([float(events), float(sweeps)], dtype=torch.float64, device=device)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return t.item(), n[0].item(), n[1].item()
+
+
+def replica_key(rank, r=0):
+    """Philox key word 1 of replica r on a rank: ranks never share a stream."""
+    return r + 100000 * rank
 
 
 def melt_sweeps(args):
@@ -89,7 +108,7 @@ def batch_descs(args, rank):
     out = []
     for d in reps:
         s = E.suggest_parameters(d["N"], d["L"], 1.0, 2.0)
-        s.update(seed=d["seed"], replica=d["replica"] + 100000 * rank, eta=d["eta"])
+        s.update(seed=d["seed"], replica=replica_key(rank, d["replica"]), eta=d["eta"])
         out.append(s)
     return out
 
@@ -341,7 +360,7 @@ def run_ours(args):
             sp = E.suggest_parameters(w.N, L, 1.0, 2.0)
             cells, ell = sp["cells_x"], sp["ell"]
         g = P.Ecmc(w.N, L, 1.0, cells, cells, ell, w.seed)
-        g.set_param(E.PARAM_REPLICA, rank)
+        g.set_param(E.PARAM_REPLICA, replica_key(rank))
         if use_paper and not args.nm:
             g.set_param(E.PARAM_N_CHAINS, sp["n_m"])
         n_total = w.N
@@ -351,6 +370,8 @@ def run_ours(args):
     if args.tpc:
         g.set_param(E.PARAM_LANES_PER_CELL, args.tpc)
     g.set_param(E.PARAM_PRECISION, args.prec)
+    if args.fmode >= 0:
+        g.set_param(E.PARAM_FRAME_MODE, args.fmode)
     # a stream of our own (torch's default stream is the legacy NULL stream,
     # which the library reads as "use your own stream")
     stream = torch.cuda.Stream()
@@ -366,7 +387,7 @@ def run_ours(args):
     g.synchronize()
     tuned = None
     if (args.autotune or args.workload in ("large", "huge", "batch", "eos")) and \
-            not args.no_autotune and not args.tpc:
+            not args.no_autotune and not args.tpc and args.fmode < 0:
         tuned, _ = g.autotune(trial_sweeps=2)
         tpc = int(g.get_param(E.PARAM_LANES_PER_CELL))
         g.sweep(1)
@@ -407,14 +428,7 @@ def run_ours(args):
     sweeps = c.sweeps
 
     if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        n = torch.tensor([float(events), float(sweeps)], dtype=torch.float64, device=dev)
-        dist.all_reduce(n, op=dist.ReduceOp.SUM)
-        ms_max = t.item()
-        events_all, sweeps_all = n[0].item(), n[1].item()
+        ms_max, events_all, sweeps_all = combine_over_ranks(ms, events, sweeps, dev)
     else:
         ms_max, events_all, sweeps_all = ms, float(events), float(sweeps)
     value = events_all / (ms_max * 1e-3)
@@ -496,6 +510,10 @@ def run_ours(args):
                        "parallelism": "replicas x%d" % world},
             "sweeps_per_s": sweeps_all / (ms_max * 1e-3),
             "events_per_sweep": events / max(sweeps, 1),
+            "per_sweep": {"chains": c.chains / max(sweeps, 1),
+                          "frozen_hits": c.frozen_hits / max(sweeps, 1),
+                          "wall_hits": c.wall_hits / max(sweeps, 1),
+                          "fp64_evals": c.fp64_evals / max(sweeps, 1)},
             "kernel_ms_per_sweep": {"bin": kt.bin_ms / max(sweeps, 1),
                                     "frame": kt.frame_ms / max(sweeps, 1),
                                     "chain": kt.phase_ms / max(sweeps, 1),
