@@ -96,6 +96,11 @@ extern "C" {
  * 2 = global memory (cells too large for shared memory), -1 = automatic
  * (default).  Changes only the speed, never the result. */
 #define ECMC_PARAM_FRAME_MODE 13
+/* 1 = replay the legs of a chain that rattles between two reflectors
+ * (frozen disks or walls) once its position after a reflection repeats bit
+ * for bit, without searching for candidates again (default 1); 0 = search on
+ * every leg.  Changes only the speed, never the result. */
+#define ECMC_PARAM_REPLAY 14
 
 #define ECMC_DIR_PM_AXIS_ALT 0
 #define ECMC_DIR_POS_ONLY 1
@@ -114,6 +119,10 @@ typedef struct {
   int64_t fp64_evals;  /* candidates evaluated in FP64 (FP32_GEOM screening)    */
   double sum_b;        /* sum over contacts of the separation along d           */
   double sum_disp;     /* sum over chains of the displacement budget ell        */
+  int64_t replayed_legs; /* reflection legs (frozen disk or wall) of a chain that
+                          * repeated the two legs before them bit for bit and were
+                          * replayed without a candidate search; included in
+                          * frozen_hits / wall_hits                             */
 } ecmc_counters_t;
 
 typedef struct {
@@ -140,7 +149,8 @@ typedef struct {
  * even and >= 2; w = L/cells_x and h = L/cells_y must exceed sigma), total
  * chain displacement ell, Philox seed `seed`.  Sec. 2 and Sec. 3.4.
  * Errors: ECMC_ERR_ARG (N not a perfect square or < 1, cells odd or < 2,
- * w or h <= sigma, L/k <= sigma so the lattice would overlap, ell < 0),
+ * w or h <= sigma, L/k <= sigma so the lattice would overlap, ell < 0,
+ * sigma outside [2^-40, 2^40] or L >= 2^40 sigma),
  * ECMC_ERR_CUDA, ECMC_ERR_OOM.  *out receives the handle (owned by the
  * library until ecmc_destroy). */
 ECMC_API int ecmc_create(ecmc_t* out, int64_t N, double L, double sigma, int cells_x, int cells_y,
@@ -304,6 +314,25 @@ ECMC_API int ecmc_chain_records(ecmc_t h, ecmc_chain_rec_t* out, int64_t n);
  * (GFLOP/s); the roofline denominators of the chain kernel.  No handle is
  * needed; takes a few milliseconds. */
 ECMC_API int ecmc_device_peaks(double* smem_gbs, double* fp64_gflops);
+
+/* The square root of the chain kernel's hit distance (Sec. 3.2: the
+ * distance to contact s = b - sqrt(sigma^2 - c^2) is formed in FP64 with the
+ * square root correctly rounded to nearest, as IEEE 754 sqrt).  The kernel
+ * takes it on the integer pipes (an FP32 reciprocal-square-root estimate,
+ * two fixed-point Newton steps, an exact integer remainder for the
+ * rounding); this entry evaluates that routine on n inputs:
+ *   where = 0  host memory, on the host, with the estimate replaced by the
+ *              exact reciprocal square root of the float seed times
+ *              (1 + rel_error), |rel_error| <= 2^-20; tests the Newton steps
+ *              and the rounding against estimates far worse than the SFU's
+ *   where = 1  device memory x, out; on the device exactly as the chain
+ *              kernel evaluates it; stream = cudaStream_t (NULL = legacy
+ *              default); returns after the kernel has finished
+ * Inputs that are not positive normal doubles give NaN.  Errors:
+ * ECMC_ERR_ARG (NULL pointers with n > 0, n < 0, bad where or rel_error),
+ * ECMC_ERR_CUDA. */
+ECMC_API int ecmc_sqrt_rn(const double* x, double* out, int64_t n, int where, double rel_error,
+                          void* stream);
 
 /* Size of the static scratch array behind ecmc_sweep_noalloc (16 MiB). */
 #define ECMC_NOALLOC_SCRATCH_BYTES (16u << 20)

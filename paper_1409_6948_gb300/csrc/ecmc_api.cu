@@ -225,7 +225,7 @@ int compute_layout(ecmc_ctx* h) {
   h->b.stage = nullptr;
   h->b.stage_bytes = 0;
   if (frame_build_smem(h->lay) > limit) {
-    h->b.stage_bytes = frame_build_smem(h->lay);
+    h->b.stage_bytes = frame_stage_bytes(h->lay);
     CK(cudaMalloc(&h->b.stage, h->b.stage_bytes * (size_t)h->b.A_total));
   }
   if ((!h->b.stage && configure_frame_build(h->lay)) ||
@@ -486,6 +486,10 @@ int setup_geom(const ecmc_replica_desc_t& d, Geom& g) {
   if (k * k != N) return fail(ECMC_ERR_ARG, "N must be a perfect square (lattice start)");
   if (!(d.L > 0.0) || !(d.sigma > 0.0) || !std::isfinite(d.L) || !std::isfinite(d.sigma))
     return fail(ECMC_ERR_ARG, "L and sigma must be positive");
+  // sigma^2 - c^2 and every frame coordinate stay normal numbers in FP64 and FP32
+  if (!(d.sigma >= std::ldexp(1.0, -40) && d.sigma <= std::ldexp(1.0, 40)) ||
+      !(d.L < std::ldexp(d.sigma, 40)))
+    return fail(ECMC_ERR_ARG, "sigma must lie in [2^-40, 2^40] and L below 2^40 sigma");
   if (d.cells_x < 2 || d.cells_y < 2 || (d.cells_x & 1) || (d.cells_y & 1))
     return fail(ECMC_ERR_ARG, "cells per side must be even and >= 2");
   if (!(d.L / d.cells_x > d.sigma) || !(d.L / d.cells_y > d.sigma))
@@ -530,6 +534,7 @@ int create_impl(ecmc_t* out, const ecmc_replica_desc_t* desc, int R) {
   ecmc_ctx* h = new (std::nothrow) ecmc_ctx();
   if (!h) return fail(ECMC_ERR_OOM, "host allocation failed");
   std::memset(&h->b, 0, sizeof(h->b));
+  h->b.replay = 1;
   auto bail = [&](int rc) {
     free_all(h);
     delete h;
@@ -715,6 +720,7 @@ void to_counters(const RunTotals& t, ecmc_counters_t* out) {
   out->fp64_evals = t.fp64_evals;
   out->sum_b = t.sum_b;
   out->sum_disp = t.sum_disp;
+  out->replayed_legs = t.replayed;
 }
 
 }  // namespace
@@ -863,6 +869,11 @@ int ecmc_set_param(ecmc_t h, int key, double v) {
       h->use_graph = v != 0.0;
       drop_graphs(h);
       return ECMC_OK;
+    case ECMC_PARAM_REPLAY:
+      if (v != 0.0 && v != 1.0) return fail(ECMC_ERR_ARG, "replay must be 0 or 1");
+      h->b.replay = (int)v;
+      drop_graphs(h);
+      return ECMC_OK;
     case ECMC_PARAM_FRAME_MODE: {
       const int m = (int)v;
       if ((double)m != v || m < -1 || m > 2) return fail(ECMC_ERR_ARG, "frame mode");
@@ -891,6 +902,7 @@ int ecmc_get_param(ecmc_t h, int key, double* v) {
     case ECMC_PARAM_WARPS_PER_BLOCK: *v = h->warps; break;
     case ECMC_PARAM_USE_GRAPH: *v = h->use_graph; break;
     case ECMC_PARAM_FRAME_MODE: *v = h->fmode; break;
+    case ECMC_PARAM_REPLAY: *v = h->b.replay; break;
     default: return fail(ECMC_ERR_ARG, "unknown parameter %d", key);
   }
   return ECMC_OK;
@@ -990,6 +1002,7 @@ int ecmc_counters(ecmc_t h, ecmc_counters_t* out) {
     s.frozen += v.frozen;
     s.walls += v.walls;
     s.fp64_evals += v.fp64_evals;
+    s.replayed += v.replayed;
   }
   to_counters(s, out);
   return ECMC_OK;
@@ -1259,6 +1272,23 @@ int ecmc_device_peaks(double* smem_gbs, double* fp64_gflops) {
   if (!smem_gbs || !fp64_gflops) return fail(ECMC_ERR_ARG, "NULL argument");
   if (probe_peaks(smem_gbs, fp64_gflops))
     return fail(ECMC_ERR_CUDA, "peak probe failed: %s", cudaGetErrorString(cudaGetLastError()));
+  return ECMC_OK;
+}
+
+int ecmc_sqrt_rn(const double* x, double* out, int64_t n, int where, double rel_error,
+                 void* stream) {
+  if (n < 0 || (n > 0 && (!x || !out))) return fail(ECMC_ERR_ARG, "bad arguments");
+  if (where == 0) {
+    if (!(std::fabs(rel_error) <= std::ldexp(1.0, -20)))
+      return fail(ECMC_ERR_ARG, "rel_error must be within 2^-20");
+    host_sqrt_rn(x, out, n, rel_error);
+    return ECMC_OK;
+  }
+  if (where != 1) return fail(ECMC_ERR_ARG, "where must be 0 (host) or 1 (device)");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (launch_sqrt_rn(x, out, n, s) || cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(ECMC_ERR_CUDA, "square-root kernel failed: %s",
+                cudaGetErrorString(cudaGetLastError()));
   return ECMC_OK;
 }
 

@@ -205,11 +205,11 @@ __global__ void __launch_bounds__(256) k_sweep_partials(const CellStats* __restr
                                                         const int2* __restrict__ chunks,
                                                         ChunkSums* __restrict__ out) {
   __shared__ double sd[2][8];
-  __shared__ long long sl[6][8];
+  __shared__ long long sl[7][8];
   const int2 ch = chunks[blockIdx.x];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   double b = 0.0, bw = 0.0;
-  long long v[6] = {0, 0, 0, 0, 0, 0};
+  long long v[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int c = ch.x + tid; c < ch.y; c += blockDim.x) {
     const CellStats s = cs[c];
     b += s.sum_b;
@@ -220,25 +220,26 @@ __global__ void __launch_bounds__(256) k_sweep_partials(const CellStats* __restr
     v[3] += s.walls;
     v[4] += s.fp64_evals;
     v[5] += s.chains;
+    v[6] += s.replayed;
   }
   b = warp_sum_d(b);
   bw = warp_sum_d(bw);
-  for (int q = 0; q < 6; ++q) v[q] = warp_sum_ll(v[q]);
+  for (int q = 0; q < 7; ++q) v[q] = warp_sum_ll(v[q]);
   if (lane == 0) {
     sd[0][wid] = b;
     sd[1][wid] = bw;
-    for (int q = 0; q < 6; ++q) sl[q][wid] = v[q];
+    for (int q = 0; q < 7; ++q) sl[q][wid] = v[q];
   }
   __syncthreads();
   if (tid == 0) {
     ChunkSums r;
     r.sum_b = 0.0;
     r.sum_b_w = 0.0;
-    for (int q = 0; q < 6; ++q) r.v[q] = 0;
+    for (int q = 0; q < 7; ++q) r.v[q] = 0;
     for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) {
       r.sum_b += sd[0][wv];
       r.sum_b_w += sd[1][wv];
-      for (int q = 0; q < 6; ++q) r.v[q] += sl[q][wv];
+      for (int q = 0; q < 7; ++q) r.v[q] += sl[q][wv];
     }
     out[blockIdx.x] = r;
   }
@@ -259,11 +260,11 @@ __global__ void k_sweep_end(const Geom* __restrict__ rg, SweepState* st,
   if (rep >= R) return;
   const Geom& g = rg[rep];
   double b = 0.0, bw = 0.0;
-  long long v[6] = {0, 0, 0, 0, 0, 0};
+  long long v[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int k = chunk_off[rep]; k < chunk_off[rep + 1]; ++k) {
     b += part[k].sum_b;
     bw += part[k].sum_b_w;
-    for (int q = 0; q < 6; ++q) v[q] += part[k].v[q];
+    for (int q = 0; q < 7; ++q) v[q] += part[k].v[q];
   }
   RunTotals& T = tot[rep];
   SweepState& S = st[rep];
@@ -278,6 +279,7 @@ __global__ void k_sweep_end(const Geom* __restrict__ rg, SweepState* st,
   T.walls += v[3];
   T.fp64_evals += v[4];
   T.chains += v[5];
+  T.replayed += v[6];
   T.sweeps += 1;
   if (history != nullptr && S.history_len < history_cap) {
     double* h = history + 2 * ((int64_t)rep * history_cap + S.history_len);

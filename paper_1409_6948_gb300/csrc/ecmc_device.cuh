@@ -140,3 +140,97 @@ __device__ __forceinline__ double wrap_half_i(double v, double L, double hL) {
 }
 
 }  // namespace ecmc
+
+namespace ecmc {
+
+// ---- correctly rounded FP64 square root on the integer pipes --------------
+// The hit distance of Sec. 3.2 needs sqrt(sigma^2 - c^2) rounded to nearest
+// as IEEE 754 defines it.  For a positive normal double x write
+// x = t 2^E with t = M 2^-52 in [1, 4) and E even (M = the significand,
+// doubled when the unbiased exponent is odd).  Then
+//   sqrt(x) = sqrt(N) 2^(E/2 - 52),   N = M 2^52 in [2^104, 2^106),
+// and sqrt(N) lies in [2^52, 2^53).  Starting from S0 = M Y 2^-31, where
+// Y ~ 2^31 / sqrt(t) is an estimate with relative error below 2^-20, two
+// Newton steps S <- S + (N - S^2) Y 2^-84 (the residual exact in 128 bits,
+// truncated before the product) leave |S - sqrt(N)| < 1.02 (the bound:
+// 2^33 after the estimate, 2^14.1 after the first step).  The exact
+// remainder N - S^2, which then fits 64 bits, moves S to floor(sqrt(N))
+// and decides the rounding: (S + 1/2)^2 = S^2 + S + 1/4 is never an integer,
+// so the nearest value is S + 1 exactly when N - S^2 > S, and there are no
+// ties.  A result S + 1 = 2^53 carries into the exponent by the addition.
+__host__ __device__ __forceinline__ uint64_t mulhi_u64(uint64_t a, uint64_t b) {
+#ifdef __CUDA_ARCH__
+  return __umul64hi(a, b);
+#else
+  return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+// Bit pattern of the float t (truncated to 24 bits): the input of the
+// reciprocal-square-root estimate.  u is the bit pattern of x.
+__host__ __device__ __forceinline__ uint32_t sqrt_seed_bits(uint64_t u) {
+  const uint32_t odd = ((uint32_t)(u >> 52) & 1u) ^ 1u;  // unbiased exponent odd
+  return ((127u + odd) << 23) | (uint32_t)((u >> 29) & 0x7fffffu);
+}
+
+// round(y 2^31) of a float y in [2^-2, 2) given by its bit pattern (exact:
+// y has 24 significant bits)
+__host__ __device__ __forceinline__ uint32_t fixed31_of(uint32_t yb) {
+  return (0x800000u | (yb & 0x7fffffu)) << ((yb >> 23) - 119u);
+}
+
+__host__ __device__ __forceinline__ double sqrt_rn_with(uint64_t u, uint32_t Y) {
+  const int e = (int)(u >> 52);
+  const int odd = (e & 1) ^ 1;
+  const uint64_t M = ((u & 0xfffffffffffffull) | 0x10000000000000ull) << odd;
+  const uint64_t Nhi = M >> 12, Nlo = M << 52;
+  uint64_t S = ((M >> 22) * (uint64_t)Y) >> 9;
+  {  // |N - S^2| < 2^87: use (N - S^2) >> 56
+    const uint64_t lo = S * S, hi = mulhi_u64(S, S);
+    const uint64_t dlo = Nlo - lo, dhi = Nhi - hi - (Nlo < lo ? 1u : 0u);
+    const int64_t D = (int64_t)((dhi << 8) | (dlo >> 56));
+    S += (uint64_t)((D * (int64_t)Y) >> 28);
+  }
+  {  // |N - S^2| < 2^68.1: use (N - S^2) >> 38
+    const uint64_t lo = S * S, hi = mulhi_u64(S, S);
+    const uint64_t dlo = Nlo - lo, dhi = Nhi - hi - (Nlo < lo ? 1u : 0u);
+    const int64_t D = (int64_t)((dhi << 26) | (dlo >> 38));
+    S += (uint64_t)((D * (int64_t)Y) >> 46);
+  }
+  // |N - S^2| < 2^55.1: the remainder modulo 2^64 is the remainder
+  int64_t rem = (int64_t)(Nlo - S * S);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const bool down = rem < 0;
+    S -= down ? 1u : 0u;
+    rem += down ? (int64_t)(2 * S + 1) : 0;
+  }
+  {
+    const bool up = rem > (int64_t)(2 * S);
+    rem -= up ? (int64_t)(2 * S + 1) : 0;
+    S += up ? 1u : 0u;
+  }
+  S += rem > (int64_t)S ? 1u : 0u;
+  const int64_t half = (int64_t)(e - 1023) >> 1;  // floor(E / 2)
+  const uint64_t bits = ((uint64_t)(half + 1022) << 52) + S;
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)bits);
+#else
+  double r;
+  __builtin_memcpy(&r, &bits, sizeof r);
+  return r;
+#endif
+}
+
+#ifdef __CUDACC__
+// The estimate Y from the SFU's reciprocal square root (relative error of
+// a few units in the last place of a float, far inside 2^-20).
+__device__ __forceinline__ double sqrt_rn(double x) {
+  const uint64_t u = (uint64_t)__double_as_longlong(x);
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(__uint_as_float(sqrt_seed_bits(u))));
+  return sqrt_rn_with(u, fixed31_of(__float_as_uint(y)));
+}
+#endif
+
+}  // namespace ecmc

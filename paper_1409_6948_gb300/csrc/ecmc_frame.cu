@@ -17,6 +17,13 @@
 
 namespace ecmc {
 
+// Head of the builder's dynamic shared memory: neighbour cells and their
+// prefix sums, then one 64-entry compaction buffer per warp.
+constexpr size_t kBuildAuxHead = 128;
+__host__ __device__ constexpr size_t build_aux_bytes(int threads) {
+  return kBuildAuxHead + (size_t)(threads / 32) * 64 * sizeof(int2);
+}
+
 struct BuildSmem {
   double* a64;
   double* b64;
@@ -35,7 +42,7 @@ __global__ void k_frame_build(const Geom* __restrict__ rg, const SweepState* __r
                               unsigned char* __restrict__ records, RecLayout lay,
                               unsigned char* __restrict__ stage, size_t stage_bytes, int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_nobj, s_nmem, s_overflow;
+  __shared__ int s_nobj, s_overflow, s_nnb;
   const int tid = threadIdx.x, bt = blockDim.x;
   const int a = blockIdx.x;  // global active cell
   const int rep = act_rep[a];
@@ -53,11 +60,19 @@ __global__ void k_frame_build(const Geom* __restrict__ rg, const SweepState* __r
   const double oy = st->sy + (double)cy * g.h;
   const double wl = g.w + sigma, hl = g.h + sigma;
 
+  // shared-memory part that never moves to global memory: the neighbour
+  // list and one compaction buffer of 64 entries per warp
+  const int lane = tid & 31, warp = tid >> 5;
+  int* s_nb = (int*)smem;      // distinct neighbour cells (<= 8)
+  int* s_pre = s_nb + 8;       // prefix sums of their disk counts (<= 9)
+  int2* wbuf = (int2*)(smem + kBuildAuxHead) + warp * 64;
+
   BuildSmem s;
   {
     // staging area: shared memory, or a global region per block when the
     // frame is too large for shared memory
-    unsigned char* p = stage ? stage + (size_t)blockIdx.x * stage_bytes : smem;
+    unsigned char* p = stage ? stage + (size_t)blockIdx.x * stage_bytes
+                             : smem + build_aux_bytes(bt);
     s.a64 = (double*)p; p += sizeof(double) * lay.cap_obj;
     s.b64 = (double*)p; p += sizeof(double) * lay.cap_obj;
     s.key = (int*)p; p += sizeof(int) * lay.cap_obj;
@@ -70,6 +85,26 @@ __global__ void k_frame_build(const Geom* __restrict__ rg, const SweepState* __r
   if (tid == 0) {
     s_nobj = 0;
     s_overflow = 0;
+    // distinct neighbour cells of the 3x3 block; their disks are visited as
+    // one index range [0, s_pre[nnb])
+    int nnb = 0;
+    for (int oyc = -1; oyc <= 1; ++oyc)
+      for (int oxc = -1; oxc <= 1; ++oxc) {
+        const int qx = ((cx + oxc) % g.cells_x + g.cells_x) % g.cells_x;
+        const int qy = ((cy + oyc) % g.cells_y + g.cells_y) % g.cells_y;
+        const int q = g.cell_off + qy * g.cells_x + qx;
+        if (q == c) continue;
+        bool dup = false;
+        for (int e = 0; e < nnb; ++e) dup |= (s_nb[e] == q);
+        if (!dup) s_nb[nnb++] = q;
+      }
+    int run = 0;
+    for (int e = 0; e < nnb; ++e) {
+      s_pre[e] = run;
+      run += min(cnt[s_nb[e]], cap);
+    }
+    for (int e = nnb; e <= 8; ++e) s_pre[e] = run;
+    s_nnb = nnb;
   }
   __syncthreads();
 
@@ -87,84 +122,103 @@ __global__ void k_frame_build(const Geom* __restrict__ rg, const SweepState* __r
     s.slot[i] = (int)q;
   }
   __syncthreads();
-  if (tid == 0) s_nmem = s_nobj;
-
-  // distinct neighbour cells of the 3x3 block
-  int nb[8];
-  int nnb = 0;
-  for (int oyc = -1; oyc <= 1; ++oyc)
-    for (int oxc = -1; oxc <= 1; ++oxc) {
-      const int qx = ((cx + oxc) % g.cells_x + g.cells_x) % g.cells_x;
-      const int qy = ((cy + oyc) % g.cells_y + g.cells_y) % g.cells_y;
-      const int q = g.cell_off + qy * g.cells_x + qx;
-      if (q == c) continue;
-      bool dup = false;
-      for (int e = 0; e < nnb; ++e) dup |= (nb[e] == q);
-      if (!dup) nb[nnb++] = q;
-    }
+  // every thread takes the member count before any thread appends a frozen
+  // image (blocks of several warps would otherwise race)
+  const int nmem = s_nobj;
+  __syncthreads();
 
   // frozen images within sigma of the cell rectangle.  An FP32 screen with a
   // margin well above its rounding error (|error| < 4 * 2^-23 L) discards the
   // disks that no image can bring near the cell; the others take the FP64
   // test, so the frame is exactly the one the FP64 test alone would build.
+  // The survivors of the screen are compacted per warp before the FP64 work,
+  // so that every FP64 instruction serves 32 candidates (an FP64 warp
+  // instruction costs the same whatever the number of active lanes).
   const float Lf = (float)L;
   const float oxf = to_float_trunc(ox), oyf = to_float_trunc(oy);
   const float mf = 8.0f * 1.1920929e-7f * Lf + 1e-6f;
   const float xlo = -(float)sigma - mf, xhi = (float)wl + mf;
   const float ylo = -(float)sigma - mf, yhi = (float)hl + mf;
-  for (int e = 0; e < nnb; ++e) {
-    const int n = nb[e];
-    const int nn = min(cnt[n], cap);
-    for (int k = tid; k < nn; k += bt) {
-      const int64_t q = (int64_t)n * cap + k;
-      const double xq = px[q], yq = py[q];
-      // offsets j*L (j = -2..2) of the unwrapped difference that the FP32
-      // screen keeps; an FP64 image k of the wrapped difference is offset
-      // j = k - (wrap shift), so the screen is tested per actual image
-      unsigned imgx = 0, imgy = 0;
-      {
-        const float rxf = to_float_trunc(xq) - oxf, ryf = to_float_trunc(yq) - oyf;
-        for (int j = -2; j <= 2; ++j) {
-          const float Xf = rxf + (float)j * Lf, Yf = ryf + (float)j * Lf;
-          imgx |= (Xf > xlo && Xf < xhi) ? (1u << (j + 2)) : 0u;
-          imgy |= (Yf > ylo && Yf < yhi) ? (1u << (j + 2)) : 0u;
+  const int nnb = s_nnb, T = s_pre[nnb];
+  const unsigned FULL = 0xffffffffu;
+
+  // FP64 placement of one screened disk: the wrapped difference, then the
+  // images the screen kept (offsets j*L of the unwrapped difference; an FP64
+  // image k of the wrapped difference is offset j = k - (wrap shift))
+  auto place = [&](int2 v) {
+    // neighbour e (3 bits) and bucket slot k (29 bits), packed unsigned
+    const unsigned ek = (unsigned)v.x;
+    const int e = (int)(ek >> 29), k = (int)(ek & ((1u << 29) - 1u));
+    const unsigned imgx = (unsigned)v.y & 31u, imgy = (unsigned)v.y >> 5;
+    const int64_t q = (int64_t)s_nb[e] * cap + k;
+    const double rx = px[q] - ox, ry = py[q] - oy;
+    const int swx = !dlt(rx, hL) ? 1 : (dlt(rx, -hL) ? -1 : 0);
+    const int swy = !dlt(ry, hL) ? 1 : (dlt(ry, -hL) ? -1 : 0);
+    // wrap_half(r, L): r - L, r + L (as r - (-L)) or r - 0
+    const double X0 = rx - (swx == 0 ? 0.0 : flip_if(L, swx < 0));
+    const double Y0 = ry - (swy == 0 ? 0.0 : flip_if(L, swy < 0));
+    const int id = pid[q];
+    for (int kx = -1; kx <= 1; ++kx) {
+      if (!(imgx & (1u << (kx - swx + 2)))) continue;
+      const double X = (kx == 0) ? X0 : X0 + flip_if(L, kx < 0);
+      if (!(dlt(-sigma, X) && dlt(X, wl))) continue;
+      for (int ky = -1; ky <= 1; ++ky) {
+        if (!(imgy & (1u << (ky - swy + 2)))) continue;
+        const double Y = (ky == 0) ? Y0 : Y0 + flip_if(L, ky < 0);
+        if (!(dlt(-sigma, Y) && dlt(Y, hl))) continue;
+        const int i = atomicAdd(&s_nobj, 1);
+        if (i >= lay.cap_obj) {
+          s_overflow = 1;
+          continue;
         }
-        if (!(imgx && imgy)) continue;
-      }
-      const double rx = xq - ox, ry = yq - oy;
-      const int swx = !dlt(rx, hL) ? 1 : (dlt(rx, -hL) ? -1 : 0);
-      const int swy = !dlt(ry, hL) ? 1 : (dlt(ry, -hL) ? -1 : 0);
-      const double X0 = swx > 0 ? rx - L : (swx < 0 ? rx + L : rx);  // wrap_half(rx, L)
-      const double Y0 = swy > 0 ? ry - L : (swy < 0 ? ry + L : ry);
-      const int id = pid[q];
-      for (int kx = -1; kx <= 1; ++kx) {
-        if (!(imgx & (1u << (kx - swx + 2)))) continue;
-        const double X = (kx == 0) ? X0 : (kx > 0 ? X0 + L : X0 - L);
-        if (!(dlt(-sigma, X) && dlt(X, wl))) continue;
-        for (int ky = -1; ky <= 1; ++ky) {
-          if (!(imgy & (1u << (ky - swy + 2)))) continue;
-          const double Y = (ky == 0) ? Y0 : (ky > 0 ? Y0 + L : Y0 - L);
-          if (!(dlt(-sigma, Y) && dlt(Y, hl))) continue;
-          const int i = atomicAdd(&s_nobj, 1);
-          if (i >= lay.cap_obj) {
-            s_overflow = 1;
-            continue;
-          }
-          s.a64[i] = axis == 0 ? X : Y;
-          s.b64[i] = axis == 0 ? Y : X;
-          s.key[i] = id * 16 + (kx + 1) * 3 + (ky + 1);
-          s.slot[i] = -1;
-        }
+        s.a64[i] = axis == 0 ? X : Y;
+        s.b64[i] = axis == 0 ? Y : X;
+        s.key[i] = id * 16 + (kx + 1) * 3 + (ky + 1);
+        s.slot[i] = -1;
       }
     }
+  };
+
+  int nbuf = 0;  // warp-uniform fill of this warp's buffer (< 32 between chunks)
+  for (int base = warp * 32; base < T; base += bt) {
+    const int idx = base + lane;
+    bool keep = false;
+    int2 ent = make_int2(0, 0);
+    if (idx < T) {
+      int e = 0;
+      while (e + 1 < nnb && s_pre[e + 1] <= idx) ++e;
+      const int k = idx - s_pre[e];
+      const int64_t q = (int64_t)s_nb[e] * cap + k;
+      const float rxf = to_float_trunc(px[q]) - oxf, ryf = to_float_trunc(py[q]) - oyf;
+      unsigned imgx = 0, imgy = 0;
+      for (int j = -2; j <= 2; ++j) {
+        const float Xf = rxf + (float)j * Lf, Yf = ryf + (float)j * Lf;
+        imgx |= (Xf > xlo && Xf < xhi) ? (1u << (j + 2)) : 0u;
+        imgy |= (Yf > ylo && Yf < yhi) ? (1u << (j + 2)) : 0u;
+      }
+      keep = imgx && imgy;
+      ent = make_int2((int)(((unsigned)e << 29) | (unsigned)k), (int)(imgx | (imgy << 5)));
+    }
+    const unsigned bal = __ballot_sync(FULL, keep);
+    if (keep) wbuf[nbuf + __popc(bal & ((1u << lane) - 1u))] = ent;
+    nbuf += __popc(bal);
+    __syncwarp();
+    if (nbuf >= 32) {
+      const int2 v = wbuf[lane];
+      __syncwarp();
+      if (lane < nbuf - 32) wbuf[lane] = wbuf[lane + 32];
+      nbuf -= 32;
+      __syncwarp();
+      place(v);
+    }
   }
+  if (lane < nbuf) place(wbuf[lane]);
   for (int k = tid; k <= lay.nbin; k += bt) s.hist[k] = 0;
   __syncthreads();
   if (s_overflow) {
     if (tid == 0) atomicCAS(err, DEV_OK, DEV_CAPACITY);
   }
   const int nobj = min(s_nobj, lay.cap_obj);
-  const int nmem = s_nmem;
 
   // members ranked by disk id (start disks are drawn by rank)
   for (int i = tid; i < nmem; i += bt) {
@@ -232,24 +286,36 @@ __global__ void k_frame_build(const Geom* __restrict__ rg, const SweepState* __r
   }
 }
 
-static size_t build_smem(const RecLayout& lay) {
-  return (sizeof(double) * 2 + sizeof(int) * 4) * (size_t)lay.cap_obj +
-         sizeof(int) * (size_t)lay.cap_mem + sizeof(int) * (size_t)(lay.nbin + 1) + 64;
+// the staging area of one cell (shared memory, or global memory per block)
+static size_t build_stage(const RecLayout& lay) {
+  return align16((sizeof(double) * 2 + sizeof(int) * 4) * (size_t)lay.cap_obj +
+                 sizeof(int) * (size_t)lay.cap_mem + sizeof(int) * (size_t)(lay.nbin + 1) + 64);
 }
 
-void launch_frame_build(const DevBufs& b, const RecLayout& lay, int colour_index,
-                        cudaStream_t s) {
-  const size_t sm = b.stage ? 0 : build_smem(lay);
+static int build_threads(const RecLayout& lay) {
   int bt = 32;
   if (lay.cap_obj > 256) bt = 128;
   if (lay.cap_obj > 1024) bt = 256;
   if (lay.cap_obj > 4096) bt = 1024;
+  return bt;
+}
+
+static size_t build_smem(const RecLayout& lay) {
+  return build_aux_bytes(build_threads(lay)) + build_stage(lay);
+}
+
+void launch_frame_build(const DevBufs& b, const RecLayout& lay, int colour_index,
+                        cudaStream_t s) {
+  const int bt = build_threads(lay);
+  const size_t sm = b.stage ? build_aux_bytes(bt) : build_smem(lay);
   k_frame_build<<<b.A_total, bt, sm, s>>>(b.rg, b.state, b.act_rep, b.cap, colour_index,
                                           b.px[b.cur], b.py[b.cur], b.pid[b.cur], b.count[b.cur],
                                           b.records, lay, b.stage, b.stage_bytes, b.err);
 }
 
-size_t frame_build_smem(const RecLayout& lay) { return align16(build_smem(lay)); }
+size_t frame_build_smem(const RecLayout& lay) { return build_smem(lay); }
+
+size_t frame_stage_bytes(const RecLayout& lay) { return build_stage(lay); }
 
 // largest amount the kernel can have, for the same reason as configure_phase
 int configure_frame_build(const RecLayout& lay) {

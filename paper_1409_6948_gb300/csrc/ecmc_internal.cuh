@@ -46,19 +46,19 @@ struct SweepState {
 struct CellStats {
   double sum_b;     // contact sum of the cell's chains, in chain order
   int events, lifts, frozen, walls;
-  int fp64_evals, chains, n_mem, pad;
+  int fp64_evals, chains, n_mem, replayed;
 };
 
 // Partial sums of one chunk of a replica's cells (end-of-sweep reduction).
 struct ChunkSums {
   double sum_b, sum_b_w;
-  long long v[6];  // events, lifts, frozen, walls, fp64_evals, chains
+  long long v[7];  // events, lifts, frozen, walls, fp64_evals, chains, replayed
 };
 
 // Running totals (device).
 struct RunTotals {
   double sum_b, sum_disp, sum_b_w, sum_disp_w;
-  long long sweeps, chains, events, lifts, frozen, walls, fp64_evals;
+  long long sweeps, chains, events, lifts, frozen, walls, fp64_evals, replayed;
 };
 
 struct ChainRec {
@@ -160,6 +160,7 @@ struct DevBufs {
   const int* chunk_off;    // [R + 1] first chunk of every replica
   ChunkSums* partials;     // [n_chunks]
   int n_chunks;
+  int replay;              // 1 = replay repeating reflection legs (chain kernel)
   int R, C_total, A_total, cap;
   int64_t N_total;
 };
@@ -183,9 +184,12 @@ void launch_min_dist(const Geom& g, const DevBufs& b, double rcut, unsigned long
 void launch_gr(const Geom& g, const DevBufs& b, double dr, int nbins, unsigned long long* counts,
                cudaStream_t s);
 size_t frame_build_smem(const RecLayout& lay);
+size_t frame_stage_bytes(const RecLayout& lay);
 int configure_frame_build(const RecLayout& lay);
 int configure_phase(const RecLayout& lay, int tpc, int warps, int fmode);
 int probe_peaks(double* smem_gbs, double* fp64_gflops);
+int launch_sqrt_rn(const double* x, double* out, int64_t n, cudaStream_t s);
+void host_sqrt_rn(const double* x, double* out, int64_t n, double rel_error);
 // fmode: 0 = whole frame in shared memory, 1 = FP64 coordinates in global
 // memory, 2 = whole frame in global memory
 size_t phase_smem_bytes(const RecLayout& lay, int warps_per_block, int fmode = 0);

@@ -2,6 +2,11 @@
 // pair-correlation histogram of Sec. 2 (ordered pairs, bins
 // [sigma + i dr, sigma + (i+1) dr)) and the smallest pair distance (the
 // no-overlap invariant).  Both walk the cell buckets of the last binning.
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <limits>
+
 #include "ecmc_device.cuh"
 #include "ecmc_internal.cuh"
 
@@ -131,6 +136,43 @@ __global__ void k_probe_fp64(double* out, int iters) {
   }
   const double s = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
   if (s == 123.456) out[0] = s;
+}
+
+// The chain kernel's square root on an array: positive normal inputs only,
+// anything else gives NaN.
+__global__ void k_sqrt_rn(const double* __restrict__ x, double* __restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t u = (uint64_t)__double_as_longlong(x[i]);
+  const uint32_t e = (uint32_t)(u >> 52);
+  out[i] = (e >= 1u && e <= 2046u) ? sqrt_rn(x[i]) : __longlong_as_double(0x7ff8000000000000ll);
+}
+
+int launch_sqrt_rn(const double* x, double* out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return 0;
+  const int64_t blocks = (n + 255) / 256;
+  if (blocks > INT_MAX) return -1;
+  k_sqrt_rn<<<(unsigned)blocks, 256, 0, s>>>(x, out, n);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// Host evaluation of the same routine with a chosen estimate: the exact
+// reciprocal square root of the float seed times (1 + rel_error).
+void host_sqrt_rn(const double* x, double* out, int64_t n, double rel_error) {
+  for (int64_t i = 0; i < n; ++i) {
+    uint64_t u;
+    std::memcpy(&u, &x[i], sizeof u);
+    const uint32_t e = (uint32_t)(u >> 52);
+    if (e < 1u || e > 2046u) {
+      out[i] = std::numeric_limits<double>::quiet_NaN();
+      continue;
+    }
+    const uint32_t tb = sqrt_seed_bits(u);
+    float tf;
+    std::memcpy(&tf, &tb, sizeof tf);
+    const double y = (1.0 / std::sqrt((double)tf)) * (1.0 + rel_error);
+    out[i] = sqrt_rn_with(u, (uint32_t)std::llround(std::ldexp(y, 31)));
+  }
 }
 
 int probe_peaks(double* smem_gbs, double* fp64_gflops) {

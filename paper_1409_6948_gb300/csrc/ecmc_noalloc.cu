@@ -69,7 +69,8 @@ extern "C" int ecmc_sweep_noalloc(double* xy, int64_t N, double L, double sigma,
   if (!xy || N < 1 || N >= (int64_t(1) << 27) || !(L > 0.0) || !(sigma > 0.0) ||
       !std::isfinite(L) || cells_x < 2 || cells_y < 2 || (cells_x & 1) || (cells_y & 1) ||
       !(L / cells_x > sigma) || !(L / cells_y > sigma) || !(ell >= 0.0) || !std::isfinite(ell) ||
-      n_m < 1 || t0 < 0 || n_sweeps < 0)
+      n_m < 1 || t0 < 0 || n_sweeps < 0 || !(sigma >= std::ldexp(1.0, -40)) ||
+      !(sigma <= std::ldexp(1.0, 40)) || !(L < std::ldexp(sigma, 40)))
     return ECMC_ERR_ARG;
 
   // geometry and capacities, as for a handle
@@ -159,6 +160,7 @@ extern "C" int ecmc_sweep_noalloc(double* xy, int64_t N, double L, double sigma,
   if (scratch_address(&base) != ECMC_OK) return ECMC_ERR_CUDA;
   DevBufs b;
   std::memset(&b, 0, sizeof(b));
+  b.replay = 1;
   for (int i = 0; i < 2; ++i) {
     b.px[i] = reinterpret_cast<double*>(base + o_px[i]);
     b.py[i] = reinterpret_cast<double*>(base + o_py[i]);

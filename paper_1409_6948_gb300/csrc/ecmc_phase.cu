@@ -45,9 +45,11 @@ struct Frame {
 // written as the general expressions reduce for d = (+-1, 0):
 //   b = (x_j - x_m) . d,  c = (x_j - x_m) x d,  hit iff b > 0 and c^2 < sigma^2,
 //   s = max(0, b - sqrt(sigma^2 - c^2)).
-// The arithmetic is exactly the reference's; comparisons and sign changes run
-// on the integer pipes (see ecmc_device.cuh), and the square root is taken of
-// a positive placeholder when the candidate misses, so there is no branch.
+// The arithmetic is exactly the reference's; comparisons, sign changes and
+// the correctly rounded square root run on the integer pipes (ecmc_device.cuh),
+// and the square root is taken of a positive placeholder when the candidate
+// misses, so there is no branch.  sigma^2 - c^2 > 0 is a normal number for
+// every hit (sigma is restricted to [2^-40, 2^40]), as sqrt_rn requires.
 __device__ __forceinline__ bool exact_hit(double aj, double bj, double P, double Q, int sg,
                                           double sig2, double& s, double& b) {
   const double da = aj - P;
@@ -58,7 +60,7 @@ __device__ __forceinline__ bool exact_hit(double aj, double bj, double P, double
   const double c2 = db * db;
   const bool hit = ahead && lt_nn(c2, sig2);
   const double x = sig2 - c2;
-  const double sq = sqrt(hit ? x : 1.0);
+  const double sq = sqrt_rn(hit ? x : 1.0);
   s = clamp0(b - sq);
   return hit;
 }
@@ -81,7 +83,7 @@ __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
                                                int n_active, double* __restrict__ px,
                                                double* __restrict__ py, CellStats* __restrict__ cs,
                                                ChainRec* __restrict__ recs, int rec_stride,
-                                               int* err) {
+                                               int replay, int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int CPW = 32 / TPC;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -161,6 +163,12 @@ __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
   float P32 = 0.f, Q32 = 0.f;
   int64_t n_iter = 0;
   int ch_events = 0, ch_walls = 0, start_key = 0;
+  // the reflection leg before the current one: start position, step, the
+  // contact sum it added, wall or frozen disk; n_refl counts the consecutive
+  // reflection legs just completed
+  double Pm1 = 0.0, s_m1 = 0.0, add_m1 = 0.0;
+  bool wall_m1 = false;
+  int n_refl = 0, n_replayed = 0;
   bool done = (!valid) || nmem == 0;
 
   for (;;) {
@@ -184,6 +192,7 @@ __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
         n_iter = 0;
         ch_events = 0;
         ch_walls = 0;
+        n_refl = 0;
         active = true;
         ++k;
         ++n_chains;
@@ -385,11 +394,51 @@ __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
         Q32 = f.b32[m * CPW + gi];
         f.touched[m * CPW + gi] = 1;
       } else {
+        const double Pk = P;
         P = Pnew;
         P32 = P32n;
-        // frozen disk or wall: the chain turns back along its axis
-        if (!is_end) sg = -sg;
+        if (!is_end) {
+          // frozen disk or wall: the chain turns back along its axis
+          sg = -sg;
+          if (replay && n_refl > 0 && dbits(Pnew) == dbits(Pm1)) {
+            // The chain is back, bit for bit, where the previous reflection
+            // leg started, moving the same way: between two reflectors
+            // (frozen disks or walls) nothing else moves, so the legs
+            // repeat exactly -- same step, same contact -- for as long as
+            // the budget exceeds the step.  Replay them with their
+            // subtractions only; the full search resumes for the last leg.
+            const double sA = s_m1, aA = add_m1, PA = Pk;  // leg from Pnew
+            const bool wA = wall_m1;
+            const double sB = step, aB = addb, PB = Pnew;  // leg from Pk
+            const bool wB = is_wall;
+            for (int leg = 0;; leg ^= 1) {
+              const double sl = leg ? sB : sA;
+              if (n_iter >= kMaxEventsPerChain || le_nn(r, sl)) break;
+              const bool wl = leg ? wB : wA;
+              r = r - sl;
+              n_iter += 1;
+              n_replayed += 1;
+              n_walls += wl ? 1 : 0;
+              ch_walls += wl ? 1 : 0;
+              n_events += wl ? 0 : 1;
+              ch_events += wl ? 0 : 1;
+              n_frozen += wl ? 0 : 1;
+              if (!wl) sum_b += leg ? aB : aA;
+              P = leg ? PB : PA;
+              sg = -sg;
+            }
+            P32 = to_float_trunc(P);
+            n_refl = 0;
+          } else {
+            Pm1 = Pk;
+            s_m1 = step;
+            add_m1 = addb;
+            wall_m1 = is_wall;
+            n_refl += 1;
+          }
+        }
       }
+      if (is_lift) n_refl = 0;
       end_chain = is_end;
     }
     if (end_chain) {
@@ -431,7 +480,7 @@ __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
     s.fp64_evals = n_fp64;
     s.chains = n_chains;
     s.n_mem = nmem;
-    s.pad = 0;
+    s.replayed = n_replayed;
     cs[c] = s;
   }
 }
@@ -454,7 +503,7 @@ static int launch_t(const DevBufs& b, const RecLayout& lay, int colour_index, in
   k_phase<TPC, SCREEN, FM><<<blocks, 32 * warps, sm, s>>>(                                 \
       b.rg, b.state, b.act_rep, colour_index, b.records, b.gtouch, lay, n_active,          \
       b.px[b.cur], b.py[b.cur], b.cell_stats, records_on ? b.chain_recs : nullptr,         \
-      b.rec_stride, b.err)
+      b.rec_stride, b.replay, b.err)
   if (b.fmode == 2) ECMC_PHASE(2);
   else if (b.fmode == 1) ECMC_PHASE(1);
   else ECMC_PHASE(0);

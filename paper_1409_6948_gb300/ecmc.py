@@ -31,6 +31,7 @@ PARAM_RECORD_CHAINS = 10
 PARAM_WARPS_PER_BLOCK = 11
 PARAM_USE_GRAPH = 12
 PARAM_FRAME_MODE = 13
+PARAM_REPLAY = 14
 
 DIR_PM_AXIS_ALT = 0
 DIR_POS_ONLY = 1
@@ -41,7 +42,8 @@ PREC_FP32_GEOM = 1
 class Counters(C.Structure):
     _fields_ = [("sweeps", C.c_int64), ("chains", C.c_int64), ("events", C.c_int64),
                 ("lifts", C.c_int64), ("frozen_hits", C.c_int64), ("wall_hits", C.c_int64),
-                ("fp64_evals", C.c_int64), ("sum_b", C.c_double), ("sum_disp", C.c_double)]
+                ("fp64_evals", C.c_int64), ("sum_b", C.c_double), ("sum_disp", C.c_double),
+                ("replayed_legs", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -113,6 +115,8 @@ _SIGS = {
     "ecmc_kernel_times": (C.c_int, [_H, C.POINTER(Timing)]),
     "ecmc_chain_records": (C.c_int, [_H, C.c_void_p, C.c_int64]),
     "ecmc_device_peaks": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "ecmc_sqrt_rn": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_double,
+                               C.c_void_p]),
     "ecmc_sweep_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_double, C.c_int,
                                      C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_uint64,
                                      C.c_int64, C.c_int64, C.c_void_p]),
@@ -377,3 +381,30 @@ def device_peaks():
     a, b = C.c_double(), C.c_double()
     _check(load().ecmc_device_peaks(C.byref(a), C.byref(b)), "ecmc_device_peaks")
     return a.value, b.value
+
+
+def sqrt_rn(x, rel_error=None, stream=None):
+    """The chain kernel's correctly rounded square root on an array.
+
+    A float64 numpy array is evaluated on the host with the reciprocal
+    square-root estimate perturbed by `rel_error` (|rel_error| <= 2^-20); a
+    CUDA float64 tensor is evaluated on its device exactly as the kernel does.
+    Returns an array (or tensor) of the same shape.
+    """
+    if isinstance(x, np.ndarray):
+        xa = np.ascontiguousarray(x, dtype=np.float64)
+        out = np.empty_like(xa)
+        _check(load().ecmc_sqrt_rn(xa.ctypes.data, out.ctypes.data, xa.size, 0,
+                                   float(rel_error or 0.0), None), "ecmc_sqrt_rn")
+        return out
+    if rel_error is not None:
+        raise ValueError("rel_error applies to the host evaluation only")
+    if not (x.is_cuda and x.dtype.is_floating_point and x.element_size() == 8):
+        raise TypeError("expected a float64 numpy array or CUDA tensor")
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    xc = x.contiguous()
+    out = xc.new_empty(xc.shape)
+    _check(load().ecmc_sqrt_rn(C.c_void_p(xc.data_ptr()), C.c_void_p(out.data_ptr()),
+                               xc.numel(), 1, 0.0, C.c_void_p(stream or 0)), "ecmc_sqrt_rn")
+    return out

@@ -26,6 +26,7 @@ import paper_1409_6948_gb300 as P  # noqa: E402
 from paper_1409_6948_gb300 import ecmc as E  # noqa: E402
 
 REL = 1e-12
+LAST = {}  # counters of the most recent run_pair, for tests that inspect them
 
 
 def make(N, eta, cells_x, cells_y, ell, nm, seed, tpc=0, prec=1, dir_mode=0, records=False,
@@ -79,6 +80,7 @@ def run_pair(N, eta, cells_x, cells_y, ell, nm, seed, n_sweeps, records=True, **
             assert np.array_equal(gr["walls"][ran], orr["walls"][ran]), "walls, sweep %d" % s
         assert_positions_equal(g, x, y, L)
     c = g.counters()
+    LAST["counters"] = c.as_dict()
     assert c.events == st_total.events and c.lifts == st_total.lifts
     assert c.frozen_hits == st_total.frozen_hits and c.wall_hits == st_total.wall_hits
     assert c.chains == st_total.chains and c.sweeps == n_sweeps
@@ -148,6 +150,29 @@ def test_large_system_full_size_two_sweeps():
     # screening); every position compared after each sweep
     N = 1048576
     run_pair(N, 0.72, 128, 128, 8.0, 1, 3, 2, records=False)
+
+
+def test_replayed_reflections_at_the_paper_parameters():
+    # 1024^2 disks at eta = 0.72 with the paper's cells, ell and n_m after a
+    # melt: the regime where disks rattle between frozen neighbours for
+    # hundreds of legs; every position compared after each sweep
+    N, eta = 1048576, 0.72
+    L = W.box_side(N, eta)
+    par = E.suggest_parameters(N, L)
+    g, p, _ = make(N, eta, par["cells_x"], par["cells_y"], par["ell"], par["n_m"], 8)
+    x, y = W.square_lattice(N, L)
+    oracle.sweeps(p, x, y, 0, 6)
+    g.sweep(6)
+    assert_positions_equal(g, x, y, L)
+    st, _ = oracle.sweeps(p, x, y, 6, 2)
+    g.reset_stats()
+    g.sweep(2)
+    assert_positions_equal(g, x, y, L)
+    c = g.counters()
+    assert c.events == st.events and c.frozen_hits == st.frozen_hits
+    assert c.wall_hits == st.wall_hits and c.lifts == st.lifts
+    assert c.replayed_legs > 0, c.replayed_legs
+    g.close()
 
 
 def test_gr_counts_and_min_distance_match():
@@ -234,6 +259,22 @@ def test_graph_replay_equals_direct_launches():
 ])
 def test_large_cells(N, eta, cells, ell, nm):
     run_pair(N, eta, cells, cells, ell, nm, 5, 2)
+
+
+@pytest.mark.parametrize("replay", [0, 1])
+def test_replay_switch_gives_identical_trajectories(replay):
+    # 1024 disks, 8x8 cells, ell = 6 sigma: chains cross whole cells and
+    # rattle between walls and frozen disks; both settings match the oracle
+    g, p, L = make(1024, 0.70, 8, 8, 6.0, 2, 13)
+    g.set_param(E.PARAM_REPLAY, replay)
+    x, y = W.square_lattice(1024, L)
+    st, _ = oracle.sweeps(p, x, y, 0, 12)
+    g.sweep(12)
+    assert_positions_equal(g, x, y, L)
+    c = g.counters()
+    assert c.events == st.events and c.wall_hits == st.wall_hits
+    assert (c.replayed_legs > 0) == bool(replay)
+    g.close()
 
 
 @pytest.mark.parametrize("fmode", [0, 1, 2])
