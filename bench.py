@@ -34,7 +34,19 @@ UNIT = "events/s"
 # candidates in the region the first hit can come from (about 2 disks at
 # eta = 0.72) read as FP64 coordinates (2 x 16 B), plus the active disk's
 # coordinates read and written (16 B)
-BYTES_PER_EVENT = 48.0
+# Roofline of the chain kernel: the FP64 pipe.  Each iteration of a chain's
+# event loop (a contact, a wall reflection or the end of the budget) needs, in
+# the method's exact arithmetic, 10 FP64 operations: the hit test of the first
+# candidate (x_j - x_m, y_j - y_m, c^2, sigma^2 - c^2, b - sqrt), the wall
+# distance, the new position, the new budget and the contact sum (b - s and
+# its accumulation).  The square root runs on the integer pipes.
+FP64_OPS_PER_ITERATION = 10
+# FP64 lanes per SM and clock on GB300 (the dfma peak ncu reports per SM)
+FP64_LANES_PER_SM_CLK = 2
+# DRAM bytes (read + write) of one k_phase launch at the large workload with the
+# paper's parameters, melted, TPC 8, frames in shared memory, from
+# `ncu --set full` (profiles/k_phase_large_melted.md); None once the kernel changes
+K_PHASE_DRAM_BYTES = 39.11e6
 
 
 def parse():
@@ -486,9 +498,13 @@ def run_ours(args):
     line = None
     if rank == 0:
         phase_avg_ms = kt.phase_ms / max(kt.phase_launches, 1)
-        bytes_per_launch = BYTES_PER_EVENT * events / max(kt.phase_launches, 1)
-        smem_gbs, fp64_gflops = P.ecmc.device_peaks()
-        achieved = bytes_per_launch / (phase_avg_ms * 1e-3) / 1e9
+        iters = c.events + c.wall_hits + c.chains
+        ops_per_launch = FP64_OPS_PER_ITERATION * iters / max(kt.phase_launches, 1)
+        achieved = ops_per_launch / (phase_avg_ms * 1e-3) / 1e9
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        sm_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+        fp64_peak = FP64_LANES_PER_SM_CLK * n_sm * sm_mhz * 1e6 / 1e9
+        _, fp64_probe = P.ecmc.device_peaks()
         cpu = None
         if not args.skip_cpu and descs is None:
             cpu = cpu_baseline(w, cells, ell, nm, args.cpu_seconds, melt_sweeps(args))
@@ -518,12 +534,16 @@ def run_ours(args):
                                     "frame": kt.frame_ms / max(sweeps, 1),
                                     "chain": kt.phase_ms / max(sweeps, 1),
                                     "reduce": kt.other_ms / max(sweeps, 1)},
-            "roofline": {"kernel": "k_phase (chain kernel)", "bound": "smem",
-                         "achieved": achieved, "peak": smem_gbs, "unit": "GB/s",
-                         "frac": achieved / smem_gbs, "traffic": None,
-                         "bytes_per_event": BYTES_PER_EVENT,
-                         "peak_source": "ecmc_device_peaks shared-memory probe (measured)",
-                         "fp64_peak_gflops": fp64_gflops},
+            "roofline": {"kernel": "k_phase (chain kernel)", "bound": "alu",
+                         "achieved": achieved, "peak": fp64_peak, "unit": "GFLOP/s",
+                         "frac": achieved / fp64_peak,
+                         "traffic": K_PHASE_DRAM_BYTES if tpc == 8 and not descs else None,
+                         "pipe": "fp64", "fp64_ops_per_iteration": FP64_OPS_PER_ITERATION,
+                         "iterations_per_launch": iters / max(kt.phase_launches, 1),
+                         "launch_ms": phase_avg_ms,
+                         "peak_source": "2 FP64 lanes/clk/SM x %d SMs x %.0f MHz (unit counts)"
+                                        % (n_sm, sm_mhz),
+                         "fp64_probe_gflops": fp64_probe},
             # per sweep: draws, binning, 4 x (frame builder, chain kernel), chunk
             # sums, end of sweep
             "gpu_launches": 12 * args.steps * world,
