@@ -27,6 +27,20 @@
 
 namespace ecmc {
 
+// Legs of the current chain kept for cycle detection (a power of two): a
+// chain that rattles through a row of up to kHist/2 disks between two
+// reflectors repeats with a period of at most kHist legs.
+constexpr int kHist = 16;
+constexpr size_t kHistLegBytes = 32;  // P, step, contact sum (FP64); disk, flags
+
+struct LegHist {
+  double* P;     // start position along the axis
+  double* step;  // length of the leg
+  double* addb;  // contribution to the contact sum (contacts)
+  int* m;        // active disk (frame index)
+  int* flags;    // bit 0: moving in -d; bit 1: frozen disk; bit 2: wall; 0 in both: lift
+};
+
 struct Frame {
   const int* bst;
   const int* mrank;
@@ -69,6 +83,85 @@ __device__ __forceinline__ bool better(double s, int key, double bs, int bkey) {
   return s < bs || (s == bs && key < bkey);
 }
 
+// Cycle replay.  Called after a reflection, with the state (m, sg, P) the next
+// leg starts from.  If for some even K <= kHist the configuration equals the
+// one K legs earlier -- the same active disk, direction and position bit for
+// bit, and every other disk that moved in those K legs back where it was --
+// then nothing else distinguishes the two moments (frozen disks and walls do
+// not move, the decision depends on the budget only through its end), so the
+// next legs repeat those K legs exactly, step for step, as long as the budget
+// exceeds the step.  They are replayed from the history with one subtraction
+// each; at the leg where the budget runs out the disks are put where the
+// recorded legs left them and the full search resumes (and ends the chain).
+__device__ __forceinline__ void replay_cycle(const Frame& f, const LegHist& hs, int gi,
+                                             int& n_leg, int& m, int& sg, double& P,
+                                             float& P32, double& Q, float& Q32, double& r,
+                                             int64_t& n_iter, double& sum_b, int& n_events,
+                                             int& n_lifts, int& n_frozen, int& n_walls,
+                                             int& ch_events, int& ch_walls, int& n_replayed) {
+  const int CPW = f.cpw;
+  int Kf = 0;
+  for (int K = 2; K <= kHist && K <= n_leg; K += 2) {
+    const int s0 = ((n_leg - K) & (kHist - 1)) * CPW + gi;
+    if (hs.m[s0] != m || dbits(hs.P[s0]) != dbits(P) || ((hs.flags[s0] & 1) != (sg < 0 ? 1 : 0)))
+      continue;
+    bool same = true;
+    for (int i = n_leg - K; i < n_leg && same; ++i) {
+      const int si = (i & (kHist - 1)) * CPW + gi;
+      const int D = hs.m[si];
+      if (D == m) continue;
+      bool first = true;  // D's first leg in the window starts where D was
+      for (int j = n_leg - K; j < i; ++j) first &= (hs.m[(j & (kHist - 1)) * CPW + gi] != D);
+      if (first) same = dbits(f.a64[D * CPW + gi]) == dbits(hs.P[si]);
+    }
+    if (same) {
+      Kf = K;
+      break;
+    }
+  }
+  if (Kf == 0) return;
+  const int base = n_leg - Kf;
+  int o = 0;
+  for (;;) {
+    const int si = ((base + o) & (kHist - 1)) * CPW + gi;
+    const double sl = hs.step[si];
+    if (n_iter >= kMaxEventsPerChain || le_nn(r, sl)) break;
+    const int fl = hs.flags[si];
+    const bool wall = (fl & 4) != 0, frozen = (fl & 2) != 0;
+    r = r - sl;
+    n_iter += 1;
+    n_replayed += 1;
+    n_walls += wall ? 1 : 0;
+    ch_walls += wall ? 1 : 0;
+    n_events += wall ? 0 : 1;
+    ch_events += wall ? 0 : 1;
+    n_frozen += frozen ? 1 : 0;
+    n_lifts += (wall || frozen) ? 0 : 1;
+    if (!wall) sum_b += hs.addb[si];
+    o = (o + 1 == Kf) ? 0 : o + 1;
+  }
+  // the configuration at offset o of the cycle: disks that stopped in the
+  // first o legs stand where those legs left them
+  for (int i = 0; i < o; ++i) {
+    const int si = ((base + i) & (kHist - 1)) * CPW + gi;
+    const int fl = hs.flags[si];
+    if ((fl & 6) == 0) {
+      const double end = hs.P[si] + flip_if(hs.step[si], (fl & 1) != 0);
+      const int D = hs.m[si];
+      f.a64[D * CPW + gi] = end;
+      f.a32[D * CPW + gi] = to_float_trunc(end);
+    }
+  }
+  const int so = ((base + o) & (kHist - 1)) * CPW + gi;
+  m = hs.m[so];
+  sg = (hs.flags[so] & 1) ? -1 : 1;
+  P = hs.P[so];
+  P32 = to_float_trunc(P);
+  Q = f.b64[m * CPW + gi];
+  Q32 = f.b32[m * CPW + gi];
+  n_leg = 0;
+}
+
 // FMODE 0: the warp copies its group's whole record into shared memory;
 // FMODE 1: only the light part (FP32 coordinates, keys, strips, members), the
 // FP64 coordinates are read and written in place in global memory (more
@@ -93,16 +186,20 @@ __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
 
   const size_t rec_bytes = lay.bytes;
   const size_t t_bytes = align16((size_t)lay.cap_obj * CPW);
+  const size_t h_bytes = kHistLegBytes * kHist * CPW;
   unsigned char* const grec = records + (size_t)G * rec_bytes;
   unsigned char* base;
   unsigned char* tbase;
+  unsigned char* hbase;
   if (FMODE == 2) {
     base = grec;
     tbase = gtouch + (size_t)G * t_bytes;
+    hbase = smem + (size_t)warp * h_bytes;
   } else {
     const size_t copy = FMODE == 1 ? lay.light_bytes : rec_bytes;
-    base = smem + (size_t)warp * (copy + t_bytes);
+    base = smem + (size_t)warp * (copy + t_bytes + h_bytes);
     tbase = base + copy;
+    hbase = tbase + t_bytes;
     const int4* src = reinterpret_cast<const int4*>(grec);
     int4* dst = reinterpret_cast<int4*>(base);
     const int n16 = (int)(copy / 16);
@@ -128,6 +225,12 @@ __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
   f.info = (const int*)(base + lay.off_info);
   f.touched = tbase;
   const int* hdr = (const int*)(base + lay.off_hdr);
+  LegHist hs;  // interleaved [leg][group] like the frame
+  hs.P = (double*)hbase;
+  hs.step = hs.P + kHist * CPW;
+  hs.addb = hs.step + kHist * CPW;
+  hs.m = (int*)(hs.addb + kHist * CPW);
+  hs.flags = hs.m + kHist * CPW;
 
   const int gi = lane / TPC, sub = lane - gi * TPC;
   const int a = G * CPW + gi;  // global active cell of this lane group
@@ -163,12 +266,8 @@ __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
   float P32 = 0.f, Q32 = 0.f;
   int64_t n_iter = 0;
   int ch_events = 0, ch_walls = 0, start_key = 0;
-  // the reflection leg before the current one: start position, step, the
-  // contact sum it added, wall or frozen disk; n_refl counts the consecutive
-  // reflection legs just completed
-  double Pm1 = 0.0, s_m1 = 0.0, add_m1 = 0.0;
-  bool wall_m1 = false;
-  int n_refl = 0, n_replayed = 0;
+  int n_leg = 0;  // legs of the current chain recorded in the history
+  int n_replayed = 0;
   bool done = (!valid) || nmem == 0;
 
   for (;;) {
@@ -192,7 +291,7 @@ __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
         n_iter = 0;
         ch_events = 0;
         ch_walls = 0;
-        n_refl = 0;
+        n_leg = 0;
         active = true;
         ++k;
         ++n_chains;
@@ -383,6 +482,17 @@ __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
       n_walls += is_wall ? 1 : 0;
       ch_walls += is_wall ? 1 : 0;
       n_iter += (is_contact || is_wall) ? 1 : 0;
+      if (replay && !is_end) {
+        // every lane of the group writes the same values, so each lane reads
+        // back its own writes
+        const int hl = (n_leg & (kHist - 1)) * CPW + gi;
+        hs.P[hl] = P;
+        hs.step[hl] = step;
+        hs.addb[hl] = addb;
+        hs.m[hl] = m;
+        hs.flags[hl] = (sg < 0 ? 1 : 0) | (is_lift ? 0 : (is_wall ? 4 : 2));
+        ++n_leg;
+      }
       if (is_lift) {
         // the hit member carries on with the rest of the budget
         f.a64[m * CPW + gi] = Pnew;
@@ -394,51 +504,16 @@ __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
         Q32 = f.b32[m * CPW + gi];
         f.touched[m * CPW + gi] = 1;
       } else {
-        const double Pk = P;
         P = Pnew;
         P32 = P32n;
         if (!is_end) {
           // frozen disk or wall: the chain turns back along its axis
           sg = -sg;
-          if (replay && n_refl > 0 && dbits(Pnew) == dbits(Pm1)) {
-            // The chain is back, bit for bit, where the previous reflection
-            // leg started, moving the same way: between two reflectors
-            // (frozen disks or walls) nothing else moves, so the legs
-            // repeat exactly -- same step, same contact -- for as long as
-            // the budget exceeds the step.  Replay them with their
-            // subtractions only; the full search resumes for the last leg.
-            const double sA = s_m1, aA = add_m1, PA = Pk;  // leg from Pnew
-            const bool wA = wall_m1;
-            const double sB = step, aB = addb, PB = Pnew;  // leg from Pk
-            const bool wB = is_wall;
-            for (int leg = 0;; leg ^= 1) {
-              const double sl = leg ? sB : sA;
-              if (n_iter >= kMaxEventsPerChain || le_nn(r, sl)) break;
-              const bool wl = leg ? wB : wA;
-              r = r - sl;
-              n_iter += 1;
-              n_replayed += 1;
-              n_walls += wl ? 1 : 0;
-              ch_walls += wl ? 1 : 0;
-              n_events += wl ? 0 : 1;
-              ch_events += wl ? 0 : 1;
-              n_frozen += wl ? 0 : 1;
-              if (!wl) sum_b += leg ? aB : aA;
-              P = leg ? PB : PA;
-              sg = -sg;
-            }
-            P32 = to_float_trunc(P);
-            n_refl = 0;
-          } else {
-            Pm1 = Pk;
-            s_m1 = step;
-            add_m1 = addb;
-            wall_m1 = is_wall;
-            n_refl += 1;
-          }
+          if (replay) replay_cycle(f, hs, gi, n_leg, m, sg, P, P32, Q, Q32, r, n_iter, sum_b,
+                                   n_events, n_lifts, n_frozen, n_walls, ch_events, ch_walls,
+                                   n_replayed);
         }
       }
-      if (is_lift) n_refl = 0;
       end_chain = is_end;
     }
     if (end_chain) {
@@ -486,9 +561,10 @@ __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
 }
 
 size_t phase_smem_bytes(const RecLayout& lay, int warps_per_block, int fmode) {
-  if (fmode == 2) return 0;
+  const size_t hist = kHistLegBytes * kHist * (size_t)lay.cpw;
+  if (fmode == 2) return (size_t)warps_per_block * hist;
   const size_t copy = fmode == 1 ? lay.light_bytes : lay.bytes;
-  return (size_t)warps_per_block * (copy + align16((size_t)lay.cap_obj * lay.cpw));
+  return (size_t)warps_per_block * (copy + align16((size_t)lay.cap_obj * lay.cpw) + hist);
 }
 
 template <int TPC, bool SCREEN>
@@ -546,11 +622,22 @@ static int configure_t(size_t sm) {
 // amount the kernel can have, so that a handle with small frames never lowers
 // the limit that a handle with larger frames needs.
 int configure_phase(const RecLayout& lay, int tpc, int warps, int fmode) {
-  if (fmode == 2) return 0;  // frames in global memory need no shared memory
   const size_t sm = phase_smem_bytes(lay, warps, fmode);
 #define ECMC_CFG(T)                                                          \
   case T:                                                                    \
     return fmode == 1 ? configure_t<T, 1>(sm) : configure_t<T, 0>(sm);
+  if (fmode == 2) {
+    // frames in global memory: only the leg histories use shared memory
+    switch (tpc) {
+      case 1: return configure_t<1, 2>(sm);
+      case 2: return configure_t<2, 2>(sm);
+      case 4: return configure_t<4, 2>(sm);
+      case 8: return configure_t<8, 2>(sm);
+      case 16: return configure_t<16, 2>(sm);
+      case 32: return configure_t<32, 2>(sm);
+      default: return -1;
+    }
+  }
   switch (tpc) {
     ECMC_CFG(1)
     ECMC_CFG(2)
