@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--autotune", action="store_true", help="tune the launch shape first")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--fmode", type=int, default=-1, help="frame placement 0/1/2 (-1 automatic)")
+    ap.add_argument("--persistent", type=int, default=-1,
+                    help="1 one persistent launch per sweep, 0 per-phase launches (-1 default)")
     ap.add_argument("--melt", type=int, default=-1,
                     help="untimed sweeps from the lattice before warm-up (default 20; the "
                          "oracle arms run the same sweeps and reach the same state)")
@@ -384,6 +386,8 @@ def run_ours(args):
     g.set_param(E.PARAM_PRECISION, args.prec)
     if args.fmode >= 0:
         g.set_param(E.PARAM_FRAME_MODE, args.fmode)
+    if args.persistent >= 0:
+        g.set_param(E.PARAM_PERSISTENT, args.persistent)
     # a stream of our own (torch's default stream is the legacy NULL stream,
     # which the library reads as "use your own stream")
     stream = torch.cuda.Stream()
@@ -435,6 +439,8 @@ def run_ours(args):
     ms = sum(a.elapsed_time(b) for a, b in evs)
     c = g.counters()
     kt = g.kernel_times()
+    kernels_per_sweep = int(g.get_param(E.PARAM_KERNELS_PER_SWEEP))
+    persistent = int(g.get_param(E.PARAM_PERSISTENT))
     g.set_param(E.PARAM_TIMING, 0)
     events = c.events
     sweeps = c.sweeps
@@ -523,7 +529,8 @@ def run_ours(args):
                        "l2": "none" if args.no_flush else "flushed (256 MB write) between steps",
                        "start": "square lattice, %d untimed sweeps, then %d warm-up sweeps"
                                 % (melt_sweeps(args), args.warmup),
-                       "parallelism": "replicas x%d" % world},
+                       "parallelism": "replicas x%d" % world,
+                       "launch": "persistent sweep kernel" if persistent else "per-phase kernels"},
             "sweeps_per_s": sweeps_all / (ms_max * 1e-3),
             "events_per_sweep": events / max(sweeps, 1),
             "per_sweep": {"chains": c.chains / max(sweeps, 1),
@@ -534,19 +541,21 @@ def run_ours(args):
                                     "frame": kt.frame_ms / max(sweeps, 1),
                                     "chain": kt.phase_ms / max(sweeps, 1),
                                     "reduce": kt.other_ms / max(sweeps, 1)},
-            "roofline": {"kernel": "k_phase (chain kernel)", "bound": "alu",
+            "roofline": {"kernel": "k_sweep_fused (persistent sweep kernel)" if persistent
+                         else "k_phase (chain kernel)", "bound": "alu",
                          "achieved": achieved, "peak": fp64_peak, "unit": "GFLOP/s",
                          "frac": achieved / fp64_peak,
-                         "traffic": K_PHASE_DRAM_BYTES if tpc == 8 and not descs else None,
+                         "traffic": (None if persistent else K_PHASE_DRAM_BYTES)
+                         if tpc == 8 and not descs else None,
                          "pipe": "fp64", "fp64_ops_per_iteration": FP64_OPS_PER_ITERATION,
                          "iterations_per_launch": iters / max(kt.phase_launches, 1),
                          "launch_ms": phase_avg_ms,
                          "peak_source": "2 FP64 lanes/clk/SM x %d SMs x %.0f MHz (unit counts)"
                                         % (n_sm, sm_mhz),
                          "fp64_probe_gflops": fp64_probe},
-            # per sweep: draws, binning, 4 x (frame builder, chain kernel), chunk
-            # sums, end of sweep
-            "gpu_launches": 12 * args.steps * world,
+            # per sweep: draws, binning, the persistent sweep kernel (or 4 x frame
+            # builder + chain kernel), chunk sums, end of sweep
+            "gpu_launches": kernels_per_sweep * args.steps * world,
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": cpu,

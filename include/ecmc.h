@@ -101,6 +101,24 @@ extern "C" {
  * for bit, without searching for candidates again (default 1); 0 = search on
  * every leg.  Changes only the speed, never the result. */
 #define ECMC_PARAM_REPLAY 14
+/* 1 = run the four colour phases of a sweep in one persistent launch when a
+ * warp's frames fit in shared memory (default 1): warps take cell groups from
+ * a work list ordered by phase, wait until the neighbours of earlier phases
+ * have finished (bounded waits), build the frames themselves and run the
+ * chains; 0 = one frame-builder and one chain launch per phase.  Reading it
+ * returns the mode in use.  Changes only the speed, never the result. */
+#define ECMC_PARAM_PERSISTENT 15
+/* Limit of one dependency wait of the persistent kernel, in ms (default
+ * 5000).  A wait that exceeds it abandons the sweep: ecmc_sweep or the next
+ * call reports ECMC_ERR_TIMEOUT and the positions must be set again. */
+#define ECMC_PARAM_WAIT_LIMIT_MS 16
+/* 1 = the persistent kernel's dependency waits look for a value that no cell
+ * ever writes, so every wait runs into the limit (a test of the failure path
+ * that faults nothing; default 0). */
+#define ECMC_PARAM_WAIT_TEST 17
+/* Read-only: kernel launches per sweep of the current configuration (5 with
+ * the persistent kernel, 12 with per-phase launches). */
+#define ECMC_PARAM_KERNELS_PER_SWEEP 18
 
 #define ECMC_DIR_PM_AXIS_ALT 0
 #define ECMC_DIR_POS_ONLY 1

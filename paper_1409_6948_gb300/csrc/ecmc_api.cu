@@ -59,6 +59,10 @@ struct ecmc_ctx {
   int tpc_param = 0;    // 0 = automatic
   int fmode = 0;        // frame placement in use (see phase_smem_bytes)
   int fmode_param = -1; // -1 = automatic
+  int persist_param = 1; // 1 = one persistent launch per sweep when the frames fit
+  int persistent = 0;    // in use
+  int fused_blocks = 0;  // grid of the persistent sweep kernel
+  double wait_ms = 5000.0;
   int n_sm = 0;
   std::vector<int2> chunks;
   std::vector<int> chunk_off;
@@ -232,6 +236,21 @@ int compute_layout(ecmc_ctx* h) {
       configure_phase(h->lay, h->tpc, h->warps, fmode))
     return fail(ECMC_ERR_CUDA, "kernel configuration failed: %s",
                 cudaGetErrorString(cudaGetLastError()));
+  // one persistent launch per sweep when a warp's frames, histories and
+  // builder scratch fit in shared memory at least twice per SM
+  h->persistent = 0;
+  h->fused_blocks = 0;
+  if (h->persist_param && fmode < 2 && fused_smem_bytes(h->lay) <= limit / 2) {
+    int per_sm = 0;
+    if (configure_fused(h->lay, h->tpc, &per_sm) == 0) {
+      const int n_groups_all = 4 * ((h->b.A_total + h->lay.cpw - 1) / h->lay.cpw);
+      const int grid = per_sm * h->n_sm;
+      h->fused_blocks = grid < n_groups_all ? grid : n_groups_all;
+      h->persistent = 1;
+    } else {
+      cudaGetLastError();
+    }
+  }
   return upload_geometry(h);
 }
 
@@ -296,6 +315,21 @@ int enqueue_sweep(ecmc_ctx* h) {
     launch_bin(h->b, src, dst, h->stream);
   }
   h->b.cur = dst;
+  if (h->persistent) {
+    {
+      Timed tm(h, TC_PHASE);
+      if (launch_fused(h->b, h->lay, h->tpc, h->fused_blocks, h->record_chains, h->precision,
+                       h->stream))
+        return fail(ECMC_ERR_CUDA, "sweep kernel launch failed: %s",
+                    cudaGetErrorString(cudaGetLastError()));
+    }
+    {
+      Timed tm(h, TC_OTHER);
+      launch_sweep_end(h->b, h->stream);
+    }
+    CK(cudaGetLastError());
+    return ECMC_OK;
+  }
   for (int ci = 0; ci < 4; ++ci) {
     {
       Timed tm(h, TC_FRAME);
@@ -350,6 +384,13 @@ int check_device_error(ecmc_ctx* h) {
   if (e == DEV_CHAIN_CAP) {
     h->valid_state = false;
     return fail(ECMC_ERR_CHAIN_CAP, "a chain reached the per-chain event cap");
+  }
+  if (e == DEV_WAIT_TIMEOUT) {
+    h->valid_state = false;
+    CK(cudaMemsetAsync(h->b.err, 0, sizeof(int), h->stream));
+    return fail(ECMC_ERR_TIMEOUT,
+                "a dependency wait of the persistent sweep kernel exceeded %.0f ms; the sweep "
+                "was abandoned (positions must be set again)", h->wait_ms);
   }
   return ECMC_OK;
 }
@@ -445,6 +486,8 @@ void free_all(ecmc_ctx* h) {
   cudaFree(h->b.gtouch);
   cudaFree(h->b.stage);
   cudaFree(h->b.err);
+  cudaFree(h->b.sched);
+  cudaFree(h->b.done);
   cudaFree(h->b.chain_recs);
   cudaFree(h->d_geo);
   cudaFree(h->d_cell_rep);
@@ -607,6 +650,8 @@ int create_impl(ecmc_t* out, const ecmc_replica_desc_t* desc, int R) {
       cudaMalloc(&b.cell_stats, sizeof(CellStats) * (size_t)C_total) != cudaSuccess ||
       cudaMalloc(&b.totals, sizeof(RunTotals) * R) != cudaSuccess ||
       cudaMalloc(&b.err, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&b.sched, sizeof(unsigned) * 4) != cudaSuccess ||
+      cudaMalloc(&b.done, sizeof(unsigned) * (size_t)C_total) != cudaSuccess ||
       cudaMalloc(&h->d_geo, sizeof(Geom) * R) != cudaSuccess ||
       cudaMalloc(&h->d_cell_rep, sizeof(int) * (size_t)C_total) != cudaSuccess ||
       cudaMalloc(&h->d_act_rep, sizeof(int) * (size_t)A_total) != cudaSuccess ||
@@ -620,6 +665,9 @@ int create_impl(ecmc_t* out, const ecmc_replica_desc_t* desc, int R) {
     return bail(fail(ECMC_ERR_OOM, "device allocation failed"));
   cudaMemsetAsync(b.totals, 0, sizeof(RunTotals) * R, h->stream);
   cudaMemsetAsync(b.err, 0, sizeof(int), h->stream);
+  cudaMemsetAsync(b.sched, 0, sizeof(unsigned) * 4, h->stream);
+  cudaMemsetAsync(b.done, 0, sizeof(unsigned) * (size_t)C_total, h->stream);
+  b.wait_ns = (unsigned long long)(h->wait_ms * 1e6);
   cudaMemsetAsync(b.cell_stats, 0, sizeof(CellStats) * (size_t)C_total, h->stream);
   if (cudaMemcpyAsync(h->d_cell_rep, h->cell_rep.data(), sizeof(int) * C_total,
                       cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
@@ -869,6 +917,24 @@ int ecmc_set_param(ecmc_t h, int key, double v) {
       h->use_graph = v != 0.0;
       drop_graphs(h);
       return ECMC_OK;
+    case ECMC_PARAM_PERSISTENT:
+      if (v != 0.0 && v != 1.0) return fail(ECMC_ERR_ARG, "persistent must be 0 or 1");
+      h->persist_param = (int)v;
+      drop_graphs(h);
+      return compute_layout(h);
+    case ECMC_PARAM_WAIT_LIMIT_MS:
+      if (!(v >= 0.001 && v <= 600000.0)) return fail(ECMC_ERR_ARG, "wait limit out of range");
+      h->wait_ms = v;
+      h->b.wait_ns = (unsigned long long)(v * 1e6);
+      drop_graphs(h);
+      return ECMC_OK;
+    case ECMC_PARAM_WAIT_TEST:
+      if (v != 0.0 && v != 1.0) return fail(ECMC_ERR_ARG, "wait test must be 0 or 1");
+      h->b.wait_test = (int)v;
+      drop_graphs(h);
+      return ECMC_OK;
+    case ECMC_PARAM_KERNELS_PER_SWEEP:
+      return fail(ECMC_ERR_ARG, "kernels per sweep is read-only");
     case ECMC_PARAM_REPLAY:
       if (v != 0.0 && v != 1.0) return fail(ECMC_ERR_ARG, "replay must be 0 or 1");
       h->b.replay = (int)v;
@@ -903,6 +969,10 @@ int ecmc_get_param(ecmc_t h, int key, double* v) {
     case ECMC_PARAM_USE_GRAPH: *v = h->use_graph; break;
     case ECMC_PARAM_FRAME_MODE: *v = h->fmode; break;
     case ECMC_PARAM_REPLAY: *v = h->b.replay; break;
+    case ECMC_PARAM_PERSISTENT: *v = h->persistent; break;
+    case ECMC_PARAM_WAIT_LIMIT_MS: *v = h->wait_ms; break;
+    case ECMC_PARAM_WAIT_TEST: *v = h->b.wait_test; break;
+    case ECMC_PARAM_KERNELS_PER_SWEEP: *v = h->persistent ? 5 : 12; break;
     default: return fail(ECMC_ERR_ARG, "unknown parameter %d", key);
   }
   return ECMC_OK;

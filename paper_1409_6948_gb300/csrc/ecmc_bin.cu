@@ -12,8 +12,15 @@ namespace ecmc {
 
 // One thread per replica: shift and colour order of sweep state->t from
 // Philox(t, 0, 0, 0) under the replica's key.
-__global__ void k_sweep_begin(const Geom* __restrict__ rg, SweepState* st, int R) {
+__global__ void k_sweep_begin(const Geom* __restrict__ rg, SweepState* st, int R,
+                              unsigned* sched) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r == 0 && sched != nullptr) {
+    // persistent sweep: work list from the start, a new epoch, no abort
+    sched[0] = 0u;
+    sched[1] += 1u;
+    sched[2] = 0u;
+  }
   if (r >= R) return;
   const Geom& g = rg[r];
   SweepState& s = st[r];
@@ -39,7 +46,7 @@ __global__ void k_sweep_begin(const Geom* __restrict__ rg, SweepState* st, int R
 }
 
 void launch_sweep_begin(const DevBufs& b, cudaStream_t s) {
-  k_sweep_begin<<<(b.R + 31) / 32, 32, 0, s>>>(b.rg, b.state, b.R);
+  k_sweep_begin<<<(b.R + 31) / 32, 32, 0, s>>>(b.rg, b.state, b.R, b.sched);
 }
 
 __device__ __forceinline__ void bin_one(const Geom& g, const SweepState& st, double x, double y,

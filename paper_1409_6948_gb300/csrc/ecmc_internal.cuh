@@ -27,6 +27,7 @@ enum DevErr : int {
   DEV_CAPACITY = 1,   // a bucket or frame record overflowed its rigorous bound
   DEV_CHAIN_CAP = 2,  // a chain reached the per-chain event cap
   DEV_OVERLAP = 3,
+  DEV_WAIT_TIMEOUT = 4,  // a dependency wait of the persistent sweep kernel gave up
 };
 
 constexpr int64_t kMaxEventsPerChain = int64_t(1) << 22;
@@ -161,6 +162,10 @@ struct DevBufs {
   ChunkSums* partials;     // [n_chunks]
   int n_chunks;
   int replay;              // 1 = replay repeating reflection legs (chain kernel)
+  unsigned* sched;         // persistent sweep: [0] next work item, [1] epoch, [2] abort
+  unsigned* done;          // [C_total] epoch in which each cell last finished
+  unsigned long long wait_ns;  // limit of one dependency wait
+  int wait_test;           // 1 = dependency waits look for a value nobody writes
   int R, C_total, A_total, cap;
   int64_t N_total;
 };
@@ -188,6 +193,10 @@ size_t frame_stage_bytes(const RecLayout& lay);
 int configure_frame_build(const RecLayout& lay);
 int configure_phase(const RecLayout& lay, int tpc, int warps, int fmode);
 int probe_peaks(double* smem_gbs, double* fp64_gflops);
+size_t fused_smem_bytes(const RecLayout& lay);
+int configure_fused(const RecLayout& lay, int tpc, int* blocks_per_sm);
+int launch_fused(const DevBufs& b, const RecLayout& lay, int tpc, int blocks, int records_on,
+                 int precision, cudaStream_t s);
 int launch_sqrt_rn(const double* x, double* out, int64_t n, cudaStream_t s);
 void host_sqrt_rn(const double* x, double* out, int64_t n, double rel_error);
 // fmode: 0 = whole frame in shared memory, 1 = FP64 coordinates in global

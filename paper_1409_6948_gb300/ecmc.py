@@ -32,6 +32,10 @@ PARAM_WARPS_PER_BLOCK = 11
 PARAM_USE_GRAPH = 12
 PARAM_FRAME_MODE = 13
 PARAM_REPLAY = 14
+PARAM_PERSISTENT = 15
+PARAM_WAIT_LIMIT_MS = 16
+PARAM_WAIT_TEST = 17
+PARAM_KERNELS_PER_SWEEP = 18
 
 DIR_PM_AXIS_ALT = 0
 DIR_POS_ONLY = 1

@@ -30,7 +30,7 @@ LAST = {}  # counters of the most recent run_pair, for tests that inspect them
 
 
 def make(N, eta, cells_x, cells_y, ell, nm, seed, tpc=0, prec=1, dir_mode=0, records=False,
-         replica=0, fmode=-1):
+         replica=0, fmode=-1, persistent=1):
     L = W.box_side(N, eta)
     g = P.Ecmc(N, L, 1.0, cells_x, cells_y, ell, seed)
     g.set_param(E.PARAM_N_CHAINS, nm)
@@ -41,6 +41,7 @@ def make(N, eta, cells_x, cells_y, ell, nm, seed, tpc=0, prec=1, dir_mode=0, rec
         g.set_param(E.PARAM_LANES_PER_CELL, tpc)
     if fmode >= 0:
         g.set_param(E.PARAM_FRAME_MODE, fmode)
+    g.set_param(E.PARAM_PERSISTENT, persistent)
     if records:
         g.set_param(E.PARAM_RECORD_CHAINS, 1)
     p = oracle.make_params(N, L, 1.0, cells_x, cells_y, ell, nm, seed, replica,
@@ -280,5 +281,59 @@ def test_replay_switch_gives_identical_trajectories(replay):
 @pytest.mark.parametrize("fmode", [0, 1, 2])
 @pytest.mark.parametrize("tpc", [1, 4, 32])
 def test_frame_placements(fmode, tpc):
-    # frames in shared memory, FP64 part in global memory, all in global memory
-    run_pair(4096, 0.72, 16, 16, 3.0, 2, 17, 3, tpc=tpc, fmode=fmode)
+    # per-phase launches with frames in shared memory, FP64 part in global
+    # memory, all in global memory
+    run_pair(4096, 0.72, 16, 16, 3.0, 2, 17, 3, tpc=tpc, fmode=fmode, persistent=0)
+
+
+@pytest.mark.parametrize("N,eta,cx,cy,ell,nm,tpc", [
+    (256, 0.70, 2, 2, 4.0, 2, 8),      # two cells per side: neighbours coincide
+    (1024, 0.70, 8, 8, 6.0, 2, 4),     # chains across whole cells, rattles
+    (4096, 0.72, 4, 8, 4.0, 3, 8),     # rectangular cells, 128 disks each
+    (4096, 0.72, 16, 16, 2.0, 1, 32),  # one cell per warp
+])
+def test_persistent_sweep_matches_oracle(N, eta, cx, cy, ell, nm, tpc):
+    # one launch per sweep: work list over (phase, group) with waits on the
+    # neighbours of earlier phases; same trajectory as the phase launches
+    g, _, _ = make(N, eta, cx, cy, ell, nm, 7, tpc=tpc)
+    assert g.get_param(E.PARAM_PERSISTENT) == 1
+    assert g.get_param(E.PARAM_KERNELS_PER_SWEEP) == 5
+    g.close()
+    run_pair(N, eta, cx, cy, ell, nm, 7, 4, tpc=tpc)
+
+
+def test_persistent_and_phase_launches_are_bitwise_equal():
+    N, eta = 65536, 0.708
+    a, _, L = make(N, eta, 32, 32, 8.0, 1, 2)
+    b, _, _ = make(N, eta, 32, 32, 8.0, 1, 2, persistent=0)
+    assert a.get_param(E.PARAM_PERSISTENT) == 1 and b.get_param(E.PARAM_PERSISTENT) == 0
+    a.sweep(6)
+    b.sweep(6)
+    assert np.array_equal(a.positions(), b.positions())
+    assert a.counters().as_dict() == b.counters().as_dict()
+    a.close()
+    b.close()
+
+
+def test_dependency_wait_timeout_is_reported_and_recoverable():
+    # the waits of the persistent kernel look for a value nobody writes: every
+    # wait runs into a 20 ms limit, the sweep is abandoned with a timeout
+    # status the host reads, and the handle works again once positions are set
+    N, eta = 4096, 0.72
+    g, p, L = make(N, eta, 16, 16, 2.0, 1, 5)
+    x, y = W.square_lattice(N, L)
+    g.set_param(E.PARAM_WAIT_LIMIT_MS, 20.0)
+    g.set_param(E.PARAM_WAIT_TEST, 1)
+    with pytest.raises(E.EcmcError) as ei:
+        g.sweep(1)
+        g.positions()
+    assert ei.value.code == E.ERR_TIMEOUT
+    with pytest.raises(E.EcmcError) as ei:
+        g.sweep(1)
+    assert ei.value.code == E.ERR_STATE
+    g.set_param(E.PARAM_WAIT_TEST, 0)
+    g.set_positions(np.stack([x, y], 1).ravel(), t0=0)
+    g.sweep(3)
+    oracle.sweeps(p, x, y, 0, 3)
+    assert_positions_equal(g, x, y, L)
+    g.close()
