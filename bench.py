@@ -403,7 +403,7 @@ def run_ours(args):
     g.synchronize()
     tuned = None
     if (args.autotune or args.workload in ("large", "huge", "batch", "eos")) and \
-            not args.no_autotune and not args.tpc and args.fmode < 0:
+            not args.no_autotune and not args.tpc and args.fmode < 0 and args.persistent < 0:
         tuned, _ = g.autotune(trial_sweeps=2)
         tpc = int(g.get_param(E.PARAM_LANES_PER_CELL))
         g.sweep(1)

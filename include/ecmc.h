@@ -94,7 +94,9 @@ extern "C" {
 /* Where the chain kernel keeps the cell frames: 0 = shared memory, 1 = FP32
  * screening data in shared memory and FP64 coordinates in global memory,
  * 2 = global memory (cells too large for shared memory), -1 = automatic
- * (default).  Changes only the speed, never the result. */
+ * (default).  The persistent sweep kernel uses 0 or 1 (automatic: 0; with 1
+ * its FP64 coordinates live in a per-warp scratch area).  Changes only the
+ * speed, never the result. */
 #define ECMC_PARAM_FRAME_MODE 13
 /* 1 = replay the legs of a chain that rattles between two reflectors
  * (frozen disks or walls) once its position after a reflection repeats bit
@@ -224,17 +226,19 @@ ECMC_API int ecmc_replica_counters(ecmc_t h, int r, ecmc_counters_t* out);
 ECMC_API int ecmc_suggest_parameters(int64_t N, double L, double sigma, double min_cell_side,
                                      ecmc_replica_desc_t* out);
 
-/* One launch shape of the chain kernel and its measured time per sweep. */
+/* One launch shape and its measured time per sweep. */
 typedef struct {
   int lanes_per_cell;
-  int warps_per_block;
-  int frame_mode;
+  int warps_per_block; /* per-phase kernels only                              */
+  int frame_mode;      /* per-phase kernels only                              */
+  int persistent;      /* 1 = the persistent sweep kernel (ECMC_PARAM_PERSISTENT) */
   double ms_per_sweep;
 } ecmc_tune_result_t;
 
 /* Time trial_sweeps sweeps (after one warm-up sweep) for every launch shape
- * that fits (lanes per cell 1..32, warps per block 1 and 2, frame modes 0
- * and 1, or 2 when nothing else fits), keep the
+ * that fits (the persistent sweep kernel with lanes per cell 1..32; the
+ * per-phase kernels with lanes per cell 1..32, warps per block 1 and 2, frame
+ * modes 0 and 1, or 2 when nothing else fits), keep the
  * fastest, and put the handle back exactly where it was (positions, sweep
  * counter, statistics): every shape gives bit-identical trajectories, so the
  * tuning does not change the simulation.  best receives the chosen shape;

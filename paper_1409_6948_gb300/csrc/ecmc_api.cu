@@ -240,13 +240,27 @@ int compute_layout(ecmc_ctx* h) {
   // builder scratch fit in shared memory at least twice per SM
   h->persistent = 0;
   h->fused_blocks = 0;
-  if (h->persist_param && fmode < 2 && fused_smem_bytes(h->lay) <= limit / 2) {
+  // the persistent kernel keeps its frames in shared memory (frame mode 0)
+  // unless mode 1 is asked for: FP64 coordinates in a per-warp scratch area of
+  // global memory, more warps per SM (measured at N = 1M, eta = 0.72: 1.64
+  // against 1.58 * 10^9 events/s)
+  const int fm = h->fmode_param == 1 ? 1 : 0;
+  if (h->persist_param && fmode < 2 && fused_smem_bytes(h->lay, fm) <= limit / 2) {
     int per_sm = 0;
-    if (configure_fused(h->lay, h->tpc, &per_sm) == 0) {
-      const int n_groups_all = 4 * ((h->b.A_total + h->lay.cpw - 1) / h->lay.cpw);
-      const int grid = per_sm * h->n_sm;
-      h->fused_blocks = grid < n_groups_all ? grid : n_groups_all;
+    if (configure_fused(h->lay, h->tpc, fm, &per_sm) == 0) {
+      const int n_items = 4 * n_groups;
+      const int grid = per_sm * h->n_sm < n_items ? per_sm * h->n_sm : n_items;
+      const size_t scratch = (size_t)grid * fused_scratch_bytes(h->lay);
+      if (scratch > h->records_cap) {
+        cudaFree(h->b.records);
+        h->b.records = nullptr;
+        CK(cudaMalloc(&h->b.records, scratch));
+        h->records_cap = scratch;
+      }
+      h->fused_blocks = grid;
       h->persistent = 1;
+      h->fmode = fm;
+      h->b.fmode = fm;
     } else {
       cudaGetLastError();
     }
@@ -1260,7 +1274,7 @@ int ecmc_autotune(ecmc_t h, int trial_sweeps, ecmc_tune_result_t* best, ecmc_tun
                   h->stream);
   const int64_t t_saved = h->t_host, hist_saved = h->hist_len_host;
   const int tpc0 = h->tpc_param, warps0 = h->warps_param, timing0 = h->timing;
-  const int fmode0 = h->fmode_param;
+  const int fmode0 = h->fmode_param, persist0 = h->persist_param;
   h->timing = 0;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -1269,15 +1283,26 @@ int ecmc_autotune(ecmc_t h, int trial_sweeps, ecmc_tune_result_t* best, ecmc_tun
   int rc = ECMC_OK;
   const int tpcs[6] = {1, 2, 4, 8, 16, 32};
   const int wps[2] = {1, 2};
+  // the persistent sweep kernel for every lanes-per-cell choice and both
+  // placements of the FP64 coordinates (warps per block do not apply to it),
+  // then the per-phase kernels for every shape
+  for (int pm = 1; pm >= 0 && rc == ECMC_OK; --pm)
   for (int fm = 0; fm < 3 && rc == ECMC_OK; ++fm)
   for (int ti = 0; ti < 6 && rc == ECMC_OK; ++ti)
     for (int wi = 0; wi < 2 && rc == ECMC_OK; ++wi) {
+      if (pm == 1 && (fm > 1 || wi > 0)) continue;
+      h->persist_param = pm;
       h->tpc_param = tpcs[ti];
       h->warps_param = wps[wi];
       h->fmode_param = fm;
       drop_graphs(h);
-      if (compute_layout(h) != ECMC_OK || h->warps != wps[wi] || h->fmode != fm) continue;
-      if (fm == 2 && res.size() > 0) continue;  // global frames only when nothing else fits
+      if (compute_layout(h) != ECMC_OK) {
+        cudaGetLastError();
+        continue;
+      }
+      if (h->persistent != pm || h->fmode != fm) continue;
+      if (!pm && h->warps != wps[wi]) continue;
+      if (!pm && fm == 2 && res.size() > 0) continue;  // global frames only when nothing else fits
       rc = ecmc_sweep(h, 1);
       if (rc) break;
       cudaEventRecord(e0, h->stream);
@@ -1292,6 +1317,7 @@ int ecmc_autotune(ecmc_t h, int trial_sweeps, ecmc_tune_result_t* best, ecmc_tun
       r.lanes_per_cell = h->tpc;
       r.warps_per_block = h->warps;
       r.frame_mode = h->fmode;
+      r.persistent = h->persistent;
       r.ms_per_sweep = ms / trial_sweeps;
       res.push_back(r);
       // back to the saved state before the next shape
@@ -1312,10 +1338,12 @@ int ecmc_autotune(ecmc_t h, int trial_sweeps, ecmc_tune_result_t* best, ecmc_tun
     h->tpc_param = res[bi].lanes_per_cell;
     h->warps_param = res[bi].warps_per_block;
     h->fmode_param = res[bi].frame_mode;
+    h->persist_param = res[bi].persistent;
   } else {
     h->tpc_param = tpc0;
     h->warps_param = warps0;
     h->fmode_param = fmode0;
+    h->persist_param = persist0;
   }
   drop_graphs(h);
   int rc2 = compute_layout(h);

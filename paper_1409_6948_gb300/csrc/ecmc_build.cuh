@@ -50,7 +50,8 @@ struct BuildArgs {
   unsigned char* aux;         // build_aux_bytes(threads) of shared memory
   unsigned char* stage;       // build_stage_bytes(lay), shared or global memory
   unsigned char* rec;         // record of the group: header, strips, members, FP32 part
-  unsigned char* rec64;       // base of the FP64 coordinates (rec for an in-place record)
+  double* a64;                // the group's FP64 coordinates along / across the axis
+  double* b64;                // (in the record, or in a separate scratch area)
   RecLayout lay;
   int gi;                     // column of this cell in the record
   int* err;
@@ -300,8 +301,8 @@ __device__ void build_frame(const BuildArgs& A) {
   int* ms = (int*)(rec + lay.off_mslot);
   float* a32 = (float*)(rec + lay.off_a32);
   float* b32 = (float*)(rec + lay.off_b32);
-  double* a64 = (double*)(A.rec64 + lay.off_a64);
-  double* b64 = (double*)(A.rec64 + lay.off_b64);
+  double* a64 = A.a64;
+  double* b64 = A.b64;
   int* key = (int*)(rec + lay.off_key);
   int* info = (int*)(rec + lay.off_info);
   if (tid == 0) {

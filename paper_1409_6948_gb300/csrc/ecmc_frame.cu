@@ -36,7 +36,8 @@ __global__ void k_frame_build(const Geom* __restrict__ rg, const SweepState* __r
   A.stage = stage ? stage + (size_t)blockIdx.x * stage_bytes : smem + build_aux_bytes(blockDim.x);
   const int G = a / lay.cpw;
   A.rec = records + (size_t)G * lay.bytes;
-  A.rec64 = A.rec;
+  A.a64 = (double*)(A.rec + lay.off_a64);
+  A.b64 = (double*)(A.rec + lay.off_b64);
   A.lay = lay;
   A.gi = a - G * lay.cpw;
   A.err = err;

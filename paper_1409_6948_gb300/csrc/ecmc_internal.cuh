@@ -193,8 +193,9 @@ size_t frame_stage_bytes(const RecLayout& lay);
 int configure_frame_build(const RecLayout& lay);
 int configure_phase(const RecLayout& lay, int tpc, int warps, int fmode);
 int probe_peaks(double* smem_gbs, double* fp64_gflops);
-size_t fused_smem_bytes(const RecLayout& lay);
-int configure_fused(const RecLayout& lay, int tpc, int* blocks_per_sm);
+size_t fused_smem_bytes(const RecLayout& lay, int fm);
+size_t fused_scratch_bytes(const RecLayout& lay);
+int configure_fused(const RecLayout& lay, int tpc, int fm, int* blocks_per_sm);
 int launch_fused(const DevBufs& b, const RecLayout& lay, int tpc, int blocks, int records_on,
                  int precision, cudaStream_t s);
 int launch_sqrt_rn(const double* x, double* out, int64_t n, cudaStream_t s);

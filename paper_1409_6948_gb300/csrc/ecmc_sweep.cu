@@ -44,24 +44,35 @@ __host__ __device__ inline size_t fused_hist_bytes(const RecLayout& lay) {
   const size_t s = build_stage_bytes(lay);
   return h > s ? h : s;
 }
-__host__ __device__ inline size_t fused_warp_bytes(const RecLayout& lay) {
-  return lay.bytes + fused_touch_bytes(lay) + fused_hist_bytes(lay) + build_aux_bytes(32);
+// FM 0: the whole record in shared memory; FM 1: the FP64 coordinates in a
+// per-warp scratch area of global memory (L1/L2), so that more warps fit.
+__host__ __device__ inline size_t fused_fp64_bytes(const RecLayout& lay) {
+  return lay.bytes - lay.light_bytes;
+}
+__host__ __device__ inline size_t fused_warp_bytes(const RecLayout& lay, int fm) {
+  return (fm == 1 ? lay.light_bytes : lay.bytes) + fused_touch_bytes(lay) +
+         fused_hist_bytes(lay) + build_aux_bytes(32);
 }
 
-template <int TPC, bool SCREEN>
+template <int TPC, bool SCREEN, int FM>
 __global__ void __launch_bounds__(32, 16) k_sweep_fused(
     const Geom* __restrict__ rg, const SweepState* __restrict__ sts,
     const int* __restrict__ act_rep, int n_active, int cap, double* __restrict__ px,
     double* __restrict__ py, const int* __restrict__ pid, const int* __restrict__ cnt,
     RecLayout lay, CellStats* __restrict__ cs, ChainRec* __restrict__ recs, int rec_stride,
     int replay, unsigned* sched, unsigned* done, unsigned long long wait_ns, int wait_test,
-    int* err) {
+    unsigned char* __restrict__ fscratch, int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int CPW = 32 / TPC;
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   unsigned char* const rec = smem;
-  unsigned char* const tbase = rec + lay.bytes;
+  unsigned char* const tbase = rec + (FM == 1 ? lay.light_bytes : lay.bytes);
+  // the FP64 coordinates: in the record, or in this warp's scratch area
+  double* const a64 =
+      FM == 1 ? (double*)(fscratch + (size_t)blockIdx.x * fused_fp64_bytes(lay))
+              : (double*)(rec + lay.off_a64);
+  double* const b64 = a64 + (lay.off_b64 - lay.off_a64) / sizeof(double);
   unsigned char* const hbase = tbase + fused_touch_bytes(lay);
   unsigned char* const aux = hbase + fused_hist_bytes(lay);
 
@@ -72,8 +83,8 @@ __global__ void __launch_bounds__(32, 16) k_sweep_fused(
   f.mslot = (const int*)(rec + lay.off_mslot);
   f.a32 = (float*)(rec + lay.off_a32);
   f.b32 = (const float*)(rec + lay.off_b32);
-  f.a64 = (double*)(rec + lay.off_a64);
-  f.b64 = (const double*)(rec + lay.off_b64);
+  f.a64 = a64;
+  f.b64 = b64;
   f.key = (const int*)(rec + lay.off_key);
   f.info = (const int*)(rec + lay.off_info);
   f.touched = tbase;
@@ -175,7 +186,8 @@ __global__ void __launch_bounds__(32, 16) k_sweep_fused(
       A.aux = aux;
       A.stage = hbase;
       A.rec = rec;
-      A.rec64 = rec;
+      A.a64 = a64;
+      A.b64 = b64;
       A.lay = lay;
       A.gi = g2;
       A.err = err;
@@ -188,6 +200,7 @@ __global__ void __launch_bounds__(32, 16) k_sweep_fused(
     }
     __syncwarp();
 
+    __syncwarp();
     run_group<TPC, SCREEN>(f, hs, hdr, rg, sts, rep, a, valid, ci, lay, px, py, cs, recs,
                            rec_stride, replay, err);
 
@@ -203,17 +216,18 @@ __global__ void __launch_bounds__(32, 16) k_sweep_fused(
   }
 }
 
-size_t fused_smem_bytes(const RecLayout& lay) { return fused_warp_bytes(lay); }
+size_t fused_smem_bytes(const RecLayout& lay, int fm) { return fused_warp_bytes(lay, fm); }
+size_t fused_scratch_bytes(const RecLayout& lay) { return fused_fp64_bytes(lay); }
 
-template <int TPC>
+template <int TPC, int FM>
 static int configure_fused_t(size_t sm, int* blocks_per_sm) {
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return -1;
   int nb0 = 0, nb1 = 0;
-  auto k0 = k_sweep_fused<TPC, false>;
-  auto k1 = k_sweep_fused<TPC, true>;
+  auto k0 = k_sweep_fused<TPC, false, FM>;
+  auto k1 = k_sweep_fused<TPC, true, FM>;
   cudaFuncAttributes fa0, fa1;
   if (cudaFuncGetAttributes(&fa0, k0) != cudaSuccess ||
       cudaFuncGetAttributes(&fa1, k1) != cudaSuccess)
@@ -230,36 +244,42 @@ static int configure_fused_t(size_t sm, int* blocks_per_sm) {
   return *blocks_per_sm > 0 ? 0 : -1;
 }
 
-int configure_fused(const RecLayout& lay, int tpc, int* blocks_per_sm) {
-  const size_t sm = fused_smem_bytes(lay);
+int configure_fused(const RecLayout& lay, int tpc, int fm, int* blocks_per_sm) {
+  const size_t sm = fused_smem_bytes(lay, fm);
+#define ECMC_FCFG(T) \
+  case T: return fm == 1 ? configure_fused_t<T, 1>(sm, blocks_per_sm) \
+                         : configure_fused_t<T, 0>(sm, blocks_per_sm);
   switch (tpc) {
-    case 1: return configure_fused_t<1>(sm, blocks_per_sm);
-    case 2: return configure_fused_t<2>(sm, blocks_per_sm);
-    case 4: return configure_fused_t<4>(sm, blocks_per_sm);
-    case 8: return configure_fused_t<8>(sm, blocks_per_sm);
-    case 16: return configure_fused_t<16>(sm, blocks_per_sm);
-    case 32: return configure_fused_t<32>(sm, blocks_per_sm);
+    ECMC_FCFG(1)
+    ECMC_FCFG(2)
+    ECMC_FCFG(4)
+    ECMC_FCFG(8)
+    ECMC_FCFG(16)
+    ECMC_FCFG(32)
     default: return -1;
   }
+#undef ECMC_FCFG
 }
 
-template <int TPC, bool SCREEN>
+template <int TPC, bool SCREEN, int FM>
 static int launch_fused_t(const DevBufs& b, const RecLayout& lay, int blocks, int records_on,
                           cudaStream_t s) {
-  k_sweep_fused<TPC, SCREEN><<<blocks, 32, fused_smem_bytes(lay), s>>>(
+  k_sweep_fused<TPC, SCREEN, FM><<<blocks, 32, fused_smem_bytes(lay, FM), s>>>(
       b.rg, b.state, b.act_rep, b.A_total, b.cap, b.px[b.cur], b.py[b.cur], b.pid[b.cur],
       b.count[b.cur], lay, b.cell_stats, records_on ? b.chain_recs : nullptr, b.rec_stride,
-      b.replay, b.sched, b.done, b.wait_ns, b.wait_test, b.err);
+      b.replay, b.sched, b.done, b.wait_ns, b.wait_test, b.records, b.err);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int launch_fused(const DevBufs& b, const RecLayout& lay, int tpc, int blocks, int records_on,
                  int precision, cudaStream_t s) {
   const bool scr = precision == 1;
-#define ECMC_FCASE(T)                                                        \
-  case T:                                                                    \
-    return scr ? launch_fused_t<T, true>(b, lay, blocks, records_on, s)      \
-               : launch_fused_t<T, false>(b, lay, blocks, records_on, s);
+#define ECMC_FCASE(T)                                                                   \
+  case T:                                                                               \
+    return scr ? (b.fmode == 1 ? launch_fused_t<T, true, 1>(b, lay, blocks, records_on, s)    \
+                               : launch_fused_t<T, true, 0>(b, lay, blocks, records_on, s))   \
+               : (b.fmode == 1 ? launch_fused_t<T, false, 1>(b, lay, blocks, records_on, s)   \
+                               : launch_fused_t<T, false, 0>(b, lay, blocks, records_on, s));
   switch (tpc) {
     ECMC_FCASE(1)
     ECMC_FCASE(2)

@@ -65,7 +65,8 @@ class Timing(C.Structure):
 
 class TuneResult(C.Structure):
     _fields_ = [("lanes_per_cell", C.c_int), ("warps_per_block", C.c_int),
-                ("frame_mode", C.c_int), ("ms_per_sweep", C.c_double)]
+                ("frame_mode", C.c_int), ("persistent", C.c_int),
+                ("ms_per_sweep", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -136,6 +136,9 @@ def test_autotune_keeps_the_trajectory():
     b.sweep(2)
     best, shapes = a.autotune(trial_sweeps=2)
     assert len(shapes) >= 3 and best["ms_per_sweep"] == min(s["ms_per_sweep"] for s in shapes)
+    # both the persistent sweep kernel and the per-phase kernels were timed
+    assert {s["persistent"] for s in shapes} == {0, 1}
+    assert a.get_param(E.PARAM_PERSISTENT) == best["persistent"]
     assert a.get_param(E.PARAM_LANES_PER_CELL) == best["lanes_per_cell"]
     assert a.sweep_index() == 2 and np.array_equal(a.positions(), b.positions())
     assert a.counters().sweeps == b.counters().sweeps

@@ -292,14 +292,17 @@ def test_frame_placements(fmode, tpc):
     (4096, 0.72, 4, 8, 4.0, 3, 8),     # rectangular cells, 128 disks each
     (4096, 0.72, 16, 16, 2.0, 1, 32),  # one cell per warp
 ])
-def test_persistent_sweep_matches_oracle(N, eta, cx, cy, ell, nm, tpc):
+@pytest.mark.parametrize("fmode", [0, 1])
+def test_persistent_sweep_matches_oracle(N, eta, cx, cy, ell, nm, tpc, fmode):
     # one launch per sweep: work list over (phase, group) with waits on the
-    # neighbours of earlier phases; same trajectory as the phase launches
-    g, _, _ = make(N, eta, cx, cy, ell, nm, 7, tpc=tpc)
+    # neighbours of earlier phases; frames wholly in shared memory (0) or FP64
+    # coordinates in a per-warp global scratch area (1)
+    g, _, _ = make(N, eta, cx, cy, ell, nm, 7, tpc=tpc, fmode=fmode)
     assert g.get_param(E.PARAM_PERSISTENT) == 1
+    assert g.get_param(E.PARAM_FRAME_MODE) == fmode
     assert g.get_param(E.PARAM_KERNELS_PER_SWEEP) == 5
     g.close()
-    run_pair(N, eta, cx, cy, ell, nm, 7, 4, tpc=tpc)
+    run_pair(N, eta, cx, cy, ell, nm, 7, 4, tpc=tpc, fmode=fmode)
 
 
 def test_persistent_and_phase_launches_are_bitwise_equal():
