@@ -5,7 +5,7 @@
 
 namespace ecmc {
 
-__global__ void k_frame_build(const Geom* __restrict__ rg, const SweepState* __restrict__ sts,
+__global__ void __launch_bounds__(1024) k_frame_build(const Geom* __restrict__ rg, const SweepState* __restrict__ sts,
                               const int* __restrict__ act_rep, int cap, int colour_index,
                               const double* __restrict__ px, const double* __restrict__ py,
                               const int* __restrict__ pid, const int* __restrict__ cnt,
