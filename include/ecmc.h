@@ -64,7 +64,11 @@ extern "C" {
 #define ECMC_PARAM_N_CHAINS 1
 /* Direction rule: ECMC_DIR_PM_AXIS_ALT (default) = axis x on even sweeps and
  * y on odd sweeps, sign drawn per chain; ECMC_DIR_POS_ONLY = sign always +
- * (a variant that is not reversible, Sec. 3.2; kept for negative tests). */
+ * (a variant that is not reversible, Sec. 3.2; kept for negative tests);
+ * ECMC_DIR_ISOTROPIC = a uniform unit direction per chain (rejection-sampled
+ * point of the unit disc divided by its length), specular reflection at
+ * frozen disks (Fig. 1, Sec. 3.4), every candidate tested in FP64; runs in the
+ * per-phase kernels. */
 #define ECMC_PARAM_DIR_MODE 2
 /* Candidate geometry: ECMC_PREC_FP64 = every candidate tested in FP64;
  * ECMC_PREC_FP32_GEOM (default) = candidates screened in FP32 cell-relative
@@ -124,6 +128,7 @@ extern "C" {
 
 #define ECMC_DIR_PM_AXIS_ALT 0
 #define ECMC_DIR_POS_ONLY 1
+#define ECMC_DIR_ISOTROPIC 2
 #define ECMC_PREC_FP64 0
 #define ECMC_PREC_FP32_GEOM 1
 

@@ -245,7 +245,8 @@ int compute_layout(ecmc_ctx* h) {
   // global memory, more warps per SM (measured at N = 1M, eta = 0.72: 1.64
   // against 1.58 * 10^9 events/s)
   const int fm = h->fmode_param == 1 ? 1 : 0;
-  if (h->persist_param && fmode < 2 && fused_smem_bytes(h->lay, fm) <= limit / 2) {
+  // isotropic chains run in the per-phase kernels only
+  if (h->persist_param && !h->b.iso && fmode < 2 && fused_smem_bytes(h->lay, fm) <= limit / 2) {
     int per_sm = 0;
     if (configure_fused(h->lay, h->tpc, fm, &per_sm) == 0) {
       const int n_items = 4 * n_groups;
@@ -878,10 +879,13 @@ int ecmc_set_param(ecmc_t h, int key, double v) {
       if (rc) return rc;
       return realloc_chain_recs(h);
     }
-    case ECMC_PARAM_DIR_MODE:
-      if (v != 0.0 && v != 1.0) return fail(ECMC_ERR_ARG, "direction mode");
+    case ECMC_PARAM_DIR_MODE: {
+      if (v != 0.0 && v != 1.0 && v != 2.0) return fail(ECMC_ERR_ARG, "direction mode");
       for (Geom& g : h->geo) g.dir_mode = (int)v;
-      return upload_geometry(h);
+      h->b.iso = v == 2.0 ? 1 : 0;
+      drop_graphs(h);
+      return compute_layout(h);
+    }
     case ECMC_PARAM_PRECISION:
       if (v != 0.0 && v != 1.0) return fail(ECMC_ERR_ARG, "precision");
       h->precision = (int)v;

@@ -42,7 +42,9 @@ __global__ void k_sweep_begin(const Geom* __restrict__ rg, SweepState* st, int R
     --left;
   }
   s.perm[3] = pool[0];
-  s.axis = (int)(t & 1);
+  // axis chains alternate x (even sweeps) and y; isotropic chains use the
+  // frame coordinates in (x, y) order
+  s.axis = g.dir_mode == 2 ? 0 : (int)(t & 1);
 }
 
 void launch_sweep_begin(const DevBufs& b, cudaStream_t s) {

@@ -51,7 +51,7 @@ struct Frame {
   float* a32;
   const float* b32;
   double* a64;
-  const double* b64;
+  double* b64;  // written only by isotropic chains (axis chains keep the cross coordinate)
   const int* key;
   const int* info;
   unsigned char* touched;

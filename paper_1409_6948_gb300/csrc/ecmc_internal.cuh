@@ -162,6 +162,7 @@ struct DevBufs {
   ChunkSums* partials;     // [n_chunks]
   int n_chunks;
   int replay;              // 1 = replay repeating reflection legs (chain kernel)
+  int iso;                 // 1 = isotropic directions (per-phase chain kernel only)
   unsigned* sched;         // persistent sweep: [0] next work item, [1] epoch, [2] abort
   unsigned* done;          // [C_total] epoch in which each cell last finished
   unsigned long long wait_ns;  // limit of one dependency wait

@@ -2,6 +2,7 @@
 // launch per phase, frames staged by k_frame_build (the chain loop itself is
 // in ecmc_chain.cuh).
 #include "ecmc_chain.cuh"
+#include "ecmc_chain_iso.cuh"
 
 namespace ecmc {
 
@@ -10,7 +11,7 @@ namespace ecmc {
 // FP64 coordinates are read and written in place in global memory (more
 // cells fit in shared memory at once); FMODE 2: the whole record is used in
 // place in global memory (cells too large for shared memory).
-template <int TPC, bool SCREEN, int FMODE>
+template <int TPC, bool SCREEN, int FMODE, bool ISO = false>
 __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
                                                const SweepState* __restrict__ sts,
                                                const int* __restrict__ act_rep, int colour_index,
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
   f.a32 = (float*)(base + lay.off_a32);
   f.b32 = (const float*)(base + lay.off_b32);
   f.a64 = (double*)((FMODE == 1 ? grec : base) + lay.off_a64);
-  f.b64 = (const double*)((FMODE == 1 ? grec : base) + lay.off_b64);
+  f.b64 = (double*)((FMODE == 1 ? grec : base) + lay.off_b64);
   f.key = (const int*)(base + lay.off_key);
   f.info = (const int*)(base + lay.off_info);
   f.touched = tbase;
@@ -79,8 +80,12 @@ __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
   const int a = G * CPW + gi;  // global active cell of this lane group
   const bool valid = a < n_active;
   const int rep = valid ? act_rep[a] : act_rep[n_active - 1];
-  run_group<TPC, SCREEN>(f, hs, hdr, rg, sts, rep, a, valid, colour_index, lay, px, py, cs, recs,
-                         rec_stride, replay, err);
+  if constexpr (ISO)
+    run_group_iso<TPC>(f, hdr, rg, sts, rep, a, valid, colour_index, px, py, cs, recs, rec_stride,
+                       err);
+  else
+    run_group<TPC, SCREEN>(f, hs, hdr, rg, sts, rep, a, valid, colour_index, lay, px, py, cs,
+                           recs, rec_stride, replay, err);
 }
 
 size_t phase_smem_bytes(const RecLayout& lay, int warps_per_block, int fmode) {
@@ -98,14 +103,20 @@ static int launch_t(const DevBufs& b, const RecLayout& lay, int colour_index, in
   const int n_groups = (n_active + cpw - 1) / cpw;
   const int blocks = (n_groups + warps - 1) / warps;
   const size_t sm = phase_smem_bytes(lay, warps, b.fmode);
-#define ECMC_PHASE(FM)                                                                     \
-  k_phase<TPC, SCREEN, FM><<<blocks, 32 * warps, sm, s>>>(                                 \
+#define ECMC_PHASE(FM, ISO)                                                                \
+  k_phase<TPC, SCREEN && !ISO, FM, ISO><<<blocks, 32 * warps, sm, s>>>(                    \
       b.rg, b.state, b.act_rep, colour_index, b.records, b.gtouch, lay, n_active,          \
       b.px[b.cur], b.py[b.cur], b.cell_stats, records_on ? b.chain_recs : nullptr,         \
       b.rec_stride, b.replay, b.err)
-  if (b.fmode == 2) ECMC_PHASE(2);
-  else if (b.fmode == 1) ECMC_PHASE(1);
-  else ECMC_PHASE(0);
+  if (b.iso) {
+    if (b.fmode == 2) ECMC_PHASE(2, true);
+    else if (b.fmode == 1) ECMC_PHASE(1, true);
+    else ECMC_PHASE(0, true);
+  } else {
+    if (b.fmode == 2) ECMC_PHASE(2, false);
+    else if (b.fmode == 1) ECMC_PHASE(1, false);
+    else ECMC_PHASE(0, false);
+  }
 #undef ECMC_PHASE
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -138,6 +149,7 @@ template <int TPC, int FM>
 static int configure_t(size_t sm) {
   if (configure_fn(k_phase<TPC, true, FM>, sm)) return -1;
   if (configure_fn(k_phase<TPC, false, FM>, sm)) return -1;
+  if (configure_fn(k_phase<TPC, false, FM, true>, sm)) return -1;
   return 0;
 }
 

@@ -39,6 +39,7 @@ PARAM_KERNELS_PER_SWEEP = 18
 
 DIR_PM_AXIS_ALT = 0
 DIR_POS_ONLY = 1
+DIR_ISOTROPIC = 2
 PREC_FP64 = 0
 PREC_FP32_GEOM = 1
 

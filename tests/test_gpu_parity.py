@@ -126,6 +126,18 @@ def test_positive_only_direction_rule():
     run_pair(1024, 0.70, 4, 4, 4.0, 2, 3, 4, dir_mode=1)
 
 
+@pytest.mark.parametrize("N,eta,cx,ell,nm,tpc", [
+    (256, 0.70, 2, 4.0, 2, 8),     # two cells per side
+    (1024, 0.70, 8, 6.0, 2, 4),    # chains longer than a cell: many wall reflections
+    (4096, 0.72, 16, 2.0, 1, 32),
+    (1024, 0.30, 4, 3.0, 3, 0),    # dilute, automatic lanes per cell
+])
+def test_isotropic_directions(N, eta, cx, ell, nm, tpc):
+    # uniform directions per chain, specular reflection at frozen disks (Fig. 1)
+    st = run_pair(N, eta, cx, cx, ell, nm, 7, 5, tpc=tpc, dir_mode=2)
+    assert st.frozen_hits > 0 and st.wall_hits > 0
+
+
 def test_replica_key_changes_the_stream():
     st = run_pair(1024, 0.70, 4, 4, 4.0, 2, 3, 2, replica=5)
     assert st.chains == 2 * 16 * 2
