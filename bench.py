@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--autotune", action="store_true", help="tune the launch shape first")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--fmode", type=int, default=-1, help="frame placement 0/1/2 (-1 automatic)")
+    ap.add_argument("--dir", default="axis", choices=["axis", "iso"],
+                    help="chain directions: alternating axes (default) or isotropic")
     ap.add_argument("--persistent", type=int, default=-1,
                     help="1 one persistent launch per sweep, 0 per-phase launches (-1 default)")
     ap.add_argument("--melt", type=int, default=-1,
@@ -186,7 +188,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(w, cells, ell, nm, seconds, melt=0, max_sweeps=1000):
+def cpu_baseline(w, cells, ell, nm, seconds, melt=0, max_sweeps=1000, dir_mode=0):
     """The oracle, as it stands, single-threaded on this host: the same melt
     sweeps (untimed), then sweeps of the same workload until `seconds` have
     passed."""
@@ -196,7 +198,7 @@ def cpu_baseline(w, cells, ell, nm, seconds, melt=0, max_sweeps=1000):
     x, y = W.square_lattice(w.N, L)
     if nm == 0:
         nm = oracle.default_nm(w.N, L, 1.0, cells, cells, ell)
-    p = oracle.make_params(w.N, L, 1.0, cells, cells, ell, nm, w.seed)
+    p = oracle.make_params(w.N, L, 1.0, cells, cells, ell, nm, w.seed, dir_mode=dir_mode)
     oracle.sweeps(p, x, y, 0, melt)
     st = oracle.Stats()
     t0 = time.perf_counter()
@@ -388,6 +390,8 @@ def run_ours(args):
         g.set_param(E.PARAM_FRAME_MODE, args.fmode)
     if args.persistent >= 0:
         g.set_param(E.PARAM_PERSISTENT, args.persistent)
+    if args.dir == "iso":
+        g.set_param(E.PARAM_DIR_MODE, E.DIR_ISOTROPIC)
     # a stream of our own (torch's default stream is the legacy NULL stream,
     # which the library reads as "use your own stream")
     stream = torch.cuda.Stream()
@@ -513,7 +517,8 @@ def run_ours(args):
         _, fp64_probe = P.ecmc.device_peaks()
         cpu = None
         if not args.skip_cpu and descs is None:
-            cpu = cpu_baseline(w, cells, ell, nm, args.cpu_seconds, melt_sweeps(args))
+            cpu = cpu_baseline(w, cells, ell, nm, args.cpu_seconds, melt_sweeps(args),
+                               dir_mode=2 if args.dir == "iso" else 0)
         elif not args.skip_cpu:
             cpu = cpu_baseline_batch(descs, args.cpu_seconds)
         line = {
@@ -530,7 +535,8 @@ def run_ours(args):
                        "start": "square lattice, %d untimed sweeps, then %d warm-up sweeps"
                                 % (melt_sweeps(args), args.warmup),
                        "parallelism": "replicas x%d" % world,
-                       "launch": "persistent sweep kernel" if persistent else "per-phase kernels"},
+                       "launch": "persistent sweep kernel" if persistent else "per-phase kernels",
+                       "directions": "isotropic" if args.dir == "iso" else "alternating axes"},
             "sweeps_per_s": sweeps_all / (ms_max * 1e-3),
             "events_per_sweep": events / max(sweeps, 1),
             "per_sweep": {"chains": c.chains / max(sweeps, 1),

@@ -25,10 +25,11 @@ from test_oracle_pressure import virial  # noqa: E402
 
 
 def gpu_batches(N, eta, cells, ell, nm, seed, n_batches, per_batch, warm, gr_every=0, dr=0.02,
-                nbins=10):
+                nbins=10, dir_mode=0):
     L = W.box_side(N, eta)
     g = P.Ecmc(N, L, 1.0, cells, cells, ell, seed)
     g.set_param(E.PARAM_N_CHAINS, nm)
+    g.set_param(E.PARAM_DIR_MODE, dir_mode)
     g.set_param(E.PARAM_GR_DR, dr)
     g.set_param(E.PARAM_GR_RMAX, 1.0 + dr * nbins)
     g.sweep(warm)
@@ -114,3 +115,13 @@ def test_pressure_error_bar_is_batch_means():
     rho = N / L**2
     assert se > 0 and se < 0.05 * p and p > rho
     g.close()
+
+
+def test_isotropic_and_axis_chains_sample_the_same_pressure():
+    # both direction rules are reversible and sample the uniform measure
+    # (Sec. 3.2-3.4): independent runs must agree within 3 combined errors
+    args = (1024, 0.68, 4, 3.0, 2)
+    Pa, sa, _ = gpu_batches(*args, seed=31, n_batches=20, per_batch=300, warm=300)
+    Pi, si, _ = gpu_batches(*args, seed=32, n_batches=20, per_batch=300, warm=300, dir_mode=2)
+    assert abs(Pa - Pi) < 3.0 * math.hypot(sa, si), (Pa, sa, Pi, si)
+
