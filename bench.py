@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large",
                     choices=["small", "medium", "large", "huge", "batch", "eos"])
+    ap.add_argument("--listbias", action="store_true",
+                    help="pressure vs n_m with start lists drawn with and without replacement")
     ap.add_argument("--grid", action="store_true",
                     help="parallelisation grid at N = 1M (cells x ell), one JSON line")
     ap.add_argument("--paper-params", action="store_true",
@@ -289,6 +291,50 @@ def run_grid(args):
             g.close()
     print(json.dumps({"mode": "grid", "workload": w.name, "steps": args.steps,
                       "warmup": args.warmup, "lambda0_eq": lam0, "points": pts}))
+    return 0
+
+
+def run_listbias(args):
+    """Start lists with and without replacement (Sec. 3.4, Fig. 3 right): the
+    chain-estimator pressure against the number n_m of chains per cell for
+    N = 256^2 disks at eta = 0.708 (32 x 32 cells, ell = 8 sigma), after a
+    melt of 100 sweeps; each point runs 4000 / n_m sweeps (the same number of
+    chains), error bars from batch means."""
+    import torch
+
+    import paper_1409_6948_gb300 as P
+    from paper_1409_6948_gb300 import ecmc as E
+
+    torch.cuda.set_device(0)
+    w = W.MEDIUM
+    pts = []
+    for nm in (1, 2, 4, 8, 16):
+        for mode in (E.LIST_WITH_REPL, E.LIST_WITHOUT_REPL):
+            g = P.Ecmc(w.N, w.L, 1.0, w.cells, w.cells, w.ell, w.seed)
+            g.set_param(E.PARAM_N_CHAINS, nm)
+            g.set_param(E.PARAM_LIST_MODE, mode)
+            g.sweep(100)
+            g.reset_stats()
+            s = torch.cuda.Stream()
+            g.set_stream(s)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            g.sweep(4000 // nm)
+            b.record(s)
+            torch.cuda.synchronize()
+            p, se = g.pressure()
+            c = g.counters()
+            pts.append({"n_m": nm, "list": "with replacement" if mode == 0 else "shuffled",
+                        "betaP_sigma2": p, "stderr": se, "sweeps": 4000 // nm,
+                        "events_per_s": c.events / (a.elapsed_time(b) * 1e-3)})
+            g.set_stream(None)
+            g.close()
+    for nm in (1, 2, 4, 8, 16):
+        pw = [q for q in pts if q["n_m"] == nm]
+        d = pw[1]["betaP_sigma2"] - pw[0]["betaP_sigma2"]
+        pw[1]["difference_in_combined_se"] = d / math.hypot(pw[0]["stderr"], pw[1]["stderr"])
+    print(json.dumps({"mode": "list_bias", "workload": "N=65536 eta=0.708 cells=32x32 ell=8",
+                      "points": pts}))
     return 0
 
 
@@ -622,6 +668,8 @@ def main():
         return run_reference(args)
     if args.grid:
         return run_grid(args)
+    if args.listbias:
+        return run_listbias(args)
     return run_ours(args)
 
 

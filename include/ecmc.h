@@ -125,6 +125,16 @@ extern "C" {
 /* Read-only: kernel launches per sweep of the current configuration (5 with
  * the persistent kernel, 12 with per-phase launches). */
 #define ECMC_PARAM_KERNELS_PER_SWEEP 18
+/* Start lists (Sec. 3.4 step 5): ECMC_LIST_WITH_REPL (default), every start
+ * disk drawn independently among the members (the paper's correct rule);
+ * ECMC_LIST_WITHOUT_REPL, a negative control: the first start as drawn, then a
+ * uniformly shuffled list of the other members (Fisher-Yates with Philox
+ * draws), cycled when n_m exceeds the members -- the list form the paper shows
+ * to bias the pressure (Fig. 3).  Needs cells of at most 128 disks
+ * (ECMC_ERR_UNSUPPORTED otherwise); disables the replay of rattling chains. */
+#define ECMC_PARAM_LIST_MODE 19
+#define ECMC_LIST_WITH_REPL 0
+#define ECMC_LIST_WITHOUT_REPL 1
 
 #define ECMC_DIR_PM_AXIS_ALT 0
 #define ECMC_DIR_POS_ONLY 1

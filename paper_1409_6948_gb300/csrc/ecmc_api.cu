@@ -953,6 +953,18 @@ int ecmc_set_param(ecmc_t h, int key, double v) {
       return ECMC_OK;
     case ECMC_PARAM_KERNELS_PER_SWEEP:
       return fail(ECMC_ERR_ARG, "kernels per sweep is read-only");
+    case ECMC_PARAM_LIST_MODE: {
+      if (v != 0.0 && v != 1.0) return fail(ECMC_ERR_ARG, "list mode must be 0 or 1");
+      if (v == 1.0)
+        for (const Geom& g : h->geo)
+          if (g.cap_mem > 128)
+            return fail(ECMC_ERR_UNSUPPORTED,
+                        "shuffled start lists need cells of at most 128 disks (bound %d)",
+                        g.cap_mem);
+      for (Geom& g : h->geo) g.list_mode = (int)v;
+      drop_graphs(h);
+      return upload_geometry(h);
+    }
     case ECMC_PARAM_REPLAY:
       if (v != 0.0 && v != 1.0) return fail(ECMC_ERR_ARG, "replay must be 0 or 1");
       h->b.replay = (int)v;
@@ -991,6 +1003,7 @@ int ecmc_get_param(ecmc_t h, int key, double* v) {
     case ECMC_PARAM_WAIT_LIMIT_MS: *v = h->wait_ms; break;
     case ECMC_PARAM_WAIT_TEST: *v = h->b.wait_test; break;
     case ECMC_PARAM_KERNELS_PER_SWEEP: *v = h->persistent ? 5 : 12; break;
+    case ECMC_PARAM_LIST_MODE: *v = h->geo[0].list_mode; break;
     default: return fail(ECMC_ERR_ARG, "unknown parameter %d", key);
   }
   return ECMC_OK;

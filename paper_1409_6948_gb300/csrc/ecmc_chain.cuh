@@ -86,6 +86,33 @@ __device__ __forceinline__ bool better(double s, int key, double bs, int bkey) {
   return s < bs || (s == bs && key < bkey);
 }
 
+// Start list without replacement (the negative control of Sec. 3.4): entry 0
+// is the member drawn for chain 0, entries 1..n-1 the other members in
+// ascending rank, shuffled by Fisher-Yates from the top: position i (n-1 down
+// to 2) swaps with 1 + floor(u n_i / 2^64), u word i mod 4 of the Philox draw
+// (sweep, shuffle purpose, cell, i / 4).  pl holds up to kHist * 8 entries per
+// group, interleaved [entry][group].
+__device__ __forceinline__ void shuffled_list(int* pl, int CPW, int gi, int n, int first,
+                                              int64_t t, int lc, uint64_t seed,
+                                              uint64_t replica) {
+  int q = 0;
+  pl[gi] = first;
+  for (int i = 0; i < n; ++i)
+    if (i != first) pl[(++q) * CPW + gi] = i;
+  U64x4 u;
+  int cur = -1;
+  for (int i = n - 1; i >= 2; --i) {
+    if ((i >> 2) != cur) {
+      cur = i >> 2;
+      u = philox((uint64_t)t, kPurposeShuffle, (uint64_t)lc, (uint64_t)cur, seed, replica);
+    }
+    const int j = 1 + (int)below_n(u.v[i & 3], (uint64_t)i);
+    const int a = pl[i * CPW + gi];
+    pl[i * CPW + gi] = pl[j * CPW + gi];
+    pl[j * CPW + gi] = a;
+  }
+}
+
 // Cycle replay.  Called after a reflection, with the state (m, sg, P) the next
 // leg starts from.  If for some even K <= kHist the configuration equals the
 // one K legs earlier -- the same active disk, direction and position bit for
@@ -223,7 +250,15 @@ __device__ __forceinline__ void run_group(const Frame& f, const LegHist& hs, con
         // start disk drawn with replacement among the members, sign of d
         const U64x4 v = philox((uint64_t)t, kPurposeChain, (uint64_t)lc, (uint64_t)k, g.seed,
                                g.replica);
-        const int idx = (int)below_n(v.v[0], (uint64_t)nmem);
+        int idx = (int)below_n(v.v[0], (uint64_t)nmem);
+        if (g.list_mode == 1) {
+          // negative control: the first start as drawn, then a uniformly
+          // shuffled list of the other members, cycled (kept in the leg
+          // history's space: no replay in this mode)
+          int* pl = (int*)hs.P;
+          if (k == 0) shuffled_list(pl, CPW, gi, nmem, idx, t, lc, g.seed, g.replica);
+          idx = pl[(k % nmem) * CPW + gi];
+        }
         m = f.mrank[idx * CPW + gi];
         sg = (g.dir_mode == 1) ? 1 : ((v.v[1] >> 63) ? -1 : 1);
         P = f.a64[m * CPW + gi];
@@ -427,7 +462,7 @@ __device__ __forceinline__ void run_group(const Frame& f, const LegHist& hs, con
       n_walls += is_wall ? 1 : 0;
       ch_walls += is_wall ? 1 : 0;
       n_iter += (is_contact || is_wall) ? 1 : 0;
-      if (replay && !is_end) {
+      if (replay && g.list_mode == 0 && !is_end) {
         // every lane of the group writes the same values, so each lane reads
         // back its own writes
         const int hl = (n_leg & (kHist - 1)) * CPW + gi;
@@ -454,7 +489,7 @@ __device__ __forceinline__ void run_group(const Frame& f, const LegHist& hs, con
         if (!is_end) {
           // frozen disk or wall: the chain turns back along its axis
           sg = -sg;
-          if (replay) replay_cycle(f, hs, gi, n_leg, m, sg, P, P32, Q, Q32, r, n_iter, sum_b,
+          if (replay && g.list_mode == 0) replay_cycle(f, hs, gi, n_leg, m, sg, P, P32, Q, Q32, r, n_iter, sum_b,
                                    n_events, n_lifts, n_frozen, n_walls, ch_events, ch_walls,
                                    n_replayed);
         }

@@ -54,7 +54,7 @@ __device__ __forceinline__ void iso_direction(int64_t t, int lc, int k, uint64_t
 }
 
 template <int TPC>
-__device__ __forceinline__ void run_group_iso(const Frame& f, const int* hdr,
+__device__ __forceinline__ void run_group_iso(const Frame& f, const int* hdr, void* hl,
                                               const Geom* __restrict__ rg,
                                               const SweepState* __restrict__ sts, int rep, int a,
                                               bool valid, int colour_index,
@@ -98,7 +98,12 @@ __device__ __forceinline__ void run_group_iso(const Frame& f, const int* hdr,
       } else {
         const U64x4 v = philox((uint64_t)t, kPurposeChain, (uint64_t)lc, (uint64_t)k, g.seed,
                                g.replica);
-        const int idx = (int)below_n(v.v[0], (uint64_t)nmem);
+        int idx = (int)below_n(v.v[0], (uint64_t)nmem);
+        if (g.list_mode == 1) {
+          int* pl = (int*)hl;
+          if (k == 0) shuffled_list(pl, CPW, gi, nmem, idx, t, lc, g.seed, g.replica);
+          idx = pl[(k % nmem) * CPW + gi];
+        }
         m = f.mrank[idx * CPW + gi];
         iso_direction(t, lc, k, g.seed, g.replica, dx, dy);
         X = f.a64[m * CPW + gi];

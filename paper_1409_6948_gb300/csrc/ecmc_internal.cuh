@@ -31,7 +31,7 @@ enum DevErr : int {
 };
 
 constexpr int64_t kMaxEventsPerChain = int64_t(1) << 22;
-constexpr uint64_t kPurposeSweep = 0, kPurposeChain = 1;
+constexpr uint64_t kPurposeSweep = 0, kPurposeChain = 1, kPurposeShuffle = 2;
 
 // ---- per-sweep device state ------------------------------------------------
 struct SweepState {
@@ -82,6 +82,7 @@ struct Geom {
   int cells_x, cells_y, ncell;
   int n_m;
   int dir_mode;
+  int list_mode;     // 0 start disks drawn with replacement, 1 a shuffled list (negative control)
   uint64_t seed, replica;
   int cap_mem;       // slots per cell bucket (members)
   int cap_obj;       // objects per frame (members + frozen images)

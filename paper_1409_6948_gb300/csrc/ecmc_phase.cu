@@ -81,8 +81,8 @@ __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
   const bool valid = a < n_active;
   const int rep = valid ? act_rep[a] : act_rep[n_active - 1];
   if constexpr (ISO)
-    run_group_iso<TPC>(f, hdr, rg, sts, rep, a, valid, colour_index, px, py, cs, recs, rec_stride,
-                       err);
+    run_group_iso<TPC>(f, hdr, hs.P, rg, sts, rep, a, valid, colour_index, px, py, cs, recs,
+                       rec_stride, err);
   else
     run_group<TPC, SCREEN>(f, hs, hdr, rg, sts, rep, a, valid, colour_index, lay, px, py, cs,
                            recs, rec_stride, replay, err);

@@ -36,6 +36,9 @@ PARAM_PERSISTENT = 15
 PARAM_WAIT_LIMIT_MS = 16
 PARAM_WAIT_TEST = 17
 PARAM_KERNELS_PER_SWEEP = 18
+PARAM_LIST_MODE = 19
+LIST_WITH_REPL = 0
+LIST_WITHOUT_REPL = 1
 
 DIR_PM_AXIS_ALT = 0
 DIR_POS_ONLY = 1

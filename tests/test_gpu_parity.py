@@ -30,7 +30,7 @@ LAST = {}  # counters of the most recent run_pair, for tests that inspect them
 
 
 def make(N, eta, cells_x, cells_y, ell, nm, seed, tpc=0, prec=1, dir_mode=0, records=False,
-         replica=0, fmode=-1, persistent=1):
+         replica=0, fmode=-1, persistent=1, list_mode=0):
     L = W.box_side(N, eta)
     g = P.Ecmc(N, L, 1.0, cells_x, cells_y, ell, seed)
     g.set_param(E.PARAM_N_CHAINS, nm)
@@ -42,10 +42,11 @@ def make(N, eta, cells_x, cells_y, ell, nm, seed, tpc=0, prec=1, dir_mode=0, rec
     if fmode >= 0:
         g.set_param(E.PARAM_FRAME_MODE, fmode)
     g.set_param(E.PARAM_PERSISTENT, persistent)
+    g.set_param(E.PARAM_LIST_MODE, list_mode)
     if records:
         g.set_param(E.PARAM_RECORD_CHAINS, 1)
     p = oracle.make_params(N, L, 1.0, cells_x, cells_y, ell, nm, seed, replica,
-                           dir_mode=dir_mode)
+                           dir_mode=dir_mode, list_mode=list_mode)
     return g, p, L
 
 
@@ -136,6 +137,18 @@ def test_isotropic_directions(N, eta, cx, ell, nm, tpc):
     # uniform directions per chain, specular reflection at frozen disks (Fig. 1)
     st = run_pair(N, eta, cx, cx, ell, nm, 7, 5, tpc=tpc, dir_mode=2)
     assert st.frozen_hits > 0 and st.wall_hits > 0
+
+
+@pytest.mark.parametrize("N,eta,cx,ell,nm,dir_mode,persistent", [
+    (1024, 0.70, 8, 4.0, 3, 0, 1),   # n_m < members: a prefix of the shuffled list
+    (64, 0.05, 8, 5.0, 3, 0, 1),     # about one member per cell: the list cycles
+    (1024, 0.70, 8, 4.0, 20, 0, 0),  # n_m > members, per-phase kernels
+    (1024, 0.70, 8, 4.0, 3, 2, 0),   # isotropic directions
+])
+def test_shuffled_start_lists(N, eta, cx, ell, nm, dir_mode, persistent):
+    # the negative control of Sec. 3.4: start lists without replacement
+    run_pair(N, eta, cx, cx, ell, nm, 9, 4, dir_mode=dir_mode, persistent=persistent,
+             list_mode=1)
 
 
 def test_replica_key_changes_the_stream():
