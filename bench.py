@@ -21,6 +21,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -57,6 +59,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large",
                     choices=["small", "medium", "large", "huge", "batch", "eos"])
+    ap.add_argument("--tau", action="store_true",
+                    help="autocorrelation time of Psi against n_m and ell (N = 64^2)")
+    ap.add_argument("--tau-max", type=int, default=20000,
+                    help="most sweeps per point of the --tau experiment")
     ap.add_argument("--listbias", action="store_true",
                     help="pressure vs n_m with start lists drawn with and without replacement")
     ap.add_argument("--grid", action="store_true",
@@ -297,9 +303,11 @@ def run_grid(args):
 def run_listbias(args):
     """Start lists with and without replacement (Sec. 3.4, Fig. 3 right): the
     chain-estimator pressure against the number n_m of chains per cell for
-    N = 256^2 disks at eta = 0.708 (32 x 32 cells, ell = 8 sigma), after a
-    melt of 100 sweeps; each point runs 4000 / n_m sweeps (the same number of
-    chains), error bars from batch means."""
+    N = 256^2 disks at eta = 0.708 (32 x 32 cells, ell = 8 sigma).  Every
+    point melts the lattice with 4000 / n_m sweeps and measures over
+    8000 / n_m sweeps (the same number of chains for every n_m); error bars
+    from batch means.  Both list rules start from the same key, so at n_m = 1,
+    where the lists coincide, the runs are identical."""
     import torch
 
     import paper_1409_6948_gb300 as P
@@ -313,19 +321,19 @@ def run_listbias(args):
             g = P.Ecmc(w.N, w.L, 1.0, w.cells, w.cells, w.ell, w.seed)
             g.set_param(E.PARAM_N_CHAINS, nm)
             g.set_param(E.PARAM_LIST_MODE, mode)
-            g.sweep(100)
+            g.sweep(4000 // nm)
             g.reset_stats()
             s = torch.cuda.Stream()
             g.set_stream(s)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(s)
-            g.sweep(4000 // nm)
+            g.sweep(8000 // nm)
             b.record(s)
             torch.cuda.synchronize()
             p, se = g.pressure()
             c = g.counters()
             pts.append({"n_m": nm, "list": "with replacement" if mode == 0 else "shuffled",
-                        "betaP_sigma2": p, "stderr": se, "sweeps": 4000 // nm,
+                        "betaP_sigma2": p, "stderr": se, "sweeps": 8000 // nm,
                         "events_per_s": c.events / (a.elapsed_time(b) * 1e-3)})
             g.set_stream(None)
             g.close()
@@ -335,6 +343,80 @@ def run_listbias(args):
         pw[1]["difference_in_combined_se"] = d / math.hypot(pw[0]["stderr"], pw[1]["stderr"])
     print(json.dumps({"mode": "list_bias", "workload": "N=65536 eta=0.708 cells=32x32 ell=8",
                       "points": pts}))
+    return 0
+
+
+def run_tau(args):
+    """Sampling efficiency (Sec. 2 eq. tau; Figs. 5-6): the autocorrelation
+    time tau of the hexatic order parameter Psi for N = 64^2 disks at
+    eta = 0.704 in 4 x 4 cells (n = 4 blocks), for several chains per cell n_m
+    (ell = 1.28 sigma) and chain displacements ell (n_m from eq. nm).  Each
+    point is a batch of 32 independent replicas (Philox key (8, r)) advanced
+    together, melted by 1000 sweeps; Psi of every replica (Delaunay
+    neighbours within 2.5 sigma, every cell certified) is measured every 5
+    sweeps and the autocorrelation is averaged over the replicas.  Each point
+    runs until the series are at least 30 tau long (at most --tau-max sweeps);
+    tau is given in sweeps and in wall time per replica-sweep.  One JSON line
+    per point, then the summary."""
+    import torch
+
+    import paper_1409_6948_gb300 as P
+    from paper_1409_6948_gb300 import ecmc as E
+
+    torch.cuda.set_device(0)
+    N, eta, cells, seed, R, every = 4096, 0.704, 4, 8, 32, 5
+    L = W.box_side(N, eta)
+    lam0 = (W.ETA_HCP - eta) / (2 * W.ETA_HCP)
+    pts = []
+    settings = [(1, 1.28), (5, 1.28), (20, 1.28), (0, 0.4), (0, 4.0)]
+    for nm, ell in settings:
+        nm_used = nm or max(1, int(math.floor(N / (cells * cells) * lam0 / ell + 0.5)))
+        descs = [dict(N=N, L=L, sigma=1.0, cells_x=cells, cells_y=cells, ell=ell, n_m=nm_used,
+                      seed=seed, replica=r) for r in range(R)]
+        g = P.Ecmc.batch(descs)
+        g.sweep(1000)
+        g.synchronize()
+        series = []
+        n = 0
+        tau = float("inf")
+        t_sweep = t_psi = 0.0
+        n_bad = 0
+        while n < args.tau_max:
+            for _ in range(400):
+                a = time.perf_counter()
+                g.sweep(every)
+                g.synchronize()
+                b = time.perf_counter()
+                psi, _, _, bad = g.hexatic(rs=2.5, per_disk=True)
+                series.append(psi)
+                t_sweep += b - a
+                t_psi += time.perf_counter() - b
+                n_bad += bad
+            n += 400 * every
+            z = np.array(series)            # [samples, replicas]
+            m = z.shape[0]
+            lag = m // 4
+            denom = np.mean(np.abs(z) ** 2)
+            c = np.array([np.real(np.mean(np.conj(z[:m - d]) * z[d:])) / denom
+                          for d in range(lag + 1)])
+            below = np.flatnonzero(c < math.exp(-1.0))
+            if below.size:
+                d = below[0]
+                tau = every * ((d - 1) + (c[d - 1] - math.exp(-1.0)) / (c[d - 1] - c[d]))
+            if n >= 30 * tau:
+                break
+        cnt = g.counters()
+        pt = {"n_m": nm_used, "ell": ell, "tau_sweeps": tau, "sweeps": n, "replicas": R,
+              "mean_abs_psi": float(np.mean(np.abs(series))), "uncertified_cells": n_bad,
+              "ms_per_batch_sweep": 1e3 * t_sweep / n,
+              "ms_per_psi_measurement": 1e3 * t_psi / (n // every),
+              "tau_wall_ms_per_replica": tau * 1e3 * t_sweep / n / R,
+              "events_per_replica_sweep": cnt.events / max(cnt.sweeps, 1) / R}
+        print(json.dumps(pt), flush=True)
+        pts.append(pt)
+        g.close()
+    print(json.dumps({"mode": "tau", "workload": "N=4096 eta=0.704 cells=4x4, 32 replicas",
+                      "lambda0_eq": lam0, "points": pts}))
     return 0
 
 
@@ -670,6 +752,8 @@ def main():
         return run_grid(args)
     if args.listbias:
         return run_listbias(args)
+    if args.tau:
+        return run_tau(args)
     return run_ours(args)
 
 

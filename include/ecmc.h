@@ -352,6 +352,27 @@ ECMC_API int ecmc_chain_records(ecmc_t h, ecmc_chain_rec_t* out, int64_t n);
  * needed; takes a few milliseconds. */
 ECMC_API int ecmc_device_peaks(double* smem_gbs, double* fp64_gflops);
 
+/* Hexatic order parameter of every replica (Sec. 2, eq. Psi): Psi = N^-1 sum_k
+ * Psi_k, Psi_k = sum over the next neighbours l of exp(6 i phi_kl) / n_k, phi
+ * the angle of the vector k -> l to the x axis, next neighbours = Delaunay
+ * neighbours (the paper triangulates with a library).  Disk l within rs of k
+ * (minimum image) is a neighbour when the perpendicular bisector of k and l
+ * keeps a piece of positive length after the half-planes of every other disk
+ * within rs cut it (the Voronoi edge); the result is the exact Delaunay graph
+ * when every Voronoi vertex of k lies within rs/2, and *n_bad counts the
+ * disks for which that check fails (0 in dense fluids with the default rs).
+ *   rs     neighbour radius (<= 0: 3.5 sigma of each replica); L must exceed 2 rs
+ *   psi    [2R] receives Re, Im of Psi of replica r at [2r], [2r+1] (summed
+ *          in disk-id order)
+ *   psi_k  [2N] per-disk Re, Im, disks of all replicas concatenated in id
+ *          order (as ecmc_positions), or NULL
+ *   n_nb   [N] neighbour counts, same order, or NULL
+ *   n_bad  number of uncertified disks, or NULL
+ * Errors: ECMC_ERR_ARG, ECMC_ERR_STATE, ECMC_ERR_CAPACITY (more than 64
+ * disks within rs of one disk), ECMC_ERR_CUDA.  Synchronises the stream. */
+ECMC_API int ecmc_hexatic(ecmc_t h, double rs, double* psi, double* psi_k, int32_t* n_nb,
+                          int64_t* n_bad);
+
 /* The square root of the chain kernel's hit distance (Sec. 3.2: the
  * distance to contact s = b - sqrt(sigma^2 - c^2) is formed in FP64 with the
  * square root correctly rounded to nearest, as IEEE 754 sqrt).  The kernel

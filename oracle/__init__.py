@@ -82,6 +82,9 @@ def lib():
         L.orc_run_chain_frame.restype = C.c_int
         L.orc_sweeps_snap.argtypes = [C.POINTER(Params), d, d, i64, i64, C.POINTER(Stats), d, d]
         L.orc_sweeps_snap.restype = C.c_int
+        L.orc_hexatic.argtypes = [i64, C.c_double, d, d, C.c_double, C.c_void_p, C.c_void_p,
+                                  C.c_void_p]
+        L.orc_hexatic.restype = C.c_int
         _lib = L
     return _lib
 
@@ -173,6 +176,21 @@ def gr_counts(L, x, y, sigma, dr, nbins, i_begin=0, i_end=None, counts=None):
                         int(nbins), int(i_begin), int(i_end),
                         counts.ctypes.data_as(C.POINTER(C.c_int64)))
     return counts
+
+
+def hexatic(L, x, y, rs=3.5):
+    """Hexatic order parameter (eq. Psi) with Delaunay next neighbours.
+    Returns (Psi as a complex number, per-disk Psi_k as complex array,
+    neighbour counts, number of disks whose Voronoi cell was not certified)."""
+    N = x.shape[0]
+    pk = np.empty(2 * N)
+    nn = np.empty(N, np.int32)
+    ps = np.empty(2)
+    bad = lib().orc_hexatic(int(N), float(L), _dptr(x), _dptr(y), float(rs),
+                            pk.ctypes.data, nn.ctypes.data, ps.ctypes.data)
+    if bad < 0:
+        raise ValueError("box too small for the neighbour radius")
+    return complex(ps[0], ps[1]), pk[0::2] + 1j * pk[1::2], nn, bad
 
 
 def min_dist2(L, x, y, rcut=2.0):

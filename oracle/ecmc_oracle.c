@@ -688,6 +688,102 @@ void orc_gr_counts(int64_t N, double L, const double* x, const double* y, double
 }
 
 /* ------------------------------------------------------------------------ */
+/* Hexatic order parameter (Sec. 2, eq. Psi)                                 */
+/* ------------------------------------------------------------------------ */
+/* Next neighbours are the Delaunay neighbours.  Disk l (relative position
+ * d_l from disk k, minimum image) is a Delaunay neighbour of k when the
+ * perpendicular bisector of k and l keeps a piece of positive length after it
+ * is cut by the half-planes p.d_m <= |d_m|^2 / 2 of every other disk m within
+ * rs of k: that piece is the Voronoi edge between k and l.  The result is the
+ * exact Delaunay graph when every Voronoi vertex of k lies within rs/2 of k
+ * (a disk beyond rs cannot cut the cell then); disks for which that check
+ * fails are counted in the return value.  Psi_k = sum over neighbours of
+ * exp(6 i phi_kl) / n_k, exp(6 i phi) = (dx + i dy)^6 / |d|^6 with no
+ * trigonometric function.  Returns -1 if L <= 2 rs. */
+int orc_hexatic(int64_t N, double L, const double* x, const double* y, double rs,
+                double* psi_k, int32_t* n_nb, double* psi) {
+  if (!(L > 2.0 * rs) || N < 1) return -1;
+  int cap = 64;
+  double* cx = (double*)malloc(sizeof(double) * cap);
+  double* cy = (double*)malloc(sizeof(double) * cap);
+  const double rs2 = rs * rs, v2max = 0.25 * rs * rs;
+  double sre = 0.0, sim = 0.0;
+  int bad = 0;
+  for (int64_t k = 0; k < N; ++k) {
+    int nc = 0;
+    for (int64_t j = 0; j < N; ++j) {
+      if (j == k) continue;
+      double ddx = wrap_centered(x[j] - x[k], L);
+      double ddy = wrap_centered(y[j] - y[k], L);
+      if (!(ddx * ddx + ddy * ddy < rs2)) continue;
+      if (nc == cap) {
+        cap *= 2;
+        cx = (double*)realloc(cx, sizeof(double) * cap);
+        cy = (double*)realloc(cy, sizeof(double) * cap);
+      }
+      cx[nc] = ddx;
+      cy[nc] = ddy;
+      nc++;
+    }
+    double re = 0.0, im = 0.0;
+    int n = 0, ok = 1;
+    for (int l = 0; l < nc; ++l) {
+      const double ux = -cy[l], uy = cx[l];          /* along the bisector   */
+      const double px0 = 0.5 * cx[l], py0 = 0.5 * cy[l]; /* its midpoint    */
+      double tlo = -INFINITY, thi = INFINITY;
+      for (int m = 0; m < nc && tlo < thi; ++m) {
+        if (m == l) continue;
+        const double a = ux * cx[m] + uy * cy[m];
+        const double b = 0.5 * (cx[m] * cx[m] + cy[m] * cy[m]) - (px0 * cx[m] + py0 * cy[m]);
+        if (a > 0.0) {
+          const double t = b / a;
+          if (t < thi) thi = t;
+        } else if (a < 0.0) {
+          const double t = b / a;
+          if (t > tlo) tlo = t;
+        } else if (b < 0.0) {
+          thi = -INFINITY;
+        }
+      }
+      if (!(tlo < thi)) continue;
+      if (!(tlo > -INFINITY) || !(thi < INFINITY)) {
+        ok = 0;
+      } else {
+        const double vx0 = px0 + tlo * ux, vy0 = py0 + tlo * uy;
+        const double vx1 = px0 + thi * ux, vy1 = py0 + thi * uy;
+        if (!(vx0 * vx0 + vy0 * vy0 < v2max) || !(vx1 * vx1 + vy1 * vy1 < v2max)) ok = 0;
+      }
+      /* exp(6 i phi) = z^6 / |z|^6 */
+      const double zx = cx[l], zy = cy[l];
+      const double z2x = zx * zx - zy * zy, z2y = 2.0 * zx * zy;
+      const double z3x = z2x * zx - z2y * zy, z3y = z2x * zy + z2y * zx;
+      const double z6x = z3x * z3x - z3y * z3y, z6y = 2.0 * z3x * z3y;
+      const double r2 = zx * zx + zy * zy;
+      const double r6 = r2 * r2 * r2;
+      re += z6x / r6;
+      im += z6y / r6;
+      n++;
+    }
+    if (!ok) bad++;
+    const double pk_re = n > 0 ? re / (double)n : 0.0, pk_im = n > 0 ? im / (double)n : 0.0;
+    if (psi_k) {
+      psi_k[2 * k] = pk_re;
+      psi_k[2 * k + 1] = pk_im;
+    }
+    if (n_nb) n_nb[k] = n;
+    sre += pk_re;
+    sim += pk_im;
+  }
+  free(cx);
+  free(cy);
+  if (psi) {
+    psi[0] = sre / (double)N;
+    psi[1] = sim / (double)N;
+  }
+  return bad;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Smallest pair distance (overlap check), plain uniform grid                */
 /* ------------------------------------------------------------------------ */
 double orc_min_dist2(int64_t N, double L, const double* x, const double* y, double rcut) {

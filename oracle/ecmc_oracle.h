@@ -120,6 +120,14 @@ int orc_seq_sweeps(int64_t N, double L, double sigma, double ell, int64_t n_chai
 void orc_gr_counts(int64_t N, double L, const double* x, const double* y, double sigma,
                    double dr, int nbins, int64_t i_begin, int64_t i_end, int64_t* counts);
 
+/* Hexatic order parameter (Sec. 2, eq. Psi) with Delaunay next neighbours,
+ * decided by clipping bisectors with the disks within rs (exact when every
+ * Voronoi vertex lies within rs/2; the number of disks failing that check is
+ * returned, -1 if L <= 2 rs).  psi_k[2N] (per disk, re/im), n_nb[N] and
+ * psi[2] (the mean) may each be NULL. */
+int orc_hexatic(int64_t N, double L, const double* x, const double* y, double rs,
+                double* psi_k, int32_t* n_nb, double* psi);
+
 /* Smallest minimum-image pair distance squared among all pairs closer than
  * rcut (returns rcut*rcut if there is none), by a plain uniform grid. */
 double orc_min_dist2(int64_t N, double L, const double* x, const double* y, double rcut);

@@ -1159,6 +1159,50 @@ int ecmc_gr_measure(ecmc_t h) {
   return ECMC_OK;
 }
 
+int ecmc_hexatic(ecmc_t h, double rs, double* psi, double* psi_k, int32_t* n_nb,
+                 int64_t* n_bad) {
+  if (!h || !psi) return fail(ECMC_ERR_ARG, "NULL argument");
+  if (!h->valid_state) return fail(ECMC_ERR_STATE, "state invalid after an earlier error");
+  for (const Geom& g : h->geo) {
+    const double r = rs > 0.0 ? rs : 3.5 * g.sigma;
+    if (!(g.L > 2.0 * r)) return fail(ECMC_ERR_ARG, "box side must exceed 2 rs");
+  }
+  const int64_t N = h->b.N_total;
+  unsigned long long* bad = h->u64_tmp + 1;
+  CK(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), h->stream));
+  double2* pk = reinterpret_cast<double2*>(h->xy_tmp);
+  if (launch_hexatic(h->b, rs, pk, h->int_tmp, bad, h->stream))
+    return fail(ECMC_ERR_CUDA, "hexatic kernel launch failed: %s",
+                cudaGetErrorString(cudaGetLastError()));
+  std::vector<double> hk(2 * (size_t)N);
+  std::vector<int32_t> hn((size_t)N);
+  unsigned long long hb = 0;
+  CK(cudaMemcpyAsync(hk.data(), pk, sizeof(double) * 2 * (size_t)N, cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaMemcpyAsync(hn.data(), h->int_tmp, sizeof(int32_t) * (size_t)N, cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaMemcpyAsync(&hb, bad, sizeof(hb), cudaMemcpyDeviceToHost, h->stream));
+  int rc = check_device_error(h);
+  if (rc) return rc;
+  for (size_t r = 0; r < h->geo.size(); ++r) {
+    const int64_t a = h->n_off[r], e = h->n_off[r + 1];
+    double sre = 0.0, sim = 0.0;
+    for (int64_t k = a; k < e; ++k) {
+      if (hn[k] < 0)
+        return fail(ECMC_ERR_CAPACITY, "more than 64 disks within rs of disk %lld of replica %d",
+                    (long long)(k - a), (int)r);
+      sre += hk[2 * k];
+      sim += hk[2 * k + 1];
+    }
+    psi[2 * r] = sre / (double)(e - a);
+    psi[2 * r + 1] = sim / (double)(e - a);
+  }
+  if (psi_k) std::memcpy(psi_k, hk.data(), sizeof(double) * 2 * (size_t)N);
+  if (n_nb) std::memcpy(n_nb, hn.data(), sizeof(int32_t) * (size_t)N);
+  if (n_bad) *n_bad = (int64_t)hb;
+  return ECMC_OK;
+}
+
 int ecmc_gr_nbins(ecmc_t h, int* nbins) {
   if (!h || !nbins) return fail(ECMC_ERR_ARG, "NULL argument");
   *nbins = h->gr_nbins;

@@ -186,6 +186,8 @@ void launch_sweep_end(const DevBufs& b, cudaStream_t s);
 void launch_gather(const DevBufs& b, double* xy_out, cudaStream_t s);
 void launch_load_flat(const DevBufs& b, const double* xy_dev, cudaStream_t s);
 void launch_cells_of(const Geom& g, const DevBufs& b, int* cell_of_id, cudaStream_t s);
+int launch_hexatic(const DevBufs& b, double rs, double2* psi_k, int* nn,
+                   unsigned long long* bad, cudaStream_t s);
 void launch_min_dist(const Geom& g, const DevBufs& b, double rcut, unsigned long long* out,
                      cudaStream_t s);
 void launch_gr(const Geom& g, const DevBufs& b, double dr, int nbins, unsigned long long* counts,

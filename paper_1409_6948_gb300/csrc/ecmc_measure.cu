@@ -104,6 +104,141 @@ void launch_gr(const Geom& g, const DevBufs& b, double dr, int nbins, unsigned l
       g, b.cap, b.px[b.cur], b.py[b.cur], b.count[b.cur], rcut, dr, nbins, counts);
 }
 
+// Hexatic order parameter (Sec. 2, eq. Psi) with Delaunay next neighbours.
+// One thread per bucket slot: the disks within rs (minimum image) are gathered
+// from the neighbour cells into shared memory and sorted by disk id; disk l is
+// a Delaunay neighbour when the perpendicular bisector of the pair keeps a
+// piece of positive length after every other gathered disk m cuts it with the
+// half-plane p.d_m <= |d_m|^2/2 (the Voronoi edge).  The graph is exact when
+// every Voronoi vertex lies within rs/2 (else the disk is counted in *bad).
+// Psi_k = mean over the neighbours of (dx + i dy)^6 / |d|^6, summed in
+// ascending neighbour id.  Every replica of the handle; written per disk in
+// the concatenated id order.  rs <= 0: 3.5 sigma of each replica.
+constexpr int kHexMaxCand = 64;
+
+__global__ void k_hexatic(const Geom* __restrict__ rg, const int* __restrict__ cell_rep,
+                          int C_total, int cap, const double* __restrict__ px,
+                          const double* __restrict__ py, const int* __restrict__ pid,
+                          const int* __restrict__ cnt, double rs_arg,
+                          double2* __restrict__ psi_out, int* __restrict__ nn_out,
+                          unsigned long long* bad) {
+  extern __shared__ __align__(16) unsigned char hsm[];
+  double2* cand = reinterpret_cast<double2*>(hsm) + (size_t)threadIdx.x * kHexMaxCand;
+  int* cid = reinterpret_cast<int*>(reinterpret_cast<double2*>(hsm) + (size_t)blockDim.x *
+                                                                          kHexMaxCand) +
+             (size_t)threadIdx.x * kHexMaxCand;
+  const int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (li >= (int64_t)C_total * cap) return;
+  const int c = (int)(li / cap);
+  const int k = (int)(li - (int64_t)c * cap);
+  if (k >= min(cnt[c], cap)) return;
+  const Geom& g = rg[cell_rep[c]];
+  const int lcell = c - g.cell_off;
+  const int64_t i = (int64_t)c * cap + k;
+  const int cx = lcell % g.cells_x, cy = lcell / g.cells_x;
+  const double xi = px[i], yi = py[i];
+  const double L = g.L;
+  const double rs = rs_arg > 0.0 ? rs_arg : 3.5 * g.sigma;
+  const double rs2 = rs * rs, v2max = 0.25 * rs * rs;
+  const int Rx = (int)ceil(rs * g.inv_w * (1.0 + 1e-9));
+  const int Ry = (int)ceil(rs * g.inv_h * (1.0 + 1e-9));
+  const NbRange rx = nb_range(Rx, g.cells_x), ry = nb_range(Ry, g.cells_y);
+  const bool absx = (2 * Rx + 1 >= g.cells_x), absy = (2 * Ry + 1 >= g.cells_y);
+  int nc = 0;
+  bool over = false;
+  for (int oy = 0; oy < ry.n; ++oy) {
+    const int qy = absy ? oy : ((cy + ry.first + oy) % g.cells_y + g.cells_y) % g.cells_y;
+    for (int ox = 0; ox < rx.n; ++ox) {
+      const int qx = absx ? ox : ((cx + rx.first + ox) % g.cells_x + g.cells_x) % g.cells_x;
+      const int q = g.cell_off + qy * g.cells_x + qx;
+      const int nq = min(cnt[q], cap);
+      const int64_t b0 = (int64_t)q * cap;
+      for (int kk = 0; kk < nq; ++kk) {
+        const int64_t j = b0 + kk;
+        if (j == i) continue;
+        const double ddx = wrap_half(px[j] - xi, L);
+        const double ddy = wrap_half(py[j] - yi, L);
+        if (!(ddx * ddx + ddy * ddy < rs2)) continue;
+        if (nc == kHexMaxCand) {
+          over = true;
+          continue;
+        }
+        // insertion by disk id (the order the sums below run in)
+        const int id = pid[j];
+        int pos = nc;
+        while (pos > 0 && cid[pos - 1] > id) {
+          cand[pos] = cand[pos - 1];
+          cid[pos] = cid[pos - 1];
+          --pos;
+        }
+        cand[pos] = make_double2(ddx, ddy);
+        cid[pos] = id;
+        ++nc;
+      }
+    }
+  }
+  double re = 0.0, im = 0.0;
+  int n = 0;
+  bool ok = !over;
+  for (int l = 0; l < nc; ++l) {
+    const double2 dl = cand[l];
+    const double ux = -dl.y, uy = dl.x;
+    const double px0 = 0.5 * dl.x, py0 = 0.5 * dl.y;
+    double tlo = -__longlong_as_double(0x7ff0000000000000ll);
+    double thi = __longlong_as_double(0x7ff0000000000000ll);
+    for (int m = 0; m < nc && tlo < thi; ++m) {
+      if (m == l) continue;
+      const double2 dm = cand[m];
+      const double a = ux * dm.x + uy * dm.y;
+      const double b = 0.5 * (dm.x * dm.x + dm.y * dm.y) - (px0 * dm.x + py0 * dm.y);
+      if (a > 0.0) {
+        const double t = b / a;
+        if (t < thi) thi = t;
+      } else if (a < 0.0) {
+        const double t = b / a;
+        if (t > tlo) tlo = t;
+      } else if (b < 0.0) {
+        thi = -__longlong_as_double(0x7ff0000000000000ll);
+      }
+    }
+    if (!(tlo < thi)) continue;
+    if (isinf(tlo) || isinf(thi)) {
+      ok = false;
+    } else {
+      const double vx0 = px0 + tlo * ux, vy0 = py0 + tlo * uy;
+      const double vx1 = px0 + thi * ux, vy1 = py0 + thi * uy;
+      if (!(vx0 * vx0 + vy0 * vy0 < v2max) || !(vx1 * vx1 + vy1 * vy1 < v2max)) ok = false;
+    }
+    const double zx = dl.x, zy = dl.y;
+    const double z2x = zx * zx - zy * zy, z2y = 2.0 * zx * zy;
+    const double z3x = z2x * zx - z2y * zy, z3y = z2x * zy + z2y * zx;
+    const double z6x = z3x * z3x - z3y * z3y, z6y = 2.0 * z3x * z3y;
+    const double r2 = zx * zx + zy * zy;
+    const double r6 = r2 * r2 * r2;
+    re += z6x / r6;
+    im += z6y / r6;
+    ++n;
+  }
+  if (!ok) atomicAdd(bad, 1ull);
+  const int64_t id = g.n_off + pid[i];
+  psi_out[id] = make_double2(n > 0 ? re / (double)n : 0.0, n > 0 ? im / (double)n : 0.0);
+  nn_out[id] = over ? -1 : n;
+}
+
+size_t hexatic_smem_bytes(int threads) {
+  return (size_t)threads * kHexMaxCand * (sizeof(double2) + sizeof(int));
+}
+
+int launch_hexatic(const DevBufs& b, double rs, double2* psi_k, int* nn,
+                   unsigned long long* bad, cudaStream_t s) {
+  const int bs = 32;
+  const int64_t total = (int64_t)b.C_total * b.cap;
+  k_hexatic<<<(unsigned)((total + bs - 1) / bs), bs, hexatic_smem_bytes(bs), s>>>(
+      b.rg, b.cell_rep, b.C_total, b.cap, b.px[b.cur], b.py[b.cur], b.pid[b.cur],
+      b.count[b.cur], rs, psi_k, nn, bad);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 }  // namespace ecmc
 
 // ---- device peak probes (roofline denominators) ---------------------------

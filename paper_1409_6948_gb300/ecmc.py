@@ -8,6 +8,7 @@ used); host buffers as numpy arrays.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 
 import numpy as np
@@ -126,6 +127,8 @@ _SIGS = {
     "ecmc_device_peaks": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "ecmc_sqrt_rn": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_double,
                                C.c_void_p]),
+    "ecmc_hexatic": (C.c_int, [_H, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.POINTER(C.c_int64)]),
     "ecmc_sweep_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_double, C.c_int,
                                      C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_uint64,
                                      C.c_int64, C.c_int64, C.c_void_p]),
@@ -226,10 +229,36 @@ class Ecmc:
                                     C.byref(n)), "ecmc_autotune")
         return best.as_dict(), [arr[i].as_dict() for i in range(n.value)]
 
+    def hexatic(self, rs=0.0, per_disk=False):
+        """Hexatic order parameter (eq. Psi) with Delaunay next neighbours.
+        Returns Psi (complex; an array of one per replica for a batch), or
+        (Psi, Psi_k complex array, neighbour counts, uncertified disks) with
+        per_disk."""
+        R = self.num_replicas()
+        N = sum(self.replica_desc(r)["N"] for r in range(R))
+        psi = np.empty(2 * R)
+        nbad = C.c_int64()
+        pk = np.empty(2 * N) if per_disk else None
+        nn = np.empty(N, np.int32) if per_disk else None
+        _check(load().ecmc_hexatic(self._h, float(rs), psi.ctypes.data,
+                                   pk.ctypes.data if per_disk else None,
+                                   nn.ctypes.data if per_disk else None, C.byref(nbad)),
+               "ecmc_hexatic")
+        z = psi[0::2] + 1j * psi[1::2]
+        z = complex(z[0]) if R == 1 else z
+        if not per_disk:
+            return z
+        return z, pk[0::2] + 1j * pk[1::2], nn, nbad.value
+
     def replica_desc(self, r):
         d = ReplicaDesc()
         _check(load().ecmc_replica_desc(self._h, int(r), C.byref(d)), "ecmc_replica_desc")
         return d.as_dict()
+
+    def num_replicas(self):
+        n = C.c_int()
+        _check(load().ecmc_num_replicas(self._h, C.byref(n)), "ecmc_num_replicas")
+        return n.value
 
     def replica_pressure(self, r):
         p, se = C.c_double(), C.c_double()
@@ -417,3 +446,24 @@ def sqrt_rn(x, rel_error=None, stream=None):
     _check(load().ecmc_sqrt_rn(C.c_void_p(xc.data_ptr()), C.c_void_p(out.data_ptr()),
                                xc.numel(), 1, 0.0, C.c_void_p(stream or 0)), "ecmc_sqrt_rn")
     return out
+
+
+def autocorrelation_time(psi_series, max_lag=None):
+    """Autocorrelation time tau of a complex order-parameter series (eq. tau):
+    C(dt) = Re <Psi*(t) Psi(t+dt)> / <|Psi|^2> (the mean of Psi is taken as
+    zero, as the definition prescribes), tau = the lag at which C falls to
+    1/e, interpolated linearly between lags.  Returns (tau, C)."""
+    z = np.asarray(psi_series, dtype=complex)
+    n = z.size
+    if max_lag is None:
+        max_lag = n // 4
+    denom = np.mean(np.abs(z) ** 2)
+    c = np.array([np.real(np.mean(np.conj(z[:n - d]) * z[d:])) / denom
+                  for d in range(max_lag + 1)])
+    below = np.flatnonzero(c < math.exp(-1.0))
+    if below.size == 0:
+        return float("inf"), c
+    d = below[0]
+    c0, c1 = c[d - 1], c[d]
+    return (d - 1) + (c0 - math.exp(-1.0)) / (c0 - c1), c
+
