@@ -47,8 +47,12 @@ FP64_OPS_PER_ITERATION = 10
 FP64_LANES_PER_SM_CLK = 2
 # DRAM bytes (read + write) of one k_phase launch at the large workload with the
 # paper's parameters, melted, TPC 8, frames in shared memory, from
-# `ncu --set full` (profiles/k_phase_large_melted.md); None once the kernel changes
+# `ncu --set full` (profiles/k_phase_large_paper_params.md), taken before the
+# kernel's last changes and therefore no longer reported
 K_PHASE_DRAM_BYTES = 39.11e6
+# the same for one k_sweep_fused launch (a whole sweep), from `ncu --set full`
+# (profiles/k_sweep_fused_large_paper_params.md)
+K_SWEEP_FUSED_DRAM_BYTES = 40.66e6
 
 
 def parse():
@@ -679,8 +683,8 @@ def run_ours(args):
                          else "k_phase (chain kernel)", "bound": "alu",
                          "achieved": achieved, "peak": fp64_peak, "unit": "GFLOP/s",
                          "frac": achieved / fp64_peak,
-                         "traffic": (None if persistent else K_PHASE_DRAM_BYTES)
-                         if tpc == 8 and not descs else None,
+                         "traffic": (K_SWEEP_FUSED_DRAM_BYTES if persistent else None)
+                         if tpc == 8 and not descs and args.dir == "axis" else None,
                          "pipe": "fp64", "fp64_ops_per_iteration": FP64_OPS_PER_ITERATION,
                          "iterations_per_launch": iters / max(kt.phase_launches, 1),
                          "launch_ms": phase_avg_ms,
