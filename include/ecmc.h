@@ -67,8 +67,9 @@ extern "C" {
  * (a variant that is not reversible, Sec. 3.2; kept for negative tests);
  * ECMC_DIR_ISOTROPIC = a uniform unit direction per chain (rejection-sampled
  * point of the unit disc divided by its length), specular reflection at
- * frozen disks (Fig. 1, Sec. 3.4), every candidate tested in FP64; runs in the
- * per-phase kernels. */
+ * frozen disks (Fig. 1, Sec. 3.4); candidates screened in FP32 with rigorous
+ * bounds (ECMC_PARAM_PRECISION 1) or all tested in FP64 (0), the same
+ * trajectory either way. */
 #define ECMC_PARAM_DIR_MODE 2
 /* Candidate geometry: ECMC_PREC_FP64 = every candidate tested in FP64;
  * ECMC_PREC_FP32_GEOM (default) = candidates screened in FP32 cell-relative

@@ -138,6 +138,16 @@ void set_screen_bounds(Geom& g) {
   g.sig_minus = std::nextafter((float)(sig - e - std::ldexp(sig, -40)), -1e30f);
   g.sig2f = (float)(sig * sig);
   g.sigf = (float)sig;
+  // isotropic chains: the FP32 frame differences are within 1.5 * 2^-22 M of
+  // the FP64 ones; the FP32 projections on a unit direction rounded to FP32
+  // (two products and a sum) within 6 * 2^-22 M; twice that as the bound
+  g.iso_e = (float)(12.0 * std::ldexp(1.0, -22) * M + std::ldexp(sig, -40));
+  // sqrt(sigma^2 - c^2) from FP32 operands: |x32 - x| <= 3 * 2^-24 sigma^2, and
+  // the square root is 1/2-Hoelder: sqrt(3 * 2^-24) sigma < 2^-11 sigma
+  g.iso_sq = (float)(std::ldexp(sig, -11) + std::ldexp(sig, -22));
+  g.iso_r = (float)(std::ldexp(1.0, -22) * (2.0 * M + sig));
+  g.iso_sig_lo = std::nextafter((float)(sig * (1.0 - std::ldexp(1.0, -21))), -1e30f);
+  g.iso_sig_hi = std::nextafter((float)(sig * (1.0 + std::ldexp(1.0, -21))), 1e30f);
   g.strip_margin = (float)(4.0 * e + 1e-5 * sig);
 }
 
@@ -243,12 +253,11 @@ int compute_layout(ecmc_ctx* h) {
   // the persistent kernel keeps its frames in shared memory (frame mode 0)
   // unless mode 1 is asked for: FP64 coordinates in a per-warp scratch area of
   // global memory, more warps per SM (measured at N = 1M, eta = 0.72: 1.64
-  // against 1.58 * 10^9 events/s)
-  const int fm = h->fmode_param == 1 ? 1 : 0;
-  // isotropic chains run in the per-phase kernels only
-  if (h->persist_param && !h->b.iso && fmode < 2 && fused_smem_bytes(h->lay, fm) <= limit / 2) {
+  // against 1.58 * 10^9 events/s); isotropic chains use mode 0
+  const int fm = (h->fmode_param == 1 && !h->b.iso) ? 1 : 0;
+  if (h->persist_param && fmode < 2 && fused_smem_bytes(h->lay, fm) <= limit / 2) {
     int per_sm = 0;
-    if (configure_fused(h->lay, h->tpc, fm, &per_sm) == 0) {
+    if (configure_fused(h->lay, h->tpc, fm, h->b.iso, &per_sm) == 0) {
       const int n_items = 4 * n_groups;
       const int grid = per_sm * h->n_sm < n_items ? per_sm * h->n_sm : n_items;
       const size_t scratch = (size_t)grid * fused_scratch_bytes(h->lay);

@@ -49,7 +49,7 @@ struct Frame {
   const int* mrank;
   const int* mslot;
   float* a32;
-  const float* b32;
+  float* b32;  // written only by isotropic chains
   double* a64;
   double* b64;  // written only by isotropic chains (axis chains keep the cross coordinate)
   const int* key;

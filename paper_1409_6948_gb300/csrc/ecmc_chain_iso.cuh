@@ -18,9 +18,15 @@
 // at its centre, divided by its length: square root and division are IEEE
 // operations, so the direction is reproducible to the last bit.
 //
-// Every candidate of the frame is tested in FP64 with the expressions of the
-// reference arithmetic (no contraction), so trajectories are bit-identical to
-// it.  Frames are built with axis 0 (frame coordinates a = x, b = y).
+// SCREEN = false: every candidate of the frame is tested in FP64 with the
+// expressions of the reference arithmetic (no contraction).  SCREEN = true:
+// the projections b = D.d and c = D x d of every candidate are first computed
+// in FP32 from the frame's FP32 coordinates and bracketed by rigorous error
+// bounds, giving an interval for its hit distance; only candidates whose lower
+// bound reaches the smallest certain upper bound (or the budget and wall
+// distance) are tested in FP64, so the first hit and the new position are
+// those of the full FP64 search.  Either way trajectories are bit-identical to
+// the reference.  Frames are built with axis 0 (frame coordinates a = x, b = y).
 #pragma once
 
 #include "ecmc_chain.cuh"
@@ -53,7 +59,46 @@ __device__ __forceinline__ void iso_direction(int64_t t, int lc, int k, uint64_t
   dy = 0.0;
 }
 
-template <int TPC>
+// FP64 hit test of candidate j along d, the reference expressions
+__device__ __forceinline__ bool iso_hit(const Frame& f, int j, int CPW, int gi, double X, double Y,
+                                        double dx, double dy, double sig2, double& s, double& b) {
+  const double ddx = f.a64[j * CPW + gi] - X;
+  const double ddy = f.b64[j * CPW + gi] - Y;
+  b = ddx * dx + ddy * dy;
+  if (!(b > 0.0)) return false;
+  const double cc = ddx * dy - ddy * dx;
+  const double c2 = cc * cc;
+  if (!(c2 < sig2)) return false;
+  s = b - sqrt_rn(sig2 - c2);
+  if (s < 0.0) s = 0.0;
+  return true;
+}
+
+// FP32 bracket [lo, hi] of the hit distance of candidate j (certain: j hits
+// for sure, so hi bounds the first hit); false when j certainly misses
+__device__ __forceinline__ bool iso_bracket(const Frame& f, const Geom& g, int j, int CPW, int gi,
+                                            float X32, float Y32, float dx32, float dy32,
+                                            float& lo, float& hi, bool& certain) {
+  const float ex = __fsub_rn(f.a32[j * CPW + gi], X32);
+  const float ey = __fsub_rn(f.b32[j * CPW + gi], Y32);
+  const float b32 = __fadd_rn(__fmul_rn(ex, dx32), __fmul_rn(ey, dy32));
+  const float e = g.iso_e;
+  if (!(b32 > -e)) return false;
+  const float c32 = __fsub_rn(__fmul_rn(ex, dy32), __fmul_rn(ey, dx32));
+  const float ac = fabsf(c32);
+  if (!(ac < __fadd_rn(g.iso_sig_hi, e))) return false;
+  const float cl = fmaxf(__fsub_rn(ac, e), 0.0f), ch = __fadd_rn(ac, e);
+  const float xhi = fmaxf(__fsub_rn(g.sig2f, __fmul_rn(cl, cl)), 0.0f);
+  const float xlo = fmaxf(__fsub_rn(g.sig2f, __fmul_rn(ch, ch)), 0.0f);
+  const float sq_hi = __fadd_rn(__fsqrt_rn(xhi), g.iso_sq);
+  const float sq_lo = fmaxf(__fsub_rn(__fsqrt_rn(xlo), g.iso_sq), 0.0f);
+  lo = __fsub_rn(__fsub_rn(__fsub_rn(b32, e), sq_hi), g.iso_r);
+  hi = fmaxf(__fadd_rn(__fsub_rn(__fadd_rn(b32, e), sq_lo), g.iso_r), 0.0f);
+  certain = __fsub_rn(b32, e) > 0.0f && __fadd_rn(ch, e) < g.iso_sig_lo;
+  return true;
+}
+
+template <int TPC, bool SCREEN>
 __device__ __forceinline__ void run_group_iso(const Frame& f, const int* hdr, void* hl,
                                               const Geom* __restrict__ rg,
                                               const SweepState* __restrict__ sts, int rep, int a,
@@ -135,23 +180,14 @@ __device__ __forceinline__ void run_group_iso(const Frame& f, const int* hdr, vo
     if (swy < 0.0) swy = 0.0;
     const double swall = swx < swy ? swx : swy;
 
-    // first contact along d over every object of the frame
+    // first contact along d
     double best_s = INF, best_b = 0.0;
     int best_key = INT_MAX, best_j = m;
     int nev = 0;
-    if (go) {
-      for (int j = sub; j < nobj; j += TPC) {
-        if (j == m) continue;
-        const double ddx = f.a64[j * CPW + gi] - X;
-        const double ddy = f.b64[j * CPW + gi] - Y;
-        const double b = ddx * dx + ddy * dy;
-        if (!(b > 0.0)) continue;
-        const double cc = ddx * dy - ddy * dx;
-        const double c2 = cc * cc;
-        if (!(c2 < sig2)) continue;
-        ++nev;
-        double s = b - sqrt_rn(sig2 - c2);
-        if (s < 0.0) s = 0.0;
+    auto consider = [&](int j) {
+      double s, b;
+      ++nev;
+      if (iso_hit(f, j, CPW, gi, X, Y, dx, dy, sig2, s, b)) {
         const int kj = f.key[j * CPW + gi];
         if (better(s, kj, best_s, best_key)) {
           best_s = s;
@@ -160,6 +196,63 @@ __device__ __forceinline__ void run_group_iso(const Frame& f, const int* hdr, vo
           best_j = j;
         }
       }
+    };
+    if (SCREEN) {
+      // FP32 brackets; the candidates that can be the first hit go to FP64
+      const float X32 = to_float_trunc(X), Y32 = to_float_trunc(Y);
+      const float dx32 = __double2float_rn(dx), dy32 = __double2float_rn(dy);
+      float U = __int_as_float(0x7f800000), L1 = U, L2 = U;
+      int j1 = m;
+      if (go) {
+        for (int j = sub; j < nobj; j += TPC) {
+          if (j == m) continue;
+          float lo, hi;
+          bool certain;
+          if (!iso_bracket(f, g, j, CPW, gi, X32, Y32, dx32, dy32, lo, hi, certain)) continue;
+          if (lo < L1) {
+            L2 = L1;
+            L1 = lo;
+            j1 = j;
+          } else if (lo < L2) {
+            L2 = lo;
+          }
+          if (certain) U = fminf(U, hi);
+        }
+      }
+      if (TPC > 1) {
+#pragma unroll
+        for (int o = 1; o < TPC; o <<= 1) {
+          const float oU = __shfl_xor_sync(FULL, U, o);
+          const float oL1 = __shfl_xor_sync(FULL, L1, o);
+          const float oL2 = __shfl_xor_sync(FULL, L2, o);
+          const int oj1 = __shfl_xor_sync(FULL, j1, o);
+          U = fminf(U, oU);
+          const float nL2 = fminf(fmaxf(L1, oL1), fminf(L2, oL2));
+          if (oL1 < L1 || (oL1 == L1 && oj1 < j1)) {
+            L1 = oL1;
+            j1 = oj1;
+          }
+          L2 = nL2;
+        }
+      }
+      const float Lam = fminf(U, to_float_up_nn(r < swall ? r : swall));
+      const bool need = go && (L1 <= Lam);
+      const bool multi = need && (L2 <= Lam);
+      if (need && !multi && sub == 0) consider(j1);
+      if (__any_sync(FULL, multi)) {
+        if (multi) {
+          for (int j = sub; j < nobj; j += TPC) {
+            if (j == m) continue;
+            float lo, hi;
+            bool certain;
+            if (!iso_bracket(f, g, j, CPW, gi, X32, Y32, dx32, dy32, lo, hi, certain)) continue;
+            if (lo <= Lam) consider(j);
+          }
+        }
+      }
+    } else if (go) {
+      for (int j = sub; j < nobj; j += TPC)
+        if (j != m) consider(j);
     }
     if (TPC > 1) {
 #pragma unroll
@@ -197,8 +290,11 @@ __device__ __forceinline__ void run_group_iso(const Frame& f, const int* hdr, vo
         if (f.info[best_j * CPW + gi] >= 0) {
           // lift: the hit member moves on along d
           ++n_lifts;
+          // the stopped disk, in FP64 and in the FP32 copy the screen reads
           f.a64[m * CPW + gi] = nX;
           f.b64[m * CPW + gi] = nY;
+          f.a32[m * CPW + gi] = to_float_trunc(nX);
+          f.b32[m * CPW + gi] = to_float_trunc(nY);
           m = best_j;
           X = f.a64[m * CPW + gi];
           Y = f.b64[m * CPW + gi];
@@ -234,6 +330,8 @@ __device__ __forceinline__ void run_group_iso(const Frame& f, const int* hdr, vo
     if (end_chain) {
       f.a64[m * CPW + gi] = X;
       f.b64[m * CPW + gi] = Y;
+      f.a32[m * CPW + gi] = to_float_trunc(X);
+      f.b32[m * CPW + gi] = to_float_trunc(Y);
       if (recs != nullptr && sub == 0) {
         ChainRec rc;
         rc.start_id = start_key >> 4;

@@ -96,6 +96,12 @@ struct Geom {
   float sig_minus;   // FP32 certain-hit threshold on |perpendicular offset|
   float sig2f;
   float strip_margin;
+  // FP32 screening of isotropic chains (general directions)
+  float iso_e;       // bound on |FP32 - FP64| of the projections b = D.d and c = D x d
+  float iso_sq;      // bound on the error of the FP32 square root of sigma^2 - c^2
+  float iso_r;       // FP32 rounding of the hit-distance bounds
+  float iso_sig_lo;  // certain-hit threshold on |c| (below sigma)
+  float iso_sig_hi;  // certain-miss threshold on |c| (above sigma)
   int precision;     // 0 FP64 candidates, 1 FP32 screening
 };
 
@@ -163,7 +169,7 @@ struct DevBufs {
   ChunkSums* partials;     // [n_chunks]
   int n_chunks;
   int replay;              // 1 = replay repeating reflection legs (chain kernel)
-  int iso;                 // 1 = isotropic directions (per-phase chain kernel only)
+  int iso;                 // 1 = isotropic directions
   unsigned* sched;         // persistent sweep: [0] next work item, [1] epoch, [2] abort
   unsigned* done;          // [C_total] epoch in which each cell last finished
   unsigned long long wait_ns;  // limit of one dependency wait
@@ -199,7 +205,7 @@ int configure_phase(const RecLayout& lay, int tpc, int warps, int fmode);
 int probe_peaks(double* smem_gbs, double* fp64_gflops);
 size_t fused_smem_bytes(const RecLayout& lay, int fm);
 size_t fused_scratch_bytes(const RecLayout& lay);
-int configure_fused(const RecLayout& lay, int tpc, int fm, int* blocks_per_sm);
+int configure_fused(const RecLayout& lay, int tpc, int fm, int iso, int* blocks_per_sm);
 int launch_fused(const DevBufs& b, const RecLayout& lay, int tpc, int blocks, int records_on,
                  int precision, cudaStream_t s);
 int launch_sqrt_rn(const double* x, double* out, int64_t n, cudaStream_t s);

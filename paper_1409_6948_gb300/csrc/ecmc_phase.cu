@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
   f.mrank = (const int*)(base + lay.off_mrank);
   f.mslot = (const int*)(base + lay.off_mslot);
   f.a32 = (float*)(base + lay.off_a32);
-  f.b32 = (const float*)(base + lay.off_b32);
+  f.b32 = (float*)(base + lay.off_b32);
   f.a64 = (double*)((FMODE == 1 ? grec : base) + lay.off_a64);
   f.b64 = (double*)((FMODE == 1 ? grec : base) + lay.off_b64);
   f.key = (const int*)(base + lay.off_key);
@@ -81,8 +81,8 @@ __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
   const bool valid = a < n_active;
   const int rep = valid ? act_rep[a] : act_rep[n_active - 1];
   if constexpr (ISO)
-    run_group_iso<TPC>(f, hdr, hs.P, rg, sts, rep, a, valid, colour_index, px, py, cs, recs,
-                       rec_stride, err);
+    run_group_iso<TPC, SCREEN>(f, hdr, hs.P, rg, sts, rep, a, valid, colour_index, px, py, cs,
+                               recs, rec_stride, err);
   else
     run_group<TPC, SCREEN>(f, hs, hdr, rg, sts, rep, a, valid, colour_index, lay, px, py, cs,
                            recs, rec_stride, replay, err);
@@ -104,7 +104,7 @@ static int launch_t(const DevBufs& b, const RecLayout& lay, int colour_index, in
   const int blocks = (n_groups + warps - 1) / warps;
   const size_t sm = phase_smem_bytes(lay, warps, b.fmode);
 #define ECMC_PHASE(FM, ISO)                                                                \
-  k_phase<TPC, SCREEN && !ISO, FM, ISO><<<blocks, 32 * warps, sm, s>>>(                    \
+  k_phase<TPC, SCREEN, FM, ISO><<<blocks, 32 * warps, sm, s>>>(                            \
       b.rg, b.state, b.act_rep, colour_index, b.records, b.gtouch, lay, n_active,          \
       b.px[b.cur], b.py[b.cur], b.cell_stats, records_on ? b.chain_recs : nullptr,         \
       b.rec_stride, b.replay, b.err)
@@ -150,6 +150,7 @@ static int configure_t(size_t sm) {
   if (configure_fn(k_phase<TPC, true, FM>, sm)) return -1;
   if (configure_fn(k_phase<TPC, false, FM>, sm)) return -1;
   if (configure_fn(k_phase<TPC, false, FM, true>, sm)) return -1;
+  if (configure_fn(k_phase<TPC, true, FM, true>, sm)) return -1;
   return 0;
 }
 

@@ -133,9 +133,12 @@ def test_positive_only_direction_rule():
     (4096, 0.72, 16, 2.0, 1, 32),
     (1024, 0.30, 4, 3.0, 3, 0),    # dilute, automatic lanes per cell
 ])
-def test_isotropic_directions(N, eta, cx, ell, nm, tpc):
-    # uniform directions per chain, specular reflection at frozen disks (Fig. 1)
-    st = run_pair(N, eta, cx, cx, ell, nm, 7, 5, tpc=tpc, dir_mode=2)
+@pytest.mark.parametrize("prec,persistent", [(1, 1), (0, 0), (1, 0)])
+def test_isotropic_directions(N, eta, cx, ell, nm, tpc, prec, persistent):
+    # uniform directions per chain, specular reflection at frozen disks (Fig. 1);
+    # FP32-screened or all-FP64 candidates, persistent or per-phase launches
+    st = run_pair(N, eta, cx, cx, ell, nm, 7, 5, tpc=tpc, dir_mode=2, prec=prec,
+                  persistent=persistent)
     assert st.frozen_hits > 0 and st.wall_hits > 0
 
 
