@@ -1,7 +1,9 @@
 // ecmc_measure.cu -- measurements on the current configuration: the
 // pair-correlation histogram of Sec. 2 (ordered pairs, bins
-// [sigma + i dr, sigma + (i+1) dr)) and the smallest pair distance (the
-// no-overlap invariant).  Both walk the cell buckets of the last binning.
+// [sigma + i dr, sigma + (i+1) dr)), the smallest pair distance (the
+// no-overlap invariant; an integer scan on fixed-point positions, FP64 for
+// small boxes) and the hexatic order parameter.  All walk the cell buckets of
+// the last binning.
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -28,71 +30,291 @@ __device__ __forceinline__ NbRange nb_range(int R, int cells) {
   return r;
 }
 
+// g(r) histograms of up to this many bins are accumulated per block in shared
+// memory (integer counts: the order of the additions does not matter)
+constexpr int kGrSharedBins = 4096;
+
 template <bool GR>
 __global__ void k_pairs(Geom g, int cap, const double* __restrict__ px,
                         const double* __restrict__ py, const int* __restrict__ cnt, double rcut,
                         double dr, int nbins, unsigned long long* __restrict__ out) {
+  extern __shared__ unsigned long long hist_sm[];  // g(r): per-block histogram
+  const bool block_hist = GR && nbins <= kGrSharedBins;
+  if (block_hist) {
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) hist_sm[b] = 0ull;
+    __syncthreads();
+  }
+  const int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long best = __double_as_longlong(rcut * rcut);
+  // every lane reaches the warp reduction at the end: slots without a disk
+  // only skip the scan
+  bool valid = li < (int64_t)g.ncell * cap;
+  const int lcell = valid ? (int)(li / cap) : 0;
+  const int k = valid ? (int)(li - (int64_t)lcell * cap) : 0;
+  const int c = g.cell_off + lcell;
+  const int64_t i = (int64_t)c * cap + k;
+  valid = valid && k < min(cnt[c], cap);
+  if (valid) {
+    const int cx = lcell % g.cells_x, cy = lcell / g.cells_x;
+    const double xi = px[i], yi = py[i];
+    const double L = g.L;
+    const int Rx = (int)ceil(rcut * g.inv_w * (1.0 + 1e-9));
+    const int Ry = (int)ceil(rcut * g.inv_h * (1.0 + 1e-9));
+    const NbRange rx = nb_range(Rx, g.cells_x), ry = nb_range(Ry, g.cells_y);
+    const bool absx = (2 * Rx + 1 >= g.cells_x), absy = (2 * Ry + 1 >= g.cells_y);
+    const float Lf = (float)L, hLf = 0.5f * Lf;
+    const float xif = to_float_trunc(xi), yif = to_float_trunc(yi);
+    const float rcf = (float)rcut + 8.0f * 1.1920929e-7f * Lf + 1e-6f;
+    for (int oy = 0; oy < ry.n; ++oy) {
+      const int qy = absy ? oy : ((cy + ry.first + oy) % g.cells_y + g.cells_y) % g.cells_y;
+      for (int ox = 0; ox < rx.n; ++ox) {
+        const int qx = absx ? ox : ((cx + rx.first + ox) % g.cells_x + g.cells_x) % g.cells_x;
+        const int q = g.cell_off + qy * g.cells_x + qx;
+        const int nq = min(cnt[q], cap);
+        const int64_t b0 = (int64_t)q * cap;
+        for (int kk = 0; kk < nq; ++kk) {
+          const int64_t j = b0 + kk;
+          if (j == i) continue;
+          if (!GR) {
+            // FP32 screen: pairs farther than rcut (plus a margin above the
+            // FP32 rounding error) cannot change the minimum
+            float fx = to_float_trunc(px[j]) - xif, fy = to_float_trunc(py[j]) - yif;
+            fx = fx >= hLf ? fx - Lf : (fx < -hLf ? fx + Lf : fx);
+            fy = fy >= hLf ? fy - Lf : (fy < -hLf ? fy + Lf : fy);
+            if (fabsf(fx) > rcf || fabsf(fy) > rcf) continue;
+          }
+          const double ddx = wrap_half(px[j] - xi, L);
+          const double ddy = wrap_half(py[j] - yi, L);
+          if (GR) {
+            const double d = sqrt(ddx * ddx + ddy * ddy);
+            const double qv = (d - g.sigma) / dr;
+            if (!(qv >= 0.0)) continue;
+            if (!(qv < (double)nbins)) continue;
+            atomicAdd(block_hist ? &hist_sm[(int)qv] : &out[(int)qv], 1ull);
+          } else {
+            const double d2 = ddx * ddx + ddy * ddy;
+            const unsigned long long bits = __double_as_longlong(d2);
+            if (bits < best) best = bits;
+          }
+        }
+      }
+    }
+  }
+  if (block_hist) {
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+      if (hist_sm[b]) atomicAdd(&out[b], hist_sm[b]);
+  }
+  if (!GR) {
+    // one atomic per warp: the minimum of the warp first
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+      best = other < best ? other : best;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMin(out, best);
+  }
+}
+
+// ---- smallest pair distance (the no-overlap invariant) --------------------
+// The FP64 scan above spends its time on the FP64 pipe: a warp covers ~18
+// disks of one cell, and some lane nearly always lets a candidate through the
+// FP32 screen.  This path keeps the scan on the integer pipes and evaluates
+// FP64 once per disk.
+//
+// Fixed point.  Every coordinate becomes X = floor(x 2^32 / L) mod 2^32, a
+// 32-bit fraction of the box side, so X_j - X_i read as int32 is the minimum
+// image of x_j - x_i in units of L / 2^32.  Let T be the exact scaled
+// difference; the two floors, the rounding of x 2^32 / L and of 2^32 / L
+// leave |dX - T| <= e = 1 + 2^-16 for every pair within L / 4.
+//
+// Exact squared distances.  D = dX^2 + dY^2 is exact in 64 bits (|dX| <
+// 2^30).  With D* the scaled squared distance of the FP64 positions,
+// |D - D*| <= 2 e (|dX| + |dY| + 2 e) + 2 e^2 <= 2 sqrt(2) e sqrt(D) + 6 e^2,
+// and the FP64 formula d2 = dx dx + dy dy (each operation rounded; the wrap
+// adds at most 2 u L) sits within 2^-19 sqrt(2 D*) + 2^-51 D* of D*.  Both
+// are below Bt(D) = 2.9 sqrt(D) + 8 + D / 2^40.
+//
+// Selection.  Each lane keeps the two smallest D of its candidates (m1 <= m2)
+// and the argmin j1.  If m2 - Bt(m2) > m1 + Bt(m1), no other candidate can
+// have an FP64 d2 at or below that of j1, and d2(i, j1) is the lane's
+// minimum.  Otherwise (exact ties, as on a lattice) the lane rescans and
+// evaluates FP64 for every candidate with D <= m1 + 4 Bt(m1) + 64, a window
+// that holds every candidate whose d2 can be the smallest.  The result is the
+// same double, bit for bit, as the minimum of the FP64 formula over all pairs.
+
+// 32-bit fractions of the box side, one uint2 per bucket slot
+__global__ void k_fixed_point(Geom g, int cap, const double* __restrict__ px,
+                              const double* __restrict__ py, const int* __restrict__ cnt,
+                              double scale, uint2* __restrict__ fxy) {
   const int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (li >= (int64_t)g.ncell * cap) return;
   const int lcell = (int)(li / cap);
   const int k = (int)(li - (int64_t)lcell * cap);
   const int c = g.cell_off + lcell;
-  const int64_t i = (int64_t)c * cap + k;
   if (k >= min(cnt[c], cap)) return;
-  const int cx = lcell % g.cells_x, cy = lcell / g.cells_x;
-  const double xi = px[i], yi = py[i];
-  const double L = g.L;
-  const int Rx = (int)ceil(rcut * g.inv_w * (1.0 + 1e-9));
-  const int Ry = (int)ceil(rcut * g.inv_h * (1.0 + 1e-9));
-  const NbRange rx = nb_range(Rx, g.cells_x), ry = nb_range(Ry, g.cells_y);
-  const bool absx = (2 * Rx + 1 >= g.cells_x), absy = (2 * Ry + 1 >= g.cells_y);
-  unsigned long long best = __double_as_longlong(rcut * rcut);
-  const float Lf = (float)L, hLf = 0.5f * Lf;
-  const float xif = to_float_trunc(xi), yif = to_float_trunc(yi);
-  const float rcf = (float)rcut + 8.0f * 1.1920929e-7f * Lf + 1e-6f;
-  for (int oy = 0; oy < ry.n; ++oy) {
-    const int qy = absy ? oy : ((cy + ry.first + oy) % g.cells_y + g.cells_y) % g.cells_y;
-    for (int ox = 0; ox < rx.n; ++ox) {
-      const int qx = absx ? ox : ((cx + rx.first + ox) % g.cells_x + g.cells_x) % g.cells_x;
-      const int q = g.cell_off + qy * g.cells_x + qx;
-      const int nq = min(cnt[q], cap);
-      const int64_t b0 = (int64_t)q * cap;
-      for (int kk = 0; kk < nq; ++kk) {
-        const int64_t j = b0 + kk;
-        if (j == i) continue;
-        if (!GR) {
-          // FP32 screen: pairs farther than rcut (plus a margin above the
-          // FP32 rounding error) cannot change the minimum
-          float fx = to_float_trunc(px[j]) - xif, fy = to_float_trunc(py[j]) - yif;
-          fx = fx >= hLf ? fx - Lf : (fx < -hLf ? fx + Lf : fx);
-          fy = fy >= hLf ? fy - Lf : (fy < -hLf ? fy + Lf : fy);
-          if (fabsf(fx) > rcf || fabsf(fy) > rcf) continue;
-        }
-        const double ddx = wrap_half(px[j] - xi, L);
-        const double ddy = wrap_half(py[j] - yi, L);
-        if (GR) {
-          const double d = sqrt(ddx * ddx + ddy * ddy);
-          const double qv = (d - g.sigma) / dr;
-          if (!(qv >= 0.0)) continue;
-          if (!(qv < (double)nbins)) continue;
-          atomicAdd(&out[(int)qv], 1ull);
-        } else {
-          const double d2 = ddx * ddx + ddy * ddy;
-          const unsigned long long bits = __double_as_longlong(d2);
-          if (bits < best) best = bits;
-        }
-      }
-    }
-  }
-  if (!GR) atomicMin(out, best);
+  const int64_t i = (int64_t)c * cap + k;
+  // floor, then modulo 2^32: x slightly below 0 or rounded up to 2^32 wraps
+  const long long X = __double2ll_rd(px[i] * scale);
+  const long long Y = __double2ll_rd(py[i] * scale);
+  fxy[i] = make_uint2((unsigned)X, (unsigned)Y);
 }
 
+__device__ __forceinline__ unsigned long long bt_bound(unsigned long long x) {
+  return (unsigned long long)(2.9f * sqrtf((float)x)) + 8ull + (x >> 40);
+}
+
+// FP64 squared minimum-image distance, the formula of the FP64 scan
+__device__ __forceinline__ double pair_d2(const double* __restrict__ px,
+                                          const double* __restrict__ py, int64_t i, int64_t j,
+                                          double L) {
+  const double ddx = wrap_half(px[j] - px[i], L);
+  const double ddy = wrap_half(py[j] - py[i], L);
+  return ddx * ddx + ddy * ddy;
+}
+
+// One warp per cell; lane l takes members l, l + 32, ...  HALF: each
+// unordered pair once (own cell with kk > k, then the offsets (ox, 0), ox > 0,
+// and (ox, oy), oy > 0), valid when 2R + 1 <= cells in both directions.
+// Otherwise every neighbour cell of the FP64 scan's enumeration, minus self.
+template <bool HALF>
+__global__ void __launch_bounds__(256) k_min_dist_fixed(
+    Geom g, int cap, const double* __restrict__ px, const double* __restrict__ py,
+    const uint2* __restrict__ fxy, const int* __restrict__ cnt, int Rx, int Ry, unsigned RC,
+    unsigned long long r2_bits, unsigned long long* __restrict__ out) {
+  constexpr unsigned kFull = 0xffffffffu;
+  constexpr unsigned long long kNone = ~0ull;
+  const int lcell = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (lcell >= g.ncell) return;  // warp-uniform
+  const int lane = threadIdx.x & 31;
+  const int c = g.cell_off + lcell;
+  const int cx = lcell % g.cells_x, cy = lcell / g.cells_x;
+  const int nmem = min(cnt[c], cap);
+  const NbRange rx = nb_range(Rx, g.cells_x), ry = nb_range(Ry, g.cells_y);
+  const bool absx = (2 * Rx + 1 >= g.cells_x), absy = (2 * Ry + 1 >= g.cells_y);
+  unsigned long long best = r2_bits;
+
+  for (int m0 = 0; m0 < nmem; m0 += 32) {
+    const int k = m0 + lane;
+    const bool act = k < nmem;
+    const int64_t i = (int64_t)c * cap + (act ? k : 0);
+    const uint2 pi = fxy[i];
+
+    // visits every candidate cell with its exclusion rule: kk > kmin, kk != kskip
+    auto scan = [&](auto&& visit) {
+      if (HALF) {
+        visit(c, k, -1);
+        for (int oy = 0; oy <= Ry; ++oy) {
+          const int qy = (cy + oy) % g.cells_y;
+          for (int ox = (oy == 0 ? 1 : -Rx); ox <= Rx; ++ox) {
+            const int qx = ((cx + ox) % g.cells_x + g.cells_x) % g.cells_x;
+            visit(g.cell_off + qy * g.cells_x + qx, -1, -1);
+          }
+        }
+      } else {
+        for (int oy = 0; oy < ry.n; ++oy) {
+          const int qy = absy ? oy : ((cy + ry.first + oy) % g.cells_y + g.cells_y) % g.cells_y;
+          for (int ox = 0; ox < rx.n; ++ox) {
+            const int qx =
+                absx ? ox : ((cx + rx.first + ox) % g.cells_x + g.cells_x) % g.cells_x;
+            const int q = g.cell_off + qy * g.cells_x + qx;
+            visit(q, -1, q == c ? k : -1);
+          }
+        }
+      }
+    };
+    // exact D of a candidate, kNone when screened out or excluded
+    auto dist = [&](uint2 pj, int kk, int kmin, int kskip) -> unsigned long long {
+      const int dx = (int)(pj.x - pi.x), dy = (int)(pj.y - pi.y);
+      const bool s = ((unsigned)dx + RC <= 2u * RC) & ((unsigned)dy + RC <= 2u * RC) &
+                     (kk > kmin) & (kk != kskip);
+      const unsigned long long D =
+          (unsigned long long)((long long)dx * dx + (long long)dy * dy);
+      return s ? D : kNone;
+    };
+
+    unsigned long long m1 = kNone, m2 = kNone;
+    int64_t j1 = 0;
+    scan([&](int q, int kmin, int kskip) {
+      const int64_t b0 = (int64_t)q * cap;
+      const int nq = min(cnt[q], cap);
+#pragma unroll 4
+      for (int kk = 0; kk < nq; ++kk) {
+        const unsigned long long D = dist(fxy[b0 + kk], kk, kmin, kskip);
+        const bool lt1 = D < m1, lt2 = D < m2;
+        m2 = lt1 ? m1 : (lt2 ? D : m2);
+        j1 = lt1 ? b0 + kk : j1;
+        m1 = lt1 ? D : m1;
+      }
+    });
+
+    bool amb = false;
+    if (act && m1 != kNone) {
+      amb = m2 != kNone && m2 - m1 <= bt_bound(m1) + bt_bound(m2);
+      if (!amb) {
+        const unsigned long long bits = __double_as_longlong(pair_d2(px, py, i, j1, g.L));
+        best = bits < best ? bits : best;
+      }
+    }
+    if (__any_sync(kFull, amb)) {
+      const unsigned long long win = amb ? m1 + 4ull * bt_bound(m1) + 64ull : 0ull;
+      scan([&](int q, int kmin, int kskip) {
+        const int64_t b0 = (int64_t)q * cap;
+        const int nq = min(cnt[q], cap);
+        for (int kk = 0; kk < nq; ++kk) {
+          const unsigned long long D = dist(fxy[b0 + kk], kk, kmin, kskip);
+          if (amb && D <= win) {
+            const unsigned long long bits =
+                __double_as_longlong(pair_d2(px, py, i, b0 + kk, g.L));
+            best = bits < best ? bits : best;
+          }
+        }
+      });
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_xor_sync(kFull, best, o);
+    best = other < best ? other : best;
+  }
+  if (lane == 0 && best < r2_bits) atomicMin(out, best);
+}
+
+// The fixed-point scan needs rcut < L / 4 (|dX| < 2^30) and int32 slot
+// indices; other boxes take the FP64 scan.  The fractions go to the
+// position buffer the next binning overwrites.
 void launch_min_dist(const Geom& g, const DevBufs& b, double rcut, unsigned long long* out,
                      cudaStream_t s) {
-  const int bs = 128;
   const int64_t total = (int64_t)g.ncell * b.cap;
-  k_pairs<false><<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(
-      g, b.cap, b.px[b.cur], b.py[b.cur], b.count[b.cur], rcut, 0.0, 0, out);
+  const int64_t slots_end = (int64_t)(g.cell_off + g.ncell) * b.cap;
+  if (!(rcut < 0.25 * g.L) || slots_end >= ((int64_t)1 << 31)) {
+    const int bs = 128;
+    k_pairs<false><<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(
+        g, b.cap, b.px[b.cur], b.py[b.cur], b.count[b.cur], rcut, 0.0, 0, out);
+    return;
+  }
+  const double scale = 4294967296.0 / g.L;
+  uint2* fxy = reinterpret_cast<uint2*>(b.px[1 - b.cur]);
+  {
+    const int bs = 256;
+    k_fixed_point<<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(
+        g, b.cap, b.px[b.cur], b.py[b.cur], b.count[b.cur], scale, fxy);
+  }
+  const int Rx = (int)std::ceil(rcut * g.inv_w * (1.0 + 1e-9));
+  const int Ry = (int)std::ceil(rcut * g.inv_h * (1.0 + 1e-9));
+  const unsigned RC = (unsigned)std::ceil(rcut * scale) + 4u;
+  const double r2 = rcut * rcut;
+  unsigned long long r2_bits = 0;
+  std::memcpy(&r2_bits, &r2, sizeof(r2));
+  const bool half = 2 * Rx + 1 <= g.cells_x && 2 * Ry + 1 <= g.cells_y;
+  const int bs = 256;
+  const unsigned grid = (unsigned)(((int64_t)g.ncell * 32 + bs - 1) / bs);
+  if (half)
+    k_min_dist_fixed<true><<<grid, bs, 0, s>>>(g, b.cap, b.px[b.cur], b.py[b.cur], fxy,
+                                                b.count[b.cur], Rx, Ry, RC, r2_bits, out);
+  else
+    k_min_dist_fixed<false><<<grid, bs, 0, s>>>(g, b.cap, b.px[b.cur], b.py[b.cur], fxy,
+                                                 b.count[b.cur], Rx, Ry, RC, r2_bits, out);
 }
 
 void launch_gr(const Geom& g, const DevBufs& b, double dr, int nbins, unsigned long long* counts,
@@ -100,7 +322,8 @@ void launch_gr(const Geom& g, const DevBufs& b, double dr, int nbins, unsigned l
   const int bs = 128;
   const int64_t total = (int64_t)g.ncell * b.cap;
   const double rcut = g.sigma + dr * nbins;
-  k_pairs<true><<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(
+  const size_t sm = nbins <= kGrSharedBins ? sizeof(unsigned long long) * nbins : 0;
+  k_pairs<true><<<(unsigned)((total + bs - 1) / bs), bs, sm, s>>>(
       g, b.cap, b.px[b.cur], b.py[b.cur], b.count[b.cur], rcut, dr, nbins, counts);
 }
 
