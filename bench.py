@@ -646,7 +646,7 @@ def run_ours(args):
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         sm_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
         fp64_peak = FP64_LANES_PER_SM_CLK * n_sm * sm_mhz * 1e6 / 1e9
-        _, fp64_probe = P.ecmc.device_peaks()
+        smem_peak, fp64_probe = P.ecmc.device_peaks()
         cpu = None
         if not args.skip_cpu and descs is None:
             cpu = cpu_baseline(w, cells, ell, nm, args.cpu_seconds, melt_sweeps(args),
@@ -691,6 +691,8 @@ def run_ours(args):
                          "peak_source": "2 FP64 lanes/clk/SM x %d SMs x %.0f MHz (unit counts)"
                                         % (n_sm, sm_mhz),
                          "fp64_probe_gflops": fp64_probe},
+            "smem_roofline": smem_roofline(w, descs, c, iters, value, args.prec, smem_peak),
+            "latency": latency_ceiling(g, descs, cells, c, kt, clk, sm_mhz),
             # per sweep: draws, binning, the persistent sweep kernel (or 4 x frame
             # builder + chain kernel), chunk sums, end of sweep
             "gpu_launches": kernels_per_sweep * args.steps * world,
@@ -707,6 +709,44 @@ def run_ours(args):
 
         dist.destroy_process_group()
     return 0
+
+
+def smem_roofline(w, descs, c, iters, value, prec, smem_peak):
+    """The chain loop against shared-memory bandwidth, counting ALGORITHMIC
+    bytes: an event must inspect the disks whose centres lie in the strip that
+    can hold the first hit, area 2 sigma (sigma + lambda0) with lambda0 the
+    measured mean free path, at 8 B (FP32 x, y) or 16 B (FP64) each, plus 16 B
+    to read and write the mover."""
+    if descs is not None or iters <= 0:
+        return None
+    rho = w.N / (w.L * w.L)
+    lam0 = c.sum_disp / iters
+    disks = rho * 2.0 * (1.0 + lam0)
+    per = disks * (8.0 if prec else 16.0) + 16.0
+    achieved = value * per / 1e9
+    return {"bytes_per_event": per, "candidates_per_event": disks, "mean_free_path": lam0,
+            "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
+            "frac": achieved / smem_peak if smem_peak else None,
+            "peak_source": "ld.shared.v4 probe on this device"}
+
+
+def latency_ceiling(g, descs, cells, c, kt, clk, sm_mhz):
+    """Cycles one event costs a chain, from the dominant launch's time, the
+    SM clock and the chains the launch runs at once; and the events/s that
+    rate would give if every cell of a colour phase ran at the same time."""
+    from paper_1409_6948_gb300 import ecmc as E
+
+    flight = g.get_param(E.PARAM_CHAINS_IN_FLIGHT)
+    if descs is not None or flight <= 0 or kt.phase_launches <= 0 or c.events <= 0:
+        return None
+    mhz = (clk or {}).get("sm_mhz") or sm_mhz
+    launch_ms = kt.phase_ms / kt.phase_launches
+    events_per_launch = c.events / kt.phase_launches
+    cyc = launch_ms * 1e-3 * mhz * 1e6 * flight / events_per_launch
+    active = cells * cells / 4
+    return {"chains_in_flight": flight, "active_cells_per_phase": active,
+            "cycles_per_event_per_chain": cyc, "sm_mhz": mhz,
+            "ceiling_all_active_cells": active * mhz * 1e6 / cyc, "unit": "events/s"}
 
 
 def run_reference_batch(args):

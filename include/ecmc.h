@@ -134,6 +134,25 @@ extern "C" {
  * to bias the pressure (Fig. 3).  Needs cells of at most 128 disks
  * (ECMC_ERR_UNSUPPORTED otherwise); disables the replay of rattling chains. */
 #define ECMC_PARAM_LIST_MODE 19
+/* Read-only: cells whose chains run at the same time with the current launch
+ * shape -- the persistent kernel's grid (all blocks resident) times the cells
+ * a warp serves (32 / lanes per cell); 0 with per-phase launches, whose
+ * residency the hardware scheduler decides. */
+#define ECMC_PARAM_CHAINS_IN_FLIGHT 20
+/* Boundary rule (Sec. 3.4 and the comparison of Fig. 3):
+ * ECMC_BOUNDARY_REFLECT (default), chains reflect at cell walls and frozen
+ * disks (the paper's rule); ECMC_BOUNDARY_REJECT, a chain that reaches a cell
+ * wall or a frozen disk is rejected as a whole -- every disk it moved returns
+ * to its position at the chain's start, its contacts are counted in events,
+ * lifts, frozen_hits and wall_hits but not in sum_b, and its budget is not in
+ * sum_disp (ecmc_pressure then averages over accepted chains only, an
+ * estimator not derived for this rule; the paper reads the pressure of this
+ * variant from g(sigma+)).  Axis chains only (ECMC_ERR_UNSUPPORTED with
+ * isotropic directions); allocates an undo log of 32 bytes per bucket slot
+ * (ECMC_ERR_OOM if that fails). */
+#define ECMC_PARAM_BOUNDARY 21
+#define ECMC_BOUNDARY_REFLECT 0
+#define ECMC_BOUNDARY_REJECT 1
 #define ECMC_LIST_WITH_REPL 0
 #define ECMC_LIST_WITHOUT_REPL 1
 
@@ -159,6 +178,7 @@ typedef struct {
                           * repeated the two legs before them bit for bit and were
                           * replayed without a candidate search; included in
                           * frozen_hits / wall_hits                             */
+  int64_t rejected_chains; /* chains rejected under ECMC_BOUNDARY_REJECT          */
 } ecmc_counters_t;
 
 typedef struct {

@@ -25,20 +25,23 @@ FLAG_BRUTE_FROZEN = 2
 FLAG_REVERSE_CELLS = 4
 FLAG_FIXED_COLOURS = 8
 FLAG_SPECULAR_AXIS = 16
+BOUNDARY_REFLECT = 0
+BOUNDARY_REJECT = 1
 
 
 class Params(C.Structure):
     _fields_ = [("N", C.c_int64), ("L", C.c_double), ("sigma", C.c_double),
                 ("cells_x", C.c_int), ("cells_y", C.c_int), ("ell", C.c_double),
                 ("n_m", C.c_int), ("seed", C.c_uint64), ("replica", C.c_uint64),
-                ("dir_mode", C.c_int), ("list_mode", C.c_int), ("flags", C.c_uint)]
+                ("dir_mode", C.c_int), ("list_mode", C.c_int), ("flags", C.c_uint),
+                ("boundary", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("sweeps", C.c_int64), ("chains", C.c_int64), ("events", C.c_int64),
                 ("lifts", C.c_int64), ("frozen_hits", C.c_int64), ("wall_hits", C.c_int64),
                 ("capped", C.c_int64), ("sum_b", C.c_double), ("sum_disp", C.c_double),
-                ("sum_b_w", C.c_double), ("sum_disp_w", C.c_double)]
+                ("sum_b_w", C.c_double), ("sum_disp_w", C.c_double), ("rejected", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -103,9 +106,11 @@ def philox(ctr, key):
 
 
 def make_params(N, L, sigma, cells_x, cells_y, ell, n_m, seed, replica=0,
-                dir_mode=DIR_PM_AXIS_ALT, list_mode=LIST_WITH_REPL, flags=0):
+                dir_mode=DIR_PM_AXIS_ALT, list_mode=LIST_WITH_REPL, flags=0,
+                boundary=BOUNDARY_REFLECT):
     return Params(int(N), float(L), float(sigma), int(cells_x), int(cells_y), float(ell),
-                  int(n_m), int(seed), int(replica), int(dir_mode), int(list_mode), int(flags))
+                  int(n_m), int(seed), int(replica), int(dir_mode), int(list_mode), int(flags),
+                  int(boundary))
 
 
 def sweep_draws(p, t):
@@ -198,7 +203,7 @@ def min_dist2(L, x, y, rcut=2.0):
 
 
 def run_chain_frame(X, Y, n_mem, m, dx, dy, ell, w, h, sigma=1.0, ids=None, imgs=None,
-                    specular=False):
+                    specular=False, reject=False):
     """One chain on an explicit frame; returns (X, Y, stats, record)."""
     X = np.ascontiguousarray(X, dtype=np.float64).copy()
     Y = np.ascontiguousarray(Y, dtype=np.float64).copy()
@@ -211,7 +216,7 @@ def run_chain_frame(X, Y, n_mem, m, dx, dy, ell, w, h, sigma=1.0, ids=None, imgs
                                    ids.ctypes.data_as(C.POINTER(C.c_int64)),
                                    imgs.ctypes.data_as(C.POINTER(C.c_int32)), float(w), float(h),
                                    float(sigma), int(m), float(dx), float(dy), float(ell),
-                                   int(bool(specular)), C.byref(st),
+                                   int(bool(specular)) | 2 * int(bool(reject)), C.byref(st),
                                    rec.ctypes.data_as(C.c_void_p))
     if rc != 0:
         raise ValueError("bad frame")

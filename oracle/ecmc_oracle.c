@@ -26,6 +26,9 @@
  *   Sec. 3.4 (Fig. 2)    why the start list is drawn with replacement; the
  *                        shuffled list of distinct members is kept only as a
  *                        negative control (ORC_LIST_WITHOUT_REPL).
+ *   Sec. 3.4 (Fig. 3)    the rejecting boundary rule the paper compares
+ *                        against (ORC_BOUNDARY_REJECT): a chain that reaches
+ *                        a wall or a frozen disk is rejected as a whole.
  *   Sec. 2               pair-correlation histogram with the centred-bin rule.
  *   Sec. 4, eq. (nm)     default number of chains per cell.
  *
@@ -274,6 +277,10 @@ typedef struct {
   orc_stats* st;
   unsigned char* touched; /* per member: was the active disk of a chain */
   int specular;           /* frozen-disk contact: 1 specular, 0 reversal */
+  int reject;             /* ORC_BOUNDARY_REJECT                         */
+  double* X0;             /* reject: members' coordinates at chain start */
+  double* Y0;
+  unsigned char* touched0;
 } chain_ctx;
 
 /*
@@ -285,12 +292,24 @@ typedef struct {
  *   - the first wall of the cell rectangle,
  * moves the active disk there and lifts (member hit), reflects specularly
  * (frozen disk hit) or flips the normal component of d (wall).
+ *
+ * Under the rejecting rule the members' coordinates are saved at the start;
+ * the first wall or frozen-disk event restores them and ends the chain
+ * (return value 1), and the chain's contact sum is dropped.  Otherwise the
+ * chain's contact sum is added to the statistics as it accrues.
  */
-static void run_chain(frame_t* f, const chain_ctx* cx, int m, double dx, double dy, double ell,
-                      orc_chain_rec* rec) {
+static int run_chain(frame_t* f, const chain_ctx* cx, int m, double dx, double dy, double ell,
+                     orc_chain_rec* rec) {
   const double w = cx->w, h = cx->h, sig2 = cx->sig2;
   double r = ell;
   int64_t nev = 0, nwall = 0;
+  int rejected = 0;
+  double chain_b = 0.0; /* reject: the chain's contact sum until it is accepted */
+  if (cx->reject) {
+    memcpy(cx->X0, f->X, sizeof(double) * (size_t)f->n_mem);
+    memcpy(cx->Y0, f->Y, sizeof(double) * (size_t)f->n_mem);
+    if (cx->touched) memcpy(cx->touched0, cx->touched, (size_t)f->n_mem);
+  }
   if (cx->touched) cx->touched[m] = 1;
   for (int64_t iter = 0;; ++iter) {
     if (iter >= ORC_MAX_EVENTS_PER_CHAIN) {
@@ -333,6 +352,26 @@ static void run_chain(frame_t* f, const chain_ctx* cx, int m, double dx, double 
     if (r <= best_s && r <= swall) { /* budget used up: the chain ends */
       f->X[m] = Xm + r * dx;
       f->Y[m] = Ym + r * dy;
+      if (cx->reject && cx->st) cx->st->sum_b += chain_b;
+      break;
+    }
+    if (cx->reject && !(best_s <= swall && best < f->n_mem)) {
+      /* the chain reaches a wall or a frozen disk: rejected as a whole */
+      if (best_s <= swall) {
+        nev++;
+        if (cx->st) {
+          cx->st->events++;
+          cx->st->frozen_hits++;
+        }
+      } else {
+        nwall++;
+        if (cx->st) cx->st->wall_hits++;
+      }
+      memcpy(f->X, cx->X0, sizeof(double) * (size_t)f->n_mem);
+      memcpy(f->Y, cx->Y0, sizeof(double) * (size_t)f->n_mem);
+      if (cx->touched) memcpy(cx->touched, cx->touched0, (size_t)f->n_mem);
+      if (cx->st) cx->st->rejected++;
+      rejected = 1;
       break;
     }
     if (best_s <= swall) { /* contact */
@@ -344,7 +383,8 @@ static void run_chain(frame_t* f, const chain_ctx* cx, int m, double dx, double 
       nev++;
       if (cx->st) {
         cx->st->events++;
-        cx->st->sum_b += best_b - s;
+        if (cx->reject) chain_b += best_b - s;
+        else cx->st->sum_b += best_b - s;
       }
       if (best < f->n_mem) { /* lift: the hit member moves on along d */
         if (cx->st) cx->st->lifts++;
@@ -387,6 +427,7 @@ static void run_chain(frame_t* f, const chain_ctx* cx, int m, double dx, double 
     rec->events = nev;
     rec->walls = nwall;
   }
+  return rejected;
 }
 
 static int check_params(const orc_params* p) {
@@ -394,6 +435,7 @@ static int check_params(const orc_params* p) {
   if (p->cells_x < 2 || p->cells_y < 2 || (p->cells_x & 1) || (p->cells_y & 1)) return -1;
   if (!(p->L / p->cells_x > p->sigma) || !(p->L / p->cells_y > p->sigma)) return -1;
   if (!(p->ell >= 0.0) || p->n_m < 1) return -1;
+  if (p->boundary != ORC_BOUNDARY_REFLECT && p->boundary != ORC_BOUNDARY_REJECT) return -1;
   return 0;
 }
 
@@ -405,7 +447,8 @@ int orc_sweeps(const orc_params* p, double* x, double* y, int64_t t0, int64_t n_
   const int ncx = p->cells_x, ncy = p->cells_y, ncell = ncx * ncy;
   const double w = L / (double)ncx, h = L / (double)ncy;
   chain_ctx ctx = {w, h, sigma, sigma * sigma, st, NULL,
-                   p->dir_mode == ORC_DIR_ISOTROPIC || (p->flags & ORC_FLAG_SPECULAR_AXIS)};
+                   p->dir_mode == ORC_DIR_ISOTROPIC || (p->flags & ORC_FLAG_SPECULAR_AXIS),
+                   p->boundary == ORC_BOUNDARY_REJECT, NULL, NULL, NULL};
 
   int32_t* cell = (int32_t*)malloc(sizeof(int32_t) * N);
   int64_t* start = (int64_t*)malloc(sizeof(int64_t) * (ncell + 1));
@@ -485,6 +528,9 @@ int orc_sweeps(const orc_params* p, double* x, double* y, int64_t t0, int64_t n_
         if (f.n_mem > cap0) {
           cap0 = f.n_mem;
           touched = (unsigned char*)realloc(touched, (size_t)cap0);
+          ctx.X0 = (double*)realloc(ctx.X0, sizeof(double) * (size_t)cap0);
+          ctx.Y0 = (double*)realloc(ctx.Y0, sizeof(double) * (size_t)cap0);
+          ctx.touched0 = (unsigned char*)realloc(ctx.touched0, (size_t)cap0);
         }
         memset(touched, 0, (size_t)f.n_mem);
         ctx.touched = touched;
@@ -527,6 +573,7 @@ int orc_sweeps(const orc_params* p, double* x, double* y, int64_t t0, int64_t n_
 
         /* step 6: one chain per list entry, in list order */
         const double sum_b_before = st ? st->sum_b : 0.0;
+        int accepted = 0;
         for (int k2 = 0; k2 < p->n_m; ++k2) {
           orc_chain_rec* rec = recs ? &recs[(s * ncell + c) * p->n_m + k2] : NULL;
           if (rec) {
@@ -549,18 +596,19 @@ int orc_sweeps(const orc_params* p, double* x, double* y, int64_t t0, int64_t n_
           }
           int m = (int)list[k2];
           if (rec) rec->start_id = f.id[m];
-          run_chain(&f, &ctx, m, dx, dy, p->ell, rec);
+          const int rej = run_chain(&f, &ctx, m, dx, dy, p->ell, rec);
           if (st) {
             st->chains++;
-            st->sum_disp += p->ell;
+            if (!rej) st->sum_disp += p->ell;
           }
+          accepted += rej ? 0 : 1;
         }
 
         /* member-weighted pressure sums: the cell's contact sum and its
          * displacement, each weighted by the number of members n_c */
         if (st && nc > 0) {
           st->sum_b_w += (double)nc * (st->sum_b - sum_b_before);
-          st->sum_disp_w += (double)nc * ((double)p->n_m * p->ell);
+          st->sum_disp_w += (double)nc * ((double)accepted * p->ell);
         }
 
         /* write back, in box coordinates, every member that was the active
@@ -581,6 +629,9 @@ int orc_sweeps(const orc_params* p, double* x, double* y, int64_t t0, int64_t n_
   free(fill);
   free(order);
   free(touched);
+  free(ctx.X0);
+  free(ctx.Y0);
+  free(ctx.touched0);
   free(list);
   free(perm_buf);
   free(f.X);
@@ -837,20 +888,25 @@ double orc_min_dist2(int64_t N, double L, const double* x, const double* y, doub
 /* ------------------------------------------------------------------------ */
 int orc_run_chain_frame(int n, int n_mem, double* X, double* Y, const int64_t* id,
                         const int32_t* img, double w, double h, double sigma, int m, double dx,
-                        double dy, double ell, int specular, orc_stats* st,
+                        double dy, double ell, int mode, orc_stats* st,
                         orc_chain_rec* rec) {
   if (n < 1 || n_mem < 1 || n_mem > n || m < 0 || m >= n_mem) return -1;
   frame_t f;
   memset(&f, 0, sizeof(f));
   for (int q = 0; q < n; ++q) frame_push(&f, X[q], Y[q], id[q], img[q]);
   f.n_mem = n_mem;
-  chain_ctx ctx = {w, h, sigma, sigma * sigma, st, NULL, specular};
+  const int reject = (mode & 2) != 0;
+  double* X0 = reject ? (double*)malloc(sizeof(double) * (size_t)n_mem) : NULL;
+  double* Y0 = reject ? (double*)malloc(sizeof(double) * (size_t)n_mem) : NULL;
+  chain_ctx ctx = {w, h, sigma, sigma * sigma, st, NULL, mode & 1, reject, X0, Y0, NULL};
   if (rec) rec->start_id = id[m];
-  run_chain(&f, &ctx, m, dx, dy, ell, rec);
+  const int rej = run_chain(&f, &ctx, m, dx, dy, ell, rec);
   if (st) {
     st->chains++;
-    st->sum_disp += ell;
+    if (!rej) st->sum_disp += ell;
   }
+  free(X0);
+  free(Y0);
   for (int q = 0; q < n; ++q) {
     X[q] = f.X[q];
     Y[q] = f.Y[q];

@@ -30,6 +30,12 @@ extern "C" {
 #define ORC_LIST_WITH_REPL 0    /* n_m draws with replacement (the paper's rule)   */
 #define ORC_LIST_WITHOUT_REPL 1 /* shuffled distinct members (negative control)    */
 
+/* Boundary rule (Sec. 3.4, discussion of Fig. 3). */
+#define ORC_BOUNDARY_REFLECT 0 /* reflect at walls and frozen disks (the paper's rule) */
+#define ORC_BOUNDARY_REJECT 1  /* reject the whole chain when it reaches a wall or a
+                                  frozen disk: every disk it moved returns to its
+                                  position at the chain's start                      */
+
 /* flags */
 #define ORC_FLAG_NO_SHIFT 1u       /* grid shift forced to (0,0) (closed-form tests) */
 #define ORC_FLAG_BRUTE_FROZEN 2u   /* frozen set from ALL disks, not neighbour cells */
@@ -61,6 +67,7 @@ typedef struct {
   int dir_mode;    /* ORC_DIR_*                                        */
   int list_mode;   /* ORC_LIST_*                                       */
   unsigned flags;  /* ORC_FLAG_*                                       */
+  int boundary;    /* ORC_BOUNDARY_*                                   */
 } orc_params;
 
 typedef struct {
@@ -74,7 +81,11 @@ typedef struct {
   double sum_b;        /* sum over contacts of the separation projected on d */
   double sum_disp;     /* sum over chains of the displacement budget ell     */
   double sum_b_w;      /* sum over cells of n_c * (contact sum of the cell)  */
-  double sum_disp_w;   /* sum over cells of n_c * n_m * ell                  */
+  double sum_disp_w;   /* sum over cells of n_c * (accepted chains) * ell    */
+  int64_t rejected;    /* chains rejected under ORC_BOUNDARY_REJECT; their
+                          contacts are counted in events, lifts, frozen_hits
+                          and wall_hits but not in sum_b, and their budget is
+                          not in sum_disp                                      */
 } orc_stats;
 
 /* Optional per-chain record (debugging and parity tests). */
@@ -139,12 +150,13 @@ int orc_sweeps_snap(const orc_params* p, double* x, double* y, int64_t t0, int64
 
 /* Run one chain on a caller-built frame: objects 0..n_mem-1 are members of
  * the active cell [0,w] x [0,h], the rest frozen (img = image code used only
- * for tie-breaks).  Object m starts with direction (dx,dy) and budget ell;
- * specular = 1 reflects specularly at frozen objects, 0 turns the chain back.
+ * for tie-breaks).  Object m starts with direction (dx,dy) and budget ell.
+ * mode bit 0: reflect specularly at frozen objects (else turn the chain
+ * back); bit 1: the rejecting boundary rule (ORC_BOUNDARY_REJECT).
  * X, Y are updated in place. */
 int orc_run_chain_frame(int n, int n_mem, double* X, double* Y, const int64_t* id,
                         const int32_t* img, double w, double h, double sigma, int m, double dx,
-                        double dy, double ell, int specular, orc_stats* st,
+                        double dy, double ell, int mode, orc_stats* st,
                         orc_chain_rec* rec);
 
 #ifdef __cplusplus

@@ -100,6 +100,7 @@ struct ecmc_ctx {
   double* xy_tmp = nullptr;
   int* int_tmp = nullptr;
   unsigned long long* u64_tmp = nullptr;
+  UndoEntry* undo = nullptr;  // rejecting boundary rule: [C_total][cap] undo logs
 };
 
 namespace {
@@ -254,10 +255,10 @@ int compute_layout(ecmc_ctx* h) {
   // unless mode 1 is asked for: FP64 coordinates in a per-warp scratch area of
   // global memory, more warps per SM (measured at N = 1M, eta = 0.72: 1.64
   // against 1.58 * 10^9 events/s); isotropic chains use mode 0
-  const int fm = (h->fmode_param == 1 && !h->b.iso) ? 1 : 0;
+  const int fm = (h->fmode_param == 1 && chain_kind(h->b) == 0) ? 1 : 0;
   if (h->persist_param && fmode < 2 && fused_smem_bytes(h->lay, fm) <= limit / 2) {
     int per_sm = 0;
-    if (configure_fused(h->lay, h->tpc, fm, h->b.iso, &per_sm) == 0) {
+    if (configure_fused(h->lay, h->tpc, fm, chain_kind(h->b), &per_sm) == 0) {
       const int n_items = 4 * n_groups;
       const int grid = per_sm * h->n_sm < n_items ? per_sm * h->n_sm : n_items;
       const size_t scratch = (size_t)grid * fused_scratch_bytes(h->lay);
@@ -524,6 +525,7 @@ void free_all(ecmc_ctx* h) {
   cudaFree(h->xy_tmp);
   cudaFree(h->int_tmp);
   cudaFree(h->u64_tmp);
+  cudaFree(h->undo);
   for (auto& e : h->pending) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
@@ -793,6 +795,7 @@ void to_counters(const RunTotals& t, ecmc_counters_t* out) {
   out->sum_b = t.sum_b;
   out->sum_disp = t.sum_disp;
   out->replayed_legs = t.replayed;
+  out->rejected_chains = t.rejected;
 }
 
 }  // namespace
@@ -890,6 +893,8 @@ int ecmc_set_param(ecmc_t h, int key, double v) {
     }
     case ECMC_PARAM_DIR_MODE: {
       if (v != 0.0 && v != 1.0 && v != 2.0) return fail(ECMC_ERR_ARG, "direction mode");
+      if (v == 2.0 && h->geo[0].boundary == 1)
+        return fail(ECMC_ERR_UNSUPPORTED, "the rejecting boundary rule needs axis chains");
       for (Geom& g : h->geo) g.dir_mode = (int)v;
       h->b.iso = v == 2.0 ? 1 : 0;
       drop_graphs(h);
@@ -962,6 +967,8 @@ int ecmc_set_param(ecmc_t h, int key, double v) {
       return ECMC_OK;
     case ECMC_PARAM_KERNELS_PER_SWEEP:
       return fail(ECMC_ERR_ARG, "kernels per sweep is read-only");
+    case ECMC_PARAM_CHAINS_IN_FLIGHT:
+      return fail(ECMC_ERR_ARG, "chains in flight is read-only");
     case ECMC_PARAM_LIST_MODE: {
       if (v != 0.0 && v != 1.0) return fail(ECMC_ERR_ARG, "list mode must be 0 or 1");
       if (v == 1.0)
@@ -973,6 +980,28 @@ int ecmc_set_param(ecmc_t h, int key, double v) {
       for (Geom& g : h->geo) g.list_mode = (int)v;
       drop_graphs(h);
       return upload_geometry(h);
+    }
+    case ECMC_PARAM_BOUNDARY: {
+      if (v != 0.0 && v != 1.0) return fail(ECMC_ERR_ARG, "boundary rule must be 0 or 1");
+      if (v == 1.0 && h->b.iso)
+        return fail(ECMC_ERR_UNSUPPORTED, "the rejecting boundary rule needs axis chains");
+      if (v == 1.0 && !h->undo) {
+        const size_t n = (size_t)h->b.C_total * (size_t)h->b.cap;
+        if (cudaMalloc(&h->undo, sizeof(UndoEntry) * n) != cudaSuccess) {
+          cudaGetLastError();
+          h->undo = nullptr;
+          return fail(ECMC_ERR_OOM, "undo logs of the rejecting boundary rule (%zu bytes)",
+                      sizeof(UndoEntry) * n);
+        }
+      }
+      for (Geom& g : h->geo) {
+        g.boundary = (int)v;
+        g.undo = h->undo;
+        g.undo_stride = h->b.cap;
+      }
+      h->b.reject = (int)v;
+      drop_graphs(h);
+      return compute_layout(h);
     }
     case ECMC_PARAM_REPLAY:
       if (v != 0.0 && v != 1.0) return fail(ECMC_ERR_ARG, "replay must be 0 or 1");
@@ -1012,7 +1041,11 @@ int ecmc_get_param(ecmc_t h, int key, double* v) {
     case ECMC_PARAM_WAIT_LIMIT_MS: *v = h->wait_ms; break;
     case ECMC_PARAM_WAIT_TEST: *v = h->b.wait_test; break;
     case ECMC_PARAM_KERNELS_PER_SWEEP: *v = h->persistent ? 5 : 12; break;
+    case ECMC_PARAM_CHAINS_IN_FLIGHT:
+      *v = h->persistent ? (double)h->fused_blocks * (32 / h->tpc) : 0.0;
+      break;
     case ECMC_PARAM_LIST_MODE: *v = h->geo[0].list_mode; break;
+    case ECMC_PARAM_BOUNDARY: *v = h->geo[0].boundary; break;
     default: return fail(ECMC_ERR_ARG, "unknown parameter %d", key);
   }
   return ECMC_OK;
@@ -1113,6 +1146,7 @@ int ecmc_counters(ecmc_t h, ecmc_counters_t* out) {
     s.walls += v.walls;
     s.fp64_evals += v.fp64_evals;
     s.replayed += v.replayed;
+    s.rejected += v.rejected;
   }
   to_counters(s, out);
   return ECMC_OK;

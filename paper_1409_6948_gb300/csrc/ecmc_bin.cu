@@ -213,12 +213,13 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
 __global__ void __launch_bounds__(256) k_sweep_partials(const CellStats* __restrict__ cs,
                                                         const int2* __restrict__ chunks,
                                                         ChunkSums* __restrict__ out) {
+  constexpr int NV = 9;
   __shared__ double sd[2][8];
-  __shared__ long long sl[7][8];
+  __shared__ long long sl[NV][8];
   const int2 ch = chunks[blockIdx.x];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   double b = 0.0, bw = 0.0;
-  long long v[7] = {0, 0, 0, 0, 0, 0, 0};
+  long long v[NV] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (int c = ch.x + tid; c < ch.y; c += blockDim.x) {
     const CellStats s = cs[c];
     b += s.sum_b;
@@ -230,25 +231,27 @@ __global__ void __launch_bounds__(256) k_sweep_partials(const CellStats* __restr
     v[4] += s.fp64_evals;
     v[5] += s.chains;
     v[6] += s.replayed;
+    v[7] += s.rejected;
+    v[8] += (long long)s.n_mem * s.rejected;
   }
   b = warp_sum_d(b);
   bw = warp_sum_d(bw);
-  for (int q = 0; q < 7; ++q) v[q] = warp_sum_ll(v[q]);
+  for (int q = 0; q < NV; ++q) v[q] = warp_sum_ll(v[q]);
   if (lane == 0) {
     sd[0][wid] = b;
     sd[1][wid] = bw;
-    for (int q = 0; q < 7; ++q) sl[q][wid] = v[q];
+    for (int q = 0; q < NV; ++q) sl[q][wid] = v[q];
   }
   __syncthreads();
   if (tid == 0) {
     ChunkSums r;
     r.sum_b = 0.0;
     r.sum_b_w = 0.0;
-    for (int q = 0; q < 7; ++q) r.v[q] = 0;
+    for (int q = 0; q < NV; ++q) r.v[q] = 0;
     for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) {
       r.sum_b += sd[0][wv];
       r.sum_b_w += sd[1][wv];
-      for (int q = 0; q < 7; ++q) r.v[q] += sl[q][wv];
+      for (int q = 0; q < NV; ++q) r.v[q] += sl[q][wv];
     }
     out[blockIdx.x] = r;
   }
@@ -269,18 +272,19 @@ __global__ void k_sweep_end(const Geom* __restrict__ rg, SweepState* st,
   if (rep >= R) return;
   const Geom& g = rg[rep];
   double b = 0.0, bw = 0.0;
-  long long v[7] = {0, 0, 0, 0, 0, 0, 0};
+  long long v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (int k = chunk_off[rep]; k < chunk_off[rep + 1]; ++k) {
     b += part[k].sum_b;
     bw += part[k].sum_b_w;
-    for (int q = 0; q < 7; ++q) v[q] += part[k].v[q];
+    for (int q = 0; q < 9; ++q) v[q] += part[k].v[q];
   }
   RunTotals& T = tot[rep];
   SweepState& S = st[rep];
-  const double disp_w = (double)g.N * (double)g.n_m * g.ell;
+  // displacement of the accepted chains, each weighted by its cell's members
+  const double disp_w = (double)(g.N * (long long)g.n_m - v[8]) * g.ell;
   T.sum_b += b;
   T.sum_b_w += bw;
-  T.sum_disp += (double)v[5] * g.ell;
+  T.sum_disp += (double)(v[5] - v[7]) * g.ell;
   T.sum_disp_w += disp_w;
   T.events += v[0];
   T.lifts += v[1];
@@ -289,6 +293,7 @@ __global__ void k_sweep_end(const Geom* __restrict__ rg, SweepState* st,
   T.fp64_evals += v[4];
   T.chains += v[5];
   T.replayed += v[6];
+  T.rejected += v[7];
   T.sweeps += 1;
   if (history != nullptr && S.history_len < history_cap) {
     double* h = history + 2 * ((int64_t)rep * history_cap + S.history_len);

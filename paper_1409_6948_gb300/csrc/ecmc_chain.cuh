@@ -196,7 +196,36 @@ __device__ __forceinline__ void replay_cycle(const Frame& f, const LegHist& hs, 
 // and per-cell statistics.  Lane group gi of the warp works on global active
 // cell a (valid: a exists) of colour phase colour_index, whose frame is column
 // gi of f.
-template <int TPC, bool SCREEN>
+// Rejecting boundary rule: log the frame state of member m before it moves
+// (entry e of cell c's undo log), and restore a whole log, newest first.
+// Every lane of the group writes and reads the same values.
+__device__ __forceinline__ void undo_push(const Geom& g, int c, int e, const Frame& f, int m,
+                                          int gi) {
+  const int i = m * f.cpw + gi;
+  UndoEntry u;
+  u.a = f.a64[i];
+  u.b = f.b64[i];
+  u.a32 = f.a32[i];
+  u.b32 = f.b32[i];
+  u.m = m;
+  u.touched = f.touched[i];
+  g.undo[(int64_t)c * g.undo_stride + e] = u;
+}
+
+__device__ __forceinline__ void undo_restore(const Geom& g, int c, int n, const Frame& f,
+                                             int gi) {
+  for (int e = n - 1; e >= 0; --e) {
+    const UndoEntry u = g.undo[(int64_t)c * g.undo_stride + e];
+    const int i = u.m * f.cpw + gi;
+    f.a64[i] = u.a;
+    f.b64[i] = u.b;
+    f.a32[i] = u.a32;
+    f.b32[i] = u.b32;
+    f.touched[i] = (unsigned char)u.touched;
+  }
+}
+
+template <int TPC, bool SCREEN, bool REJECT>
 __device__ __forceinline__ void run_group(const Frame& f, const LegHist& hs, const int* hdr,
                                           const Geom* __restrict__ rg,
                                           const SweepState* __restrict__ sts, int rep, int a,
@@ -240,6 +269,12 @@ __device__ __forceinline__ void run_group(const Frame& f, const LegHist& hs, con
   int ch_events = 0, ch_walls = 0, start_key = 0;
   int n_leg = 0;  // legs of the current chain recorded in the history
   int n_replayed = 0;
+  // rejecting boundary rule: movers logged, the chain's contact sum until
+  // the chain is accepted, chains rejected
+  constexpr bool reject_rule = REJECT;
+  int n_undo = 0, n_rejected = 0;
+  double ch_b = 0.0;
+  if (reject_rule) replay = 0;
   bool done = (!valid) || nmem == 0;
 
   for (;;) {
@@ -266,6 +301,11 @@ __device__ __forceinline__ void run_group(const Frame& f, const LegHist& hs, con
         P32 = f.a32[m * CPW + gi];
         Q32 = f.b32[m * CPW + gi];
         r = g.ell;
+        if (reject_rule) {
+          undo_push(g, c, 0, f, m, gi);
+          n_undo = 1;
+          ch_b = 0.0;
+        }
         f.touched[m * CPW + gi] = 1;
         start_key = f.key[m * CPW + gi];
         n_iter = 0;
@@ -451,8 +491,12 @@ __device__ __forceinline__ void run_group(const Frame& f, const LegHist& hs, con
     const double addb = best_b - best_s;
     const float P32n = to_float_trunc(Pnew);
     bool end_chain = capped;
+    bool rejected_now = false;
     if (go) {
-      if (is_contact) sum_b += addb;
+      if (is_contact) {
+        if (reject_rule) ch_b += addb;
+        else sum_b += addb;
+      }
       r = rnew;
       const bool is_lift = is_contact && (f.info[best_j * CPW + gi] >= 0);
       n_events += is_contact ? 1 : 0;
@@ -462,7 +506,13 @@ __device__ __forceinline__ void run_group(const Frame& f, const LegHist& hs, con
       n_walls += is_wall ? 1 : 0;
       ch_walls += is_wall ? 1 : 0;
       n_iter += (is_contact || is_wall) ? 1 : 0;
-      if (replay && g.list_mode == 0 && !is_end) {
+      rejected_now = reject_rule && (is_wall || (is_contact && !is_lift));
+      if (rejected_now) {
+        // the chain reached a wall or a frozen disk: every disk it moved
+        // returns to its position at the chain's start
+        undo_restore(g, c, n_undo < g.cap_mem ? n_undo : g.cap_mem, f, gi);
+        ++n_rejected;
+      } else if (replay && g.list_mode == 0 && !is_end) {
         // every lane of the group writes the same values, so each lane reads
         // back its own writes
         const int hl = (n_leg & (kHist - 1)) * CPW + gi;
@@ -473,7 +523,8 @@ __device__ __forceinline__ void run_group(const Frame& f, const LegHist& hs, con
         hs.flags[hl] = (sg < 0 ? 1 : 0) | (is_lift ? 0 : (is_wall ? 4 : 2));
         ++n_leg;
       }
-      if (is_lift) {
+      if (rejected_now) {
+      } else if (is_lift) {
         // the hit member carries on with the rest of the budget
         f.a64[m * CPW + gi] = Pnew;
         f.a32[m * CPW + gi] = P32n;
@@ -482,6 +533,11 @@ __device__ __forceinline__ void run_group(const Frame& f, const LegHist& hs, con
         Q = f.b64[m * CPW + gi];
         P32 = f.a32[m * CPW + gi];
         Q32 = f.b32[m * CPW + gi];
+        if (reject_rule) {
+          if (n_undo < g.cap_mem) undo_push(g, c, n_undo, f, m, gi);
+          else atomicCAS(err, DEV_OK, DEV_CAPACITY);
+          ++n_undo;
+        }
         f.touched[m * CPW + gi] = 1;
       } else {
         P = Pnew;
@@ -494,11 +550,14 @@ __device__ __forceinline__ void run_group(const Frame& f, const LegHist& hs, con
                                    n_replayed);
         }
       }
-      end_chain = is_end;
+      end_chain = is_end || rejected_now;
+      if (reject_rule && is_end) sum_b += ch_b;
     }
     if (end_chain) {
-      f.a64[m * CPW + gi] = P;
-      f.a32[m * CPW + gi] = P32;
+      if (!rejected_now) {
+        f.a64[m * CPW + gi] = P;
+        f.a32[m * CPW + gi] = P32;
+      }
       if (recs != nullptr && sub == 0) {
         ChainRec rc;
         rc.start_id = start_key >> 4;
@@ -536,6 +595,7 @@ __device__ __forceinline__ void run_group(const Frame& f, const LegHist& hs, con
     s.chains = n_chains;
     s.n_mem = nmem;
     s.replayed = n_replayed;
+    s.rejected = n_rejected;
     cs[c] = s;
   }
 }

@@ -366,6 +366,7 @@ __device__ __forceinline__ void run_group_iso(const Frame& f, const int* hdr, vo
     s.chains = n_chains;
     s.n_mem = nmem;
     s.replayed = 0;
+    s.rejected = 0;
     cs[c] = s;
   }
 }

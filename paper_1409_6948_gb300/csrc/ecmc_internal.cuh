@@ -48,18 +48,20 @@ struct CellStats {
   double sum_b;     // contact sum of the cell's chains, in chain order
   int events, lifts, frozen, walls;
   int fp64_evals, chains, n_mem, replayed;
+  int rejected;     // chains rejected under the rejecting boundary rule
 };
 
 // Partial sums of one chunk of a replica's cells (end-of-sweep reduction).
 struct ChunkSums {
   double sum_b, sum_b_w;
-  long long v[7];  // events, lifts, frozen, walls, fp64_evals, chains, replayed
+  long long v[9];  // events, lifts, frozen, walls, fp64_evals, chains, replayed,
+                   // rejected, sum of n_mem * rejected
 };
 
 // Running totals (device).
 struct RunTotals {
   double sum_b, sum_disp, sum_b_w, sum_disp_w;
-  long long sweeps, chains, events, lifts, frozen, walls, fp64_evals, replayed;
+  long long sweeps, chains, events, lifts, frozen, walls, fp64_evals, replayed, rejected;
 };
 
 struct ChainRec {
@@ -67,6 +69,17 @@ struct ChainRec {
 };
 
 // ---- static geometry and capacities of one replica -------------------------
+// Undo log of one chain under the rejecting boundary rule: every disk that
+// became the mover, with its frame coordinates and touched flag before it
+// moved.  A straight chain without reflections passes no disk twice (each
+// new mover lies ahead of the previous one along d), so a cell needs at most
+// one entry per member.
+struct UndoEntry {
+  double a, b;
+  float a32, b32;
+  int m, touched;
+};
+
 // A handle holds R independent replicas (R = 1 for ecmc_create).  Their cells
 // are numbered globally: replica r owns cells [cell_off, cell_off + ncell) and,
 // in every colour phase, active cells [act_off, act_off + nact).  All cell
@@ -103,6 +116,9 @@ struct Geom {
   float iso_sig_lo;  // certain-hit threshold on |c| (below sigma)
   float iso_sig_hi;  // certain-miss threshold on |c| (above sigma)
   int precision;     // 0 FP64 candidates, 1 FP32 screening
+  int boundary;      // 0 reflect at walls and frozen disks, 1 reject the whole chain
+  UndoEntry* undo;   // boundary 1: undo logs, undo_stride entries per global cell
+  int undo_stride;   // largest bucket capacity of the handle (>= cap_mem)
 };
 
 // Frame record layout of one group of cpw cells (all arrays [index][cpw]).
@@ -170,6 +186,7 @@ struct DevBufs {
   int n_chunks;
   int replay;              // 1 = replay repeating reflection legs (chain kernel)
   int iso;                 // 1 = isotropic directions
+  int reject;              // 1 = rejecting boundary rule (axis chains)
   unsigned* sched;         // persistent sweep: [0] next work item, [1] epoch, [2] abort
   unsigned* done;          // [C_total] epoch in which each cell last finished
   unsigned long long wait_ns;  // limit of one dependency wait
@@ -205,7 +222,12 @@ int configure_phase(const RecLayout& lay, int tpc, int warps, int fmode);
 int probe_peaks(double* smem_gbs, double* fp64_gflops);
 size_t fused_smem_bytes(const RecLayout& lay, int fm);
 size_t fused_scratch_bytes(const RecLayout& lay);
-int configure_fused(const RecLayout& lay, int tpc, int fm, int iso, int* blocks_per_sm);
+// Chain-loop variant of the kernels: 0 axis chains reflected at walls and
+// frozen disks, 1 isotropic chains, 2 axis chains under the rejecting
+// boundary rule (a compile-time variant, so that the default loop carries
+// none of its bookkeeping).
+inline int chain_kind(const DevBufs& b) { return b.iso ? 1 : (b.reject ? 2 : 0); }
+int configure_fused(const RecLayout& lay, int tpc, int fm, int kind, int* blocks_per_sm);
 int launch_fused(const DevBufs& b, const RecLayout& lay, int tpc, int blocks, int records_on,
                  int precision, cudaStream_t s);
 int launch_sqrt_rn(const double* x, double* out, int64_t n, cudaStream_t s);

@@ -11,7 +11,7 @@ namespace ecmc {
 // FP64 coordinates are read and written in place in global memory (more
 // cells fit in shared memory at once); FMODE 2: the whole record is used in
 // place in global memory (cells too large for shared memory).
-template <int TPC, bool SCREEN, int FMODE, bool ISO = false>
+template <int TPC, bool SCREEN, int FMODE, int KIND = 0>
 __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
                                                const SweepState* __restrict__ sts,
                                                const int* __restrict__ act_rep, int colour_index,
@@ -80,12 +80,12 @@ __global__ void __launch_bounds__(256) k_phase(const Geom* __restrict__ rg,
   const int a = G * CPW + gi;  // global active cell of this lane group
   const bool valid = a < n_active;
   const int rep = valid ? act_rep[a] : act_rep[n_active - 1];
-  if constexpr (ISO)
+  if constexpr (KIND == 1)
     run_group_iso<TPC, SCREEN>(f, hdr, hs.P, rg, sts, rep, a, valid, colour_index, px, py, cs,
                                recs, rec_stride, err);
   else
-    run_group<TPC, SCREEN>(f, hs, hdr, rg, sts, rep, a, valid, colour_index, lay, px, py, cs,
-                           recs, rec_stride, replay, err);
+    run_group<TPC, SCREEN, KIND == 2>(f, hs, hdr, rg, sts, rep, a, valid, colour_index, lay, px,
+                                      py, cs, recs, rec_stride, replay, err);
 }
 
 size_t phase_smem_bytes(const RecLayout& lay, int warps_per_block, int fmode) {
@@ -103,19 +103,24 @@ static int launch_t(const DevBufs& b, const RecLayout& lay, int colour_index, in
   const int n_groups = (n_active + cpw - 1) / cpw;
   const int blocks = (n_groups + warps - 1) / warps;
   const size_t sm = phase_smem_bytes(lay, warps, b.fmode);
-#define ECMC_PHASE(FM, ISO)                                                                \
-  k_phase<TPC, SCREEN, FM, ISO><<<blocks, 32 * warps, sm, s>>>(                            \
+#define ECMC_PHASE(FM, KIND)                                                               \
+  k_phase<TPC, SCREEN, FM, KIND><<<blocks, 32 * warps, sm, s>>>(                           \
       b.rg, b.state, b.act_rep, colour_index, b.records, b.gtouch, lay, n_active,          \
       b.px[b.cur], b.py[b.cur], b.cell_stats, records_on ? b.chain_recs : nullptr,         \
       b.rec_stride, b.replay, b.err)
-  if (b.iso) {
-    if (b.fmode == 2) ECMC_PHASE(2, true);
-    else if (b.fmode == 1) ECMC_PHASE(1, true);
-    else ECMC_PHASE(0, true);
+  const int kind = chain_kind(b);
+  if (kind == 1) {
+    if (b.fmode == 2) ECMC_PHASE(2, 1);
+    else if (b.fmode == 1) ECMC_PHASE(1, 1);
+    else ECMC_PHASE(0, 1);
+  } else if (kind == 2) {
+    if (b.fmode == 2) ECMC_PHASE(2, 2);
+    else if (b.fmode == 1) ECMC_PHASE(1, 2);
+    else ECMC_PHASE(0, 2);
   } else {
-    if (b.fmode == 2) ECMC_PHASE(2, false);
-    else if (b.fmode == 1) ECMC_PHASE(1, false);
-    else ECMC_PHASE(0, false);
+    if (b.fmode == 2) ECMC_PHASE(2, 0);
+    else if (b.fmode == 1) ECMC_PHASE(1, 0);
+    else ECMC_PHASE(0, 0);
   }
 #undef ECMC_PHASE
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
@@ -149,8 +154,10 @@ template <int TPC, int FM>
 static int configure_t(size_t sm) {
   if (configure_fn(k_phase<TPC, true, FM>, sm)) return -1;
   if (configure_fn(k_phase<TPC, false, FM>, sm)) return -1;
-  if (configure_fn(k_phase<TPC, false, FM, true>, sm)) return -1;
-  if (configure_fn(k_phase<TPC, true, FM, true>, sm)) return -1;
+  if (configure_fn(k_phase<TPC, false, FM, 1>, sm)) return -1;
+  if (configure_fn(k_phase<TPC, true, FM, 1>, sm)) return -1;
+  if (configure_fn(k_phase<TPC, false, FM, 2>, sm)) return -1;
+  if (configure_fn(k_phase<TPC, true, FM, 2>, sm)) return -1;
   return 0;
 }
 

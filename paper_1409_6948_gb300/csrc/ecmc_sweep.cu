@@ -55,7 +55,7 @@ __host__ __device__ inline size_t fused_warp_bytes(const RecLayout& lay, int fm)
          fused_hist_bytes(lay) + build_aux_bytes(32);
 }
 
-template <int TPC, bool SCREEN, int FM, bool ISO = false>
+template <int TPC, bool SCREEN, int FM, int KIND = 0>
 __global__ void __launch_bounds__(32, 16) k_sweep_fused(
     const Geom* __restrict__ rg, const SweepState* __restrict__ sts,
     const int* __restrict__ act_rep, int n_active, int cap, double* __restrict__ px,
@@ -202,12 +202,12 @@ __global__ void __launch_bounds__(32, 16) k_sweep_fused(
     __syncwarp();
 
     __syncwarp();
-    if constexpr (ISO)
+    if constexpr (KIND == 1)
       run_group_iso<TPC, SCREEN>(f, hdr, hs.P, rg, sts, rep, a, valid, ci, px, py, cs, recs,
                                  rec_stride, err);
     else
-      run_group<TPC, SCREEN>(f, hs, hdr, rg, sts, rep, a, valid, ci, lay, px, py, cs, recs,
-                             rec_stride, replay, err);
+      run_group<TPC, SCREEN, KIND == 2>(f, hs, hdr, rg, sts, rep, a, valid, ci, lay, px, py,
+                                        cs, recs, rec_stride, replay, err);
 
     // publish: every lane's write-back is visible before the cell is marked
     __threadfence();
@@ -224,15 +224,15 @@ __global__ void __launch_bounds__(32, 16) k_sweep_fused(
 size_t fused_smem_bytes(const RecLayout& lay, int fm) { return fused_warp_bytes(lay, fm); }
 size_t fused_scratch_bytes(const RecLayout& lay) { return fused_fp64_bytes(lay); }
 
-template <int TPC, int FM, bool ISO>
+template <int TPC, int FM, int KIND>
 static int configure_fused_t(size_t sm, int* blocks_per_sm) {
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return -1;
   int nb0 = 0, nb1 = 0;
-  auto k0 = k_sweep_fused<TPC, false, FM, ISO>;
-  auto k1 = k_sweep_fused<TPC, true, FM, ISO>;
+  auto k0 = k_sweep_fused<TPC, false, FM, KIND>;
+  auto k1 = k_sweep_fused<TPC, true, FM, KIND>;
   cudaFuncAttributes fa0, fa1;
   if (cudaFuncGetAttributes(&fa0, k0) != cudaSuccess ||
       cudaFuncGetAttributes(&fa1, k1) != cudaSuccess)
@@ -249,13 +249,14 @@ static int configure_fused_t(size_t sm, int* blocks_per_sm) {
   return *blocks_per_sm > 0 ? 0 : -1;
 }
 
-int configure_fused(const RecLayout& lay, int tpc, int fm, int iso, int* blocks_per_sm) {
+int configure_fused(const RecLayout& lay, int tpc, int fm, int kind, int* blocks_per_sm) {
   const size_t sm = fused_smem_bytes(lay, fm);
 #define ECMC_FCFG(T)                                                             \
   case T:                                                                        \
-    return iso ? configure_fused_t<T, 0, true>(sm, blocks_per_sm)                \
-               : (fm == 1 ? configure_fused_t<T, 1, false>(sm, blocks_per_sm)    \
-                          : configure_fused_t<T, 0, false>(sm, blocks_per_sm));
+    return kind == 1   ? configure_fused_t<T, 0, 1>(sm, blocks_per_sm)           \
+           : kind == 2 ? configure_fused_t<T, 0, 2>(sm, blocks_per_sm)           \
+           : (fm == 1 ? configure_fused_t<T, 1, 0>(sm, blocks_per_sm)            \
+                      : configure_fused_t<T, 0, 0>(sm, blocks_per_sm));
   switch (tpc) {
     ECMC_FCFG(1)
     ECMC_FCFG(2)
@@ -268,10 +269,10 @@ int configure_fused(const RecLayout& lay, int tpc, int fm, int iso, int* blocks_
 #undef ECMC_FCFG
 }
 
-template <int TPC, bool SCREEN, int FM, bool ISO = false>
+template <int TPC, bool SCREEN, int FM, int KIND = 0>
 static int launch_fused_t(const DevBufs& b, const RecLayout& lay, int blocks, int records_on,
                           cudaStream_t s) {
-  k_sweep_fused<TPC, SCREEN, FM, ISO><<<blocks, 32, fused_smem_bytes(lay, FM), s>>>(
+  k_sweep_fused<TPC, SCREEN, FM, KIND><<<blocks, 32, fused_smem_bytes(lay, FM), s>>>(
       b.rg, b.state, b.act_rep, b.A_total, b.cap, b.px[b.cur], b.py[b.cur], b.pid[b.cur],
       b.count[b.cur], lay, b.cell_stats, records_on ? b.chain_recs : nullptr, b.rec_stride,
       b.replay, b.sched, b.done, b.wait_ns, b.wait_test, b.records, b.err);
@@ -284,8 +285,11 @@ int launch_fused(const DevBufs& b, const RecLayout& lay, int tpc, int blocks, in
 #define ECMC_FCASE(T)                                                                      \
   case T:                                                                                  \
     if (b.iso)                                                                             \
-      return scr ? launch_fused_t<T, true, 0, true>(b, lay, blocks, records_on, s)         \
-                 : launch_fused_t<T, false, 0, true>(b, lay, blocks, records_on, s);       \
+      return scr ? launch_fused_t<T, true, 0, 1>(b, lay, blocks, records_on, s)            \
+                 : launch_fused_t<T, false, 0, 1>(b, lay, blocks, records_on, s);          \
+    if (b.reject)                                                                          \
+      return scr ? launch_fused_t<T, true, 0, 2>(b, lay, blocks, records_on, s)            \
+                 : launch_fused_t<T, false, 0, 2>(b, lay, blocks, records_on, s);          \
     return scr ? (b.fmode == 1 ? launch_fused_t<T, true, 1>(b, lay, blocks, records_on, s)    \
                                : launch_fused_t<T, true, 0>(b, lay, blocks, records_on, s))   \
                : (b.fmode == 1 ? launch_fused_t<T, false, 1>(b, lay, blocks, records_on, s)   \

@@ -38,6 +38,10 @@ PARAM_WAIT_LIMIT_MS = 16
 PARAM_WAIT_TEST = 17
 PARAM_KERNELS_PER_SWEEP = 18
 PARAM_LIST_MODE = 19
+PARAM_CHAINS_IN_FLIGHT = 20
+PARAM_BOUNDARY = 21
+BOUNDARY_REFLECT = 0
+BOUNDARY_REJECT = 1
 LIST_WITH_REPL = 0
 LIST_WITHOUT_REPL = 1
 
@@ -52,7 +56,7 @@ class Counters(C.Structure):
     _fields_ = [("sweeps", C.c_int64), ("chains", C.c_int64), ("events", C.c_int64),
                 ("lifts", C.c_int64), ("frozen_hits", C.c_int64), ("wall_hits", C.c_int64),
                 ("fp64_evals", C.c_int64), ("sum_b", C.c_double), ("sum_disp", C.c_double),
-                ("replayed_legs", C.c_int64)]
+                ("replayed_legs", C.c_int64), ("rejected_chains", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

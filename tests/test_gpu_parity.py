@@ -30,7 +30,7 @@ LAST = {}  # counters of the most recent run_pair, for tests that inspect them
 
 
 def make(N, eta, cells_x, cells_y, ell, nm, seed, tpc=0, prec=1, dir_mode=0, records=False,
-         replica=0, fmode=-1, persistent=1, list_mode=0):
+         replica=0, fmode=-1, persistent=1, list_mode=0, boundary=0):
     L = W.box_side(N, eta)
     g = P.Ecmc(N, L, 1.0, cells_x, cells_y, ell, seed)
     g.set_param(E.PARAM_N_CHAINS, nm)
@@ -43,10 +43,12 @@ def make(N, eta, cells_x, cells_y, ell, nm, seed, tpc=0, prec=1, dir_mode=0, rec
         g.set_param(E.PARAM_FRAME_MODE, fmode)
     g.set_param(E.PARAM_PERSISTENT, persistent)
     g.set_param(E.PARAM_LIST_MODE, list_mode)
+    if boundary:
+        g.set_param(E.PARAM_BOUNDARY, boundary)
     if records:
         g.set_param(E.PARAM_RECORD_CHAINS, 1)
     p = oracle.make_params(N, L, 1.0, cells_x, cells_y, ell, nm, seed, replica,
-                           dir_mode=dir_mode, list_mode=list_mode)
+                           dir_mode=dir_mode, list_mode=list_mode, boundary=boundary)
     return g, p, L
 
 
@@ -86,7 +88,10 @@ def run_pair(N, eta, cells_x, cells_y, ell, nm, seed, n_sweeps, records=True, **
     assert c.events == st_total.events and c.lifts == st_total.lifts
     assert c.frozen_hits == st_total.frozen_hits and c.wall_hits == st_total.wall_hits
     assert c.chains == st_total.chains and c.sweeps == n_sweeps
+    assert c.rejected_chains == st_total.rejected
     assert c.sum_b == pytest.approx(st_total.sum_b, rel=1e-11, abs=1e-12)
+    # the oracle adds ell chain by chain, the library multiplies a count by ell
+    assert c.sum_disp == pytest.approx(st_total.sum_disp, rel=1e-11)
     if st_total.sum_disp_w > 0:
         P_gpu, _ = g.pressure()
         rho = N / L**2

@@ -47,11 +47,11 @@ def test_exact_distribution_matches_rejection_sampling():
 
 
 def sample_z(L, ell, nm, n_sweeps, list_mode=oracle.LIST_WITH_REPL,
-             dir_mode=oracle.DIR_PM_AXIS_ALT, flags=0, seed=7):
+             dir_mode=oracle.DIR_PM_AXIS_ALT, flags=0, seed=7, boundary=oracle.BOUNDARY_REFLECT):
     x = np.array([0.3, 1.6, 2.9])
     y = np.array([0.4, 2.2, 1.0])
     p = oracle.make_params(3, L, 1.0, 2, 2, ell, nm, seed, 0, dir_mode=dir_mode,
-                           list_mode=list_mode, flags=flags)
+                           list_mode=list_mode, flags=flags, boundary=boundary)
     oracle.sweeps(p, x, y, 0, 100)
     st, sx, sy = oracle.sweeps_snap(p, x, y, 100, n_sweeps)
 
