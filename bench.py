@@ -69,6 +69,9 @@ def parse():
                     help="most sweeps per point of the --tau experiment")
     ap.add_argument("--listbias", action="store_true",
                     help="pressure vs n_m with start lists drawn with and without replacement")
+    ap.add_argument("--fig3", action="store_true",
+                    help="g(r) near contact and P(g(sigma+)) vs n_m: reflecting and rejecting "
+                         "boundary rules, start lists with and without replacement")
     ap.add_argument("--grid", action="store_true",
                     help="parallelisation grid at N = 1M (cells x ell), one JSON line")
     ap.add_argument("--paper-params", action="store_true",
@@ -346,6 +349,99 @@ def run_listbias(args):
         d = pw[1]["betaP_sigma2"] - pw[0]["betaP_sigma2"]
         pw[1]["difference_in_combined_se"] = d / math.hypot(pw[0]["stderr"], pw[1]["stderr"])
     print(json.dumps({"mode": "list_bias", "workload": "N=65536 eta=0.708 cells=32x32 ell=8",
+                      "points": pts}))
+    return 0
+
+
+def contact_value(r, g, sigma=1.0, nfit=5):
+    """g(sigma+) from a quadratic least-squares fit over the first nfit bins,
+    evaluated at sigma (the contact extrapolation of the pressure route)."""
+    return float(np.polyfit(r[:nfit] - sigma, g[:nfit], 2)[-1])
+
+
+def run_fig3(args):
+    """The comparison of Sec. 3.4, Fig. 3: pair correlations near contact and
+    the pressure read from g(sigma+) (eq. pressure) against the number n_m of
+    chains per cell, for N = 256^2 disks at eta = 0.708 in 32 x 32 cells.
+    Rules: reflection at walls and frozen disks (PEC-refl, ell = 8 sigma) and
+    rejection of the whole chain (PEC-rej, ell = 0.25 sigma: a chain's front
+    advances about beta P / rho ~ 11 times its budget, so longer chains
+    rarely stay inside an 8.4 sigma cell); each with start lists drawn with
+    replacement and shuffled.  Every point starts from one configuration
+    melted by the paper's algorithm, equilibrates for S / (4 n_m) sweeps and
+    measures g(r) every 10 sweeps over S / n_m sweeps, the same number of
+    chains for every n_m.  Error bars from 8 batches."""
+    import torch
+
+    import paper_1409_6948_gb300 as P
+    from paper_1409_6948_gb300 import ecmc as E
+
+    torch.cuda.set_device(0)
+    w = W.MEDIUM
+    N, L = w.N, w.L
+    rho = N / (L * L)
+    dr, rmax, nbatch = 0.01, 1.5, 8
+    g0 = P.Ecmc(N, L, 1.0, w.cells, w.cells, w.ell, w.seed)
+    g0.set_param(E.PARAM_N_CHAINS, 4)
+    g0.sweep(2000)
+    xy0 = g0.positions().copy()
+    t0 = g0.sweep_index()
+    g0.close()
+    nb = int(round((rmax - 1.0) / dr))
+    e0 = 1.0 + dr * np.arange(nb)
+    e1 = e0 + dr
+    R = 2.0 * (e1**3 - e0**3) / (3.0 * (e1**2 - e0**2))
+    norm = N * rho * 2.0 * math.pi * R * dr
+    pts = []
+    for rule, ell, S in (("reflect", 8.0, 8000), ("reject", 0.25, 32000)):
+        for nm in (1, 2, 4, 8, 16):
+            for mode in (E.LIST_WITH_REPL, E.LIST_WITHOUT_REPL):
+                g = P.Ecmc(N, L, 1.0, w.cells, w.cells, ell, w.seed + 1)
+                g.set_param(E.PARAM_N_CHAINS, nm)
+                g.set_param(E.PARAM_LIST_MODE, mode)
+                if rule == "reject":
+                    g.set_param(E.PARAM_BOUNDARY, E.BOUNDARY_REJECT)
+                g.set_param(E.PARAM_GR_DR, dr)
+                g.set_param(E.PARAM_GR_RMAX, rmax)
+                g.set_positions(xy0, t0=t0)
+                g.sweep(max(1, S // (4 * nm)))
+                g.reset_stats()
+                per_batch = max(1, S // nm // nbatch // 10)
+                prev = np.zeros(nb)
+                prev_n = 0
+                gs, ps = [], []
+                for _ in range(nbatch):
+                    for _ in range(per_batch):
+                        g.sweep(10)
+                        g.gr_measure()
+                    cnt, nmeas = g.gr_counts()
+                    cnt = cnt[:nb].astype(float)
+                    gb = ((cnt - prev) / (nmeas - prev_n)) / norm
+                    prev, prev_n = cnt, nmeas
+                    gs.append(gb)
+                    gc = contact_value(R, gb)
+                    ps.append(rho * (1.0 + 0.5 * math.pi * rho * gc))
+                gm = np.mean(gs, 0)
+                c = g.counters()
+                pt = {"rule": rule, "ell": ell, "n_m": nm,
+                      "list": "with replacement" if mode == 0 else "shuffled",
+                      "betaP_sigma2_gcontact": float(np.mean(ps)),
+                      "stderr": float(np.std(ps, ddof=1) / math.sqrt(nbatch)),
+                      "g_contact": contact_value(R, gm),
+                      "g_first_bins": [round(float(v), 4) for v in gm[:12]],
+                      "sweeps": per_batch * nbatch * 10,
+                      "rejected_fraction": c.rejected_chains / max(c.chains, 1)}
+                if rule == "reflect":
+                    pt["betaP_sigma2_chain"] = g.pressure()[0]
+                pts.append(pt)
+                g.close()
+                print(json.dumps(pt), flush=True)
+    for rule in ("reflect", "reject"):
+        for nm in (1, 2, 4, 8, 16):
+            pw = [q for q in pts if q["n_m"] == nm and q["rule"] == rule]
+            d = pw[1]["betaP_sigma2_gcontact"] - pw[0]["betaP_sigma2_gcontact"]
+            pw[1]["difference_in_combined_se"] = d / math.hypot(pw[0]["stderr"], pw[1]["stderr"])
+    print(json.dumps({"mode": "fig3", "workload": "N=65536 eta=0.708 cells=32x32",
                       "points": pts}))
     return 0
 
@@ -796,6 +892,8 @@ def main():
         return run_grid(args)
     if args.listbias:
         return run_listbias(args)
+    if args.fig3:
+        return run_fig3(args)
     if args.tau:
         return run_tau(args)
     return run_ours(args)
