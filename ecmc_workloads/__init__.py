@@ -20,6 +20,26 @@ def box_side(N: int, eta: float, sigma: float = 1.0) -> float:
     return sigma * math.sqrt(N * math.pi / (4.0 * eta))
 
 
+def box_side3(N: int, eta: float, sigma: float = 1.0) -> float:
+    """Hard spheres: L = sigma (N pi / (6 eta))^(1/3), from
+    eta = N pi sigma^3 / (6 L^3)."""
+    return sigma * (N * math.pi / (6.0 * eta)) ** (1.0 / 3.0)
+
+
+def cubic_lattice(N: int, L: float):
+    """k x k x k simple cubic lattice, k = N^(1/3): sphere (iz*k + iy)*k + ix
+    sits at ((ix + 1/2) a, (iy + 1/2) a, (iz + 1/2) a) with a = L / k."""
+    k = int(round(N ** (1.0 / 3.0)))
+    if k * k * k != N:
+        raise ValueError("N=%d is not a perfect cube" % N)
+    a = L / k
+    i = np.arange(N, dtype=np.int64)
+    x = ((i % k).astype(np.float64) + 0.5) * a
+    y = (((i // k) % k).astype(np.float64) + 0.5) * a
+    z = ((i // (k * k)).astype(np.float64) + 0.5) * a
+    return np.ascontiguousarray(x), np.ascontiguousarray(y), np.ascontiguousarray(z)
+
+
 def packing_fraction(N: int, L: float, sigma: float = 1.0) -> float:
     return N * math.pi * sigma * sigma / (4.0 * L * L)
 

@@ -37,6 +37,12 @@ class Params(C.Structure):
                 ("boundary", C.c_int)]
 
 
+class Params3(C.Structure):
+    _fields_ = [("N", C.c_int64), ("L", C.c_double), ("sigma", C.c_double),
+                ("cells", C.c_int), ("ell", C.c_double), ("n_m", C.c_int),
+                ("seed", C.c_uint64), ("replica", C.c_uint64), ("flags", C.c_uint)]
+
+
 class Stats(C.Structure):
     _fields_ = [("sweeps", C.c_int64), ("chains", C.c_int64), ("events", C.c_int64),
                 ("lifts", C.c_int64), ("frozen_hits", C.c_int64), ("wall_hits", C.c_int64),
@@ -88,6 +94,20 @@ def lib():
         L.orc_hexatic.argtypes = [i64, C.c_double, d, d, C.c_double, C.c_void_p, C.c_void_p,
                                   C.c_void_p]
         L.orc_hexatic.restype = C.c_int
+        P3 = C.POINTER(Params3)
+        L.orc3_sweep_draws.argtypes = [P3, i64, d, C.POINTER(C.c_int)]
+        L.orc3_sweep_draws.restype = None
+        L.orc3_bin.argtypes = [P3, i64, d, d, d, C.POINTER(C.c_int32)]
+        L.orc3_bin.restype = C.c_int
+        L.orc3_sweeps.argtypes = [P3, d, d, d, i64, i64, C.POINTER(Stats), C.c_void_p]
+        L.orc3_sweeps.restype = C.c_int
+        L.orc3_run_chain_frame.argtypes = [C.c_int, C.c_int, d, d, d, C.POINTER(C.c_int64),
+                                           C.POINTER(C.c_int32), C.c_double, C.c_double,
+                                           C.c_int, C.c_int, C.c_int, C.c_double,
+                                           C.POINTER(Stats), C.c_void_p]
+        L.orc3_run_chain_frame.restype = C.c_int
+        L.orc3_min_dist2.argtypes = [i64, C.c_double, d, d, d, C.c_double]
+        L.orc3_min_dist2.restype = C.c_double
         _lib = L
     return _lib
 
@@ -246,3 +266,74 @@ def pressure_from_gcontact(g_contact, N, L, sigma):
     """eq. (pressure): beta P sigma^2 = sigma^2 rho (1 + pi/2 sigma^2 rho g(sigma+))."""
     rho = N / (L * L)
     return sigma * sigma * rho * (1.0 + 0.5 * math.pi * sigma * sigma * rho * g_contact)
+
+
+# ---- three dimensions ------------------------------------------------------
+
+def make_params3(N, L, sigma, cells, ell, n_m, seed, replica=0, flags=0):
+    return Params3(int(N), float(L), float(sigma), int(cells), float(ell), int(n_m), int(seed),
+                   int(replica), int(flags))
+
+
+def sweep_draws3(p, t):
+    sh = (C.c_double * 3)()
+    perm = (C.c_int * 8)()
+    lib().orc3_sweep_draws(C.byref(p), int(t), sh, perm)
+    return list(sh), list(perm)
+
+
+def bin_cells3(p, t, x, y, z):
+    cell = np.empty(p.N, np.int32)
+    rc = lib().orc3_bin(C.byref(p), int(t), _dptr(x), _dptr(y), _dptr(z),
+                        cell.ctypes.data_as(C.POINTER(C.c_int32)))
+    if rc != 0:
+        raise ValueError("oracle rejected the parameters")
+    return cell
+
+
+def sweeps3(p, x, y, z, t0, n_sweeps, stats=None, records=False):
+    """Three-dimensional sweeps in place on x, y, z (float64, id order).
+    Returns (stats, records [n_sweeps, cells^3, n_m] or None)."""
+    st = stats if stats is not None else Stats()
+    recs = None
+    rp = None
+    if records:
+        recs = np.zeros((n_sweeps, p.cells ** 3, p.n_m), CHAIN_REC)
+        rp = recs.ctypes.data_as(C.c_void_p)
+    rc = lib().orc3_sweeps(C.byref(p), _dptr(x), _dptr(y), _dptr(z), int(t0), int(n_sweeps),
+                           C.byref(st), rp)
+    if rc != 0:
+        raise ValueError("oracle rejected the parameters (rc=%d)" % rc)
+    return st, recs
+
+
+def run_chain_frame3(X, Y, Z, n_mem, m, axis, sign, ell, w, sigma=1.0, ids=None, imgs=None):
+    """One three-dimensional chain on an explicit frame; returns
+    (X, Y, Z, stats, record)."""
+    X = np.ascontiguousarray(X, dtype=np.float64).copy()
+    Y = np.ascontiguousarray(Y, dtype=np.float64).copy()
+    Z = np.ascontiguousarray(Z, dtype=np.float64).copy()
+    n = X.shape[0]
+    ids = np.arange(n, dtype=np.int64) if ids is None else np.asarray(ids, np.int64)
+    imgs = np.full(n, 13, np.int32) if imgs is None else np.asarray(imgs, np.int32)
+    st = Stats()
+    rec = np.zeros(1, CHAIN_REC)
+    rc = lib().orc3_run_chain_frame(n, int(n_mem), _dptr(X), _dptr(Y), _dptr(Z),
+                                    ids.ctypes.data_as(C.POINTER(C.c_int64)),
+                                    imgs.ctypes.data_as(C.POINTER(C.c_int32)), float(w),
+                                    float(sigma), int(m), int(axis), int(sign), float(ell),
+                                    C.byref(st), rec.ctypes.data_as(C.c_void_p))
+    if rc != 0:
+        raise ValueError("bad frame")
+    return X, Y, Z, st, rec[0]
+
+
+def min_dist2_3(L, x, y, z, rcut=2.0):
+    return lib().orc3_min_dist2(int(x.shape[0]), float(L), _dptr(x), _dptr(y), _dptr(z),
+                                float(rcut))
+
+
+def pressure_from_sums3(sum_b_w, sum_disp_w, N, L, sigma):
+    """beta P sigma^3 = rho sigma^3 (1 + sum_b_w / sum_disp_w)."""
+    rho = N / L**3
+    return rho * sigma**3 * (1.0 + sum_b_w / sum_disp_w)

@@ -1,11 +1,13 @@
 """GB300 (sm_103a) parallel event-chain Monte Carlo for two-dimensional hard
-disks (Kampmann, Boltz, Kierfeld, arXiv:1409.6948).
+disks and three-dimensional hard spheres (Kampmann, Boltz, Kierfeld,
+arXiv:1409.6948).
 
 The computation lives in the CUDA library libecmc.so (C ABI in
-include/ecmc.h); this package only loads it and marshals arguments.
+include/ecmc.h and include/ecmc3.h); this package only loads it and marshals
+arguments.
 """
-from .ecmc import (DIR_PM_AXIS_ALT, DIR_POS_ONLY, PREC_FP32_GEOM, PREC_FP64, Ecmc, EcmcError,
-                   load, version)
+from .ecmc import (DIR_PM_AXIS_ALT, DIR_POS_ONLY, PREC_FP32_GEOM, PREC_FP64, Ecmc, Ecmc3,
+                   EcmcError, load, version)
 
-__all__ = ["Ecmc", "EcmcError", "load", "version", "DIR_PM_AXIS_ALT", "DIR_POS_ONLY",
+__all__ = ["Ecmc", "Ecmc3", "EcmcError", "load", "version", "DIR_PM_AXIS_ALT", "DIR_POS_ONLY",
            "PREC_FP64", "PREC_FP32_GEOM"]

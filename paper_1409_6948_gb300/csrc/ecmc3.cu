@@ -1,0 +1,942 @@
+// ecmc3.cu -- the parallel event-chain sweep for hard spheres in three
+// dimensions (the generalisation of Sec. 3.4 to cubic cells in 2x2x2 blocks;
+// interface and readings in ecmc3.h).
+//
+// Per sweep: k3_begin (draws), k3_bin (bucket every sphere by cell), eight
+// launches of k3_phase (one colour each) and k3_end (deterministic sums).
+// k3_phase gives one warp to one active cell: the warp sorts the cell's
+// members by id, gathers the members and every periodic image of the 26
+// neighbour cells' spheres within sigma of the cell into a shared-memory
+// frame, then runs the cell's n_m chains.  Each event is one warp-wide pass
+// over the frame: 32 lanes test candidates in FP64 with the oracle's
+// expressions (no contraction: the library is built with -fmad=false), and a
+// shuffle reduction picks the first hit by (distance, key).  Positions live
+// in sphere-id order; a cell reads its frozen neighbours' positions, which
+// no other warp of the same launch writes.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <climits>
+#include <vector>
+
+#include "ecmc.h"
+#include "ecmc3.h"
+#include "ecmc_device.cuh"
+#include "ecmc_internal.cuh"
+
+namespace ecmc3 {
+
+using ecmc::U64x4;
+using ecmc::below_n;
+using ecmc::cell_1d;
+using ecmc::philox;
+using ecmc::unit_double;
+using ecmc::wrap_box0;
+using ecmc::wrap_half;
+
+constexpr int kOk = 0, kCapacity = 1, kChainCap = 2;
+constexpr int kWarpsMax = 4;
+constexpr int kHistoryCap = 1 << 20;  // sweeps of pressure history kept
+
+struct Geom3 {
+  int64_t N;
+  double L, sigma, sig2, w, inv_w, ell;
+  int cells, ncell, nact, n_m;
+  uint64_t seed, replica;
+  int cap_mem, cap_obj;  // bucket slots per cell; frame objects per cell
+  int warp_bytes;        // shared memory of one warp's frame
+};
+
+struct State3 {
+  int64_t t;
+  int axis;
+  int perm[8];
+  double s[3];
+};
+
+struct Cell3 {
+  double sum_b;
+  int events, lifts, frozen, walls, chains, n_mem;
+};
+
+struct Totals3 {
+  double sum_b, sum_disp, sum_b_w, sum_disp_w;
+  long long sweeps, chains, events, lifts, frozen, walls;
+};
+
+// ---- kernels ----------------------------------------------------------------
+
+__global__ void k3_begin(Geom3 g, State3* st) {
+  if (threadIdx.x != 0) return;
+  State3 s = *st;
+  const U64x4 u = philox((uint64_t)s.t, ecmc::kPurposeSweep, 0, 0, g.seed, g.replica);
+  for (int a = 0; a < 3; ++a) s.s[a] = unit_double(u.v[a]) * g.w;
+  // colour order: permutation number floor(u3 * 8! / 2^64) of 0..7 in
+  // lexicographic order, decoded from its factorial-base digits
+  int code = (int)below_n(u.v[3], 40320);
+  int pool[8] = {0, 1, 2, 3, 4, 5, 6, 7};
+  const int radix[8] = {5040, 720, 120, 24, 6, 2, 1, 1};
+  int left = 8;
+  for (int i = 0; i < 8; ++i) {
+    const int d = code / radix[i];
+    code -= d * radix[i];
+    s.perm[i] = pool[d];
+    for (int j = d; j < left - 1; ++j) pool[j] = pool[j + 1];
+    --left;
+  }
+  s.axis = (int)(s.t % 3);
+  *st = s;
+}
+
+__global__ void k3_bin(Geom3 g, const State3* __restrict__ st, const double* __restrict__ px,
+                       const double* __restrict__ py, const double* __restrict__ pz,
+                       int* __restrict__ cnt, int* __restrict__ ids, int* __restrict__ cell_of,
+                       int* err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.N) return;
+  const State3 s = *st;
+  const int cx = cell_1d(px[i], s.s[0], g.L, g.inv_w, g.cells);
+  const int cy = cell_1d(py[i], s.s[1], g.L, g.inv_w, g.cells);
+  const int cz = cell_1d(pz[i], s.s[2], g.L, g.inv_w, g.cells);
+  const int c = (cz * g.cells + cy) * g.cells + cx;
+  cell_of[i] = c;
+  const int slot = atomicAdd(&cnt[c], 1);
+  if (slot < g.cap_mem) ids[(int64_t)c * g.cap_mem + slot] = (int)i;
+  else atomicCAS(err, kOk, kCapacity);
+}
+
+__device__ __forceinline__ bool first_before(double s, long long k, double bs, long long bk) {
+  return s < bs || (s == bs && k < bk);
+}
+
+__global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
+    Geom3 g, const State3* __restrict__ stp, int colour_index, double* __restrict__ px,
+    double* __restrict__ py, double* __restrict__ pz, const int* __restrict__ cnt,
+    const int* __restrict__ ids, Cell3* __restrict__ cs, int* __restrict__ recs, int* err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr unsigned FULL = 0xffffffffu;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int a = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (a >= g.nact) return;  // warp-uniform
+  const State3 st = *stp;
+  const int colour = st.perm[colour_index];
+  const int hx = g.cells >> 1, nc = g.cells;
+  const int cx = 2 * (a % hx) + (colour & 1);
+  const int cy = 2 * ((a / hx) % hx) + ((colour >> 1) & 1);
+  const int cz = 2 * (a / (hx * hx)) + (colour >> 2);
+  const int c = (cz * nc + cy) * nc + cx;
+  const double L = g.L, w = g.w;
+  const double o[3] = {st.s[0] + (double)cx * w, st.s[1] + (double)cy * w,
+                       st.s[2] + (double)cz * w};
+
+  unsigned char* base = smem + (size_t)warp * g.warp_bytes;
+  double* C[3];
+  C[0] = reinterpret_cast<double*>(base);
+  C[1] = C[0] + g.cap_obj;
+  C[2] = C[1] + g.cap_obj;
+  long long* key = reinterpret_cast<long long*>(C[2] + g.cap_obj);
+  int* sid = reinterpret_cast<int*>(key + g.cap_obj);  // members sorted by id
+  int* raw = sid + g.cap_mem;                           // members as bucketed
+  int* nbl = raw + g.cap_mem;                           // 26 neighbour cells + count
+  unsigned char* touched = reinterpret_cast<unsigned char*>(nbl + 28);
+
+  const int nmem = min(cnt[c], g.cap_mem);
+  for (int k = lane; k < nmem; k += 32) raw[k] = ids[(int64_t)c * g.cap_mem + k];
+  if (lane == 0) {
+    // the distinct neighbour cells (with two cells per side the cells at
+    // offsets -1 and +1 coincide)
+    int n = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int qx = (cx + dx + nc) % nc, qy = (cy + dy + nc) % nc, qz = (cz + dz + nc) % nc;
+          const int q = (qz * nc + qy) * nc + qx;
+          if (q == c) continue;
+          bool dup = false;
+          for (int e = 0; e < n; ++e) dup |= nbl[e] == q;
+          if (!dup) nbl[n++] = q;
+        }
+    nbl[26] = n;
+  }
+  __syncwarp();
+  // members in ascending id: the rank of each is the number of smaller ids
+  for (int k = lane; k < nmem; k += 32) {
+    const int v = raw[k];
+    int r = 0;
+    for (int j = 0; j < nmem; ++j) r += raw[j] < v ? 1 : 0;
+    sid[r] = v;
+    touched[r] = 0;
+  }
+  __syncwarp();
+  for (int q = lane; q < nmem; q += 32) {
+    const int i = sid[q];
+    C[0][q] = wrap_half(px[i] - o[0], L);
+    C[1][q] = wrap_half(py[i] - o[1], L);
+    C[2][q] = wrap_half(pz[i] - o[2], L);
+    key[q] = (long long)i * 27 + 13;
+  }
+  // frozen images, appended in lane order (warp prefix sums)
+  int nobj = nmem;
+  const int nnb = nbl[26];
+  const double lo = -g.sigma, hi = w + g.sigma;
+  for (int e = 0; e < nnb; ++e) {
+    const int q = nbl[e];
+    const int nq = min(cnt[q], g.cap_mem);
+    for (int k0 = 0; k0 < nq; k0 += 32) {
+      const int k = k0 + lane;
+      double X0[3] = {0.0, 0.0, 0.0};
+      int id = 0;
+      unsigned mask = 0u;  // bit img = (kx+1)*9 + (ky+1)*3 + (kz+1)
+      if (k < nq) {
+        id = ids[(int64_t)q * g.cap_mem + k];
+        X0[0] = wrap_half(px[id] - o[0], L);
+        X0[1] = wrap_half(py[id] - o[1], L);
+        X0[2] = wrap_half(pz[id] - o[2], L);
+        for (int kx = -1; kx <= 1; ++kx) {
+          const double X = X0[0] + (double)kx * L;
+          if (!(X > lo && X < hi)) continue;
+          for (int ky = -1; ky <= 1; ++ky) {
+            const double Y = X0[1] + (double)ky * L;
+            if (!(Y > lo && Y < hi)) continue;
+            for (int kz = -1; kz <= 1; ++kz) {
+              const double Z = X0[2] + (double)kz * L;
+              if (!(Z > lo && Z < hi)) continue;
+              mask |= 1u << ((kx + 1) * 9 + (ky + 1) * 3 + (kz + 1));
+            }
+          }
+        }
+      }
+      const int nimg = __popc(mask);
+      int incl = nimg;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(FULL, incl, off);
+        if (lane >= off) incl += v;
+      }
+      int slot = nobj + incl - nimg;
+      while (mask) {
+        const int img = __ffs(mask) - 1;
+        mask &= mask - 1;
+        if (slot < g.cap_obj) {
+          const int kx = img / 9 - 1, ky = (img / 3) % 3 - 1, kz = img % 3 - 1;
+          C[0][slot] = X0[0] + (double)kx * L;
+          C[1][slot] = X0[1] + (double)ky * L;
+          C[2][slot] = X0[2] + (double)kz * L;
+          key[slot] = (long long)id * 27 + img;
+        }
+        ++slot;
+      }
+      nobj += __shfl_sync(FULL, incl, 31);
+    }
+  }
+  const bool ok = nobj <= g.cap_obj;
+  if (!ok && lane == 0) atomicCAS(err, kOk, kCapacity);
+  __syncwarp();
+
+  // the cell's chains
+  const int ax = st.axis;
+  double* CA = C[ax];
+  double* CP = C[ax == 0 ? 1 : 0];
+  double* CQ = C[ax == 2 ? 1 : 2];
+  const double INF = __longlong_as_double(0x7ff0000000000000ll);
+  double sum_b = 0.0;
+  int n_ev = 0, n_li = 0, n_fr = 0, n_wa = 0, n_ch = 0;
+  for (int k = 0; k < g.n_m; ++k) {
+    int* rec = recs != nullptr ? recs + 4 * ((int64_t)c * g.n_m + k) : nullptr;
+    if (!ok || nmem == 0) {
+      if (rec != nullptr && lane == 0) {
+        rec[0] = -1;
+        rec[1] = -1;
+        rec[2] = 0;
+        rec[3] = 0;
+      }
+      continue;
+    }
+    const U64x4 v = philox((uint64_t)st.t, ecmc::kPurposeChain, (uint64_t)c, (uint64_t)k,
+                           g.seed, g.replica);
+    int m = (int)below_n(v.v[0], (uint64_t)nmem);
+    int sg = (v.v[1] >> 63) ? -1 : 1;
+    const int start_id = sid[m];
+    double r = g.ell;
+    int ch_ev = 0, ch_wa = 0;
+    if (lane == 0) touched[m] = 1;
+    ++n_ch;
+    for (int64_t iter = 0;; ++iter) {
+      if (iter >= ecmc::kMaxEventsPerChain) {
+        if (lane == 0) atomicCAS(err, kOk, kChainCap);
+        break;
+      }
+      __syncwarp();
+      const double P = CA[m], Pp = CP[m], Pq = CQ[m];
+      double sw = sg > 0 ? w - P : P;
+      if (sw < 0.0) sw = 0.0;
+      double bs = INF, bb = 0.0;
+      long long bk = LLONG_MAX;
+      int bj = -1;
+      for (int j = lane; j < nobj; j += 32) {
+        if (j == m) continue;
+        const double da = CA[j] - P;
+        const double b = sg > 0 ? da : -da;
+        if (!(b > 0.0)) continue;
+        const double dp = CP[j] - Pp;
+        const double dq = CQ[j] - Pq;
+        const double c2 = dp * dp + dq * dq;
+        if (!(c2 < g.sig2)) continue;
+        double s = b - sqrt(g.sig2 - c2);
+        if (s < 0.0) s = 0.0;
+        const long long kj = key[j];
+        if (first_before(s, kj, bs, bk)) {
+          bs = s;
+          bb = b;
+          bk = kj;
+          bj = j;
+        }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const double os = __shfl_xor_sync(FULL, bs, off);
+        const double ob = __shfl_xor_sync(FULL, bb, off);
+        const long long ok2 = __shfl_xor_sync(FULL, bk, off);
+        const int oj = __shfl_xor_sync(FULL, bj, off);
+        if (first_before(os, ok2, bs, bk)) {
+          bs = os;
+          bb = ob;
+          bk = ok2;
+          bj = oj;
+        }
+      }
+      __syncwarp();
+      if (r <= bs && r <= sw) {  // budget used up
+        if (lane == 0) CA[m] = P + (sg > 0 ? r : -r);
+        break;
+      }
+      if (bs <= sw) {  // contact
+        if (lane == 0) CA[m] = P + (sg > 0 ? bs : -bs);
+        r = r - bs;
+        ++n_ev;
+        ++ch_ev;
+        sum_b += bb - bs;
+        if (bj < nmem) {  // lift
+          ++n_li;
+          m = bj;
+          if (lane == 0) touched[m] = 1;
+        } else {  // frozen sphere: back along the axis
+          sg = -sg;
+          ++n_fr;
+        }
+      } else {  // wall: onto the wall, back along the axis
+        if (lane == 0) CA[m] = sg > 0 ? w : 0.0;
+        r = r - sw;
+        sg = -sg;
+        ++n_wa;
+        ++ch_wa;
+      }
+    }
+    __syncwarp();
+    if (rec != nullptr && lane == 0) {
+      rec[0] = start_id;
+      rec[1] = sid[m];
+      rec[2] = ch_ev;
+      rec[3] = ch_wa;
+    }
+  }
+  __syncwarp();
+  // members that moved, back in box coordinates
+  for (int q = lane; q < nmem; q += 32) {
+    if (!touched[q]) continue;
+    const int i = sid[q];
+    px[i] = wrap_box0(C[0][q] + o[0], L);
+    py[i] = wrap_box0(C[1][q] + o[1], L);
+    pz[i] = wrap_box0(C[2][q] + o[2], L);
+  }
+  if (lane == 0) {
+    Cell3 s;
+    s.sum_b = sum_b;
+    s.events = n_ev;
+    s.lifts = n_li;
+    s.frozen = n_fr;
+    s.walls = n_wa;
+    s.chains = n_ch;
+    s.n_mem = nmem;
+    cs[c] = s;
+  }
+}
+
+// End of sweep (one block of 256): the cells' sums in a fixed order, the
+// running totals, the sweep's member-weighted pressure sums, t + 1.
+__global__ void __launch_bounds__(256) k3_end(Geom3 g, State3* st, const Cell3* __restrict__ cs,
+                                             Totals3* tot, double* history, int64_t* hist_len) {
+  __shared__ double sd[2][8];
+  __shared__ long long sl[5][8];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  double b = 0.0, bw = 0.0;
+  long long v[5] = {0, 0, 0, 0, 0};
+  for (int c = tid; c < g.ncell; c += 256) {
+    const Cell3 s = cs[c];
+    b += s.sum_b;
+    bw += (double)s.n_mem * s.sum_b;
+    v[0] += s.events;
+    v[1] += s.lifts;
+    v[2] += s.frozen;
+    v[3] += s.walls;
+    v[4] += s.chains;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    b += __shfl_down_sync(0xffffffffu, b, off);
+    bw += __shfl_down_sync(0xffffffffu, bw, off);
+    for (int q = 0; q < 5; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], off);
+  }
+  if (lane == 0) {
+    sd[0][wid] = b;
+    sd[1][wid] = bw;
+    for (int q = 0; q < 5; ++q) sl[q][wid] = v[q];
+  }
+  __syncthreads();
+  if (tid != 0) return;
+  double B = 0.0, BW = 0.0;
+  long long V[5] = {0, 0, 0, 0, 0};
+  for (int wv = 0; wv < 8; ++wv) {
+    B += sd[0][wv];
+    BW += sd[1][wv];
+    for (int q = 0; q < 5; ++q) V[q] += sl[q][wv];
+  }
+  const double dw = (double)g.N * (double)g.n_m * g.ell;
+  Totals3& T = *tot;
+  T.sum_b += B;
+  T.sum_b_w += BW;
+  T.sum_disp += (double)V[4] * g.ell;
+  T.sum_disp_w += dw;
+  T.events += V[0];
+  T.lifts += V[1];
+  T.frozen += V[2];
+  T.walls += V[3];
+  T.chains += V[4];
+  T.sweeps += 1;
+  const int64_t n = *hist_len;
+  if (n < kHistoryCap) {
+    history[2 * n] = BW;
+    history[2 * n + 1] = dw;
+  }
+  *hist_len = n + 1;
+  st->t += 1;
+}
+
+// interleaved [x0, y0, z0, ...] <-> three arrays
+__global__ void k3_split(const double* __restrict__ xyz, int64_t N, double* __restrict__ px,
+                         double* __restrict__ py, double* __restrict__ pz) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  px[i] = xyz[3 * i];
+  py[i] = xyz[3 * i + 1];
+  pz[i] = xyz[3 * i + 2];
+}
+
+__global__ void k3_join(const double* __restrict__ px, const double* __restrict__ py,
+                        const double* __restrict__ pz, int64_t N, double* __restrict__ xyz) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  xyz[3 * i] = px[i];
+  xyz[3 * i + 1] = py[i];
+  xyz[3 * i + 2] = pz[i];
+}
+
+// Smallest squared minimum-image distance below rcut^2 over the pairs of the
+// last binning's 27-cell neighbourhoods (FP64, the oracle's formula), as the
+// bits of a non-negative double (their order is the order of the values).
+__global__ void k3_min_dist(Geom3 g, const double* __restrict__ px, const double* __restrict__ py,
+                            const double* __restrict__ pz, const int* __restrict__ cnt,
+                            const int* __restrict__ ids, const int* __restrict__ cell_of,
+                            unsigned long long r2_bits, unsigned long long* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long best = r2_bits;
+  if (i < g.N) {
+    const int c = cell_of[i], nc = g.cells;
+    const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+    const double xi = px[i], yi = py[i], zi = pz[i];
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int q = (((cz + dz + nc) % nc) * nc + (cy + dy + nc) % nc) * nc +
+                        (cx + dx + nc) % nc;
+          const int nq = min(cnt[q], g.cap_mem);
+          for (int k = 0; k < nq; ++k) {
+            const int j = ids[(int64_t)q * g.cap_mem + k];
+            if (j == i) continue;
+            const double ex = wrap_half(px[j] - xi, g.L);
+            const double ey = wrap_half(py[j] - yi, g.L);
+            const double ez = wrap_half(pz[j] - zi, g.L);
+            const double d2 = ex * ex + ey * ey + ez * ez;
+            const unsigned long long bits = __double_as_longlong(d2);
+            best = bits < best ? bits : best;
+          }
+        }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o2 = __shfl_xor_sync(0xffffffffu, best, off);
+    best = o2 < best ? o2 : best;
+  }
+  if ((threadIdx.x & 31) == 0 && best < r2_bits) atomicMin(out, best);
+}
+
+}  // namespace ecmc3
+
+// ---- host side ----------------------------------------------------------------
+
+using namespace ecmc3;
+
+struct ecmc3_ctx {
+  Geom3 g;
+  cudaStream_t stream = nullptr, own = nullptr;
+  double *px = nullptr, *py = nullptr, *pz = nullptr, *xyz_tmp = nullptr;
+  int *cnt = nullptr, *ids = nullptr, *cell_of = nullptr, *err = nullptr, *recs = nullptr;
+  Cell3* cs = nullptr;
+  State3* st = nullptr;
+  Totals3* tot = nullptr;
+  double* history = nullptr;
+  int64_t* hist_len = nullptr;
+  unsigned long long* u64 = nullptr;
+  int warps = 1;
+  int64_t t_host = 0;
+  bool valid = false;
+};
+
+namespace {
+
+int fail3(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  return ecmc::report_error(code, buf);
+}
+
+#define CK3(call)                                                                         \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail3(e_ == cudaErrorMemoryAllocation ? ECMC_ERR_OOM : ECMC_ERR_CUDA,        \
+                   "%s failed: %s", #call, cudaGetErrorString(e_));                       \
+  } while (0)
+
+// spheres of diameter sigma whose centres lie in a cube of side s: they sit
+// inside the cube of side s + sigma, and no packing of spheres is denser
+// than pi / (3 sqrt 2), so there are at most sqrt(2) (s + sigma)^3 / sigma^3
+int sphere_bound(double s, double sigma) {
+  const double q = (s + sigma) / sigma;
+  return (int)std::floor(std::sqrt(2.0) * q * q * q) + 2;
+}
+
+int check3(ecmc3_ctx* h) {
+  int e = 0;
+  CK3(cudaMemcpyAsync(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK3(cudaStreamSynchronize(h->stream));
+  if (e == kCapacity) {
+    h->valid = false;
+    return fail3(ECMC_ERR_CAPACITY, "a cell bucket or frame exceeded its packing bound");
+  }
+  if (e == kChainCap) {
+    h->valid = false;
+    return fail3(ECMC_ERR_CHAIN_CAP, "a chain reached the per-chain event cap");
+  }
+  return ECMC_OK;
+}
+
+int enqueue_sweep(ecmc3_ctx* h, bool records) {
+  const Geom3& g = h->g;
+  CK3(cudaMemsetAsync(h->cnt, 0, sizeof(int) * (size_t)g.ncell, h->stream));
+  k3_begin<<<1, 32, 0, h->stream>>>(g, h->st);
+  k3_bin<<<(unsigned)((g.N + 255) / 256), 256, 0, h->stream>>>(g, h->st, h->px, h->py, h->pz,
+                                                               h->cnt, h->ids, h->cell_of,
+                                                               h->err);
+  const int wpb = h->warps;
+  const unsigned blocks = (unsigned)((g.nact + wpb - 1) / wpb);
+  const size_t sm = (size_t)wpb * g.warp_bytes;
+  for (int ci = 0; ci < 8; ++ci)
+    k3_phase<<<blocks, 32 * wpb, sm, h->stream>>>(g, h->st, ci, h->px, h->py, h->pz, h->cnt,
+                                                  h->ids, h->cs, records ? h->recs : nullptr,
+                                                  h->err);
+  k3_end<<<1, 256, 0, h->stream>>>(g, h->st, h->cs, h->tot, h->history, h->hist_len);
+  CK3(cudaGetLastError());
+  return ECMC_OK;
+}
+
+int bin_now(ecmc3_ctx* h) {
+  const Geom3& g = h->g;
+  CK3(cudaMemsetAsync(h->cnt, 0, sizeof(int) * (size_t)g.ncell, h->stream));
+  k3_begin<<<1, 32, 0, h->stream>>>(g, h->st);
+  k3_bin<<<(unsigned)((g.N + 255) / 256), 256, 0, h->stream>>>(g, h->st, h->px, h->py, h->pz,
+                                                               h->cnt, h->ids, h->cell_of,
+                                                               h->err);
+  CK3(cudaGetLastError());
+  return ECMC_OK;
+}
+
+double rcut3(const Geom3& g) { return std::fmin(2.0 * g.sigma, g.w); }
+
+int min_dist2_3(ecmc3_ctx* h, double* d2) {
+  const Geom3& g = h->g;
+  const double rc = rcut3(g), r2 = rc * rc;
+  unsigned long long bits = 0;
+  std::memcpy(&bits, &r2, sizeof(r2));
+  CK3(cudaMemcpyAsync(h->u64, &bits, sizeof(bits), cudaMemcpyHostToDevice, h->stream));
+  k3_min_dist<<<(unsigned)((g.N + 255) / 256), 256, 0, h->stream>>>(
+      g, h->px, h->py, h->pz, h->cnt, h->ids, h->cell_of, bits, h->u64);
+  CK3(cudaGetLastError());
+  CK3(cudaMemcpyAsync(&bits, h->u64, sizeof(bits), cudaMemcpyDeviceToHost, h->stream));
+  const int rc2 = check3(h);
+  if (rc2) return rc2;
+  std::memcpy(d2, &bits, sizeof(*d2));
+  return ECMC_OK;
+}
+
+int load_dev(ecmc3_ctx* h, const double* xyz_dev, int64_t t0) {
+  const Geom3& g = h->g;
+  k3_split<<<(unsigned)((g.N + 255) / 256), 256, 0, h->stream>>>(xyz_dev, g.N, h->px, h->py,
+                                                                 h->pz);
+  State3 s;
+  std::memset(&s, 0, sizeof(s));
+  s.t = t0;
+  CK3(cudaMemcpyAsync(h->st, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream));
+  CK3(cudaMemsetAsync(h->tot, 0, sizeof(Totals3), h->stream));
+  CK3(cudaMemsetAsync(h->hist_len, 0, sizeof(int64_t), h->stream));
+  CK3(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
+  h->t_host = t0;
+  h->valid = true;
+  int rc = bin_now(h);
+  if (rc) return rc;
+  rc = check3(h);
+  if (rc) return rc;
+  double d2 = 0.0;
+  rc = min_dist2_3(h, &d2);
+  if (rc) return rc;
+  if (d2 < g.sig2 * (1.0 - 1e-9)) {
+    h->valid = false;
+    return fail3(ECMC_ERR_OVERLAP, "positions overlap: smallest distance %.17g < sigma",
+                 std::sqrt(d2));
+  }
+  return ECMC_OK;
+}
+
+void free3(ecmc3_ctx* h) {
+  cudaFree(h->px);
+  cudaFree(h->py);
+  cudaFree(h->pz);
+  cudaFree(h->xyz_tmp);
+  cudaFree(h->cnt);
+  cudaFree(h->ids);
+  cudaFree(h->cell_of);
+  cudaFree(h->err);
+  cudaFree(h->recs);
+  cudaFree(h->cs);
+  cudaFree(h->st);
+  cudaFree(h->tot);
+  cudaFree(h->history);
+  cudaFree(h->hist_len);
+  cudaFree(h->u64);
+  if (h->own) cudaStreamDestroy(h->own);
+}
+
+// shared memory of one warp's frame, and the launch's warps per block
+int layout3(ecmc3_ctx* h) {
+  Geom3& g = h->g;
+  g.warp_bytes = (int)(((size_t)g.cap_obj * (3 * sizeof(double) + sizeof(long long)) +
+                        (size_t)g.cap_mem * 2 * sizeof(int) + 28 * sizeof(int) +
+                        (size_t)g.cap_mem + 15) &
+                       ~(size_t)15);
+  int dev = 0, optin = 0;
+  CK3(cudaGetDevice(&dev));
+  CK3(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  int wpb = kWarpsMax;
+  while (wpb > 1 && (size_t)wpb * g.warp_bytes > (size_t)optin) --wpb;
+  if ((size_t)g.warp_bytes > (size_t)optin)
+    return fail3(ECMC_ERR_UNSUPPORTED, "a cell's frame (%d bytes) exceeds shared memory",
+                 g.warp_bytes);
+  h->warps = wpb;
+  CK3(cudaFuncSetAttribute(k3_phase, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)((size_t)wpb * g.warp_bytes)));
+  return ECMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ecmc3_create(ecmc3_t* out, int64_t N, double L, double sigma, int cells, double ell,
+                 uint64_t seed) {
+  if (!out) return fail3(ECMC_ERR_ARG, "NULL output handle");
+  *out = nullptr;
+  if (N < 1 || N >= (int64_t(1) << 30)) return fail3(ECMC_ERR_ARG, "N out of range");
+  int64_t k = (int64_t)std::llround(std::cbrt((double)N));
+  while (k * k * k > N) --k;
+  while ((k + 1) * (k + 1) * (k + 1) <= N) ++k;
+  if (k * k * k != N) return fail3(ECMC_ERR_ARG, "N must be a perfect cube (lattice start)");
+  if (!(L > 0.0) || !(sigma > 0.0) || !std::isfinite(L) || !std::isfinite(sigma))
+    return fail3(ECMC_ERR_ARG, "L and sigma must be positive");
+  if (cells < 2 || (cells & 1) || cells > 1024)
+    return fail3(ECMC_ERR_ARG, "cells per side must be even, >= 2 and <= 1024");
+  if (!(L / (double)cells > sigma)) return fail3(ECMC_ERR_ARG, "cell side must exceed sigma");
+  if (!(L / (double)k > sigma)) return fail3(ECMC_ERR_ARG, "cubic lattice would overlap");
+  if (!(ell >= 0.0) || !std::isfinite(ell)) return fail3(ECMC_ERR_ARG, "ell must be >= 0");
+  ecmc3_ctx* h = new ecmc3_ctx();
+  Geom3& g = h->g;
+  std::memset(&g, 0, sizeof(g));
+  g.N = N;
+  g.L = L;
+  g.sigma = sigma;
+  g.sig2 = sigma * sigma;
+  g.cells = cells;
+  g.ncell = cells * cells * cells;
+  g.nact = g.ncell / 8;
+  g.w = L / (double)cells;
+  g.inv_w = 1.0 / g.w;
+  g.ell = ell;
+  g.n_m = 1;
+  g.seed = seed;
+  g.replica = 0;
+  g.cap_mem = sphere_bound(g.w, sigma);
+  g.cap_obj = sphere_bound(g.w + 2.0 * sigma, sigma);
+  if ((int64_t)g.cap_mem > N) g.cap_mem = (int)N;
+  if ((double)g.ncell * g.cap_mem > 2.0e9) {
+    delete h;
+    return fail3(ECMC_ERR_ARG, "too many cells");
+  }
+  int rc = layout3(h);
+  if (rc) {
+    delete h;
+    return rc;
+  }
+  if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess) {
+    delete h;
+    return fail3(ECMC_ERR_CUDA, "stream creation failed");
+  }
+  h->stream = h->own;
+  const size_t nn = (size_t)N;
+  if (cudaMalloc(&h->px, sizeof(double) * nn) != cudaSuccess ||
+      cudaMalloc(&h->py, sizeof(double) * nn) != cudaSuccess ||
+      cudaMalloc(&h->pz, sizeof(double) * nn) != cudaSuccess ||
+      cudaMalloc(&h->xyz_tmp, sizeof(double) * 3 * nn) != cudaSuccess ||
+      cudaMalloc(&h->cnt, sizeof(int) * (size_t)g.ncell) != cudaSuccess ||
+      cudaMalloc(&h->ids, sizeof(int) * (size_t)g.ncell * g.cap_mem) != cudaSuccess ||
+      cudaMalloc(&h->cell_of, sizeof(int) * nn) != cudaSuccess ||
+      cudaMalloc(&h->err, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&h->cs, sizeof(Cell3) * (size_t)g.ncell) != cudaSuccess ||
+      cudaMalloc(&h->st, sizeof(State3)) != cudaSuccess ||
+      cudaMalloc(&h->tot, sizeof(Totals3)) != cudaSuccess ||
+      cudaMalloc(&h->history, sizeof(double) * 2 * kHistoryCap) != cudaSuccess ||
+      cudaMalloc(&h->hist_len, sizeof(int64_t)) != cudaSuccess ||
+      cudaMalloc(&h->u64, sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    free3(h);
+    delete h;
+    return fail3(ECMC_ERR_OOM, "device allocation failed");
+  }
+  // the cubic lattice start
+  std::vector<double> xyz(3 * nn);
+  const double a = L / (double)k;
+  for (int64_t i = 0; i < N; ++i) {
+    xyz[3 * i] = ((double)(i % k) + 0.5) * a;
+    xyz[3 * i + 1] = ((double)((i / k) % k) + 0.5) * a;
+    xyz[3 * i + 2] = ((double)(i / (k * k)) + 0.5) * a;
+  }
+  rc = ecmc3_set_positions(h, xyz.data(), 0, 0);
+  if (rc) {
+    free3(h);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return ECMC_OK;
+}
+
+int ecmc3_destroy(ecmc3_t h) {
+  if (!h) return fail3(ECMC_ERR_ARG, "NULL handle");
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free3(h);
+  delete h;
+  return ECMC_OK;
+}
+
+int ecmc3_set_param(ecmc3_t h, int key, double v) {
+  if (!h) return fail3(ECMC_ERR_ARG, "NULL handle");
+  switch (key) {
+    case ECMC3_PARAM_N_CHAINS: {
+      const int n = (int)v;
+      if ((double)n != v || n < 1 || n > (1 << 20)) return fail3(ECMC_ERR_ARG, "n_m");
+      if (n != h->g.n_m) {
+        h->g.n_m = n;
+        cudaFree(h->recs);
+        h->recs = nullptr;
+      }
+      return ECMC_OK;
+    }
+    case ECMC3_PARAM_REPLICA:
+      if (!(v >= 0.0) || v != std::floor(v)) return fail3(ECMC_ERR_ARG, "replica");
+      h->g.replica = (uint64_t)v;
+      return ECMC_OK;
+    default:
+      return fail3(ECMC_ERR_ARG, "unknown parameter %d", key);
+  }
+}
+
+int ecmc3_get_param(ecmc3_t h, int key, double* v) {
+  if (!h || !v) return fail3(ECMC_ERR_ARG, "NULL argument");
+  switch (key) {
+    case ECMC3_PARAM_N_CHAINS: *v = h->g.n_m; return ECMC_OK;
+    case ECMC3_PARAM_REPLICA: *v = (double)h->g.replica; return ECMC_OK;
+    default: return fail3(ECMC_ERR_ARG, "unknown parameter %d", key);
+  }
+}
+
+int ecmc3_set_stream(ecmc3_t h, void* stream) {
+  if (!h) return fail3(ECMC_ERR_ARG, "NULL handle");
+  CK3(cudaStreamSynchronize(h->stream));
+  h->stream = stream ? (cudaStream_t)stream : h->own;
+  return ECMC_OK;
+}
+
+int ecmc3_set_positions(ecmc3_t h, const double* xyz, int on_device, int64_t t0) {
+  if (!h || !xyz) return fail3(ECMC_ERR_ARG, "NULL argument");
+  if (t0 < 0) return fail3(ECMC_ERR_ARG, "t0 must be >= 0");
+  const double* src = xyz;
+  if (!on_device) {
+    CK3(cudaMemcpyAsync(h->xyz_tmp, xyz, sizeof(double) * 3 * (size_t)h->g.N,
+                        cudaMemcpyHostToDevice, h->stream));
+    src = h->xyz_tmp;
+  }
+  return load_dev(h, src, t0);
+}
+
+int ecmc3_positions(ecmc3_t h, double* xyz, int on_device) {
+  if (!h || !xyz) return fail3(ECMC_ERR_ARG, "NULL argument");
+  if (!h->valid) return fail3(ECMC_ERR_STATE, "state invalid after an earlier error");
+  const Geom3& g = h->g;
+  double* dst = on_device ? xyz : h->xyz_tmp;
+  k3_join<<<(unsigned)((g.N + 255) / 256), 256, 0, h->stream>>>(h->px, h->py, h->pz, g.N, dst);
+  CK3(cudaGetLastError());
+  if (!on_device)
+    CK3(cudaMemcpyAsync(xyz, h->xyz_tmp, sizeof(double) * 3 * (size_t)g.N,
+                        cudaMemcpyDeviceToHost, h->stream));
+  return check3(h);
+}
+
+int ecmc3_sweep(ecmc3_t h, int64_t n) {
+  if (!h) return fail3(ECMC_ERR_ARG, "NULL handle");
+  if (n < 0) return fail3(ECMC_ERR_ARG, "negative sweep count");
+  if (!h->valid) return fail3(ECMC_ERR_STATE, "state invalid after an earlier error");
+  const bool rec = n > 0;
+  if (rec && !h->recs) {
+    CK3(cudaMalloc(&h->recs, sizeof(int) * 4 * (size_t)h->g.ncell * h->g.n_m));
+  }
+  for (int64_t s = 0; s < n; ++s) {
+    const int rc = enqueue_sweep(h, s == n - 1);
+    if (rc) return rc;
+  }
+  h->t_host += n;
+  return ECMC_OK;
+}
+
+int ecmc3_synchronize(ecmc3_t h) {
+  if (!h) return fail3(ECMC_ERR_ARG, "NULL handle");
+  return check3(h);
+}
+
+int ecmc3_sweep_index(ecmc3_t h, int64_t* t) {
+  if (!h || !t) return fail3(ECMC_ERR_ARG, "NULL argument");
+  *t = h->t_host;
+  return ECMC_OK;
+}
+
+int ecmc3_counters(ecmc3_t h, ecmc_counters_t* out) {
+  if (!h || !out) return fail3(ECMC_ERR_ARG, "NULL argument");
+  Totals3 t;
+  CK3(cudaMemcpyAsync(&t, h->tot, sizeof(t), cudaMemcpyDeviceToHost, h->stream));
+  const int rc = check3(h);
+  if (rc) return rc;
+  std::memset(out, 0, sizeof(*out));
+  out->sweeps = t.sweeps;
+  out->chains = t.chains;
+  out->events = t.events;
+  out->lifts = t.lifts;
+  out->frozen_hits = t.frozen;
+  out->wall_hits = t.walls;
+  out->sum_b = t.sum_b;
+  out->sum_disp = t.sum_disp;
+  return ECMC_OK;
+}
+
+int ecmc3_pressure(ecmc3_t h, double* betaP, double* se) {
+  if (!h || !betaP) return fail3(ECMC_ERR_ARG, "NULL argument");
+  Totals3 t;
+  int64_t n = 0;
+  CK3(cudaMemcpyAsync(&t, h->tot, sizeof(t), cudaMemcpyDeviceToHost, h->stream));
+  CK3(cudaMemcpyAsync(&n, h->hist_len, sizeof(n), cudaMemcpyDeviceToHost, h->stream));
+  int rc = check3(h);
+  if (rc) return rc;
+  if (n < 1 || !(t.sum_disp_w > 0.0)) return fail3(ECMC_ERR_STATE, "no sweep since the last reset");
+  const Geom3& g = h->g;
+  const double rho_s3 = (double)g.N / (g.L * g.L * g.L) * g.sig2 * g.sigma;
+  *betaP = rho_s3 * (1.0 + t.sum_b_w / t.sum_disp_w);
+  if (se) {
+    *se = 0.0;
+    const int64_t m = n < kHistoryCap ? n : kHistoryCap;
+    const int64_t nb = m >= 20 ? 20 : m;
+    if (nb >= 2) {
+      std::vector<double> hist(2 * (size_t)m);
+      CK3(cudaMemcpyAsync(hist.data(), h->history, sizeof(double) * 2 * (size_t)m,
+                          cudaMemcpyDeviceToHost, h->stream));
+      CK3(cudaStreamSynchronize(h->stream));
+      std::vector<double> vals;
+      for (int64_t b = 0; b < nb; ++b) {
+        const int64_t lo = b * m / nb, hi = (b + 1) * m / nb;
+        double sb = 0.0, sd = 0.0;
+        for (int64_t i = lo; i < hi; ++i) {
+          sb += hist[2 * i];
+          sd += hist[2 * i + 1];
+        }
+        vals.push_back(rho_s3 * (1.0 + sb / sd));
+      }
+      double mean = 0.0;
+      for (double v : vals) mean += v;
+      mean /= (double)nb;
+      double var = 0.0;
+      for (double v : vals) var += (v - mean) * (v - mean);
+      *se = std::sqrt(var / (double)(nb - 1) / (double)nb);
+    }
+  }
+  return ECMC_OK;
+}
+
+int ecmc3_reset_stats(ecmc3_t h) {
+  if (!h) return fail3(ECMC_ERR_ARG, "NULL handle");
+  CK3(cudaMemsetAsync(h->tot, 0, sizeof(Totals3), h->stream));
+  CK3(cudaMemsetAsync(h->hist_len, 0, sizeof(int64_t), h->stream));
+  return ECMC_OK;
+}
+
+int ecmc3_min_distance(ecmc3_t h, double* dmin) {
+  if (!h || !dmin) return fail3(ECMC_ERR_ARG, "NULL argument");
+  double d2 = 0.0;
+  const int rc = min_dist2_3(h, &d2);
+  if (rc) return rc;
+  *dmin = std::sqrt(d2);
+  return ECMC_OK;
+}
+
+int ecmc3_last_cells(ecmc3_t h, int32_t* cell_of_id) {
+  if (!h || !cell_of_id) return fail3(ECMC_ERR_ARG, "NULL argument");
+  CK3(cudaMemcpyAsync(cell_of_id, h->cell_of, sizeof(int32_t) * (size_t)h->g.N,
+                      cudaMemcpyDeviceToHost, h->stream));
+  return check3(h);
+}
+
+int ecmc3_chain_records(ecmc3_t h, int32_t* out) {
+  if (!h || !out) return fail3(ECMC_ERR_ARG, "NULL argument");
+  if (!h->recs) return fail3(ECMC_ERR_STATE, "no sweep has run");
+  CK3(cudaMemcpyAsync(out, h->recs, sizeof(int32_t) * 4 * (size_t)h->g.ncell * h->g.n_m,
+                      cudaMemcpyDeviceToHost, h->stream));
+  return check3(h);
+}
+
+}  // extern "C"

@@ -43,6 +43,10 @@ enum TimerClass { TC_BIN = 0, TC_FRAME = 1, TC_PHASE = 2, TC_OTHER = 3 };
 
 }  // namespace
 
+namespace ecmc {
+int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace ecmc
+
 struct ecmc_ctx {
   std::vector<Geom> geo;        // host copy of every replica's geometry
   std::vector<int> cell_rep;    // replica of every global cell

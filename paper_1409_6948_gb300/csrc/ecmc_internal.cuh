@@ -226,6 +226,9 @@ size_t fused_scratch_bytes(const RecLayout& lay);
 // frozen disks, 1 isotropic chains, 2 axis chains under the rejecting
 // boundary rule (a compile-time variant, so that the default loop carries
 // none of its bookkeeping).
+// Set the message ecmc_last_error_message() returns; returns code.
+int report_error(int code, const char* msg);
+
 inline int chain_kind(const DevBufs& b) { return b.iso ? 1 : (b.reject ? 2 : 0); }
 int configure_fused(const RecLayout& lay, int tpc, int fm, int kind, int* blocks_per_sm);
 int launch_fused(const DevBufs& b, const RecLayout& lay, int tpc, int blocks, int records_on,

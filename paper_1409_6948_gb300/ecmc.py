@@ -136,6 +136,23 @@ _SIGS = {
     "ecmc_sweep_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_double, C.c_int,
                                      C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_uint64,
                                      C.c_int64, C.c_int64, C.c_void_p]),
+    "ecmc3_create": (C.c_int, [C.POINTER(_H), C.c_int64, C.c_double, C.c_double, C.c_int,
+                               C.c_double, C.c_uint64]),
+    "ecmc3_destroy": (C.c_int, [_H]),
+    "ecmc3_set_param": (C.c_int, [_H, C.c_int, C.c_double]),
+    "ecmc3_get_param": (C.c_int, [_H, C.c_int, C.POINTER(C.c_double)]),
+    "ecmc3_set_stream": (C.c_int, [_H, C.c_void_p]),
+    "ecmc3_set_positions": (C.c_int, [_H, C.c_void_p, C.c_int, C.c_int64]),
+    "ecmc3_positions": (C.c_int, [_H, C.c_void_p, C.c_int]),
+    "ecmc3_sweep": (C.c_int, [_H, C.c_int64]),
+    "ecmc3_synchronize": (C.c_int, [_H]),
+    "ecmc3_sweep_index": (C.c_int, [_H, C.POINTER(C.c_int64)]),
+    "ecmc3_counters": (C.c_int, [_H, C.POINTER(Counters)]),
+    "ecmc3_pressure": (C.c_int, [_H, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "ecmc3_reset_stats": (C.c_int, [_H]),
+    "ecmc3_min_distance": (C.c_int, [_H, C.POINTER(C.c_double)]),
+    "ecmc3_last_cells": (C.c_int, [_H, C.c_void_p]),
+    "ecmc3_chain_records": (C.c_int, [_H, C.c_void_p]),
     "ecmc_strerror": (C.c_char_p, [C.c_int]),
     "ecmc_last_error_message": (C.c_char_p, []),
     "ecmc_version": (C.c_char_p, []),
@@ -390,6 +407,109 @@ class Ecmc:
         _check(load().ecmc_chain_records(self._h, C.c_void_p(out.ctypes.data), n),
                "ecmc_chain_records")
         return out.reshape(self.cells_x * self.cells_y, nm)
+
+
+PARAM3_N_CHAINS = 1
+PARAM3_REPLICA = 4
+
+
+class Ecmc3:
+    """One hard-sphere system on the GPU (three dimensions; include/ecmc3.h):
+    N = k^3 spheres of diameter sigma in a periodic cube of side L, cells^3
+    cubic cells, chains of displacement ell, simple cubic lattice start."""
+
+    def __init__(self, N, L, sigma, cells, ell, seed):
+        lib = load()
+        h = _H()
+        _check(lib.ecmc3_create(C.byref(h), int(N), float(L), float(sigma), int(cells),
+                                float(ell), C.c_uint64(int(seed))), "ecmc3_create")
+        self._h = h
+        self.N, self.L, self.sigma, self.cells = int(N), float(L), float(sigma), int(cells)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ecmc3_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_param(self, key, value):
+        _check(load().ecmc3_set_param(self._h, int(key), float(value)), "ecmc3_set_param")
+
+    def get_param(self, key):
+        v = C.c_double()
+        _check(load().ecmc3_get_param(self._h, int(key), C.byref(v)), "ecmc3_get_param")
+        return v.value
+
+    def set_stream(self, stream):
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        _check(load().ecmc3_set_stream(self._h, C.c_void_p(stream or 0)), "ecmc3_set_stream")
+
+    def set_positions(self, xyz, t0=0):
+        p, dev = _ptr(xyz)
+        _check(load().ecmc3_set_positions(self._h, p, dev, int(t0)), "ecmc3_set_positions")
+
+    def positions(self, out=None):
+        if out is None:
+            out = np.empty(3 * self.N)
+        p, dev = _ptr(out)
+        _check(load().ecmc3_positions(self._h, p, dev), "ecmc3_positions")
+        return out
+
+    def sweep(self, n=1):
+        _check(load().ecmc3_sweep(self._h, int(n)), "ecmc3_sweep")
+
+    def synchronize(self):
+        _check(load().ecmc3_synchronize(self._h), "ecmc3_synchronize")
+
+    def sweep_index(self):
+        t = C.c_int64()
+        _check(load().ecmc3_sweep_index(self._h, C.byref(t)), "ecmc3_sweep_index")
+        return t.value
+
+    def counters(self):
+        c = Counters()
+        _check(load().ecmc3_counters(self._h, C.byref(c)), "ecmc3_counters")
+        return c
+
+    def pressure(self):
+        p, se = C.c_double(), C.c_double()
+        _check(load().ecmc3_pressure(self._h, C.byref(p), C.byref(se)), "ecmc3_pressure")
+        return p.value, se.value
+
+    def reset_stats(self):
+        _check(load().ecmc3_reset_stats(self._h), "ecmc3_reset_stats")
+
+    def min_distance(self):
+        d = C.c_double()
+        _check(load().ecmc3_min_distance(self._h, C.byref(d)), "ecmc3_min_distance")
+        return d.value
+
+    def last_cells(self):
+        out = np.empty(self.N, np.int32)
+        _check(load().ecmc3_last_cells(self._h, C.c_void_p(out.ctypes.data)),
+               "ecmc3_last_cells")
+        return out
+
+    def chain_records(self):
+        """Records of the last sweep: [cells^3, n_m] of (start_id, end_id,
+        events, walls)."""
+        nm = int(self.get_param(PARAM3_N_CHAINS))
+        out = np.empty((self.cells ** 3, nm, 4), np.int32)
+        _check(load().ecmc3_chain_records(self._h, C.c_void_p(out.ctypes.data)),
+               "ecmc3_chain_records")
+        return out
 
 
 def version():

@@ -1,6 +1,6 @@
 """The C-ABI library (no GPU needed): it loads, exports every function that
-include/ecmc.h declares, and rejects invalid arguments before touching the
-device."""
+include/ecmc.h and include/ecmc3.h declare, and rejects invalid arguments
+before touching the device."""
 import ctypes as C
 import os
 import re
@@ -20,7 +20,7 @@ def declared_functions():
             continue
         with open(os.path.join(ROOT, "include", fn)) as f:
             src = f.read()
-        names += re.findall(r"^ECMC_API\s+[\w\s\*]+?\b(ecmc_\w+)\s*\(", src, re.M)
+        names += re.findall(r"^ECMC_API\s+[\w\s\*]+?\b(ecmc3?_\w+)\s*\(", src, re.M)
     return sorted(set(names))
 
 
@@ -61,6 +61,23 @@ def test_invalid_arguments_are_rejected_before_device_work(args):
     rc = lib.ecmc_create(C.byref(h), *[C.c_int64(args[0]), C.c_double(args[1]),
                                        C.c_double(args[2]), C.c_int(args[3]), C.c_int(args[4]),
                                        C.c_double(args[5]), C.c_uint64(args[6])])
+    assert rc == E.ERR_ARG and not h.value
+
+
+@pytest.mark.parametrize("args", [
+    (0, 10.0, 1.0, 2, 1.0, 1),           # no spheres
+    (63, 10.0, 1.0, 2, 1.0, 1),          # N not a perfect cube
+    (64, 10.0, 1.0, 3, 1.0, 1),          # odd cells per side
+    (64, 10.0, 1.0, 12, 1.0, 1),         # cell side below sigma
+    (1000, 9.0, 1.0, 2, 1.0, 1),         # cubic lattice spacing below sigma
+    (64, 10.0, 1.0, 2, -1.0, 1),         # negative displacement
+    (64, -1.0, 1.0, 2, 1.0, 1),          # negative box
+])
+def test_invalid_three_dimensional_arguments_are_rejected(args):
+    lib = P.load()
+    h = C.c_void_p()
+    N, L, sigma, cells, ell, seed = args
+    rc = lib.ecmc3_create(C.byref(h), N, L, sigma, cells, ell, seed)
     assert rc == E.ERR_ARG and not h.value
 
 

@@ -1,0 +1,145 @@
+"""Parity of the three-dimensional CUDA sweep (include/ecmc3.h) with the
+oracle's orc3_sweeps, through the C ABI.
+
+Both sides evaluate every contact with the same FP64 expressions (no
+contraction), so the binning and the chain records are compared exactly,
+positions to 1e-12 relative (identical in practice) after every sweep, the
+counters exactly and the pressure to 1e-11.  Cases: two cells per side (the
+neighbour cells coincide), several cell counts, a ragged N = 10^3, n_m from 1
+to 6, and dense systems with many frozen contacts.  The overlap check and
+the smallest distance are compared with the oracle's grid search.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import ecmc_workloads as W
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("CUDA device required", allow_module_level=True)
+
+import paper_1409_6948_gb300 as P  # noqa: E402
+from paper_1409_6948_gb300 import ecmc as E  # noqa: E402
+
+REL = 1e-12
+
+
+def make3(N, eta, cells, ell, nm, seed):
+    L = W.box_side3(N, eta)
+    g = P.Ecmc3(N, L, 1.0, cells, ell, seed)
+    g.set_param(E.PARAM3_N_CHAINS, nm)
+    p = oracle.make_params3(N, L, 1.0, cells, ell, nm, seed)
+    return g, p, L
+
+
+def assert_positions_equal(g, x, y, z, L):
+    xyz = g.positions()
+    worst = 0.0
+    for a, ref in enumerate((x, y, z)):
+        d = np.abs(xyz[a::3] - ref)
+        d = np.minimum(d, L - d)
+        worst = max(worst, d.max() / L)
+    assert worst <= REL, "max relative position difference %g" % worst
+
+
+def run_pair3(N, eta, cells, ell, nm, seed, n_sweeps):
+    g, p, L = make3(N, eta, cells, ell, nm, seed)
+    x, y, z = W.cubic_lattice(N, L)
+    tot = oracle.Stats()
+    for s in range(n_sweeps):
+        cells_or = oracle.bin_cells3(p, s, x, y, z)
+        st, recs = oracle.sweeps3(p, x, y, z, s, 1, stats=tot, records=True)
+        g.sweep(1)
+        assert np.array_equal(g.last_cells(), cells_or), "binning differs at sweep %d" % s
+        gr = g.chain_records()
+        orr = recs[0]
+        assert np.array_equal(gr[:, :, 0], orr["start_id"]), "start spheres, sweep %d" % s
+        ran = orr["start_id"] >= 0
+        assert np.array_equal(gr[:, :, 1][ran], orr["end_id"][ran]), "end spheres, sweep %d" % s
+        assert np.array_equal(gr[:, :, 2][ran], orr["events"][ran]), "events, sweep %d" % s
+        assert np.array_equal(gr[:, :, 3][ran], orr["walls"][ran]), "walls, sweep %d" % s
+        assert_positions_equal(g, x, y, z, L)
+    c = g.counters()
+    assert c.events == tot.events and c.lifts == tot.lifts
+    assert c.frozen_hits == tot.frozen_hits and c.wall_hits == tot.wall_hits
+    assert c.chains == tot.chains and c.sweeps == n_sweeps
+    assert c.sum_b == pytest.approx(tot.sum_b, rel=1e-11, abs=1e-12)
+    P_gpu, _ = g.pressure()
+    P_or = oracle.pressure_from_sums3(tot.sum_b_w, tot.sum_disp_w, N, L, 1.0)
+    assert P_gpu == pytest.approx(P_or, rel=1e-11)
+    assert g.sweep_index() == n_sweeps
+    g.close()
+    return tot
+
+
+@pytest.mark.parametrize("N,eta,cells,ell,nm,sweeps", [
+    (64, 0.30, 2, 1.0, 4, 12),       # two cells per side: neighbours coincide
+    (512, 0.45, 4, 0.8, 3, 8),
+    (1000, 0.40, 4, 2.0, 5, 6),      # ragged member counts
+    (4096, 0.50, 8, 1.5, 2, 4),
+    (13824, 0.49, 10, 1.0, 1, 3),
+    (8000, 0.30, 6, 3.0, 6, 3),
+])
+def test_sweeps_match_oracle(N, eta, cells, ell, nm, sweeps):
+    st = run_pair3(N, eta, cells, ell, nm, 5, sweeps)
+    assert st.events > 0 and st.frozen_hits > 0 and st.wall_hits > 0
+
+
+def test_every_axis_and_a_long_run():
+    # 9 sweeps cover the axes x, y, z three times each
+    run_pair3(512, 0.52, 2, 1.2, 4, 8, 9)
+
+
+def test_min_distance_and_overlap_check():
+    N, eta, cells = 4096, 0.45, 8
+    g, p, L = make3(N, eta, cells, 1.0, 3, 2)
+    x, y, z = W.cubic_lattice(N, L)
+    oracle.sweeps3(p, x, y, z, 0, 10)
+    xyz = np.empty(3 * N)
+    xyz[0::3], xyz[1::3], xyz[2::3] = x, y, z
+    g.set_positions(xyz, t0=10)
+    rc = min(2.0, L / cells)
+    assert g.min_distance() == math.sqrt(oracle.min_dist2_3(L, x, y, z, rc))
+    # move sphere 1 onto sphere 0 at distance 0.5: rejected
+    bad = xyz.copy()
+    bad[3:6] = bad[0:3] + np.array([0.5, 0.0, 0.0])
+    with pytest.raises(E.EcmcError) as ei:
+        g.set_positions(bad, t0=10)
+    assert ei.value.code == E.ERR_OVERLAP
+    g.set_positions(xyz, t0=10)
+    g.sweep(2)
+    assert np.allclose(g.positions()[:3], g.positions()[:3])
+    g.close()
+
+
+def test_resume_from_positions_is_bitwise():
+    N, eta, cells = 512, 0.45, 4
+    g, p, L = make3(N, eta, cells, 1.0, 2, 4)
+    g.sweep(6)
+    ref = g.positions().copy()
+    g.close()
+    g, p, L = make3(N, eta, cells, 1.0, 2, 4)
+    g.sweep(3)
+    mid = g.positions().copy()
+    g.close()
+    g, p, L = make3(N, eta, cells, 1.0, 2, 4)
+    g.set_positions(mid, t0=3)
+    g.sweep(3)
+    assert np.array_equal(g.positions(), ref)
+    g.close()
+
+
+def test_pressure_has_an_error_bar_and_resets():
+    g, p, L = make3(1000, 0.3, 4, 2.0, 8, 6)
+    g.sweep(100)
+    P1, se = g.pressure()
+    assert se > 0.0 and P1 > 0.0
+    g.reset_stats()
+    with pytest.raises(E.EcmcError):
+        g.pressure()
+    g.close()

@@ -1,0 +1,187 @@
+"""Pins of the three-dimensional oracle (hard spheres; the generalisation of
+the sweep of Sec. 3.4 to cubic cells in 2x2x2 blocks).
+
+  - closed forms of single chains on hand-built frames: head-on lift, an
+    offset contact with the impact parameter split over both perpendicular
+    axes (s = b - sqrt(sigma^2 - c^2)), every axis and sign, spheres beside
+    and behind, a frozen sphere and a wall turning the chain back, ties;
+  - one sphere per cell with no contact possible: the chain's end is the
+    fold of x +- ell into [0, w], recomputed from Philox;
+  - the pressure against the virial series (B2 = 2 pi sigma^3 / 3,
+    B3 = 5/8 B2^2, B4 = 0.28695 B2^3) at eta = 0.05 and the Carnahan-Starling
+    equation at eta = 0.3;
+  - no overlap after dense sweeps; identical trajectories when the cells of
+    a colour are visited in reverse or the frozen set is taken from all
+    spheres; the colour order is a permutation of the eight colours.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import ecmc_workloads as W
+import oracle
+
+W_CELL = 10.0
+
+
+def chain(X, Y, Z, n_mem, m, axis, sign, ell, imgs=None, ids=None):
+    return oracle.run_chain_frame3(X, Y, Z, n_mem, m, axis, sign, ell, W_CELL, imgs=imgs,
+                                   ids=ids)
+
+
+def test_head_on_lift_along_z():
+    X, Y, Z, st, rec = chain([5, 5], [5, 5], [1.0, 3.5], 2, 0, 2, 1, 2.0)
+    assert Z.tolist() == [2.5, 4.0] and X.tolist() == [5, 5] and Y.tolist() == [5, 5]
+    assert st.events == 1 and st.lifts == 1 and rec["end_id"] == 1
+    assert st.sum_b == pytest.approx(1.0, abs=1e-15)
+
+
+def test_offset_contact_over_both_perpendicular_axes():
+    # c^2 = 0.36^2 + 0.48^2 = 0.36: contact after b - sqrt(1 - 0.36) = 3 - 0.8
+    X, Y, Z, st, rec = chain([5.0, 5.36], [5.0, 5.48], [1.0, 4.0], 2, 0, 2, 1, 3.0)
+    assert Z[0] == pytest.approx(3.2, abs=1e-14) and Z[1] == pytest.approx(4.8, abs=1e-14)
+    assert st.sum_b == pytest.approx(0.8, abs=1e-14)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+@pytest.mark.parametrize("sign", [1, -1])
+def test_every_axis_and_sign(axis, sign):
+    A = [5.0, 5.0, 5.0]
+    B = [5.0, 5.0, 5.0]
+    B[axis] += sign * 2.5
+    C = [list(v) for v in zip(A, B)]
+    X, Y, Z, st, _ = chain(C[0], C[1], C[2], 2, 0, axis, sign, 2.0)
+    out = [X, Y, Z]
+    assert out[axis][0] == 5.0 + sign * 1.5 and out[axis][1] == 5.0 + sign * 3.0
+    assert st.lifts == 1
+
+
+def test_beside_and_behind_are_not_hit():
+    # sphere 1 beside (c = sigma exactly: no hit), sphere 2 behind
+    X, Y, Z, st, _ = chain([5, 6, 5], [5, 5, 5], [2, 4, 1.5], 3, 0, 2, 1, 2.0)
+    assert Z.tolist() == [4.0, 4.0, 1.5] and st.events == 0
+
+
+def test_frozen_sphere_turns_the_chain_back():
+    # member at z = 3, frozen sphere at z = 5.5: contact after 1.5, back 1.0
+    X, Y, Z, st, _ = chain([5, 5], [5, 5], [3.0, 5.5], 1, 0, 2, 1, 2.5)
+    assert Z[0] == 3.5 and st.frozen_hits == 1 and st.events == 1
+    assert st.sum_b == pytest.approx(1.0, abs=1e-15)
+
+
+def test_wall_turns_the_chain_back():
+    X, Y, Z, st, _ = chain([8.5], [5.0], [5.0], 1, 0, 0, 1, 4.0)
+    assert X[0] == 10.0 - 2.5 and st.wall_hits == 1 and st.events == 0
+
+
+def test_equal_distance_tie_takes_smaller_key():
+    # two members at the same hit distance (offsets +-0.25 in x): the one
+    # with the smaller key (id 3) is lifted and carries the rest of the budget
+    X, Y, Z, st, rec = chain([5, 5.25, 4.75], [5, 5, 5], [2, 4, 4], 3, 0, 2, 1, 1.5,
+                             ids=[0, 5, 3])
+    assert st.lifts == 1 and rec["end_id"] == 3
+    assert Z[1] == 4.0 and Z[2] > 4.0
+
+
+def fold(u, w):
+    u = u % (2 * w)
+    return 2 * w - u if u > w else u
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_one_sphere_per_cell_folds(seed):
+    # 2x2x2 cells of side 5 without shift; sweep 0 runs along x.  Spheres
+    # of x-neighbouring cells differ by 2 in y, so no contact is possible
+    L, ell = 10.0, 7.3
+    rng = np.random.default_rng(seed)
+    x, y, z = [], [], []
+    cells = []
+    for cz in (0, 1):
+        for cy in (0, 1):
+            for cx in (0, 1):
+                x.append(5.0 * cx + rng.uniform(0.2, 4.8))
+                y.append(5.0 * cy + 0.5 + 2.0 * cx + rng.uniform(0, 0.5))
+                z.append(5.0 * cz + 2.5)
+                cells.append((cz * 2 + cy) * 2 + cx)
+    x, y, z = np.array(x), np.array(y), np.array(z)
+    p = oracle.make_params3(8, L, 1.0, 2, ell, 1, 50 + seed, flags=oracle.FLAG_NO_SHIFT)
+    xe = x.copy()
+    for i in range(8):
+        v = oracle.philox([0, 1, cells[i], 0], [50 + seed, 0])
+        sg = -1.0 if (v[1] >> 63) else 1.0
+        cx = int(x[i] // 5.0)
+        xe[i] = 5.0 * cx + fold(x[i] - 5.0 * cx + sg * ell, 5.0)
+    xx, yy, zz = x.copy(), y.copy(), z.copy()
+    st, _ = oracle.sweeps3(p, xx, yy, zz, 0, 1)
+    assert st.events == 0 and st.chains == 8
+    np.testing.assert_allclose(xx, xe, rtol=0, atol=1e-12)
+    assert yy.tolist() == y.tolist() and zz.tolist() == z.tolist()
+
+
+def pressure_batches(N, eta, cells, ell, nm, melt, nbatch, per_batch, seed):
+    L = W.box_side3(N, eta)
+    x, y, z = W.cubic_lattice(N, L)
+    p = oracle.make_params3(N, L, 1.0, cells, ell, nm, seed)
+    oracle.sweeps3(p, x, y, z, 0, melt)
+    vals = []
+    t = melt
+    for _ in range(nbatch):
+        st, _ = oracle.sweeps3(p, x, y, z, t, per_batch)
+        t += per_batch
+        vals.append(st.sum_b_w / st.sum_disp_w)  # beta P / rho - 1
+    vals = np.array(vals)
+    return 1.0 + vals.mean(), vals.std(ddof=1) / math.sqrt(nbatch), L
+
+
+def test_low_density_pressure_matches_virial_series():
+    N, eta = 1000, 0.05
+    z, se, L = pressure_batches(N, eta, 4, 3.0, 20, 20, 20, 40, 3)
+    B2 = 2.0 * math.pi / 3.0
+    rho = N / L**3
+    virial = 1.0 + B2 * rho + 0.625 * (B2 * rho) ** 2 + 0.28695 * (B2 * rho) ** 3
+    assert abs(z - virial) < 3.5 * se + 1e-3, (z, virial, se)
+
+
+def test_moderate_density_pressure_matches_carnahan_starling():
+    N, eta = 512, 0.30
+    z, se, L = pressure_batches(N, eta, 2, 2.0, 30, 50, 20, 25, 4)
+    cs = (1 + eta + eta**2 - eta**3) / (1 - eta) ** 3
+    assert abs(z - cs) < 3.5 * se + 0.004 * cs, (z, cs, se)
+
+
+def test_dense_sweeps_keep_spheres_apart():
+    N, eta = 512, 0.50
+    L = W.box_side3(N, eta)
+    x, y, z = W.cubic_lattice(N, L)
+    p = oracle.make_params3(N, L, 1.0, 2, 1.0, 20, 5)
+    st, _ = oracle.sweeps3(p, x, y, z, 0, 30)
+    assert st.events > 10000 and st.frozen_hits > 0 and st.wall_hits > 0
+    assert oracle.min_dist2_3(L, x, y, z) >= 1.0 - 1e-12
+
+
+@pytest.mark.parametrize("flag", [oracle.FLAG_REVERSE_CELLS, oracle.FLAG_BRUTE_FROZEN])
+def test_cell_order_and_frozen_set_do_not_change_the_trajectory(flag):
+    N, eta = 216, 0.45
+    L = W.box_side3(N, eta)
+    a = W.cubic_lattice(N, L)
+    b = [v.copy() for v in a]
+    a = [v.copy() for v in a]
+    p = oracle.make_params3(N, L, 1.0, 2, 1.5, 6, 9)
+    q = oracle.make_params3(N, L, 1.0, 2, 1.5, 6, 9, flags=flag)
+    sa, _ = oracle.sweeps3(p, *a, 0, 8)
+    sb, _ = oracle.sweeps3(q, *b, 0, 8)
+    for u, v in zip(a, b):
+        assert u.tolist() == v.tolist()
+    assert sa.events == sb.events and sa.sum_b == sb.sum_b
+
+
+def test_colour_orders_are_permutations():
+    p = oracle.make_params3(8, 10.0, 1.0, 2, 1.0, 1, 3)
+    seen = set()
+    for t in range(200):
+        sh, perm = oracle.sweep_draws3(p, t)
+        assert sorted(perm) == list(range(8))
+        assert all(0.0 <= s < 5.0 for s in sh)
+        seen.add(tuple(perm))
+    assert len(seen) > 190  # 8! orders: repeats are rare
