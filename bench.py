@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--fig3", action="store_true",
                     help="g(r) near contact and P(g(sigma+)) vs n_m: reflecting and rejecting "
                          "boundary rules, start lists with and without replacement")
+    ap.add_argument("--dim3", action="store_true",
+                    help="hard spheres in three dimensions: events/s over cells x ell (N = 64^3)")
     ap.add_argument("--grid", action="store_true",
                     help="parallelisation grid at N = 1M (cells x ell), one JSON line")
     ap.add_argument("--paper-params", action="store_true",
@@ -451,6 +453,75 @@ def run_fig3(args):
             pw[1]["difference_in_combined_se"] = d / math.hypot(pw[0]["stderr"], pw[1]["stderr"])
     print(json.dumps({"mode": "fig3", "workload": "N=65536 eta=0.708 cells=32x32",
                       "points": pts}))
+    return 0
+
+
+def run_dim3(args):
+    """Hard spheres in three dimensions (the generalisation of Sec. 3.4;
+    include/ecmc3.h): N = 64^3 spheres at eta = 0.45 (dense liquid) from the
+    simple cubic lattice, for a small grid of cells per side and chain
+    displacements ell, n_m chosen so that a sweep displaces about every
+    sphere once (eq. nm with the mean free path measured at this density).
+    Each point melts 30 sweeps and times --steps sweeps with CUDA events on
+    the library's stream.  The 3D oracle is timed on a bounded sample of the
+    first point on one host core."""
+    import torch
+
+    import oracle
+    import paper_1409_6948_gb300 as P
+    from paper_1409_6948_gb300 import ecmc as E
+
+    torch.cuda.set_device(0)
+    N, eta, seed = 262144, 0.45, 7
+    L = W.box_side3(N, eta)
+    lam0 = 0.06  # mean free path at eta = 0.45 (the points report their own)
+    pts = []
+    for cells in (16, 20, 26):
+        for ell in (0.5, 1.0, 2.0):
+            nm = max(1, int(round(N / cells**3 * lam0 / ell)))
+            g = P.Ecmc3(N, L, 1.0, cells, ell, seed)
+            g.set_param(E.PARAM3_N_CHAINS, nm)
+            s = torch.cuda.Stream()
+            g.set_stream(s)
+            g.sweep(30)
+            g.reset_stats()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            g.sweep(args.steps)
+            b.record(s)
+            g.synchronize()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            c = g.counters()
+            iters = c.events + c.wall_hits + c.chains
+            pt = {"cells": cells, "ell": ell, "n_m": nm, "sweeps": args.steps,
+                  "events_per_s": c.events / (ms * 1e-3), "sweeps_per_s": args.steps / (ms * 1e-3),
+                  "ms_per_sweep": ms / args.steps, "events_per_sweep": c.events / args.steps,
+                  "mean_free_path": c.sum_disp / max(iters, 1),
+                  "betaP_sigma3": g.pressure()[0]}
+            pts.append(pt)
+            print(json.dumps(pt), flush=True)
+            g.set_stream(None)
+            g.close()
+    # the oracle on the first point's workload, one host core, bounded sample
+    p0 = pts[0]
+    x, y, z = W.cubic_lattice(N, L)
+    p = oracle.make_params3(N, L, 1.0, p0["cells"], p0["ell"], p0["n_m"], seed)
+    oracle.sweeps3(p, x, y, z, 0, 2)
+    t0 = time.perf_counter()
+    n = 0
+    st = oracle.Stats()
+    while time.perf_counter() - t0 < args.cpu_seconds and n < 50:
+        oracle.sweeps3(p, x, y, z, 2 + n, 1, stats=st)
+        n += 1
+    dt = time.perf_counter() - t0
+    best = max(pts, key=lambda q: q["events_per_s"])
+    print(json.dumps({"mode": "dim3", "workload": "N=262144 (64^3) hard spheres eta=0.45",
+                      "best": best, "points": pts,
+                      "cpu_baseline": {"value": st.events / dt, "unit": "events/s", "cores": 1,
+                                       "kind": "oracle",
+                                       "sample": "%d sweeps of the first point (%.1f s)"
+                                                 % (n, dt)}}))
     return 0
 
 
@@ -902,6 +973,8 @@ def main():
         return run_listbias(args)
     if args.fig3:
         return run_fig3(args)
+    if args.dim3:
+        return run_dim3(args)
     if args.tau:
         return run_tau(args)
     return run_ours(args)

@@ -7,10 +7,13 @@
 // k3_phase gives one warp to one active cell: the warp sorts the cell's
 // members by id, gathers the members and every periodic image of the 26
 // neighbour cells' spheres within sigma of the cell into a shared-memory
-// frame, then runs the cell's n_m chains.  Each event is one warp-wide pass
-// over the frame: 32 lanes test candidates in FP64 with the oracle's
-// expressions (no contraction: the library is built with -fmad=false), and a
-// shuffle reduction picks the first hit by (distance, key).  Positions live
+// frame (FP64 coordinates and their FP32 roundings), then runs the cell's
+// n_m chains.  Each event is one warp-wide pass over the frame: 32 lanes
+// screen candidates in FP32 with a rigorous margin (a sphere behind the
+// mover or with perpendicular offset >= sigma cannot be hit), test the
+// survivors in FP64 with the oracle's expressions (no contraction: the
+// library is built with -fmad=false), and a shuffle reduction picks the
+// first hit by (distance, key).  Positions live
 // in sphere-id order; a cell reads its frozen neighbours' positions, which
 // no other warp of the same launch writes.
 #include <cmath>
@@ -46,6 +49,17 @@ struct Geom3 {
   uint64_t seed, replica;
   int cap_mem, cap_obj;  // bucket slots per cell; frame objects per cell
   int warp_bytes;        // shared memory of one warp's frame
+  // FP32 screen: frame coordinates lie in (-sigma, w + sigma) and round to
+  // FP32 with error <= 2^-24 M (M >= w + sigma), so FP32 differences are
+  // within d = 4 2^-24 M of the FP64 ones; a hit (b > 0, c^2 < sigma^2)
+  // then has b32 > -d and c2_32 < sigma^2 + 4 d sigma + 2 d^2 + FP32
+  // rounding; the thresholds below are twice those bounds
+  float scr_b;           // pass iff b32 > -scr_b
+  float scr_c2;          // pass iff c2_32 < scr_c2
+  // L >= 2 (w + sigma): a periodic image X0 +- L of a wrapped coordinate
+  // X0 in [-L/2, L/2) lies outside (-sigma, w + sigma), so only the
+  // unshifted image can enter a frame
+  int single_image;
 };
 
 struct State3 {
@@ -136,10 +150,15 @@ __global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
   C[1] = C[0] + g.cap_obj;
   C[2] = C[1] + g.cap_obj;
   long long* key = reinterpret_cast<long long*>(C[2] + g.cap_obj);
-  int* sid = reinterpret_cast<int*>(key + g.cap_obj);  // members sorted by id
+  float* F[3];  // FP32 roundings of C, kept current as members move
+  F[0] = reinterpret_cast<float*>(key + g.cap_obj);
+  F[1] = F[0] + g.cap_obj;
+  F[2] = F[1] + g.cap_obj;
+  int* sid = reinterpret_cast<int*>(F[2] + g.cap_obj);  // members sorted by id
   int* raw = sid + g.cap_mem;                           // members as bucketed
   int* nbl = raw + g.cap_mem;                           // 26 neighbour cells + count
-  unsigned char* touched = reinterpret_cast<unsigned char*>(nbl + 28);
+  int* cand = nbl + 28;                                 // FP32 screen survivors
+  unsigned char* touched = reinterpret_cast<unsigned char*>(cand + g.cap_obj);
 
   const int nmem = min(cnt[c], g.cap_mem);
   for (int k = lane; k < nmem; k += 32) raw[k] = ids[(int64_t)c * g.cap_mem + k];
@@ -174,6 +193,9 @@ __global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
     C[0][q] = wrap_half(px[i] - o[0], L);
     C[1][q] = wrap_half(py[i] - o[1], L);
     C[2][q] = wrap_half(pz[i] - o[2], L);
+    F[0][q] = (float)C[0][q];
+    F[1][q] = (float)C[1][q];
+    F[2][q] = (float)C[2][q];
     key[q] = (long long)i * 27 + 13;
   }
   // frozen images, appended in lane order (warp prefix sums)
@@ -193,6 +215,10 @@ __global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
         X0[0] = wrap_half(px[id] - o[0], L);
         X0[1] = wrap_half(py[id] - o[1], L);
         X0[2] = wrap_half(pz[id] - o[2], L);
+        if (g.single_image) {
+          if (X0[0] > lo && X0[0] < hi && X0[1] > lo && X0[1] < hi && X0[2] > lo && X0[2] < hi)
+            mask = 1u << 13;
+        } else {
         for (int kx = -1; kx <= 1; ++kx) {
           const double X = X0[0] + (double)kx * L;
           if (!(X > lo && X < hi)) continue;
@@ -205,6 +231,7 @@ __global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
               mask |= 1u << ((kx + 1) * 9 + (ky + 1) * 3 + (kz + 1));
             }
           }
+        }
         }
       }
       const int nimg = __popc(mask);
@@ -223,6 +250,9 @@ __global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
           C[0][slot] = X0[0] + (double)kx * L;
           C[1][slot] = X0[1] + (double)ky * L;
           C[2][slot] = X0[2] + (double)kz * L;
+          F[0][slot] = (float)C[0][slot];
+          F[1][slot] = (float)C[1][slot];
+          F[2][slot] = (float)C[2][slot];
           key[slot] = (long long)id * 27 + img;
         }
         ++slot;
@@ -235,10 +265,13 @@ __global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
   __syncwarp();
 
   // the cell's chains
-  const int ax = st.axis;
+  const int ax = st.axis, axp = ax == 0 ? 1 : 0, axq = ax == 2 ? 1 : 2;
   double* CA = C[ax];
-  double* CP = C[ax == 0 ? 1 : 0];
-  double* CQ = C[ax == 2 ? 1 : 2];
+  double* CP = C[axp];
+  double* CQ = C[axq];
+  float* FA = F[ax];
+  const float* FP = F[axp];
+  const float* FQ = F[axq];
   const double INF = __longlong_as_double(0x7ff0000000000000ll);
   double sum_b = 0.0;
   int n_ev = 0, n_li = 0, n_fr = 0, n_wa = 0, n_ch = 0;
@@ -269,13 +302,31 @@ __global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
       }
       __syncwarp();
       const double P = CA[m], Pp = CP[m], Pq = CQ[m];
+      const float P32 = FA[m], Pp32 = FP[m], Pq32 = FQ[m];
       double sw = sg > 0 ? w - P : P;
       if (sw < 0.0) sw = 0.0;
       double bs = INF, bb = 0.0;
       long long bk = LLONG_MAX;
       int bj = -1;
-      for (int j = lane; j < nobj; j += 32) {
-        if (j == m) continue;
+      // FP32 screen of the whole frame, survivors compacted into cand[] so
+      // that the FP64 tests below take one warp-wide pass
+      int ns = 0;
+      for (int j0 = 0; j0 < nobj; j0 += 32) {
+        const int j = j0 + lane;
+        bool pass = false;
+        if (j < nobj && j != m) {
+          const float da32 = FA[j] - P32;
+          const float dp32 = FP[j] - Pp32, dq32 = FQ[j] - Pq32;
+          pass = ((sg > 0 ? da32 : -da32) > -g.scr_b) &&
+                 (dp32 * dp32 + dq32 * dq32 < g.scr_c2);
+        }
+        const unsigned bal = __ballot_sync(FULL, pass);
+        if (pass) cand[ns + __popc(bal & ((1u << lane) - 1u))] = j;
+        ns += __popc(bal);
+      }
+      __syncwarp();
+      for (int t = lane; t < ns; t += 32) {
+        const int j = cand[t];
         const double da = CA[j] - P;
         const double b = sg > 0 ? da : -da;
         if (!(b > 0.0)) continue;
@@ -308,11 +359,17 @@ __global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
       }
       __syncwarp();
       if (r <= bs && r <= sw) {  // budget used up
-        if (lane == 0) CA[m] = P + (sg > 0 ? r : -r);
+        if (lane == 0) {
+          CA[m] = P + (sg > 0 ? r : -r);
+          FA[m] = (float)CA[m];
+        }
         break;
       }
       if (bs <= sw) {  // contact
-        if (lane == 0) CA[m] = P + (sg > 0 ? bs : -bs);
+        if (lane == 0) {
+          CA[m] = P + (sg > 0 ? bs : -bs);
+          FA[m] = (float)CA[m];
+        }
         r = r - bs;
         ++n_ev;
         ++ch_ev;
@@ -326,7 +383,10 @@ __global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
           ++n_fr;
         }
       } else {  // wall: onto the wall, back along the axis
-        if (lane == 0) CA[m] = sg > 0 ? w : 0.0;
+        if (lane == 0) {
+          CA[m] = sg > 0 ? w : 0.0;
+          FA[m] = (float)CA[m];
+        }
         r = r - sw;
         sg = -sg;
         ++n_wa;
@@ -641,7 +701,8 @@ void free3(ecmc3_ctx* h) {
 // shared memory of one warp's frame, and the launch's warps per block
 int layout3(ecmc3_ctx* h) {
   Geom3& g = h->g;
-  g.warp_bytes = (int)(((size_t)g.cap_obj * (3 * sizeof(double) + sizeof(long long)) +
+  g.warp_bytes = (int)(((size_t)g.cap_obj * (3 * sizeof(double) + sizeof(long long) +
+                                             3 * sizeof(float) + sizeof(int)) +
                         (size_t)g.cap_mem * 2 * sizeof(int) + 28 * sizeof(int) +
                         (size_t)g.cap_mem + 15) &
                        ~(size_t)15);
@@ -695,6 +756,15 @@ int ecmc3_create(ecmc3_t* out, int64_t N, double L, double sigma, int cells, dou
   g.n_m = 1;
   g.seed = seed;
   g.replica = 0;
+  {
+    const double M = g.w + 2.0 * sigma;
+    const double d = 4.0 * std::ldexp(1.0, -24) * M;
+    g.scr_b = (float)(2.0 * d);
+    const double c2 = sigma * sigma + 4.0 * d * sigma + 2.0 * d * d +
+                      4.0 * std::ldexp(1.0, -24) * (sigma * sigma + 4.0 * M * M);
+    g.scr_c2 = std::nextafter((float)(sigma * sigma + 2.0 * (c2 - sigma * sigma)), 1e30f);
+  }
+  g.single_image = L >= 2.0 * (g.w + sigma) ? 1 : 0;
   g.cap_mem = sphere_bound(g.w, sigma);
   g.cap_obj = sphere_bound(g.w + 2.0 * sigma, sigma);
   if ((int64_t)g.cap_mem > N) g.cap_mem = (int)N;
