@@ -105,6 +105,11 @@ struct ecmc_ctx {
   int* int_tmp = nullptr;
   unsigned long long* u64_tmp = nullptr;
   UndoEntry* undo = nullptr;  // rejecting boundary rule: [C_total][cap] undo logs
+  // pinned staging for the small copies of ecmc_set_positions, so that the
+  // whole load (states up, binning, overlap check, result down) needs one
+  // synchronisation
+  SweepState* pin_states = nullptr;       // [R]
+  unsigned long long* pin_bits = nullptr;  // [2]: initial and resulting minimum
 };
 
 namespace {
@@ -424,45 +429,56 @@ int check_device_error(ecmc_ctx* h) {
   return ECMC_OK;
 }
 
-// smallest pair distance squared over all replicas (pairs closer than 2 sigma)
-int min_dist2(ecmc_ctx* h, double* d2) {
+// smallest pair distance squared over all replicas (pairs closer than 2
+// sigma), enqueued: the result lands in pin_bits[1] once the stream has
+// passed it
+int enqueue_min_dist2(ecmc_ctx* h) {
   double sig_max = 0.0;
   for (const Geom& g : h->geo) sig_max = g.sigma > sig_max ? g.sigma : sig_max;
-  unsigned long long init = 0;
   const double r2 = 4.0 * sig_max * sig_max;
-  std::memcpy(&init, &r2, sizeof(r2));
-  CK(cudaMemcpyAsync(h->u64_tmp, &init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
+  std::memcpy(&h->pin_bits[0], &r2, sizeof(r2));
+  CK(cudaMemcpyAsync(h->u64_tmp, &h->pin_bits[0], sizeof(unsigned long long),
+                     cudaMemcpyHostToDevice, h->stream));
   for (const Geom& g : h->geo) launch_min_dist(g, h->b, 2.0 * g.sigma, h->u64_tmp, h->stream);
-  unsigned long long bits = 0;
-  CK(cudaMemcpyAsync(&bits, h->u64_tmp, sizeof(bits), cudaMemcpyDeviceToHost, h->stream));
-  int rc = check_device_error(h);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(&h->pin_bits[1], h->u64_tmp, sizeof(unsigned long long),
+                     cudaMemcpyDeviceToHost, h->stream));
+  return ECMC_OK;
+}
+
+int min_dist2(ecmc_ctx* h, double* d2) {
+  int rc = enqueue_min_dist2(h);
   if (rc) return rc;
-  std::memcpy(d2, &bits, sizeof(*d2));
+  rc = check_device_error(h);
+  if (rc) return rc;
+  std::memcpy(d2, &h->pin_bits[1], sizeof(*d2));
   return ECMC_OK;
 }
 
 int load_positions_dev(ecmc_ctx* h, const double* xy_dev, int64_t t0) {
   launch_load_flat(h->b, xy_dev, h->stream);
-  std::vector<SweepState> st(h->b.R);
-  for (auto& v : st) {
+  for (int r = 0; r < h->b.R; ++r) {
+    SweepState& v = h->pin_states[r];
     std::memset(&v, 0, sizeof(v));
     v.t = t0;
     v.history_len = h->hist_len_host;
   }
-  CK(cudaMemcpyAsync(h->b.state, st.data(), sizeof(SweepState) * st.size(),
+  CK(cudaMemcpyAsync(h->b.state, h->pin_states, sizeof(SweepState) * (size_t)h->b.R,
                      cudaMemcpyHostToDevice, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
   launch_sweep_begin(h->b, h->stream);
   launch_bin(h->b, -1, h->b.cur, h->stream);
   CK(cudaGetLastError());
   h->t_host = t0;
   h->valid_state = true;
-  int rc = check_device_error(h);
+  // the overlap check follows in the same stream; one synchronisation reports
+  // a binning error and delivers the smallest distance
+  int rc = enqueue_min_dist2(h);
   if (rc) return rc;
-  // no two disks may overlap beyond rounding
+  rc = check_device_error(h);
+  if (rc) return rc;
   double d2 = 0.0;
-  rc = min_dist2(h, &d2);
-  if (rc) return rc;
+  std::memcpy(&d2, &h->pin_bits[1], sizeof(d2));
+  // no two disks may overlap beyond rounding
   double sig2_min = 1e300;
   for (const Geom& g : h->geo) sig2_min = g.sig2 < sig2_min ? g.sig2 : sig2_min;
   if (d2 < sig2_min * (1.0 - 1e-9)) {
@@ -530,6 +546,8 @@ void free_all(ecmc_ctx* h) {
   cudaFree(h->int_tmp);
   cudaFree(h->u64_tmp);
   cudaFree(h->undo);
+  cudaFreeHost(h->pin_states);
+  cudaFreeHost(h->pin_bits);
   for (auto& e : h->pending) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
@@ -691,7 +709,9 @@ int create_impl(ecmc_t* out, const ecmc_replica_desc_t* desc, int R) {
       cudaMalloc(&h->d_partials, sizeof(ChunkSums) * h->chunks.size()) != cudaSuccess ||
       cudaMalloc(&h->xy_tmp, sizeof(double) * 2 * (size_t)N_total) != cudaSuccess ||
       cudaMalloc(&h->int_tmp, sizeof(int) * (size_t)N_total) != cudaSuccess ||
-      cudaMalloc(&h->u64_tmp, sizeof(unsigned long long) * 4) != cudaSuccess)
+      cudaMalloc(&h->u64_tmp, sizeof(unsigned long long) * 4) != cudaSuccess ||
+      cudaMallocHost(&h->pin_states, sizeof(SweepState) * R) != cudaSuccess ||
+      cudaMallocHost(&h->pin_bits, sizeof(unsigned long long) * 2) != cudaSuccess)
     return bail(fail(ECMC_ERR_OOM, "device allocation failed"));
   cudaMemsetAsync(b.totals, 0, sizeof(RunTotals) * R, h->stream);
   cudaMemsetAsync(b.err, 0, sizeof(int), h->stream);

@@ -143,3 +143,19 @@ def test_pressure_has_an_error_bar_and_resets():
     with pytest.raises(E.EcmcError):
         g.pressure()
     g.close()
+
+
+def test_pressure_matches_carnahan_starling():
+    # the CUDA path's own sampling at scale (not only its parity): eta = 0.3,
+    # where the Carnahan-Starling equation is accurate to about 0.1 %
+    N, eta = 4096, 0.30
+    g, p, L = make3(N, eta, 6, 2.0, 20, 12)
+    g.sweep(300)
+    g.reset_stats()
+    g.sweep(3000)
+    P3, se = g.pressure()
+    rho = N / L**3
+    z, zse = P3 / rho, se / rho
+    cs = (1 + eta + eta**2 - eta**3) / (1 - eta) ** 3
+    assert abs(z - cs) < 4.0 * zse + 0.003 * cs, (z, cs, zse)
+    g.close()
