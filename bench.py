@@ -494,11 +494,22 @@ def run_dim3(args):
             ms = a.elapsed_time(b)
             c = g.counters()
             iters = c.events + c.wall_hits + c.chains
+            # FP64 pipe: 13 algorithmic operations per event-loop iteration
+            # (hit test of the first candidate: da, dp, dq, dp^2, dq^2, c^2,
+            # sigma^2 - c^2, b - sqrt; update: wall distance, new position,
+            # new budget, b - s and its sum), against the peak of 2 FP64
+            # lanes/clock/SM x SMs x the clock
+            n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+            peak = 2 * n_sm * 2070e6 / 1e9
+            achieved = 13 * iters / (ms * 1e-3) / 1e9
             pt = {"cells": cells, "ell": ell, "n_m": nm, "sweeps": args.steps,
                   "events_per_s": c.events / (ms * 1e-3), "sweeps_per_s": args.steps / (ms * 1e-3),
                   "ms_per_sweep": ms / args.steps, "events_per_sweep": c.events / args.steps,
                   "mean_free_path": c.sum_disp / max(iters, 1),
-                  "betaP_sigma3": g.pressure()[0]}
+                  "betaP_sigma3": g.pressure()[0],
+                  "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved,
+                               "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
+                               "fp64_ops_per_iteration": 13}}
             pts.append(pt)
             print(json.dumps(pt), flush=True)
             g.set_stream(None)

@@ -13,7 +13,10 @@
 // mover or with perpendicular offset >= sigma cannot be hit), test the
 // survivors in FP64 with the oracle's expressions (no contraction: the
 // library is built with -fmad=false), and a shuffle reduction picks the
-// first hit by (distance, key).  Positions live
+// first hit by (distance, key).  As in the two-dimensional loop, the
+// comparisons of FP64 values and the square root run on the integer pipes
+// (bit-pattern orders, the correctly rounded sqrt_rn), which give the same
+// results as the FP64 instructions and leave the FP64 pipe the arithmetic.  Positions live
 // in sphere-id order; a cell reads its frozen neighbours' positions, which
 // no other warp of the same launch writes.
 #include <cmath>
@@ -33,10 +36,18 @@ namespace ecmc3 {
 using ecmc::U64x4;
 using ecmc::below_n;
 using ecmc::cell_1d;
+using ecmc::clamp0;
+using ecmc::dbits;
+using ecmc::dlt;
+using ecmc::flip_if;
+using ecmc::le_nn;
+using ecmc::lt_nn;
 using ecmc::philox;
+using ecmc::sqrt_rn;
 using ecmc::unit_double;
 using ecmc::wrap_box0;
 using ecmc::wrap_half;
+using ecmc::wrap_half_i;
 
 constexpr int kOk = 0, kCapacity = 1, kChainCap = 2;
 constexpr int kWarpsMax = 4;
@@ -120,8 +131,10 @@ __global__ void k3_bin(Geom3 g, const State3* __restrict__ st, const double* __r
   else atomicCAS(err, kOk, kCapacity);
 }
 
+// (s, key) before (bs, bk) for hit distances s, bs >= +0 (or +inf): the
+// bit patterns compare like the values
 __device__ __forceinline__ bool first_before(double s, long long k, double bs, long long bk) {
-  return s < bs || (s == bs && k < bk);
+  return lt_nn(s, bs) || (dbits(s) == dbits(bs) && k < bk);
 }
 
 __global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
@@ -188,11 +201,12 @@ __global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
     touched[r] = 0;
   }
   __syncwarp();
+  const double hL = 0.5 * L;
   for (int q = lane; q < nmem; q += 32) {
     const int i = sid[q];
-    C[0][q] = wrap_half(px[i] - o[0], L);
-    C[1][q] = wrap_half(py[i] - o[1], L);
-    C[2][q] = wrap_half(pz[i] - o[2], L);
+    C[0][q] = wrap_half_i(px[i] - o[0], L, hL);
+    C[1][q] = wrap_half_i(py[i] - o[1], L, hL);
+    C[2][q] = wrap_half_i(pz[i] - o[2], L, hL);
     F[0][q] = (float)C[0][q];
     F[1][q] = (float)C[1][q];
     F[2][q] = (float)C[2][q];
@@ -212,11 +226,12 @@ __global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
       unsigned mask = 0u;  // bit img = (kx+1)*9 + (ky+1)*3 + (kz+1)
       if (k < nq) {
         id = ids[(int64_t)q * g.cap_mem + k];
-        X0[0] = wrap_half(px[id] - o[0], L);
-        X0[1] = wrap_half(py[id] - o[1], L);
-        X0[2] = wrap_half(pz[id] - o[2], L);
+        X0[0] = wrap_half_i(px[id] - o[0], L, hL);
+        X0[1] = wrap_half_i(py[id] - o[1], L, hL);
+        X0[2] = wrap_half_i(pz[id] - o[2], L, hL);
         if (g.single_image) {
-          if (X0[0] > lo && X0[0] < hi && X0[1] > lo && X0[1] < hi && X0[2] > lo && X0[2] < hi)
+          if (dlt(lo, X0[0]) && dlt(X0[0], hi) && dlt(lo, X0[1]) && dlt(X0[1], hi) &&
+              dlt(lo, X0[2]) && dlt(X0[2], hi))
             mask = 1u << 13;
         } else {
         for (int kx = -1; kx <= 1; ++kx) {
@@ -303,8 +318,7 @@ __global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
       __syncwarp();
       const double P = CA[m], Pp = CP[m], Pq = CQ[m];
       const float P32 = FA[m], Pp32 = FP[m], Pq32 = FQ[m];
-      double sw = sg > 0 ? w - P : P;
-      if (sw < 0.0) sw = 0.0;
+      const double sw = clamp0(sg > 0 ? w - P : P);
       double bs = INF, bb = 0.0;
       long long bk = LLONG_MAX;
       int bj = -1;
@@ -328,14 +342,15 @@ __global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
       for (int t = lane; t < ns; t += 32) {
         const int j = cand[t];
         const double da = CA[j] - P;
-        const double b = sg > 0 ? da : -da;
-        if (!(b > 0.0)) continue;
+        const double b = flip_if(da, sg < 0);
+        if (dbits(b) <= 0) continue;  // b > 0
         const double dp = CP[j] - Pp;
         const double dq = CQ[j] - Pq;
         const double c2 = dp * dp + dq * dq;
-        if (!(c2 < g.sig2)) continue;
-        double s = b - sqrt(g.sig2 - c2);
-        if (s < 0.0) s = 0.0;
+        if (!lt_nn(c2, g.sig2)) continue;
+        // sigma^2 - c^2 is a positive normal number here (sigma in
+        // [2^-40, 2^40]), as sqrt_rn requires
+        const double s = clamp0(b - sqrt_rn(g.sig2 - c2));
         const long long kj = key[j];
         if (first_before(s, kj, bs, bk)) {
           bs = s;
@@ -358,14 +373,14 @@ __global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
         }
       }
       __syncwarp();
-      if (r <= bs && r <= sw) {  // budget used up
+      if (le_nn(r, bs) && le_nn(r, sw)) {  // budget used up
         if (lane == 0) {
           CA[m] = P + (sg > 0 ? r : -r);
           FA[m] = (float)CA[m];
         }
         break;
       }
-      if (bs <= sw) {  // contact
+      if (le_nn(bs, sw)) {  // contact
         if (lane == 0) {
           CA[m] = P + (sg > 0 ? bs : -bs);
           FA[m] = (float)CA[m];
@@ -735,6 +750,9 @@ int ecmc3_create(ecmc3_t* out, int64_t N, double L, double sigma, int cells, dou
   if (k * k * k != N) return fail3(ECMC_ERR_ARG, "N must be a perfect cube (lattice start)");
   if (!(L > 0.0) || !(sigma > 0.0) || !std::isfinite(L) || !std::isfinite(sigma))
     return fail3(ECMC_ERR_ARG, "L and sigma must be positive");
+  if (!(sigma >= std::ldexp(1.0, -40) && sigma <= std::ldexp(1.0, 40) &&
+        L < std::ldexp(sigma, 40)))
+    return fail3(ECMC_ERR_ARG, "sigma must lie in [2^-40, 2^40] and L below 2^40 sigma");
   if (cells < 2 || (cells & 1) || cells > 1024)
     return fail3(ECMC_ERR_ARG, "cells per side must be even, >= 2 and <= 1024");
   if (!(L / (double)cells > sigma)) return fail3(ECMC_ERR_ARG, "cell side must exceed sigma");
