@@ -65,6 +65,8 @@ def parse():
                     choices=["small", "medium", "large", "huge", "batch", "eos"])
     ap.add_argument("--tau", action="store_true",
                     help="autocorrelation time of Psi against n_m and ell (N = 64^2)")
+    ap.add_argument("--tau-eta", type=float, default=0.704,
+                    help="packing fraction of the --tau experiment")
     ap.add_argument("--tau-max", type=int, default=20000,
                     help="most sweeps per point of the --tau experiment")
     ap.add_argument("--listbias", action="store_true",
@@ -539,7 +541,8 @@ def run_dim3(args):
 def run_tau(args):
     """Sampling efficiency (Sec. 2 eq. tau; Figs. 5-6): the autocorrelation
     time tau of the hexatic order parameter Psi for N = 64^2 disks at
-    eta = 0.704 in 4 x 4 cells (n = 4 blocks), for several chains per cell n_m
+    eta = --tau-eta (0.704, the paper's) in 4 x 4 cells (n = 4 blocks), for
+    several chains per cell n_m
     (ell = 1.28 sigma) and chain displacements ell (n_m from eq. nm).  Each
     point is a batch of 32 independent replicas (Philox key (8, r)) advanced
     together, melted by 1000 sweeps; Psi of every replica (Delaunay
@@ -554,7 +557,7 @@ def run_tau(args):
     from paper_1409_6948_gb300 import ecmc as E
 
     torch.cuda.set_device(0)
-    N, eta, cells, seed, R, every = 4096, 0.704, 4, 8, 32, 5
+    N, eta, cells, seed, R, every = 4096, args.tau_eta, 4, 8, 32, 5
     L = W.box_side(N, eta)
     lam0 = (W.ETA_HCP - eta) / (2 * W.ETA_HCP)
     pts = []
@@ -605,7 +608,7 @@ def run_tau(args):
         print(json.dumps(pt), flush=True)
         pts.append(pt)
         g.close()
-    print(json.dumps({"mode": "tau", "workload": "N=4096 eta=0.704 cells=4x4, 32 replicas",
+    print(json.dumps({"mode": "tau", "workload": "N=4096 eta=%g cells=4x4, 32 replicas" % eta,
                       "lambda0_eq": lam0, "points": pts}))
     return 0
 
