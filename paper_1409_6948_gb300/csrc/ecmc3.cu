@@ -71,6 +71,13 @@ struct Geom3 {
   // X0 in [-L/2, L/2) lies outside (-sigma, w + sigma), so only the
   // unshifted image can enter a frame
   int single_image;
+  // candidate bins across the chain axis: the frame's extent w + 2 sigma
+  // along each perpendicular axis is cut into nbin bins of side
+  // >= sigma (1 + 2^-12); a sphere the mover can hit (|dp|, |dq| < sigma)
+  // then lies in the mover's bin or a neighbour on both axes, also after
+  // the FP32 rounding of the coordinates the bin index is computed from
+  int nbin;
+  float inv_hb;          // 1 / bin side
 };
 
 struct State3 {
@@ -171,7 +178,11 @@ __global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
   int* raw = sid + g.cap_mem;                           // members as bucketed
   int* nbl = raw + g.cap_mem;                           // 26 neighbour cells + count
   int* cand = nbl + 28;                                 // FP32 screen survivors
-  unsigned char* touched = reinterpret_cast<unsigned char*>(cand + g.cap_obj);
+  int* ord = cand + g.cap_obj;                          // objects sorted by bin
+  const int nb = g.nbin, nb2 = nb * nb;
+  int* bst = ord + g.cap_obj;                           // bin starts, nb2 + 1
+  int* cur = bst + nb2 + 1;                             // scatter cursors, nb2
+  unsigned char* touched = reinterpret_cast<unsigned char*>(cur + nb2);
 
   const int nmem = min(cnt[c], g.cap_mem);
   for (int k = lane; k < nmem; k += 32) raw[k] = ids[(int64_t)c * g.cap_mem + k];
@@ -279,8 +290,30 @@ __global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
   if (!ok && lane == 0) atomicCAS(err, kOk, kCapacity);
   __syncwarp();
 
-  // the cell's chains
+  // bins across the sweep's axis (members move only along it, so the bins
+  // hold for the whole phase): counting sort of the objects, q-major
   const int ax = st.axis, axp = ax == 0 ? 1 : 0, axq = ax == 2 ? 1 : 2;
+  const float sigf = (float)g.sigma;
+  auto bin_of = [&](float v) {
+    const int b = (int)((v + sigf) * g.inv_hb);
+    return b < 0 ? 0 : (b >= nb ? nb - 1 : b);
+  };
+  const int nobj_ok = ok ? nobj : 0;
+  for (int i = lane; i <= nb2; i += 32) bst[i] = 0;
+  __syncwarp();
+  for (int o2 = lane; o2 < nobj_ok; o2 += 32)
+    atomicAdd(&bst[1 + bin_of(F[axq][o2]) * nb + bin_of(F[axp][o2])], 1);
+  __syncwarp();
+  if (lane == 0)
+    for (int i = 1; i <= nb2; ++i) bst[i] += bst[i - 1];
+  __syncwarp();
+  for (int i = lane; i < nb2; i += 32) cur[i] = bst[i];
+  __syncwarp();
+  for (int o2 = lane; o2 < nobj_ok; o2 += 32)
+    ord[atomicAdd(&cur[bin_of(F[axq][o2]) * nb + bin_of(F[axp][o2])], 1)] = o2;
+  __syncwarp();
+
+  // the cell's chains
   double* CA = C[ax];
   double* CP = C[axp];
   double* CQ = C[axq];
@@ -322,13 +355,31 @@ __global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
       double bs = INF, bb = 0.0;
       long long bk = LLONG_MAX;
       int bj = -1;
-      // FP32 screen of the whole frame, survivors compacted into cand[] so
-      // that the FP64 tests below take one warp-wide pass
+      // candidates: the three rows of bins around the mover, each a
+      // contiguous run of ord[]; FP32 screen, survivors compacted into
+      // cand[] so that the FP64 tests below take one warp-wide pass
+      const int bpm = bin_of(Pp32), bqm = bin_of(Pq32);
+      const int plo = bpm > 0 ? bpm - 1 : 0, phi = bpm < nb - 1 ? bpm + 1 : nb - 1;
+      int rs[3], rl[3];
+#pragma unroll
+      for (int k3 = 0; k3 < 3; ++k3) {
+        const int row = bqm - 1 + k3;
+        const bool in = row >= 0 && row < nb;
+        rs[k3] = in ? bst[row * nb + plo] : 0;
+        rl[k3] = in ? bst[row * nb + phi + 1] - rs[k3] : 0;
+      }
+      const int n_c = rl[0] + rl[1] + rl[2];
       int ns = 0;
-      for (int j0 = 0; j0 < nobj; j0 += 32) {
-        const int j = j0 + lane;
+      for (int t0 = 0; t0 < n_c; t0 += 32) {
+        const int t = t0 + lane;
         bool pass = false;
-        if (j < nobj && j != m) {
+        int j = -1;
+        if (t < n_c) {
+          j = t < rl[0] ? ord[rs[0] + t]
+                        : (t < rl[0] + rl[1] ? ord[rs[1] + t - rl[0]]
+                                             : ord[rs[2] + t - rl[0] - rl[1]]);
+        }
+        if (t < n_c && j != m) {
           const float da32 = FA[j] - P32;
           const float dp32 = FP[j] - Pp32, dq32 = FQ[j] - Pq32;
           pass = ((sg > 0 ? da32 : -da32) > -g.scr_b) &&
@@ -717,7 +768,8 @@ void free3(ecmc3_ctx* h) {
 int layout3(ecmc3_ctx* h) {
   Geom3& g = h->g;
   g.warp_bytes = (int)(((size_t)g.cap_obj * (3 * sizeof(double) + sizeof(long long) +
-                                             3 * sizeof(float) + sizeof(int)) +
+                                             3 * sizeof(float) + 2 * sizeof(int)) +
+                        (size_t)(2 * g.nbin * g.nbin + 1) * sizeof(int) +
                         (size_t)g.cap_mem * 2 * sizeof(int) + 28 * sizeof(int) +
                         (size_t)g.cap_mem + 15) &
                        ~(size_t)15);
@@ -783,6 +835,14 @@ int ecmc3_create(ecmc3_t* out, int64_t N, double L, double sigma, int cells, dou
     g.scr_c2 = std::nextafter((float)(sigma * sigma + 2.0 * (c2 - sigma * sigma)), 1e30f);
   }
   g.single_image = L >= 2.0 * (g.w + sigma) ? 1 : 0;
+  {
+    const double ext = g.w + 2.0 * sigma;
+    int nb = (int)std::floor(ext / (sigma * (1.0 + std::ldexp(1.0, -12))));
+    if (nb < 1) nb = 1;
+    if (nb > 64) nb = 64;
+    g.nbin = nb;
+    g.inv_hb = (float)((double)nb / ext);
+  }
   g.cap_mem = sphere_bound(g.w, sigma);
   g.cap_obj = sphere_bound(g.w + 2.0 * sigma, sigma);
   if ((int64_t)g.cap_mem > N) g.cap_mem = (int)N;
