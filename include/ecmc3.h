@@ -45,6 +45,18 @@ typedef struct ecmc3_ctx* ecmc3_t;
 /* Parameters for ecmc3_set_param / ecmc3_get_param. */
 #define ECMC3_PARAM_N_CHAINS 1   /* chains per cell and sweep, n_m >= 1 (default 1) */
 #define ECMC3_PARAM_REPLICA 4    /* Philox key word 1 (default 0)                   */
+/* 1 (default): one persistent launch per sweep, in which each cell waits
+ * (bounded, ECMC_ERR_TIMEOUT after 5 s) for the neighbours of earlier colours
+ * of the sweep; 0: one launch per colour phase.  Same results bit for bit;
+ * reading it back gives the schedule in use. */
+#define ECMC3_PARAM_PERSISTENT 15
+/* Limit of one dependency wait of the persistent sweep in ms (default 5000). */
+#define ECMC3_PARAM_WAIT_LIMIT_MS 16
+/* Failure test: 1 makes the persistent sweep's dependency waits look for a
+ * value nobody writes, so that they run out after the wait limit and the
+ * sweep reports ECMC_ERR_TIMEOUT (no device fault; the handle recovers when
+ * positions are set again). */
+#define ECMC3_PARAM_WAIT_TEST 17
 
 /* N spheres of diameter sigma in a periodic cube of side L, cells^3 cubic
  * cells (cells even, >= 2, L / cells > sigma), chains of total displacement

@@ -49,7 +49,7 @@ using ecmc::wrap_box0;
 using ecmc::wrap_half;
 using ecmc::wrap_half_i;
 
-constexpr int kOk = 0, kCapacity = 1, kChainCap = 2;
+constexpr int kOk = 0, kCapacity = 1, kChainCap = 2, kWaitTimeout = 4;
 constexpr int kWarpsMax = 4;
 constexpr int kHistoryCap = 1 << 20;  // sweeps of pressure history kept
 
@@ -99,8 +99,12 @@ struct Totals3 {
 
 // ---- kernels ----------------------------------------------------------------
 
-__global__ void k3_begin(Geom3 g, State3* st) {
+__global__ void k3_begin(Geom3 g, State3* st, unsigned* sched) {
   if (threadIdx.x != 0) return;
+  // persistent sweep: the work list from the start, a new epoch, no abort
+  sched[0] = 0u;
+  sched[1] += 1u;
+  sched[2] = 0u;
   State3 s = *st;
   const U64x4 u = philox((uint64_t)s.t, ecmc::kPurposeSweep, 0, 0, g.seed, g.replica);
   for (int a = 0; a < 3; ++a) s.s[a] = unit_double(u.v[a]) * g.w;
@@ -144,16 +148,25 @@ __device__ __forceinline__ bool first_before(double s, long long k, double bs, l
   return lt_nn(s, bs) || (dbits(s) == dbits(bs) && k < bk);
 }
 
-__global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
-    Geom3 g, const State3* __restrict__ stp, int colour_index, double* __restrict__ px,
-    double* __restrict__ py, double* __restrict__ pz, const int* __restrict__ cnt,
-    const int* __restrict__ ids, Cell3* __restrict__ cs, int* __restrict__ recs, int* err) {
-  extern __shared__ __align__(16) unsigned char smem[];
+// Position loads: through L1 in the per-phase kernels (the writers finished
+// in an earlier launch), from L2 in the persistent kernel (the writers may
+// be warps of other SMs in the same launch).
+template <bool CG>
+__device__ __forceinline__ double ldpos(const double* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
+// One active cell of colour phase colour_index, by one warp: frame, chains,
+// write-back, cell statistics.  base: the warp's shared memory.
+template <bool CG>
+__device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colour_index, int a,
+                                      unsigned char* base, double* __restrict__ px,
+                                      double* __restrict__ py, double* __restrict__ pz,
+                                      const int* __restrict__ cnt, const int* __restrict__ ids,
+                                      Cell3* __restrict__ cs, int* __restrict__ recs, int* err) {
   constexpr unsigned FULL = 0xffffffffu;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int a = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (a >= g.nact) return;  // warp-uniform
-  const State3 st = *stp;
+  const int lane = threadIdx.x & 31;
   const int colour = st.perm[colour_index];
   const int hx = g.cells >> 1, nc = g.cells;
   const int cx = 2 * (a % hx) + (colour & 1);
@@ -164,7 +177,6 @@ __global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
   const double o[3] = {st.s[0] + (double)cx * w, st.s[1] + (double)cy * w,
                        st.s[2] + (double)cz * w};
 
-  unsigned char* base = smem + (size_t)warp * g.warp_bytes;
   double* C[3];
   C[0] = reinterpret_cast<double*>(base);
   C[1] = C[0] + g.cap_obj;
@@ -215,9 +227,9 @@ __global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
   const double hL = 0.5 * L;
   for (int q = lane; q < nmem; q += 32) {
     const int i = sid[q];
-    C[0][q] = wrap_half_i(px[i] - o[0], L, hL);
-    C[1][q] = wrap_half_i(py[i] - o[1], L, hL);
-    C[2][q] = wrap_half_i(pz[i] - o[2], L, hL);
+    C[0][q] = wrap_half_i(ldpos<CG>(px + i) - o[0], L, hL);
+    C[1][q] = wrap_half_i(ldpos<CG>(py + i) - o[1], L, hL);
+    C[2][q] = wrap_half_i(ldpos<CG>(pz + i) - o[2], L, hL);
     F[0][q] = (float)C[0][q];
     F[1][q] = (float)C[1][q];
     F[2][q] = (float)C[2][q];
@@ -237,9 +249,9 @@ __global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
       unsigned mask = 0u;  // bit img = (kx+1)*9 + (ky+1)*3 + (kz+1)
       if (k < nq) {
         id = ids[(int64_t)q * g.cap_mem + k];
-        X0[0] = wrap_half_i(px[id] - o[0], L, hL);
-        X0[1] = wrap_half_i(py[id] - o[1], L, hL);
-        X0[2] = wrap_half_i(pz[id] - o[2], L, hL);
+        X0[0] = wrap_half_i(ldpos<CG>(px + id) - o[0], L, hL);
+        X0[1] = wrap_half_i(ldpos<CG>(py + id) - o[1], L, hL);
+        X0[2] = wrap_half_i(ldpos<CG>(pz + id) - o[2], L, hL);
         if (g.single_image) {
           if (dlt(lo, X0[0]) && dlt(X0[0], hi) && dlt(lo, X0[1]) && dlt(X0[1], hi) &&
               dlt(lo, X0[2]) && dlt(X0[2], hi))
@@ -489,6 +501,104 @@ __global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
   }
 }
 
+__global__ void __launch_bounds__(32 * kWarpsMax) k3_phase(
+    Geom3 g, const State3* __restrict__ stp, int colour_index, double* __restrict__ px,
+    double* __restrict__ py, double* __restrict__ pz, const int* __restrict__ cnt,
+    const int* __restrict__ ids, Cell3* __restrict__ cs, int* __restrict__ recs, int* err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5;
+  const int a = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (a >= g.nact) return;  // warp-uniform
+  const State3 st = *stp;
+  cell3<false>(g, st, colour_index, a, smem + (size_t)warp * g.warp_bytes, px, py, pz, cnt, ids,
+               cs, recs, err);
+}
+
+__device__ __forceinline__ unsigned long long global_ns3() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned load_volatile3(const unsigned* p) {
+  return *(const volatile unsigned*)p;
+}
+
+// The persistent sweep: all eight colour phases in one launch.  Work item
+// i = ci * nact + a (colour phase ci, active cell a) is taken from a device
+// counter; the warp waits until each of the cell's 26 neighbours whose colour
+// comes earlier in this sweep's order has finished (done[] holds the sweep's
+// epoch), then processes the cell and publishes it.  A cell of a later
+// colour has not moved yet and waits for this one in turn, so the result is
+// that of the per-phase launches bit for bit.  Progress: an item waits only
+// for smaller items, taken earlier by running warps that wait only for still
+// smaller ones.  Every wait is bounded (global timer): on timeout the kernel
+// raises kWaitTimeout and an abort flag that makes every warp leave.
+__global__ void __launch_bounds__(32 * kWarpsMax) k3_sweep(
+    Geom3 g, const State3* __restrict__ stp, double* __restrict__ px, double* __restrict__ py,
+    double* __restrict__ pz, const int* __restrict__ cnt, const int* __restrict__ ids,
+    Cell3* __restrict__ cs, int* __restrict__ recs, unsigned* sched, unsigned* done,
+    unsigned long long wait_ns, int wait_test, int* err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr unsigned FULL = 0xffffffffu;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* base = smem + (size_t)warp * g.warp_bytes;
+  const State3 st = *stp;
+  const unsigned epoch = load_volatile3(&sched[1]);
+  // the failure test waits for a value nobody writes
+  const unsigned want = wait_test ? (epoch ^ 0x80000000u) : epoch;
+  int phase_of[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) phase_of[st.perm[k]] = k;
+  const int n_items = 8 * g.nact, hx = g.cells >> 1, nc = g.cells;
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = (int)atomicAdd(&sched[0], 1u);
+    item = __shfl_sync(FULL, item, 0);
+    if (item >= n_items || load_volatile3(&sched[2]) != 0u) break;
+    const int ci = item / g.nact, a = item - ci * g.nact;
+    const int colour = st.perm[ci];
+    const int cx = 2 * (a % hx) + (colour & 1);
+    const int cy = 2 * ((a / hx) % hx) + ((colour >> 1) & 1);
+    const int cz = 2 * (a / (hx * hx)) + (colour >> 2);
+    bool ok = true;
+    if (ci > 0 && lane < 26) {
+      // lane d waits for neighbour d of the 3x3x3 block (the centre skipped)
+      const int e = lane < 13 ? lane : lane + 1;
+      const int dx = e % 3 - 1, dy = (e / 3) % 3 - 1, dz = e / 9 - 1;
+      const int ncol = colour ^ (dx != 0 ? 1 : 0) ^ (dy != 0 ? 2 : 0) ^ (dz != 0 ? 4 : 0);
+      if (phase_of[ncol] < ci) {
+        const int q = (((cz + dz + nc) % nc) * nc + (cy + dy + nc) % nc) * nc + (cx + dx + nc) % nc;
+        if (load_volatile3(&done[q]) != want) {
+          const unsigned long long t0 = global_ns3();
+          while (load_volatile3(&done[q]) != want) {
+            if (load_volatile3(&sched[2]) != 0u) {
+              ok = false;
+              break;
+            }
+            if (global_ns3() - t0 > wait_ns) {
+              atomicCAS(err, kOk, kWaitTimeout);
+              atomicExch(&sched[2], 1u);
+              ok = false;
+              break;
+            }
+            __nanosleep(256);
+          }
+        }
+      }
+    }
+    if (!__all_sync(FULL, ok)) break;
+    __threadfence();  // the finished neighbours' positions are visible from here on
+    cell3<true>(g, st, ci, a, base, px, py, pz, cnt, ids, cs, recs, err);
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence();
+      *(volatile unsigned*)&done[(cz * nc + cy) * nc + cx] = epoch;
+    }
+    __syncwarp();
+  }
+}
+
 // End of sweep (one block of 256): the cells' sums in a fixed order, the
 // running totals, the sweep's member-weighted pressure sums, t + 1.
 __global__ void __launch_bounds__(256) k3_end(Geom3 g, State3* st, const Cell3* __restrict__ cs,
@@ -616,6 +726,10 @@ struct ecmc3_ctx {
   cudaStream_t stream = nullptr, own = nullptr;
   double *px = nullptr, *py = nullptr, *pz = nullptr, *xyz_tmp = nullptr;
   int *cnt = nullptr, *ids = nullptr, *cell_of = nullptr, *err = nullptr, *recs = nullptr;
+  unsigned *sched = nullptr, *done = nullptr;  // persistent sweep: work counter, epoch, abort
+  int persistent = 1, fused_blocks = 0;
+  unsigned long long wait_ns = 5000000000ull;
+  int wait_test = 0;
   Cell3* cs = nullptr;
   State3* st = nullptr;
   Totals3* tot = nullptr;
@@ -666,23 +780,36 @@ int check3(ecmc3_ctx* h) {
     h->valid = false;
     return fail3(ECMC_ERR_CHAIN_CAP, "a chain reached the per-chain event cap");
   }
+  if (e == kWaitTimeout) {
+    h->valid = false;
+    CK3(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
+    return fail3(ECMC_ERR_TIMEOUT, "a dependency wait of the persistent sweep exceeded %.0f ms; "
+                 "the sweep was abandoned (positions must be set again)",
+                 (double)h->wait_ns * 1e-6);
+  }
   return ECMC_OK;
 }
 
 int enqueue_sweep(ecmc3_ctx* h, bool records) {
   const Geom3& g = h->g;
   CK3(cudaMemsetAsync(h->cnt, 0, sizeof(int) * (size_t)g.ncell, h->stream));
-  k3_begin<<<1, 32, 0, h->stream>>>(g, h->st);
+  k3_begin<<<1, 32, 0, h->stream>>>(g, h->st, h->sched);
   k3_bin<<<(unsigned)((g.N + 255) / 256), 256, 0, h->stream>>>(g, h->st, h->px, h->py, h->pz,
                                                                h->cnt, h->ids, h->cell_of,
                                                                h->err);
   const int wpb = h->warps;
-  const unsigned blocks = (unsigned)((g.nact + wpb - 1) / wpb);
   const size_t sm = (size_t)wpb * g.warp_bytes;
-  for (int ci = 0; ci < 8; ++ci)
-    k3_phase<<<blocks, 32 * wpb, sm, h->stream>>>(g, h->st, ci, h->px, h->py, h->pz, h->cnt,
-                                                  h->ids, h->cs, records ? h->recs : nullptr,
-                                                  h->err);
+  if (h->persistent && h->fused_blocks > 0) {
+    k3_sweep<<<(unsigned)h->fused_blocks, 32 * wpb, sm, h->stream>>>(
+        g, h->st, h->px, h->py, h->pz, h->cnt, h->ids, h->cs, records ? h->recs : nullptr,
+        h->sched, h->done, h->wait_ns, h->wait_test, h->err);
+  } else {
+    const unsigned blocks = (unsigned)((g.nact + wpb - 1) / wpb);
+    for (int ci = 0; ci < 8; ++ci)
+      k3_phase<<<blocks, 32 * wpb, sm, h->stream>>>(g, h->st, ci, h->px, h->py, h->pz, h->cnt,
+                                                    h->ids, h->cs, records ? h->recs : nullptr,
+                                                    h->err);
+  }
   k3_end<<<1, 256, 0, h->stream>>>(g, h->st, h->cs, h->tot, h->history, h->hist_len);
   CK3(cudaGetLastError());
   return ECMC_OK;
@@ -691,7 +818,7 @@ int enqueue_sweep(ecmc3_ctx* h, bool records) {
 int bin_now(ecmc3_ctx* h) {
   const Geom3& g = h->g;
   CK3(cudaMemsetAsync(h->cnt, 0, sizeof(int) * (size_t)g.ncell, h->stream));
-  k3_begin<<<1, 32, 0, h->stream>>>(g, h->st);
+  k3_begin<<<1, 32, 0, h->stream>>>(g, h->st, h->sched);
   k3_bin<<<(unsigned)((g.N + 255) / 256), 256, 0, h->stream>>>(g, h->st, h->px, h->py, h->pz,
                                                                h->cnt, h->ids, h->cell_of,
                                                                h->err);
@@ -761,6 +888,8 @@ void free3(ecmc3_ctx* h) {
   cudaFree(h->history);
   cudaFree(h->hist_len);
   cudaFree(h->u64);
+  cudaFree(h->sched);
+  cudaFree(h->done);
   if (h->own) cudaStreamDestroy(h->own);
 }
 
@@ -782,8 +911,18 @@ int layout3(ecmc3_ctx* h) {
     return fail3(ECMC_ERR_UNSUPPORTED, "a cell's frame (%d bytes) exceeds shared memory",
                  g.warp_bytes);
   h->warps = wpb;
-  CK3(cudaFuncSetAttribute(k3_phase, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)((size_t)wpb * g.warp_bytes)));
+  const int sm = (int)((size_t)wpb * g.warp_bytes);
+  CK3(cudaFuncSetAttribute(k3_phase, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK3(cudaFuncSetAttribute(k3_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  // the persistent grid: as many blocks as are resident at once, at most one
+  // warp per work item
+  int per_sm = 0, n_sm = 0;
+  CK3(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_sweep, 32 * wpb, (size_t)sm));
+  CK3(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  const long long items = 8LL * g.nact;
+  long long blocks = (long long)per_sm * n_sm;
+  if (blocks > (items + wpb - 1) / wpb) blocks = (items + wpb - 1) / wpb;
+  h->fused_blocks = per_sm > 0 ? (int)blocks : 0;
   return ECMC_OK;
 }
 
@@ -874,12 +1013,16 @@ int ecmc3_create(ecmc3_t* out, int64_t N, double L, double sigma, int cells, dou
       cudaMalloc(&h->tot, sizeof(Totals3)) != cudaSuccess ||
       cudaMalloc(&h->history, sizeof(double) * 2 * kHistoryCap) != cudaSuccess ||
       cudaMalloc(&h->hist_len, sizeof(int64_t)) != cudaSuccess ||
-      cudaMalloc(&h->u64, sizeof(unsigned long long)) != cudaSuccess) {
+      cudaMalloc(&h->u64, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(&h->sched, sizeof(unsigned) * 4) != cudaSuccess ||
+      cudaMalloc(&h->done, sizeof(unsigned) * (size_t)g.ncell) != cudaSuccess) {
     cudaGetLastError();
     free3(h);
     delete h;
     return fail3(ECMC_ERR_OOM, "device allocation failed");
   }
+  cudaMemsetAsync(h->sched, 0, sizeof(unsigned) * 4, h->stream);
+  cudaMemsetAsync(h->done, 0, sizeof(unsigned) * (size_t)g.ncell, h->stream);
   // the cubic lattice start
   std::vector<double> xyz(3 * nn);
   const double a = L / (double)k;
@@ -923,6 +1066,18 @@ int ecmc3_set_param(ecmc3_t h, int key, double v) {
       if (!(v >= 0.0) || v != std::floor(v)) return fail3(ECMC_ERR_ARG, "replica");
       h->g.replica = (uint64_t)v;
       return ECMC_OK;
+    case ECMC3_PARAM_PERSISTENT:
+      if (v != 0.0 && v != 1.0) return fail3(ECMC_ERR_ARG, "persistent must be 0 or 1");
+      h->persistent = (int)v;
+      return ECMC_OK;
+    case ECMC3_PARAM_WAIT_LIMIT_MS:
+      if (!(v >= 1.0 && v <= 600000.0)) return fail3(ECMC_ERR_ARG, "wait limit in [1, 600000] ms");
+      h->wait_ns = (unsigned long long)(v * 1e6);
+      return ECMC_OK;
+    case ECMC3_PARAM_WAIT_TEST:
+      if (v != 0.0 && v != 1.0) return fail3(ECMC_ERR_ARG, "wait test must be 0 or 1");
+      h->wait_test = (int)v;
+      return ECMC_OK;
     default:
       return fail3(ECMC_ERR_ARG, "unknown parameter %d", key);
   }
@@ -933,6 +1088,10 @@ int ecmc3_get_param(ecmc3_t h, int key, double* v) {
   switch (key) {
     case ECMC3_PARAM_N_CHAINS: *v = h->g.n_m; return ECMC_OK;
     case ECMC3_PARAM_REPLICA: *v = (double)h->g.replica; return ECMC_OK;
+    case ECMC3_PARAM_PERSISTENT: *v = (h->persistent && h->fused_blocks > 0) ? 1.0 : 0.0;
+      return ECMC_OK;
+    case ECMC3_PARAM_WAIT_LIMIT_MS: *v = (double)h->wait_ns * 1e-6; return ECMC_OK;
+    case ECMC3_PARAM_WAIT_TEST: *v = h->wait_test; return ECMC_OK;
     default: return fail3(ECMC_ERR_ARG, "unknown parameter %d", key);
   }
 }

@@ -411,6 +411,9 @@ class Ecmc:
 
 PARAM3_N_CHAINS = 1
 PARAM3_REPLICA = 4
+PARAM3_PERSISTENT = 15
+PARAM3_WAIT_LIMIT_MS = 16
+PARAM3_WAIT_TEST = 17
 
 
 class Ecmc3:

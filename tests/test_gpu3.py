@@ -29,10 +29,11 @@ from paper_1409_6948_gb300 import ecmc as E  # noqa: E402
 REL = 1e-12
 
 
-def make3(N, eta, cells, ell, nm, seed):
+def make3(N, eta, cells, ell, nm, seed, persistent=1):
     L = W.box_side3(N, eta)
     g = P.Ecmc3(N, L, 1.0, cells, ell, seed)
     g.set_param(E.PARAM3_N_CHAINS, nm)
+    g.set_param(E.PARAM3_PERSISTENT, persistent)
     p = oracle.make_params3(N, L, 1.0, cells, ell, nm, seed)
     return g, p, L
 
@@ -47,8 +48,9 @@ def assert_positions_equal(g, x, y, z, L):
     assert worst <= REL, "max relative position difference %g" % worst
 
 
-def run_pair3(N, eta, cells, ell, nm, seed, n_sweeps):
-    g, p, L = make3(N, eta, cells, ell, nm, seed)
+def run_pair3(N, eta, cells, ell, nm, seed, n_sweeps, persistent=1):
+    g, p, L = make3(N, eta, cells, ell, nm, seed, persistent)
+    assert g.get_param(E.PARAM3_PERSISTENT) == persistent
     x, y, z = W.cubic_lattice(N, L)
     tot = oracle.Stats()
     for s in range(n_sweeps):
@@ -85,8 +87,9 @@ def run_pair3(N, eta, cells, ell, nm, seed, n_sweeps):
     (13824, 0.49, 10, 1.0, 1, 3),
     (8000, 0.30, 6, 3.0, 6, 3),
 ])
-def test_sweeps_match_oracle(N, eta, cells, ell, nm, sweeps):
-    st = run_pair3(N, eta, cells, ell, nm, 5, sweeps)
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_sweeps_match_oracle(N, eta, cells, ell, nm, sweeps, persistent):
+    st = run_pair3(N, eta, cells, ell, nm, 5, sweeps, persistent)
     assert st.events > 0 and st.frozen_hits > 0 and st.wall_hits > 0
 
 
@@ -159,3 +162,40 @@ def test_pressure_matches_carnahan_starling():
     cs = (1 + eta + eta**2 - eta**3) / (1 - eta) ** 3
     assert abs(z - cs) < 4.0 * zse + 0.003 * cs, (z, cs, zse)
     g.close()
+
+
+def test_persistent_and_per_phase_sweeps_are_bitwise_equal():
+    a, p, L = make3(32768, 0.45, 16, 1.0, 3, 21, persistent=1)
+    b, p, L = make3(32768, 0.45, 16, 1.0, 3, 21, persistent=0)
+    a.sweep(12)
+    b.sweep(12)
+    assert np.array_equal(a.positions(), b.positions())
+    ca, cb = a.counters(), b.counters()
+    assert ca.events == cb.events and ca.sum_b == cb.sum_b
+    a.close()
+    b.close()
+
+
+def test_dependency_wait_times_out_and_recovers():
+    # the failure test: every wait looks for a value nobody writes and runs
+    # out after 200 ms; the sweep reports a timeout, the handle recovers once
+    # positions are set again (no device fault)
+    g, p, L = make3(4096, 0.40, 8, 1.0, 2, 3)
+    g.sweep(2)
+    xyz = g.positions().copy()
+    t = g.sweep_index()
+    g.set_param(E.PARAM3_WAIT_LIMIT_MS, 200)
+    g.set_param(E.PARAM3_WAIT_TEST, 1)
+    g.sweep(1)
+    with pytest.raises(E.EcmcError) as ei:
+        g.synchronize()
+    assert ei.value.code == E.ERR_TIMEOUT
+    g.set_param(E.PARAM3_WAIT_TEST, 0)
+    g.set_positions(xyz, t0=t)
+    g.sweep(2)
+    g.synchronize()
+    ref, _, _ = make3(4096, 0.40, 8, 1.0, 2, 3)
+    ref.sweep(4)
+    assert np.array_equal(g.positions(), ref.positions())
+    g.close()
+    ref.close()
