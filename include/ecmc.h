@@ -54,7 +54,7 @@ extern "C" {
 #define ECMC_ERR_TIMEOUT -5     /* a bounded device-side wait gave up            */
 #define ECMC_ERR_STATE -6       /* call not valid in the handle's current state  */
 #define ECMC_ERR_CAPACITY -7    /* a cell frame exceeded its capacity            */
-#define ECMC_ERR_UNSUPPORTED -8 /* option not available in this build            */
+#define ECMC_ERR_UNSUPPORTED -8 /* option not supported for these parameters    */
 #define ECMC_ERR_CHAIN_CAP -9   /* a chain hit the per-chain event cap           */
 
 /* ---- parameters (ecmc_set_param / ecmc_get_param) ---------------------- */
