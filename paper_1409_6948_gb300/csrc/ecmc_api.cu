@@ -603,6 +603,7 @@ int setup_geom(const ecmc_replica_desc_t& d, Geom& g) {
   g.h = d.L / (double)d.cells_y;
   g.inv_w = 1.0 / g.w;
   g.inv_h = 1.0 / g.h;
+  set_bin_screen(g);
   g.ell = d.ell;
   g.seed = d.seed;
   g.replica = d.replica;

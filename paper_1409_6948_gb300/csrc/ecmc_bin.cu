@@ -51,14 +51,53 @@ void launch_sweep_begin(const DevBufs& b, cudaStream_t s) {
   k_sweep_begin<<<(b.R + 31) / 32, 32, 0, s>>>(b.rg, b.state, b.R, b.sched);
 }
 
-__device__ __forceinline__ void bin_one(const Geom& g, const SweepState& st, double x, double y,
-                                        int id, double* __restrict__ qx, double* __restrict__ qy,
-                                        int* __restrict__ qid, int* __restrict__ cnt_dst, int cap,
-                                        int* err) {
-  const int cx = cell_1d(x, st.sx, g.L, g.inv_w, g.cells_x);
-  const int cy = cell_1d(y, st.sy, g.L, g.inv_h, g.cells_y);
-  const int cn = g.cell_off + cy * g.cells_x + cx;
-  const int r = atomicAdd(&cnt_dst[cn], 1);
+// Cell index along one axis as cell_1d computes it in FP64, first estimated
+// in FP32 (inputs rounded toward zero on the integer pipes): when the
+// estimate's error interval [q - eq, q + eq] holds no cell boundary and lies
+// inside (0, cells), its floor is the FP64 result; otherwise (about 2 eq of
+// the disks) the FP64 formula runs.
+__device__ __forceinline__ int cell_1d_screened(double v, double shift, double L, double inv_w,
+                                                int cells, float Lf, float inv_wf, float eq) {
+  float uf = to_float_trunc(v) - to_float_trunc(shift);
+  uf = uf < 0.0f ? uf + Lf : uf;
+  const float qf = uf * inv_wf;
+  const float lo = qf - eq, hi = qf + eq;
+  if (lo > 0.0f && hi < (float)cells) {
+    const int ilo = (int)lo, ihi = (int)hi;  // both positive: truncation is floor
+    if (ilo == ihi) return ilo;
+  }
+  return cell_1d(v, shift, L, inv_w, cells);
+}
+
+// Append disk (x, y, id) to its bucket in dst.  Called by every lane of the
+// warp (valid = false for lanes without a disk): lanes bound for the same
+// cell -- a cell's disks reach at most four cells of the shifted grid --
+// take consecutive slots with one atomic per group, so the writes coalesce.
+// The slot order inside a bucket is immaterial (frames sort members by id).
+__device__ __forceinline__ void bin_one(const Geom* __restrict__ rg,
+                                        const SweepState* __restrict__ sts, int rep, bool valid,
+                                        double x, double y, int id, double* __restrict__ qx,
+                                        double* __restrict__ qy, int* __restrict__ qid,
+                                        int* __restrict__ cnt_dst, int cap, int* err) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  int cn = -1;
+  if (valid) {
+    const Geom& g = rg[rep];
+    const SweepState& st = sts[rep];
+    const int cx = cell_1d_screened(x, st.sx, g.L, g.inv_w, g.cells_x, g.Lf, g.inv_wf,
+                                    g.bin_eq_x);
+    const int cy = cell_1d_screened(y, st.sy, g.L, g.inv_h, g.cells_y, g.Lf, g.inv_hf,
+                                    g.bin_eq_y);
+    cn = g.cell_off + cy * g.cells_x + cx;
+  }
+  const unsigned grp = __match_any_sync(FULL, cn);
+  const int leader = __ffs(grp) - 1;
+  int base = 0;
+  if (valid && lane == leader) base = atomicAdd(&cnt_dst[cn], __popc(grp));
+  base = __shfl_sync(FULL, base, leader);
+  if (!valid) return;
+  const int r = base + __popc(grp & ((1u << lane) - 1u));
   if (r >= cap) {
     atomicCAS(err, DEV_OK, DEV_CAPACITY);
     return;
@@ -78,12 +117,13 @@ __global__ void k_bin_bucketed(const Geom* __restrict__ rg, const SweepState* __
                                double* __restrict__ qx, double* __restrict__ qy,
                                int* __restrict__ qid, int* __restrict__ cnt_dst, int* err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)C_total * cap) return;
-  const int c = (int)(i / cap);
-  const int k = (int)(i - (int64_t)c * cap);
-  if (k >= min(__ldg(&cnt_src[c]), cap)) return;
-  const int r = cell_rep[c];
-  bin_one(rg[r], st[r], px[i], py[i], pid[i], qx, qy, qid, cnt_dst, cap, err);
+  const bool in = i < (int64_t)C_total * cap;  // whole warps reach bin_one
+  const int c = in ? (int)(i / cap) : 0;
+  const int k = in ? (int)(i - (int64_t)c * cap) : 0;
+  const bool valid = in && k < min(__ldg(&cnt_src[c]), cap);
+  const int r = valid ? cell_rep[c] : 0;
+  bin_one(rg, st, r, valid, valid ? px[i] : 0.0, valid ? py[i] : 0.0, valid ? pid[i] : 0, qx,
+          qy, qid, cnt_dst, cap, err);
 }
 
 __device__ __forceinline__ int replica_of_disk(const int64_t* __restrict__ n_off, int R,
@@ -105,9 +145,10 @@ __global__ void k_bin_flat(const Geom* __restrict__ rg, const SweepState* __rest
                            double* __restrict__ qx, double* __restrict__ qy, int* __restrict__ qid,
                            int* __restrict__ cnt_dst, int* err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N_total) return;
-  const int r = replica_of_disk(n_off, R, i);
-  bin_one(rg[r], st[r], px[i], py[i], (int)(i - n_off[r]), qx, qy, qid, cnt_dst, cap, err);
+  const bool valid = i < N_total;  // whole warps reach bin_one
+  const int r = valid ? replica_of_disk(n_off, R, i) : 0;
+  bin_one(rg, st, r, valid, valid ? px[i] : 0.0, valid ? py[i] : 0.0,
+          valid ? (int)(i - n_off[r]) : 0, qx, qy, qid, cnt_dst, cap, err);
 }
 
 void launch_bin(const DevBufs& b, int src, int dst, cudaStream_t s) {

@@ -16,6 +16,7 @@
 //   - a small device struct holds the sweep counter and the per-sweep draws,
 //     so one sweep is a fixed sequence of launches (graph-capturable).
 #pragma once
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -116,6 +117,10 @@ struct Geom {
   float iso_sig_lo;  // certain-hit threshold on |c| (below sigma)
   float iso_sig_hi;  // certain-miss threshold on |c| (above sigma)
   int precision;     // 0 FP64 candidates, 1 FP32 screening
+  // FP32 cell index of the binning pass: q = (v - s mod L) / w estimated in
+  // FP32 within bin_eq_* of the FP64 product; the FP64 formula decides only
+  // when that interval touches a cell boundary
+  float Lf, inv_wf, inv_hf, bin_eq_x, bin_eq_y;
   int boundary;      // 0 reflect at walls and frozen disks, 1 reject the whole chain
   UndoEntry* undo;   // boundary 1: undo logs, undo_stride entries per global cell
   int undo_stride;   // largest bucket capacity of the handle (>= cap_mem)
@@ -228,6 +233,21 @@ size_t fused_scratch_bytes(const RecLayout& lay);
 // none of its bookkeeping).
 // Set the message ecmc_last_error_message() returns; returns code.
 int report_error(int code, const char* msg);
+
+// The FP32 binning screen of replica g (host).  With v, s rounded toward
+// zero to FP32 (relative error 2^-23) and each FP32 operation rounded
+// (2^-24), |u32 - u| <= 2^-21 (L + w) after the wrap, so the FP32 quotient
+// is within 2^-21 (L + w) / w + 2^-23 cells of the FP64 product; bin_eq_*
+// is twice that.
+inline void set_bin_screen(Geom& g) {
+  g.Lf = (float)g.L;
+  g.inv_wf = (float)g.inv_w;
+  g.inv_hf = (float)g.inv_h;
+  g.bin_eq_x = (float)(2.0 * (std::ldexp(1.0, -21) * (g.L + g.w) * g.inv_w * 1.01 +
+                              std::ldexp(1.0, -23) * g.cells_x));
+  g.bin_eq_y = (float)(2.0 * (std::ldexp(1.0, -21) * (g.L + g.h) * g.inv_h * 1.01 +
+                              std::ldexp(1.0, -23) * g.cells_y));
+}
 
 inline int chain_kind(const DevBufs& b) { return b.iso ? 1 : (b.reject ? 2 : 0); }
 int configure_fused(const RecLayout& lay, int tpc, int fm, int kind, int* blocks_per_sm);

@@ -87,6 +87,7 @@ extern "C" int ecmc_sweep_noalloc(double* xy, int64_t N, double L, double sigma,
   g.h = L / (double)cells_y;
   g.inv_w = 1.0 / g.w;
   g.inv_h = 1.0 / g.h;
+  set_bin_screen(g);
   g.ell = ell;
   g.n_m = n_m;
   g.seed = seed;
