@@ -129,19 +129,23 @@ __global__ void k_pairs(Geom g, int cap, const double* __restrict__ px,
 // leave |dX - T| <= e = 1 + 2^-16 for every pair within L / 4.
 //
 // Exact squared distances.  D = dX^2 + dY^2 is exact in 64 bits (|dX| <
-// 2^30).  With D* the scaled squared distance of the FP64 positions,
+// 2^30); the scan works with its FP32 value.  With D* the scaled squared distance of the FP64 positions,
 // |D - D*| <= 2 e (|dX| + |dY| + 2 e) + 2 e^2 <= 2 sqrt(2) e sqrt(D) + 6 e^2,
 // and the FP64 formula d2 = dx dx + dy dy (each operation rounded; the wrap
 // adds at most 2 u L) sits within 2^-19 sqrt(2 D*) + 2^-51 D* of D*.  Both
 // are below Bt(D) = 2.9 sqrt(D) + 8 + D / 2^40.
 //
-// Selection.  Each lane keeps the two smallest D of its candidates (m1 <= m2)
-// and the argmin j1.  If m2 - Bt(m2) > m1 + Bt(m1), no other candidate can
-// have an FP64 d2 at or below that of j1, and d2(i, j1) is the lane's
-// minimum.  Otherwise (exact ties, as on a lattice) the lane rescans and
-// evaluates FP64 for every candidate with D <= m1 + 4 Bt(m1) + 64, a window
-// that holds every candidate whose d2 can be the smallest.  The result is the
-// same double, bit for bit, as the minimum of the FP64 formula over all pairs.
+// Selection.  Each lane keeps, in FP32, the two smallest values of D over its
+// candidates (m1 <= m2) and the argmin j1; the FP32 value of D (two exact
+// int-to-float conversions below 2^24, two products and a sum) is within
+// eps = 2^-21 of D relatively.  If m2 - m1 > Bt(m1) + Bt(m2) + 2^-20 m2, no
+// other candidate can have an FP64 d2 at or below that of j1, and d2(i, j1)
+// is the lane's minimum.  Otherwise (exact ties, as on a lattice) the lane
+// rescans and evaluates FP64 for every candidate with FP32 D below
+// (m1 + 4 Bt(m1) + 64)(1 + 2^-19), a window that holds every candidate whose
+// d2 can be the smallest.  A lane whose m1 exceeds the FP32 image of
+// (rcut^2 + Bt) (1 + 2^-19) has no pair within rcut.  The result is the same
+// double, bit for bit, as the minimum of the FP64 formula over all pairs.
 
 // 32-bit fractions of the box side, one uint2 per bucket slot
 __global__ void k_fixed_point(Geom g, int cap, const double* __restrict__ px,
@@ -160,8 +164,8 @@ __global__ void k_fixed_point(Geom g, int cap, const double* __restrict__ px,
   fxy[i] = make_uint2((unsigned)X, (unsigned)Y);
 }
 
-__device__ __forceinline__ unsigned long long bt_bound(unsigned long long x) {
-  return (unsigned long long)(2.9f * sqrtf((float)x)) + 8ull + (x >> 40);
+__device__ __forceinline__ float bt_bound(float x) {
+  return 2.9f * sqrtf(x) + 8.0f + x * 0x1p-40f;
 }
 
 // FP64 squared minimum-image distance, the formula of the FP64 scan
@@ -180,10 +184,10 @@ __device__ __forceinline__ double pair_d2(const double* __restrict__ px,
 template <bool HALF>
 __global__ void __launch_bounds__(256) k_min_dist_fixed(
     Geom g, int cap, const double* __restrict__ px, const double* __restrict__ py,
-    const uint2* __restrict__ fxy, const int* __restrict__ cnt, int Rx, int Ry, unsigned RC,
+    const uint2* __restrict__ fxy, const int* __restrict__ cnt, int Rx, int Ry, float t_skip,
     unsigned long long r2_bits, unsigned long long* __restrict__ out) {
   constexpr unsigned kFull = 0xffffffffu;
-  constexpr unsigned long long kNone = ~0ull;
+  const float kInf = __int_as_float(0x7f800000);
   const int lcell = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (lcell >= g.ncell) return;  // warp-uniform
   const int lane = threadIdx.x & 31;
@@ -223,46 +227,43 @@ __global__ void __launch_bounds__(256) k_min_dist_fixed(
         }
       }
     };
-    // exact D of a candidate, kNone when screened out or excluded
-    auto dist = [&](uint2 pj, int kk, int kmin, int kskip) -> unsigned long long {
-      const int dx = (int)(pj.x - pi.x), dy = (int)(pj.y - pi.y);
-      const bool s = ((unsigned)dx + RC <= 2u * RC) & ((unsigned)dy + RC <= 2u * RC) &
-                     (kk > kmin) & (kk != kskip);
-      const unsigned long long D =
-          (unsigned long long)((long long)dx * dx + (long long)dy * dy);
-      return s ? D : kNone;
+    // FP32 value of D of a candidate, +inf when excluded
+    auto dist = [&](uint2 pj, int kk, int kmin, int kskip) -> float {
+      const float dx = (float)(int)(pj.x - pi.x), dy = (float)(int)(pj.y - pi.y);
+      const float D = dx * dx + dy * dy;
+      return ((kk > kmin) & (kk != kskip)) ? D : kInf;
     };
 
-    unsigned long long m1 = kNone, m2 = kNone;
-    int64_t j1 = 0;
+    float m1 = kInf, m2 = kInf;
+    int j1 = 0;  // slot indices are below 2^31 (checked by the launcher)
     scan([&](int q, int kmin, int kskip) {
-      const int64_t b0 = (int64_t)q * cap;
+      const int b0 = q * cap;
       const int nq = min(cnt[q], cap);
 #pragma unroll 4
       for (int kk = 0; kk < nq; ++kk) {
-        const unsigned long long D = dist(fxy[b0 + kk], kk, kmin, kskip);
-        const bool lt1 = D < m1, lt2 = D < m2;
-        m2 = lt1 ? m1 : (lt2 ? D : m2);
+        const float D = dist(fxy[b0 + kk], kk, kmin, kskip);
+        const bool lt1 = D < m1;
+        m2 = lt1 ? m1 : fminf(m2, D);
         j1 = lt1 ? b0 + kk : j1;
         m1 = lt1 ? D : m1;
       }
     });
 
     bool amb = false;
-    if (act && m1 != kNone) {
-      amb = m2 != kNone && m2 - m1 <= bt_bound(m1) + bt_bound(m2);
+    if (act && m1 <= t_skip) {
+      amb = !(m2 - m1 > bt_bound(m1) + bt_bound(m2) + m2 * 0x1p-20f);
       if (!amb) {
         const unsigned long long bits = __double_as_longlong(pair_d2(px, py, i, j1, g.L));
         best = bits < best ? bits : best;
       }
     }
     if (__any_sync(kFull, amb)) {
-      const unsigned long long win = amb ? m1 + 4ull * bt_bound(m1) + 64ull : 0ull;
+      const float win = amb ? (m1 + 4.0f * bt_bound(m1) + 64.0f) * (1.0f + 0x1p-19f) : -1.0f;
       scan([&](int q, int kmin, int kskip) {
-        const int64_t b0 = (int64_t)q * cap;
+        const int b0 = q * cap;
         const int nq = min(cnt[q], cap);
         for (int kk = 0; kk < nq; ++kk) {
-          const unsigned long long D = dist(fxy[b0 + kk], kk, kmin, kskip);
+          const float D = dist(fxy[b0 + kk], kk, kmin, kskip);
           if (amb && D <= win) {
             const unsigned long long bits =
                 __double_as_longlong(pair_d2(px, py, i, b0 + kk, g.L));
@@ -302,19 +303,24 @@ void launch_min_dist(const Geom& g, const DevBufs& b, double rcut, unsigned long
   }
   const int Rx = (int)std::ceil(rcut * g.inv_w * (1.0 + 1e-9));
   const int Ry = (int)std::ceil(rcut * g.inv_h * (1.0 + 1e-9));
-  const unsigned RC = (unsigned)std::ceil(rcut * scale) + 4u;
   const double r2 = rcut * rcut;
   unsigned long long r2_bits = 0;
   std::memcpy(&r2_bits, &r2, sizeof(r2));
+  // FP32 D above which no pair lies within rcut: (R + Bt(R) + 1)(1 + 2^-19)
+  // with R = (rcut 2^32 / L)^2, rounded up
+  const double R = (rcut * scale) * (rcut * scale);
+  const double t_skip_d = (R + 2.9 * std::sqrt(R) + 8.0 + R * std::ldexp(1.0, -40) + 1.0) *
+                          (1.0 + std::ldexp(1.0, -19));
+  const float t_skip = std::nextafter((float)t_skip_d, 3.0e38f);
   const bool half = 2 * Rx + 1 <= g.cells_x && 2 * Ry + 1 <= g.cells_y;
   const int bs = 256;
   const unsigned grid = (unsigned)(((int64_t)g.ncell * 32 + bs - 1) / bs);
   if (half)
     k_min_dist_fixed<true><<<grid, bs, 0, s>>>(g, b.cap, b.px[b.cur], b.py[b.cur], fxy,
-                                                b.count[b.cur], Rx, Ry, RC, r2_bits, out);
+                                                b.count[b.cur], Rx, Ry, t_skip, r2_bits, out);
   else
     k_min_dist_fixed<false><<<grid, bs, 0, s>>>(g, b.cap, b.px[b.cur], b.py[b.cur], fxy,
-                                                 b.count[b.cur], Rx, Ry, RC, r2_bits, out);
+                                                 b.count[b.cur], Rx, Ry, t_skip, r2_bits, out);
 }
 
 void launch_gr(const Geom& g, const DevBufs& b, double dr, int nbins, unsigned long long* counts,
