@@ -114,9 +114,13 @@ def test_min_distance_and_overlap_check():
     with pytest.raises(E.EcmcError) as ei:
         g.set_positions(bad, t0=10)
     assert ei.value.code == E.ERR_OVERLAP
+    # the handle recovers from the rejected input; sweeps keep spheres apart
     g.set_positions(xyz, t0=10)
     g.sweep(2)
-    assert np.allclose(g.positions()[:3], g.positions()[:3])
+    after = g.positions()
+    x2, y2, z2 = after[0::3].copy(), after[1::3].copy(), after[2::3].copy()
+    assert oracle.min_dist2_3(L, x2, y2, z2, rc) >= 1.0 - 1e-12
+    assert g.min_distance() == math.sqrt(oracle.min_dist2_3(L, x2, y2, z2, rc))
     g.close()
 
 
