@@ -52,7 +52,7 @@ FP64_LANES_PER_SM_CLK = 2
 K_PHASE_DRAM_BYTES = 39.11e6
 # the same for one k_sweep_fused launch (a whole sweep), from `ncu --set full`
 # (profiles/k_sweep_fused_large_paper_params.md)
-K_SWEEP_FUSED_DRAM_BYTES = 40.72e6
+K_SWEEP_FUSED_DRAM_BYTES = 40.83e6
 
 
 def parse():
