@@ -66,6 +66,7 @@ typedef struct ecmc3_ctx* ecmc3_t;
  * if one cell's frame does not fit in shared memory. */
 ECMC_API int ecmc3_create(ecmc3_t* out, int64_t N, double L, double sigma, int cells,
                           double ell, uint64_t seed);
+/* Release the handle (NULL: nothing to do, ECMC_OK). */
 ECMC_API int ecmc3_destroy(ecmc3_t h);
 
 ECMC_API int ecmc3_set_param(ecmc3_t h, int key, double value);

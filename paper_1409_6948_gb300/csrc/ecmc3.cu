@@ -1042,7 +1042,7 @@ int ecmc3_create(ecmc3_t* out, int64_t N, double L, double sigma, int cells, dou
 }
 
 int ecmc3_destroy(ecmc3_t h) {
-  if (!h) return fail3(ECMC_ERR_ARG, "NULL handle");
+  if (!h) return ECMC_OK;  // like ecmc_destroy: nothing to release
   if (h->stream) cudaStreamSynchronize(h->stream);
   free3(h);
   delete h;

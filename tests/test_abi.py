@@ -87,6 +87,9 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.ecmc_destroy(None) == 0
     d = C.c_double()
     assert lib.ecmc_pressure(None, C.byref(d), None) == E.ERR_ARG
+    assert lib.ecmc3_sweep(None, 1) == E.ERR_ARG
+    assert lib.ecmc3_destroy(None) == 0
+    assert lib.ecmc3_pressure(None, C.byref(d), None) == E.ERR_ARG
 
 
 @pytest.mark.parametrize("N,eta", [(1048576, 0.72), (262144, 0.70), (4096, 0.60), (65536, 0.708),
