@@ -902,23 +902,40 @@ int layout3(ecmc3_ctx* h) {
                         (size_t)g.cap_mem * 2 * sizeof(int) + 28 * sizeof(int) +
                         (size_t)g.cap_mem + 15) &
                        ~(size_t)15);
-  int dev = 0, optin = 0;
+  int dev = 0, optin = 0, n_sm = 0;
   CK3(cudaGetDevice(&dev));
   CK3(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  int wpb = kWarpsMax;
-  while (wpb > 1 && (size_t)wpb * g.warp_bytes > (size_t)optin) --wpb;
+  CK3(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   if ((size_t)g.warp_bytes > (size_t)optin)
     return fail3(ECMC_ERR_UNSUPPORTED, "a cell's frame (%d bytes) exceeds shared memory",
                  g.warp_bytes);
+  // The attribute is per kernel for the whole process: request the most the
+  // kernels can have, so that a handle with small frames never lowers the
+  // limit a handle with larger frames launches with.
+  cudaFuncAttributes fa;
+  CK3(cudaFuncGetAttributes(&fa, k3_phase));
+  CK3(cudaFuncSetAttribute(k3_phase, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - (int)fa.sharedSizeBytes));
+  CK3(cudaFuncGetAttributes(&fa, k3_sweep));
+  CK3(cudaFuncSetAttribute(k3_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - (int)fa.sharedSizeBytes));
+  // block shape: the warps per block (one cell each) that keep the most
+  // cells resident per SM; larger blocks on ties
+  int wpb = 1, per_sm = 0, best = -1;
+  for (int w = 1; w <= kWarpsMax; ++w) {
+    const size_t smw = (size_t)w * g.warp_bytes;
+    if (smw > (size_t)optin) break;
+    int nb = 0;
+    CK3(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k3_sweep, 32 * w, smw));
+    if (nb * w >= best) {
+      best = nb * w;
+      wpb = w;
+      per_sm = nb;
+    }
+  }
   h->warps = wpb;
-  const int sm = (int)((size_t)wpb * g.warp_bytes);
-  CK3(cudaFuncSetAttribute(k3_phase, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  CK3(cudaFuncSetAttribute(k3_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   // the persistent grid: as many blocks as are resident at once, at most one
   // warp per work item
-  int per_sm = 0, n_sm = 0;
-  CK3(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_sweep, 32 * wpb, (size_t)sm));
-  CK3(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   const long long items = 8LL * g.nact;
   long long blocks = (long long)per_sm * n_sm;
   if (blocks > (items + wpb - 1) / wpb) blocks = (items + wpb - 1) / wpb;

@@ -203,3 +203,20 @@ def test_dependency_wait_times_out_and_recovers():
     assert np.array_equal(g.positions(), ref.positions())
     g.close()
     ref.close()
+
+
+def test_handles_with_different_frame_sizes_coexist():
+    # the kernels' shared-memory limit is process-wide: a handle with small
+    # frames created after one with large frames must not break the latter
+    big, pb, Lb = make3(4096, 0.45, 4, 1.0, 2, 31)      # cells of 4 sigma
+    small, ps, Ls = make3(32768, 0.45, 16, 1.0, 2, 32)  # cells of 2 sigma
+    small.sweep(2)
+    big.sweep(2)
+    small.sweep(1)
+    big.synchronize()
+    small.synchronize()
+    x, y, z = W.cubic_lattice(4096, Lb)
+    oracle.sweeps3(pb, x, y, z, 0, 2)
+    assert_positions_equal(big, x, y, z, Lb)
+    big.close()
+    small.close()
