@@ -1,0 +1,53 @@
+"""Host-side arithmetic of bench.py (no GPU): the contact-value fit of the
+pressure route, the shared-memory roofline's algorithmic bytes, the latency
+ceiling and the all-cores batch CPU baseline."""
+import math
+from types import SimpleNamespace
+
+import numpy as np
+import pytest
+
+import bench
+import ecmc_workloads as W
+
+
+def test_contact_value_recovers_a_quadratic_exactly():
+    r = 1.0 + 0.01 * (np.arange(10) + 0.5)
+    g = 6.5 - 40.0 * (r - 1.0) + 300.0 * (r - 1.0) ** 2
+    assert bench.contact_value(r, g) == pytest.approx(6.5, abs=1e-9)
+
+
+def test_smem_roofline_counts_the_strip_that_can_hold_the_first_hit():
+    w = SimpleNamespace(N=1048576, L=W.box_side(1048576, 0.72))
+    c = SimpleNamespace(sum_disp=0.05 * 1000.0)
+    out = bench.smem_roofline(w, None, c, 1000, 1.0e9, 1, 40000.0)
+    rho = w.N / w.L**2
+    disks = rho * 2.0 * (1.0 + 0.05)
+    assert out["candidates_per_event"] == pytest.approx(disks)
+    assert out["bytes_per_event"] == pytest.approx(disks * 8.0 + 16.0)
+    assert out["achieved"] == pytest.approx(1.0e9 * out["bytes_per_event"] / 1e9)
+    assert out["frac"] == pytest.approx(out["achieved"] / 40000.0)
+    assert bench.smem_roofline(w, [1], c, 1000, 1.0e9, 1, 40000.0) is None
+
+
+def test_latency_ceiling_arithmetic():
+    class FakeHandle:
+        def get_param(self, key):
+            return 9120.0
+
+    c = SimpleNamespace(events=2.4e6)
+    kt = SimpleNamespace(phase_ms=2.6, phase_launches=2)
+    out = bench.latency_ceiling(FakeHandle(), None, 240, c, kt, {"sm_mhz": 2000.0}, 2070.0)
+    cyc = 1.3e-3 * 2000e6 * 9120 / 1.2e6
+    assert out["cycles_per_event_per_chain"] == pytest.approx(cyc)
+    assert out["ceiling_all_active_cells"] == pytest.approx(14400 * 2000e6 / cyc)
+
+
+def test_batch_cpu_baseline_uses_all_cores():
+    descs = []
+    for r, d in enumerate(W.replica_batch(R=4)):
+        descs.append(dict(N=min(d["N"], 4096), L=W.box_side(min(d["N"], 4096), d["eta"]),
+                          cells_x=4, cells_y=4, ell=2.0, n_m=2, seed=d["seed"], replica=r))
+    out = bench.cpu_baseline_batch(descs, 0.5)
+    assert out["kind"] == "oracle" and out["value"] > 0
+    assert 1 <= out["cores"] <= 4 and "processes" in out["sample"]
