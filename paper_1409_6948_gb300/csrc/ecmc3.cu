@@ -2,23 +2,25 @@
 // dimensions (the generalisation of Sec. 3.4 to cubic cells in 2x2x2 blocks;
 // interface and readings in ecmc3.h).
 //
-// Per sweep: k3_begin (draws), k3_bin (bucket every sphere by cell), eight
-// launches of k3_phase (one colour each) and k3_end (deterministic sums).
-// k3_phase gives one warp to one active cell: the warp sorts the cell's
-// members by id, gathers the members and every periodic image of the 26
-// neighbour cells' spheres within sigma of the cell into a shared-memory
-// frame (FP64 coordinates and their FP32 roundings), then runs the cell's
-// n_m chains.  Each event is one warp-wide pass over the frame: 32 lanes
-// screen candidates in FP32 with a rigorous margin (a sphere behind the
-// mover or with perpendicular offset >= sigma cannot be hit), test the
-// survivors in FP64 with the oracle's expressions (no contraction: the
-// library is built with -fmad=false), and a shuffle reduction picks the
-// first hit by (distance, key).  As in the two-dimensional loop, the
-// comparisons of FP64 values and the square root run on the integer pipes
-// (bit-pattern orders, the correctly rounded sqrt_rn), which give the same
-// results as the FP64 instructions and leave the FP64 pipe the arithmetic.  Positions live
-// in sphere-id order; a cell reads its frozen neighbours' positions, which
-// no other warp of the same launch writes.
+// Per sweep: k3_begin (draws), k3_bin (bucket every sphere by cell), the
+// eight colour phases -- one persistent k3_sweep launch by default, or eight
+// k3_phase launches -- and k3_end (deterministic sums).  Either way one warp
+// processes one active cell (cell3): it sorts the cell's members by id,
+// gathers the members and every periodic image of the 26 neighbour cells'
+// spheres within sigma of the cell into a shared-memory frame (FP64
+// coordinates and their FP32 roundings), bins the frame across the sweep's
+// axis, and runs the cell's n_m chains.  Each event takes the three rows of
+// bins around the mover, screens their spheres in FP32 with a rigorous
+// margin (a sphere behind the mover or with perpendicular offset >= sigma
+// cannot be hit), tests the survivors in FP64 with the oracle's expressions
+// (no contraction: the library is built with -fmad=false) in one warp-wide
+// pass, and a shuffle reduction picks the first hit by (distance, key).  As
+// in the two-dimensional loop, comparisons of FP64 values and the square
+// root run on the integer pipes (bit-pattern orders, the correctly rounded
+// sqrt_rn): the same results as the FP64 instructions, with the FP64 pipe
+// left the arithmetic.  Positions live in sphere-id order; a cell reads its
+// frozen neighbours' positions, which no warp writes while it runs (later
+// colours wait for it, earlier ones have finished).
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
