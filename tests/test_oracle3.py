@@ -7,9 +7,10 @@ the sweep of Sec. 3.4 to cubic cells in 2x2x2 blocks).
     and behind, a frozen sphere and a wall turning the chain back, ties;
   - one sphere per cell with no contact possible: the chain's end is the
     fold of x +- ell into [0, w], recomputed from Philox;
-  - the pressure against the virial series (B2 = 2 pi sigma^3 / 3,
-    B3 = 5/8 B2^2, B4 = 0.28695 B2^3) at eta = 0.05 and the Carnahan-Starling
-    equation at eta = 0.3;
+  - the pressure against the virial series (B2 = 2 pi sigma^3 / 3, B3 and B4
+    from tests/golden/hard_sphere_virial.txt, itself checked against the
+    closed forms) at eta = 0.05 and the Carnahan-Starling equation at
+    eta = 0.3;
   - no overlap after dense sweeps; identical trajectories when the cells of
     a colour are visited in reverse or the frozen set is taken from all
     spheres; the colour order is a permutation of the eight colours.
@@ -134,12 +135,34 @@ def pressure_batches(N, eta, cells, ell, nm, melt, nbatch, per_batch, seed):
     return 1.0 + vals.mean(), vals.std(ddof=1) / math.sqrt(nbatch), L
 
 
+def sphere_virial_golden():
+    import os
+
+    here = os.path.dirname(os.path.abspath(__file__))
+    vals = {}
+    with open(os.path.join(here, "golden", "hard_sphere_virial.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals
+
+
+def test_sphere_virial_golden_matches_closed_forms():
+    v = sphere_virial_golden()
+    assert v["B3_over_B2sq"] == 0.625
+    b4 = (2707 * math.pi + 438 * math.sqrt(2.0) - 4131 * math.acos(1.0 / 3.0)) / (4480 * math.pi)
+    assert abs(v["B4_over_B2cu"] - b4) < 1e-10
+
+
 def test_low_density_pressure_matches_virial_series():
     N, eta = 1000, 0.05
     z, se, L = pressure_batches(N, eta, 4, 3.0, 20, 20, 20, 40, 3)
+    v = sphere_virial_golden()
     B2 = 2.0 * math.pi / 3.0
     rho = N / L**3
-    virial = 1.0 + B2 * rho + 0.625 * (B2 * rho) ** 2 + 0.28695 * (B2 * rho) ** 3
+    x = B2 * rho
+    virial = 1.0 + x + v["B3_over_B2sq"] * x**2 + v["B4_over_B2cu"] * x**3
     assert abs(z - virial) < 3.5 * se + 1e-3, (z, virial, se)
 
 
