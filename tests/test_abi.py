@@ -110,3 +110,27 @@ def test_suggested_parameters_follow_the_papers_strategy(N, eta):
     assert d["ell"] == pytest.approx(lam * math.sqrt(N / (eta * n)), rel=1e-12)
     assert d["ell"] > 10 * lam
     assert d["n_m"] == max(1, int(math.floor(N / (4 * n) * lam / d["ell"] + 0.5)))
+
+
+def test_headers_compile_as_plain_c():
+    # the boundary is a C ABI: both headers must compile as C99 on their own,
+    # and every declared function must be referable from C
+    import shutil
+    import subprocess
+    import tempfile
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    names = declared_functions()
+    src = '#include "ecmc.h"\n#include "ecmc3.h"\n'
+    src += "typedef void (*fn)(void);\n"
+    src += "fn refs[] = {%s};\n" % ", ".join("(fn)&%s" % n for n in names)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "use.c")
+        with open(path, "w") as f:
+            f.write(src)
+        r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                            "-fsyntax-only", "-I", os.path.join(ROOT, "include"), path],
+                           capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
