@@ -76,7 +76,8 @@ extern "C" {
  * coordinates with rigorous error bounds, the contact decided in FP64.  Both
  * give bit-identical trajectories. */
 #define ECMC_PARAM_PRECISION 3
-/* Replica number: second word of the Philox key (seed, replica). */
+/* Replica number: second word of the Philox key (seed, replica); an integer
+ * in [0, 9e15], so that the double passed to set_param holds it exactly. */
 #define ECMC_PARAM_REPLICA 4
 /* Lanes cooperating on one cell in the sweep kernel: 1, 2, 4, 8, 16, 32, or
  * 0 = automatic (default). */

@@ -44,7 +44,7 @@ typedef struct ecmc3_ctx* ecmc3_t;
 
 /* Parameters for ecmc3_set_param / ecmc3_get_param. */
 #define ECMC3_PARAM_N_CHAINS 1   /* chains per cell and sweep, n_m >= 1 (default 1) */
-#define ECMC3_PARAM_REPLICA 4    /* Philox key word 1 (default 0)                   */
+#define ECMC3_PARAM_REPLICA 4    /* Philox key word 1, integer in [0, 9e15] (default 0) */
 /* 1 (default): one persistent launch per sweep, in which each cell waits
  * (bounded, ECMC_ERR_TIMEOUT after 5 s) for the neighbours of earlier colours
  * of the sweep; 0: one launch per colour phase.  Same results bit for bit;

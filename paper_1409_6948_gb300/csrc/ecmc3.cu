@@ -1082,7 +1082,7 @@ int ecmc3_set_param(ecmc3_t h, int key, double v) {
       return ECMC_OK;
     }
     case ECMC3_PARAM_REPLICA:
-      if (!(v >= 0.0) || v != std::floor(v)) return fail3(ECMC_ERR_ARG, "replica");
+      if (!(v >= 0.0) || v != std::floor(v) || v > 9.0e15) return fail3(ECMC_ERR_ARG, "replica");
       h->g.replica = (uint64_t)v;
       return ECMC_OK;
     case ECMC3_PARAM_PERSISTENT:
