@@ -108,6 +108,17 @@ def lib():
         L.orc3_run_chain_frame.restype = C.c_int
         L.orc3_min_dist2.argtypes = [i64, C.c_double, d, d, d, C.c_double]
         L.orc3_min_dist2.restype = C.c_double
+        L.orc_stripe_draws.argtypes = [C.POINTER(Params), i64, d, C.POINTER(C.c_int)]
+        L.orc_stripe_draws.restype = None
+        L.orc_stripe_bin.argtypes = [C.POINTER(Params), i64, d, d, C.POINTER(C.c_int32)]
+        L.orc_stripe_bin.restype = C.c_int
+        L.orc_stripe_sweeps.argtypes = [C.POINTER(Params), d, d, i64, i64, C.POINTER(Stats),
+                                        C.c_void_p]
+        L.orc_stripe_sweeps.restype = C.c_int
+        L.orc_run_chain_stripe.argtypes = [C.c_int, C.c_int, d, d, C.POINTER(C.c_int64),
+                                           C.c_double, C.c_double, C.c_int, C.c_int,
+                                           C.c_double, C.c_int, C.POINTER(Stats), C.c_void_p]
+        L.orc_run_chain_stripe.restype = C.c_int
         _lib = L
     return _lib
 
@@ -266,6 +277,57 @@ def pressure_from_gcontact(g_contact, N, L, sigma):
     """eq. (pressure): beta P sigma^2 = sigma^2 rho (1 + pi/2 sigma^2 rho g(sigma+))."""
     rho = N / (L * L)
     return sigma * sigma * rho * (1.0 + 0.5 * math.pi * sigma * sigma * rho * g_contact)
+
+
+# ---- striped decomposition (Fig. 3 "stripes") -----------------------------
+
+def stripe_draws(p, t):
+    """(shift across the axis, colour that runs first) of sweep t."""
+    sh, first = C.c_double(), C.c_int()
+    lib().orc_stripe_draws(C.byref(p), int(t), C.byref(sh), C.byref(first))
+    return sh.value, first.value
+
+
+def stripe_bin(p, t, x, y):
+    out = np.empty(p.N, np.int32)
+    rc = lib().orc_stripe_bin(C.byref(p), int(t), _dptr(x), _dptr(y),
+                              out.ctypes.data_as(C.POINTER(C.c_int32)))
+    if rc != 0:
+        raise ValueError("oracle rejected the parameters")
+    return out
+
+
+def stripe_sweeps(p, x, y, t0, n_sweeps, stats=None, records=False):
+    """Sweeps of the striped decomposition in place on x, y (p.cells_x
+    stripes).  Returns (stats, records [n_sweeps, stripes, n_m] or None)."""
+    st = stats if stats is not None else Stats()
+    recs = None
+    rp = None
+    if records:
+        recs = np.zeros((n_sweeps, p.cells_x, p.n_m), CHAIN_REC)
+        rp = recs.ctypes.data_as(C.c_void_p)
+    rc = lib().orc_stripe_sweeps(C.byref(p), _dptr(x), _dptr(y), int(t0), int(n_sweeps),
+                                 C.byref(st), rp)
+    if rc != 0:
+        raise ValueError("oracle rejected the parameters (rc=%d)" % rc)
+    return st, recs
+
+
+def run_chain_stripe(U, V, n_mem, m, sign, ell, L, sigma=1.0, keys=None, reject=True):
+    """One chain on an explicit stripe frame; returns (U, stats, record, rejected)."""
+    U = np.ascontiguousarray(U, dtype=np.float64).copy()
+    V = np.ascontiguousarray(V, dtype=np.float64).copy()
+    n = U.shape[0]
+    keys = np.arange(n, dtype=np.int64) if keys is None else np.asarray(keys, np.int64)
+    st = Stats()
+    rec = np.zeros(1, CHAIN_REC)
+    rc = lib().orc_run_chain_stripe(n, int(n_mem), _dptr(U), _dptr(V),
+                                    keys.ctypes.data_as(C.POINTER(C.c_int64)), float(L),
+                                    float(sigma), int(m), int(sign), float(ell), int(reject),
+                                    C.byref(st), rec.ctypes.data_as(C.c_void_p))
+    if rc < 0:
+        raise ValueError("bad frame")
+    return U, st, rec[0], rc == 1
 
 
 # ---- three dimensions ------------------------------------------------------

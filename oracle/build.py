@@ -10,8 +10,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
-SRC = [os.path.join(HERE, "ecmc_oracle.c"), os.path.join(HERE, "ecmc_oracle3.c")]
-HDR = [os.path.join(HERE, "ecmc_oracle.h"), os.path.join(HERE, "ecmc_oracle3.h")]
+SRC = [os.path.join(HERE, f) for f in ("ecmc_oracle.c", "ecmc_oracle3.c", "ecmc_oracle_stripes.c")]
+HDR = [os.path.join(HERE, f) for f in ("ecmc_oracle.h", "ecmc_oracle3.h", "ecmc_oracle_stripes.h")]
 
 # -ffp-contract=off: no fused multiply-add anywhere, so every product and sum
 # is rounded on its own, on x86-64 and on aarch64 alike.
