@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libecmc.so")
 SOURCES = ["ecmc_api.cu", "ecmc_bin.cu", "ecmc_frame.cu", "ecmc_phase.cu", "ecmc_measure.cu",
-           "ecmc_noalloc.cu", "ecmc_sweep.cu", "ecmc3.cu"]
+           "ecmc_noalloc.cu", "ecmc_sweep.cu", "ecmc3.cu", "ecmc_stripes.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fvisibility=hidden", "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -30,7 +30,7 @@ def nvcc():
 
 def _deps():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    files.append(os.path.join(ROOT, "include", "ecmc.h"))
+    files += [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))]
     files.append(os.path.abspath(__file__))
     return files
 

@@ -153,6 +153,22 @@ _SIGS = {
     "ecmc3_min_distance": (C.c_int, [_H, C.POINTER(C.c_double)]),
     "ecmc3_last_cells": (C.c_int, [_H, C.c_void_p]),
     "ecmc3_chain_records": (C.c_int, [_H, C.c_void_p]),
+    "ecmc_stripes_create": (C.c_int, [C.POINTER(_H), C.c_int64, C.c_double, C.c_double, C.c_int,
+                                      C.c_double, C.c_uint64]),
+    "ecmc_stripes_destroy": (C.c_int, [_H]),
+    "ecmc_stripes_set_param": (C.c_int, [_H, C.c_int, C.c_double]),
+    "ecmc_stripes_get_param": (C.c_int, [_H, C.c_int, C.POINTER(C.c_double)]),
+    "ecmc_stripes_set_stream": (C.c_int, [_H, C.c_void_p]),
+    "ecmc_stripes_set_positions": (C.c_int, [_H, C.c_void_p, C.c_int, C.c_int64]),
+    "ecmc_stripes_positions": (C.c_int, [_H, C.c_void_p, C.c_int]),
+    "ecmc_stripes_sweep": (C.c_int, [_H, C.c_int64]),
+    "ecmc_stripes_synchronize": (C.c_int, [_H]),
+    "ecmc_stripes_sweep_index": (C.c_int, [_H, C.POINTER(C.c_int64)]),
+    "ecmc_stripes_counters": (C.c_int, [_H, C.POINTER(Counters)]),
+    "ecmc_stripes_pressure": (C.c_int, [_H, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "ecmc_stripes_reset_stats": (C.c_int, [_H]),
+    "ecmc_stripes_last_stripes": (C.c_int, [_H, C.c_void_p]),
+    "ecmc_stripes_chain_records": (C.c_int, [_H, C.c_void_p]),
     "ecmc_strerror": (C.c_char_p, [C.c_int]),
     "ecmc_last_error_message": (C.c_char_p, []),
     "ecmc_version": (C.c_char_p, []),
@@ -512,6 +528,111 @@ class Ecmc3:
         out = np.empty((self.cells ** 3, nm, 4), np.int32)
         _check(load().ecmc3_chain_records(self._h, C.c_void_p(out.ctypes.data)),
                "ecmc3_chain_records")
+        return out
+
+
+PARAM_STRIPES_N_CHAINS = 1
+PARAM_STRIPES_REPLICA = 4
+PARAM_STRIPES_BOUNDARY = 21
+
+
+class EcmcStripes:
+    """One hard-disk system swept with the striped decomposition of Fig. 3
+    (include/ecmc_stripes.h): N = k^2 disks in a periodic square of side L,
+    `stripes` stripes parallel to the chain axis, chains of displacement
+    ell, rejected at a frozen disk by default; square lattice start."""
+
+    def __init__(self, N, L, sigma, stripes, ell, seed):
+        lib = load()
+        h = _H()
+        _check(lib.ecmc_stripes_create(C.byref(h), int(N), float(L), float(sigma), int(stripes),
+                                       float(ell), C.c_uint64(int(seed))), "ecmc_stripes_create")
+        self._h = h
+        self.N, self.L, self.sigma, self.stripes = int(N), float(L), float(sigma), int(stripes)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ecmc_stripes_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_param(self, key, value):
+        _check(load().ecmc_stripes_set_param(self._h, int(key), float(value)),
+               "ecmc_stripes_set_param")
+
+    def get_param(self, key):
+        v = C.c_double()
+        _check(load().ecmc_stripes_get_param(self._h, int(key), C.byref(v)),
+               "ecmc_stripes_get_param")
+        return v.value
+
+    def set_stream(self, stream):
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        _check(load().ecmc_stripes_set_stream(self._h, C.c_void_p(stream or 0)),
+               "ecmc_stripes_set_stream")
+
+    def set_positions(self, xy, t0=0):
+        p, dev = _ptr(xy)
+        _check(load().ecmc_stripes_set_positions(self._h, p, dev, int(t0)),
+               "ecmc_stripes_set_positions")
+
+    def positions(self, out=None):
+        if out is None:
+            out = np.empty(2 * self.N)
+        p, dev = _ptr(out)
+        _check(load().ecmc_stripes_positions(self._h, p, dev), "ecmc_stripes_positions")
+        return out
+
+    def sweep(self, n=1):
+        _check(load().ecmc_stripes_sweep(self._h, int(n)), "ecmc_stripes_sweep")
+
+    def synchronize(self):
+        _check(load().ecmc_stripes_synchronize(self._h), "ecmc_stripes_synchronize")
+
+    def sweep_index(self):
+        t = C.c_int64()
+        _check(load().ecmc_stripes_sweep_index(self._h, C.byref(t)), "ecmc_stripes_sweep_index")
+        return t.value
+
+    def counters(self):
+        c = Counters()
+        _check(load().ecmc_stripes_counters(self._h, C.byref(c)), "ecmc_stripes_counters")
+        return c
+
+    def pressure(self):
+        p, se = C.c_double(), C.c_double()
+        _check(load().ecmc_stripes_pressure(self._h, C.byref(p), C.byref(se)),
+               "ecmc_stripes_pressure")
+        return p.value, se.value
+
+    def reset_stats(self):
+        _check(load().ecmc_stripes_reset_stats(self._h), "ecmc_stripes_reset_stats")
+
+    def last_stripes(self):
+        out = np.empty(self.N, np.int32)
+        _check(load().ecmc_stripes_last_stripes(self._h, C.c_void_p(out.ctypes.data)),
+               "ecmc_stripes_last_stripes")
+        return out
+
+    def chain_records(self):
+        """Records of the last sweep: [stripes, n_m] of (start_id, end_id,
+        contacts, 0)."""
+        nm = int(self.get_param(PARAM_STRIPES_N_CHAINS))
+        out = np.empty((self.stripes, nm, 4), np.int32)
+        _check(load().ecmc_stripes_chain_records(self._h, C.c_void_p(out.ctypes.data)),
+               "ecmc_stripes_chain_records")
         return out
 
 

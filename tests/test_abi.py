@@ -1,5 +1,5 @@
 """The C-ABI library (no GPU needed): it loads, exports every function that
-include/ecmc.h and include/ecmc3.h declare, and rejects invalid arguments
+the headers under include/ declare, and rejects invalid arguments
 before touching the device."""
 import ctypes as C
 import os
@@ -81,6 +81,24 @@ def test_invalid_three_dimensional_arguments_are_rejected(args):
     assert rc == E.ERR_ARG and not h.value
 
 
+@pytest.mark.parametrize("args", [
+    (0, 10.0, 1.0, 2, 1.0, 1),           # no disks
+    (63, 10.0, 1.0, 2, 1.0, 1),          # N not a perfect square
+    (64, 10.0, 1.0, 3, 1.0, 1),          # odd number of stripes
+    (64, 10.0, 1.0, 12, 1.0, 1),         # stripe width below sigma
+    (144, 11.0, 1.0, 2, 1.0, 1),         # square lattice spacing below sigma
+    (64, 10.0, 1.0, 2, -1.0, 1),         # negative displacement
+    (64, float("inf"), 1.0, 2, 1.0, 1),  # infinite box
+])
+def test_invalid_stripe_arguments_are_rejected(args):
+    lib = P.load()
+    h = C.c_void_p()
+    N, L, sigma, stripes, ell, seed = args
+    rc = lib.ecmc_stripes_create(C.byref(h), N, L, sigma, stripes, ell, seed)
+    assert rc == E.ERR_ARG and not h.value
+    assert lib.ecmc_stripes_create(None, 64, 10.0, 1.0, 2, 1.0, 1) == E.ERR_ARG
+
+
 def test_null_handle_calls_fail_cleanly():
     lib = P.load()
     assert lib.ecmc_sweep(None, 1) == E.ERR_ARG
@@ -90,6 +108,10 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.ecmc3_sweep(None, 1) == E.ERR_ARG
     assert lib.ecmc3_destroy(None) == 0
     assert lib.ecmc3_pressure(None, C.byref(d), None) == E.ERR_ARG
+    assert lib.ecmc_stripes_sweep(None, 1) == E.ERR_ARG
+    assert lib.ecmc_stripes_destroy(None) == 0
+    assert lib.ecmc_stripes_pressure(None, C.byref(d), None) == E.ERR_ARG
+    assert lib.ecmc_stripes_set_param(None, 1, 1.0) == E.ERR_ARG
 
 
 @pytest.mark.parametrize("N,eta", [(1048576, 0.72), (262144, 0.70), (4096, 0.60), (65536, 0.708),
@@ -113,7 +135,7 @@ def test_suggested_parameters_follow_the_papers_strategy(N, eta):
 
 
 def test_headers_compile_as_plain_c():
-    # the boundary is a C ABI: both headers must compile as C99 on their own,
+    # the boundary is a C ABI: every header must compile as C99 on its own,
     # and every declared function must be referable from C
     import shutil
     import subprocess
@@ -123,7 +145,8 @@ def test_headers_compile_as_plain_c():
     if gcc is None:
         pytest.skip("no C compiler")
     names = declared_functions()
-    src = '#include "ecmc.h"\n#include "ecmc3.h"\n'
+    headers = sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h"))
+    src = "".join('#include "%s"\n' % f for f in headers)
     src += "typedef void (*fn)(void);\n"
     src += "fn refs[] = {%s};\n" % ", ".join("(fn)&%s" % n for n in names)
     with tempfile.TemporaryDirectory() as d:
