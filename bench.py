@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--fig3", action="store_true",
                     help="g(r) near contact and P(g(sigma+)) vs n_m: reflecting and rejecting "
                          "boundary rules, start lists with and without replacement")
+    ap.add_argument("--stripes", action="store_true",
+                    help="striped decomposition of Fig. 3: events/s at N = 256^2, eta = 0.708 "
+                         "over stripes x ell, both boundary rules")
     ap.add_argument("--dim3", action="store_true",
                     help="hard spheres in three dimensions: events/s over cells x ell (N = 64^3)")
     ap.add_argument("--grid", action="store_true",
@@ -562,6 +565,77 @@ def run_dim3(args):
     return 0
 
 
+def run_stripes(args):
+    """The striped decomposition of Fig. 3 (include/ecmc_stripes.h) on the
+    Fig. 3 system, N = 256^2 disks at eta = 0.708 from the square lattice:
+    stripes S in {16, 32, 64}, chain displacement ell in {1, 8} sigma, n_m per
+    stripe chosen so that a sweep displaces about every disk once (N / S
+    lambda / ell with the mean free path lambda = 0.05 sigma measured at this
+    density), for the rejecting (the paper's) and the reflecting rule.  Each
+    point melts 20 sweeps and times --steps sweeps with CUDA events on the
+    library's stream.  The oracle (orc_stripe_sweeps) is timed on a bounded
+    sample of the first point on one host core."""
+    import torch
+
+    import oracle
+    import paper_1409_6948_gb300 as P
+    from paper_1409_6948_gb300 import ecmc as E
+
+    torch.cuda.set_device(0)
+    N, eta, seed, lam = 65536, 0.708, 7, 0.05
+    L = W.box_side(N, eta)
+    pts = []
+    for boundary in (E.BOUNDARY_REJECT, E.BOUNDARY_REFLECT):
+        for S in (16, 32, 64):
+            for ell in (1.0, 8.0):
+                nm = max(1, int(round(N / S * lam / ell)))
+                g = P.EcmcStripes(N, L, 1.0, S, ell, seed)
+                g.set_param(E.PARAM_STRIPES_N_CHAINS, nm)
+                g.set_param(E.PARAM_STRIPES_BOUNDARY, boundary)
+                s = torch.cuda.Stream()
+                g.set_stream(s)
+                g.sweep(20)
+                g.reset_stats()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(s)
+                g.sweep(args.steps)
+                b.record(s)
+                g.synchronize()
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b)
+                c = g.counters()
+                pt = {"boundary": "reject" if boundary == E.BOUNDARY_REJECT else "reflect",
+                      "stripes": S, "ell": ell, "n_m": nm, "sweeps": args.steps,
+                      "events_per_s": c.events / (ms * 1e-3),
+                      "sweeps_per_s": args.steps / (ms * 1e-3), "ms_per_sweep": ms / args.steps,
+                      "events_per_sweep": c.events / args.steps,
+                      "rejected_fraction": c.rejected_chains / max(c.chains, 1)}
+                pts.append(pt)
+                print(json.dumps(pt), flush=True)
+                g.set_stream(None)
+                g.close()
+    cpu = None
+    if args.cpu_seconds > 0:
+        p0 = pts[0]
+        x, y = W.square_lattice(N, L)
+        p = oracle.make_params(N, L, 1.0, p0["stripes"], p0["stripes"], p0["ell"], p0["n_m"],
+                               seed, boundary=oracle.BOUNDARY_REJECT)
+        oracle.stripe_sweeps(p, x, y, 0, 2)
+        t0 = time.perf_counter()
+        n = 0
+        st = oracle.Stats()
+        while time.perf_counter() - t0 < args.cpu_seconds and n < 200:
+            oracle.stripe_sweeps(p, x, y, 2 + n, 1, stats=st)
+            n += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": st.events / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
+               "sample": "%d sweeps of the first point (%.1f s)" % (n, dt)}
+    best = max(pts, key=lambda q: q["events_per_s"])
+    print(json.dumps({"mode": "stripes", "workload": "N=65536 (256^2) disks eta=0.708, stripes",
+                      "best": best, "points": pts, "cpu_baseline": cpu}))
+    return 0
+
+
 def run_tau(args):
     """Sampling efficiency (Sec. 2 eq. tau; Figs. 5-6): the autocorrelation
     time tau of the hexatic order parameter Psi for N = 64^2 disks at
@@ -1011,6 +1085,8 @@ def main():
         return run_listbias(args)
     if args.fig3:
         return run_fig3(args)
+    if args.stripes:
+        return run_stripes(args)
     if args.dim3:
         return run_dim3(args)
     if args.tau:
