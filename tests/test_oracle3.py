@@ -13,7 +13,12 @@ the sweep of Sec. 3.4 to cubic cells in 2x2x2 blocks).
     eta = 0.3;
   - no overlap after dense sweeps; identical trajectories when the cells of
     a colour are visited in reverse or the frozen set is taken from all
-    spheres; the colour order is a permutation of the eight colours.
+    spheres; the colour order is a permutation of the eight colours;
+  - three spheres in a periodic cube: the sampled pair-distance histogram
+    below L/2 matches the exact distribution of the uniform measure
+    (tests/threesphere_exact.py, itself checked against rejection sampling).
+    A sign always + or a chain that stops at the wall instead of turning
+    back fails it by orders of magnitude.
 """
 import math
 
@@ -22,6 +27,7 @@ import pytest
 
 import ecmc_workloads as W
 import oracle
+import threesphere_exact as T3
 
 W_CELL = 10.0
 
@@ -208,3 +214,57 @@ def test_colour_orders_are_permutations():
         assert all(0.0 <= s < 5.0 for s in sh)
         seen.add(tuple(perm))
     assert len(seen) > 190  # 8! orders: repeats are rare
+
+
+# -- three spheres: the uniform measure ----------------------------------------
+L3S = 3.2
+EDGES3 = np.linspace(1.0, 0.5 * L3S, 11)
+
+
+def test_exact_three_sphere_distribution_matches_rejection_sampling():
+    p = T3.bin_probabilities(EDGES3, L3S, 1.0)
+    assert np.abs(T3.bin_probabilities(EDGES3, L3S, 1.0, n_dir=12000, n_r=20) / p - 1).max() < 1e-7
+    rng = np.random.default_rng(5)
+    hist = np.zeros(len(EDGES3) - 1)
+    for _ in range(8):
+        P = rng.random((500_000, 3, 3)) * L3S
+
+        def md(a, b):
+            d = a - b
+            d -= L3S * np.round(d / L3S)
+            return np.sqrt((d * d).sum(-1))
+
+        d12, d13, d23 = md(P[:, 0], P[:, 1]), md(P[:, 0], P[:, 2]), md(P[:, 1], P[:, 2])
+        ok = (d12 >= 1.0) & (d13 >= 1.0) & (d23 >= 1.0)
+        hist += np.histogram(np.concatenate([d12[ok], d13[ok], d23[ok]]), EDGES3)[0]
+    n = hist.sum() / 3.0  # conservative: the three pairs of a sample are dependent
+    z = (hist / hist.sum() - p) / np.sqrt(p * (1 - p) / n)
+    assert np.max(np.abs(z)) < 5.0
+
+
+@pytest.mark.parametrize("ell,nm", [(2.0, 4), (0.7, 2)])
+def test_three_spheres_sample_the_uniform_measure(ell, nm):
+    x = np.array([0.3, 1.5, 2.6])
+    y = np.array([0.4, 2.1, 1.1])
+    z = np.array([0.2, 1.2, 2.5])
+    p3 = oracle.make_params3(3, L3S, 1.0, 2, ell, nm, 3)
+    oracle.sweeps3(p3, x, y, z, 0, 100)
+    n = 200_000
+    S = np.empty((n, 3, 3))
+    st = oracle.Stats()
+    for s in range(n):
+        oracle.sweeps3(p3, x, y, z, 100 + s, 1, stats=st)
+        S[s, :, 0], S[s, :, 1], S[s, :, 2] = x, y, z
+
+    def md(i, j):
+        d = S[:, i] - S[:, j]
+        d -= L3S * np.round(d / L3S)
+        return np.sqrt((d * d).sum(-1))
+
+    d = np.stack([md(0, 1), md(0, 2), md(1, 2)], 1)
+    hb = np.array([np.histogram(b.ravel(), EDGES3)[0] for b in np.array_split(d, 50)], float)
+    hb /= hb.sum(1, keepdims=True)
+    se = hb.std(0, ddof=1) / math.sqrt(50)
+    zz = (hb.mean(0) - T3.bin_probabilities(EDGES3, L3S, 1.0)) / se
+    assert st.frozen_hits > 0 and st.wall_hits > 0 and st.lifts > 0
+    assert np.mean(zz**2) < 2.5 and np.max(np.abs(zz)) < 4.5
