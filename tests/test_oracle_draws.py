@@ -107,3 +107,27 @@ def test_3d_binning_matches_exact_arithmetic():
     assert bad <= 2
     counts = np.bincount(cell, minlength=cells**3)
     assert counts.sum() == N and len(counts) == cells**3
+
+
+@pytest.mark.parametrize("seed,replica", [(4, 0), (99, 7)])
+def test_start_disks_are_drawn_with_replacement_by_the_stated_rule(seed, replica):
+    # every chain record's start disk is member floor(v0 n_c / 2^64), in
+    # ascending id, of its cell, v0 the first Philox word of (t, 1, c, k)
+    N, eta, cells, nm = 1024, 0.70, 4, 6
+    L = W.box_side(N, eta)
+    x, y = W.square_lattice(N, L)
+    p = oracle.make_params(N, L, 1.0, cells, cells, 1.0, nm, seed, replica)
+    oracle.sweeps(p, x, y, 0, 2)
+    repeats = 0
+    for t in (2, 3):
+        cell = oracle.bin_cells(p, t, x, y)
+        _, recs = oracle.sweeps(p, x, y, t, 1, records=True)
+        for c in range(cells * cells):
+            members = np.flatnonzero(cell == c)  # ascending id
+            starts = []
+            for k in range(nm):
+                v = numpy_philox([t, 1, c, k], [seed, replica])
+                starts.append(int(members[(v[0] * len(members)) >> 64]))
+            assert recs[0, c, :]["start_id"].tolist() == starts
+            repeats += len(starts) - len(set(starts))
+    assert repeats > 0  # 6 draws from about 64 members repeat in about a fifth of the cells
