@@ -103,8 +103,8 @@ class Workload:
 
 # The paper's workloads (Sec. 3.4 and Sec. 4: N = 256^2 at eta 0.698-0.718,
 # N = 64^2 at 0.704) and the sizes used here, all started from square lattices.
-SMALL = Workload("N=256 eta=0.70 2x2 cells ell=4", 256, 0.70, 2, 4.0, seed=1, sweeps=1000)
-MEDIUM = Workload("N=65536 eta=0.708 32x32 cells ell=8", 65536, 0.708, 32, 8.0, seed=2,
+SMALL = Workload("N=256 eta=0.70", 256, 0.70, 2, 4.0, seed=1, sweeps=1000)
+MEDIUM = Workload("N=65536 eta=0.708", 65536, 0.708, 32, 8.0, seed=2,
                   sweeps=10000)
 LARGE = Workload("N=1048576 eta=0.72", 1048576, 0.72, 128, 8.0, seed=3)
 HUGE = Workload("N=4194304 eta=0.716", 4194304, 0.716, 256, 8.0, seed=5)
