@@ -200,3 +200,41 @@ def test_single_disk_plus_minus_keeps_uniform_density():
     assert ok.all()
     hist = np.histogram(x1, bins=10, range=(0, 5))[0]
     assert np.sum((hist - 400.0) ** 2 / 400.0) < 30.0  # 9 degrees of freedom
+
+
+# -- no disk passes through another ------------------------------------------
+def cyclic_orders_kept(along0, along1, across, L):
+    """Disks less than sigma apart across the axis can never pass each other
+    along it, so in every sigma-wide strip across the axis the cyclic order
+    along the axis is the same after a sweep as before."""
+    strip = np.floor(across).astype(np.int64)
+    checked = 0
+    for q in np.unique(strip):
+        ids = np.flatnonzero(strip == q)
+        if len(ids) < 3:
+            continue
+        before = ids[np.argsort(along0[ids], kind="stable")].tolist()
+        after = ids[np.argsort(along1[ids], kind="stable")].tolist()
+        k = after.index(before[0])
+        if after[k:] + after[:k] != before:
+            return False, checked
+        checked += 1
+    return True, checked
+
+
+@pytest.mark.parametrize("boundary", [oracle.BOUNDARY_REFLECT, oracle.BOUNDARY_REJECT])
+@pytest.mark.parametrize("N,cells,ell,nm", [(4096, 16, 1.5, 6),
+                                            (1024, 2, 4.0, 64)])  # frames span half the box
+def test_chains_never_carry_a_disk_through_another(boundary, N, cells, ell, nm):
+    eta = 0.72
+    L = W.box_side(N, eta)
+    x, y = W.square_lattice(N, L)
+    p = oracle.make_params(N, L, 1.0, cells, cells, ell, nm, 13, boundary=boundary)
+    oracle.sweeps(p, x, y, 0, 4)
+    for t in range(4, 10):
+        x0, y0 = x.copy(), y.copy()
+        oracle.sweeps(p, x, y, t, 1)
+        along0, along1, across = (x0, x, y0) if t % 2 == 0 else (y0, y, x0)
+        ok, checked = cyclic_orders_kept(along0, along1, across, L)
+        assert ok, "a disk passed through another in sweep %d" % t
+        assert checked >= 0.8 * math.floor(L)  # nearly every strip holds 3 or more

@@ -35,6 +35,7 @@ from test_oracle_gcontact import virial_golden
 from test_oracle_threedisk import FAIL_CHI2, NBATCH, PASS_CHI2, edges_for
 
 L10 = 10.0
+REJECT_, REFLECT_ = oracle.BOUNDARY_REJECT, oracle.BOUNDARY_REFLECT
 
 
 def chain(U, V, n_mem, m, sign, ell, reject=True, keys=None):
@@ -259,3 +260,18 @@ def test_low_density_pressure_matches_virial_series(boundary):
     v = np.array(via_chain if boundary == oracle.BOUNDARY_REFLECT else via_g)
     z, se = v.mean(), v.std(ddof=1) / math.sqrt(len(v))
     assert abs(z - vir) < 4.0 * se + 1e-3, (z, vir, se)
+
+
+@pytest.mark.parametrize("boundary", [REJECT_, REFLECT_])
+def test_stripe_chains_never_carry_a_disk_through_another(boundary):
+    from test_oracle_invariants import cyclic_orders_kept
+
+    p, x, y, L = dense(boundary=boundary, ell=3.0)
+    oracle.stripe_sweeps(p, x, y, 0, 4)
+    for t in range(4, 10):
+        x0, y0 = x.copy(), y.copy()
+        oracle.stripe_sweeps(p, x, y, t, 1)
+        along0, along1, across = (x0, x, y0) if t % 2 == 0 else (y0, y, x0)
+        ok, checked = cyclic_orders_kept(along0, along1, across, L)
+        assert ok, "a disk passed through another in sweep %d" % t
+        assert checked > 10
