@@ -268,3 +268,36 @@ def test_three_spheres_sample_the_uniform_measure(ell, nm):
     zz = (hb.mean(0) - T3.bin_probabilities(EDGES3, L3S, 1.0)) / se
     assert st.frozen_hits > 0 and st.wall_hits > 0 and st.lifts > 0
     assert np.mean(zz**2) < 2.5 and np.max(np.abs(zz)) < 4.5
+
+
+def test_chains_never_carry_a_sphere_through_another():
+    # spheres in one column of side sigma / sqrt 2 across the axis are less
+    # than sigma apart across it, so they can never pass each other along
+    # it: the cyclic order along the axis in every column survives a sweep
+    N, eta = 4096, 0.45
+    L = W.box_side3(N, eta)
+    x, y, z = W.cubic_lattice(N, L)
+    p = oracle.make_params3(N, L, 1.0, 8, 2.0, 4, 17)
+    oracle.sweeps3(p, x, y, z, 0, 3)
+    side = 1.0 / math.sqrt(2.0)
+    checked = 0
+    for t in range(3, 9):
+        before = [x.copy(), y.copy(), z.copy()]
+        oracle.sweeps3(p, x, y, z, t, 1)
+        a = t % 3
+        pa, qa = [k for k in range(3) if k != a]
+        col = (np.floor(before[pa] / side).astype(np.int64) * 100000
+               + np.floor(before[qa] / side).astype(np.int64))
+        after = [x, y, z][a]
+        for c in np.unique(col):
+            ids = np.flatnonzero(col == c)
+            if len(ids) < 3:
+                continue
+            o0 = ids[np.argsort(before[a][ids], kind="stable")].tolist()
+            o1 = ids[np.argsort(after[ids], kind="stable")].tolist()
+            k = o1.index(o0[0])
+            assert o1[k:] + o1[:k] == o0, "a sphere passed through another in sweep %d" % t
+            checked += 1
+        # across the axis only the frame round trip's rounding moves a sphere
+        assert np.abs(before[pa] - [x, y, z][pa]).max() < 1e-12 * L
+    assert checked > 100
