@@ -157,3 +157,66 @@ def test_headers_compile_as_plain_c():
                             "-fsyntax-only", "-I", os.path.join(ROOT, "include"), path],
                            capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def header_constants():
+    out = {}
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            with open(os.path.join(ROOT, "include", fn)) as f:
+                for m in re.finditer(r"^#define\s+(ECMC\w*)\s+(-?\d+)\b", f.read(), re.M):
+                    out[m.group(1)] = int(m.group(2))
+    return out
+
+
+def test_binding_constants_equal_the_headers():
+    # ECMC_X -> X, ECMC3_PARAM_X -> PARAM3_X, ECMC_STRIPES_PARAM_X -> PARAM_STRIPES_X
+    consts = header_constants()
+    assert len(consts) > 40
+    for name, value in consts.items():
+        if name.startswith("ECMC3_PARAM_"):
+            py = "PARAM3_" + name[len("ECMC3_PARAM_"):]
+        elif name.startswith("ECMC_STRIPES_PARAM_"):
+            py = "PARAM_STRIPES_" + name[len("ECMC_STRIPES_PARAM_"):]
+        else:
+            py = name[len("ECMC_"):]
+        assert getattr(E, py) == value, (name, py)
+
+
+def test_binding_structs_match_the_c_layout():
+    # sizes and field offsets as the C compiler lays the header's structs out
+    import shutil
+    import subprocess
+    import tempfile
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    structs = {"ecmc_counters_t": E.Counters, "ecmc_timing_t": E.Timing,
+               "ecmc_tune_result_t": E.TuneResult, "ecmc_replica_desc_t": E.ReplicaDesc}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ecmc.h"', 'int main(void) {']
+    for cname, cls in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines.append('printf("ecmc_chain_rec_t %zu\\n", sizeof(ecmc_chain_rec_t));')
+    for f in E.CHAIN_REC.names:
+        lines.append('printf("ecmc_chain_rec_t.%s %%zu\\n", offsetof(ecmc_chain_rec_t, %s));'
+                     % (f, f))
+    lines.append("return 0; }")
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        with open(src, "w") as f:
+            f.write("\n".join(lines))
+        r = subprocess.run([gcc, "-std=c99", "-I", os.path.join(ROOT, "include"), src, "-o", exe],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    c = dict(ln.rsplit(" ", 1) for ln in out.splitlines())
+    for cname, cls in structs.items():
+        assert int(c[cname]) == C.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert int(c[cname + "." + f]) == getattr(cls, f).offset, (cname, f)
+    assert int(c["ecmc_chain_rec_t"]) == E.CHAIN_REC.itemsize
+    for f in E.CHAIN_REC.names:
+        assert int(c["ecmc_chain_rec_t." + f]) == E.CHAIN_REC.fields[f][1], f
