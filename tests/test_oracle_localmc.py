@@ -7,7 +7,10 @@ paper's Fig. 3: N = 100 disks at eta = 0.55, ordered-pair counts in ten
     Monte Carlo in every bin;
   - shuffled lists of distinct starts (n_m = 10 > 1) distort g(r) right at
     contact, as Fig. 3 (left) shows: the first bin falls many standard errors
-    below the reference.
+    below the reference;
+  - the same for the striped decomposition under the rejecting rule (two
+    stripes of 50 disks, n_m = 40): with replacement it agrees, shuffled
+    lists are biased.
 """
 import ctypes as C
 import math
@@ -85,3 +88,31 @@ def test_with_replacement_matches_local_monte_carlo(local_mc):
 def test_shuffled_lists_distort_contact_values(local_mc):
     z = zscores(local_mc, pec_counts(oracle.LIST_WITHOUT_REPL))
     assert z[0] < -6.0 and np.mean(z**2) > 10.0, z
+
+
+def stripe_counts(list_mode, nm=40):
+    # two stripes of 50 disks: n_m = 40 chains per stripe
+    L = W.box_side(N, ETA)
+    x, y = W.square_lattice(N, L)
+    p = oracle.make_params(N, L, 1.0, 2, 2, 1.0, nm, 5, list_mode=list_mode,
+                           boundary=oracle.BOUNDARY_REJECT)
+    oracle.stripe_sweeps(p, x, y, 0, 500)
+    t, out = 500, []
+    for _ in range(NBATCH):
+        c = np.zeros(NB, np.int64)
+        for _ in range(PER):
+            oracle.stripe_sweeps(p, x, y, t, 1)
+            t += 1
+            c += oracle.gr_counts(L, x, y, R0, DR, NB)
+        out.append(c / PER)
+    return np.array(out)
+
+
+def test_stripes_with_replacement_match_local_monte_carlo(local_mc):
+    z = zscores(local_mc, stripe_counts(oracle.LIST_WITH_REPL))
+    assert np.mean(z**2) < 2.5 and np.max(np.abs(z)) < 4.5, z
+
+
+def test_stripes_with_shuffled_lists_are_biased(local_mc):
+    z = zscores(local_mc, stripe_counts(oracle.LIST_WITHOUT_REPL))
+    assert np.mean(z**2) > 10.0, z
