@@ -4,7 +4,8 @@ paper's Fig. 3: N = 100 disks at eta = 0.55, ordered-pair counts in ten
 0.05 sigma bins from sigma, batch means on both sides.
 
   - the PEC sweep with start disks drawn with replacement agrees with local
-    Monte Carlo in every bin;
+    Monte Carlo in every bin, for the reflecting and the rejecting rule
+    ("PEC-refl" and "PEC-rej" of Fig. 3);
   - shuffled lists of distinct starts (n_m = 10 > 1) distort g(r) right at
     contact, as Fig. 3 (left) shows: the first bin falls many standard errors
     below the reference;
@@ -59,12 +60,15 @@ def local_mc():
     return np.array(out)
 
 
-def pec_counts(list_mode):
+def pec_counts(list_mode, boundary=oracle.BOUNDARY_REFLECT):
+    # the rejecting rule needs short chains to mix (a third of them are
+    # rejected at ell = 0.3) and a longer melt from the lattice
+    ell, melt = (1.0, 500) if boundary == oracle.BOUNDARY_REFLECT else (0.3, 2000)
     L = W.box_side(N, ETA)
     x, y = W.square_lattice(N, L)
-    p = oracle.make_params(N, L, 1.0, 2, 2, 1.0, 10, 5, list_mode=list_mode)
-    oracle.sweeps(p, x, y, 0, 500)
-    t, out = 500, []
+    p = oracle.make_params(N, L, 1.0, 2, 2, ell, 10, 5, list_mode=list_mode, boundary=boundary)
+    oracle.sweeps(p, x, y, 0, melt)
+    t, out = melt, []
     for _ in range(NBATCH):
         c = np.zeros(NB, np.int64)
         for _ in range(PER):
@@ -80,13 +84,15 @@ def zscores(a, b):
     return (b.mean(0) - a.mean(0)) / se
 
 
-def test_with_replacement_matches_local_monte_carlo(local_mc):
-    z = zscores(local_mc, pec_counts(oracle.LIST_WITH_REPL))
+@pytest.mark.parametrize("boundary", [oracle.BOUNDARY_REFLECT, oracle.BOUNDARY_REJECT])
+def test_with_replacement_matches_local_monte_carlo(local_mc, boundary):
+    z = zscores(local_mc, pec_counts(oracle.LIST_WITH_REPL, boundary))
     assert np.mean(z**2) < 2.5 and np.max(np.abs(z)) < 4.5, z
 
 
-def test_shuffled_lists_distort_contact_values(local_mc):
-    z = zscores(local_mc, pec_counts(oracle.LIST_WITHOUT_REPL))
+@pytest.mark.parametrize("boundary", [oracle.BOUNDARY_REFLECT, oracle.BOUNDARY_REJECT])
+def test_shuffled_lists_distort_contact_values(local_mc, boundary):
+    z = zscores(local_mc, pec_counts(oracle.LIST_WITHOUT_REPL, boundary))
     assert z[0] < -6.0 and np.mean(z**2) > 10.0, z
 
 
