@@ -68,3 +68,48 @@ long long localmc_run(int N, double L, double sigma, double delta, double* x, do
   }
   return acc;
 }
+
+/* The same in three dimensions (spheres of diameter sigma in a periodic
+ * cube; displacements uniform on [-delta, delta]^3). */
+long long localmc3_run(int N, double L, double sigma, double delta, double* x, double* y,
+                       double* z, long long sweeps, uint64_t seed, double r0, double dr, int nb,
+                       long long* counts) {
+  uint64_t s = seed;
+  const double s2 = sigma * sigma;
+  long long acc = 0;
+  for (long long sw = 0; sw < sweeps; ++sw) {
+    for (int mv = 0; mv < N; ++mv) {
+      const int i = (int)(unif(&s) * N);
+      double nx = x[i] + (2.0 * unif(&s) - 1.0) * delta;
+      double ny = y[i] + (2.0 * unif(&s) - 1.0) * delta;
+      double nz = z[i] + (2.0 * unif(&s) - 1.0) * delta;
+      nx -= L * floor(nx / L);
+      ny -= L * floor(ny / L);
+      nz -= L * floor(nz / L);
+      int ok = 1;
+      for (int j = 0; j < N && ok; ++j) {
+        if (j == i) continue;
+        const double dx = wrapc(nx - x[j], L), dy = wrapc(ny - y[j], L), dz = wrapc(nz - z[j], L);
+        if (dx * dx + dy * dy + dz * dz < s2) ok = 0;
+      }
+      if (ok) {
+        x[i] = nx;
+        y[i] = ny;
+        z[i] = nz;
+        acc++;
+      }
+    }
+    if (counts) {
+      for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) {
+          if (j == i) continue;
+          const double dx = wrapc(x[j] - x[i], L), dy = wrapc(y[j] - y[i], L),
+                       dz = wrapc(z[j] - z[i], L);
+          const double d = sqrt(dx * dx + dy * dy + dz * dz);
+          const int b = (int)floor((d - r0) / dr);
+          if (b >= 0 && b < nb) counts[b]++;
+        }
+    }
+  }
+  return acc;
+}

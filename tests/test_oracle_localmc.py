@@ -11,7 +11,9 @@ paper's Fig. 3: N = 100 disks at eta = 0.55, ordered-pair counts in ten
     below the reference;
   - the same for the striped decomposition under the rejecting rule (two
     stripes of 50 disks, n_m = 40): with replacement it agrees, shuffled
-    lists are biased.
+    lists are biased;
+  - the three-dimensional sweep against local Monte Carlo of hard spheres
+    (N = 125 at eta = 0.40).
 """
 import ctypes as C
 import math
@@ -122,3 +124,55 @@ def test_stripes_with_replacement_match_local_monte_carlo(local_mc):
 def test_stripes_with_shuffled_lists_are_biased(local_mc):
     z = zscores(local_mc, stripe_counts(oracle.LIST_WITHOUT_REPL))
     assert np.mean(z**2) > 10.0, z
+
+
+# -- three dimensions ------------------------------------------------------------
+def test_spheres_match_local_monte_carlo():
+    # N = 125 spheres at eta = 0.40, 2 x 2 x 2 cells, against localmc3_run
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    n3, eta3, nbatch, per = 125, 0.40, 20, 400
+    d = tempfile.mkdtemp()
+    so = os.path.join(d, "localmc.so")
+    subprocess.run([gcc, "-O2", "-shared", "-fPIC", os.path.join(HERE, "localmc.c"), "-o", so,
+                    "-lm"], check=True)
+    lib = C.CDLL(so)
+    lib.localmc3_run.restype = C.c_longlong
+    lib.localmc3_run.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_void_p,
+                                 C.c_void_p, C.c_void_p, C.c_longlong, C.c_uint64, C.c_double,
+                                 C.c_double, C.c_int, C.c_void_p]
+    L = W.box_side3(n3, eta3)
+    x, y, z = W.cubic_lattice(n3, L)
+    lib.localmc3_run(n3, L, 1.0, 0.12, x.ctypes.data, y.ctypes.data, z.ctypes.data, 1500, 7,
+                     R0, DR, NB, None)
+    lm = []
+    for b in range(nbatch):
+        c = np.zeros(NB, np.int64)
+        lib.localmc3_run(n3, L, 1.0, 0.12, x.ctypes.data, y.ctypes.data, z.ctypes.data, per,
+                         100 + b, R0, DR, NB, c.ctypes.data)
+        lm.append(c / per)
+    shutil.rmtree(d, ignore_errors=True)
+
+    def counts3(x, y, z):
+        sep = []
+        for a in (x, y, z):
+            da = a[None, :] - a[:, None]
+            sep.append(da - L * np.floor(da / L + 0.5))
+        dd = np.sqrt(sep[0] ** 2 + sep[1] ** 2 + sep[2] ** 2)
+        np.fill_diagonal(dd, -1.0)
+        return np.histogram(dd.ravel(), bins=NB, range=(R0, R0 + NB * DR))[0]
+
+    x, y, z = W.cubic_lattice(n3, L)
+    p3 = oracle.make_params3(n3, L, 1.0, 2, 1.0, 10, 5)
+    oracle.sweeps3(p3, x, y, z, 0, 500)
+    t, pe = 500, []
+    for _ in range(nbatch):
+        c = np.zeros(NB, np.int64)
+        for _ in range(per):
+            oracle.sweeps3(p3, x, y, z, t, 1)
+            t += 1
+            c += counts3(x, y, z)
+        pe.append(c / per)
+    zz = zscores(np.array(lm), np.array(pe))
+    assert np.mean(zz**2) < 2.5 and np.max(np.abs(zz)) < 4.5, zz
