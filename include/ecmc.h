@@ -431,14 +431,26 @@ ECMC_API int ecmc_sqrt_rn(const double* x, double* out, int64_t n, int where, do
  *              Philox key; t0 the Philox counter of the first sweep
  *   stream     cudaStream_t (NULL = legacy default stream)
  * The sweeps are the same as those of a handle with the same parameters
- * (ecmc_set_positions(xy, t0), ecmc_sweep(n_sweeps)), screening in FP32.
- * The call returns after the work on `stream` has finished.  Errors:
- * ECMC_ERR_ARG (as ecmc_create, or n_m < 1, t0 < 0), ECMC_ERR_CAPACITY (the
- * system needs more scratch than the array holds; roughly N <= 64k disks at
- * eta 0.7; or the input overlaps), ECMC_ERR_CUDA.  The first call on a
- * device looks up the array's device address; make it before any stream
- * capture.  Every call shares the array: calls that overlap on the GPU race
- * and must be serialised by the caller. */
+ * (ecmc_set_positions(xy, t0), ecmc_sweep(n_sweeps)), screening in FP32: the
+ * same argument checks (except that N need not be a perfect square), the
+ * same geometry and the same overlap check of the input.  The call returns
+ * after the work on `stream` has finished.  Errors, each leaving xy as it
+ * was passed in:
+ *   ECMC_ERR_ARG         as ecmc_create (N >= 1 any size below 2^27), or
+ *                        n_m < 1, t0 < 0, n_sweeps < 0, xy NULL;
+ *   ECMC_ERR_OVERLAP     two input disks closer than sigma (1 - 1e-9)^(1/2);
+ *   ECMC_ERR_CAPACITY    the system needs more scratch than the array holds
+ *                        (roughly N <= 64k disks at eta 0.7), or a cell of
+ *                        the input holds more disks than its packing bound;
+ *   ECMC_ERR_UNSUPPORTED cell frames too large for shared memory (the handle
+ *                        would use frames in global memory instead);
+ *   ECMC_ERR_CHAIN_CAP   a chain reached the per-chain event cap;
+ *   ECMC_ERR_CUDA        a CUDA call failed.
+ * The first call on a device looks up the array's device address and caches
+ * it; make it before any stream capture, and do not call this entry point on
+ * a device after cudaDeviceReset in the same process (the cached address is
+ * then stale).  Every call shares the array: calls that overlap on the GPU
+ * race and must be serialised by the caller. */
 ECMC_API int ecmc_sweep_noalloc(double* xy, int64_t N, double L, double sigma, int cells_x,
                                 int cells_y, double ell, int n_m, uint64_t seed, uint64_t replica,
                                 int64_t t0, int64_t n_sweeps, void* stream);

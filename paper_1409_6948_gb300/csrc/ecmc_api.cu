@@ -75,7 +75,7 @@ struct ecmc_ctx {
   ChunkSums* d_partials = nullptr;
   int warps = 0;
   int warps_param = 0;
-  float strip_w = 0.5f;
+  float strip_w = (float)kDefaultStripWidth;
   size_t records_cap = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t own_stream = nullptr;
@@ -125,6 +125,10 @@ double packing_bound(double W, double H, double sigma) {
   return (W + sp) * (H + sp) / (pi * sp * sp / 4.0);
 }
 
+}  // namespace
+
+namespace ecmc {
+
 void set_screen_bounds(Geom& g) {
   // M: power of two bounding every frame coordinate, |v| < max(w,h) + sigma
   const double ext = (g.w > g.h ? g.w : g.h) + 1.01 * g.sigma;
@@ -161,6 +165,18 @@ void set_screen_bounds(Geom& g) {
   g.strip_margin = (float)(4.0 * e + 1e-5 * sig);
 }
 
+void set_strip_bins(Geom& g, double strip_w) {
+  const double bw = strip_w * g.sigma;
+  const double extB = (g.w > g.h ? g.w : g.h) + 2.0 * g.sigma;
+  g.nbin = (int)std::ceil(extB / bw) + 1;
+  g.bin_w = (float)bw;
+  g.inv_bin_w = (float)(1.0 / bw);
+}
+
+}  // namespace ecmc
+
+namespace {
+
 int upload_geometry(ecmc_ctx* h) {
   CK(cudaMemcpyAsync(h->d_geo, h->geo.data(), sizeof(Geom) * h->geo.size(),
                      cudaMemcpyHostToDevice, h->stream));
@@ -188,13 +204,7 @@ int choose_tpc(ecmc_ctx* h, int fmode) {
 }
 
 int compute_layout(ecmc_ctx* h) {
-  for (Geom& g : h->geo) {
-    const double bw = h->strip_w * g.sigma;
-    const double extB = (g.w > g.h ? g.w : g.h) + 2.0 * g.sigma;
-    g.nbin = (int)std::ceil(extB / bw) + 1;
-    g.bin_w = (float)bw;
-    g.inv_bin_w = (float)(1.0 / bw);
-  }
+  for (Geom& g : h->geo) set_strip_bins(g, h->strip_w);
   const size_t limit = 232448;  // opt-in shared memory per block on sm_103
   if (h->n_sm == 0) {
     int dev = 0;
@@ -569,12 +579,14 @@ int setup_gr(ecmc_ctx* h) {
   return ECMC_OK;
 }
 
-// Geometry, capacities and FP32 screening bounds of one replica.
-int setup_geom(const ecmc_replica_desc_t& d, Geom& g) {
+// Geometry, capacities and FP32 screening bounds of one replica.  With
+// lattice_start, N must be a perfect square whose lattice does not overlap.
+int setup_geom(const ecmc_replica_desc_t& d, Geom& g, bool lattice_start = true) {
   const int64_t N = d.N;
   if (N < 1 || N >= (int64_t(1) << 27)) return fail(ECMC_ERR_ARG, "N out of range");
   const int64_t k = (int64_t)std::llround(std::sqrt((double)N));
-  if (k * k != N) return fail(ECMC_ERR_ARG, "N must be a perfect square (lattice start)");
+  if (lattice_start && k * k != N)
+    return fail(ECMC_ERR_ARG, "N must be a perfect square (lattice start)");
   if (!(d.L > 0.0) || !(d.sigma > 0.0) || !std::isfinite(d.L) || !std::isfinite(d.sigma))
     return fail(ECMC_ERR_ARG, "L and sigma must be positive");
   // sigma^2 - c^2 and every frame coordinate stay normal numbers in FP64 and FP32
@@ -585,7 +597,8 @@ int setup_geom(const ecmc_replica_desc_t& d, Geom& g) {
     return fail(ECMC_ERR_ARG, "cells per side must be even and >= 2");
   if (!(d.L / d.cells_x > d.sigma) || !(d.L / d.cells_y > d.sigma))
     return fail(ECMC_ERR_ARG, "cell side must exceed sigma");
-  if (!(d.L / (double)k > d.sigma)) return fail(ECMC_ERR_ARG, "square lattice would overlap");
+  if (lattice_start && !(d.L / (double)k > d.sigma))
+    return fail(ECMC_ERR_ARG, "square lattice would overlap");
   if (!(d.ell >= 0.0) || !std::isfinite(d.ell)) return fail(ECMC_ERR_ARG, "ell must be >= 0");
   if ((int64_t)d.cells_x * d.cells_y > (int64_t(1) << 26))
     return fail(ECMC_ERR_ARG, "too many cells");
@@ -618,6 +631,16 @@ int setup_geom(const ecmc_replica_desc_t& d, Geom& g) {
   set_screen_bounds(g);
   return ECMC_OK;
 }
+
+}  // namespace
+
+namespace ecmc {
+int setup_replica_geom(const ecmc_replica_desc_t& d, Geom& g, int lattice_start) {
+  return setup_geom(d, g, lattice_start != 0);
+}
+}  // namespace ecmc
+
+namespace {
 
 int create_impl(ecmc_t* out, const ecmc_replica_desc_t* desc, int R) {
   if (!out) return fail(ECMC_ERR_ARG, "out is NULL");

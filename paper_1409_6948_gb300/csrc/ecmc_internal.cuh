@@ -20,6 +20,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "ecmc.h"
+
 namespace ecmc {
 
 // ---- error word (device) ------------------------------------------------
@@ -32,6 +34,8 @@ enum DevErr : int {
 };
 
 constexpr int64_t kMaxEventsPerChain = int64_t(1) << 22;
+// Default width of the candidate strips across the chain axis, in sigma.
+constexpr double kDefaultStripWidth = 0.5;
 constexpr uint64_t kPurposeSweep = 0, kPurposeChain = 1, kPurposeShuffle = 2;
 
 // ---- per-sweep device state ------------------------------------------------
@@ -248,6 +252,16 @@ inline void set_bin_screen(Geom& g) {
   g.bin_eq_y = (float)(2.0 * (std::ldexp(1.0, -21) * (g.L + g.h) * g.inv_h * 1.01 +
                               std::ldexp(1.0, -23) * g.cells_y));
 }
+
+// Shared by the handle path and the allocation-free entry point
+// (ecmc_api.cu): argument checks, geometry, bucket and frame capacities and
+// n_m of one replica (returns ECMC_OK or ECMC_ERR_ARG with the message set;
+// lattice_start = 1 also requires N to be a perfect square whose square
+// lattice does not overlap); the FP32 screening bounds of the chain kernel;
+// the strips across the chain axis, strip_w in units of sigma.
+int setup_replica_geom(const ecmc_replica_desc_t& d, Geom& g, int lattice_start);
+void set_screen_bounds(Geom& g);
+void set_strip_bins(Geom& g, double strip_w);
 
 inline int chain_kind(const DevBufs& b) { return b.iso ? 1 : (b.reject ? 2 : 0); }
 int configure_fused(const RecLayout& lay, int tpc, int fm, int kind, int* blocks_per_sm);

@@ -14,8 +14,14 @@
 // The array is shared by every call: calls that overlap on the GPU (on
 // different streams, or from different host threads) race on it and must be
 // serialised by the caller.  What must start at zero (bucket counts,
-// running totals, the error word) is cleared by every call; the rest is
-// written before it is read.
+// running totals, the error word, the overlap check's minimum) is set by
+// every call; the rest is written before it is read.
+//
+// Argument checks, geometry, capacities and the FP32 screening bounds come
+// from the same functions the handle path uses (ecmc_api.cu), and the input
+// passes the same overlap check as ecmc_set_positions.  On any error the
+// caller's positions are left as they were passed in: device errors are read
+// before the positions are written back.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -35,7 +41,10 @@ unsigned char* g_noalloc_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device.  In host code
 // the name g_noalloc_scratch is only a host-side stand-in, so the address is
-// looked up once per device (with that device current) and cached.
+// looked up once per device (with that device current) and cached.  The
+// cache is not invalidated: after cudaDeviceReset the cached address is
+// stale, so a process that resets a device must not call this entry point
+// on it again.
 int scratch_address(unsigned char** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ECMC_ERR_CUDA;
@@ -56,68 +65,33 @@ size_t carve(size_t& off, size_t bytes) {
   return at;
 }
 
-double packing(double W, double H, double sigma) {
-  const double sp = sigma * (1.0 - 1e-6);
-  return (W + sp) * (H + sp) / (3.14159265358979323846 * sp * sp / 4.0);
-}
-
 }  // namespace
 
 extern "C" int ecmc_sweep_noalloc(double* xy, int64_t N, double L, double sigma, int cells_x,
                                   int cells_y, double ell, int n_m, uint64_t seed,
                                   uint64_t replica, int64_t t0, int64_t n_sweeps, void* stream) {
-  if (!xy || N < 1 || N >= (int64_t(1) << 27) || !(L > 0.0) || !(sigma > 0.0) ||
-      !std::isfinite(L) || cells_x < 2 || cells_y < 2 || (cells_x & 1) || (cells_y & 1) ||
-      !(L / cells_x > sigma) || !(L / cells_y > sigma) || !(ell >= 0.0) || !std::isfinite(ell) ||
-      n_m < 1 || t0 < 0 || n_sweeps < 0 || !(sigma >= std::ldexp(1.0, -40)) ||
-      !(sigma <= std::ldexp(1.0, 40)) || !(L < std::ldexp(sigma, 40)))
-    return ECMC_ERR_ARG;
+  if (!xy) return report_error(ECMC_ERR_ARG, "xy is NULL");
+  if (n_m < 1 || t0 < 0 || n_sweeps < 0)
+    return report_error(ECMC_ERR_ARG, "n_m must be >= 1, t0 and n_sweeps >= 0");
 
-  // geometry and capacities, as for a handle
+  // geometry, capacities and screening bounds exactly as for a handle (any
+  // N: the caller supplies the positions, no lattice start)
+  ecmc_replica_desc_t d;
+  std::memset(&d, 0, sizeof(d));
+  d.N = N;
+  d.L = L;
+  d.sigma = sigma;
+  d.cells_x = cells_x;
+  d.cells_y = cells_y;
+  d.ell = ell;
+  d.n_m = n_m;
+  d.seed = seed;
+  d.replica = replica;
   Geom g;
-  std::memset(&g, 0, sizeof(g));
-  g.N = N;
-  g.L = L;
-  g.sigma = sigma;
-  g.sig2 = sigma * sigma;
-  g.cells_x = cells_x;
-  g.cells_y = cells_y;
-  g.ncell = cells_x * cells_y;
-  g.w = L / (double)cells_x;
-  g.h = L / (double)cells_y;
-  g.inv_w = 1.0 / g.w;
-  g.inv_h = 1.0 / g.h;
-  set_bin_screen(g);
-  g.ell = ell;
-  g.n_m = n_m;
-  g.seed = seed;
-  g.replica = replica;
-  g.dir_mode = 0;
-  g.precision = 1;
-  g.nact = (cells_x / 2) * (cells_y / 2);
-  g.cap_mem = (int)std::floor(packing(g.w, g.h, sigma)) + 2;
-  g.cap_obj = (int)std::floor(packing(g.w + 2 * sigma, g.h + 2 * sigma, sigma)) + 2;
-  if (g.cap_mem > g.cap_obj) g.cap_mem = g.cap_obj;
-  if ((int64_t)g.ncell * g.cap_mem < N) return ECMC_ERR_ARG;
-  {
-    const double ext = (g.w > g.h ? g.w : g.h) + 1.01 * sigma;
-    double M = 1.0;
-    while (M < ext) M *= 2.0;
-    const double e = 6.5 * std::ldexp(1.0, -24) * M;
-    const double ex = (2.0 * sigma + 2.0 * e) * e + 3.0 * std::ldexp(1.0, -24) * sigma * sigma;
-    g.eps_d = (float)(e * 1.0000001);
-    g.s_margin = (float)(1.25 * (e + std::sqrt(ex) + std::ldexp(1.0, -20) * sigma +
-                                 std::ldexp(1.0, -23) * (2.0 * M + sigma)));
-    g.sig_plus = std::nextafter((float)(sigma + e + std::ldexp(sigma, -40)), 1e30f);
-    g.sig_minus = std::nextafter((float)(sigma - e - std::ldexp(sigma, -40)), -1e30f);
-    g.sig2f = (float)(sigma * sigma);
-    g.sigf = (float)sigma;
-    g.strip_margin = (float)(4.0 * e + 1e-5 * sigma);
-    const double bw = 0.5 * sigma;
-    g.nbin = (int)std::ceil(((g.w > g.h ? g.w : g.h) + 2.0 * sigma) / bw) + 1;
-    g.bin_w = (float)bw;
-    g.inv_bin_w = (float)(1.0 / bw);
-  }
+  const int grc = setup_replica_geom(d, g, 0);
+  if (grc != ECMC_OK) return grc;
+  set_strip_bins(g, kDefaultStripWidth);
+
   int tpc = 32;
   for (int t = 4; t <= 32; t *= 2) {
     if (phase_smem_bytes(make_layout(32 / t, g.nbin, g.cap_mem, g.cap_obj), 1, 0) <= 52 * 1024) {
@@ -126,12 +100,14 @@ extern "C" int ecmc_sweep_noalloc(double* xy, int64_t N, double L, double sigma,
     }
   }
   const RecLayout lay = make_layout(32 / tpc, g.nbin, g.cap_mem, g.cap_obj);
+  // the handle would fall back to frames in global memory here, which needs
+  // scratch beyond what this entry point carves
   if (phase_smem_bytes(lay, 1, 0) > 232448 || frame_build_smem(lay) > 232448)
-    return ECMC_ERR_UNSUPPORTED;
+    return report_error(ECMC_ERR_UNSUPPORTED, "cell frames too large for shared memory");
 
   // carve the scratch array
   const size_t slots = (size_t)g.ncell * g.cap_mem;
-  const int n_active = (cells_x / 2) * (cells_y / 2);
+  const int n_active = g.nact;
   const int n_groups = (n_active + lay.cpw - 1) / lay.cpw;
   size_t off = 0;
   size_t o_px[2], o_py[2], o_pid[2], o_cnt[2];
@@ -145,6 +121,7 @@ extern "C" int ecmc_sweep_noalloc(double* xy, int64_t N, double L, double sigma,
   const size_t o_stats = carve(off, sizeof(CellStats) * (size_t)g.ncell);
   const size_t o_tot = carve(off, sizeof(RunTotals));
   const size_t o_err = carve(off, sizeof(int));
+  const size_t o_min = carve(off, sizeof(unsigned long long));
   const size_t o_rec = carve(off, (size_t)n_groups * lay.bytes);
   const size_t o_geo = carve(off, sizeof(Geom));
   const size_t o_crep = carve(off, sizeof(int) * (size_t)g.ncell);
@@ -155,10 +132,12 @@ extern "C" int ecmc_sweep_noalloc(double* xy, int64_t N, double L, double sigma,
   const size_t o_choff = carve(off, sizeof(int) * 2);
   const size_t o_part = carve(off, sizeof(ChunkSums) * (size_t)n_chunks);
   // larger systems than the static array can serve are rejected up front
-  if (off > (size_t)ECMC_NOALLOC_SCRATCH_BYTES) return ECMC_ERR_CAPACITY;
+  if (off > (size_t)ECMC_NOALLOC_SCRATCH_BYTES)
+    return report_error(ECMC_ERR_CAPACITY, "system needs more scratch than the static array");
 
   unsigned char* base = nullptr;
-  if (scratch_address(&base) != ECMC_OK) return ECMC_ERR_CUDA;
+  if (scratch_address(&base) != ECMC_OK)
+    return report_error(ECMC_ERR_CUDA, "device address of the scratch array not available");
   DevBufs b;
   std::memset(&b, 0, sizeof(b));
   b.replay = 1;
@@ -172,6 +151,7 @@ extern "C" int ecmc_sweep_noalloc(double* xy, int64_t N, double L, double sigma,
   b.cell_stats = reinterpret_cast<CellStats*>(base + o_stats);
   b.totals = reinterpret_cast<RunTotals*>(base + o_tot);
   b.err = reinterpret_cast<int*>(base + o_err);
+  unsigned long long* d_min = reinterpret_cast<unsigned long long*>(base + o_min);
   b.records = base + o_rec;
   b.history = nullptr;
   b.history_cap = 0;
@@ -194,9 +174,14 @@ extern "C" int ecmc_sweep_noalloc(double* xy, int64_t N, double L, double sigma,
   b.fmode = 0;
   const int64_t n_off_host[2] = {0, N};
   const int chunk_off_host[2] = {0, n_chunks};
+  // the overlap check's running minimum starts at (2 sigma)^2, the cut-off
+  const double r2 = 4.0 * g.sig2;
+  unsigned long long r2_bits = 0;
+  std::memcpy(&r2_bits, &r2, sizeof(r2));
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (configure_frame_build(lay) || configure_phase(lay, tpc, 1, 0)) return ECMC_ERR_CUDA;
+  if (configure_frame_build(lay) || configure_phase(lay, tpc, 1, 0))
+    return report_error(ECMC_ERR_CUDA, "kernel configuration failed");
 
   // clear what must start at zero, set the sweep counter
   SweepState st;
@@ -212,21 +197,43 @@ extern "C" int ecmc_sweep_noalloc(double* xy, int64_t N, double L, double sigma,
       cudaMemcpyAsync((void*)b.n_off, n_off_host, sizeof(n_off_host), cudaMemcpyHostToDevice,
                       s) != cudaSuccess ||
       cudaMemcpyAsync(b.state, &st, sizeof(st), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(d_min, &r2_bits, sizeof(r2_bits), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
       cudaMemcpyAsync((void*)b.chunk_off, chunk_off_host, sizeof(chunk_off_host),
                       cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return ECMC_ERR_CUDA;
+    return report_error(ECMC_ERR_CUDA, "scratch initialisation failed");
   for (int k = 0; k < n_chunks; ++k) {
     const int2 ch = make_int2(k * 2048, (k + 1) * 2048 < g.ncell ? (k + 1) * 2048 : g.ncell);
     if (cudaMemcpyAsync((void*)(b.chunks + k), &ch, sizeof(ch), cudaMemcpyHostToDevice, s) !=
         cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
-      return ECMC_ERR_CUDA;
+      return report_error(ECMC_ERR_CUDA, "scratch initialisation failed");
   }
-  if (cudaStreamSynchronize(s) != cudaSuccess) return ECMC_ERR_CUDA;
 
-  // caller positions -> buckets, n sweeps, buckets -> caller positions
+  // caller positions -> buckets; then the overlap check of ecmc_set_positions
+  // (its fixed-point copy lives in the second bucket buffer, free until the
+  // first sweep)
   launch_load_flat(b, xy, s);
   launch_sweep_begin(b, s);
   launch_bin(b, -1, b.cur, s);
+  launch_min_dist(g, b, 2.0 * g.sigma, d_min, s);
+  int err = 0;
+  unsigned long long min_bits = 0;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(&err, b.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&min_bits, d_min, sizeof(min_bits), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return report_error(ECMC_ERR_CUDA, "loading the positions failed");
+  if (err == DEV_CAPACITY)
+    return report_error(ECMC_ERR_CAPACITY, "a cell bucket exceeded its packing bound (overlap)");
+  if (err != DEV_OK) return report_error(ECMC_ERR_CUDA, "device error while loading positions");
+  double d2 = 0.0;
+  std::memcpy(&d2, &min_bits, sizeof(d2));
+  if (d2 < g.sig2 * (1.0 - 1e-9))
+    return report_error(ECMC_ERR_OVERLAP, "positions overlap: smallest distance below sigma");
+
+  // n sweeps, then the device error word; the positions go back to the
+  // caller only if no sweep raised an error
   for (int64_t i = 0; i < n_sweeps; ++i) {
     const int src = b.cur, dst = 1 - b.cur;
     launch_sweep_begin(b, s);
@@ -234,17 +241,22 @@ extern "C" int ecmc_sweep_noalloc(double* xy, int64_t N, double L, double sigma,
     b.cur = dst;
     for (int ci = 0; ci < 4; ++ci) {
       launch_frame_build(b, lay, ci, s);
-      if (launch_phase(b, lay, ci, tpc, 1, 0, 1, s)) return ECMC_ERR_CUDA;
+      if (launch_phase(b, lay, ci, tpc, 1, 0, 1, s))
+        return report_error(ECMC_ERR_CUDA, "chain kernel launch failed");
     }
     launch_sweep_end(b, s);
   }
-  launch_gather(b, xy, s);
-  if (cudaGetLastError() != cudaSuccess) return ECMC_ERR_CUDA;
-  int err = 0;
-  if (cudaMemcpyAsync(&err, b.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(&err, b.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
-    return ECMC_ERR_CUDA;
-  if (err == DEV_CAPACITY) return ECMC_ERR_CAPACITY;
-  if (err == DEV_CHAIN_CAP) return ECMC_ERR_CHAIN_CAP;
+    return report_error(ECMC_ERR_CUDA, "sweep failed");
+  if (err == DEV_CAPACITY)
+    return report_error(ECMC_ERR_CAPACITY, "a cell bucket or frame exceeded its packing bound");
+  if (err == DEV_CHAIN_CAP)
+    return report_error(ECMC_ERR_CHAIN_CAP, "a chain reached the per-chain event cap");
+  if (err != DEV_OK) return report_error(ECMC_ERR_CUDA, "device error during the sweeps");
+  launch_gather(b, xy, s);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+    return report_error(ECMC_ERR_CUDA, "writing the positions back failed");
   return ECMC_OK;
 }

@@ -643,8 +643,19 @@ def version():
 def sweep_noalloc(xy, N, L, sigma, cells_x, cells_y, ell, n_m, seed, replica, t0, n_sweeps,
                   stream=None):
     """ecmc_sweep_noalloc: sweeps of caller-held device positions `xy` (a
-    torch CUDA float64 tensor of 2N values, overwritten) using only the
-    library's static scratch array; no device allocation."""
+    contiguous torch CUDA float64 tensor of at least 2N values on the current
+    device, overwritten) using only the library's static scratch array; no
+    device allocation."""
+    import torch
+    if not isinstance(xy, torch.Tensor) or not xy.is_cuda:
+        raise ValueError("xy must be a CUDA tensor")
+    if xy.dtype != torch.float64 or not xy.is_contiguous():
+        raise ValueError("xy must be a contiguous float64 tensor")
+    if xy.numel() < 2 * int(N):
+        raise ValueError("xy holds %d values, 2N = %d needed" % (xy.numel(), 2 * int(N)))
+    if xy.device.index != torch.cuda.current_device():
+        raise ValueError("xy lives on cuda:%d, the current device is cuda:%d"
+                         % (xy.device.index, torch.cuda.current_device()))
     if stream is not None and hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
     _check(load().ecmc_sweep_noalloc(C.c_void_p(xy.data_ptr()), int(N), float(L), float(sigma),

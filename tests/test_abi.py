@@ -114,6 +114,29 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.ecmc_stripes_set_param(None, 1, 1.0) == E.ERR_ARG
 
 
+def test_noalloc_rejects_invalid_arguments_before_device_work():
+    # the allocation-free sweep shares the handle path's argument checks; each
+    # of these returns before any CUDA call, so the pointer is never used
+    lib = P.load()
+    fake = C.c_void_p(256)
+    L = 131600.0
+    cases = [
+        # cells_x * cells_y above 2^26 (the int cell count would overflow)
+        (1000, L, 1.0, 131584, 130562, 8.0, 1, 0, 1),
+        (256, 16.9, 1.0, 3, 2, 4.0, 1, 0, 1),      # odd cells
+        (256, 16.9, 1.0, 2, 2, 4.0, 0, 0, 1),      # n_m < 1
+        (256, 16.9, 1.0, 2, 2, 4.0, 1, -1, 1),     # t0 < 0
+        (256, 16.9, 1.0, 2, 2, 4.0, 1, 0, -1),     # n_sweeps < 0
+        (256, 16.9, 1.0, 18, 18, 4.0, 1, 0, 1),    # cell side below sigma
+        (0, 16.9, 1.0, 2, 2, 4.0, 1, 0, 1),        # N < 1
+    ]
+    for (N, Lb, sig, cx, cy, ell, nm, t0, ns) in cases:
+        rc = lib.ecmc_sweep_noalloc(fake, N, Lb, sig, cx, cy, ell, nm, 1, 0, t0, ns, None)
+        assert rc == E.ERR_ARG, (N, cx, cy, nm, t0, ns, rc)
+    assert lib.ecmc_sweep_noalloc(None, 256, 16.9, 1.0, 2, 2, 4.0, 1, 1, 0, 0, 1,
+                                  None) == E.ERR_ARG
+
+
 @pytest.mark.parametrize("N,eta", [(1048576, 0.72), (262144, 0.70), (4096, 0.60), (65536, 0.708),
                                    (4194304, 0.716)])
 def test_suggested_parameters_follow_the_papers_strategy(N, eta):
