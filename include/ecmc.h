@@ -351,6 +351,17 @@ ECMC_API int ecmc_gr(ecmc_t h, double* g_out, double* r_out, int nbins);
 /* Number of histogram bins for the current GR_DR / GR_RMAX. */
 ECMC_API int ecmc_gr_nbins(ecmc_t h, int* nbins);
 
+/* The same three for replica r of a batch (ecmc_gr_measure, ecmc_gr_counts
+ * and ecmc_gr are these with r = 0).  Every replica has its own histogram of
+ * ecmc_gr_nbins bins [sigma_r + i dr, sigma_r + (i+1) dr) and its own
+ * measurement count; ecmc_replica_gr_measure with r = -1 adds the current
+ * configuration of every replica to its histogram (one launch per replica,
+ * enqueued on the stream).  ECMC_ERR_ARG if r is out of range. */
+ECMC_API int ecmc_replica_gr_measure(ecmc_t h, int r);
+ECMC_API int ecmc_replica_gr_counts(ecmc_t h, int r, int64_t* counts, int nbins,
+                                    int64_t* n_meas);
+ECMC_API int ecmc_replica_gr(ecmc_t h, int r, double* g_out, double* r_out, int nbins);
+
 /* Smallest minimum-image pair distance of the current configuration among
  * pairs closer than 2 sigma (2 sigma if none), over all replicas. */
 ECMC_API int ecmc_min_distance(ecmc_t h, double* dmin);

@@ -82,6 +82,9 @@ def lib():
         L.orc_gr_counts.argtypes = [i64, C.c_double, d, d, C.c_double, C.c_double, C.c_int,
                                     i64, i64, C.POINTER(C.c_int64)]
         L.orc_gr_counts.restype = None
+        L.orc_gr_counts_cells.argtypes = [i64, C.c_double, d, d, C.c_double, C.c_double,
+                                          C.c_int, C.POINTER(C.c_int64)]
+        L.orc_gr_counts_cells.restype = None
         L.orc_min_dist2.argtypes = [i64, C.c_double, d, d, C.c_double]
         L.orc_min_dist2.restype = C.c_double
         L.orc_run_chain_frame.argtypes = [C.c_int, C.c_int, d, d, C.POINTER(C.c_int64),
@@ -211,6 +214,17 @@ def gr_counts(L, x, y, sigma, dr, nbins, i_begin=0, i_end=None, counts=None):
     lib().orc_gr_counts(int(N), float(L), _dptr(x), _dptr(y), float(sigma), float(dr),
                         int(nbins), int(i_begin), int(i_end),
                         counts.ctypes.data_as(C.POINTER(C.c_int64)))
+    return counts
+
+
+def gr_counts_cells(L, x, y, sigma, dr, nbins, counts=None):
+    """gr_counts over all disks, pairs found through a cell list (same
+    counts; for large N)."""
+    N = x.shape[0]
+    if counts is None:
+        counts = np.zeros(nbins, np.int64)
+    lib().orc_gr_counts_cells(int(N), float(L), _dptr(x), _dptr(y), float(sigma), float(dr),
+                              int(nbins), counts.ctypes.data_as(C.POINTER(C.c_int64)))
     return counts
 
 

@@ -738,6 +738,59 @@ void orc_gr_counts(int64_t N, double L, const double* x, const double* y, double
   }
 }
 
+/* The same histogram with the pairs found through a cell list: the box is
+ * cut into nc x nc square cells of side at least r_max (1 + 1e-6), r_max =
+ * sigma + nbins dr, so that a pair within r_max (minimum image) lies in the
+ * same or in adjacent cells; with nc >= 3 the nine cells around a disk are
+ * distinct and no pair is seen twice.  Every pair is then tested with exactly
+ * the expressions of orc_gr_counts, so the counts are identical; with nc < 3
+ * this is orc_gr_counts.  Needs positions in [0, L). */
+void orc_gr_counts_cells(int64_t N, double L, const double* x, const double* y, double sigma,
+                         double dr, int nbins, int64_t* counts) {
+  const double rmax = sigma + dr * (double)nbins;
+  const int64_t nc = (int64_t)floor(L / (rmax * (1.0 + 1e-6)));
+  if (nc < 3 || N < 2) {
+    orc_gr_counts(N, L, x, y, sigma, dr, nbins, 0, N, counts);
+    return;
+  }
+  const double cs = L / (double)nc;
+  int64_t* head = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nc * nc));
+  int64_t* next = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
+  int64_t* cell = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
+  for (int64_t c = 0; c < nc * nc; ++c) head[c] = -1;
+  for (int64_t i = 0; i < N; ++i) {
+    int64_t cx = (int64_t)(x[i] / cs), cy = (int64_t)(y[i] / cs);
+    if (cx < 0) cx = 0;
+    if (cx > nc - 1) cx = nc - 1;
+    if (cy < 0) cy = 0;
+    if (cy > nc - 1) cy = nc - 1;
+    cell[i] = cy * nc + cx;
+    next[i] = head[cell[i]];
+    head[cell[i]] = i;
+  }
+  for (int64_t i = 0; i < N; ++i) {
+    const int64_t cx = cell[i] % nc, cy = cell[i] / nc;
+    for (int64_t oy = -1; oy <= 1; ++oy) {
+      for (int64_t ox = -1; ox <= 1; ++ox) {
+        const int64_t c = ((cy + oy + nc) % nc) * nc + (cx + ox + nc) % nc;
+        for (int64_t j = head[c]; j >= 0; j = next[j]) {
+          if (j == i) continue;
+          double ddx = wrap_centered(x[j] - x[i], L);
+          double ddy = wrap_centered(y[j] - y[i], L);
+          double d = sqrt(ddx * ddx + ddy * ddy);
+          double q = (d - sigma) / dr;
+          if (!(q >= 0.0)) continue;
+          if (!(q < (double)nbins)) continue;
+          counts[(int)q]++;
+        }
+      }
+    }
+  }
+  free(head);
+  free(next);
+  free(cell);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Hexatic order parameter (Sec. 2, eq. Psi)                                 */
 /* ------------------------------------------------------------------------ */

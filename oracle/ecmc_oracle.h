@@ -131,6 +131,13 @@ int orc_seq_sweeps(int64_t N, double L, double sigma, double ell, int64_t n_chai
 void orc_gr_counts(int64_t N, double L, const double* x, const double* y, double sigma,
                    double dr, int nbins, int64_t i_begin, int64_t i_end, int64_t* counts);
 
+/* The same counts over all disks, with the pairs found through a cell list
+ * of cells no smaller than sigma + nbins dr (each pair tested with the
+ * expressions of orc_gr_counts, so the counts are identical); positions in
+ * [0, L).  counts[] is accumulated. */
+void orc_gr_counts_cells(int64_t N, double L, const double* x, const double* y, double sigma,
+                         double dr, int nbins, int64_t* counts);
+
 /* Hexatic order parameter (Sec. 2, eq. Psi) with Delaunay next neighbours,
  * decided by clipping bisectors with the disks within rs (exact when every
  * Voronoi vertex lies within rs/2; the number of disks failing that check is

@@ -95,11 +95,12 @@ struct ecmc_ctx {
   std::vector<cudaEvent_t> pool;
   double ms[4] = {0, 0, 0, 0};
   int64_t launches[4] = {0, 0, 0, 0};
-  // g(r) of replica 0
+  // g(r): one histogram of gr_nbins bins per replica ([R][gr_nbins]) and
+  // the number of measurements of each replica
   double gr_dr = 0.01, gr_rmax = 5.0;
   int gr_nbins = 0;
   unsigned long long* gr_counts = nullptr;
-  int64_t gr_meas = 0;
+  std::vector<int64_t> gr_meas;
   // scratch
   double* xy_tmp = nullptr;
   int* int_tmp = nullptr;
@@ -573,9 +574,10 @@ int setup_gr(ecmc_ctx* h) {
   if (h->gr_counts) cudaFree(h->gr_counts);
   h->gr_counts = nullptr;
   h->gr_nbins = nb;
-  CK(cudaMalloc(&h->gr_counts, sizeof(unsigned long long) * nb));
-  CK(cudaMemsetAsync(h->gr_counts, 0, sizeof(unsigned long long) * nb, h->stream));
-  h->gr_meas = 0;
+  const size_t total = (size_t)nb * h->geo.size();
+  CK(cudaMalloc(&h->gr_counts, sizeof(unsigned long long) * total));
+  CK(cudaMemsetAsync(h->gr_counts, 0, sizeof(unsigned long long) * total, h->stream));
+  h->gr_meas.assign(h->geo.size(), 0);
   return ECMC_OK;
 }
 
@@ -1220,8 +1222,9 @@ int ecmc_reset_stats(ecmc_t h) {
     CK(cudaMemcpyAsync((char*)(h->b.state + r) + offsetof(SweepState, history_len), &zero,
                        sizeof(zero), cudaMemcpyHostToDevice, h->stream));
   h->hist_len_host = 0;
-  CK(cudaMemsetAsync(h->gr_counts, 0, sizeof(unsigned long long) * h->gr_nbins, h->stream));
-  h->gr_meas = 0;
+  CK(cudaMemsetAsync(h->gr_counts, 0, sizeof(unsigned long long) * h->gr_nbins * h->geo.size(),
+                     h->stream));
+  h->gr_meas.assign(h->geo.size(), 0);
   CK(cudaStreamSynchronize(h->stream));
   if (h->timing) harvest_timing(h);
   for (int c = 0; c < 4; ++c) {
@@ -1242,11 +1245,19 @@ int ecmc_replica_pressure(ecmc_t h, int r, double* betaP, double* se) {
   return pressure_of(h, r, betaP, se);
 }
 
-int ecmc_gr_measure(ecmc_t h) {
+int ecmc_gr_measure(ecmc_t h) { return ecmc_replica_gr_measure(h, 0); }
+
+int ecmc_replica_gr_measure(ecmc_t h, int r) {
   if (!h) return fail(ECMC_ERR_ARG, "NULL handle");
-  launch_gr(h->geo[0], h->b, h->gr_dr, h->gr_nbins, h->gr_counts, h->stream);
+  const int R = (int)h->geo.size();
+  if (r < -1 || r >= R) return fail(ECMC_ERR_ARG, "replica %d out of range", r);
+  const int r0 = r < 0 ? 0 : r, r1 = r < 0 ? R : r + 1;
+  for (int q = r0; q < r1; ++q) {
+    launch_gr(h->geo[q], h->b, h->gr_dr, h->gr_nbins, h->gr_counts + (size_t)q * h->gr_nbins,
+              h->stream);
+    h->gr_meas[q] += 1;
+  }
   CK(cudaGetLastError());
-  h->gr_meas += 1;
   return ECMC_OK;
 }
 
@@ -1301,24 +1312,33 @@ int ecmc_gr_nbins(ecmc_t h, int* nbins) {
 }
 
 int ecmc_gr_counts(ecmc_t h, int64_t* counts, int nbins, int64_t* n_meas) {
+  return ecmc_replica_gr_counts(h, 0, counts, nbins, n_meas);
+}
+
+int ecmc_replica_gr_counts(ecmc_t h, int r, int64_t* counts, int nbins, int64_t* n_meas) {
   if (!h || !counts) return fail(ECMC_ERR_ARG, "NULL argument");
+  if (r < 0 || r >= (int)h->geo.size()) return fail(ECMC_ERR_ARG, "replica %d out of range", r);
   if (nbins != h->gr_nbins) return fail(ECMC_ERR_ARG, "nbins must be %d", h->gr_nbins);
-  CK(cudaMemcpyAsync(counts, h->gr_counts, sizeof(int64_t) * nbins, cudaMemcpyDeviceToHost,
-                     h->stream));
+  CK(cudaMemcpyAsync(counts, h->gr_counts + (size_t)r * h->gr_nbins, sizeof(int64_t) * nbins,
+                     cudaMemcpyDeviceToHost, h->stream));
   int rc = check_device_error(h);
   if (rc) return rc;
-  if (n_meas) *n_meas = h->gr_meas;
+  if (n_meas) *n_meas = h->gr_meas[r];
   return ECMC_OK;
 }
 
 int ecmc_gr(ecmc_t h, double* g_out, double* r_out, int nbins) {
+  return ecmc_replica_gr(h, 0, g_out, r_out, nbins);
+}
+
+int ecmc_replica_gr(ecmc_t h, int r, double* g_out, double* r_out, int nbins) {
   if (!h || !g_out) return fail(ECMC_ERR_ARG, "NULL argument");
   std::vector<int64_t> c(nbins > 0 ? nbins : 1);
   int64_t nm = 0;
-  int rc = ecmc_gr_counts(h, c.data(), nbins, &nm);
+  int rc = ecmc_replica_gr_counts(h, r, c.data(), nbins, &nm);
   if (rc) return rc;
   if (nm < 1) return fail(ECMC_ERR_STATE, "no g(r) measurement yet");
-  const Geom& g = h->geo[0];
+  const Geom& g = h->geo[r];
   const double pi = 3.14159265358979323846;
   const double N = (double)g.N, rho = N / (g.L * g.L), dr = h->gr_dr;
   for (int i = 0; i < nbins; ++i) {

@@ -281,6 +281,100 @@ __global__ void __launch_bounds__(256) k_min_dist_fixed(
   if (lane == 0 && best < r2_bits) atomicMin(out, best);
 }
 
+// ---- pair-correlation histogram on fixed-point positions ------------------
+// The counts are the integers of the FP64 scan (k_pairs<true>), found with
+// integer and FP32 work for nearly every pair.  Every pair is screened on its
+// exact fixed-point squared distance D = dX^2 + dY^2 (the fractions of
+// k_fixed_point); a pair within reach of the bins is binned by an FP32
+// estimate q32 of q = (d - sigma) / dr when [q32 - qm, q32 + qm] lies inside
+// one bin, and otherwise by the FP64 expression of the FP64 scan.  With u =
+// L / 2^32 the fixed-point unit:
+//   - |sqrt(D) - d64 / u| <= 1.5: dX and dY are each within 1 + 2^-16 of the
+//     exact scaled difference (pairs within L / 4), and the FP64 formula is
+//     within 2^-18 u of the exact distance at these sizes;
+//   - q32 = fl(fl(sqrtf(fl(D))) * a) - b) with a = fl(u / dr), b = fl(sigma /
+//     dr) is within 3.7 2^-24 t + 2^-24 (sigma / dr + |q| + 1) of sqrt(D) u /
+//     dr - sigma / dr, t = d / dr;
+// qm (host) is twice the sum of these bounds at d = rcut plus the FP32
+// spacing at nbins, so the rounding of q32 -/+ qm is covered as well.
+// D outside [dmin, dmax] puts d certainly below sigma or beyond rcut.
+// One warp per cell, lane l takes members l, l + 32, ...; each unordered pair
+// is visited once (own cell kk > k, then the half stencil, valid when 2R + 1
+// <= cells in both directions) and adds 2: the FP64 distance is symmetric, as
+// x_i - x_j rounds to -(x_j - x_i).  Per-warp 32-bit histograms in shared
+// memory are summed into the 64-bit counts at the end.
+struct GrFixed {
+  unsigned long long dmin, dmax;
+  float a, b, qm, nb_f;
+  double dr;
+  int nbins;
+};
+
+__global__ void __launch_bounds__(128) k_gr_fixed(
+    Geom g, int cap, const double* __restrict__ px, const double* __restrict__ py,
+    const uint2* __restrict__ fxy, const int* __restrict__ cnt, int Rx, int Ry, GrFixed p,
+    unsigned long long* __restrict__ out) {
+  extern __shared__ unsigned int whist[];  // [warps][nbins]
+  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int t = threadIdx.x; t < nw * p.nbins; t += blockDim.x) whist[t] = 0u;
+  __syncthreads();
+  unsigned int* hist = whist + warp * p.nbins;
+  const int lcell = blockIdx.x * nw + warp;
+  if (lcell < g.ncell) {  // warp-uniform
+    const int c = g.cell_off + lcell;
+    const int cx = lcell % g.cells_x, cy = lcell / g.cells_x;
+    const int nmem = min(cnt[c], cap);
+    for (int m0 = 0; m0 < nmem; m0 += 32) {
+      const int k = m0 + lane;
+      const bool act = k < nmem;
+      const int i = c * cap + (act ? k : 0);
+      const uint2 pi = fxy[i];
+      auto visit = [&](int q, int kmin) {
+        const int b0 = q * cap;
+        const int nq = min(cnt[q], cap);
+        for (int kk = 0; kk < nq; ++kk) {
+          const uint2 pj = fxy[b0 + kk];
+          const int dx = (int)(pj.x - pi.x), dy = (int)(pj.y - pi.y);
+          const unsigned ax = dx < 0 ? 0u - (unsigned)dx : (unsigned)dx;
+          const unsigned ay = dy < 0 ? 0u - (unsigned)dy : (unsigned)dy;
+          const unsigned long long D =
+              (unsigned long long)ax * ax + (unsigned long long)ay * ay;
+          if (!(act && kk > kmin && D >= p.dmin && D <= p.dmax)) continue;
+          const float q32 = __fsub_rn(__fmul_rn(__fsqrt_rn((float)D), p.a), p.b);
+          const float lo = __fsub_rn(q32, p.qm), hi = __fadd_rn(q32, p.qm);
+          if (hi < 0.0f || lo >= p.nb_f) continue;
+          int bin = -1;
+          if (lo >= 0.0f && hi < p.nb_f && floorf(lo) == floorf(hi)) {
+            bin = (int)lo;
+          } else {
+            const int64_t j = (int64_t)b0 + kk;
+            const double ddx = wrap_half(px[j] - px[i], g.L);
+            const double ddy = wrap_half(py[j] - py[i], g.L);
+            const double d = sqrt(ddx * ddx + ddy * ddy);
+            const double qv = (d - g.sigma) / p.dr;
+            if (qv >= 0.0 && qv < (double)p.nbins) bin = (int)qv;
+          }
+          if (bin >= 0) atomicAdd(&hist[bin], 2u);
+        }
+      };
+      visit(c, k);
+      for (int oy = 0; oy <= Ry; ++oy) {
+        const int qy = (cy + oy) % g.cells_y;
+        for (int ox = (oy == 0 ? 1 : -Rx); ox <= Rx; ++ox) {
+          const int qx = ((cx + ox) % g.cells_x + g.cells_x) % g.cells_x;
+          visit(g.cell_off + qy * g.cells_x + qx, -1);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < p.nbins; t += blockDim.x) {
+    unsigned long long sum = 0;
+    for (int w = 0; w < nw; ++w) sum += whist[w * p.nbins + t];
+    if (sum) atomicAdd(&out[t], sum);
+  }
+}
+
 // The fixed-point scan needs rcut < L / 4 (|dX| < 2^30) and int32 slot
 // indices; other boxes take the FP64 scan.  The fractions go to the
 // position buffer the next binning overwrites.
@@ -323,14 +417,54 @@ void launch_min_dist(const Geom& g, const DevBufs& b, double rcut, unsigned long
                                                  b.count[b.cur], Rx, Ry, t_skip, r2_bits, out);
 }
 
+// The fixed-point histogram needs rcut < L / 4, int32 slot indices, a half
+// stencil (2R + 1 <= cells per side) and at most kGrFixedBins bins; other
+// systems (small boxes) take the FP64 scan.  Like the overlap check, it keeps
+// its fractions in the position buffer the next binning overwrites.
+constexpr int kGrFixedBins = 2048;
+
 void launch_gr(const Geom& g, const DevBufs& b, double dr, int nbins, unsigned long long* counts,
                cudaStream_t s) {
-  const int bs = 128;
   const int64_t total = (int64_t)g.ncell * b.cap;
+  const int64_t slots_end = (int64_t)(g.cell_off + g.ncell) * b.cap;
   const double rcut = g.sigma + dr * nbins;
-  const size_t sm = nbins <= kGrSharedBins ? sizeof(unsigned long long) * nbins : 0;
-  k_pairs<true><<<(unsigned)((total + bs - 1) / bs), bs, sm, s>>>(
-      g, b.cap, b.px[b.cur], b.py[b.cur], b.count[b.cur], rcut, dr, nbins, counts);
+  const int Rx = (int)std::ceil(rcut * g.inv_w * (1.0 + 1e-9));
+  const int Ry = (int)std::ceil(rcut * g.inv_h * (1.0 + 1e-9));
+  if (!(rcut < 0.25 * g.L) || slots_end >= ((int64_t)1 << 31) || 2 * Rx + 1 > g.cells_x ||
+      2 * Ry + 1 > g.cells_y || nbins > kGrFixedBins) {
+    const int bs = 128;
+    const size_t sm = nbins <= kGrSharedBins ? sizeof(unsigned long long) * nbins : 0;
+    k_pairs<true><<<(unsigned)((total + bs - 1) / bs), bs, sm, s>>>(
+        g, b.cap, b.px[b.cur], b.py[b.cur], b.count[b.cur], rcut, dr, nbins, counts);
+    return;
+  }
+  const double scale = 4294967296.0 / g.L;
+  uint2* fxy = reinterpret_cast<uint2*>(b.px[1 - b.cur]);
+  {
+    const int bs = 256;
+    k_fixed_point<<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(
+        g, b.cap, b.px[b.cur], b.py[b.cur], b.count[b.cur], scale, fxy);
+  }
+  const double u = g.L / 4294967296.0;
+  const double ed = 1.5;  // |sqrt(D) - d64 / u| in units of u
+  const double tmax = rcut / dr + 1.0;
+  const double e = ed * u / dr + 3.7 * std::ldexp(1.0, -24) * tmax +
+                   std::ldexp(1.0, -24) * (g.sigma / dr + nbins + 3.0) +
+                   std::ldexp(1.0, -50) * tmax;
+  GrFixed p;
+  p.qm = (float)(2.0 * e + std::ldexp(1.0, -21) * (nbins + 2.0));
+  p.a = (float)(u / dr);
+  p.b = (float)(g.sigma / dr);
+  p.nb_f = (float)nbins;
+  p.dr = dr;
+  p.nbins = nbins;
+  const double hi = rcut / u + ed + 1.0, lo = g.sigma / u - ed - 1.0;
+  p.dmax = (unsigned long long)std::ceil(hi * hi);
+  p.dmin = lo > 0.0 ? (unsigned long long)std::floor(lo * lo) : 0ull;
+  const int bs = 128, nw = bs / 32;
+  const size_t sm = sizeof(unsigned int) * (size_t)nw * nbins;
+  k_gr_fixed<<<(unsigned)((g.ncell + nw - 1) / nw), bs, sm, s>>>(
+      g, b.cap, b.px[b.cur], b.py[b.cur], fxy, b.count[b.cur], Rx, Ry, p, counts);
 }
 
 // Hexatic order parameter (Sec. 2, eq. Psi) with Delaunay next neighbours.

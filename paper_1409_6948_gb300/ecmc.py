@@ -124,6 +124,10 @@ _SIGS = {
     "ecmc_gr_counts": (C.c_int, [_H, C.c_void_p, C.c_int, C.POINTER(C.c_int64)]),
     "ecmc_gr": (C.c_int, [_H, C.c_void_p, C.c_void_p, C.c_int]),
     "ecmc_gr_nbins": (C.c_int, [_H, C.POINTER(C.c_int)]),
+    "ecmc_replica_gr_measure": (C.c_int, [_H, C.c_int]),
+    "ecmc_replica_gr_counts": (C.c_int, [_H, C.c_int, C.c_void_p, C.c_int,
+                                         C.POINTER(C.c_int64)]),
+    "ecmc_replica_gr": (C.c_int, [_H, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
     "ecmc_min_distance": (C.c_int, [_H, C.POINTER(C.c_double)]),
     "ecmc_last_cells": (C.c_int, [_H, C.c_void_p]),
     "ecmc_kernel_times": (C.c_int, [_H, C.POINTER(Timing)]),
@@ -377,28 +381,34 @@ class Ecmc:
         _check(load().ecmc_pressure(self._h, C.byref(p), C.byref(se)), "ecmc_pressure")
         return p.value, se.value
 
-    def gr_measure(self):
-        _check(load().ecmc_gr_measure(self._h), "ecmc_gr_measure")
+    def gr_measure(self, replica=None):
+        """Add the current configuration to the pair histogram of replica 0
+        (default), of one replica, or of every replica (replica=-1)."""
+        if replica is None:
+            _check(load().ecmc_gr_measure(self._h), "ecmc_gr_measure")
+        else:
+            _check(load().ecmc_replica_gr_measure(self._h, int(replica)),
+                   "ecmc_replica_gr_measure")
 
     def gr_nbins(self):
         n = C.c_int()
         _check(load().ecmc_gr_nbins(self._h, C.byref(n)), "ecmc_gr_nbins")
         return n.value
 
-    def gr_counts(self):
+    def gr_counts(self, replica=0):
         nb = self.gr_nbins()
         out = np.zeros(nb, np.int64)
         nm = C.c_int64()
-        _check(load().ecmc_gr_counts(self._h, C.c_void_p(out.ctypes.data), nb, C.byref(nm)),
-               "ecmc_gr_counts")
+        _check(load().ecmc_replica_gr_counts(self._h, int(replica), C.c_void_p(out.ctypes.data),
+                                             nb, C.byref(nm)), "ecmc_replica_gr_counts")
         return out, nm.value
 
-    def gr(self):
+    def gr(self, replica=0):
         nb = self.gr_nbins()
         g = np.zeros(nb)
         r = np.zeros(nb)
-        _check(load().ecmc_gr(self._h, C.c_void_p(g.ctypes.data), C.c_void_p(r.ctypes.data), nb),
-               "ecmc_gr")
+        _check(load().ecmc_replica_gr(self._h, int(replica), C.c_void_p(g.ctypes.data),
+                                      C.c_void_p(r.ctypes.data), nb), "ecmc_replica_gr")
         return r, g
 
     def min_distance(self):

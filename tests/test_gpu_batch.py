@@ -147,3 +147,32 @@ def test_autotune_keeps_the_trajectory():
     assert np.array_equal(a.positions(), b.positions())
     a.close()
     b.close()
+
+
+def test_every_replica_has_its_own_pair_histogram():
+    # ecmc_replica_gr_measure(-1) adds each replica's configuration to its own
+    # histogram: integer counts equal the oracle's pair counts of that replica
+    ds = descs(REPLICAS[:4])
+    g = P.Ecmc.batch(ds)
+    g.set_param(E.PARAM_GR_DR, 0.02)
+    g.set_param(E.PARAM_GR_RMAX, 3.0)
+    nb = g.gr_nbins()
+    g.sweep(3)
+    g.gr_measure(-1)
+    g.sweep(2)
+    g.gr_measure(-1)
+    g.gr_measure(1)
+    for r, d in enumerate(REPLICAS[:4]):
+        want = np.zeros(nb, np.int64)
+        x, y, _, L = oracle_run(d, 3)
+        oracle.gr_counts(L, x, y, 1.0, 0.02, nb, counts=want)
+        p = oracle.make_params(d["N"], L, 1.0, d["cells_x"], d["cells_y"], d["ell"], d["n_m"],
+                               d["seed"], d["replica"])
+        oracle.sweeps(p, x, y, 3, 2)
+        oracle.gr_counts(L, x, y, 1.0, 0.02, nb, counts=want)
+        if r == 1:
+            oracle.gr_counts(L, x, y, 1.0, 0.02, nb, counts=want)
+        got, n_meas = g.gr_counts(r)
+        assert n_meas == (3 if r == 1 else 2)
+        assert np.array_equal(got, want), r
+    g.close()

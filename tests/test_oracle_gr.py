@@ -54,3 +54,29 @@ def test_pressure_formula_low_density_limit():
     rho = N / L**2
     assert oracle.pressure_from_gcontact(1.0, N, L, 1.0) == pytest.approx(
         rho * (1 + math.pi / 2 * rho))
+
+
+@pytest.mark.parametrize("N,L,dr,nb,kind", [
+    (300, 30.0, 0.05, 80, "uniform"),       # 7 cells per side
+    (900, 33.0, 0.01, 400, "melted"),       # r_max = 5: 6 cells per side
+    (256, 16.9, 0.01, 400, "lattice"),      # fewer than 3 cells: the brute force itself
+    (2000, 60.0, 0.02, 100, "uniform"),
+])
+def test_cell_list_counts_equal_brute_force(N, L, dr, nb, kind):
+    # the cell-list search must find every pair the brute force finds: the
+    # histograms are equal bin by bin, including pairs across the boundary
+    rng = np.random.default_rng(N)
+    if kind == "uniform":
+        x, y = rng.random(N) * L, rng.random(N) * L
+    else:
+        k = int(round(math.sqrt(N)))
+        a = L / k
+        i = np.arange(k * k)
+        x, y = (i % k + 0.5) * a, (i // k + 0.5) * a
+        if kind == "melted":
+            p = oracle.make_params(N, L, 1.0, 2, 2, 3.0, 4, 9)
+            oracle.sweeps(p, x, y, 0, 30)
+    brute = oracle.gr_counts(L, x, y, 1.0, dr, nb)
+    cells = oracle.gr_counts_cells(L, x, y, 1.0, dr, nb)
+    assert brute.sum() > 0
+    assert np.array_equal(brute, cells)
