@@ -137,15 +137,24 @@ def workload(args):
     return w, cells, ell
 
 
-def batch_descs(args, rank):
+def batch_descs(args, rank, reference=False):
     """Replica batch descriptors: the paper's strategy (Sec. 4) picks cells,
-    ell and n_m for every replica; every rank runs its own replica keys."""
-    from paper_1409_6948_gb300 import ecmc as E
-
+    ell and n_m for every replica; every rank runs its own replica keys.  The
+    reference arm takes the strategy from the oracle, ours from the
+    library (the two give the same choice; tests/test_oracle_strategy.py)."""
     reps = W.replica_batch() if args.workload == "batch" else W.eos_batch()
     out = []
     for d in reps:
-        s = E.suggest_parameters(d["N"], d["L"], 1.0, 2.0)
+        if reference:
+            import oracle
+
+            c, ell, nm = oracle.suggest_parameters(d["N"], d["L"], 1.0, 2.0)
+            s = {"N": d["N"], "L": d["L"], "sigma": 1.0, "cells_x": c, "cells_y": c, "ell": ell,
+                 "n_m": nm}
+        else:
+            from paper_1409_6948_gb300 import ecmc as E
+
+            s = E.suggest_parameters(d["N"], d["L"], 1.0, 2.0)
         s.update(seed=d["seed"], replica=replica_key(rank, d["replica"]), eta=d["eta"])
         out.append(s)
     return out
@@ -724,11 +733,8 @@ def run_reference(args):
     nm = args.nm
     if not args.fixed_params and not args.cells and not args.ell and \
             args.workload in ("large", "huge") or args.paper_params:
-        from paper_1409_6948_gb300 import ecmc as E  # parameter choice only (host arithmetic)
-
-        sp = E.suggest_parameters(w.N, L, 1.0, 2.0)
-        cells, ell = sp["cells_x"], sp["ell"]
-        nm = nm or sp["n_m"]
+        cells, ell, sp_nm = oracle.suggest_parameters(w.N, L, 1.0, 2.0)
+        nm = nm or sp_nm
     nm = nm or oracle.default_nm(w.N, L, 1.0, cells, cells, ell)
     x, y = W.square_lattice(w.N, L)
     p = oracle.make_params(w.N, L, 1.0, cells, cells, ell, nm, w.seed)
@@ -1041,9 +1047,7 @@ def run_reference_batch(args):
     sweep of one replica, the replicas taken in turn."""
     import oracle
 
-    from paper_1409_6948_gb300 import ecmc as E  # parameter choice only (host arithmetic)
-
-    descs = batch_descs(args, 0)
+    descs = batch_descs(args, 0, reference=True)
     states = []
     for d in descs:
         x, y = W.square_lattice(d["N"], d["L"])

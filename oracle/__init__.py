@@ -85,6 +85,13 @@ def lib():
         L.orc_gr_counts_cells.argtypes = [i64, C.c_double, d, d, C.c_double, C.c_double,
                                           C.c_int, C.POINTER(C.c_int64)]
         L.orc_gr_counts_cells.restype = None
+        L.orc_suggest_parameters.argtypes = [i64, C.c_double, C.c_double, C.c_double,
+                                             C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                             C.POINTER(C.c_int)]
+        L.orc_suggest_parameters.restype = C.c_int
+        L.orc_autocorrelation_time.argtypes = [d, d, i64, i64, C.POINTER(C.c_double),
+                                               C.c_void_p]
+        L.orc_autocorrelation_time.restype = C.c_int
         L.orc_min_dist2.argtypes = [i64, C.c_double, d, d, C.c_double]
         L.orc_min_dist2.restype = C.c_double
         L.orc_run_chain_frame.argtypes = [C.c_int, C.c_int, d, d, C.POINTER(C.c_int64),
@@ -164,6 +171,30 @@ def bin_cells(p, t, x, y):
 def default_nm(N, L, sigma, cells_x, cells_y, ell):
     return lib().orc_default_nm(int(N), float(L), float(sigma), int(cells_x), int(cells_y),
                                 float(ell))
+
+
+def suggest_parameters(N, L, sigma=1.0, min_cell_side=0.0):
+    """The closing strategy of Sec. 4: (cells per side, ell, n_m)."""
+    c, ell, nm = C.c_int(), C.c_double(), C.c_int()
+    rc = lib().orc_suggest_parameters(int(N), float(L), float(sigma), float(min_cell_side),
+                                      C.byref(c), C.byref(ell), C.byref(nm))
+    if rc != 0:
+        raise ValueError("no grid of 2x2 cells fits (rc=%d)" % rc)
+    return c.value, ell.value, nm.value
+
+
+def autocorrelation_time(psi_series, max_lag):
+    """tau of a complex series (eq. tau) and C(0..max_lag)."""
+    z = np.asarray(psi_series, dtype=complex)
+    re = np.ascontiguousarray(z.real)
+    im = np.ascontiguousarray(z.imag)
+    c = np.empty(int(max_lag) + 1)
+    tau = C.c_double()
+    rc = lib().orc_autocorrelation_time(_dptr(re), _dptr(im), int(z.size), int(max_lag),
+                                        C.byref(tau), c.ctypes.data_as(C.c_void_p))
+    if rc != 0:
+        raise ValueError("bad series (rc=%d)" % rc)
+    return tau.value, c
 
 
 def sweeps(p, x, y, t0, n_sweeps, stats=None, records=False):

@@ -32,13 +32,17 @@
  *   Sec. 2               pair-correlation histogram with the centred-bin rule.
  *   Sec. 4, eq. (nm)     default number of chains per cell.
  *
- * Readings where the paper is silent (each also listed in the design notes):
+ * Readings where the paper is silent, ambiguous or garbled:
  *   - direction: axis x on even sweeps and y on odd sweeps, sign +/- drawn
  *     per chain (the "+x/+y only" variant is not reversible, Sec. 3.2);
  *   - shift uniform on [0,w) x [0,h); colour order uniform over the 24
  *     orders, shared by all blocks; colour = (cx mod 2) + 2 (cy mod 2);
  *   - a disk belongs to the cell holding its centre (half-open cells),
- *     cx = floor((x - s_x mod L) * (1/w)) clamped to the grid;
+ *     cx = floor((x - s_x mod L) * (1/w)) clamped to the grid.  The paper
+ *     fixes no rounding rule at cell walls; the reciprocal is multiplied
+ *     (one rounded product, as the CUDA binning computes it) rather than
+ *     divided, so both sides put a disk lying on a wall to rounding in the
+ *     same cell;
  *     start disk = member number floor(v n_c / 2^64) in ascending-id order;
  *   - geometry is done in the frame of the active cell: the cell occupies
  *     [0,w] x [0,h]; its members and every periodic image of every other
@@ -49,11 +53,25 @@
  *   - ties: equal hit distances are broken by the smaller (id, image) key;
  *     at equal distance the chain end beats a contact, and a contact beats
  *     a wall; a corner reflects both components;
- *   - reflection at a frozen disk is specular about the line of centres at
- *     contact; reflection at a wall flips the normal component of d.
- *   - pressure estimator: the projected separation b of every contact (lifts
- *     and frozen-disk reflections) is summed; beta P / rho = 1 + sum_b /
- *     sum_ell (the collision form of eq. (pressure), see the design notes).
+ *   - reflection (Fig. 1, angle of incidence equal to angle of reflection):
+ *     a chain along an axis turns back along that axis at a frozen disk, as
+ *     it does at a wall -- the reflection about the contact's tangent taken
+ *     with respect to the chain axis.  This keeps every chain its own
+ *     reverse (the detailed-balance argument around Fig. 2); a specular
+ *     reflection about the line of centres would leave the axes, so the
+ *     reverse chain would never be proposed (kept as ORC_FLAG_SPECULAR_AXIS,
+ *     which the exact three-disk law rejects).  Isotropic chains reflect
+ *     specularly about the line of centres; a wall flips the normal
+ *     component of d;
+ *   - pressure estimator, the collision form of eq. (pressure) that the
+ *     paper names as an extension: the projected separation b of every
+ *     contact (lifts and frozen-disk reflections) is summed per cell, and
+ *     each cell's sum and displacement are weighted by its member count n_c:
+ *     beta P / rho = 1 + sum_cells n_c sum_b / sum_cells n_c n_m ell.  Every
+ *     cell receives the same displacement n_m ell whatever n_c, so the
+ *     unweighted ratio over-weights sparse cells and reads low (the
+ *     low-density virial series shows it); the unweighted sums are kept in
+ *     sum_b, sum_disp.
  */
 #include "ecmc_oracle.h"
 
@@ -181,6 +199,37 @@ int orc_default_nm(int64_t N, double L, double sigma, int cells_x, int cells_y, 
   double nm = per_cell * lambda0 / ell;                               /* eq. (nm) */
   int r = (int)floor(nm + 0.5);
   return r < 1 ? 1 : r;
+}
+
+/* The strategy that closes Sec. 4 for the degree of parallelisation, the
+ * displacement and the chain starts, on a square grid of an even number of
+ * cells per side (n = h^2 blocks of 2x2 cells, h blocks per side):
+ *   1) h as large as possible with N / (eta n) > 100, which keeps the
+ *      displacement of step 2 above 10 lambda0; then, while the cell side
+ *      L / (2h) is not above max(sigma, min_cell_side), one block per side
+ *      less (at least one);
+ *   2) ell = lambda0 (N / (eta n))^(1/2), the second form of eq. (criterion),
+ *      so that a chain spans about one cell;
+ *   3) n_m from eq. (nm) (orc_default_nm).
+ * Returns 0, or -1 if eta is at or above close packing or 2x2 cells of side
+ * above the minimum do not fit. */
+int orc_suggest_parameters(int64_t N, double L, double sigma, double min_cell_side,
+                           int* cells_per_side, double* ell, int* n_m) {
+  const double pi = 3.14159265358979323846;
+  double eta = (double)N * pi * sigma * sigma / (4.0 * L * L); /* eq. (1) */
+  double eta_hcp = pi / (2.0 * sqrt(3.0));
+  double lambda0 = sigma * (eta_hcp - eta) / (2.0 * eta_hcp); /* Sec. 4 */
+  if (!(lambda0 > 0.0) || N < 1) return -1;
+  double side_min = min_cell_side > sigma ? min_cell_side : sigma;
+  int64_t h = 1;
+  while ((double)N / (eta * (double)((h + 1) * (h + 1))) > 100.0) h++;
+  while (h > 1 && !(L / (double)(2 * h) > side_min)) h--;
+  if (!(L / (double)(2 * h) > side_min)) return -1;
+  double n = (double)(h * h);
+  *cells_per_side = (int)(2 * h);
+  *ell = lambda0 * sqrt((double)N / (eta * n));
+  *n_m = orc_default_nm(N, L, sigma, (int)(2 * h), (int)(2 * h), *ell);
+  return 0;
 }
 
 /* Uniformly distributed unit vector for chain k of cell c in sweep t: the
@@ -981,6 +1030,45 @@ int orc_sweeps_snap(const orc_params* p, double* x, double* y, int64_t t0, int64
     if (rc) return rc;
     memcpy(snap_x + s * p->N, x, sizeof(double) * p->N);
     memcpy(snap_y + s * p->N, y, sizeof(double) * p->N);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Autocorrelation time of the hexatic order parameter (Sec. 2, eq. tau)     */
+/* ------------------------------------------------------------------------ */
+/* C(dt) = Re <conj(Psi(t)) Psi(t+dt)> / <|Psi(t)|^2>, each average over the
+ * samples available (n - dt pairs at lag dt, n samples for the norm), the mean
+ * of Psi taken as zero as the definition says.  tau = the first lag with
+ * C < 1/e, moved back linearly towards the lag before it; INFINITY if there is
+ * none up to max_lag.  re[], im[] hold the series; c[] (may be NULL) receives
+ * C(0..max_lag).  Returns 0, or -1 for a bad argument. */
+int orc_autocorrelation_time(const double* re, const double* im, int64_t n, int64_t max_lag,
+                             double* tau, double* c) {
+  if (n < 2 || max_lag < 1 || max_lag >= n) return -1;
+  double power = 0.0;
+  for (int64_t t = 0; t < n; ++t) power += re[t] * re[t] + im[t] * im[t];
+  power = power / (double)n;
+  if (!(power > 0.0)) return -1;
+  double threshold = exp(-1.0);
+  double c_prev = 0.0;
+  *tau = INFINITY;
+  for (int64_t lag = 0; lag <= max_lag; ++lag) {
+    double sum = 0.0;
+    int64_t pairs = n - lag;
+    for (int64_t t = 0; t < pairs; ++t) {
+      /* real part of conj(a) * b */
+      sum += re[t] * re[t + lag] + im[t] * im[t + lag];
+    }
+    double c_lag = (sum / (double)pairs) / power;
+    if (c) c[lag] = c_lag;
+    if (c_lag < threshold && isinf(*tau)) {
+      if (lag == 0)
+        *tau = 0.0;
+      else
+        *tau = (double)(lag - 1) + (c_prev - threshold) / (c_prev - c_lag);
+    }
+    c_prev = c_lag;
   }
   return 0;
 }

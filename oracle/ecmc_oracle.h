@@ -108,6 +108,13 @@ int orc_bin(const orc_params* p, int64_t t, const double* x, const double* y, in
 /* Default n_m from eq. (nm) with the mean free path estimate of Sec. 4. */
 int orc_default_nm(int64_t N, double L, double sigma, int cells_x, int cells_y, double ell);
 
+/* The paper's closing strategy of Sec. 4 on square grids: the largest number
+ * of 2x2 blocks n = h^2 with N / (eta n) > 100 (cell side above
+ * max(sigma, min_cell_side)), ell = lambda0 (N / (eta n))^(1/2) (eq.
+ * criterion), n_m from eq. (nm).  Returns 0 or -1 (no such grid). */
+int orc_suggest_parameters(int64_t N, double L, double sigma, double min_cell_side,
+                           int* cells_per_side, double* ell, int* n_m);
+
 /* Run sweeps t0 .. t0+n_sweeps-1 in place on positions x[N], y[N] (disk-id
  * order, wrapped to [0,L)).  Statistics are accumulated into *st (may be
  * NULL).  If recs is not NULL it receives one record per (sweep, cell, chain)
@@ -165,6 +172,13 @@ int orc_run_chain_frame(int n, int n_mem, double* X, double* Y, const int64_t* i
                         const int32_t* img, double w, double h, double sigma, int m, double dx,
                         double dy, double ell, int mode, orc_stats* st,
                         orc_chain_rec* rec);
+
+/* Autocorrelation time of a complex series (Sec. 2, eq. tau): C(dt) = Re
+ * <conj(Psi(t)) Psi(t+dt)> / <|Psi|^2> with the mean of Psi taken as zero, tau
+ * = the 1/e lag, interpolated linearly; INFINITY if C stays above 1/e up to
+ * max_lag.  c (may be NULL) receives C(0..max_lag).  Returns 0 or -1. */
+int orc_autocorrelation_time(const double* re, const double* im, int64_t n, int64_t max_lag,
+                             double* tau, double* c);
 
 #ifdef __cplusplus
 }

@@ -7,7 +7,7 @@
  * compiled with -ffp-contract=off, one sphere and one candidate at a time.
  *
  * The two-dimensional readings carry over, with these choices for the third
- * dimension (each listed in the design notes):
+ * dimension:
  *   - cells: the box is cut into cells^3 cubes of side w = L / cells on a
  *     lattice shifted by s uniform on [0,w)^3; a sphere belongs to the cube
  *     holding its centre; colour = (cx mod 2) + 2 (cy mod 2) + 4 (cz mod 2);

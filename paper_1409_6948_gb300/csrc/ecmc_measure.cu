@@ -712,3 +712,46 @@ int probe_peaks(double* smem_gbs, double* fp64_gflops) {
 }
 
 }  // namespace ecmc
+
+// ---- autocorrelation time of the hexatic order parameter (Sec. 2, eq. tau)
+// Host arithmetic on a short series.  C(dt) = Re <Psi*(t) Psi(t + dt)>_t /
+// <|Psi(t)|^2>_t: the numerator averages the n - dt products available at lag
+// dt, the denominator all n samples; no mean is subtracted, since <Psi> = 0 by
+// the arbitrary phase (the paper builds this into the definition).  tau is
+// the lag where C first falls below 1/e, interpolated linearly between the
+// two lags around it; +infinity if C stays at or above 1/e up to max_lag.
+// Sums run in increasing t, so the result does not depend on threading.
+extern "C" int ecmc_autocorrelation_time(const double* psi, int64_t n, int64_t max_lag,
+                                         double* tau, double* c_out) {
+  if (!psi || !tau || n < 2) return ecmc::report_error(ECMC_ERR_ARG, "need psi, tau and n >= 2");
+  if (max_lag <= 0) max_lag = n / 4 > 1 ? n / 4 : 1;
+  if (max_lag > n - 1) return ecmc::report_error(ECMC_ERR_ARG, "max_lag must be below n");
+  double norm = 0.0;
+  for (int64_t t = 0; t < n; ++t) {
+    const double re = psi[2 * t], im = psi[2 * t + 1];
+    norm += re * re + im * im;
+  }
+  norm /= (double)n;
+  if (!(norm > 0.0) || !std::isfinite(norm))
+    return ecmc::report_error(ECMC_ERR_ARG, "the series has no positive finite power");
+  const double inv_e = std::exp(-1.0);
+  double prev = 1.0;
+  *tau = std::numeric_limits<double>::infinity();
+  bool found = false;
+  for (int64_t d = 0; d <= max_lag; ++d) {
+    double acc = 0.0;
+    for (int64_t t = 0; t + d < n; ++t) {
+      // Re(conj(a) b) = a_re b_re + a_im b_im
+      acc += psi[2 * t] * psi[2 * (t + d)] + psi[2 * t + 1] * psi[2 * (t + d) + 1];
+    }
+    const double c = (acc / (double)(n - d)) / norm;
+    if (c_out) c_out[d] = c;
+    if (!found && c < inv_e) {
+      *tau = d == 0 ? 0.0 : (double)(d - 1) + (prev - inv_e) / (prev - c);
+      found = true;
+      if (!c_out) break;
+    }
+    prev = c;
+  }
+  return ECMC_OK;
+}

@@ -137,6 +137,8 @@ _SIGS = {
                                C.c_void_p]),
     "ecmc_hexatic": (C.c_int, [_H, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.POINTER(C.c_int64)]),
+    "ecmc_autocorrelation_time": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64,
+                                            C.POINTER(C.c_double), C.c_void_p]),
     "ecmc_sweep_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_double, C.c_int,
                                      C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_uint64,
                                      C.c_int64, C.c_int64, C.c_void_p]),
@@ -718,21 +720,17 @@ def sqrt_rn(x, rel_error=None, stream=None):
 
 
 def autocorrelation_time(psi_series, max_lag=None):
-    """Autocorrelation time tau of a complex order-parameter series (eq. tau):
-    C(dt) = Re <Psi*(t) Psi(t+dt)> / <|Psi|^2> (the mean of Psi is taken as
-    zero, as the definition prescribes), tau = the lag at which C falls to
-    1/e, interpolated linearly between lags.  Returns (tau, C)."""
-    z = np.asarray(psi_series, dtype=complex)
+    """Autocorrelation time tau of a complex order-parameter series (eq. tau),
+    computed by ecmc_autocorrelation_time.  Returns (tau, C[0..max_lag])."""
+    z = np.ascontiguousarray(np.asarray(psi_series, dtype=complex))
     n = z.size
     if max_lag is None:
         max_lag = n // 4
-    denom = np.mean(np.abs(z) ** 2)
-    c = np.array([np.real(np.mean(np.conj(z[:n - d]) * z[d:])) / denom
-                  for d in range(max_lag + 1)])
-    below = np.flatnonzero(c < math.exp(-1.0))
-    if below.size == 0:
-        return float("inf"), c
-    d = below[0]
-    c0, c1 = c[d - 1], c[d]
-    return (d - 1) + (c0 - math.exp(-1.0)) / (c0 - c1), c
+    buf = np.ascontiguousarray(np.stack([z.real, z.imag], 1).ravel())
+    c = np.empty(int(max_lag) + 1)
+    tau = C.c_double()
+    _check(load().ecmc_autocorrelation_time(C.c_void_p(buf.ctypes.data), int(n), int(max_lag),
+                                            C.byref(tau), C.c_void_p(c.ctypes.data)),
+           "ecmc_autocorrelation_time")
+    return tau.value, c
 

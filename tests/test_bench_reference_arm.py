@@ -41,3 +41,34 @@ def test_other_ranks_exit_without_work():
     rc, out = run({"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"},
                   "--workload", "small", "--steps", "2", "--warmup", "3")
     assert rc == 0 and out.strip() == ""
+
+
+def _reference_run_loads(*args):
+    # run the reference arm in a fresh interpreter and report whether the
+    # product package or its library was loaded on the way
+    code = ("import runpy, sys\n"
+            "sys.argv = ['bench.py', '--impl', 'reference'] + %r\n"
+            "try:\n"
+            "    runpy.run_path('bench.py', run_name='__main__')\n"
+            "except SystemExit:\n"
+            "    pass\n"
+            "maps = open('/proc/self/maps').read()\n"
+            "print('PACKAGE', 'paper_1409_6948_gb300' in sys.modules)\n"
+            "print('LIBECMC', 'libecmc' in maps)\n"
+            "print('LIBORACLE', 'liboracle' in maps)\n" % (list(args),))
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr
+    lines = dict(ln.split() for ln in r.stdout.splitlines() if ln.startswith(("PACKAGE",
+                                                                               "LIBECMC",
+                                                                               "LIBORACLE")))
+    return lines
+
+
+def test_reference_arm_runs_without_the_product_library():
+    # the default workload picks its cells and ell by the paper's strategy;
+    # the reference arm takes that choice from the oracle
+    got = _reference_run_loads("--steps", "1", "--warmup", "3", "--melt", "0")
+    assert got == {"PACKAGE": "False", "LIBECMC": "False", "LIBORACLE": "True"}
+    got = _reference_run_loads("--workload", "eos", "--steps", "2", "--warmup", "3")
+    assert got == {"PACKAGE": "False", "LIBECMC": "False", "LIBORACLE": "True"}

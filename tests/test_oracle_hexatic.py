@@ -118,22 +118,3 @@ def test_dense_lattice_start_is_square_symmetric():
     psi, pk, nn, bad = oracle.hexatic(L, x, y)
     assert np.all(nn == 4)
     assert abs(psi) < 1e-12
-
-
-def test_autocorrelation_time_of_an_ar1_series():
-    # complex AR(1): z_{t+1} = a z_t + noise has C(dt) = a^dt exactly, so the
-    # 1/e lag is tau = -1 / ln a
-    from paper_1409_6948_gb300.ecmc import autocorrelation_time
-
-    rng = np.random.default_rng(7)
-    tau0 = 12.5
-    a = math.exp(-1.0 / tau0)
-    n = 200000
-    noise = rng.normal(size=n) + 1j * rng.normal(size=n)
-    z = np.empty(n, complex)
-    z[0] = noise[0]
-    for t in range(1, n):
-        z[t] = a * z[t - 1] + noise[t]
-    tau, c = autocorrelation_time(z, max_lag=100)
-    assert abs(c[10] - a ** 10) < 0.02
-    assert abs(tau - tau0) < 0.05 * tau0
