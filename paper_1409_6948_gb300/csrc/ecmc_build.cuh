@@ -215,20 +215,27 @@ __device__ void build_frame(const BuildArgs& A) {
     }
   };
 
+  // The offsets r = x - o lie in (-L, L) (x in [0, L), the frame origin o in
+  // [0, L)), and the frame (-sigma, w + sigma) is shorter than L, so only the
+  // images r - L, r, r + L can fall in it: bits 1, 2, 3 of the image masks.
+  // The neighbour of disk idx is searched from the previous round's (idx
+  // only grows).
   int nbuf = 0;  // warp-uniform fill of this warp's buffer (< 32 between chunks)
+  int e_run = 0;
   for (int base = warp * 32; base < T; base += bt) {
     const int idx = base + lane;
     bool keep = false;
     int2 ent = make_int2(0, 0);
     if (idx < T) {
-      int e = 0;
+      int e = e_run;
       while (e + 1 < nnb && s_pre[e + 1] <= idx) ++e;
+      e_run = e;
       const int k = idx - s_pre[e];
       const int64_t q = (int64_t)s_nb[e] * cap + k;
       const float rxf = to_float_trunc(load_pos<CG>(A.px + q)) - oxf;
       const float ryf = to_float_trunc(load_pos<CG>(A.py + q)) - oyf;
       unsigned imgx = 0, imgy = 0;
-      for (int j = -2; j <= 2; ++j) {
+      for (int j = -1; j <= 1; ++j) {
         const float Xf = rxf + (float)j * Lf, Yf = ryf + (float)j * Lf;
         imgx |= (Xf > xlo && Xf < xhi) ? (1u << (j + 2)) : 0u;
         imgy |= (Yf > ylo && Yf < yhi) ? (1u << (j + 2)) : 0u;

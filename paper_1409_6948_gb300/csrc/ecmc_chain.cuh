@@ -123,19 +123,23 @@ __device__ __forceinline__ void shuffled_list(int* pl, int CPW, int gi, int n, i
 // exceeds the step.  They are replayed from the history with one subtraction
 // each; at the leg where the budget runs out the disks are put where the
 // recorded legs left them and the full search resumes (and ends the chain).
-__device__ __forceinline__ void replay_cycle(const Frame& f, const LegHist& hs, int gi,
+// The smallest such K is used.  The TPC lanes of the group share the search:
+// lane sub tests K = 2 (sub + 1), 2 (sub + 1) + 2 TPC, ..., and the group
+// takes the minimum (every lane of the group arrives here with the same
+// state, so all TPC lanes take part in the shuffles).
+template <int TPC>
+__device__ __forceinline__ void replay_cycle(const Frame& f, const LegHist& hs, int gi, int sub,
                                              int& n_leg, int& m, int& sg, double& P,
                                              float& P32, double& Q, float& Q32, double& r,
                                              int64_t& n_iter, double& sum_b, int& n_events,
                                              int& n_lifts, int& n_frozen, int& n_walls,
                                              int& ch_events, int& ch_walls, int& n_replayed) {
   const int CPW = f.cpw;
-  int Kf = 0;
+  int Kf = INT_MAX;
   // the loops stay rolled: the check runs at every reflection, and unrolled
   // it grows the sweep kernel beyond what its instruction cache holds
-  // (measured 3 % slower)
 #pragma unroll 1
-  for (int K = 2; K <= kHist && K <= n_leg; K += 2) {
+  for (int K = 2 * (sub + 1); K <= kHist && K <= n_leg; K += 2 * TPC) {
     const int s0 = ((n_leg - K) & (kHist - 1)) * CPW + gi;
     if (hs.m[s0] != m || dbits(hs.P[s0]) != dbits(P) || ((hs.flags[s0] & 1) != (sg < 0 ? 1 : 0)))
       continue;
@@ -155,7 +159,15 @@ __device__ __forceinline__ void replay_cycle(const Frame& f, const LegHist& hs, 
       break;
     }
   }
-  if (Kf == 0) return;
+  if (TPC > 1) {
+    const unsigned gmask = TPC == 32 ? 0xffffffffu : (((1u << TPC) - 1u) << (gi * TPC));
+#pragma unroll
+    for (int o = 1; o < TPC; o <<= 1) {
+      const int ok = __shfl_xor_sync(gmask, Kf, o);
+      Kf = ok < Kf ? ok : Kf;
+    }
+  }
+  if (Kf == INT_MAX) return;
   const int base = n_leg - Kf;
   int o = 0;
   for (;;) {
@@ -551,7 +563,7 @@ __device__ __forceinline__ void run_group(const Frame& f, const LegHist& hs, con
         if (!is_end) {
           // frozen disk or wall: the chain turns back along its axis
           sg = -sg;
-          if (replay && g.list_mode == 0) replay_cycle(f, hs, gi, n_leg, m, sg, P, P32, Q, Q32, r, n_iter, sum_b,
+          if (replay && g.list_mode == 0) replay_cycle<TPC>(f, hs, gi, sub, n_leg, m, sg, P, P32, Q, Q32, r, n_iter, sum_b,
                                    n_events, n_lifts, n_frozen, n_walls, ch_events, ch_walls,
                                    n_replayed);
         }
