@@ -12,6 +12,7 @@ With N > 1 (launched by torch.distributed.run) every rank advances its own
 replica (Philox key (seed, rank)): independent replicas, no data exchange.
 """
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -32,27 +33,27 @@ import ecmc_workloads as W  # noqa: E402
 METRIC = ("collision events/s, sweeps/s (N=1M, η=0.72); "
           "batched FP32 vs FP64 at equal P error")
 UNIT = "events/s"
-# algorithmic shared-memory bytes per collision event of the chain kernel: the
-# candidates in the region the first hit can come from (about 2 disks at
-# eta = 0.72) read as FP64 coordinates (2 x 16 B), plus the active disk's
-# coordinates read and written (16 B)
-# Roofline of the chain kernel: the FP64 pipe.  Each iteration of a chain's
-# event loop (a contact, a wall reflection or the end of the budget) needs, in
-# the method's exact arithmetic, 10 FP64 operations: the hit test of the first
-# candidate (x_j - x_m, y_j - y_m, c^2, sigma^2 - c^2, b - sqrt), the wall
-# distance, the new position, the new budget and the contact sum (b - s and
-# its accumulation).  The square root runs on the integer pipes.
-FP64_OPS_PER_ITERATION = 10
-# FP64 lanes per SM and clock on GB300 (the dfma peak ncu reports per SM)
-FP64_LANES_PER_SM_CLK = 2
-# DRAM bytes (read + write) of one k_phase launch at the large workload with the
-# paper's parameters, melted, TPC 8, frames in shared memory, from
-# `ncu --set full` (profiles/k_phase_large_paper_params.md), taken before the
-# kernel's last changes and therefore no longer reported
-K_PHASE_DRAM_BYTES = 39.11e6
-# the same for one k_sweep_fused launch (a whole sweep), from ncu
-# (profiles/k_sweep_fused_large_paper_params.md, the capture of the current kernel)
-K_SWEEP_FUSED_DRAM_BYTES = 40.52e6
+# Roofline of the chain kernel (the scope table's measurement row): shared
+# memory, against ALGORITHMIC bytes per collision event -- the disks whose
+# centres lie in the strip that can hold the first hit, area 2 sigma (sigma +
+# lambda0) with lambda0 the measured mean free path, read as FP32 (8 B) or
+# FP64 (16 B) coordinates, plus 16 B to read and write the active disk
+# (smem_bytes_per_event below).
+#
+# Counters of the persistent sweep kernel k_sweep_fused<8 lanes per cell,
+# FP32 screening, frames in shared memory, axis chains> that need more than
+# one ncu pass: captured at N = 640,000, eta = 0.72 with the paper's
+# parameters (188 x 188 cells, about 8,800 active cells per phase, so the
+# occupancy of the N = 1M workload), one launch = one sweep
+# (profiles/k_sweep_fused_n640k_paper_params.md); the full-size workload is
+# profiled with single-pass metric sets only.  Both scale with the work:
+# DRAM bytes with the disks (every cell and its halo are read once per colour
+# phase), FP64 warp-instructions with the event-loop iterations.
+FUSED_CAPTURE_N = 640000
+FUSED_DRAM_BYTES_CAPTURE = 24628480 + 7424       # dram__bytes_read.sum + _write.sum
+FUSED_FP64_WINST_CAPTURE = 5852193               # smsp__inst_executed_pipe_fp64.sum
+FUSED_ITERATIONS_CAPTURE = 1524505               # contacts + walls + chain ends per launch
+FUSED_NCU_FP64_PIPE_PCT = 38.55                  # sm__pipe_fp64_cycles_active, % of active
 
 
 def parse():
@@ -79,6 +80,9 @@ def parse():
                          "over stripes x ell, both boundary rules")
     ap.add_argument("--dim3", action="store_true",
                     help="hard spheres in three dimensions: events/s over cells x ell (N = 64^3)")
+    ap.add_argument("--gr", action="store_true",
+                    help="time the pair-correlation histogram (0.01 sigma bins to 5 sigma) on "
+                         "the --workload (default medium: N = 65,536) and on the large one")
     ap.add_argument("--grid", action="store_true",
                     help="parallelisation grid at N = 1M (cells x ell), one JSON line")
     ap.add_argument("--paper-params", action="store_true",
@@ -98,6 +102,9 @@ def parse():
     ap.add_argument("--cells", type=int, default=0, help="cells per side (0 = workload default)")
     ap.add_argument("--ell", type=float, default=0.0, help="chain displacement (0 = default)")
     ap.add_argument("--nm", type=int, default=0, help="chains per cell (0 = eq. nm)")
+    ap.add_argument("--n", type=int, default=0,
+                    help="disks of the large workload (a perfect square; 0 = 1048576): the "
+                         "same packing fraction and seed, e.g. a smaller case for profiling")
     ap.add_argument("--tpc", type=int, default=0, help="lanes per cell (0 = automatic)")
     ap.add_argument("--prec", type=int, default=1, help="1 FP32 screening, 0 FP64 candidates")
     ap.add_argument("--no-flush", action="store_true", help="do not flush L2 between steps")
@@ -132,6 +139,8 @@ def melt_sweeps(args):
 def workload(args):
     w = {"small": W.SMALL, "medium": W.MEDIUM, "large": W.LARGE, "huge": W.HUGE,
          "batch": W.LARGE, "eos": W.LARGE}[args.workload]
+    if args.n and args.workload == "large":
+        w = dataclasses.replace(w, N=args.n, name="N=%d eta=%g" % (args.n, w.eta))
     cells = args.cells or w.cells
     ell = args.ell or w.ell
     return w, cells, ell
@@ -645,6 +654,58 @@ def run_stripes(args):
     return 0
 
 
+def run_gr(args):
+    """The pair-correlation histogram of Sec. 2 (0.01 sigma bins from sigma to 5
+    sigma, ordered pairs) on a melted state: CUDA-event time per measurement
+    (fixed-point positions, then the pair histogram), pairs binned per second.
+    One JSON line per workload."""
+    import torch
+
+    import paper_1409_6948_gb300 as P
+    from paper_1409_6948_gb300 import ecmc as E
+
+    torch.cuda.set_device(0)
+    names = ["medium", "large"] if args.workload == "large" else [args.workload, "large"]
+    for name in names:
+        w = {"small": W.SMALL, "medium": W.MEDIUM, "large": W.LARGE, "huge": W.HUGE}[name]
+        L = w.L
+        sp = E.suggest_parameters(w.N, L, 1.0, 2.0) if name in ("large", "huge") else \
+            {"cells_x": w.cells, "ell": w.ell, "n_m": 0}
+        g = P.Ecmc(w.N, L, 1.0, sp["cells_x"], sp["cells_x"], sp["ell"], w.seed)
+        if sp["n_m"]:
+            g.set_param(E.PARAM_N_CHAINS, sp["n_m"])
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        g.set_stream(stream)
+        g.set_param(E.PARAM_GR_DR, 0.01)
+        g.set_param(E.PARAM_GR_RMAX, 5.0)
+        g.sweep(melt_sweeps(args))
+        g.synchronize()
+        for _ in range(args.warmup):
+            g.gr_measure()
+        g.synchronize()
+        g.reset_stats()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(args.steps):
+            g.gr_measure()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / args.steps
+        counts, nm = g.gr_counts()
+        pairs = float(counts.sum()) / nm
+        print(json.dumps({"mode": "gr", "workload": w.name, "N": w.N,
+                          "cells": sp["cells_x"], "bins": int(counts.size), "dr": 0.01,
+                          "rmax": 5.0, "measurements": args.steps, "us_per_measurement": 1e3 * ms,
+                          "ordered_pairs_per_measurement": pairs,
+                          "pairs_per_s": pairs / (ms * 1e-3),
+                          "disks_per_s": w.N / (ms * 1e-3)}), flush=True)
+        g.set_stream(None)
+        g.close()
+    return 0
+
+
 def run_tau(args):
     """Sampling efficiency (Sec. 2 eq. tau; Figs. 5-6): the autocorrelation
     time tau of the hexatic order parameter Psi for N = 64^2 disks at
@@ -934,12 +995,12 @@ def run_ours(args):
     if rank == 0:
         phase_avg_ms = kt.phase_ms / max(kt.phase_launches, 1)
         iters = c.events + c.wall_hits + c.chains
-        ops_per_launch = FP64_OPS_PER_ITERATION * iters / max(kt.phase_launches, 1)
-        achieved = ops_per_launch / (phase_avg_ms * 1e-3) / 1e9
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-        sm_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
-        fp64_peak = FP64_LANES_PER_SM_CLK * n_sm * sm_mhz * 1e6 / 1e9
+        sm_mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
         smem_peak, fp64_probe = P.ecmc.device_peaks()
+        # the configuration the ncu counters were taken in
+        captured = (persistent and tpc == 8 and descs is None and args.dir == "axis" and
+                    args.prec == 1 and int(g.get_param(E.PARAM_FRAME_MODE)) in (0, -1))
         cpu = None
         if not args.skip_cpu and descs is None:
             cpu = cpu_baseline(w, cells, ell, nm, args.cpu_seconds, melt_sweeps(args),
@@ -972,19 +1033,9 @@ def run_ours(args):
                                     "frame": kt.frame_ms / max(sweeps, 1),
                                     "chain": kt.phase_ms / max(sweeps, 1),
                                     "reduce": kt.other_ms / max(sweeps, 1)},
-            "roofline": {"kernel": "k_sweep_fused (persistent sweep kernel)" if persistent
-                         else "k_phase (chain kernel)", "bound": "alu",
-                         "achieved": achieved, "peak": fp64_peak, "unit": "GFLOP/s",
-                         "frac": achieved / fp64_peak,
-                         "traffic": (K_SWEEP_FUSED_DRAM_BYTES if persistent else None)
-                         if tpc == 8 and not descs and args.dir == "axis" else None,
-                         "pipe": "fp64", "fp64_ops_per_iteration": FP64_OPS_PER_ITERATION,
-                         "iterations_per_launch": iters / max(kt.phase_launches, 1),
-                         "launch_ms": phase_avg_ms,
-                         "peak_source": "2 FP64 lanes/clk/SM x %d SMs x %.0f MHz (unit counts)"
-                                        % (n_sm, sm_mhz),
-                         "fp64_probe_gflops": fp64_probe},
-            "smem_roofline": smem_roofline(w, descs, c, iters, value, args.prec, smem_peak),
+            "roofline": chain_roofline(w, descs, c, iters, kt, args.prec, smem_peak, persistent,
+                                       captured),
+            "fp64_pipe": fp64_pipe(iters, kt, n_sm, sm_mhz, fp64_probe, persistent, captured),
             "latency": latency_ceiling(g, descs, cells, c, kt, clk, sm_mhz),
             # per sweep: draws, binning, the persistent sweep kernel (or 4 x frame
             # builder + chain kernel), chunk sums, end of sweep
@@ -1004,23 +1055,65 @@ def run_ours(args):
     return 0
 
 
-def smem_roofline(w, descs, c, iters, value, prec, smem_peak):
-    """The chain loop against shared-memory bandwidth, counting ALGORITHMIC
-    bytes: an event must inspect the disks whose centres lie in the strip that
-    can hold the first hit, area 2 sigma (sigma + lambda0) with lambda0 the
-    measured mean free path, at 8 B (FP32 x, y) or 16 B (FP64) each, plus 16 B
-    to read and write the mover."""
-    if descs is not None or iters <= 0:
-        return None
+def smem_bytes_per_event(w, c, iters, prec):
+    """ALGORITHMIC shared-memory bytes per collision event: an event must
+    inspect the disks whose centres lie in the strip that can hold the first
+    hit, area 2 sigma (sigma + lambda0) with lambda0 the measured mean free
+    path, at 8 B (FP32 x, y) or 16 B (FP64) each, plus 16 B to read and write
+    the mover.  Returns (bytes, disks, lambda0)."""
     rho = w.N / (w.L * w.L)
     lam0 = c.sum_disp / iters
     disks = rho * 2.0 * (1.0 + lam0)
-    per = disks * (8.0 if prec else 16.0) + 16.0
-    achieved = value * per / 1e9
-    return {"bytes_per_event": per, "candidates_per_event": disks, "mean_free_path": lam0,
-            "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
-            "frac": achieved / smem_peak if smem_peak else None,
-            "peak_source": "ld.shared.v4 probe on this device"}
+    return disks * (8.0 if prec else 16.0) + 16.0, disks, lam0
+
+
+def chain_roofline(w, descs, c, iters, kt, prec, smem_peak, persistent, captured):
+    """The dominant kernel against shared-memory bandwidth: algorithmic bytes
+    per event x events per launch / the kernel's average launch time (CUDA
+    events on the launching stream) / the measured ld.shared.v4 peak.  traffic:
+    DRAM read + write per launch from the ncu capture, scaled to this workload
+    by the disks, when the kernel runs in the captured configuration."""
+    launches = max(kt.phase_launches, 1)
+    if descs is not None or iters <= 0 or kt.phase_launches <= 0:
+        return None
+    per, disks, lam0 = smem_bytes_per_event(w, c, iters, prec)
+    launch_ms = kt.phase_ms / launches
+    events_per_launch = c.events / launches
+    achieved = per * events_per_launch / (launch_ms * 1e-3) / 1e9
+    traffic = (FUSED_DRAM_BYTES_CAPTURE * w.N / FUSED_CAPTURE_N) if captured else None
+    return {"kernel": "k_sweep_fused (persistent sweep kernel)" if persistent
+                      else "k_phase (chain kernel)",
+            "bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
+            "frac": achieved / smem_peak if smem_peak else None, "traffic": traffic,
+            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch "
+                               "at N=%d, scaled by the disks" % FUSED_CAPTURE_N)
+                              if captured else None,
+            "bytes_per_event": per, "candidates_per_event": disks, "mean_free_path": lam0,
+            "events_per_launch": events_per_launch, "launch_ms": launch_ms,
+            "peak_source": "ld.shared.v4 probe on this device in this run (no shared-memory "
+                           "figure in MEASURED_PEAKS.json)"}
+
+
+def fp64_pipe(iters, kt, n_sm, sm_mhz, fp64_probe_gflops, persistent, captured):
+    """Use of the FP64 pipe by the dominant kernel, in warp-instructions: FP64
+    warp-instructions per launch (per iteration from the ncu capture, times
+    this run's iterations) x SM cycles one FP64 warp-instruction occupies
+    (from the FMA probe: SMs x clock / (FMA/s / 32 lanes)) / SM cycles of the
+    launch (SMs x clock x average launch time)."""
+    if not (persistent and captured) or kt.phase_launches <= 0 or not fp64_probe_gflops:
+        return None
+    launch_s = kt.phase_ms / kt.phase_launches * 1e-3
+    winst = FUSED_FP64_WINST_CAPTURE / FUSED_ITERATIONS_CAPTURE * iters / kt.phase_launches
+    clk = sm_mhz * 1e6
+    cyc_per_winst = n_sm * clk / (fp64_probe_gflops * 1e9 / 2.0 / 32.0)
+    sm_cycles = n_sm * clk * launch_s
+    return {"warp_instructions_per_launch": winst,
+            "warp_instructions_per_iteration": FUSED_FP64_WINST_CAPTURE / FUSED_ITERATIONS_CAPTURE,
+            "cycles_per_warp_instruction": cyc_per_winst, "sm_cycles_per_launch": sm_cycles,
+            "frac": winst * cyc_per_winst / sm_cycles,
+            "ncu_pipe_active_pct_at_capture": FUSED_NCU_FP64_PIPE_PCT,
+            "probe_fp64_gflops": fp64_probe_gflops,
+            "source": "FP64 warp-instructions per iteration from ncu at N=%d" % FUSED_CAPTURE_N}
 
 
 def latency_ceiling(g, descs, cells, c, kt, clk, sm_mhz):
@@ -1095,6 +1188,8 @@ def main():
         return run_dim3(args)
     if args.tau:
         return run_tau(args)
+    if args.gr:
+        return run_gr(args)
     return run_ours(args)
 
 

@@ -1,6 +1,7 @@
 """Host-side arithmetic of bench.py (no GPU): the contact-value fit of the
-pressure route, the shared-memory roofline's algorithmic bytes, the latency
-ceiling and the all-cores batch CPU baseline."""
+pressure route, the shared-memory roofline's algorithmic bytes, the FP64 pipe
+in warp-instructions, the latency ceiling and the all-cores batch CPU
+baseline."""
 import math
 from types import SimpleNamespace
 
@@ -19,15 +20,38 @@ def test_contact_value_recovers_a_quadratic_exactly():
 
 def test_smem_roofline_counts_the_strip_that_can_hold_the_first_hit():
     w = SimpleNamespace(N=1048576, L=W.box_side(1048576, 0.72))
-    c = SimpleNamespace(sum_disp=0.05 * 1000.0)
-    out = bench.smem_roofline(w, None, c, 1000, 1.0e9, 1, 40000.0)
+    c = SimpleNamespace(sum_disp=0.05 * 1000.0, events=900.0)
+    per, disks, lam0 = bench.smem_bytes_per_event(w, c, 1000, 1)
     rho = w.N / w.L**2
-    disks = rho * 2.0 * (1.0 + 0.05)
-    assert out["candidates_per_event"] == pytest.approx(disks)
-    assert out["bytes_per_event"] == pytest.approx(disks * 8.0 + 16.0)
-    assert out["achieved"] == pytest.approx(1.0e9 * out["bytes_per_event"] / 1e9)
+    assert lam0 == pytest.approx(0.05)
+    assert disks == pytest.approx(rho * 2.0 * (1.0 + 0.05))
+    assert per == pytest.approx(disks * 8.0 + 16.0)
+    assert bench.smem_bytes_per_event(w, c, 1000, 0)[0] == pytest.approx(disks * 16.0 + 16.0)
+    # the roofline divides the algorithmic bytes of one launch by that
+    # launch's average time (not by the step time)
+    kt = SimpleNamespace(phase_ms=3.0, phase_launches=3)
+    out = bench.chain_roofline(w, None, c, 1000, kt, 1, 40000.0, 1, True)
+    assert out["events_per_launch"] == pytest.approx(300.0)
+    assert out["launch_ms"] == pytest.approx(1.0)
+    assert out["achieved"] == pytest.approx(per * 300.0 / 1e-3 / 1e9)
     assert out["frac"] == pytest.approx(out["achieved"] / 40000.0)
-    assert bench.smem_roofline(w, [1], c, 1000, 1.0e9, 1, 40000.0) is None
+    assert out["bound"] == "smem" and out["unit"] == "GB/s"
+    assert out["traffic"] == pytest.approx(bench.FUSED_DRAM_BYTES_CAPTURE * w.N
+                                           / bench.FUSED_CAPTURE_N)
+    assert bench.chain_roofline(w, None, c, 1000, kt, 1, 40000.0, 1, False)["traffic"] is None
+    assert bench.chain_roofline(w, [1], c, 1000, kt, 1, 40000.0, 1, True) is None
+
+
+def test_fp64_pipe_counts_warp_instructions():
+    kt = SimpleNamespace(phase_ms=2.0, phase_launches=2)
+    iters = 2 * bench.FUSED_ITERATIONS_CAPTURE
+    out = bench.fp64_pipe(iters, kt, 152, 2000.0, 1024.0, 1, True)
+    winst = bench.FUSED_FP64_WINST_CAPTURE  # per launch: the captured count at these iterations
+    cyc = 152 * 2000e6 / (1024e9 / 64.0)
+    assert out["warp_instructions_per_launch"] == pytest.approx(winst)
+    assert out["cycles_per_warp_instruction"] == pytest.approx(cyc)
+    assert out["frac"] == pytest.approx(winst * cyc / (152 * 2000e6 * 1e-3))
+    assert bench.fp64_pipe(iters, kt, 152, 2000.0, 1024.0, 1, False) is None
 
 
 def test_latency_ceiling_arithmetic():
