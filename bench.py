@@ -487,7 +487,9 @@ def run_fig3(args):
                       "g_contact": contact_value(R, gm),
                       "g_first_bins": [round(float(v), 4) for v in gm[:12]],
                       "sweeps": per_batch * nbatch * 10,
-                      "rejected_fraction": c.rejected_chains / max(c.chains, 1)}
+                      "rejected_fraction": c.rejected_chains / max(c.chains, 1),
+                      "kernel": "sorted frames" if g.get_param(E.PARAM_STRIPES_KERNEL) == 1
+                                else "block-wide scan"}
                 if rule == "reflect":
                     pt["betaP_sigma2_chain"] = g.pressure()[0]
                 pts.append(pt)
@@ -627,7 +629,9 @@ def run_stripes(args):
                       "events_per_s": c.events / (ms * 1e-3),
                       "sweeps_per_s": args.steps / (ms * 1e-3), "ms_per_sweep": ms / args.steps,
                       "events_per_sweep": c.events / args.steps,
-                      "rejected_fraction": c.rejected_chains / max(c.chains, 1)}
+                      "rejected_fraction": c.rejected_chains / max(c.chains, 1),
+                      "kernel": "sorted frames" if g.get_param(E.PARAM_STRIPES_KERNEL) == 1
+                                else "block-wide scan"}
                 pts.append(pt)
                 print(json.dumps(pt), flush=True)
                 g.set_stream(None)

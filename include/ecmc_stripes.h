@@ -60,6 +60,21 @@ typedef struct ecmc_stripes_ctx* ecmc_stripes_t;
 #define ECMC_STRIPES_PARAM_REPLICA 4  /* Philox key word 1, integer in [0, 9e15] (default 0) */
 /* ECMC_BOUNDARY_REJECT (default) or ECMC_BOUNDARY_REFLECT. */
 #define ECMC_STRIPES_PARAM_BOUNDARY 21
+/* Start lists (Sec. 3.4 step 5, Fig. 3): ECMC_LIST_WITH_REPL (default), each
+ * start disk drawn among the stripe's members; ECMC_LIST_WITHOUT_REPL, the
+ * negative control: the first start as drawn, then a Fisher-Yates shuffle of
+ * the other members with Philox draws, cycled.  The shuffled list needs the
+ * sorted-frame kernel (ECMC_ERR_UNSUPPORTED from ecmc_stripes_sweep when a
+ * stripe's frame does not fit in shared memory). */
+#define ECMC_STRIPES_PARAM_LIST_MODE 19
+/* Chain kernel: 1 (default) = the sorted-frame kernel when a stripe's frame
+ * fits in shared memory (one warp per stripe; strips of width sigma/2 across
+ * the axis, each sorted along it once per phase -- two disks of one strip
+ * cannot pass each other -- and per contact only a short window ahead of the
+ * mover in the five strips within sigma tested); 0 = the block-wide scan of
+ * the whole frame in global memory.  Reading it returns the kernel the next
+ * sweep uses.  Both give the same trajectories bit for bit. */
+#define ECMC_STRIPES_PARAM_KERNEL 24
 
 /* N disks of diameter sigma in a periodic square of side L, `stripes`
  * stripes (even, >= 2, L / stripes > sigma), chains of total displacement

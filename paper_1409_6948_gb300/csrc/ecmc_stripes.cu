@@ -47,6 +47,11 @@ struct GeomS {
   int S, n_m, reject;
   uint64_t seed, replica;
   int cap_obj;  // frame objects per stripe (packing bound of the band)
+  int cap_mem;  // members per stripe (packing bound of the stripe itself)
+  int list_mode;  // 0 start disks drawn with replacement, 1 shuffled list of distinct members
+  // sorted-frame kernel: strips of width sw across the axis, nstrip of them
+  double sw, inv_sw;
+  int nstrip;
 };
 
 struct StateS {
@@ -342,6 +347,533 @@ __global__ void __launch_bounds__(kThreads) ks_phase(
   }
 }
 
+// ---- the sorted-frame kernel ----------------------------------------------
+// One block per stripe builds the frame, then its first warp runs the chains
+// with the frame in shared memory and no block barrier per event.
+//
+// Strips.  The frame is cut across the axis into strips of width sw = sigma/2
+// (1 + 2^-30).  Two objects of one strip are less than sigma apart across,
+// so a move along the axis can never carry one past the other: the cyclic
+// order along the axis within a strip holds for the whole phase.  Each strip
+// is sorted once, by (U, key), and kept as a rotated sorted array: logical
+// index i sits at sstart[q] + (rot[q] + i) mod n_q, ascending in U.  A member
+// that wraps round the periodic axis was the last (or first) of its strip,
+// and becomes the first (or last): rot[q] moves by one.
+//
+// Search.  An object can be hit only if it lies within sigma across, that is
+// in the strips q_m - 2 .. q_m + 2 (sw >= sigma/2), and ahead along d.  In each
+// strip the lanes find the first object strictly ahead (a 6-ary search over
+// the logical order), then test a window of six objects in the order the
+// mover meets them, with the oracle's FP64 expressions.  The forward distance
+// b only grows along that order, and s >= b - sigma, so a strip is finished
+// once its last tested object has b - sigma above min(r, best s); otherwise
+// the next six are tested.  The first hit is the minimum of (s, key) over
+// the warp: the same object, distance and event as the full scan.
+constexpr int kSortThreads = 512;
+constexpr int kLanesPerStrip = 6;
+
+__device__ __forceinline__ int strip_of_v(const GeomS& g, double v) {
+  int q = (int)((v + g.sigma) * g.inv_sw);
+  return q < 0 ? 0 : (q >= g.nstrip ? g.nstrip - 1 : q);
+}
+
+__host__ __device__ inline size_t sorted_smem_bytes(int cap_obj, int cap_mem, int nstrip) {
+  return (sizeof(double) * 2 + sizeof(int) * 2) * (size_t)cap_obj + sizeof(int) * (size_t)cap_mem +
+         sizeof(int) * (size_t)(3 * nstrip + 8) + ((size_t)cap_obj + 16);
+}
+
+__global__ void __launch_bounds__(kSortThreads) ks_phase_sorted(
+    GeomS g, const StateS* __restrict__ st, int ci, double* __restrict__ px,
+    double* __restrict__ py, const int* __restrict__ stripe_of, double* __restrict__ fU,
+    double* __restrict__ fV, long long* __restrict__ fkey, int* __restrict__ fid,
+    double* __restrict__ fU0, int* __restrict__ flist, StripeS* __restrict__ stats,
+    int* __restrict__ recs, int* err) {
+  extern __shared__ __align__(16) unsigned char ssm[];
+  __shared__ int wcnt[kSortThreads / 32];
+  __shared__ int sm_over, sm_n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned FULL = 0xffffffffu;
+  const StateS s = *st;
+  const int colour = ci == 0 ? s.first : 1 - s.first;
+  const int a = blockIdx.x;
+  const int k = colour + 2 * a;
+  double* along = s.axis ? py : px;
+  const double* across = s.axis ? px : py;
+  const double L = g.L, sigma = g.sigma, sig2 = g.sig2;
+  const float g_sigf = (float)sigma;
+  const double origin = s.shift + (double)k * g.w;
+  const size_t fb = (size_t)a * (size_t)g.cap_obj;
+  double* gU = fU + fb;
+  double* gV = fV + fb;
+  long long* gK = fkey + fb;
+  int* gO = fid + fb;
+  double* U0 = fU0 + (size_t)a * (size_t)g.cap_mem;
+  int* plist = flist + (size_t)a * (size_t)g.cap_mem;
+
+  // shared layout: U, V (double), key, orig (int) per object; the member map;
+  // strip starts, rotations and their copy at a chain start
+  double* U = (double*)ssm;
+  double* V = U + g.cap_obj;
+  int* key = (int*)(V + g.cap_obj);
+  int* orig = key + g.cap_obj;
+  int* mem_g = orig + g.cap_obj;
+  int* sstart = mem_g + g.cap_mem;   // nstrip + 1
+  int* rot = sstart + g.nstrip + 1;  // nstrip
+  int* fill = rot + g.nstrip;        // nstrip (build), then rot at the chain start
+  unsigned char* sq = (unsigned char*)(fill + g.nstrip);  // strip of every object
+
+  if (tid == 0) sm_over = 0;
+  for (int q = tid; q < g.nstrip; q += kSortThreads) fill[q] = 0;
+  __syncthreads();
+
+  // frame, part 1: the members in ascending id (unsorted, in global scratch)
+  int n = 0;
+  for (int64_t i0 = 0; i0 < g.N; i0 += kSortThreads) {
+    const int64_t i = i0 + tid;
+    const bool mem = i < g.N && stripe_of[i] == k;
+    const unsigned bal = __ballot_sync(FULL, mem);
+    if (lane == 0) wcnt[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int q = 0; q < kSortThreads / 32; ++q) {
+      before += q < warp ? wcnt[q] : 0;
+      total += wcnt[q];
+    }
+    const int slot = n + before + __popc(bal & ((1u << lane) - 1u));
+    __syncthreads();
+    if (mem) {
+      if (slot < g.cap_mem) {
+        gU[slot] = along[i];
+        gV[slot] = wrap_half(across[i] - origin, L);
+        gK[slot] = (long long)i * 3 + 1;
+      } else {
+        sm_over = 1;
+      }
+    }
+    n += total;
+  }
+  const int n_mem = n;
+  __syncthreads();
+  // frame, part 2: images across (-L, 0, +L) of the other disks within sigma
+  // of the band (any order: the strips are sorted by (U, key) below)
+  if (tid == 0) sm_n = n_mem;
+  __syncthreads();
+  for (int64_t i = tid; i < g.N; i += kSortThreads) {
+    if (stripe_of[i] == k) continue;
+    const double v0 = wrap_half(across[i] - origin, L);
+    for (int im = -1; im <= 1; ++im) {
+      const double v = im == 0 ? v0 : (im > 0 ? v0 + L : v0 - L);
+      if (!(v > -sigma && v < g.w + sigma)) continue;
+      const int slot = atomicAdd(&sm_n, 1);
+      if (slot < g.cap_obj) {
+        gU[slot] = along[i];
+        gV[slot] = v;
+        gK[slot] = (long long)i * 3 + (im + 1);
+      } else {
+        sm_over = 1;
+      }
+    }
+  }
+  __syncthreads();
+  const bool over = sm_over != 0;
+  n = over ? 0 : sm_n;
+  if (over && tid == 0) atomicCAS(err, kOk, kCapacity);
+
+  // strips: counts, starts, then each object's rank within its strip by
+  // (U, key); the sorted frame goes through global scratch into shared memory
+  for (int o = tid; o < n; o += kSortThreads) atomicAdd(&fill[strip_of_v(g, gV[o])], 1);
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    for (int q = 0; q < g.nstrip; ++q) {
+      sstart[q] = acc;
+      acc += fill[q];
+      fill[q] = 0;
+      rot[q] = 0;
+    }
+    sstart[g.nstrip] = acc;
+  }
+  __syncthreads();
+  for (int o = tid; o < n; o += kSortThreads) {
+    const int q = strip_of_v(g, gV[o]);
+    const int p = sstart[q] + atomicAdd(&fill[q], 1);
+    U[p] = gU[o];
+    V[p] = gV[o];
+    key[p] = (int)gK[o];
+    orig[p] = o;
+  }
+  __syncthreads();
+  for (int q = 0; q < g.nstrip; ++q) {
+    const int b0 = sstart[q], b1 = sstart[q + 1];
+    for (int p = b0 + tid; p < b1; p += kSortThreads) {
+      const double up = U[p];
+      const int kp = key[p];
+      int r = 0;
+      for (int p2 = b0; p2 < b1; ++p2) r += (U[p2] < up || (U[p2] == up && key[p2] < kp));
+      const int f = b0 + r;
+      gU[f] = up;
+      gV[f] = V[p];
+      gK[f] = kp;
+      gO[f] = orig[p];
+    }
+  }
+  __syncthreads();
+  for (int f = tid; f < n; f += kSortThreads) {
+    U[f] = gU[f];
+    V[f] = gV[f];
+    key[f] = (int)gK[f];
+    orig[f] = gO[f];
+    sq[f] = (unsigned char)strip_of_v(g, gV[f]);
+    if (gO[f] < n_mem) mem_g[gO[f]] = f;
+  }
+  __syncthreads();
+
+  if (warp == 0) {
+    double sum_b = 0.0;
+    long long events = 0, lifts = 0, frozen = 0, rejected = 0;
+    int chains = 0, accepted = 0;
+    const int slot = lane / kLanesPerStrip, li = lane - slot * kLanesPerStrip;  // slot 5: idle
+    const double INF = __longlong_as_double(0x7ff0000000000000ll);
+    // shuffled list of distinct members (negative control), as the oracle
+    // draws it: entry 0 as drawn, then Fisher-Yates on entries 1..
+    if (g.list_mode == 1 && n_mem > 0 && !over && lane == 0) {
+      const U64x4 v0 = philox((uint64_t)s.t, ecmc::kPurposeChain, (uint64_t)k, 0, g.seed,
+                              g.replica);
+      const int fst = (int)below_n(v0.v[0], (uint64_t)n_mem);
+      int nr = 0;
+      plist[nr++] = fst;
+      for (int q = 0; q < n_mem; ++q)
+        if (q != fst) plist[nr++] = q;
+      U64x4 u;
+      int cur = -1;
+      for (int i = n_mem - 1; i >= 2; --i) {
+        if ((i >> 2) != cur) {
+          cur = i >> 2;
+          u = philox((uint64_t)s.t, ecmc::kPurposeShuffle, (uint64_t)k, (uint64_t)cur, g.seed,
+                     g.replica);
+        }
+        const int j = 1 + (int)below_n(u.v[i & 3], (uint64_t)i);
+        const int tmp = plist[i];
+        plist[i] = plist[j];
+        plist[j] = tmp;
+      }
+    }
+    __syncwarp();
+    for (int c = 0; c < g.n_m; ++c) {
+      int* rec = recs ? recs + ((size_t)k * g.n_m + c) * 4 : nullptr;
+      if (over || n_mem == 0) {
+        if (lane == 0 && rec) {
+          rec[0] = -1;
+          rec[1] = -1;
+          rec[2] = 0;
+          rec[3] = 0;
+        }
+        continue;
+      }
+      const U64x4 v = philox((uint64_t)s.t, ecmc::kPurposeChain, (uint64_t)k, (uint64_t)c,
+                             g.seed, g.replica);
+      const int q0 = g.list_mode == 1 ? plist[c % n_mem] : (int)below_n(v.v[0], (uint64_t)n_mem);
+      int m = mem_g[q0];
+      int dsg = (v.v[1] >> 63) ? -1 : 1;
+      double d = dsg < 0 ? -1.0 : 1.0;
+      double r = g.ell, chain_b = 0.0;
+      long long nev = 0;
+      if (lane == 0 && rec) rec[0] = key[m] / 3;
+      if (g.reject) {
+        for (int q = lane; q < n_mem; q += 32) U0[q] = U[mem_g[q]];
+        for (int q = lane; q < g.nstrip; q += 32) fill[q] = rot[q];
+      }
+      __syncwarp();
+      int done = 0;  // 1 budget used up, 2 rejected, 3 contact cap
+      for (long long iter = 0;; ++iter) {
+        const double Um = U[m], Vm = V[m];
+        const long long kUm = ecmc::dkey(Um);
+        const int qm = sq[m];
+        // this lane's strip, its size and the first object strictly ahead
+        const int q = qm - 2 + slot;
+        const bool sv = slot < 5 && q >= 0 && q < g.nstrip;
+        const int b0 = sv ? sstart[q] : 0;
+        const int nq = sv ? sstart[q + 1] - b0 : 0;
+        const int rq = sv ? rot[q] : 0;
+        // first logical index with U > Um (d = +1) or U >= Um (d = -1), by a
+        // 6-ary search over [lo, hi): the predicate is false ... false true ...
+        // true (compared as order-preserving integers)
+        int lo = 0, hi = nq;
+        while (__any_sync(FULL, hi - lo > 0)) {
+          const int len = hi - lo;
+          const int step = (len + kLanesPerStrip) / (kLanesPerStrip + 1);  // >= 1
+          const int probe = lo + (li + 1) * step - 1;
+          bool pred = false;
+          const bool act = sv && len > 0 && probe < hi;
+          if (act) {
+            int pi = rq + probe;
+            pi -= pi >= nq ? nq : 0;
+            const long long ku = ecmc::dkey(U[b0 + pi]);
+            pred = dsg > 0 ? (ku > kUm) : (ku >= kUm);
+          }
+          const unsigned bt = __ballot_sync(FULL, act && pred);
+          const unsigned bf = __ballot_sync(FULL, act && !pred);
+          const unsigned gm = ((1u << kLanesPerStrip) - 1u) << (slot * kLanesPerStrip);
+          const unsigned t_g = bt & gm, f_g = bf & gm;
+          if (sv && len > 0) {
+            // the true probes are a suffix of the probes: nf false probes put
+            // the answer in [lo + nf step, first true probe] (or above the
+            // last probe); the interval shrinks every round
+            const int nf = __popc(f_g);
+            const int nlo = lo + nf * step;
+            const int nhi = t_g ? lo + (nf + 1) * step - 1 : hi;
+            lo = nlo;
+            hi = nhi < nlo ? nlo : nhi;
+          }
+        }
+        // logical start of the scan: the first object ahead along d
+        int c0 = 0;
+        if (sv && nq > 0) c0 = dsg > 0 ? (lo < nq ? lo : 0) : (lo > 0 ? lo - 1 : nq - 1);
+        auto object_at = [&](int off) {
+          int lidx = dsg > 0 ? c0 + off : c0 - off;
+          lidx += lidx >= nq ? -nq : (lidx < 0 ? nq : 0);
+          int pi = rq + lidx;
+          pi -= pi >= nq ? nq : 0;
+          return b0 + pi;
+        };
+        // a strip is finished once its last tested object of window wi is too
+        // far along to be hit before lim, or the window reached its end
+        auto still_open = [&](int wi, double bl, double lim) {
+          const int last = (nq - wi * kLanesPerStrip) < kLanesPerStrip
+                               ? (nq - wi * kLanesPerStrip) - 1
+                               : kLanesPerStrip - 1;
+          const int src = slot * kLanesPerStrip + (last < 0 ? 0 : last);
+          const double blast = __shfl_sync(FULL, bl, src < 32 ? src : 31);
+          const bool end_of_strip = (wi + 1) * kLanesPerStrip >= nq;
+          return sv && nq > 0 && !end_of_strip &&
+                 !(blast - sigma * (1.0 + 1e-12) > lim + 4e-16 * L);
+        };
+
+        // window 0, screened: b, c^2 and x = sigma^2 - c^2 exactly as the
+        // oracle forms them in FP64 (so the hit decision c^2 < sigma^2 is
+        // exact; multiplying by d = +-1 is a sign flip, comparisons of these
+        // values run on the integer pipes), s estimated in FP32:
+        //   x truncated to FP32, then sqrtf: |root - sqrt(x)| <= 2^-23 sigma + 2^-63,
+        //   b32 = b truncated to FP32: |b32 - b| <= 2^-23 b,
+        //   b32 - root rounded in FP32: 2^-24 (b + sigma),
+        // and the oracle's own rounding of b - sqrt(x): 2^-53 (b + sigma);
+        // mg(b) = 2^-21 (b + sigma) + 2^-60 covers that with room to spare
+        double bs = INF, bb = 0.0;
+        int bk = INT_MAX, bj = -1;
+        double bl0 = 0.0, b_c = 0.0, x_c = 0.0;
+        float lo_c = __int_as_float(0x7f800000), hf = lo_c;
+        int j_c = -1;
+        bool cand = false;
+        if (sv && li < nq) {
+          const int j = object_at(li);
+          double bj0 = ecmc::flip_if(U[j] - Um, dsg < 0);
+          if (ecmc::dkey(bj0) <= 0) bj0 += L;  // ahead round the periodic stripe
+          bl0 = bj0;
+          if (j != m) {
+            const double cc = V[j] - Vm;
+            const double c2 = cc * cc;
+            if (ecmc::lt_nn(c2, sig2)) {
+              const double x = sig2 - c2;
+              const float b32 = ecmc::to_float_trunc(bj0);
+              const float se = b32 - sqrtf(ecmc::to_float_trunc(x));
+              const float mgf = (b32 + g_sigf) * 0x1p-20f + 0x1p-60f;
+              const float l = se - mgf, h = se + mgf;
+              lo_c = l < 0.0f ? 0.0f : l;
+              hf = h < 0.0f ? 0.0f : h;
+              cand = true;
+              b_c = bj0;
+              x_c = x;
+              j_c = j;
+            }
+          }
+        }
+        // the smallest upper bound over the warp (non-negative floats order
+        // as their bit patterns)
+        const float Hf = __uint_as_float(__reduce_min_sync(FULL, __float_as_uint(hf)));
+        const float rf = ecmc::to_float_up_nn(r);
+        const float limf = rf < Hf ? rf : Hf;
+        const double lim0 = (double)limf;
+        if (!__any_sync(FULL, still_open(0, bl0, lim0))) {
+          // every strip is finished after window 0: the first hit is among
+          // the candidates whose lower bound reaches min(r, Hf); evaluate
+          // those with the oracle's expression
+          const bool need = cand && lo_c <= limf;
+          const unsigned nb = __ballot_sync(FULL, need);
+          if (need) {
+            bs = b_c - sqrt(x_c);
+            if (bs < 0.0) bs = 0.0;
+            bk = key[j_c];
+            bj = j_c;
+            bb = b_c;
+          }
+          if (__popc(nb) == 1) {
+            const int w = __ffs(nb) - 1;
+            bs = __shfl_sync(FULL, bs, w);
+            bk = __shfl_sync(FULL, bk, w);
+            bj = __shfl_sync(FULL, bj, w);
+            bb = __shfl_sync(FULL, bb, w);
+          } else if (nb != 0) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              const double s2 = __shfl_xor_sync(FULL, bs, o);
+              const int k2 = __shfl_xor_sync(FULL, bk, o);
+              const int j2 = __shfl_xor_sync(FULL, bj, o);
+              const double b2 = __shfl_xor_sync(FULL, bb, o);
+              if (s2 < bs || (s2 == bs && k2 < bk)) {
+                bs = s2;
+                bk = k2;
+                bj = j2;
+                bb = b2;
+              }
+            }
+          }
+        } else {
+          // some strip needs more than six objects (long free flights): the
+          // exact search over windows of six, every candidate in FP64
+          bool open = sv && nq > 0;
+          for (int wi = 0; __any_sync(FULL, open); ++wi) {
+            const int off = wi * kLanesPerStrip + li;
+            const bool act = open && off < nq;
+            double bl = 0.0;
+            if (act) {
+              const int j = object_at(off);
+              double bj0 = d * (U[j] - Um);
+              if (bj0 <= 0.0) bj0 += L;
+              bl = bj0;
+              if (j != m) {
+                const double cc = V[j] - Vm;
+                const double c2 = cc * cc;
+                if (c2 < sig2) {
+                  double sj = bj0 - sqrt(sig2 - c2);
+                  if (sj < 0.0) sj = 0.0;
+                  const int kj = key[j];
+                  if (sj < bs || (sj == bs && kj < bk)) {
+                    bs = sj;
+                    bk = kj;
+                    bj = j;
+                    bb = bj0;
+                  }
+                }
+              }
+            }
+            double ws = bs;
+            int wk = bk;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              const double s2 = __shfl_xor_sync(FULL, ws, o);
+              const int k2 = __shfl_xor_sync(FULL, wk, o);
+              if (s2 < ws || (s2 == ws && k2 < wk)) {
+                ws = s2;
+                wk = k2;
+              }
+            }
+            const double lim = r < ws ? r : ws;
+            const bool keep = still_open(wi, bl, lim);
+            open = open && keep;
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const double s2 = __shfl_xor_sync(FULL, bs, o);
+            const int k2 = __shfl_xor_sync(FULL, bk, o);
+            const int j2 = __shfl_xor_sync(FULL, bj, o);
+            const double b2 = __shfl_xor_sync(FULL, bb, o);
+            if (s2 < bs || (s2 == bs && k2 < bk)) {
+              bs = s2;
+              bk = k2;
+              bj = j2;
+              bb = b2;
+            }
+          }
+        }
+        if (iter >= kMaxEvents) {
+          if (lane == 0) atomicCAS(err, kOk, kChainCap);
+          done = 3;
+          break;
+        }
+        if (r <= bs) {  // budget used up: the chain ends
+          const double x = Um + d * r;
+          if (lane == 0) {
+            U[m] = wrap_along(x, L);
+            if (x >= L || x < 0.0) {
+              const int nm_ = sstart[qm + 1] - sstart[qm];
+              int rr = rot[qm] + (dsg > 0 ? nm_ - 1 : 1);
+              rr -= rr >= nm_ ? nm_ : 0;
+              rot[qm] = rr;
+            }
+          }
+          sum_b += chain_b;
+          done = 1;
+          break;
+        }
+        nev++;
+        events++;
+        const bool is_member = orig[bj] < n_mem;
+        if (!is_member && g.reject) {  // frozen disk: the chain is rejected
+          frozen++;
+          rejected++;
+          done = 2;
+          break;
+        }
+        // the move, with the wrap round the periodic axis: bs <= b <= L, so x
+        // lies in (-L, 2L), where wrap_along is x - L (exact) or x + L
+        const double x = Um + d * bs;
+        const bool wrapped = (x >= L) || (x < 0.0);
+        if (lane == 0) {
+          U[m] = x >= L ? x - L : (x < 0.0 ? x + L : x);
+          if (wrapped) {
+            const int nm_ = sstart[qm + 1] - sstart[qm];
+            int rr = rot[qm] + (dsg > 0 ? nm_ - 1 : 1);
+            rr -= rr >= nm_ ? nm_ : 0;
+            rot[qm] = rr;
+          }
+        }
+        __syncwarp();
+        r = r - bs;
+        chain_b += bb - bs;
+        if (is_member) {  // lift
+          lifts++;
+          m = bj;
+        } else {          // frozen disk, reflecting rule: back along the axis
+          frozen++;
+          dsg = -dsg;
+          d = -d;
+        }
+      }
+      if (done == 2) {
+        for (int q = lane; q < n_mem; q += 32) U[mem_g[q]] = U0[q];
+        for (int q = lane; q < g.nstrip; q += 32) rot[q] = fill[q];
+      }
+      __syncwarp();
+      chains++;
+      accepted += done == 2 ? 0 : 1;
+      if (lane == 0 && rec) {
+        rec[1] = key[m] / 3;
+        rec[2] = (int)nev;
+        rec[3] = 0;
+      }
+    }
+    if (lane == 0) {
+      StripeS o;
+      o.sum_b = sum_b;
+      o.events = events;
+      o.lifts = lifts;
+      o.frozen = frozen;
+      o.rejected = rejected;
+      o.chains = chains;
+      o.accepted = accepted;
+      o.n_mem = over ? 0 : n_mem;
+      stats[k] = o;
+    }
+  }
+  __syncthreads();
+  // write back the members' coordinate along the axis
+  if (!over)
+    for (int q = tid; q < n_mem; q += kSortThreads) {
+      const int f = mem_g[q];
+      along[key[f] / 3] = U[f];
+    }
+}
+
 __global__ void ks_end(GeomS g, StateS* st, const StripeS* __restrict__ stats, TotalsS* tot,
                        double* history, int64_t* hist_len) {
   if (threadIdx.x != 0) return;
@@ -407,8 +939,12 @@ struct ecmc_stripes_ctx {
   TotalsS* tot = nullptr;
   double* history = nullptr;
   int64_t* hist_len = nullptr;
+  int* flist = nullptr;  // shuffled start lists, cap_mem per active stripe
   int64_t t_host = 0;
   bool valid = false;
+  int kernel_param = 1;   // 1 sorted frames when they fit, 0 block-wide scan
+  size_t sorted_smem = 0;
+  bool sorted_ok = false; // the sorted frame fits in shared memory
 };
 
 namespace {
@@ -440,6 +976,15 @@ int64_t frame_bound(double w, double L, double sigma) {
   return (int64_t)std::floor(b) + 2;
 }
 
+// Members of one stripe: centres in a band of width w, disks of radius
+// sigma / 2 in a band of width w + sigma: at most 4 (w + sigma) L / (pi sigma^2).
+int64_t member_bound(double w, double L, double sigma) {
+  const double b = 4.0 * (w + sigma) * L / (M_PI * sigma * sigma);
+  return (int64_t)std::floor(b) + 2;
+}
+
+bool use_sorted(const ecmc_stripes_ctx* h) { return h->kernel_param == 1 && h->sorted_ok; }
+
 int checks(ecmc_stripes_ctx* h) {
   int e = 0;
   CKS(cudaMemcpyAsync(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -460,10 +1005,19 @@ int enqueue_sweep(ecmc_stripes_ctx* h, bool records) {
   const unsigned nb = (unsigned)((g.N + 255) / 256);
   ks_begin<<<1, 32, 0, h->stream>>>(g, h->st);
   ks_bin<<<nb, 256, 0, h->stream>>>(g, h->st, h->px, h->py, h->stripe_of);
-  for (int ci = 0; ci < 2; ++ci)
-    ks_phase<<<(unsigned)(g.S / 2), kThreads, 0, h->stream>>>(
-        g, h->st, ci, h->px, h->py, h->stripe_of, h->fU, h->fV, h->fkey, h->fid, h->fU0,
-        h->stats, records ? h->recs : nullptr, h->err);
+  if (g.list_mode == 1 && !use_sorted(h))
+    return fails(ECMC_ERR_UNSUPPORTED,
+                 "shuffled start lists need the sorted-frame kernel, whose frame does not fit");
+  for (int ci = 0; ci < 2; ++ci) {
+    if (use_sorted(h))
+      ks_phase_sorted<<<(unsigned)(g.S / 2), kSortThreads, h->sorted_smem, h->stream>>>(
+          g, h->st, ci, h->px, h->py, h->stripe_of, h->fU, h->fV, h->fkey, h->fid, h->fU0,
+          h->flist, h->stats, records ? h->recs : nullptr, h->err);
+    else
+      ks_phase<<<(unsigned)(g.S / 2), kThreads, 0, h->stream>>>(
+          g, h->st, ci, h->px, h->py, h->stripe_of, h->fU, h->fV, h->fkey, h->fid, h->fU0,
+          h->stats, records ? h->recs : nullptr, h->err);
+  }
   ks_end<<<1, 32, 0, h->stream>>>(g, h->st, h->stats, h->tot, h->history, h->hist_len);
   CKS(cudaGetLastError());
   return ECMC_OK;
@@ -504,6 +1058,7 @@ void frees(ecmc_stripes_ctx* h) {
   cudaFree(h->tot);
   cudaFree(h->history);
   cudaFree(h->hist_len);
+  cudaFree(h->flist);
   if (h->own) cudaStreamDestroy(h->own);
 }
 
@@ -551,6 +1106,26 @@ int ecmc_stripes_create(ecmc_stripes_t* out, int64_t N, double L, double sigma, 
   g.seed = seed;
   g.replica = 0;
   g.cap_obj = (int)cap;
+  const int64_t capm = member_bound(w, L, sigma);
+  g.cap_mem = (int)(capm < cap ? capm : cap);
+  g.list_mode = 0;
+  g.sw = 0.5 * sigma * (1.0 + std::ldexp(1.0, -30));
+  g.inv_sw = 1.0 / g.sw;
+  g.nstrip = (int)std::ceil((w + 2.0 * sigma) / g.sw) + 2;
+  h->sorted_smem = sorted_smem_bytes(g.cap_obj, g.cap_mem, g.nstrip);
+  {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    h->sorted_ok = cudaGetDevice(&dev) == cudaSuccess &&
+                   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                          dev) == cudaSuccess &&
+                   cudaFuncGetAttributes(&fa, ks_phase_sorted) == cudaSuccess &&
+                   h->sorted_smem + fa.sharedSizeBytes <= (size_t)optin &&
+                   cudaFuncSetAttribute(ks_phase_sorted,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)h->sorted_smem) == cudaSuccess;
+    cudaGetLastError();
+  }
   if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess) {
     delete h;
     return fails(ECMC_ERR_CUDA, "stream creation failed");
@@ -571,7 +1146,9 @@ int ecmc_stripes_create(ecmc_stripes_t* out, int64_t N, double L, double sigma, 
       cudaMalloc(&h->st, sizeof(StateS)) != cudaSuccess ||
       cudaMalloc(&h->tot, sizeof(TotalsS)) != cudaSuccess ||
       cudaMalloc(&h->history, sizeof(double) * 2 * kHistoryCap) != cudaSuccess ||
-      cudaMalloc(&h->hist_len, sizeof(int64_t)) != cudaSuccess) {
+      cudaMalloc(&h->hist_len, sizeof(int64_t)) != cudaSuccess ||
+      cudaMalloc(&h->flist, sizeof(int) * (size_t)(stripes / 2) * (size_t)g.cap_mem) !=
+          cudaSuccess) {
     cudaGetLastError();
     frees(h);
     delete h;
@@ -625,6 +1202,15 @@ int ecmc_stripes_set_param(ecmc_stripes_t h, int key, double v) {
         return fails(ECMC_ERR_ARG, "boundary must be ECMC_BOUNDARY_REFLECT or _REJECT");
       h->g.reject = v == (double)ECMC_BOUNDARY_REJECT ? 1 : 0;
       return ECMC_OK;
+    case ECMC_STRIPES_PARAM_LIST_MODE:
+      if (v != (double)ECMC_LIST_WITH_REPL && v != (double)ECMC_LIST_WITHOUT_REPL)
+        return fails(ECMC_ERR_ARG, "list mode must be ECMC_LIST_WITH_REPL or _WITHOUT_REPL");
+      h->g.list_mode = v == (double)ECMC_LIST_WITHOUT_REPL ? 1 : 0;
+      return ECMC_OK;
+    case ECMC_STRIPES_PARAM_KERNEL:
+      if (v != 0.0 && v != 1.0) return fails(ECMC_ERR_ARG, "kernel must be 0 or 1");
+      h->kernel_param = (int)v;
+      return ECMC_OK;
     default:
       return fails(ECMC_ERR_ARG, "unknown parameter %d", key);
   }
@@ -638,6 +1224,8 @@ int ecmc_stripes_get_param(ecmc_stripes_t h, int key, double* v) {
     case ECMC_STRIPES_PARAM_BOUNDARY:
       *v = h->g.reject ? ECMC_BOUNDARY_REJECT : ECMC_BOUNDARY_REFLECT;
       return ECMC_OK;
+    case ECMC_STRIPES_PARAM_LIST_MODE: *v = h->g.list_mode; return ECMC_OK;
+    case ECMC_STRIPES_PARAM_KERNEL: *v = use_sorted(h) ? 1.0 : 0.0; return ECMC_OK;
     default: return fails(ECMC_ERR_ARG, "unknown parameter %d", key);
   }
 }

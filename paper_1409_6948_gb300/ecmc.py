@@ -546,6 +546,8 @@ class Ecmc3:
 PARAM_STRIPES_N_CHAINS = 1
 PARAM_STRIPES_REPLICA = 4
 PARAM_STRIPES_BOUNDARY = 21
+PARAM_STRIPES_LIST_MODE = 19
+PARAM_STRIPES_KERNEL = 24
 
 
 class EcmcStripes:

@@ -7,9 +7,11 @@ exactly, positions to 1e-12 relative (identical in practice) after every
 sweep, the counters exactly and the pressure sums to 1e-11.  Cases: two
 stripes (the two neighbours of a stripe coincide and a frozen disk can enter
 the band twice), several stripe counts for both boundary rules, a ragged
-N = 900, a sparse system with empty stripes, and the Fig. 3 system
-N = 256^2 at eta = 0.708.  Then the low-density pressure of the reflecting
-rule against the virial series.
+N = 900, a sparse system with empty stripes, chains much longer than the box
+(movers wrap round the periodic axis many times), shuffled start lists, and
+the Fig. 3 system N = 256^2 at eta = 0.708 -- each with the sorted-frame
+kernel and with the block-wide scan.  Then the low-density pressure of the
+reflecting rule against the virial series.
 """
 import math
 
@@ -34,13 +36,17 @@ REL = 1e-12
 REJECT, REFLECT = oracle.BOUNDARY_REJECT, oracle.BOUNDARY_REFLECT
 
 
-def make(N, eta, S, ell, nm, seed, boundary, replica=0):
+def make(N, eta, S, ell, nm, seed, boundary, replica=0, kernel=1, list_mode=0):
     L = W.box_side(N, eta)
     g = P.EcmcStripes(N, L, 1.0, S, ell, seed)
     g.set_param(E.PARAM_STRIPES_N_CHAINS, nm)
     g.set_param(E.PARAM_STRIPES_BOUNDARY, boundary)
     g.set_param(E.PARAM_STRIPES_REPLICA, replica)
-    p = oracle.make_params(N, L, 1.0, S, S, ell, nm, seed, replica, boundary=boundary)
+    g.set_param(E.PARAM_STRIPES_KERNEL, kernel)
+    g.set_param(E.PARAM_STRIPES_LIST_MODE, list_mode)
+    assert g.get_param(E.PARAM_STRIPES_KERNEL) == kernel
+    p = oracle.make_params(N, L, 1.0, S, S, ell, nm, seed, replica, boundary=boundary,
+                           list_mode=list_mode)
     return g, p, L
 
 
@@ -60,8 +66,8 @@ def assert_positions_equal(g, x, y, L):
     assert worst <= REL, "max relative position difference %g" % worst
 
 
-def run_pair(N, eta, S, ell, nm, seed, n_sweeps, boundary, replica=0):
-    g, p, L = make(N, eta, S, ell, nm, seed, boundary, replica)
+def run_pair(N, eta, S, ell, nm, seed, n_sweeps, boundary, replica=0, kernel=1, list_mode=0):
+    g, p, L = make(N, eta, S, ell, nm, seed, boundary, replica, kernel, list_mode)
     x, y = W.square_lattice(N, L)
     g.set_positions(interleave(x, y), t0=0)
     tot = oracle.Stats()
@@ -91,6 +97,10 @@ def run_pair(N, eta, S, ell, nm, seed, n_sweeps, boundary, replica=0):
     return tot
 
 
+KERNELS = [1, 0]  # sorted frames in shared memory; block-wide scan
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("boundary", [REJECT, REFLECT])
 @pytest.mark.parametrize("N,eta,S,ell,nm,sweeps", [
     (256, 0.70, 2, 4.0, 4, 10),      # two stripes: both neighbours are one stripe
@@ -98,21 +108,60 @@ def run_pair(N, eta, S, ell, nm, seed, n_sweeps, boundary, replica=0):
     (900, 0.65, 6, 2.0, 5, 8),       # ragged member counts
     (4096, 0.72, 16, 2.0, 3, 6),
 ])
-def test_sweeps_match_oracle(N, eta, S, ell, nm, sweeps, boundary):
-    st = run_pair(N, eta, S, ell, nm, 5, sweeps, boundary)
+def test_sweeps_match_oracle(N, eta, S, ell, nm, sweeps, boundary, kernel):
+    st = run_pair(N, eta, S, ell, nm, 5, sweeps, boundary, kernel=kernel)
     assert st.events > 0 and st.lifts > 0 and st.frozen_hits > 0
     if boundary == REJECT:
         assert 0 < st.rejected < st.chains
 
 
-def test_sparse_system_with_empty_stripes():
-    st = run_pair(64, 0.05, 16, 3.0, 2, 3, 12, REJECT)
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_sparse_system_with_empty_stripes(kernel):
+    st = run_pair(64, 0.05, 16, 3.0, 2, 3, 12, REJECT, kernel=kernel)
     assert st.chains < 12 * 16 * 2
 
 
-def test_fig3_system_two_sweeps():
-    # N = 256^2 at eta = 0.708, stripes of about 8.4 sigma
-    run_pair(65536, 0.708, 32, 8.0, 4, 7, 2, REJECT)
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("N,eta,S,ell,nm,boundary", [
+    (256, 0.30, 4, 60.0, 3, REFLECT),   # L = 25.9: a chain goes round the box twice
+    (144, 0.10, 2, 90.0, 4, REFLECT),   # L = 33.6, few contacts, long free flights
+    (1024, 0.55, 8, 40.0, 2, REFLECT),
+    (256, 0.30, 4, 60.0, 6, REJECT),
+])
+def test_chains_longer_than_the_box(N, eta, S, ell, nm, boundary, kernel):
+    # movers wrap round the periodic axis again and again: the sorted kernel's
+    # strips must follow their rotation
+    st = run_pair(N, eta, S, ell, nm, 9, 6, boundary, kernel=kernel)
+    assert st.events > 0
+
+
+@pytest.mark.parametrize("boundary", [REJECT, REFLECT])
+@pytest.mark.parametrize("N,eta,S,ell,nm", [
+    (1024, 0.70, 8, 1.3, 40),           # n_m beyond the members of a stripe: cycled
+    (900, 0.65, 6, 2.0, 7),
+])
+def test_shuffled_start_lists_match_oracle(N, eta, S, ell, nm, boundary):
+    st = run_pair(N, eta, S, ell, nm, 21, 4, boundary, list_mode=oracle.LIST_WITHOUT_REPL)
+    assert st.events > 0
+
+
+def test_shuffled_lists_need_the_sorted_kernel():
+    g, p, L = make(256, 0.7, 2, 4.0, 2, 1, REJECT, kernel=0)
+    g.set_param(E.PARAM_STRIPES_LIST_MODE, oracle.LIST_WITHOUT_REPL)
+    with pytest.raises(E.EcmcError) as ei:
+        g.sweep(1)
+    assert ei.value.code == E.ERR_UNSUPPORTED
+    g.close()
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_fig3_system_two_sweeps(kernel):
+    # N = 256^2 at eta = 0.708, stripes of about 8.4 sigma; the sorted frame
+    # fits in shared memory, so it is the default there
+    g, _, _ = make(65536, 0.708, 32, 8.0, 4, 7, REJECT)
+    assert g.get_param(E.PARAM_STRIPES_KERNEL) == 1
+    g.close()
+    run_pair(65536, 0.708, 32, 8.0, 4, 7, 2, REJECT, kernel=kernel)
 
 
 def test_replica_key_changes_the_stream():
