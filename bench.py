@@ -313,54 +313,63 @@ def cpu_baseline_batch(descs, seconds):
 
 
 def run_grid(args):
-    """Parallelisation grid at N = 1024^2, eta = 0.72: events/s against the
-    degree of parallelisation (cells per side) and the chain displacement,
-    with the measured mean free path and the paper's criterion (eq. criterion)
-    ell* = L lambda0 / (sqrt(n) sigma) for each grid (n = blocks = cells/4)."""
+    """Parallelisation grid at N = 1024^2, eta = 0.72 (Sec. 4, Figs. 5-6),
+    through the library's measured tuner (ecmc_tune_geometry, n_m from eq. nm):
+    1. the survey's grid -- cells 8^2 .. 512^2 x ell in {2, 8, 32} sigma --
+       with its recipe: 100 warm-up sweeps from the lattice, at least 1 s
+       timed per point;
+    2. the tuner's own candidates around the paper's strategy (cells / 2 ..
+       cells x 2 of ecmc_suggest_parameters, ell from ell*/4 to 4 ell* of
+       eq. criterion), once with the same recipe and once with short trials
+       (10 warm-up, 10 timed sweeps), to check that the short trials pick
+       what the long ones pick.
+    Each point reports events/s, sweeps/s, the measured mean free path and the
+    criterion's ell* from it; the proxy is the mean square displacement per
+    second (ECMC_TUNE_MSD)."""
     import torch
 
-    import paper_1409_6948_gb300 as P
     from paper_1409_6948_gb300 import ecmc as E
 
     torch.cuda.set_device(0)
     w = W.LARGE
     L = w.L
     lam0 = (W.ETA_HCP - w.eta) / (2 * W.ETA_HCP)
-    pts = []
-    for cells in W.LARGE_CELL_GRID:
-        for ell in W.LARGE_ELL_GRID:
-            pt = {"cells": cells, "ell": ell}
-            try:
-                g = P.Ecmc(w.N, L, 1.0, cells, cells, ell, w.seed)
-            except E.EcmcError as ex:
-                pt["unsupported"] = str(ex)
-                pts.append(pt)
-                continue
-            g.sweep(melt_sweeps(args) + args.warmup)
-            g.synchronize()
-            g.reset_stats()
-            s = torch.cuda.Stream()
-            g.set_stream(s)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(s)
-            g.sweep(args.steps)
-            b.record(s)
-            torch.cuda.synchronize()
-            ms = a.elapsed_time(b)
-            c = g.counters()
-            n_blocks = cells * cells / 4.0
-            pt.update({"n_m": int(g.get_param(E.PARAM_N_CHAINS)),
-                       "lanes_per_cell": int(g.get_param(E.PARAM_LANES_PER_CELL)),
-                       "events_per_s": c.events / (ms * 1e-3), "sweeps_per_s": c.sweeps / (ms * 1e-3),
-                       "events_per_sweep": c.events / c.sweeps,
-                       "wall_fraction": c.wall_hits / max(c.events + c.wall_hits, 1),
-                       "free_path": c.sum_disp / max(c.events + c.wall_hits + c.chains, 1),
-                       "criterion_ell": L * lam0 / math.sqrt(n_blocks),
-                       "N_over_eta_n": w.N / (w.eta * n_blocks)})
-            pts.append(pt)
-            g.close()
-    print(json.dumps({"mode": "grid", "workload": w.name, "steps": args.steps,
-                      "warmup": args.warmup, "lambda0_eq": lam0, "points": pts}))
+    warm = 100 if args.warmup < 100 else args.warmup
+    grid, gbest = E.tune_geometry(w.N, L, W.LARGE_CELL_GRID, W.LARGE_ELL_GRID, seed=w.seed,
+                                  warm_sweeps=warm, trial_sweeps=10, min_seconds=1.0,
+                                  proxy=E.TUNE_MSD)
+    for t in grid:
+        n_blocks = t["cells"] ** 2 / 4.0
+        t["criterion_ell_eq_lambda0"] = L * lam0 / math.sqrt(n_blocks)
+        t["N_over_eta_n"] = w.N / (w.eta * n_blocks)
+    sp = E.suggest_parameters(w.N, L, 1.0, 2.0)
+    c0 = sp["cells_x"]
+    cells = sorted({max(2, 2 * int(round(c0 * f / 2))) for f in (0.5, 0.7071, 1.0, 1.4142, 2.0)})
+    ells = [sp["ell"] * f for f in (0.25, 0.5, 1.0, 2.0, 4.0)]
+    long_t, lbest = E.tune_geometry(w.N, L, cells, ells, seed=w.seed, warm_sweeps=warm,
+                                    trial_sweeps=10, min_seconds=1.0, proxy=E.TUNE_MSD)
+    short_t, sbest = E.tune_geometry(w.N, L, cells, ells, seed=w.seed, warm_sweeps=10,
+                                     trial_sweeps=10, min_seconds=0.0, proxy=E.TUNE_MSD)
+
+    def pick(ts, i):
+        t = ts[i]
+        return {"cells": t["cells"], "ell": t["ell"], "n_m": t["n_m"],
+                "msd_per_s": t["score"], "events_per_s": t["events_per_s"],
+                "sweeps_per_s": t["sweeps_per_s"], "lambda0": t["lambda0"],
+                "ell_star": t["ell_star"]}
+
+    by = lambda ts, k: max(range(len(ts)), key=lambda i: ts[i][k] if ts[i]["status"] == 0  # noqa
+                           else -1.0)
+    print(json.dumps({
+        "mode": "grid", "workload": w.name, "warm_sweeps": warm, "min_seconds": 1.0,
+        "proxy": "mean square displacement per second", "lambda0_eq": lam0,
+        "survey_grid": {"points": grid, "best_msd": pick(grid, gbest),
+                        "best_events": pick(grid, by(grid, "events_per_s")),
+                        "best_sweeps": pick(grid, by(grid, "sweeps_per_s"))},
+        "paper_strategy": {"cells": c0, "ell": sp["ell"], "n_m": sp["n_m"]},
+        "tuner_candidates": {"cells": cells, "ell": ells, "long": long_t, "short": short_t,
+                             "best_long": pick(long_t, lbest), "best_short": pick(short_t, sbest),
+                             "agree": lbest == sbest}}))
     return 0
 
 

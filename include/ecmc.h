@@ -263,6 +263,51 @@ ECMC_API int ecmc_replica_counters(ecmc_t h, int r, ecmc_counters_t* out);
 ECMC_API int ecmc_suggest_parameters(int64_t N, double L, double sigma, double min_cell_side,
                                      ecmc_replica_desc_t* out);
 
+/* ---- measured choice of cells and ell (Sec. 4, Figs. 5-6) ---------------- */
+/* Sampling proxies ecmc_tune_geometry can maximise. */
+#define ECMC_TUNE_EVENTS 0 /* collision events per second                          */
+#define ECMC_TUNE_MSD 1    /* mean square displacement per disk per second         */
+#define ECMC_TUNE_TAU 2    /* sweeps per second / tau of Psi in sweeps (eq. tau)    */
+
+/* One trial of ecmc_tune_geometry. */
+typedef struct {
+  int cells;            /* cells per side                                        */
+  int n_m;              /* chains per cell and sweep, eq. (nm)                   */
+  double ell;           /* chain displacement                                    */
+  int status;           /* ECMC_OK, or why the trial did not run (ECMC_ERR_ARG:  */
+                        /* cell side not above 2 sigma, ell <= 0, ...)           */
+  int64_t sweeps;       /* timed sweeps                                          */
+  double ms_per_sweep;  /* CUDA-event time per timed sweep                       */
+  double events_per_s;
+  double sweeps_per_s;
+  double lambda0;       /* measured mean free path: displacement over contacts,  */
+                        /* wall reflections and chain ends                       */
+  double ell_star;      /* eq. (criterion) with that lambda0: L lambda0 / (sqrt(n) sigma), */
+                        /* n = cells^2 / 4 blocks                                */
+  double msd_per_sweep; /* ECMC_TUNE_MSD: mean square displacement per disk and sweep */
+  double tau_sweeps;    /* ECMC_TUNE_TAU: autocorrelation time of Psi in sweeps  */
+  double score;         /* the proxy (-1 if the trial did not run)                */
+} ecmc_geom_trial_t;
+
+/* The degree of parallelisation chosen by measurement: the paper's strategy
+ * (Sec. 4; ecmc_suggest_parameters) picks cells and ell from eqs. (nm),
+ * (lambda0) and (criterion); this entry point times the alternatives instead.
+ * For every pair (cells[i], ells[j]) -- trial index i * n_ells + j -- it
+ * builds a system with base's N, L, sigma, seed and replica, n_m from eq. (nm),
+ * starting from xy (host memory, 2N values in id order; NULL = the square
+ * lattice), runs warm_sweeps sweeps, then sweeps timed with CUDA events in
+ * batches of trial_sweeps until at least min_seconds have passed, and scores
+ * it by `proxy` (ECMC_TUNE_*; MSD and TAU run trial_sweeps further sweeps to
+ * measure it).  trials (n_cells * n_ells entries) receives every trial, *best
+ * the index of the largest score.  Cells whose side is not above 2 sigma are
+ * skipped (status ECMC_ERR_ARG).  Each trial is a separate handle: the
+ * caller's handles are not touched.  Errors: ECMC_ERR_ARG (bad arguments, no
+ * candidate ran), ECMC_ERR_OOM, ECMC_ERR_CUDA. */
+ECMC_API int ecmc_tune_geometry(const ecmc_replica_desc_t* base, const double* xy,
+                                const int* cells, int n_cells, const double* ells, int n_ells,
+                                int warm_sweeps, int trial_sweeps, double min_seconds, int proxy,
+                                ecmc_geom_trial_t* trials, int* best);
+
 /* One launch shape and its measured time per sweep. */
 typedef struct {
   int lanes_per_cell;

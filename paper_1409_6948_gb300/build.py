@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libecmc.so")
 SOURCES = ["ecmc_api.cu", "ecmc_bin.cu", "ecmc_frame.cu", "ecmc_phase.cu", "ecmc_measure.cu",
-           "ecmc_noalloc.cu", "ecmc_sweep.cu", "ecmc3.cu", "ecmc_stripes.cu"]
+           "ecmc_noalloc.cu", "ecmc_sweep.cu", "ecmc3.cu", "ecmc_stripes.cu", "ecmc_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fvisibility=hidden", "-I", os.path.join(ROOT, "include"), "-I", CSRC]

@@ -50,6 +50,9 @@ DIR_POS_ONLY = 1
 DIR_ISOTROPIC = 2
 PREC_FP64 = 0
 PREC_FP32_GEOM = 1
+TUNE_EVENTS = 0
+TUNE_MSD = 1
+TUNE_TAU = 2
 
 
 class Counters(C.Structure):
@@ -81,6 +84,18 @@ class TuneResult(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class GeomTrial(C.Structure):
+    _fields_ = [("cells", C.c_int), ("n_m", C.c_int), ("ell", C.c_double), ("status", C.c_int),
+                ("sweeps", C.c_int64), ("ms_per_sweep", C.c_double),
+                ("events_per_s", C.c_double), ("sweeps_per_s", C.c_double),
+                ("lambda0", C.c_double), ("ell_star", C.c_double),
+                ("msd_per_sweep", C.c_double), ("tau_sweeps", C.c_double),
+                ("score", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class ReplicaDesc(C.Structure):
     _fields_ = [("N", C.c_int64), ("L", C.c_double), ("sigma", C.c_double),
                 ("cells_x", C.c_int), ("cells_y", C.c_int), ("ell", C.c_double),
@@ -106,6 +121,9 @@ _SIGS = {
     "ecmc_replica_counters": (C.c_int, [_H, C.c_int, C.POINTER(Counters)]),
     "ecmc_suggest_parameters": (C.c_int, [C.c_int64, C.c_double, C.c_double, C.c_double,
                                           C.POINTER(ReplicaDesc)]),
+    "ecmc_tune_geometry": (C.c_int, [C.POINTER(ReplicaDesc), C.c_void_p, C.c_void_p, C.c_int,
+                                     C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
+                                     C.POINTER(GeomTrial), C.POINTER(C.c_int)]),
     "ecmc_autotune": (C.c_int, [_H, C.c_int, C.POINTER(TuneResult), C.POINTER(TuneResult),
                                 C.c_int, C.POINTER(C.c_int)]),
     "ecmc_destroy": (C.c_int, [_H]),
@@ -677,6 +695,27 @@ def sweep_noalloc(xy, N, L, sigma, cells_x, cells_y, ell, n_m, seed, replica, t0
                                      C.c_uint64(int(seed)), C.c_uint64(int(replica)), int(t0),
                                      int(n_sweeps), C.c_void_p(stream or 0)),
            "ecmc_sweep_noalloc")
+
+
+def tune_geometry(N, L, cells, ells, sigma=1.0, seed=0, replica=0, xy=None, warm_sweeps=10,
+                  trial_sweeps=10, min_seconds=0.0, proxy=None):
+    """ecmc_tune_geometry: one timed trial per (cells, ell), n_m from eq. nm;
+    returns (trials as dicts in the order cells-major, index of the best)."""
+    proxy = TUNE_MSD if proxy is None else proxy
+    d = ReplicaDesc(int(N), float(L), float(sigma), 0, 0, 0.0, 0, int(seed), int(replica))
+    cl = np.ascontiguousarray(np.asarray(cells, dtype=np.int32))
+    el = np.ascontiguousarray(np.asarray(ells, dtype=np.float64))
+    out = (GeomTrial * (cl.size * el.size))()
+    best = C.c_int()
+    buf = None
+    if xy is not None:
+        buf = np.ascontiguousarray(np.asarray(xy, dtype=np.float64))
+    _check(load().ecmc_tune_geometry(C.byref(d), C.c_void_p(buf.ctypes.data) if buf is not None
+                                     else None, C.c_void_p(cl.ctypes.data), int(cl.size),
+                                     C.c_void_p(el.ctypes.data), int(el.size), int(warm_sweeps),
+                                     int(trial_sweeps), float(min_seconds), int(proxy), out,
+                                     C.byref(best)), "ecmc_tune_geometry")
+    return [t.as_dict() for t in out], best.value
 
 
 def suggest_parameters(N, L, sigma=1.0, min_cell_side=0.0):

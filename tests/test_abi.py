@@ -216,7 +216,8 @@ def test_binding_structs_match_the_c_layout():
     if gcc is None:
         pytest.skip("no C compiler")
     structs = {"ecmc_counters_t": E.Counters, "ecmc_timing_t": E.Timing,
-               "ecmc_tune_result_t": E.TuneResult, "ecmc_replica_desc_t": E.ReplicaDesc}
+               "ecmc_tune_result_t": E.TuneResult, "ecmc_replica_desc_t": E.ReplicaDesc,
+               "ecmc_geom_trial_t": E.GeomTrial}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ecmc.h"', 'int main(void) {']
     for cname, cls in structs.items():
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
