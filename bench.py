@@ -68,7 +68,7 @@ def parse():
                     help="autocorrelation time of Psi against n_m and ell (N = 64^2)")
     ap.add_argument("--tau-eta", type=float, default=0.704,
                     help="packing fraction of the --tau experiment")
-    ap.add_argument("--tau-max", type=int, default=20000,
+    ap.add_argument("--tau-max", type=int, default=100000,
                     help="most sweeps per point of the --tau experiment")
     ap.add_argument("--listbias", action="store_true",
                     help="pressure vs n_m with start lists drawn with and without replacement")
@@ -320,7 +320,7 @@ def run_grid(args):
        timed per point;
     2. the tuner's own candidates around the paper's strategy (cells / 2 ..
        cells x 2 of ecmc_suggest_parameters, ell from ell*/4 to 4 ell* of
-       eq. criterion), once with the same recipe and once with short trials
+       eq. criterion... ell*/8 .. 4 ell*), once with the same recipe and once with short trials
        (10 warm-up, 10 timed sweeps), to check that the short trials pick
        what the long ones pick.
     Each point reports events/s, sweeps/s, the measured mean free path and the
@@ -345,7 +345,7 @@ def run_grid(args):
     sp = E.suggest_parameters(w.N, L, 1.0, 2.0)
     c0 = sp["cells_x"]
     cells = sorted({max(2, 2 * int(round(c0 * f / 2))) for f in (0.5, 0.7071, 1.0, 1.4142, 2.0)})
-    ells = [sp["ell"] * f for f in (0.25, 0.5, 1.0, 2.0, 4.0)]
+    ells = [sp["ell"] * f for f in (0.125, 0.25, 0.5, 1.0, 2.0, 4.0)]
     long_t, lbest = E.tune_geometry(w.N, L, cells, ells, seed=w.seed, warm_sweeps=warm,
                                     trial_sweeps=10, min_seconds=1.0, proxy=E.TUNE_MSD)
     short_t, sbest = E.tune_geometry(w.N, L, cells, ells, seed=w.seed, warm_sweeps=10,
@@ -728,7 +728,8 @@ def run_tau(args):
     point is a batch of 32 independent replicas (Philox key (8, r)) advanced
     together, melted by 1000 sweeps; Psi of every replica (Delaunay
     neighbours within 2.5 sigma, every cell certified) is measured every 5
-    sweeps and the autocorrelation is averaged over the replicas.  Each point
+    sweeps (every 25 at eta >= 0.69) and the autocorrelation is averaged over
+    the replicas by ecmc_autocorrelation_time.  Each point
     runs until the series are at least 30 tau long (at most --tau-max sweeps);
     tau is given in sweeps and in wall time per replica-sweep.  One JSON line
     per point, then the summary."""
@@ -738,7 +739,10 @@ def run_tau(args):
     from paper_1409_6948_gb300 import ecmc as E
 
     torch.cuda.set_device(0)
-    N, eta, cells, seed, R, every = 4096, args.tau_eta, 4, 8, 32, 5
+    # Psi every 5 sweeps in the liquid; every 25 at the paper's density, where
+    # tau exceeds 2500 sweeps
+    N, eta, cells, seed, R = 4096, args.tau_eta, 4, 8, 32
+    every = 5 if eta < 0.69 else 25
     L = W.box_side(N, eta)
     lam0 = (W.ETA_HCP - eta) / (2 * W.ETA_HCP)
     pts = []
@@ -767,17 +771,11 @@ def run_tau(args):
                 t_psi += time.perf_counter() - b
                 n_bad += bad
             n += 400 * every
+            # eq. tau averaged over the replicas (ecmc_autocorrelation_time)
             z = np.array(series)            # [samples, replicas]
-            m = z.shape[0]
-            lag = m // 4
-            denom = np.mean(np.abs(z) ** 2)
-            c = np.array([np.real(np.mean(np.conj(z[:m - d]) * z[d:])) / denom
-                          for d in range(lag + 1)])
-            below = np.flatnonzero(c < math.exp(-1.0))
-            if below.size:
-                d = below[0]
-                tau = every * ((d - 1) + (c[d - 1] - math.exp(-1.0)) / (c[d - 1] - c[d]))
-            if n >= 30 * tau:
+            tau_s, _ = E.autocorrelation_time(z, max_lag=z.shape[0] // 4)
+            tau = every * tau_s
+            if n >= 20 * tau:
                 break
         cnt = g.counters()
         pt = {"n_m": nm_used, "ell": ell, "tau_sweeps": tau, "sweeps": n, "replicas": R,
@@ -789,8 +787,12 @@ def run_tau(args):
         print(json.dumps(pt), flush=True)
         pts.append(pt)
         g.close()
+    # the tuning decision of Figs. 5-6: the setting with the smallest tau in
+    # wall time
+    fin = [p for p in pts if math.isfinite(p["tau_sweeps"])]
+    best = min(fin, key=lambda p: p["tau_wall_ms_per_replica"]) if fin else None
     print(json.dumps({"mode": "tau", "workload": "N=4096 eta=%g cells=4x4, 32 replicas" % eta,
-                      "lambda0_eq": lam0, "points": pts}))
+                      "lambda0_eq": lam0, "points": pts, "best_tau_wall": best}))
     return 0
 
 

@@ -451,23 +451,25 @@ ECMC_API int ecmc_device_peaks(double* smem_gbs, double* fp64_gflops);
 ECMC_API int ecmc_hexatic(ecmc_t h, double rs, double* psi, double* psi_k, int32_t* n_nb,
                           int64_t* n_bad);
 
-/* Autocorrelation time of a series of the hexatic order parameter (Sec. 2,
- * eq. tau): C(dt) = Re <Psi*(t) Psi(t + dt)>_t / <|Psi(t)|^2>_t, the
- * numerator averaged over the n - dt pairs at lag dt, the denominator over all
- * n samples, with the mean of Psi taken as zero as the definition prescribes
- * (its phase depends on the arbitrary reference axis); tau is the lag at which
- * C first falls below 1/e, interpolated linearly between the lags around it,
- * in units of the sampling interval (+infinity if C stays at or above 1/e up
- * to max_lag).
- *   psi     host memory, 2n doubles: Re, Im of Psi at equally spaced times
- *   n       samples (>= 2)
+/* Autocorrelation time of the hexatic order parameter (Sec. 2, eq. tau),
+ * from R independent series (replicas of one system) of n samples each:
+ * C(dt) = Re <Psi_r*(t) Psi_r(t + dt)>_{t,r} / <|Psi_r(t)|^2>_{t,r}, the
+ * numerator averaged over the R (n - dt) pairs at lag dt, the denominator over
+ * all R n samples, with the mean of Psi taken as zero as the definition
+ * prescribes (its phase depends on the arbitrary reference axis); tau is the
+ * lag at which C first falls below 1/e, interpolated linearly between the lags
+ * around it, in units of the sampling interval (+infinity if C stays at or
+ * above 1/e up to max_lag).
+ *   psi     host memory, 2 n R doubles, sample-major: Re, Im of series r at
+ *           sample t at [2 (t R + r)], [2 (t R + r) + 1]
+ *   n       samples per series (>= 2); R series (>= 1)
  *   max_lag largest lag evaluated (<= 0: n / 4); must be below n
  *   tau     receives tau
  *   c_out   host memory for C(0 .. max_lag), or NULL (then the scan stops at
  *           the 1/e crossing)
  * Host arithmetic, no device work.  Errors: ECMC_ERR_ARG (NULL psi or tau,
- * n < 2, max_lag >= n, a series without positive finite power). */
-ECMC_API int ecmc_autocorrelation_time(const double* psi, int64_t n, int64_t max_lag,
+ * n < 2, R < 1, max_lag >= n, series without positive finite power). */
+ECMC_API int ecmc_autocorrelation_time(const double* psi, int64_t n, int R, int64_t max_lag,
                                        double* tau, double* c_out);
 
 /* The square root of the chain kernel's hit distance (Sec. 3.2: the

@@ -89,7 +89,7 @@ def lib():
                                              C.POINTER(C.c_int), C.POINTER(C.c_double),
                                              C.POINTER(C.c_int)]
         L.orc_suggest_parameters.restype = C.c_int
-        L.orc_autocorrelation_time.argtypes = [d, d, i64, i64, C.POINTER(C.c_double),
+        L.orc_autocorrelation_time.argtypes = [d, d, i64, C.c_int, i64, C.POINTER(C.c_double),
                                                C.c_void_p]
         L.orc_autocorrelation_time.restype = C.c_int
         L.orc_min_dist2.argtypes = [i64, C.c_double, d, d, C.c_double]
@@ -184,13 +184,17 @@ def suggest_parameters(N, L, sigma=1.0, min_cell_side=0.0):
 
 
 def autocorrelation_time(psi_series, max_lag):
-    """tau of a complex series (eq. tau) and C(0..max_lag)."""
+    """tau (eq. tau) and C(0..max_lag) of one complex series [n] or of R
+    series [n, R] (replicas, averaged)."""
     z = np.asarray(psi_series, dtype=complex)
-    re = np.ascontiguousarray(z.real)
-    im = np.ascontiguousarray(z.imag)
+    if z.ndim == 1:
+        z = z[:, None]
+    n, R = z.shape
+    re = np.ascontiguousarray(z.real.T)   # series-major for the oracle
+    im = np.ascontiguousarray(z.imag.T)
     c = np.empty(int(max_lag) + 1)
     tau = C.c_double()
-    rc = lib().orc_autocorrelation_time(_dptr(re), _dptr(im), int(z.size), int(max_lag),
+    rc = lib().orc_autocorrelation_time(_dptr(re), _dptr(im), int(n), int(R), int(max_lag),
                                         C.byref(tau), c.ctypes.data_as(C.c_void_p))
     if rc != 0:
         raise ValueError("bad series (rc=%d)" % rc)

@@ -1037,18 +1037,23 @@ int orc_sweeps_snap(const orc_params* p, double* x, double* y, int64_t t0, int64
 /* ------------------------------------------------------------------------ */
 /* Autocorrelation time of the hexatic order parameter (Sec. 2, eq. tau)     */
 /* ------------------------------------------------------------------------ */
-/* C(dt) = Re <conj(Psi(t)) Psi(t+dt)> / <|Psi(t)|^2>, each average over the
- * samples available (n - dt pairs at lag dt, n samples for the norm), the mean
- * of Psi taken as zero as the definition says.  tau = the first lag with
- * C < 1/e, moved back linearly towards the lag before it; INFINITY if there is
- * none up to max_lag.  re[], im[] hold the series; c[] (may be NULL) receives
+/* R series (replicas) of n samples, series r in re[r*n .. r*n+n), im[...]:
+ * C(dt) = Re <conj(Psi_r(t)) Psi_r(t+dt)> / <|Psi_r(t)|^2>, each average over
+ * all the terms available (R (n - dt) pairs at lag dt, R n samples for the
+ * norm), the mean of Psi taken as zero as the definition says.  tau = the
+ * first lag with C < 1/e, moved back linearly towards the lag before it;
+ * INFINITY if there is none up to max_lag.  c[] (may be NULL) receives
  * C(0..max_lag).  Returns 0, or -1 for a bad argument. */
-int orc_autocorrelation_time(const double* re, const double* im, int64_t n, int64_t max_lag,
-                             double* tau, double* c) {
-  if (n < 2 || max_lag < 1 || max_lag >= n) return -1;
+int orc_autocorrelation_time(const double* re, const double* im, int64_t n, int R,
+                             int64_t max_lag, double* tau, double* c) {
+  if (n < 2 || R < 1 || max_lag < 1 || max_lag >= n) return -1;
   double power = 0.0;
-  for (int64_t t = 0; t < n; ++t) power += re[t] * re[t] + im[t] * im[t];
-  power = power / (double)n;
+  for (int r = 0; r < R; ++r)
+    for (int64_t t = 0; t < n; ++t) {
+      const int64_t i = (int64_t)r * n + t;
+      power += re[i] * re[i] + im[i] * im[i];
+    }
+  power = power / ((double)n * (double)R);
   if (!(power > 0.0)) return -1;
   double threshold = exp(-1.0);
   double c_prev = 0.0;
@@ -1056,11 +1061,15 @@ int orc_autocorrelation_time(const double* re, const double* im, int64_t n, int6
   for (int64_t lag = 0; lag <= max_lag; ++lag) {
     double sum = 0.0;
     int64_t pairs = n - lag;
-    for (int64_t t = 0; t < pairs; ++t) {
-      /* real part of conj(a) * b */
-      sum += re[t] * re[t + lag] + im[t] * im[t + lag];
+    for (int r = 0; r < R; ++r) {
+      const double* a_re = re + (int64_t)r * n;
+      const double* a_im = im + (int64_t)r * n;
+      for (int64_t t = 0; t < pairs; ++t) {
+        /* real part of conj(a) * b */
+        sum += a_re[t] * a_re[t + lag] + a_im[t] * a_im[t + lag];
+      }
     }
-    double c_lag = (sum / (double)pairs) / power;
+    double c_lag = (sum / ((double)pairs * (double)R)) / power;
     if (c) c[lag] = c_lag;
     if (c_lag < threshold && isinf(*tau)) {
       if (lag == 0)

@@ -173,12 +173,14 @@ int orc_run_chain_frame(int n, int n_mem, double* X, double* Y, const int64_t* i
                         double dy, double ell, int mode, orc_stats* st,
                         orc_chain_rec* rec);
 
-/* Autocorrelation time of a complex series (Sec. 2, eq. tau): C(dt) = Re
- * <conj(Psi(t)) Psi(t+dt)> / <|Psi|^2> with the mean of Psi taken as zero, tau
- * = the 1/e lag, interpolated linearly; INFINITY if C stays above 1/e up to
- * max_lag.  c (may be NULL) receives C(0..max_lag).  Returns 0 or -1. */
-int orc_autocorrelation_time(const double* re, const double* im, int64_t n, int64_t max_lag,
-                             double* tau, double* c);
+/* Autocorrelation time of R complex series of n samples (Sec. 2, eq. tau;
+ * series r at re[r n ..], im[r n ..]): C(dt) = Re <conj(Psi_r(t))
+ * Psi_r(t+dt)> / <|Psi_r|^2> over t and r, with the mean of Psi taken as
+ * zero, tau = the 1/e lag, interpolated linearly; INFINITY if C stays above
+ * 1/e up to max_lag.  c (may be NULL) receives C(0..max_lag).  Returns 0 or
+ * -1. */
+int orc_autocorrelation_time(const double* re, const double* im, int64_t n, int R,
+                             int64_t max_lag, double* tau, double* c);
 
 #ifdef __cplusplus
 }

@@ -714,24 +714,28 @@ int probe_peaks(double* smem_gbs, double* fp64_gflops) {
 }  // namespace ecmc
 
 // ---- autocorrelation time of the hexatic order parameter (Sec. 2, eq. tau)
-// Host arithmetic on a short series.  C(dt) = Re <Psi*(t) Psi(t + dt)>_t /
-// <|Psi(t)|^2>_t: the numerator averages the n - dt products available at lag
-// dt, the denominator all n samples; no mean is subtracted, since <Psi> = 0 by
-// the arbitrary phase (the paper builds this into the definition).  tau is
-// the lag where C first falls below 1/e, interpolated linearly between the
-// two lags around it; +infinity if C stays at or above 1/e up to max_lag.
-// Sums run in increasing t, so the result does not depend on threading.
-extern "C" int ecmc_autocorrelation_time(const double* psi, int64_t n, int64_t max_lag,
+// Host arithmetic on short series.  R independent series of n samples each
+// (replicas of one system), sample-major: psi[2 (t R + r)], psi[2 (t R + r) + 1].
+// C(dt) = Re <Psi_r*(t) Psi_r(t + dt)>_{t,r} / <|Psi_r(t)|^2>_{t,r}: the
+// numerator averages the R (n - dt) products available at lag dt, the
+// denominator all R n samples; no mean is subtracted, since <Psi> = 0 by the
+// arbitrary phase (the paper builds this into the definition).  tau is the
+// lag where C first falls below 1/e, interpolated linearly between the two
+// lags around it; +infinity if C stays at or above 1/e up to max_lag.  Sums
+// run in increasing t, then r, so the result does not depend on threading.
+extern "C" int ecmc_autocorrelation_time(const double* psi, int64_t n, int R, int64_t max_lag,
                                          double* tau, double* c_out) {
-  if (!psi || !tau || n < 2) return ecmc::report_error(ECMC_ERR_ARG, "need psi, tau and n >= 2");
+  if (!psi || !tau || n < 2 || R < 1)
+    return ecmc::report_error(ECMC_ERR_ARG, "need psi, tau, n >= 2 and R >= 1");
   if (max_lag <= 0) max_lag = n / 4 > 1 ? n / 4 : 1;
   if (max_lag > n - 1) return ecmc::report_error(ECMC_ERR_ARG, "max_lag must be below n");
   double norm = 0.0;
-  for (int64_t t = 0; t < n; ++t) {
-    const double re = psi[2 * t], im = psi[2 * t + 1];
-    norm += re * re + im * im;
-  }
-  norm /= (double)n;
+  for (int64_t t = 0; t < n; ++t)
+    for (int r = 0; r < R; ++r) {
+      const double re = psi[2 * (t * R + r)], im = psi[2 * (t * R + r) + 1];
+      norm += re * re + im * im;
+    }
+  norm /= (double)n * (double)R;
   if (!(norm > 0.0) || !std::isfinite(norm))
     return ecmc::report_error(ECMC_ERR_ARG, "the series has no positive finite power");
   const double inv_e = std::exp(-1.0);
@@ -740,11 +744,13 @@ extern "C" int ecmc_autocorrelation_time(const double* psi, int64_t n, int64_t m
   bool found = false;
   for (int64_t d = 0; d <= max_lag; ++d) {
     double acc = 0.0;
-    for (int64_t t = 0; t + d < n; ++t) {
-      // Re(conj(a) b) = a_re b_re + a_im b_im
-      acc += psi[2 * t] * psi[2 * (t + d)] + psi[2 * t + 1] * psi[2 * (t + d) + 1];
-    }
-    const double c = (acc / (double)(n - d)) / norm;
+    for (int64_t t = 0; t + d < n; ++t)
+      for (int r = 0; r < R; ++r) {
+        // Re(conj(a) b) = a_re b_re + a_im b_im
+        const int64_t i = t * R + r, j = (t + d) * R + r;
+        acc += psi[2 * i] * psi[2 * j] + psi[2 * i + 1] * psi[2 * j + 1];
+      }
+    const double c = (acc / ((double)(n - d) * (double)R)) / norm;
     if (c_out) c_out[d] = c;
     if (!found && c < inv_e) {
       *tau = d == 0 ? 0.0 : (double)(d - 1) + (prev - inv_e) / (prev - c);

@@ -119,7 +119,7 @@ int run_trial(const ecmc_replica_desc_t& desc, const double* xy, int warm, int t
         return rc;
     }
     double tau = 0.0;
-    if ((rc = ecmc_autocorrelation_time(series.data(), trial, trial / 4 > 1 ? trial / 4 : 1, &tau,
+    if ((rc = ecmc_autocorrelation_time(series.data(), trial, 1, trial / 4 > 1 ? trial / 4 : 1, &tau,
                                         nullptr)))
       return rc;
     t->tau_sweeps = tau;

@@ -155,7 +155,7 @@ _SIGS = {
                                C.c_void_p]),
     "ecmc_hexatic": (C.c_int, [_H, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.POINTER(C.c_int64)]),
-    "ecmc_autocorrelation_time": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64,
+    "ecmc_autocorrelation_time": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_int64,
                                             C.POINTER(C.c_double), C.c_void_p]),
     "ecmc_sweep_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_double, C.c_int,
                                      C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_uint64,
@@ -761,17 +761,21 @@ def sqrt_rn(x, rel_error=None, stream=None):
 
 
 def autocorrelation_time(psi_series, max_lag=None):
-    """Autocorrelation time tau of a complex order-parameter series (eq. tau),
-    computed by ecmc_autocorrelation_time.  Returns (tau, C[0..max_lag])."""
-    z = np.ascontiguousarray(np.asarray(psi_series, dtype=complex))
-    n = z.size
+    """Autocorrelation time tau of complex order-parameter series (eq. tau),
+    computed by ecmc_autocorrelation_time: psi_series is one series [n] or R
+    series [n, R] (replicas, averaged as the definition's <...>).  Returns
+    (tau, C[0..max_lag])."""
+    z = np.asarray(psi_series, dtype=complex)
+    if z.ndim == 1:
+        z = z[:, None]
+    n, R = z.shape
     if max_lag is None:
         max_lag = n // 4
-    buf = np.ascontiguousarray(np.stack([z.real, z.imag], 1).ravel())
+    buf = np.ascontiguousarray(np.stack([z.real, z.imag], -1).ravel())
     c = np.empty(int(max_lag) + 1)
     tau = C.c_double()
-    _check(load().ecmc_autocorrelation_time(C.c_void_p(buf.ctypes.data), int(n), int(max_lag),
-                                            C.byref(tau), C.c_void_p(c.ctypes.data)),
+    _check(load().ecmc_autocorrelation_time(C.c_void_p(buf.ctypes.data), int(n), int(R),
+                                            int(max_lag), C.byref(tau), C.c_void_p(c.ctypes.data)),
            "ecmc_autocorrelation_time")
     return tau.value, c
 

@@ -91,6 +91,26 @@ def test_no_crossing_gives_infinity_and_the_two_sides_agree():
     assert t_lib == pytest.approx(t_orc, rel=1e-13)
 
 
+@pytest.mark.parametrize("side", ["oracle", "library"])
+def test_replicas_average_the_closed_form(side):
+    # 16 independent AR(1) series of 20,000 samples: the replica average has
+    # the single series' C(dt) = a^dt cos(w dt); the same data as one long
+    # series would mix the replicas' ends
+    a, w = math.exp(-1.0 / 10.0), 0.07
+    z = np.stack([rotating_ar1(a, w, 20000, 100 + r) for r in range(16)], axis=1)
+    fn = oracle.autocorrelation_time if side == "oracle" else library_tau()
+    tau, c = fn(z, 60)
+    for d in (1, 5, 10, 20):
+        assert abs(c[d] - a**d * math.cos(w * d)) < 0.015, (d, c[d])
+    want = first_crossing(a, w)
+    assert abs(tau - want) < 0.04 * want, (tau, want)
+    # replicas of identical series: the average equals the single series
+    z1 = rotating_ar1(a, w, 5000, 7)
+    t1, c1 = fn(z1, 30)
+    t4, c4 = fn(np.stack([z1] * 4, axis=1), 30)
+    assert np.allclose(c1, c4, rtol=1e-12) and t1 == pytest.approx(t4, rel=1e-12)
+
+
 def test_library_rejects_bad_arguments():
     library_tau()
     import ctypes as C
@@ -98,10 +118,13 @@ def test_library_rejects_bad_arguments():
     lib = E.load()
     buf = np.ones(20)
     tau = C.c_double()
-    assert lib.ecmc_autocorrelation_time(buf.ctypes.data, 1, 0, C.byref(tau), None) == E.ERR_ARG
-    assert lib.ecmc_autocorrelation_time(buf.ctypes.data, 10, 10, C.byref(tau),
+    assert lib.ecmc_autocorrelation_time(buf.ctypes.data, 1, 1, 0, C.byref(tau),
                                          None) == E.ERR_ARG
-    assert lib.ecmc_autocorrelation_time(None, 10, 2, C.byref(tau), None) == E.ERR_ARG
+    assert lib.ecmc_autocorrelation_time(buf.ctypes.data, 10, 1, 10, C.byref(tau),
+                                         None) == E.ERR_ARG
+    assert lib.ecmc_autocorrelation_time(buf.ctypes.data, 10, 0, 2, C.byref(tau),
+                                         None) == E.ERR_ARG
+    assert lib.ecmc_autocorrelation_time(None, 10, 1, 2, C.byref(tau), None) == E.ERR_ARG
     zero = np.zeros(20)
-    assert lib.ecmc_autocorrelation_time(zero.ctypes.data, 10, 2, C.byref(tau),
+    assert lib.ecmc_autocorrelation_time(zero.ctypes.data, 10, 1, 2, C.byref(tau),
                                          None) == E.ERR_ARG
