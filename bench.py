@@ -521,8 +521,9 @@ def run_dim3(args):
     displacements ell, n_m chosen so that a sweep displaces about every
     sphere once (eq. nm with the mean free path measured at this density).
     Each point melts 30 sweeps and times --steps sweeps with CUDA events on
-    the library's stream.  The 3D oracle is timed on a bounded sample of the
-    first point on one host core."""
+    the library's stream; --cells and --ell restrict the grid to one value.
+    The 3D oracle is timed on a bounded sample of the first point on one
+    host core."""
     import torch
 
     import oracle
@@ -534,8 +535,8 @@ def run_dim3(args):
     L = W.box_side3(N, eta)
     lam0 = 0.06  # mean free path at eta = 0.45 (the points report their own)
     pts = []
-    for cells in (16, 20, 26):
-        for ell in (0.5, 1.0, 2.0):
+    for cells in ((args.cells,) if args.cells else (16, 20, 26)):
+        for ell in ((args.ell,) if args.ell else (0.5, 1.0, 2.0)):
             nm = max(1, int(round(N / cells**3 * lam0 / ell)))
             g = P.Ecmc3(N, L, 1.0, cells, ell, seed)
             g.set_param(E.PARAM3_N_CHAINS, nm)
@@ -730,7 +731,7 @@ def run_tau(args):
     neighbours within 2.5 sigma, every cell certified) is measured every 5
     sweeps (every 25 at eta >= 0.69) and the autocorrelation is averaged over
     the replicas by ecmc_autocorrelation_time.  Each point
-    runs until the series are at least 30 tau long (at most --tau-max sweeps);
+    runs until the series are at least 20 tau long (at most --tau-max sweeps);
     tau is given in sweeps and in wall time per replica-sweep.  One JSON line
     per point, then the summary."""
     import torch
