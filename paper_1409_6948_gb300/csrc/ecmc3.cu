@@ -335,6 +335,8 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
   const float* FP = F[axp];
   const float* FQ = F[axq];
   const double INF = __longlong_as_double(0x7ff0000000000000ll);
+  // keys id * 27 + image below 2^32 - 1: the reduction below may use 32-bit minima
+  const bool key32 = g.N * 27 < ((int64_t)1 << 32) - 27;
   double sum_b = 0.0;
   int n_ev = 0, n_li = 0, n_fr = 0, n_wa = 0, n_ch = 0;
   for (int k = 0; k < g.n_m; ++k) {
@@ -424,17 +426,36 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
           bj = j;
         }
       }
+      if (key32) {
+        // the first hit by (s, key) with three hardware minima: s >= +0 (or
+        // +inf) orders as its bit pattern, compared high word then low word,
+        // and keys below 2^32 break exact ties; lanes without a candidate
+        // hold (+inf, max key)
+        const unsigned long long sb = (unsigned long long)dbits(bs);
+        const unsigned hi = (unsigned)(sb >> 32), lo = (unsigned)sb;
+        const unsigned mhi = __reduce_min_sync(FULL, hi);
+        const unsigned mlo = __reduce_min_sync(FULL, hi == mhi ? lo : 0xffffffffu);
+        const bool at = hi == mhi && lo == mlo;
+        const unsigned k32 = bk == LLONG_MAX ? 0xffffffffu : (unsigned)bk;
+        const unsigned mk = __reduce_min_sync(FULL, at ? k32 : 0xffffffffu);
+        const int win = __ffs(__ballot_sync(FULL, at && k32 == mk)) - 1;
+        bs = __shfl_sync(FULL, bs, win);
+        bb = __shfl_sync(FULL, bb, win);
+        bk = __shfl_sync(FULL, bk, win);
+        bj = __shfl_sync(FULL, bj, win);
+      } else {
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const double os = __shfl_xor_sync(FULL, bs, off);
-        const double ob = __shfl_xor_sync(FULL, bb, off);
-        const long long ok2 = __shfl_xor_sync(FULL, bk, off);
-        const int oj = __shfl_xor_sync(FULL, bj, off);
-        if (first_before(os, ok2, bs, bk)) {
-          bs = os;
-          bb = ob;
-          bk = ok2;
-          bj = oj;
+        for (int off = 16; off > 0; off >>= 1) {
+          const double os = __shfl_xor_sync(FULL, bs, off);
+          const double ob = __shfl_xor_sync(FULL, bb, off);
+          const long long ok2 = __shfl_xor_sync(FULL, bk, off);
+          const int oj = __shfl_xor_sync(FULL, bj, off);
+          if (first_before(os, ok2, bs, bk)) {
+            bs = os;
+            bb = ob;
+            bk = ok2;
+            bj = oj;
+          }
         }
       }
       __syncwarp();
