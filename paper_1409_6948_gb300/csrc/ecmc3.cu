@@ -45,7 +45,9 @@ using ecmc::flip_if;
 using ecmc::le_nn;
 using ecmc::lt_nn;
 using ecmc::philox;
+using ecmc::plus_zero;
 using ecmc::sqrt_rn;
+using ecmc::to_float_trunc;
 using ecmc::unit_double;
 using ecmc::wrap_box0;
 using ecmc::wrap_half;
@@ -62,11 +64,12 @@ struct Geom3 {
   uint64_t seed, replica;
   int cap_mem, cap_obj;  // bucket slots per cell; frame objects per cell
   int warp_bytes;        // shared memory of one warp's frame
-  // FP32 screen: frame coordinates lie in (-sigma, w + sigma) and round to
-  // FP32 with error <= 2^-24 M (M >= w + sigma), so FP32 differences are
-  // within d = 4 2^-24 M of the FP64 ones; a hit (b > 0, c^2 < sigma^2)
-  // then has b32 > -d and c2_32 < sigma^2 + 4 d sigma + 2 d^2 + FP32
-  // rounding; the thresholds below are twice those bounds
+  // FP32 screen: frame coordinates lie in (-sigma, w + sigma) and are
+  // truncated to FP32 (integer pipes) with error < 2^-23 M (M >= w + sigma),
+  // so FP32 differences (two truncations and one FP32 rounding of at most
+  // 2^-24 2M) are within d = 8 2^-24 M of the FP64 ones; a hit (b > 0,
+  // c^2 < sigma^2) then has b32 > -d and c2_32 < sigma^2 + 4 d sigma +
+  // 2 d^2 + FP32 rounding; the thresholds below are twice those bounds
   float scr_b;           // pass iff b32 > -scr_b
   float scr_c2;          // pass iff c2_32 < scr_c2
   // L >= 2 (w + sigma): a periodic image X0 +- L of a wrapped coordinate
@@ -191,7 +194,8 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
   int* sid = reinterpret_cast<int*>(F[2] + g.cap_obj);  // members sorted by id
   int* raw = sid + g.cap_mem;                           // members as bucketed
   int* nbl = raw + g.cap_mem;                           // 26 neighbour cells + count
-  int* cand = nbl + 28;                                 // FP32 screen survivors
+  int* npre = nbl + 28;                                 // their bucket sizes, prefix sums
+  int* cand = npre + 28;                                // FP32 screen survivors
   int* ord = cand + g.cap_obj;                          // objects sorted by bin
   const int nb = g.nbin, nb2 = nb * nb;
   int* bst = ord + g.cap_obj;                           // bin starts, nb2 + 1
@@ -217,6 +221,21 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
     nbl[26] = n;
   }
   __syncwarp();
+  // the neighbours' objects as one list: npre[e] = sum of the bucket sizes
+  // of neighbours 0 .. e-1
+  const int nnb = nbl[26];
+  {
+    const int nq = lane < nnb ? min(cnt[nbl[lane]], g.cap_mem) : 0;
+    int incl = nq;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(FULL, incl, off);
+      if (lane >= off) incl += v;
+    }
+    if (lane == 0) npre[0] = 0;
+    if (lane < nnb) npre[lane + 1] = incl;
+  }
+  __syncwarp();
   // members in ascending id: the rank of each is the number of smaller ids
   for (int k = lane; k < nmem; k += 32) {
     const int v = raw[k];
@@ -232,25 +251,31 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
     C[0][q] = wrap_half_i(ldpos<CG>(px + i) - o[0], L, hL);
     C[1][q] = wrap_half_i(ldpos<CG>(py + i) - o[1], L, hL);
     C[2][q] = wrap_half_i(ldpos<CG>(pz + i) - o[2], L, hL);
-    F[0][q] = (float)C[0][q];
-    F[1][q] = (float)C[1][q];
-    F[2][q] = (float)C[2][q];
+    F[0][q] = to_float_trunc(C[0][q]);
+    F[1][q] = to_float_trunc(C[1][q]);
+    F[2][q] = to_float_trunc(C[2][q]);
     key[q] = (long long)i * 27 + 13;
   }
-  // frozen images, appended in lane order (warp prefix sums)
+  // frozen images, appended in the order (neighbour, bucket slot, image):
+  // 32 entries of the neighbours' joint list per round, warp prefix sums
   int nobj = nmem;
-  const int nnb = nbl[26];
   const double lo = -g.sigma, hi = w + g.sigma;
-  for (int e = 0; e < nnb; ++e) {
-    const int q = nbl[e];
-    const int nq = min(cnt[q], g.cap_mem);
-    for (int k0 = 0; k0 < nq; k0 += 32) {
-      const int k = k0 + lane;
+  const int ntot = npre[nnb];
+  for (int t0 = 0; t0 < ntot; t0 += 32) {
+    {
+      const int t = t0 + lane;
       double X0[3] = {0.0, 0.0, 0.0};
       int id = 0;
       unsigned mask = 0u;  // bit img = (kx+1)*9 + (ky+1)*3 + (kz+1)
-      if (k < nq) {
-        id = ids[(int64_t)q * g.cap_mem + k];
+      if (t < ntot) {
+        // the neighbour e with npre[e] <= t < npre[e + 1]
+        int el = 0, eh = nnb;
+        while (eh - el > 1) {
+          const int mid = (el + eh) >> 1;
+          if (npre[mid] <= t) el = mid;
+          else eh = mid;
+        }
+        id = ids[(int64_t)nbl[el] * g.cap_mem + (t - npre[el])];
         X0[0] = wrap_half_i(ldpos<CG>(px + id) - o[0], L, hL);
         X0[1] = wrap_half_i(ldpos<CG>(py + id) - o[1], L, hL);
         X0[2] = wrap_half_i(ldpos<CG>(pz + id) - o[2], L, hL);
@@ -286,13 +311,15 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
         const int img = __ffs(mask) - 1;
         mask &= mask - 1;
         if (slot < g.cap_obj) {
+          // X0 + k L for k in {-1, 0, 1}: (double)k * L is -L, +0.0 or L
+          // exactly, and adding +0.0 only turns -0.0 into +0.0
           const int kx = img / 9 - 1, ky = (img / 3) % 3 - 1, kz = img % 3 - 1;
-          C[0][slot] = X0[0] + (double)kx * L;
-          C[1][slot] = X0[1] + (double)ky * L;
-          C[2][slot] = X0[2] + (double)kz * L;
-          F[0][slot] = (float)C[0][slot];
-          F[1][slot] = (float)C[1][slot];
-          F[2][slot] = (float)C[2][slot];
+          C[0][slot] = kx == 0 ? plus_zero(X0[0]) : X0[0] + (kx > 0 ? L : -L);
+          C[1][slot] = ky == 0 ? plus_zero(X0[1]) : X0[1] + (ky > 0 ? L : -L);
+          C[2][slot] = kz == 0 ? plus_zero(X0[2]) : X0[2] + (kz > 0 ? L : -L);
+          F[0][slot] = to_float_trunc(C[0][slot]);
+          F[1][slot] = to_float_trunc(C[1][slot]);
+          F[2][slot] = to_float_trunc(C[2][slot]);
           key[slot] = (long long)id * 27 + img;
         }
         ++slot;
@@ -462,19 +489,25 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
       if (le_nn(r, bs) && le_nn(r, sw)) {  // budget used up
         if (lane == 0) {
           CA[m] = P + (sg > 0 ? r : -r);
-          FA[m] = (float)CA[m];
+          FA[m] = to_float_trunc(CA[m]);
         }
         break;
       }
       if (le_nn(bs, sw)) {  // contact
+        // one FP64 addition gives three results: lane 0 the mover's new
+        // coordinate P +- bs, lane 2 the contact term bb - bs (summed on
+        // lane 2), every other lane the budget left, r - bs; x - y is by
+        // definition x + (-y), so each equals its separate expression
+        const double z = (lane == 0 ? P : (lane == 2 ? bb : r)) +
+                         flip_if(bs, lane == 0 ? sg < 0 : true);
         if (lane == 0) {
-          CA[m] = P + (sg > 0 ? bs : -bs);
-          FA[m] = (float)CA[m];
+          CA[m] = z;
+          FA[m] = to_float_trunc(z);
         }
-        r = r - bs;
+        if (lane == 2) sum_b += z;
+        r = __shfl_sync(FULL, z, 1);
         ++n_ev;
         ++ch_ev;
-        sum_b += bb - bs;
         if (bj < nmem) {  // lift
           ++n_li;
           m = bj;
@@ -486,7 +519,7 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
       } else {  // wall: onto the wall, back along the axis
         if (lane == 0) {
           CA[m] = sg > 0 ? w : 0.0;
-          FA[m] = (float)CA[m];
+          FA[m] = to_float_trunc(CA[m]);
         }
         r = r - sw;
         sg = -sg;
@@ -511,6 +544,7 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
     py[i] = wrap_box0(C[1][q] + o[1], L);
     pz[i] = wrap_box0(C[2][q] + o[2], L);
   }
+  sum_b = __shfl_sync(FULL, sum_b, 2);  // the contact sum is kept on lane 2
   if (lane == 0) {
     Cell3 s;
     s.sum_b = sum_b;
@@ -922,7 +956,7 @@ int layout3(ecmc3_ctx* h) {
   g.warp_bytes = (int)(((size_t)g.cap_obj * (3 * sizeof(double) + sizeof(long long) +
                                              3 * sizeof(float) + 2 * sizeof(int)) +
                         (size_t)(2 * g.nbin * g.nbin + 1) * sizeof(int) +
-                        (size_t)g.cap_mem * 2 * sizeof(int) + 28 * sizeof(int) +
+                        (size_t)g.cap_mem * 2 * sizeof(int) + 56 * sizeof(int) +
                         (size_t)g.cap_mem + 15) &
                        ~(size_t)15);
   int dev = 0, optin = 0, n_sm = 0;
@@ -1007,7 +1041,7 @@ int ecmc3_create(ecmc3_t* out, int64_t N, double L, double sigma, int cells, dou
   g.replica = 0;
   {
     const double M = g.w + 2.0 * sigma;
-    const double d = 4.0 * std::ldexp(1.0, -24) * M;
+    const double d = 8.0 * std::ldexp(1.0, -24) * M;
     g.scr_b = (float)(2.0 * d);
     const double c2 = sigma * sigma + 4.0 * d * sigma + 2.0 * d * d +
                       4.0 * std::ldexp(1.0, -24) * (sigma * sigma + 4.0 * M * M);

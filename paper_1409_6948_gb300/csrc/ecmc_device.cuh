@@ -131,12 +131,19 @@ __device__ __forceinline__ long long dkey(double v) {
 __device__ __forceinline__ bool dlt(double a, double b) { return dkey(a) < dkey(b); }
 __device__ __forceinline__ bool dle(double a, double b) { return dkey(a) <= dkey(b); }
 
-// periodic wrap into [-L/2, L/2) for |v| < 3L/2 (hL = L/2), comparisons on
-// the integer pipes; the additions are the same as in wrap_half
+// periodic wrap into [-L/2, L/2) for |v| < 3L/2 (hL = L/2), the result of
+// wrap_half: comparisons on the integer pipes and one FP64 addition whatever
+// the branch (v - L is by definition v + (-L), rounded alike)
 __device__ __forceinline__ double wrap_half_i(double v, double L, double hL) {
-  if (!dlt(v, hL)) return v - L;
-  if (dlt(v, -hL)) return v + L;
-  return v;
+  const bool up = !dlt(v, hL), down = dlt(v, -hL);
+  const double r = v + (up ? -L : L);
+  return (up || down) ? r : v;
+}
+
+// v + (+0.0) without the FP64 pipe: -0.0 becomes +0.0, every other finite
+// value is unchanged
+__device__ __forceinline__ double plus_zero(double v) {
+  return __double_as_longlong(v) == (long long)0x8000000000000000ull ? 0.0 : v;
 }
 
 }  // namespace ecmc
