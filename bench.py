@@ -535,7 +535,7 @@ def run_dim3(args):
     L = W.box_side3(N, eta)
     lam0 = 0.06  # mean free path at eta = 0.45 (the points report their own)
     pts = []
-    for cells in ((args.cells,) if args.cells else (16, 20, 26)):
+    for cells in ((args.cells,) if args.cells else (16, 20, 26, 32)):
         for ell in ((args.ell,) if args.ell else (0.5, 1.0, 2.0)):
             nm = max(1, int(round(N / cells**3 * lam0 / ell)))
             g = P.Ecmc3(N, L, 1.0, cells, ell, seed)

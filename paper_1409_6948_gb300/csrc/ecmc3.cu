@@ -204,9 +204,20 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
 
   const int nmem = min(cnt[c], g.cap_mem);
   for (int k = lane; k < nmem; k += 32) raw[k] = ids[(int64_t)c * g.cap_mem + k];
-  if (lane == 0) {
-    // the distinct neighbour cells (with two cells per side the cells at
-    // offsets -1 and +1 coincide)
+  if (nc >= 3) {
+    // 26 distinct neighbour cells: lane e takes offset e of the 3x3x3 block
+    // in (dz, dy, dx) order, the centre skipped
+    if (lane < 26) {
+      const int e = lane < 13 ? lane : lane + 1;
+      int qx = cx + e % 3 - 1, qy = cy + (e / 3) % 3 - 1, qz = cz + e / 9 - 1;
+      qx = qx < 0 ? qx + nc : (qx >= nc ? qx - nc : qx);
+      qy = qy < 0 ? qy + nc : (qy >= nc ? qy - nc : qy);
+      qz = qz < 0 ? qz + nc : (qz >= nc ? qz - nc : qz);
+      nbl[lane] = (qz * nc + qy) * nc + qx;
+    }
+    if (lane == 0) nbl[26] = 26;
+  } else if (lane == 0) {
+    // two cells per side: the cells at offsets -1 and +1 coincide
     int n = 0;
     for (int dz = -1; dz <= 1; ++dz)
       for (int dy = -1; dy <= 1; ++dy)
@@ -235,55 +246,54 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
     if (lane == 0) npre[0] = 0;
     if (lane < nnb) npre[lane + 1] = incl;
   }
-  __syncwarp();
-  // members in ascending id: the rank of each is the number of smaller ids
+  // members in ascending id (the rank of each is the number of smaller
+  // ids); the positions are loaded before the rank is counted
+  const double hL = 0.5 * L;
   for (int k = lane; k < nmem; k += 32) {
     const int v = raw[k];
+    const double mx = ldpos<CG>(px + v), my = ldpos<CG>(py + v), mz = ldpos<CG>(pz + v);
     int r = 0;
     for (int j = 0; j < nmem; ++j) r += raw[j] < v ? 1 : 0;
     sid[r] = v;
     touched[r] = 0;
+    C[0][r] = wrap_half_i(mx - o[0], L, hL);
+    C[1][r] = wrap_half_i(my - o[1], L, hL);
+    C[2][r] = wrap_half_i(mz - o[2], L, hL);
+    F[0][r] = to_float_trunc(C[0][r]);
+    F[1][r] = to_float_trunc(C[1][r]);
+    F[2][r] = to_float_trunc(C[2][r]);
+    key[r] = (long long)v * 27 + 13;
   }
   __syncwarp();
-  const double hL = 0.5 * L;
-  for (int q = lane; q < nmem; q += 32) {
-    const int i = sid[q];
-    C[0][q] = wrap_half_i(ldpos<CG>(px + i) - o[0], L, hL);
-    C[1][q] = wrap_half_i(ldpos<CG>(py + i) - o[1], L, hL);
-    C[2][q] = wrap_half_i(ldpos<CG>(pz + i) - o[2], L, hL);
-    F[0][q] = to_float_trunc(C[0][q]);
-    F[1][q] = to_float_trunc(C[1][q]);
-    F[2][q] = to_float_trunc(C[2][q]);
-    key[q] = (long long)i * 27 + 13;
-  }
   // frozen images, appended in the order (neighbour, bucket slot, image):
   // 32 entries of the neighbours' joint list per round, warp prefix sums
   int nobj = nmem;
   const double lo = -g.sigma, hi = w + g.sigma;
   const int ntot = npre[nnb];
-  for (int t0 = 0; t0 < ntot; t0 += 32) {
-    {
-      const int t = t0 + lane;
-      double X0[3] = {0.0, 0.0, 0.0};
-      int id = 0;
-      unsigned mask = 0u;  // bit img = (kx+1)*9 + (ky+1)*3 + (kz+1)
-      if (t < ntot) {
-        // the neighbour e with npre[e] <= t < npre[e + 1]
-        int el = 0, eh = nnb;
-        while (eh - el > 1) {
-          const int mid = (el + eh) >> 1;
-          if (npre[mid] <= t) el = mid;
-          else eh = mid;
-        }
-        id = ids[(int64_t)nbl[el] * g.cap_mem + (t - npre[el])];
-        X0[0] = wrap_half_i(ldpos<CG>(px + id) - o[0], L, hL);
-        X0[1] = wrap_half_i(ldpos<CG>(py + id) - o[1], L, hL);
-        X0[2] = wrap_half_i(ldpos<CG>(pz + id) - o[2], L, hL);
-        if (g.single_image) {
-          if (dlt(lo, X0[0]) && dlt(X0[0], hi) && dlt(lo, X0[1]) && dlt(X0[1], hi) &&
-              dlt(lo, X0[2]) && dlt(X0[2], hi))
-            mask = 1u << 13;
-        } else {
+  // the bucket slot of entry t of the joint list (t < ntot)
+  auto slot_of = [&](int t) {
+    int el = 0, eh = nnb;  // the neighbour e with npre[e] <= t < npre[e + 1]
+    while (eh - el > 1) {
+      const int mid = (el + eh) >> 1;
+      if (npre[mid] <= t) el = mid;
+      else eh = mid;
+    }
+    return (int64_t)nbl[el] * g.cap_mem + (t - npre[el]);
+  };
+  // one round: the entries of 32 lanes (valid where in) with their box
+  // positions p, appended as frame objects in lane order
+  auto append = [&](bool in, int id, const double* p) {
+    double X0[3] = {0.0, 0.0, 0.0};
+    unsigned mask = 0u;  // bit img = (kx+1)*9 + (ky+1)*3 + (kz+1)
+    if (in) {
+      X0[0] = wrap_half_i(p[0] - o[0], L, hL);
+      X0[1] = wrap_half_i(p[1] - o[1], L, hL);
+      X0[2] = wrap_half_i(p[2] - o[2], L, hL);
+      if (g.single_image) {
+        if (dlt(lo, X0[0]) && dlt(X0[0], hi) && dlt(lo, X0[1]) && dlt(X0[1], hi) &&
+            dlt(lo, X0[2]) && dlt(X0[2], hi))
+          mask = 1u << 13;
+      } else {
         for (int kx = -1; kx <= 1; ++kx) {
           const double X = X0[0] + (double)kx * L;
           if (!(X > lo && X < hi)) continue;
@@ -297,35 +307,55 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
             }
           }
         }
-        }
       }
-      const int nimg = __popc(mask);
-      int incl = nimg;
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const int v = __shfl_up_sync(FULL, incl, off);
-        if (lane >= off) incl += v;
-      }
-      int slot = nobj + incl - nimg;
-      while (mask) {
-        const int img = __ffs(mask) - 1;
-        mask &= mask - 1;
-        if (slot < g.cap_obj) {
-          // X0 + k L for k in {-1, 0, 1}: (double)k * L is -L, +0.0 or L
-          // exactly, and adding +0.0 only turns -0.0 into +0.0
-          const int kx = img / 9 - 1, ky = (img / 3) % 3 - 1, kz = img % 3 - 1;
-          C[0][slot] = kx == 0 ? plus_zero(X0[0]) : X0[0] + (kx > 0 ? L : -L);
-          C[1][slot] = ky == 0 ? plus_zero(X0[1]) : X0[1] + (ky > 0 ? L : -L);
-          C[2][slot] = kz == 0 ? plus_zero(X0[2]) : X0[2] + (kz > 0 ? L : -L);
-          F[0][slot] = to_float_trunc(C[0][slot]);
-          F[1][slot] = to_float_trunc(C[1][slot]);
-          F[2][slot] = to_float_trunc(C[2][slot]);
-          key[slot] = (long long)id * 27 + img;
-        }
-        ++slot;
-      }
-      nobj += __shfl_sync(FULL, incl, 31);
     }
+    const int nimg = __popc(mask);
+    int incl = nimg;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(FULL, incl, off);
+      if (lane >= off) incl += v;
+    }
+    int slot = nobj + incl - nimg;
+    while (mask) {
+      const int img = __ffs(mask) - 1;
+      mask &= mask - 1;
+      if (slot < g.cap_obj) {
+        // X0 + k L for k in {-1, 0, 1}: (double)k * L is -L, +0.0 or L
+        // exactly, and adding +0.0 only turns -0.0 into +0.0
+        const int kx = img / 9 - 1, ky = (img / 3) % 3 - 1, kz = img % 3 - 1;
+        C[0][slot] = kx == 0 ? plus_zero(X0[0]) : X0[0] + (kx > 0 ? L : -L);
+        C[1][slot] = ky == 0 ? plus_zero(X0[1]) : X0[1] + (ky > 0 ? L : -L);
+        C[2][slot] = kz == 0 ? plus_zero(X0[2]) : X0[2] + (kz > 0 ? L : -L);
+        F[0][slot] = to_float_trunc(C[0][slot]);
+        F[1][slot] = to_float_trunc(C[1][slot]);
+        F[2][slot] = to_float_trunc(C[2][slot]);
+        key[slot] = (long long)id * 27 + img;
+      }
+      ++slot;
+    }
+    nobj += __shfl_sync(FULL, incl, 31);
+  };
+  // two rounds per pass, their loads issued together so that the L2
+  // latencies overlap
+  for (int t0 = 0; t0 < ntot; t0 += 64) {
+    const int ta = t0 + lane, tb = t0 + 32 + lane;
+    const bool ina = ta < ntot, inb = tb < ntot;
+    const int ida = ina ? ids[slot_of(ta)] : 0;
+    const int idb = inb ? ids[slot_of(tb)] : 0;
+    double pa[3] = {0.0, 0.0, 0.0}, pb[3] = {0.0, 0.0, 0.0};
+    if (ina) {
+      pa[0] = ldpos<CG>(px + ida);
+      pa[1] = ldpos<CG>(py + ida);
+      pa[2] = ldpos<CG>(pz + ida);
+    }
+    if (inb) {
+      pb[0] = ldpos<CG>(px + idb);
+      pb[1] = ldpos<CG>(py + idb);
+      pb[2] = ldpos<CG>(pz + idb);
+    }
+    append(ina, ida, pa);
+    if (t0 + 32 < ntot) append(inb, idb, pb);
   }
   const bool ok = nobj <= g.cap_obj;
   if (!ok && lane == 0) atomicCAS(err, kOk, kCapacity);
