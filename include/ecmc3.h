@@ -57,6 +57,13 @@ typedef struct ecmc3_ctx* ecmc3_t;
  * sweep reports ECMC_ERR_TIMEOUT (no device fault; the handle recovers when
  * positions are set again). */
 #define ECMC3_PARAM_WAIT_TEST 17
+/* 1 (default): a chain found to rattle periodically (after a turn-back, the
+ * state the next leg starts from equals the one 2, 4, ... or 16 legs
+ * earlier, with every sphere moved in between back in place, bit for bit)
+ * repeats the recorded legs without searching for contacts until the budget
+ * runs out; 0: every leg searched.  Same results bit for bit; the replayed
+ * legs are counted in ecmc_counters_t.replayed_legs. */
+#define ECMC3_PARAM_REPLAY 14
 
 /* N spheres of diameter sigma in a periodic cube of side L, cells^3 cubic
  * cells (cells even, >= 2, L / cells > sigma), chains of total displacement
@@ -93,7 +100,7 @@ ECMC_API int ecmc3_synchronize(ecmc3_t h);
 /* Sweep counter t of the next sweep. */
 ECMC_API int ecmc3_sweep_index(ecmc3_t h, int64_t* t);
 
-/* Counters since the last reset (replayed_legs and rejected_chains are 0). */
+/* Counters since the last reset (rejected_chains is 0). */
 ECMC_API int ecmc3_counters(ecmc3_t h, ecmc_counters_t* out);
 
 /* beta P sigma^3 = rho sigma^3 (1 + sum_b_w / sum_disp_w) over the sweeps

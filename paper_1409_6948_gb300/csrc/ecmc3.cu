@@ -83,6 +83,7 @@ struct Geom3 {
   // the FP32 rounding of the coordinates the bin index is computed from
   int nbin;
   float inv_hb;          // 1 / bin side
+  int replay;            // replay periodic rattles (results unchanged)
 };
 
 struct State3 {
@@ -94,13 +95,17 @@ struct State3 {
 
 struct Cell3 {
   double sum_b;
-  int events, lifts, frozen, walls, chains, n_mem;
+  int events, lifts, frozen, walls, chains, n_mem, replayed;
 };
 
 struct Totals3 {
   double sum_b, sum_disp, sum_b_w, sum_disp_w;
-  long long sweeps, chains, events, lifts, frozen, walls;
+  long long sweeps, chains, events, lifts, frozen, walls, replayed;
 };
+
+// Legs of the current chain kept for the replay of periodic rattles (a
+// power of two: the ring index is the leg number's low bits)
+constexpr int kHist3 = 16;
 
 // ---- kernels ----------------------------------------------------------------
 
@@ -187,15 +192,24 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
   C[1] = C[0] + g.cap_obj;
   C[2] = C[1] + g.cap_obj;
   long long* key = reinterpret_cast<long long*>(C[2] + g.cap_obj);
+  // the chain's last kHist3 legs: start and end coordinate of the active
+  // sphere along the axis, length, contact term bb - bs
+  double* hP = reinterpret_cast<double*>(key + g.cap_obj);
+  double* hE = hP + kHist3;
+  double* hS = hE + kHist3;
+  double* hT = hS + kHist3;
   float* F[3];  // FP32 roundings of C, kept current as members move
-  F[0] = reinterpret_cast<float*>(key + g.cap_obj);
+  F[0] = reinterpret_cast<float*>(hT + kHist3);
   F[1] = F[0] + g.cap_obj;
   F[2] = F[1] + g.cap_obj;
   int* sid = reinterpret_cast<int*>(F[2] + g.cap_obj);  // members sorted by id
   int* raw = sid + g.cap_mem;                           // members as bucketed
   int* nbl = raw + g.cap_mem;                           // 26 neighbour cells + count
   int* npre = nbl + 28;                                 // their bucket sizes, prefix sums
-  int* cand = npre + 28;                                // FP32 screen survivors
+  int* hM = npre + 28;    // legs: active sphere, direction, kind (0 lift, 1 frozen, 2 wall)
+  int* hSg = hM + kHist3;
+  int* hK = hSg + kHist3;
+  int* cand = hK + kHist3;                              // FP32 screen survivors
   int* ord = cand + g.cap_obj;                          // objects sorted by bin
   const int nb = g.nbin, nb2 = nb * nb;
   int* bst = ord + g.cap_obj;                           // bin starts, nb2 + 1
@@ -395,7 +409,7 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
   // keys id * 27 + image below 2^32 - 1: the reduction below may use 32-bit minima
   const bool key32 = g.N * 27 < ((int64_t)1 << 32) - 27;
   double sum_b = 0.0;
-  int n_ev = 0, n_li = 0, n_fr = 0, n_wa = 0, n_ch = 0;
+  int n_ev = 0, n_li = 0, n_fr = 0, n_wa = 0, n_ch = 0, n_rep = 0;
   for (int k = 0; k < g.n_m; ++k) {
     int* rec = recs != nullptr ? recs + 4 * ((int64_t)c * g.n_m + k) : nullptr;
     if (!ok || nmem == 0) {
@@ -414,10 +428,12 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
     const int start_id = sid[m];
     double r = g.ell;
     int ch_ev = 0, ch_wa = 0;
+    int n_leg = 0;        // legs recorded in the history
+    int64_t ch_rep = 0;   // legs of this chain replayed
     if (lane == 0) touched[m] = 1;
     ++n_ch;
     for (int64_t iter = 0;; ++iter) {
-      if (iter >= ecmc::kMaxEventsPerChain) {
+      if (iter + ch_rep >= ecmc::kMaxEventsPerChain) {
         if (lane == 0) atomicCAS(err, kOk, kChainCap);
         break;
       }
@@ -523,6 +539,8 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
         }
         break;
       }
+      const int hi = n_leg & (kHist3 - 1);
+      int kind;
       if (le_nn(bs, sw)) {  // contact
         // one FP64 addition gives three results: lane 0 the mover's new
         // coordinate P +- bs, lane 2 the contact term bb - bs (summed on
@@ -530,15 +548,25 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
         // definition x + (-y), so each equals its separate expression
         const double z = (lane == 0 ? P : (lane == 2 ? bb : r)) +
                          flip_if(bs, lane == 0 ? sg < 0 : true);
+        kind = bj < nmem ? 0 : 1;
         if (lane == 0) {
           CA[m] = z;
           FA[m] = to_float_trunc(z);
+          hP[hi] = P;
+          hE[hi] = z;
+          hS[hi] = bs;
+          hM[hi] = m;
+          hSg[hi] = sg;
+          hK[hi] = kind;
         }
-        if (lane == 2) sum_b += z;
+        if (lane == 2) {
+          sum_b += z;
+          hT[hi] = z;
+        }
         r = __shfl_sync(FULL, z, 1);
         ++n_ev;
         ++ch_ev;
-        if (bj < nmem) {  // lift
+        if (kind == 0) {  // lift
           ++n_li;
           m = bj;
           if (lane == 0) touched[m] = 1;
@@ -547,14 +575,87 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
           ++n_fr;
         }
       } else {  // wall: onto the wall, back along the axis
+        kind = 2;
         if (lane == 0) {
           CA[m] = sg > 0 ? w : 0.0;
           FA[m] = to_float_trunc(CA[m]);
+          hP[hi] = P;
+          hE[hi] = CA[m];
+          hS[hi] = sw;
+          hM[hi] = m;
+          hSg[hi] = sg;
+          hK[hi] = 2;
         }
         r = r - sw;
         sg = -sg;
         ++n_wa;
         ++ch_wa;
+      }
+      ++n_leg;
+      if (g.replay && kind != 0 && n_leg >= kHist3) {
+        // Replay of a periodic rattle.  After a turn-back, lane l tests the
+        // period K = 2 (l + 1): the next leg starts from the state (active
+        // sphere, direction, coordinate bit for bit) that leg n_leg - K
+        // started from, and every sphere active in those K legs is back at
+        // its coordinate at the start of its first of them.  Frozen spheres
+        // and walls do not move, so the whole frame is then as it was K
+        // legs ago and, the dynamics being deterministic with the budget
+        // entering a leg only through its end, the following legs repeat
+        // the recorded ones for as long as the budget exceeds their length.
+        __syncwarp();
+        bool per = false;
+        if (lane < kHist3 / 2) {
+          const int K = 2 * (lane + 1);
+          const int i0 = (n_leg - K) & (kHist3 - 1);
+          if (hM[i0] == m && hSg[i0] == sg && dbits(hP[i0]) == dbits(CA[m])) {
+            per = true;
+            for (int j = 1; j < K; ++j) {
+              const int ij = (n_leg - K + j) & (kHist3 - 1);
+              const int d = hM[ij];
+              bool first = true;
+              for (int i = 0; i < j; ++i) first = first && hM[(n_leg - K + i) & (kHist3 - 1)] != d;
+              if (first && dbits(CA[d]) != dbits(hP[ij])) per = false;
+            }
+          }
+        }
+        const unsigned pb = __ballot_sync(FULL, per);
+        if (pb != 0u) {
+          const int K = 2 * __ffs(pb), b0 = n_leg - K;
+          int j = 0;
+          for (;;) {  // whole legs while the budget exceeds them
+            const int ij = (b0 + j) & (kHist3 - 1);
+            const double st_j = hS[ij];
+            if (le_nn(r, st_j) || iter + ch_rep + 1 >= ecmc::kMaxEventsPerChain) break;
+            r = r - st_j;
+            const int kd = hK[ij];
+            if (kd == 2) {
+              ++n_wa;
+              ++ch_wa;
+            } else {
+              ++n_ev;
+              ++ch_ev;
+              if (kd == 0) ++n_li;
+              else ++n_fr;
+              if (lane == 2) sum_b += hT[ij];
+            }
+            ++ch_rep;
+            ++n_rep;
+            j = j + 1 == K ? 0 : j + 1;
+          }
+          // the frame is as at the start of leg b0 (and of every K legs
+          // after it); the recorded legs b0 .. b0 + j - 1 bring it to the
+          // start of the leg in which the budget runs out, which the full
+          // search then takes
+          if (lane == 0)
+            for (int i = 0; i < j; ++i) {
+              const int ii = (b0 + i) & (kHist3 - 1);
+              CA[hM[ii]] = hE[ii];
+              FA[hM[ii]] = to_float_trunc(hE[ii]);
+            }
+          m = hM[(b0 + j) & (kHist3 - 1)];
+          sg = hSg[(b0 + j) & (kHist3 - 1)];
+          n_leg = 0;
+        }
       }
     }
     __syncwarp();
@@ -584,6 +685,7 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
     s.walls = n_wa;
     s.chains = n_ch;
     s.n_mem = nmem;
+    s.replayed = n_rep;
     cs[c] = s;
   }
 }
@@ -691,10 +793,10 @@ __global__ void __launch_bounds__(32 * kWarpsMax) k3_sweep(
 __global__ void __launch_bounds__(256) k3_end(Geom3 g, State3* st, const Cell3* __restrict__ cs,
                                              Totals3* tot, double* history, int64_t* hist_len) {
   __shared__ double sd[2][8];
-  __shared__ long long sl[5][8];
+  __shared__ long long sl[6][8];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   double b = 0.0, bw = 0.0;
-  long long v[5] = {0, 0, 0, 0, 0};
+  long long v[6] = {0, 0, 0, 0, 0, 0};
   for (int c = tid; c < g.ncell; c += 256) {
     const Cell3 s = cs[c];
     b += s.sum_b;
@@ -704,25 +806,26 @@ __global__ void __launch_bounds__(256) k3_end(Geom3 g, State3* st, const Cell3* 
     v[2] += s.frozen;
     v[3] += s.walls;
     v[4] += s.chains;
+    v[5] += s.replayed;
   }
   for (int off = 16; off > 0; off >>= 1) {
     b += __shfl_down_sync(0xffffffffu, b, off);
     bw += __shfl_down_sync(0xffffffffu, bw, off);
-    for (int q = 0; q < 5; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], off);
+    for (int q = 0; q < 6; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], off);
   }
   if (lane == 0) {
     sd[0][wid] = b;
     sd[1][wid] = bw;
-    for (int q = 0; q < 5; ++q) sl[q][wid] = v[q];
+    for (int q = 0; q < 6; ++q) sl[q][wid] = v[q];
   }
   __syncthreads();
   if (tid != 0) return;
   double B = 0.0, BW = 0.0;
-  long long V[5] = {0, 0, 0, 0, 0};
+  long long V[6] = {0, 0, 0, 0, 0, 0};
   for (int wv = 0; wv < 8; ++wv) {
     B += sd[0][wv];
     BW += sd[1][wv];
-    for (int q = 0; q < 5; ++q) V[q] += sl[q][wv];
+    for (int q = 0; q < 6; ++q) V[q] += sl[q][wv];
   }
   const double dw = (double)g.N * (double)g.n_m * g.ell;
   Totals3& T = *tot;
@@ -735,6 +838,7 @@ __global__ void __launch_bounds__(256) k3_end(Geom3 g, State3* st, const Cell3* 
   T.frozen += V[2];
   T.walls += V[3];
   T.chains += V[4];
+  T.replayed += V[5];
   T.sweeps += 1;
   const int64_t n = *hist_len;
   if (n < kHistoryCap) {
@@ -987,6 +1091,7 @@ int layout3(ecmc3_ctx* h) {
                                              3 * sizeof(float) + 2 * sizeof(int)) +
                         (size_t)(2 * g.nbin * g.nbin + 1) * sizeof(int) +
                         (size_t)g.cap_mem * 2 * sizeof(int) + 56 * sizeof(int) +
+                        (size_t)kHist3 * (4 * sizeof(double) + 3 * sizeof(int)) +
                         (size_t)g.cap_mem + 15) &
                        ~(size_t)15);
   int dev = 0, optin = 0, n_sm = 0;
@@ -1067,6 +1172,7 @@ int ecmc3_create(ecmc3_t* out, int64_t N, double L, double sigma, int cells, dou
   g.inv_w = 1.0 / g.w;
   g.ell = ell;
   g.n_m = 1;
+  g.replay = 1;
   g.seed = seed;
   g.replica = 0;
   {
@@ -1182,6 +1288,10 @@ int ecmc3_set_param(ecmc3_t h, int key, double v) {
       if (v != 0.0 && v != 1.0) return fail3(ECMC_ERR_ARG, "wait test must be 0 or 1");
       h->wait_test = (int)v;
       return ECMC_OK;
+    case ECMC3_PARAM_REPLAY:
+      if (v != 0.0 && v != 1.0) return fail3(ECMC_ERR_ARG, "replay must be 0 or 1");
+      h->g.replay = (int)v;
+      return ECMC_OK;
     default:
       return fail3(ECMC_ERR_ARG, "unknown parameter %d", key);
   }
@@ -1196,6 +1306,7 @@ int ecmc3_get_param(ecmc3_t h, int key, double* v) {
       return ECMC_OK;
     case ECMC3_PARAM_WAIT_LIMIT_MS: *v = (double)h->wait_ns * 1e-6; return ECMC_OK;
     case ECMC3_PARAM_WAIT_TEST: *v = h->wait_test; return ECMC_OK;
+    case ECMC3_PARAM_REPLAY: *v = h->g.replay; return ECMC_OK;
     default: return fail3(ECMC_ERR_ARG, "unknown parameter %d", key);
   }
 }
@@ -1272,6 +1383,7 @@ int ecmc3_counters(ecmc3_t h, ecmc_counters_t* out) {
   out->lifts = t.lifts;
   out->frozen_hits = t.frozen;
   out->wall_hits = t.walls;
+  out->replayed_legs = t.replayed;
   out->sum_b = t.sum_b;
   out->sum_disp = t.sum_disp;
   return ECMC_OK;

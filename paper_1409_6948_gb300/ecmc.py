@@ -460,6 +460,7 @@ PARAM3_REPLICA = 4
 PARAM3_PERSISTENT = 15
 PARAM3_WAIT_LIMIT_MS = 16
 PARAM3_WAIT_TEST = 17
+PARAM3_REPLAY = 14
 
 
 class Ecmc3:

@@ -29,11 +29,12 @@ from paper_1409_6948_gb300 import ecmc as E  # noqa: E402
 REL = 1e-12
 
 
-def make3(N, eta, cells, ell, nm, seed, persistent=1):
+def make3(N, eta, cells, ell, nm, seed, persistent=1, replay=1):
     L = W.box_side3(N, eta)
     g = P.Ecmc3(N, L, 1.0, cells, ell, seed)
     g.set_param(E.PARAM3_N_CHAINS, nm)
     g.set_param(E.PARAM3_PERSISTENT, persistent)
+    g.set_param(E.PARAM3_REPLAY, replay)
     p = oracle.make_params3(N, L, 1.0, cells, ell, nm, seed)
     return g, p, L
 
@@ -48,8 +49,8 @@ def assert_positions_equal(g, x, y, z, L):
     assert worst <= REL, "max relative position difference %g" % worst
 
 
-def run_pair3(N, eta, cells, ell, nm, seed, n_sweeps, persistent=1):
-    g, p, L = make3(N, eta, cells, ell, nm, seed, persistent)
+def run_pair3(N, eta, cells, ell, nm, seed, n_sweeps, persistent=1, replay=1, counters=None):
+    g, p, L = make3(N, eta, cells, ell, nm, seed, persistent, replay)
     assert g.get_param(E.PARAM3_PERSISTENT) == persistent
     x, y, z = W.cubic_lattice(N, L)
     tot = oracle.Stats()
@@ -75,6 +76,8 @@ def run_pair3(N, eta, cells, ell, nm, seed, n_sweeps, persistent=1):
     P_or = oracle.pressure_from_sums3(tot.sum_b_w, tot.sum_disp_w, N, L, 1.0)
     assert P_gpu == pytest.approx(P_or, rel=1e-11)
     assert g.sweep_index() == n_sweeps
+    if counters is not None:
+        counters.append(c)
     g.close()
     return tot
 
@@ -166,6 +169,33 @@ def test_pressure_matches_carnahan_starling():
     cs = (1 + eta + eta**2 - eta**3) / (1 - eta) ** 3
     assert abs(z - cs) < 4.0 * zse + 0.003 * cs, (z, cs, zse)
     g.close()
+
+
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_replayed_rattles_match_oracle(persistent):
+    # cells of 2.1 sigma and chains of 2 sigma at eta = 0.45: a few chains
+    # rattle between frozen spheres for hundreds of legs, and the replay of
+    # their periodic legs must leave every sweep as the oracle's full search
+    # does (binning, chain records, positions, counters, pressure)
+    cs = []
+    run_pair3(32768, 0.45, 16, 2.0, 1, 9, 10, persistent, replay=1, counters=cs)
+    assert cs[0].replayed_legs > 0
+
+
+def test_replay_on_and_off_are_bitwise_equal():
+    a, p, L = make3(32768, 0.45, 16, 2.0, 1, 9, replay=1)
+    b, p, L = make3(32768, 0.45, 16, 2.0, 1, 9, replay=0)
+    assert a.get_param(E.PARAM3_REPLAY) == 1 and b.get_param(E.PARAM3_REPLAY) == 0
+    a.sweep(20)
+    b.sweep(20)
+    assert np.array_equal(a.positions(), b.positions())
+    ca, cb = a.counters(), b.counters()
+    assert ca.events == cb.events and ca.lifts == cb.lifts and ca.sum_b == cb.sum_b
+    assert ca.frozen_hits == cb.frozen_hits and ca.wall_hits == cb.wall_hits
+    assert ca.replayed_legs > 0 and cb.replayed_legs == 0
+    assert a.pressure()[0] == b.pressure()[0]
+    a.close()
+    b.close()
 
 
 def test_persistent_and_per_phase_sweeps_are_bitwise_equal():
