@@ -592,19 +592,19 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
         ++ch_wa;
       }
       ++n_leg;
-      if (g.replay && kind != 0 && n_leg >= kHist3) {
+      if (g.replay && kind != 0 && n_leg >= 2) {
         // Replay of a periodic rattle.  After a turn-back, lane l tests the
-        // period K = 2 (l + 1): the next leg starts from the state (active
-        // sphere, direction, coordinate bit for bit) that leg n_leg - K
-        // started from, and every sphere active in those K legs is back at
-        // its coordinate at the start of its first of them.  Frozen spheres
+        // period K = 2 (l + 1) <= n_leg: the next leg starts from the state
+        // (active sphere, direction, coordinate bit for bit) that leg
+        // n_leg - K started from, and every sphere active in those K legs
+        // is back at its coordinate at the start of its first of them.  Frozen spheres
         // and walls do not move, so the whole frame is then as it was K
         // legs ago and, the dynamics being deterministic with the budget
         // entering a leg only through its end, the following legs repeat
         // the recorded ones for as long as the budget exceeds their length.
         __syncwarp();
         bool per = false;
-        if (lane < kHist3 / 2) {
+        if (lane < kHist3 / 2 && 2 * (lane + 1) <= n_leg) {
           const int K = 2 * (lane + 1);
           const int i0 = (n_leg - K) & (kHist3 - 1);
           if (hM[i0] == m && hSg[i0] == sg && dbits(hP[i0]) == dbits(CA[m])) {

@@ -33,7 +33,7 @@ namespace ecmc {
 // Legs of the current chain kept for cycle detection (a power of two): a
 // chain that rattles through a row of up to kHist/2 disks between two
 // reflectors repeats with a period of at most kHist legs.
-constexpr int kHist = 16;
+constexpr int kHist = 32;
 constexpr size_t kHistLegBytes = 32;  // P, step, contact sum (FP64); disk, flags
 
 struct LegHist {
