@@ -41,19 +41,20 @@ UNIT = "events/s"
 # (smem_bytes_per_event below).
 #
 # Counters of the persistent sweep kernel k_sweep_fused<8 lanes per cell,
-# FP32 screening, frames in shared memory, axis chains> that need more than
-# one ncu pass: captured at N = 640,000, eta = 0.72 with the paper's
-# parameters (188 x 188 cells, about 8,800 active cells per phase, so the
-# occupancy of the N = 1M workload), one launch = one sweep
+# FP32 screening, FP64 frame coordinates in global scratch (frame mode 1, the
+# autotuner's choice at N = 1M), axis chains> that need more than one ncu
+# pass: captured at N = 640,000, eta = 0.72 with the paper's parameters
+# (188 x 188 cells, about 8,800 active cells per phase), one launch = one sweep
 # (profiles/k_sweep_fused_n640k_paper_params.md); the full-size workload is
 # profiled with single-pass metric sets only.  Both scale with the work:
 # DRAM bytes with the disks (every cell and its halo are read once per colour
 # phase), FP64 warp-instructions with the event-loop iterations.
 FUSED_CAPTURE_N = 640000
-FUSED_DRAM_BYTES_CAPTURE = 24628480 + 7424       # dram__bytes_read.sum + _write.sum
-FUSED_FP64_WINST_CAPTURE = 5852193               # smsp__inst_executed_pipe_fp64.sum
+FUSED_CAPTURE_FRAME_MODE = 1
+FUSED_DRAM_BYTES_CAPTURE = 24786176 + 499456     # dram__bytes_read.sum + _write.sum
+FUSED_FP64_WINST_CAPTURE = 5700619               # smsp__inst_executed_pipe_fp64.sum
 FUSED_ITERATIONS_CAPTURE = 1524505               # contacts + walls + chain ends per launch
-FUSED_NCU_FP64_PIPE_PCT = 38.55                  # sm__pipe_fp64_cycles_active, % of active
+FUSED_NCU_FP64_PIPE_PCT = 38.50                  # sm__pipe_fp64_cycles_active, % of active
 
 
 def parse():
@@ -1016,7 +1017,8 @@ def run_ours(args):
         smem_peak, fp64_probe = P.ecmc.device_peaks()
         # the configuration the ncu counters were taken in
         captured = (persistent and tpc == 8 and descs is None and args.dir == "axis" and
-                    args.prec == 1 and int(g.get_param(E.PARAM_FRAME_MODE)) in (0, -1))
+                    args.prec == 1 and
+                    int(g.get_param(E.PARAM_FRAME_MODE)) == FUSED_CAPTURE_FRAME_MODE)
         cpu = None
         if not args.skip_cpu and descs is None:
             cpu = cpu_baseline(w, cells, ell, nm, args.cpu_seconds, melt_sweeps(args),
