@@ -497,9 +497,7 @@ def run_fig3(args):
                       "g_contact": contact_value(R, gm),
                       "g_first_bins": [round(float(v), 4) for v in gm[:12]],
                       "sweeps": per_batch * nbatch * 10,
-                      "rejected_fraction": c.rejected_chains / max(c.chains, 1),
-                      "kernel": "sorted frames" if g.get_param(E.PARAM_STRIPES_KERNEL) == 1
-                                else "block-wide scan"}
+                      "rejected_fraction": c.rejected_chains / max(c.chains, 1)}
                 if rule == "reflect":
                     pt["betaP_sigma2_chain"] = g.pressure()[0]
                 pts.append(pt)
