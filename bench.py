@@ -435,7 +435,8 @@ def run_fig3(args):
     advances about beta P / rho ~ 11 times its budget, so longer chains
     rarely stay inside an 8.4 sigma cell); each with start lists drawn with
     replacement and shuffled.  Every point starts from one configuration
-    melted by the paper's algorithm, equilibrates for S / (4 n_m) sweeps and
+    melted by the paper's algorithm (2000 sweeps with n_m = 4 and ell = 8
+    sigma, or --melt), equilibrates for S / (4 n_m) sweeps and
     measures g(r) every 10 sweeps over S / n_m sweeps, the same number of
     chains for every n_m.  Error bars from 8 batches."""
     import torch
@@ -450,7 +451,7 @@ def run_fig3(args):
     dr, rmax, nbatch = 0.01, 1.5, 8
     g0 = P.Ecmc(N, L, 1.0, w.cells, w.cells, w.ell, w.seed)
     g0.set_param(E.PARAM_N_CHAINS, 4)
-    g0.sweep(2000)
+    g0.sweep(2000 if args.melt < 0 else args.melt)
     xy0 = g0.positions().copy()
     t0 = g0.sweep_index()
     g0.close()
