@@ -41,20 +41,37 @@ UNIT = "events/s"
 # (smem_bytes_per_event below).
 #
 # Counters of the persistent sweep kernel k_sweep_fused<8 lanes per cell,
-# FP32 screening, FP64 frame coordinates in global scratch (frame mode 1, the
-# autotuner's choice at N = 1M), axis chains> that need more than one ncu
-# pass: captured at N = 640,000, eta = 0.72 with the paper's parameters
+# FP32 screening, axis chains> that need more than one ncu pass, for both
+# placements of the FP64 frame coordinates the autotuner chooses between
+# (frame mode 1, global scratch: its choice at N = 1M; frame mode 0, shared
+# memory): captured at N = 640,000, eta = 0.72 with the paper's parameters
 # (188 x 188 cells, about 8,800 active cells per phase), one launch = one sweep
 # (profiles/k_sweep_fused_n640k_paper_params.md); the full-size workload is
 # profiled with single-pass metric sets only.  Both scale with the work:
 # DRAM bytes with the disks (every cell and its halo are read once per colour
 # phase), FP64 warp-instructions with the event-loop iterations.
 FUSED_CAPTURE_N = 640000
-FUSED_CAPTURE_FRAME_MODE = 1
-FUSED_DRAM_BYTES_CAPTURE = 24786176 + 499456     # dram__bytes_read.sum + _write.sum
-FUSED_FP64_WINST_CAPTURE = 5700619               # smsp__inst_executed_pipe_fp64.sum
 FUSED_ITERATIONS_CAPTURE = 1524505               # contacts + walls + chain ends per launch
-FUSED_NCU_FP64_PIPE_PCT = 38.50                  # sm__pipe_fp64_cycles_active, % of active
+FUSED_CAPTURES = {
+    # frame mode: dram__bytes_read.sum + _write.sum, smsp__inst_executed_pipe_fp64.sum,
+    # sm__pipe_fp64_cycles_active (% of active cycles)
+    1: {"dram_bytes": 24786176 + 499456, "fp64_winst": 5700619, "fp64_pipe_pct": 38.50},
+    0: {"dram_bytes": 24627456 + 3072, "fp64_winst": 5701047, "fp64_pipe_pct": 37.30},
+}
+FUSED_CAPTURE_FRAME_MODE = 1                     # the autotuner's choice at N = 1M
+FUSED_DRAM_BYTES_CAPTURE = FUSED_CAPTURES[1]["dram_bytes"]
+FUSED_FP64_WINST_CAPTURE = FUSED_CAPTURES[1]["fp64_winst"]
+FUSED_NCU_FP64_PIPE_PCT = FUSED_CAPTURES[1]["fp64_pipe_pct"]
+
+
+def fused_capture(captured):
+    """The ncu counters for the run's configuration: a frame mode with a
+    capture, True for the autotuner's usual choice, or None."""
+    if captured is True:
+        return FUSED_CAPTURES[FUSED_CAPTURE_FRAME_MODE]
+    if captured is False or captured is None:
+        return None
+    return FUSED_CAPTURES.get(captured)
 
 
 def parse():
@@ -1015,9 +1032,9 @@ def run_ours(args):
         sm_mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
         smem_peak, fp64_probe = P.ecmc.device_peaks()
         # the configuration the ncu counters were taken in
-        captured = (persistent and tpc == 8 and descs is None and args.dir == "axis" and
-                    args.prec == 1 and
-                    int(g.get_param(E.PARAM_FRAME_MODE)) == FUSED_CAPTURE_FRAME_MODE)
+        fm_used = int(g.get_param(E.PARAM_FRAME_MODE))
+        captured = (fm_used if (persistent and tpc == 8 and descs is None and args.dir == "axis"
+                                and args.prec == 1 and fm_used in FUSED_CAPTURES) else None)
         cpu = None
         if not args.skip_cpu and descs is None:
             cpu = cpu_baseline(w, cells, ell, nm, args.cpu_seconds, melt_sweeps(args),
@@ -1097,14 +1114,15 @@ def chain_roofline(w, descs, c, iters, kt, prec, smem_peak, persistent, captured
     launch_ms = kt.phase_ms / launches
     events_per_launch = c.events / launches
     achieved = per * events_per_launch / (launch_ms * 1e-3) / 1e9
-    traffic = (FUSED_DRAM_BYTES_CAPTURE * w.N / FUSED_CAPTURE_N) if captured else None
+    cap = fused_capture(captured)
+    traffic = (cap["dram_bytes"] * w.N / FUSED_CAPTURE_N) if cap else None
     return {"kernel": "k_sweep_fused (persistent sweep kernel)" if persistent
                       else "k_phase (chain kernel)",
             "bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
             "frac": achieved / smem_peak if smem_peak else None, "traffic": traffic,
             "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch "
                                "at N=%d, scaled by the disks" % FUSED_CAPTURE_N)
-                              if captured else None,
+                              if cap else None,
             "bytes_per_event": per, "candidates_per_event": disks, "mean_free_path": lam0,
             "events_per_launch": events_per_launch, "launch_ms": launch_ms,
             "peak_source": "ld.shared.v4 probe on this device in this run (no shared-memory "
@@ -1117,18 +1135,19 @@ def fp64_pipe(iters, kt, n_sm, sm_mhz, fp64_probe_gflops, persistent, captured):
     this run's iterations) x SM cycles one FP64 warp-instruction occupies
     (from the FMA probe: SMs x clock / (FMA/s / 32 lanes)) / SM cycles of the
     launch (SMs x clock x average launch time)."""
-    if not (persistent and captured) or kt.phase_launches <= 0 or not fp64_probe_gflops:
+    cap = fused_capture(captured)
+    if not (persistent and cap) or kt.phase_launches <= 0 or not fp64_probe_gflops:
         return None
     launch_s = kt.phase_ms / kt.phase_launches * 1e-3
-    winst = FUSED_FP64_WINST_CAPTURE / FUSED_ITERATIONS_CAPTURE * iters / kt.phase_launches
+    winst = cap["fp64_winst"] / FUSED_ITERATIONS_CAPTURE * iters / kt.phase_launches
     clk = sm_mhz * 1e6
     cyc_per_winst = n_sm * clk / (fp64_probe_gflops * 1e9 / 2.0 / 32.0)
     sm_cycles = n_sm * clk * launch_s
     return {"warp_instructions_per_launch": winst,
-            "warp_instructions_per_iteration": FUSED_FP64_WINST_CAPTURE / FUSED_ITERATIONS_CAPTURE,
+            "warp_instructions_per_iteration": cap["fp64_winst"] / FUSED_ITERATIONS_CAPTURE,
             "cycles_per_warp_instruction": cyc_per_winst, "sm_cycles_per_launch": sm_cycles,
             "frac": winst * cyc_per_winst / sm_cycles,
-            "ncu_pipe_active_pct_at_capture": FUSED_NCU_FP64_PIPE_PCT,
+            "ncu_pipe_active_pct_at_capture": cap["fp64_pipe_pct"],
             "probe_fp64_gflops": fp64_probe_gflops,
             "source": "FP64 warp-instructions per iteration from ncu at N=%d" % FUSED_CAPTURE_N}
 

@@ -40,6 +40,12 @@ def test_smem_roofline_counts_the_strip_that_can_hold_the_first_hit():
                                            / bench.FUSED_CAPTURE_N)
     assert bench.chain_roofline(w, None, c, 1000, kt, 1, 40000.0, 1, False)["traffic"] is None
     assert bench.chain_roofline(w, [1], c, 1000, kt, 1, 40000.0, 1, True) is None
+    # the counters follow the frame mode the run used; frame mode 0 (falsy)
+    # still selects its own capture, an uncaptured mode gives none
+    out0 = bench.chain_roofline(w, None, c, 1000, kt, 1, 40000.0, 1, 0)
+    assert out0["traffic"] == pytest.approx(bench.FUSED_CAPTURES[0]["dram_bytes"] * w.N
+                                            / bench.FUSED_CAPTURE_N)
+    assert bench.chain_roofline(w, None, c, 1000, kt, 1, 40000.0, 1, 2)["traffic"] is None
 
 
 def test_fp64_pipe_counts_warp_instructions():
@@ -52,6 +58,8 @@ def test_fp64_pipe_counts_warp_instructions():
     assert out["cycles_per_warp_instruction"] == pytest.approx(cyc)
     assert out["frac"] == pytest.approx(winst * cyc / (152 * 2000e6 * 1e-3))
     assert bench.fp64_pipe(iters, kt, 152, 2000.0, 1024.0, 1, False) is None
+    out0 = bench.fp64_pipe(iters, kt, 152, 2000.0, 1024.0, 1, 0)
+    assert out0["warp_instructions_per_launch"] == pytest.approx(bench.FUSED_CAPTURES[0]["fp64_winst"])
 
 
 def test_latency_ceiling_arithmetic():
