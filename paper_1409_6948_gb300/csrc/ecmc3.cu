@@ -368,8 +368,13 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
       pb[1] = ldpos<CG>(py + idb);
       pb[2] = ldpos<CG>(pz + idb);
     }
-    append(ina, ida, pa);
-    if (t0 + 32 < ntot) append(inb, idb, pb);
+    // one copy of the append code for both rounds
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1 && t0 + 32 >= ntot) break;
+      const double q[3] = {h ? pb[0] : pa[0], h ? pb[1] : pa[1], h ? pb[2] : pa[2]};
+      append(h ? inb : ina, h ? idb : ida, q);
+    }
   }
   const bool ok = nobj <= g.cap_obj;
   if (!ok && lane == 0) atomicCAS(err, kOk, kCapacity);
