@@ -158,6 +158,72 @@ __device__ __forceinline__ bool first_before(double s, long long k, double bs, l
   return lt_nn(s, bs) || (dbits(s) == dbits(bs) && k < bk);
 }
 
+// Cold paths of cell3, kept out of line so that the hot loop's code stays
+// small.  Every periodic image of the offset (x0, x1, x2) whose centre lies
+// in the open slab (lo, hi)^3 (boxes below the single-image size): bit
+// img = (kx+1)*9 + (ky+1)*3 + (kz+1).
+__device__ __noinline__ unsigned images_mask3(double x0, double x1, double x2, double L,
+                                              double lo, double hi) {
+  unsigned mask = 0u;
+  for (int kx = -1; kx <= 1; ++kx) {
+    const double X = x0 + (double)kx * L;
+    if (!(X > lo && X < hi)) continue;
+    for (int ky = -1; ky <= 1; ++ky) {
+      const double Y = x1 + (double)ky * L;
+      if (!(Y > lo && Y < hi)) continue;
+      for (int kz = -1; kz <= 1; ++kz) {
+        const double Z = x2 + (double)kz * L;
+        if (!(Z > lo && Z < hi)) continue;
+        mask |= 1u << ((kx + 1) * 9 + (ky + 1) * 3 + (kz + 1));
+      }
+    }
+  }
+  return mask;
+}
+
+// A lane's best candidate: hit distance, b, tie-break key, frame index.
+struct Hit3 {
+  double s, b;
+  long long k;
+  int j;
+};
+
+// The warp's first hit by (s, key) through a shuffle tree, for keys that do
+// not fit 32 bits (N >= 2^32 / 27).
+__device__ __noinline__ Hit3 first_hit_tree(Hit3 h) {
+#pragma unroll 1
+  for (int off = 16; off > 0; off >>= 1) {
+    const double os = __shfl_xor_sync(0xffffffffu, h.s, off);
+    const double ob = __shfl_xor_sync(0xffffffffu, h.b, off);
+    const long long ok2 = __shfl_xor_sync(0xffffffffu, h.k, off);
+    const int oj = __shfl_xor_sync(0xffffffffu, h.j, off);
+    if (first_before(os, ok2, h.s, h.k)) {
+      h.s = os;
+      h.b = ob;
+      h.k = ok2;
+      h.j = oj;
+    }
+  }
+  return h;
+}
+
+// The distinct neighbour cells with two cells per side, where the cells at
+// offsets -1 and +1 coincide (lane 0 only).
+__device__ __noinline__ void neighbour_list_small(int* nbl, int cx, int cy, int cz, int nc, int c) {
+  int n = 0;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int qx = (cx + dx + nc) % nc, qy = (cy + dy + nc) % nc, qz = (cz + dz + nc) % nc;
+        const int q = (qz * nc + qy) * nc + qx;
+        if (q == c) continue;
+        bool dup = false;
+        for (int e = 0; e < n; ++e) dup |= nbl[e] == q;
+        if (!dup) nbl[n++] = q;
+      }
+  nbl[26] = n;
+}
+
 // Position loads: through L1 in the per-phase kernels (the writers finished
 // in an earlier launch), from L2 in the persistent kernel (the writers may
 // be warps of other SMs in the same launch).
@@ -231,19 +297,7 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
     }
     if (lane == 0) nbl[26] = 26;
   } else if (lane == 0) {
-    // two cells per side: the cells at offsets -1 and +1 coincide
-    int n = 0;
-    for (int dz = -1; dz <= 1; ++dz)
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int qx = (cx + dx + nc) % nc, qy = (cy + dy + nc) % nc, qz = (cz + dz + nc) % nc;
-          const int q = (qz * nc + qy) * nc + qx;
-          if (q == c) continue;
-          bool dup = false;
-          for (int e = 0; e < n; ++e) dup |= nbl[e] == q;
-          if (!dup) nbl[n++] = q;
-        }
-    nbl[26] = n;
+    neighbour_list_small(nbl, cx, cy, cz, nc, c);
   }
   __syncwarp();
   // the neighbours' objects as one list: npre[e] = sum of the bucket sizes
@@ -308,19 +362,7 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
             dlt(lo, X0[2]) && dlt(X0[2], hi))
           mask = 1u << 13;
       } else {
-        for (int kx = -1; kx <= 1; ++kx) {
-          const double X = X0[0] + (double)kx * L;
-          if (!(X > lo && X < hi)) continue;
-          for (int ky = -1; ky <= 1; ++ky) {
-            const double Y = X0[1] + (double)ky * L;
-            if (!(Y > lo && Y < hi)) continue;
-            for (int kz = -1; kz <= 1; ++kz) {
-              const double Z = X0[2] + (double)kz * L;
-              if (!(Z > lo && Z < hi)) continue;
-              mask |= 1u << ((kx + 1) * 9 + (ky + 1) * 3 + (kz + 1));
-            }
-          }
-        }
+        mask = images_mask3(X0[0], X0[1], X0[2], L, lo, hi);
       }
     }
     const int nimg = __popc(mask);
@@ -522,19 +564,11 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
         bk = __shfl_sync(FULL, bk, win);
         bj = __shfl_sync(FULL, bj, win);
       } else {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          const double os = __shfl_xor_sync(FULL, bs, off);
-          const double ob = __shfl_xor_sync(FULL, bb, off);
-          const long long ok2 = __shfl_xor_sync(FULL, bk, off);
-          const int oj = __shfl_xor_sync(FULL, bj, off);
-          if (first_before(os, ok2, bs, bk)) {
-            bs = os;
-            bb = ob;
-            bk = ok2;
-            bj = oj;
-          }
-        }
+        const Hit3 hw = first_hit_tree(Hit3{bs, bb, bk, bj});
+        bs = hw.s;
+        bb = hw.b;
+        bk = hw.k;
+        bj = hw.j;
       }
       __syncwarp();
       if (le_nn(r, bs) && le_nn(r, sw)) {  // budget used up
