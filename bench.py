@@ -55,8 +55,8 @@ FUSED_ITERATIONS_CAPTURE = 1524505               # contacts + walls + chain ends
 FUSED_CAPTURES = {
     # frame mode: dram__bytes_read.sum + _write.sum, smsp__inst_executed_pipe_fp64.sum,
     # sm__pipe_fp64_cycles_active (% of active cycles)
-    1: {"dram_bytes": 24786176 + 499456, "fp64_winst": 5700619, "fp64_pipe_pct": 38.50},
-    0: {"dram_bytes": 24627456 + 3072, "fp64_winst": 5701047, "fp64_pipe_pct": 37.30},
+    1: {"dram_bytes": 24786688 + 492544, "fp64_winst": 5594937, "fp64_pipe_pct": 37.95},
+    0: {"dram_bytes": 24617216 + 1792, "fp64_winst": 5594741, "fp64_pipe_pct": 37.01},
 }
 FUSED_CAPTURE_FRAME_MODE = 1                     # the autotuner's choice at N = 1M
 FUSED_DRAM_BYTES_CAPTURE = FUSED_CAPTURES[1]["dram_bytes"]

@@ -222,41 +222,47 @@ __device__ void build_frame(const BuildArgs& A) {
   // only grows).
   int nbuf = 0;  // warp-uniform fill of this warp's buffer (< 32 between chunks)
   int e_run = 0;
-  for (int base = warp * 32; base < T; base += bt) {
-    const int idx = base + lane;
-    bool keep = false;
-    int2 ent = make_int2(0, 0);
-    if (idx < T) {
-      int e = e_run;
-      while (e + 1 < nnb && s_pre[e + 1] <= idx) ++e;
-      e_run = e;
-      const int k = idx - s_pre[e];
-      const int64_t q = (int64_t)s_nb[e] * cap + k;
-      const float rxf = to_float_trunc(load_pos<CG>(A.px + q)) - oxf;
-      const float ryf = to_float_trunc(load_pos<CG>(A.py + q)) - oyf;
-      unsigned imgx = 0, imgy = 0;
-      for (int j = -1; j <= 1; ++j) {
-        const float Xf = rxf + (float)j * Lf, Yf = ryf + (float)j * Lf;
-        imgx |= (Xf > xlo && Xf < xhi) ? (1u << (j + 2)) : 0u;
-        imgy |= (Yf > ylo && Yf < yhi) ? (1u << (j + 2)) : 0u;
+  // one call site of place() (the final partial buffer is flushed in the
+  // pass after the last chunk), so that its code is emitted once
+  for (int base = warp * 32;; base += bt) {
+    const bool more = base < T;  // warp-uniform
+    if (more) {
+      const int idx = base + lane;
+      bool keep = false;
+      int2 ent = make_int2(0, 0);
+      if (idx < T) {
+        int e = e_run;
+        while (e + 1 < nnb && s_pre[e + 1] <= idx) ++e;
+        e_run = e;
+        const int k = idx - s_pre[e];
+        const int64_t q = (int64_t)s_nb[e] * cap + k;
+        const float rxf = to_float_trunc(load_pos<CG>(A.px + q)) - oxf;
+        const float ryf = to_float_trunc(load_pos<CG>(A.py + q)) - oyf;
+        unsigned imgx = 0, imgy = 0;
+        for (int j = -1; j <= 1; ++j) {
+          const float Xf = rxf + (float)j * Lf, Yf = ryf + (float)j * Lf;
+          imgx |= (Xf > xlo && Xf < xhi) ? (1u << (j + 2)) : 0u;
+          imgy |= (Yf > ylo && Yf < yhi) ? (1u << (j + 2)) : 0u;
+        }
+        keep = imgx && imgy;
+        ent = make_int2((int)(((unsigned)e << 29) | (unsigned)k), (int)(imgx | (imgy << 5)));
       }
-      keep = imgx && imgy;
-      ent = make_int2((int)(((unsigned)e << 29) | (unsigned)k), (int)(imgx | (imgy << 5)));
+      const unsigned bal = __ballot_sync(FULL, keep);
+      if (keep) wbuf[nbuf + __popc(bal & ((1u << lane) - 1u))] = ent;
+      nbuf += __popc(bal);
+      __syncwarp();
     }
-    const unsigned bal = __ballot_sync(FULL, keep);
-    if (keep) wbuf[nbuf + __popc(bal & ((1u << lane) - 1u))] = ent;
-    nbuf += __popc(bal);
-    __syncwarp();
-    if (nbuf >= 32) {
+    if (nbuf >= 32 || (!more && nbuf > 0)) {
       const int2 v = wbuf[lane];
+      const bool has = lane < nbuf;
       __syncwarp();
       if (lane < nbuf - 32) wbuf[lane] = wbuf[lane + 32];
-      nbuf -= 32;
+      nbuf = nbuf > 32 ? nbuf - 32 : 0;
       __syncwarp();
-      place(v);
+      if (has) place(v);
     }
+    if (!more) break;
   }
-  if (lane < nbuf) place(wbuf[lane]);
   for (int k = tid; k <= lay.nbin; k += bt) s_hist[k] = 0;
   sync();
   if (s_scal[1]) {
