@@ -436,8 +436,18 @@ __device__ __forceinline__ void cell3(const Geom3& g, const State3& st, int colo
   for (int o2 = lane; o2 < nobj_ok; o2 += 32)
     atomicAdd(&bst[1 + bin_of(F[axq][o2]) * nb + bin_of(F[axp][o2])], 1);
   __syncwarp();
-  if (lane == 0)
+  if (nb2 < 32) {
+    // bin starts by a warp scan of the counts (bst[0] = 0)
+    int v = lane <= nb2 ? bst[lane] : 0;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int u = __shfl_up_sync(FULL, v, off);
+      if (lane >= off) v += u;
+    }
+    if (lane <= nb2) bst[lane] = v;
+  } else if (lane == 0) {
     for (int i = 1; i <= nb2; ++i) bst[i] += bst[i - 1];
+  }
   __syncwarp();
   for (int i = lane; i < nb2; i += 32) cur[i] = bst[i];
   __syncwarp();
